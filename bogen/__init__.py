@@ -1,0 +1,204 @@
+"""Seeded synthetic inputs for the black-oil Jacobian solver.
+
+This package builds the Newton systems A dx = b that both the GPU solver and
+the CPU oracle consume: seeded permeability/porosity fields, reservoir states
+and wells (``fields``), and the fully implicit black-oil residual and exact
+Jacobian (``assembly.cpp``; paper Sec. 2.1 Eq. 3, Sec. 2.3 Eq. 4, Alg. 1).
+It holds none of the linear solver's arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libbogen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile assembly.cpp into libbogen.so (plain g++, no arch flags)."""
+    src = os.path.join(_HERE, "assembly.cpp")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", src, "-o", _LIB_PATH])
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB_PATH)
+        _lib.bg_peaceman_wi.restype = ctypes.c_double
+        _lib.bg_peaceman_wi.argtypes = [ctypes.c_double] * 7
+        _lib.bg_cell_mass.restype = ctypes.c_double
+        _lib.bg_cell_mass.argtypes = [ctypes.POINTER(Fluid), ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        _lib.bg_nnzb.restype = ctypes.c_int64
+        _lib.bg_assemble.restype = ctypes.c_int
+    return _lib
+
+
+class Fluid(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "pref", "bw0", "cw", "muw", "bo0", "dbo", "rs0", "drs", "muo", "bg0", "dbg", "mug",
+        "rhow_sc", "rhoo_sc", "rhog_sc", "cr", "swc", "sorw", "sorg", "sgc",
+        "nw", "now", "ng", "nog", "gravity")]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("p_left", ctypes.c_double), ("p_right", ctypes.c_double)]
+
+
+def default_fluid(**over) -> Fluid:
+    """Fluid/rock constants used for every synthetic case (the paper gives
+    none for synthetic data): linear FVF and Rs tables about 3000 psi, Corey
+    exponent 2 curves with s_wc = 0.1, s_orw = s_org = 0.1, s_gc = 0."""
+    v = dict(pref=3000.0, bw0=1.0, cw=3e-6, muw=0.5,
+             bo0=1.25, dbo=6e-5, rs0=0.6, drs=1.5e-4, muo=1.0,
+             bg0=0.9, dbg=1.5e-4, mug=0.02,
+             rhow_sc=62.4, rhoo_sc=50.0, rhog_sc=0.06, cr=4e-6,
+             swc=0.1, sorw=0.1, sorg=0.1, sgc=0.0,
+             nw=2.0, now=2.0, ng=2.0, nog=2.0, gravity=1.0)
+    v.update(over)
+    return Fluid(**v)
+
+
+def incompressible_fluid(**over) -> Fluid:
+    """Test fluid: constant FVFs, Rs and porosity, no gravity."""
+    v = dict(cw=0.0, dbo=0.0, drs=0.0, dbg=0.0, cr=0.0, gravity=0.0)
+    v.update(over)
+    return default_fluid(**v)
+
+
+@dataclass
+class Well:
+    kind: int            # 0 water injector, 1 producer
+    bhp: float           # psi at dref
+    cells: np.ndarray    # perforated cell indices (int32)
+    dref: float = 0.0    # reference depth of bhp; default: the top perforation
+
+
+@dataclass
+class Case:
+    """One Newton system's worth of synthetic input."""
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    kx: np.ndarray
+    ky: np.ndarray
+    kz: np.ndarray
+    phi0: np.ndarray
+    depth: np.ndarray
+    x: np.ndarray        # state (p, Sw, Sg) interleaved, 3N
+    xn: np.ndarray       # previous time level
+    dt: float
+    wells: list = field(default_factory=list)
+    fluid: Fluid = None
+    bc: BC = None
+    rw: float = 0.25
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def grid(self) -> Grid:
+        return Grid(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz)
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def well_index(case: Case, c: int) -> float:
+    L = lib()
+    return L.bg_peaceman_wi(float(case.kx[c]), float(case.ky[c]), case.dx, case.dy, case.dz, case.rw, 0.0)
+
+
+def pattern(nx, ny, nz):
+    """7-point BSR pattern (rowptr int32[N+1], col int32[nnzb])."""
+    L = lib()
+    g = Grid(nx, ny, nz, 1.0, 1.0, 1.0)
+    nnzb = L.bg_nnzb(ctypes.byref(g))
+    rowptr = np.zeros(nx * ny * nz + 1, np.int32)
+    col = np.zeros(nnzb, np.int32)
+    L.bg_pattern(ctypes.byref(g), _ptr(rowptr, ctypes.c_int32), _ptr(col, ctypes.c_int32))
+    return rowptr, col
+
+
+def assemble(case: Case, jacobian: bool = True, x=None):
+    """Residual R (3N) and BSR Jacobian of ``case``.
+
+    Returns dict(rowptr, col, val (nnzb,3,3), R, b=-R).  Raises on a bad state.
+    """
+    L = lib()
+    g = case.grid()
+    fl = case.fluid if case.fluid is not None else default_fluid()
+    rowptr, col = pattern(case.nx, case.ny, case.nz)
+    nnzb = col.size
+    R = np.zeros(3 * case.N)
+    val = np.zeros((nnzb, 3, 3)) if jacobian else None
+    xs = _d(case.x if x is None else x)
+    wt = _i([w.kind for w in case.wells]) if case.wells else np.zeros(1, np.int32)
+    bhp = _d([w.bhp for w in case.wells]) if case.wells else np.zeros(1)
+    dref = _d([w.dref if w.dref else case.depth[int(np.min(w.cells))] for w in case.wells]) if case.wells else np.zeros(1)
+    pptr = [0]
+    cells, wis = [], []
+    for w in case.wells:
+        for c in np.asarray(w.cells).ravel():
+            cells.append(int(c))
+            wis.append(well_index(case, int(c)))
+        pptr.append(len(cells))
+    pptr = _i(pptr)
+    cells = _i(cells if cells else [0])
+    wis = _d(wis if wis else [0.0])
+    kx, ky, kz, phi0, depth, xn = map(_d, (case.kx, case.ky, case.kz, case.phi0, case.depth, case.xn))
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    rc = L.bg_assemble(ctypes.byref(g), ctypes.byref(fl),
+                       _ptr(kx, ctypes.c_double), _ptr(ky, ctypes.c_double), _ptr(kz, ctypes.c_double),
+                       _ptr(phi0, ctypes.c_double), _ptr(depth, ctypes.c_double),
+                       _ptr(xs, ctypes.c_double), _ptr(xn, ctypes.c_double), ctypes.c_double(case.dt),
+                       ctypes.c_int32(len(case.wells)), _ptr(wt, ctypes.c_int32), _ptr(bhp, ctypes.c_double),
+                       _ptr(dref, ctypes.c_double), _ptr(pptr, ctypes.c_int32), _ptr(cells, ctypes.c_int32),
+                       _ptr(wis, ctypes.c_double),
+                       ctypes.byref(case.bc) if case.bc is not None else None,
+                       _ptr(rowptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                       _ptr(R, ctypes.c_double),
+                       _ptr(val, ctypes.c_double) if val is not None else ctypes.cast(None, dp))
+    if rc != 0:
+        raise ValueError("assembly failed: non-positive pore volume or FVF")
+    return dict(rowptr=rowptr, col=col, val=val, R=R, b=-R)
+
+
+def cell_mass(fluid: Fluid, phi0, p, sw, sg, comp) -> float:
+    return lib().bg_cell_mass(ctypes.byref(fluid), phi0, p, sw, sg, comp)
+
+
+def relperm(fluid: Fluid, sw: float, sg: float):
+    out = np.zeros(3)
+    lib().bg_relperm(ctypes.byref(fluid), ctypes.c_double(sw), ctypes.c_double(sg), _ptr(out, ctypes.c_double))
+    return out
+
+
+from .fields import tiny_case, waterflood_case, gaussian_field, uniform_case  # noqa: E402,F401

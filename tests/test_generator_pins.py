@@ -1,0 +1,205 @@
+"""Pins of the black-oil Jacobian generator against physics that fixes the
+answer independently of the code: symmetric zero-row-sum transmissibility
+Laplacian under no-flow (paper Sec. 2.1 boundary condition), per-component
+mass balance, exact derivatives vs central differences, the linear pressure
+profile of incompressible flow between two constant-pressure faces, Stone II
+end-point identities and Peaceman's equivalent radius."""
+import numpy as np
+import pytest
+
+import bogen
+from bogen import BC, Well, incompressible_fluid, default_fluid
+
+
+def _dense(a):
+    nb = a["rowptr"].size - 1
+    A = np.zeros((3 * nb, 3 * nb))
+    for i in range(nb):
+        for e in range(a["rowptr"][i], a["rowptr"][i + 1]):
+            j = a["col"][e]
+            A[3 * i:3 * i + 3, 3 * j:3 * j + 3] += a["val"][e]
+    return A
+
+
+def _hetero_case(nx=6, ny=5, nz=4, seed=3, fluid=None):
+    rng = np.random.default_rng(seed)
+    c = bogen.uniform_case(nx, ny, nz, fluid=fluid)
+    N = c.N
+    c.kx = np.exp(rng.normal(4, 1.0, N))
+    c.ky = np.exp(rng.normal(4, 1.0, N))
+    c.kz = 0.1 * np.exp(rng.normal(4, 1.0, N))
+    return c, rng
+
+
+def test_pattern_is_seven_point_sorted():
+    rowptr, col = bogen.pattern(4, 3, 2)
+    N = 24
+    for c in range(N):
+        cols = col[rowptr[c]:rowptr[c + 1]]
+        assert np.all(np.diff(cols) > 0)
+        i, j, k = c % 4, (c // 4) % 3, c // 12
+        exp = {c}
+        if i > 0: exp.add(c - 1)
+        if i < 3: exp.add(c + 1)
+        if j > 0: exp.add(c - 4)
+        if j < 2: exp.add(c + 4)
+        if k > 0: exp.add(c - 12)
+        if k < 1: exp.add(c + 12)
+        assert set(cols.tolist()) == exp
+
+
+def test_transmissibility_block_symmetric_zero_row_sums():
+    # incompressible fluid, uniform saturations, no gravity, no wells: the
+    # (oil equation, pressure) entries are lambda_o times the weighted graph
+    # Laplacian of the two-point transmissibilities
+    c, _ = _hetero_case(fluid=incompressible_fluid())
+    a = bogen.assemble(c)
+    A = _dense(a)
+    T = A[0::3, 0::3]
+    scale = np.abs(T).max()
+    assert scale > 0
+    assert np.abs(T - T.T).max() <= 1e-15 * scale * 10
+    assert np.abs(T.sum(axis=1)).max() <= 1e-12 * scale
+    # off-diagonals non-positive, diagonal positive (an M-matrix Laplacian)
+    off = T - np.diag(np.diag(T))
+    assert off.max() <= 0 and np.diag(T).min() > 0
+
+
+def test_face_transmissibility_is_harmonic():
+    c = bogen.uniform_case(2, 1, 1, fluid=incompressible_fluid())
+    c.kx = np.array([50.0, 200.0])
+    a = bogen.assemble(c)
+    A = _dense(a)
+    fl = c.fluid
+    kro = bogen.relperm(fl, 0.2, 0.05)[1]
+    lam_o = kro / (fl.muo * fl.bo0)
+    T = 0.001127 * (100.0 * 20.0) / (100.0 / 2 / 50.0 + 100.0 / 2 / 200.0)
+    assert A[0, 3] == pytest.approx(-T * lam_o, rel=1e-13)
+
+
+@pytest.mark.parametrize("with_wells", [False, True])
+def test_component_mass_balance(with_wells):
+    # summing R over all cells cancels every interior flux: what remains is
+    # the accumulation minus the well terms (no-flow outer boundary)
+    c, rng = _hetero_case()
+    N = c.N
+    c.x = c.xn * rng.uniform(0.95, 1.05, 3 * N)
+    if with_wells:
+        c.wells = [Well(0, 3400.0, np.array([0, 30, 60, 90], np.int32)),
+                   Well(1, 2600.0, np.array([29, 59, 89, 119], np.int32))]
+    a = bogen.assemble(c)
+    V = c.dx * c.dy * c.dz
+    acc = np.zeros(3)
+    for i in range(N):
+        for comp in range(3):
+            m1 = bogen.cell_mass(c.fluid, c.phi0[i], *c.x[3 * i:3 * i + 3], comp)
+            m0 = bogen.cell_mass(c.fluid, c.phi0[i], *c.xn[3 * i:3 * i + 3], comp)
+            acc[comp] += V / (5.615 * c.dt) * (m1 - m0)
+    tot = a["R"].reshape(N, 3).sum(axis=0)
+    if not with_wells:
+        assert np.allclose(tot, acc, rtol=1e-10, atol=1e-9 * np.abs(a["R"]).max())
+    else:
+        q = acc - tot  # the well terms
+        # water injector adds water only; the producer removes oil and gas
+        assert q[1] != 0 and q[0] < 0 and q[2] < 0
+
+
+def test_flux_jacobian_column_sums_vanish():
+    # with no accumulation (dt -> infinity) and no wells sum_i R_c,i == 0 for
+    # every state, so every column of each component's Jacobian sums to zero
+    c, rng = _hetero_case()
+    c.dt = 1e30
+    c.x = c.xn * rng.uniform(0.95, 1.05, 3 * c.N)
+    A = _dense(bogen.assemble(c))
+    scale = np.abs(A).max()
+    for comp in range(3):
+        cs = A[comp::3, :].sum(axis=0)
+        assert np.abs(cs).max() <= 1e-11 * scale
+
+
+def test_exact_jacobian_matches_central_differences():
+    c, rng = _hetero_case(nx=4, ny=3, nz=3)
+    c.x = c.xn * rng.uniform(0.95, 1.05, 3 * c.N)
+    c.wells = [Well(0, 3400.0, np.array([0, 12, 24], np.int32)), Well(1, 2600.0, np.array([11, 23, 35], np.int32))]
+    A = _dense(bogen.assemble(c))
+    n = 3 * c.N
+    J = np.zeros((n, n))
+    for u in range(n):
+        h = 1e-6 * max(abs(c.x[u]), 1e-3)
+        xp = c.x.copy(); xp[u] += h
+        xm = c.x.copy(); xm[u] -= h
+        J[:, u] = (bogen.assemble(c, jacobian=False, x=xp)["R"] - bogen.assemble(c, jacobian=False, x=xm)["R"]) / (2 * h)
+    for u in range(n):
+        col_scale = max(np.abs(A[:, u]).max(), 1e-12)
+        assert np.abs(J[:, u] - A[:, u]).max() <= 1e-5 * col_scale
+
+
+def _linear_profile_case(kx_columns):
+    nx = len(kx_columns)
+    fl = incompressible_fluid()
+    c = bogen.uniform_case(nx, 3, 2, fluid=fl)
+    c.kx = np.tile(np.asarray(kx_columns, float), 6)
+    c.bc = BC(1, 3500.0, 2500.0)
+    return c
+
+
+def test_linear_pressure_profile_homogeneous():
+    # incompressible flow between two constant-pressure faces: one Newton
+    # step from a uniform state lands on p(x) = pL + (pR - pL) x / L at the
+    # cell centres; saturations do not change
+    c = _linear_profile_case([100.0] * 10)
+    a = bogen.assemble(c)
+    dx = np.linalg.solve(_dense(a), a["b"])
+    p = c.x[0::3] + dx[0::3]
+    xc = (np.arange(10) + 0.5) * c.dx
+    exact = 3500.0 + (2500.0 - 3500.0) * xc / (10 * c.dx)
+    assert np.abs(p - np.tile(exact, 6)).max() <= 1e-9 * 3500
+    assert np.abs(dx[1::3]).max() < 1e-9 and np.abs(dx[2::3]).max() < 1e-9
+
+
+def test_linear_pressure_profile_layered_harmonic():
+    # columns of different permeability: constant flux through resistances
+    # in series, p piecewise linear (harmonic two-point transmissibility)
+    k = np.array([10.0, 300.0, 45.0, 2000.0, 80.0, 5.0])
+    c = _linear_profile_case(k)
+    a = bogen.assemble(c)
+    dx = np.linalg.solve(_dense(a), a["b"])
+    p = (c.x[0::3] + dx[0::3])[:6]
+    h = c.dx
+    # resistance (per unit area and mobility, up to a common factor) from the
+    # left face to each cell centre
+    res_to_centre = np.cumsum(np.concatenate([[h / 2 / k[0]], h / 2 / k[:-1] + h / 2 / k[1:]]))
+    total = res_to_centre[-1] + h / 2 / k[-1]
+    exact = 3500.0 - (3500.0 - 2500.0) * res_to_centre / total
+    assert np.abs(p - exact).max() <= 1e-9 * 3500
+
+
+def test_stone2_endpoint_identities():
+    fl = default_fluid()
+    swc = fl.swc
+    for sw in [0.1, 0.2, 0.35, 0.6, 0.85]:
+        # no gas: k_ro reduces to the oil-water curve k_row(Sw)
+        krow = max(0.0, (1 - sw - fl.sorw) / (1 - swc - fl.sorw)) ** 2
+        assert bogen.relperm(fl, sw, 0.0)[1] == pytest.approx(krow, abs=1e-15)
+    for sg in [0.0, 0.05, 0.3, 0.6]:
+        # connate water: k_ro reduces to the gas-oil curve k_rog(Sg)
+        krog = max(0.0, (1 - sg - swc - fl.sorg) / (1 - swc - fl.sorg - fl.sgc)) ** 2
+        assert bogen.relperm(fl, swc, sg)[1] == pytest.approx(krog, abs=1e-15)
+
+
+def test_peaceman_equivalent_radius_square_cell():
+    # isotropic square cell: r_o = 0.28 sqrt(2) dx / 2 ~= 0.198 dx
+    dx, dz, k, rw = 100.0, 20.0, 150.0, 0.25
+    ro = 0.14 * np.sqrt(2.0) * dx
+    assert ro / dx == pytest.approx(0.198, abs=5e-4)
+    wi = bogen.lib().bg_peaceman_wi(k, k, dx, dx, dz, rw, 0.0)
+    assert wi == pytest.approx(0.001127 * 2 * np.pi * k * dz / np.log(ro / rw), rel=1e-14)
+
+
+def test_tiny_case_is_seeded_and_nonsingular():
+    a1 = bogen.assemble(bogen.tiny_case(0))
+    a2 = bogen.assemble(bogen.tiny_case(0))
+    assert np.array_equal(a1["val"], a2["val"]) and np.array_equal(a1["b"], a2["b"])
+    a3 = bogen.assemble(bogen.tiny_case(1))
+    assert not np.array_equal(a1["b"], a3["b"])
+    assert np.all(np.isfinite(a1["val"]))
