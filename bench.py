@@ -1,0 +1,348 @@
+"""Benchmark: time to a 1e-8 relative residual for 1M-cell three-phase
+black-oil Jacobians (128 x 128 x 64 grid, 3.1M unknowns), plus the BSR
+SpMV's HBM bandwidth.
+
+A step is one pass of the whole hot path on one Newton Jacobian resident
+in HBM: value ingest into the solver's layout, Quasi-IMPES decoupling,
+block-ILU(0) factorisation and AMG setup, CPR-FGMRES(30) to
+||b - A x|| <= 1e-8 ||b||, and the Newton update.  The steps cycle through
+ten seeded Jacobians (successive days of a synthetic five-spot waterflood),
+524 MB of matrix values each, so every step's inputs are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, timed alone
+
+One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel. residual, 1M-cell 3-phase Jacobian; BSR SpMV HBM GB/s"
+DIMS = (128, 128, 64)
+SEED = 42
+SAMPLE_DIMS = (64, 64, 32)  # oracle sample: 1/8 of the cells
+
+
+def _nnzb(nx, ny, nz):
+    return nx * ny * nz + 2 * ((nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1))
+
+
+def _make_jacobian(args):
+    dims, seed, day = args
+    import bogen
+    case = bogen.waterflood_case(*dims, seed=seed, day=day)
+    a = bogen.assemble(case)
+    return a["rowptr"], a["col"], a["val"].reshape(-1), a["b"], case.x
+
+
+def generate(dims, seed, days, procs):
+    """Seeded Jacobians for days 0..days-1 (spawned workers; before any CUDA call)."""
+    import bogen
+    bogen.build()
+    jobs = [(dims, seed, d) for d in range(days)]
+    if procs > 1 and days > 1:
+        with mp.get_context("spawn").Pool(min(procs, days)) as pool:
+            return pool.map(_make_jacobian, jobs)
+    return [_make_jacobian(j) for j in jobs]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the GPU works."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        load = [c for c in sm if c > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def aggregate(elapsed_ms, units, world, reduce_max):
+    """Whole-job numbers: the max elapsed time over ranks; every rank solved
+    `units` Jacobians, so the job solved units * world in that time."""
+    t = reduce_max(elapsed_ms)
+    return {"elapsed_ms": t, "ms_per_solve": t / (units * world), "solves_per_s": units * world / (t / 1e3)}
+
+
+def oracle_sample(seed=SEED, maxit=400):
+    """The FP64 oracle (single thread) on the 64x64x32 sample Jacobian: CPR-FGMRES
+    to 1e-8 from zero; returns (seconds, iterations)."""
+    import bogen
+    import oracle
+    case = bogen.waterflood_case(*SAMPLE_DIMS, seed=seed, day=0)
+    a = bogen.assemble(case)
+    A = oracle.BsrMatrix(a["rowptr"], a["col"], a["val"])
+    t0 = time.perf_counter()
+    P = oracle.cpr_prec(A, SAMPLE_DIMS, amg=oracle.AmgParams(coarse_max=128))
+    x, info = oracle.gmres(A, a["b"], tol=1e-8, maxit=maxit, prec=P)
+    return time.perf_counter() - t0, info
+
+
+def cpu_baseline_record(seconds, info):
+    scale = np.prod(DIMS) / np.prod(SAMPLE_DIMS)
+    return {"value": seconds * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle CPR-GMRES(30) (red-black block ILU(0) + AMG, FP64, one thread) on the "
+                       f"{SAMPLE_DIMS[0]}x{SAMPLE_DIMS[1]}x{SAMPLE_DIMS[2]} waterflood Jacobian to 1e-8 "
+                       f"({info['iters']} its, {seconds:.2f} s), scaled by the cell ratio x{scale:.0f}")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample()
+    times, info = [], None
+    for _ in range(args.steps):
+        s, info = oracle_sample()
+        times.append(s)
+    rec = cpu_baseline_record(statistics.mean(times), info)
+    line = {"impl": "reference", "metric": METRIC, "value": rec["value"], "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args), "cpu_baseline": rec,
+            "e2e": {"value": rec["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    nx, ny, nz = DIMS
+    return {"workload": (f"waterflood black-oil Jacobians {nx}x{ny}x{nz} (3 unknowns/cell, 3x3 BSR 7-point), "
+                         f"{args.jacobians} successive days, CPR-FGMRES({args.restart}) to 1e-8, "
+                         f"preconditioner {args.precision}"),
+            "grid": list(DIMS), "unknowns": 3 * nx * ny * nz, "nnzb": _nnzb(*DIMS), "tol": 1e-8,
+            "restart": args.restart, "precision": args.precision, "seed": SEED, "jacobians": args.jacobians,
+            "l2": "inputs larger than L2 (524 MB of matrix values per step, 10 Jacobians resident)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--jacobians", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dist-backend", default="nccl")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # inputs first (spawned generator workers must start before CUDA)
+    jac = generate(DIMS, SEED + 1000 * rank, args.jacobians, procs=min(16, os.cpu_count() or 1))
+    cpu_rec = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        s, info = oracle_sample()
+        cpu_rec = cpu_baseline_record(s, info)
+
+    import torch
+    import paper_1606_00556_gb300 as bo
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(args.dist_backend)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def reduce_max(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if args.dist_backend == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    bo.lib()
+    dev = torch.device("cuda", local)
+    ctx = bo.Context(local)
+    nx, ny, nz = DIMS
+    N = nx * ny * nz
+    n = 3 * N
+    nnzb = _nnzb(*DIMS)
+    rowptr, col = jac[0][0], jac[0][1]
+    vals = [torch.from_numpy(j[2]).to(dev) for j in jac]
+    bs = [torch.from_numpy(j[3]).to(dev) for j in jac]
+    state = torch.from_numpy(jac[0][4]).to(dev)
+    g = bo.grid(*DIMS)
+    A = bo.Matrix.from_bsr(ctx, g, rowptr, col, jac[0][2])
+    prec = bo.BO_PREC_FP32 if args.precision == "fp32" else bo.BO_PREC_FP64
+    P = bo.Preconditioner(A, precision=prec)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k, profile):
+        j = k % len(vals)
+        A.update_values(vals[j])
+        P.update()
+        info = P.solve(bs[j], x, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True, profile=profile)
+        if info["status"] != 0:
+            raise RuntimeError(f"solve failed: {info}")
+        bo.bo_newton_update(ctx, state, x)
+        return info
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for k in range(args.warmup):
+        step(k, True)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = bo.bo_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [step(args.warmup + k, True) for k in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = bo.bo_kernel_launches() - l0
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1)
+    agg = aggregate(elapsed, args.steps, world, reduce_max)
+
+    # the dominant kernel, timed live inside the steps above: the FP64 Arnoldi SpMV
+    tz = 4 if args.precision == "fp32" else 8
+    spmv_bytes = 9 * 8 * nnzb + n * tz + n * 8
+    spmv_ms = sum(i["spmv_ms"] for i in infos)
+    spmv_n = sum(i["spmv_launches"] for i in infos)
+    hbm, peak_kind = peaks()
+    ach = spmv_bytes / (spmv_ms / spmv_n * 1e-3) / 1e9 if spmv_n else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(f"arnoldi_spmv_{args.precision}")
+    except Exception:
+        pass
+
+    # standalone BSR SpMV (bo_mat_spmv, natural-order vectors), FP64 and FP32 values
+    xs = torch.randn(n, dtype=torch.float64, device=dev)
+    ys = torch.zeros_like(xs)
+    sp = {}
+    for name, pr, vb in (("fp64", bo.BO_PREC_FP64, 8), ("fp32", bo.BO_PREC_FP32, 4)):
+        for _ in range(3):
+            A.spmv(xs, ys, precision=pr)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        reps = 20
+        s0.record(stream)
+        for _ in range(reps):
+            A.spmv(xs, ys, precision=pr)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        us = s0.elapsed_time(s1) / reps * 1e3
+        byts = 9 * vb * nnzb + 2 * n * 8
+        sp[name] = {"us": us, "algorithmic_bytes": byts, "gbs": byts / (us * 1e-6) / 1e9,
+                    "frac": byts / (us * 1e-6) / 1e9 / hbm}
+
+    # end to end through the C ABI with host buffers: matrix values, b and x
+    # cross PCIe/C2C inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        hv = [torch.from_numpy(j[2]).pin_memory() for j in jac[:args.e2e_steps]]
+        hb = [torch.from_numpy(j[3]).pin_memory() for j in jac[:args.e2e_steps]]
+        hx = torch.zeros(n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            A.update_values(hv[k])
+            P.update()
+            info = P.solve(hb[k], hx, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True)
+            if info["status"] != 0:
+                raise RuntimeError(f"e2e solve failed: {info}")
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) * 1e3
+        te = reduce_max(te)
+        e2e = {"value": te / (args.e2e_steps * world), "unit": "ms", "h2d_bytes_per_step": 9 * 8 * nnzb + n * 8,
+               "d2h_bytes_per_step": n * 8}
+
+    if rank == 0:
+        iters = [i["iters"] for i in infos]
+        line = {
+            "metric": METRIC, "value": agg["ms_per_solve"], "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": agg["elapsed_ms"] / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic", "config": config_dict(args),
+            "roofline": {"bound": "hbm", "kernel": "k_arnoldi_spmv", "achieved": ach, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": (ach / hbm) if ach else None,
+                         "traffic": traffic, "algorithmic_bytes": spmv_bytes,
+                         "avg_us": spmv_ms / spmv_n * 1e3 if spmv_n else None, "launches": spmv_n},
+            "spmv": sp, "cpu_baseline": cpu_rec, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "iters": iters, "iters_mean": float(np.mean(iters)),
+            "solves_per_s": agg["solves_per_s"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * bosolve.h - C ABI of the GPU (sm_103a) CPR-FGMRES solver for the Newton
+ * Jacobians of fully implicit three-phase black-oil simulation.
+ *
+ * The problem (paper Sec. 3.1, Alg. 1): given the Jacobian A and the
+ * right-hand side b(x^l) of one Newton step, find dx with
+ *     || b - A dx ||_2 <= tol * || b ||_2.
+ * A is block sparse with 3x3 blocks (paper Sec. 3.2, Eq. for the block
+ * structure of A): one block row per cell of a structured nx x ny x nz grid
+ * (paper Sec. 3.3), 7-point two-point-flux stencil.  Unknown 3c+k of a
+ * vector is (p, Sw, Sg)[k] of cell c = i + nx (j + ny k); row r of a block is
+ * the (oil, water, gas)[r] conservation equation (paper Sec. 2.1, Eq. 3).
+ *
+ * Solver: restarted flexible GMRES, right preconditioned by CPR-FPF (paper
+ * Alg. 2) built on the Quasi-IMPES decoupled matrix (paper Sec. 3.2):
+ * red-black block ILU(0) as the local solver R, an aggregation AMG V-cycle
+ * on the pressure block A_pp.
+ *
+ * Conventions for every call:
+ *  - Return value: a bo_status (0 = BO_OK, negative = error).  No call
+ *    aborts the process or poisons the CUDA context on bad input.
+ *  - Execution: every call is ordered on the context's CUDA stream.  Calls
+ *    that return results to the host (bo_prec_setup, bo_solve, the
+ *    *_levels query) synchronise that stream.
+ *  - Memory: `mem` arguments say whether a pointer is host (BO_MEM_HOST) or
+ *    device (BO_MEM_DEVICE) memory of the context's device.  The library
+ *    copies matrix inputs into memory it owns; vectors passed to spmv /
+ *    apply / solve stay owned by the caller.
+ *  - Thread safety: one context, matrix or preconditioner must not be used
+ *    from two host threads at once.
+ */
+#ifndef BOSOLVE_H
+#define BOSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bo_ctx bo_ctx;
+typedef struct bo_mat bo_mat;
+typedef struct bo_prec bo_prec;
+
+typedef enum {
+  BO_OK = 0,
+  BO_ERR_ARG = -1,           /* bad argument (NULL, size, unsupported option)   */
+  BO_ERR_CUDA = -2,          /* a CUDA runtime call failed                       */
+  BO_ERR_OOM = -3,           /* device allocation failed                         */
+  BO_ERR_PATTERN = -4,       /* input pattern is not the grid's 7-point stencil  */
+  BO_ERR_NONFINITE = -5,     /* NaN or Inf in matrix values or right-hand side   */
+  BO_ERR_BREAKDOWN = -6,     /* singular pivot in decoupling, ILU or AMG         */
+  BO_ERR_NOT_CONVERGED = -7, /* maxit reached; x holds the last iterate          */
+  BO_ERR_TIMEOUT = -8        /* a device-side loop cap was hit                   */
+} bo_status;
+
+enum { BO_MEM_HOST = 0, BO_MEM_DEVICE = 1 };
+/* arithmetic of the preconditioner (and of bo_mat_spmv's matrix values) */
+enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1 };
+/* stages of the preconditioner that bo_prec_apply can run on their own */
+enum {
+  BO_STAGE_CPR = 0,           /* z = CPR(D_QI^{-1} r): the preconditioner FGMRES uses */
+  BO_STAGE_ILU = 1,           /* z = R^{-1} r, R = red-black block ILU(0) of D_QI^{-1} A */
+  BO_STAGE_AMG = 2,           /* z = Pi_p AMG(A_pp)^{-1} Pi_r r                         */
+  BO_STAGE_CPR_DECOUPLED = 3  /* z = CPR(r), Alg. 2 on an already decoupled r           */
+};
+
+/* Structured grid (paper Sec. 3.3).  nx must be even (the red-black layout
+ * pairs neighbouring cells of a grid row); ncontinua must be 1. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  int32_t ncontinua;
+} bo_grid;
+
+typedef struct {
+  int32_t precision;      /* BO_PREC_FP64 or BO_PREC_FP32 (mixed precision)     */
+  int32_t amg_nu1;        /* red-black Gauss-Seidel pre-sweeps  (default 1)      */
+  int32_t amg_nu2;        /* post-sweeps (default 1)                             */
+  double amg_overcorr;    /* coarse correction scale s: x += s P x_c (default 1) */
+  int32_t amg_coarse_max; /* coarsest level size, <= 128 (default 128)          */
+} bo_prec_opts;
+
+typedef struct {
+  double tol;             /* relative to ||b||_2 (paper Alg. 1 criterion)         */
+  int32_t restart;        /* m of FGMRES(m), 1..64 (default 30)                   */
+  int32_t maxit;          /* total iteration cap (default 500)                    */
+  int32_t x0_is_zero;     /* 1: ignore x on entry and start from 0                */
+  int32_t mem;            /* BO_MEM_DEVICE (default) or BO_MEM_HOST for b and x   */
+  int32_t profile;        /* 1: time the Arnoldi SpMV launches with CUDA events   */
+} bo_solve_opts;
+
+typedef struct {
+  int32_t status;         /* as returned                                          */
+  int32_t iters;          /* FGMRES iterations                                    */
+  int32_t restarts;       /* completed cycles                                     */
+  double true_rel_res;    /* ||b - A x|| / ||b|| recomputed in FP64 at exit       */
+  double est_rel_res;     /* last Arnoldi estimate                                */
+  double solve_ms;        /* host wall time of the call                           */
+  int32_t spmv_launches;  /* profile = 1: Arnoldi SpMV launches timed             */
+  double spmv_ms;         /* profile = 1: their summed CUDA-event time            */
+} bo_solve_info;
+
+const char* bo_status_str(int status);
+/* Fill defaults: FP64, nu1 = nu2 = 1, overcorr 1, coarse_max 128 / tol 1e-8,
+ * restart 30, maxit 500, device pointers. */
+void bo_prec_opts_default(bo_prec_opts* o);
+void bo_solve_opts_default(bo_solve_opts* o);
+
+/* Context on CUDA device `device`, ordering work on `cuda_stream`: a
+ * cudaStream_t of that device, cudaStreamLegacy ((void*)1) for the legacy
+ * default stream, or NULL for a new non-blocking stream owned by the
+ * context.  The context must outlive the matrices made with it. */
+int bo_ctx_create(int device, void* cuda_stream, bo_ctx** out);
+int bo_ctx_destroy(bo_ctx* ctx);
+
+/* Jacobian from BSR arrays (paper Sec. 3.3 matrix of rows; Sec. 3.2 block
+ * structure): nbrows = nx ny nz block rows, rowptr[nbrows+1], col[nnzb],
+ * val[9 nnzb] row-major 3x3 blocks.  Every block row must hold exactly the
+ * diagonal and the existing 7-point neighbours (any order).  Errors:
+ * BO_ERR_PATTERN for any other pattern, BO_ERR_NONFINITE for NaN/Inf. */
+int bo_mat_create_bsr(bo_ctx* ctx, const bo_grid* grid, int32_t nbrows, int64_t nnzb,
+                      const int32_t* rowptr, const int32_t* col, const double* val,
+                      int mem, bo_mat** out);
+/* Jacobian from scalar CSR with interleaved unknowns (row 3c+r, column
+ * 3c'+k): nrows = 3 nx ny nz.  Entries outside the 7-point block pattern
+ * give BO_ERR_PATTERN; duplicates are summed; missing entries are zero. */
+int bo_mat_create_csr(bo_ctx* ctx, const bo_grid* grid, int32_t nrows, int64_t nnz,
+                      const int32_t* rowptr, const int32_t* col, const double* val,
+                      int mem, bo_mat** out);
+/* New values on the pattern given at create (the next Newton Jacobian). */
+int bo_mat_update_values(bo_mat* A, const double* val, int mem);
+/* y = alpha A x + beta y (paper Sec. 3.3 first basic operation); x, y
+ * device vectors of length 3 nx ny nz.  precision BO_PREC_FP32 uses an FP32
+ * copy of the values (FP64 vectors, FP32 products, FP64 accumulation is not
+ * promised: the sum runs in FP32).  beta = 0 never reads y. */
+int bo_mat_spmv(bo_mat* A, double alpha, const double* x, double beta, double* y, int precision);
+int bo_mat_destroy(bo_mat* A);
+
+/* Decoupling, ILU(0) factorisation and AMG hierarchy for the current values
+ * of A (paper Sec. 3.2).  The preconditioner keeps a pointer to A.
+ * BO_ERR_BREAKDOWN: zero saturation pivot in Quasi-IMPES, singular ILU
+ * pivot block, zero AMG diagonal or singular coarsest matrix. */
+int bo_prec_setup(bo_mat* A, const bo_prec_opts* opts, bo_prec** out);
+/* Recompute all preconditioner values after bo_mat_update_values. */
+int bo_prec_update(bo_prec* P);
+/* z = stage(r), r and z device vectors of length 3 nx ny nz (FP64). */
+int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z);
+/* y = (D_QI^{-1} A) x in FP64, device vectors (paper Sec. 3.2 decoupled system). */
+int bo_prec_spmv_decoupled(bo_prec* P, const double* x, double* y);
+/* AMG level sizes: writes up to cap triples (nx, ny, nz), returns the level
+ * count (or a negative status). */
+int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap);
+int bo_prec_destroy(bo_prec* P);
+
+/* Solve A x = b with FGMRES(m) + CPR to ||b - A x|| <= tol ||b|| (paper
+ * Alg. 1 step "find dx").  b, x: length 3 nx ny nz, device or host memory
+ * per opts->mem; x holds the initial guess unless x0_is_zero.  On
+ * BO_ERR_NOT_CONVERGED x holds the last iterate and info is filled.  b = 0
+ * returns x = 0.  info may be NULL. */
+int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
+/* Estimated relative residuals of the last solve, one per iteration; returns
+ * how many were written (at most cap). */
+int bo_prec_residual_history(bo_prec* P, double* buf, int cap);
+
+/* state += dx on the device in FP64 (paper Alg. 1, x^l = x^{l-1} + dx). */
+int bo_newton_update(bo_ctx* ctx, double* state, const double* dx, int64_t n);
+
+/* Diagnostics (no counterpart in the paper): the number of CUDA kernels this
+ * library has launched in the process so far. */
+int64_t bo_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOSOLVE_H */

@@ -1,0 +1,332 @@
+"""Python binding of libbosolve (the sm_103a CPR-FGMRES black-oil Jacobian
+solver).  Argument marshalling only: every step of the solve runs in the
+library's CUDA kernels.  Functions keep the C names of include/bosolve.h;
+vectors are torch CUDA tensors (float64, length 3 nx ny nz, natural
+interleaved order: unknown 3c+k = (p, Sw, Sg)[k] of cell c), matrix inputs
+numpy arrays (host) or torch CUDA tensors (device).
+
+There is no fallback: importing works without a GPU, but every call needs
+the compiled library and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbosolve.so")
+
+BO_OK = 0
+BO_ERR_ARG = -1
+BO_ERR_CUDA = -2
+BO_ERR_OOM = -3
+BO_ERR_PATTERN = -4
+BO_ERR_NONFINITE = -5
+BO_ERR_BREAKDOWN = -6
+BO_ERR_NOT_CONVERGED = -7
+BO_ERR_TIMEOUT = -8
+BO_MEM_HOST = 0
+BO_MEM_DEVICE = 1
+BO_PREC_FP64 = 0
+BO_PREC_FP32 = 1
+BO_STAGE_CPR = 0
+BO_STAGE_ILU = 1
+BO_STAGE_AMG = 2
+BO_STAGE_CPR_DECOUPLED = 3
+
+# every symbol include/bosolve.h declares
+EXPORTS = (
+    "bo_status_str", "bo_prec_opts_default", "bo_solve_opts_default", "bo_ctx_create", "bo_ctx_destroy",
+    "bo_mat_create_bsr", "bo_mat_create_csr", "bo_mat_update_values", "bo_mat_spmv", "bo_mat_destroy",
+    "bo_prec_setup", "bo_prec_update", "bo_prec_apply", "bo_prec_spmv_decoupled", "bo_prec_amg_levels",
+    "bo_prec_destroy", "bo_solve", "bo_prec_residual_history", "bo_newton_update", "bo_kernel_launches",
+)
+
+
+class BoError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_status_str(status)} ({status})")
+
+
+class bo_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("ncontinua", ctypes.c_int32)]
+
+
+class bo_prec_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("amg_nu1", ctypes.c_int32), ("amg_nu2", ctypes.c_int32),
+                ("amg_overcorr", ctypes.c_double), ("amg_coarse_max", ctypes.c_int32)]
+
+
+class bo_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("x0_is_zero", ctypes.c_int32), ("mem", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class bo_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("true_rel_res", ctypes.c_double), ("est_rel_res", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("spmv_launches", ctypes.c_int32), ("spmv_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)
+
+
+def lib():
+    """The loaded libbosolve.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbosolve.so not built ({LIB_PATH}); run paper_1606_00556_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.bo_status_str.restype = ctypes.c_char_p
+        L.bo_status_str.argtypes = [ctypes.c_int]
+        L.bo_ctx_create.argtypes = [ctypes.c_int, _VP, ctypes.POINTER(_VP)]
+        L.bo_ctx_destroy.argtypes = [_VP]
+        for f in (L.bo_mat_create_bsr, L.bo_mat_create_csr):
+            f.argtypes = [_VP, ctypes.POINTER(bo_grid), ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int,
+                          ctypes.POINTER(_VP)]
+        L.bo_mat_update_values.argtypes = [_VP, _VP, ctypes.c_int]
+        L.bo_mat_spmv.argtypes = [_VP, ctypes.c_double, _VP, ctypes.c_double, _VP, ctypes.c_int]
+        L.bo_mat_destroy.argtypes = [_VP]
+        L.bo_prec_setup.argtypes = [_VP, ctypes.POINTER(bo_prec_opts), ctypes.POINTER(_VP)]
+        L.bo_prec_update.argtypes = [_VP]
+        L.bo_prec_apply.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+        L.bo_prec_spmv_decoupled.argtypes = [_VP, _VP, _VP]
+        L.bo_prec_amg_levels.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+        L.bo_prec_destroy.argtypes = [_VP]
+        L.bo_solve.argtypes = [_VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
+        L.bo_prec_residual_history.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.bo_newton_update.argtypes = [_VP, _VP, _VP, ctypes.c_int64]
+        L.bo_kernel_launches.restype = ctypes.c_int64
+        L.bo_kernel_launches.argtypes = []
+        L.bo_prec_opts_default.argtypes = [ctypes.POINTER(bo_prec_opts)]
+        L.bo_solve_opts_default.argtypes = [ctypes.POINTER(bo_solve_opts)]
+        _lib = L
+    return _lib
+
+
+def _status_str(s):
+    try:
+        return lib().bo_status_str(s).decode()
+    except Exception:
+        return "status"
+
+
+def _check(rc, where):
+    if rc != BO_OK:
+        raise BoError(rc, where)
+
+
+def _ptr(a):
+    """(pointer, mem kind) of a torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return _VP(a.data_ptr()), (BO_MEM_DEVICE if a.is_cuda else BO_MEM_HOST)
+    a = np.ascontiguousarray(a)
+    return _VP(a.ctypes.data), BO_MEM_HOST
+
+
+def _f64(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64:
+            raise TypeError("vectors must be float64")
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+_CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
+def _alive():
+    return not sys.is_finalizing()
+
+
+class Context:
+    """bo_ctx: a device and the CUDA stream every call is ordered on.
+
+    By default the context uses torch's current stream on `device`, so the
+    library's work is ordered with the torch operations that produce its
+    inputs and consume its outputs."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = _VP()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device)
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        s = _VP(handle if handle else _CUDA_STREAM_LEGACY)
+        _check(lib().bo_ctx_create(device, s, ctypes.byref(h)), "bo_ctx_create")
+        self.h = h
+        self.device = device
+        self.stream = stream
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_ctx_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid(nx, ny, nz, dx=100.0, dy=100.0, dz=20.0) -> bo_grid:
+    return bo_grid(nx, ny, nz, dx, dy, dz, 1)
+
+
+class Matrix:
+    """bo_mat: one Jacobian on a structured grid."""
+
+    def __init__(self, ctx: Context, g: bo_grid, h, keep):
+        self.ctx, self.grid, self.h, self._keep = ctx, g, h, keep
+        self.n = 3 * g.nx * g.ny * g.nz
+
+    @classmethod
+    def from_bsr(cls, ctx, g: bo_grid, rowptr, col, val):
+        """bo_mat_create_bsr; arrays on host (numpy) or device (torch)."""
+        rowptr = rowptr if hasattr(rowptr, "data_ptr") else np.ascontiguousarray(rowptr, np.int32)
+        col = col if hasattr(col, "data_ptr") else np.ascontiguousarray(col, np.int32)
+        val = _f64(val)
+        rp, m1 = _ptr(rowptr)
+        cp, m2 = _ptr(col)
+        vp, m3 = _ptr(val)
+        if len({m1, m2, m3}) != 1:
+            raise ValueError("rowptr, col and val must all be host or all device")
+        h = _VP()
+        nb = g.nx * g.ny * g.nz
+        nnzb = int(col.shape[0])
+        _check(lib().bo_mat_create_bsr(ctx.h, ctypes.byref(g), nb, nnzb, rp, cp, vp, m1, ctypes.byref(h)),
+               "bo_mat_create_bsr")
+        return cls(ctx, g, h, (rowptr, col, val))
+
+    @classmethod
+    def from_csr(cls, ctx, g: bo_grid, rowptr, col, val):
+        """bo_mat_create_csr (scalar CSR, interleaved unknowns)."""
+        rowptr = rowptr if hasattr(rowptr, "data_ptr") else np.ascontiguousarray(rowptr, np.int32)
+        col = col if hasattr(col, "data_ptr") else np.ascontiguousarray(col, np.int32)
+        val = _f64(val)
+        rp, m1 = _ptr(rowptr)
+        cp, _ = _ptr(col)
+        vp, _ = _ptr(val)
+        h = _VP()
+        _check(lib().bo_mat_create_csr(ctx.h, ctypes.byref(g), 3 * g.nx * g.ny * g.nz, int(col.shape[0]), rp, cp, vp,
+                                       m1, ctypes.byref(h)), "bo_mat_create_csr")
+        return cls(ctx, g, h, (rowptr, col, val))
+
+    def update_values(self, val):
+        """bo_mat_update_values."""
+        val = _f64(val)
+        vp, mem = _ptr(val)
+        _check(lib().bo_mat_update_values(self.h, vp, mem), "bo_mat_update_values")
+
+    def spmv(self, x, y, alpha=1.0, beta=0.0, precision=BO_PREC_FP64):
+        """bo_mat_spmv: y = alpha A x + beta y (device tensors)."""
+        _check(lib().bo_mat_spmv(self.h, alpha, _VP(x.data_ptr()), beta, _VP(y.data_ptr()), precision),
+               "bo_mat_spmv")
+        return y
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_mat_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Preconditioner:
+    """bo_prec: CPR-FPF (decoupling + red-black block ILU(0) + AMG)."""
+
+    def __init__(self, mat: Matrix, precision=BO_PREC_FP64, nu1=1, nu2=1, overcorr=1.0, coarse_max=128):
+        o = bo_prec_opts(precision, nu1, nu2, overcorr, coarse_max)
+        h = _VP()
+        _check(lib().bo_prec_setup(mat.h, ctypes.byref(o), ctypes.byref(h)), "bo_prec_setup")
+        self.mat, self.h, self.opts = mat, h, o
+
+    def update(self):
+        """bo_prec_update (after Matrix.update_values)."""
+        _check(lib().bo_prec_update(self.h), "bo_prec_update")
+
+    def apply(self, stage, r, z):
+        """bo_prec_apply: z = stage(r)."""
+        _check(lib().bo_prec_apply(self.h, stage, _VP(r.data_ptr()), _VP(z.data_ptr())), "bo_prec_apply")
+        return z
+
+    def spmv_decoupled(self, x, y):
+        """bo_prec_spmv_decoupled: y = D_QI^{-1} A x."""
+        _check(lib().bo_prec_spmv_decoupled(self.h, _VP(x.data_ptr()), _VP(y.data_ptr())), "bo_prec_spmv_decoupled")
+        return y
+
+    def amg_levels(self):
+        """bo_prec_amg_levels: [(nx, ny, nz), ...]."""
+        buf = (ctypes.c_int32 * (3 * 24))()
+        n = lib().bo_prec_amg_levels(self.h, buf, 24)
+        if n < 0:
+            raise BoError(n, "bo_prec_amg_levels")
+        return [tuple(buf[3 * i:3 * i + 3]) for i in range(n)]
+
+    def solve(self, b, x, tol=1e-8, restart=30, maxit=500, x0_is_zero=True, profile=False, raise_on_error=True):
+        """bo_solve: FGMRES(restart) + CPR to ||b - A x|| <= tol ||b||.
+        b, x: torch CUDA tensors (device) or numpy arrays (host).  Returns
+        the bo_solve_info fields as a dict."""
+        bp, m1 = _ptr(b)
+        xp, m2 = _ptr(x)
+        if m1 != m2:
+            raise ValueError("b and x must both be host or both device")
+        o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), m1, int(profile))
+        info = bo_solve_info()
+        rc = lib().bo_solve(self.h, bp, xp, ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error and rc not in (BO_OK, BO_ERR_NOT_CONVERGED):
+            raise BoError(rc, "bo_solve")
+        d = info.as_dict()
+        d["status"] = rc
+        return d
+
+    def residual_history(self, cap=4096):
+        buf = (ctypes.c_double * cap)()
+        n = lib().bo_prec_residual_history(self.h, buf, cap)
+        return np.array(buf[:max(n, 0)])
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_prec_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bo_kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().bo_kernel_launches())
+
+
+def bo_newton_update(ctx: Context, state, dx):
+    """state += dx on the device (paper Alg. 1 update)."""
+    _check(lib().bo_newton_update(ctx.h, _VP(state.data_ptr()), _VP(dx.data_ptr()), state.numel()),
+           "bo_newton_update")

@@ -1,0 +1,257 @@
+// Internal declarations shared by the solver's translation units.
+//
+// Data layout in HBM ("colour-split structured BSR").  Cells are split into
+// the two colours of the 7-point graph, red ((i + j + k) even) and black.
+// With nx even, cell c has half index q = c >> 1 inside its colour, and the
+// half indices of each colour run over [0, N/2).  All six neighbours of a
+// cell have the other colour, so every operation that the red-black block
+// ILU(0) and the Gauss-Seidel smoother run on one colour touches contiguous
+// memory.
+//   matrix values: plane (colour, slot, rc) is an array of N/2 scalars,
+//       offset ((colour * 7 + slot) * 9 + rc) * N/2; slot is the stencil
+//       position (-z, -y, -x, diag, +x, +y, +z), rc = 3 * row + column of
+//       the 3x3 block.  Blocks whose neighbour lies outside the grid hold 0.
+//   vectors (internal): entry (component, colour, q) at
+//       component * N + colour * N/2 + q, i.e. the pressure component of
+//       all cells first (red half, black half), then Sw, then Sg.
+// Column indices are implied by the stencil and never stored.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <atomic>
+#include <vector>
+
+#include "bosolve.h"
+
+namespace bo {
+
+constexpr int kThreads = 256;
+
+enum Slot { kZm = 0, kYm = 1, kXm = 2, kDiag = 3, kXp = 4, kYp = 5, kZp = 6 };
+
+// error bits written by device kernels
+enum : int { kErrPattern = 1, kErrNonfinite = 2, kErrBreakdown = 4, kErrTimeout = 8 };
+
+struct Geom {
+  int32_t nx, ny, nz, hx;
+  int64_t N, Nh;
+};
+
+struct Cell {
+  int32_t i, j, k, s;  // s: parity of i (the position of the cell inside its half-index pair)
+};
+
+__host__ __device__ __forceinline__ int opposite(int slot) { return 6 - slot; }
+
+__device__ __forceinline__ Cell decode(const Geom& g, int color, int64_t q) {
+  const int64_t r = q / g.hx;
+  const int32_t ih = (int32_t)(q - r * g.hx);
+  const int32_t j = (int32_t)(r % g.ny);
+  const int32_t k = (int32_t)(r / g.ny);
+  const int32_t s = (color ^ j ^ k) & 1;
+  return Cell{2 * ih + s, j, k, s};
+}
+
+// Half index (in the neighbour's colour) of the neighbour at `slot`, or -1
+// when it lies outside the grid.  slot is a compile-time constant after
+// unrolling, so the switch folds away.
+__device__ __forceinline__ int64_t nbr(const Geom& g, const Cell& c, int64_t q, int slot) {
+  switch (slot) {
+    case kZm: return c.k > 0 ? q - (int64_t)g.hx * g.ny : -1;
+    case kYm: return c.j > 0 ? q - g.hx : -1;
+    case kXm: return c.i > 0 ? q - 1 + c.s : -1;
+    case kDiag: return q;
+    case kXp: return c.i < g.nx - 1 ? q + c.s : -1;
+    case kYp: return c.j < g.ny - 1 ? q + g.hx : -1;
+    default: return c.k < g.nz - 1 ? q + (int64_t)g.hx * g.ny : -1;
+  }
+}
+
+__host__ __device__ __forceinline__ size_t plane(const Geom& g, int color, int slot, int rc) {
+  return ((size_t)(color * 7 + slot) * 9 + rc) * (size_t)g.Nh;
+}
+
+__host__ __device__ __forceinline__ size_t vidx(const Geom& g, int comp, int color, int64_t q) {
+  return (size_t)comp * (size_t)g.N + (size_t)color * (size_t)g.Nh + (size_t)q;
+}
+
+// streaming (evict-first) loads for matrix values that are read once per pass
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the thread block in a fixed order; the result is valid in every
+// thread.  `sh` must hold 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = l < nw ? sh[l] : 0.0;
+  return warp_sum(v);
+}
+
+// Ticket of the "last block done" pattern: true in the block that finished
+// last among `total`.  Partials written before the call are visible to it.
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned total) {
+  __shared__ unsigned ticket;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  return ticket == total - 1;
+}
+
+// Device-side state of one preconditioner / solve.  Lives in device memory.
+struct DevState {
+  int done;        // stop the current FGMRES cycle (device side early exit)
+  int k;           // Arnoldi steps completed in the current cycle
+  int happy;       // happy breakdown in the current cycle
+  int err;         // kErr* bits from setup and apply kernels
+  unsigned counter[8];
+  double est;      // Arnoldi estimate of ||b - A x|| after k steps
+  double target;   // tol * ||b||
+  double beta;     // ||r|| from the last true residual
+  double bnorm;    // ||b||
+  double wn0;      // ||w|| before orthogonalisation
+  double hn;       // ||w|| after orthogonalisation
+  double h[136];   // coefficients of the column under construction: pass 1 at 0, pass 2 at 64
+};
+
+// Number of kernels this library has launched (reported by bo_kernel_launches).
+extern std::atomic<long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// grid size for a grid-stride loop over n items
+inline int grid_for(int64_t n, int threads = kThreads, int max_blocks = 152 * 16) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+}  // namespace bo
+
+// ----------------------------------------------------------------- objects
+// Contexts and matrices are reference counted: a matrix holds its context
+// and a preconditioner holds its matrix, so destroying them in any order is
+// safe (the object is freed when its last holder lets go).
+struct bo_ctx {
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  int refs;
+};
+
+struct bo_mat {
+  bo_ctx* ctx;
+  int refs;
+  bo_grid grid;
+  bo::Geom g;
+  int kind;            // 0 BSR, 1 CSR
+  int64_t nnz;         // blocks (BSR) or scalars (CSR)
+  int32_t* rowptr;     // device copy of the pattern
+  int32_t* col;
+  double* stage;       // device staging of values passed from the host
+  double* A;           // 63 N FP64 values, colour-split planes
+  float* A32;          // FP32 copy for bo_mat_spmv(..., BO_PREC_FP32)
+  bool a32_valid;
+  int* flags;          // device error bits
+  int* h_flags;        // pinned host copy
+};
+
+namespace bo {
+
+// one AMG level stored in natural cell order (levels >= 1)
+struct Level {
+  int32_t nx, ny, nz;
+  int64_t n;
+  double* c64;   // 7 n FP64 coefficients [slot][cell] (setup master)
+  void* c;       // 7 n coefficients in the preconditioner precision
+  void* f;       // n right-hand side
+  void* x;       // n iterate
+};
+
+}  // namespace bo
+
+struct bo_prec {
+  bo_mat* mat;
+  bo_prec_opts opts;
+  bool fp32;               // preconditioner arithmetic FP32 (else FP64)
+  size_t tsize;            // sizeof(preconditioner scalar)
+  void* At;                // 63 N decoupled values (preconditioner precision)
+  double* w;               // 2 N Quasi-IMPES weights (w_w, w_g) [2][N] internal order
+  double* Dinv64;          // 9 N inverted ILU pivot blocks, FP64 [rc][N]
+  void* Dinv;              // same in the preconditioner precision (aliases Dinv64 for FP64)
+  // AMG: level 0 = the pressure block of At (colour-split), levels 1.. natural order
+  int nlev;
+  bo::Level lev[24];
+  int tail_from;           // first level handled by the single-block tail kernel
+  double* coarse64;        // dense coarsest matrix / inverse workspace (FP64)
+  void* coarse_inv;        // dense inverse of the coarsest level (precision T)
+  int64_t ncoarse;
+  // CPR work vectors (precision T, internal order)
+  void* f;                 // 3N decoupled input
+  void* t;                 // 3N ILU intermediates
+  void* r;                 // 3N residual
+  void* e0;                // N level-0 AMG correction
+  void* f0;                // N level-0 AMG right-hand side
+  // Krylov workspace (FP64 unless noted)
+  int mcap;                // restart length the workspace was sized for
+  double* V;               // (mcap+1) 3N
+  void* Z;                 // mcap 3N, precision T
+  double* H;               // (mcap+1) mcap
+  double* cs;
+  double* sn;
+  double* gvec;            // mcap+1
+  double* y;               // mcap
+  double* xi;              // 3N internal iterate
+  double* bi;              // 3N internal right-hand side
+  double* rk;              // 3N true residual
+  double* partials;        // reduction partials
+  int64_t npartials;
+  double* hostio;          // device staging of host b / x
+  bo::DevState* st;        // device state
+  bo::DevState* h_st;      // pinned host mirror (two slots)
+  cudaEvent_t ev[2];
+  cudaEvent_t prof_ev[2 * 512];
+  bool prof_ready;
+  double* hist;            // host residual history of the last solve
+  int nhist;
+  int hist_cap;
+};
+
+// ----------------------------------------------------------------- launchers
+namespace bo {
+
+// layout.cu
+int ingest_bsr(bo_mat* m, const double* dval);
+int ingest_csr(bo_mat* m, const double* dval);
+void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
+void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s);
+void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, bool fp32);
+void launch_gather(const Geom& g, const double* nat, double* in, cudaStream_t s);
+void launch_scatter(const Geom& g, const double* in, double* nat, cudaStream_t s);
+void launch_newton_update(double* state, const double* dx, int64_t n, cudaStream_t s);
+
+// precond.cu
+int prec_values(bo_prec* P);   // decoupling + ILU + AMG values (stream-ordered, flags in st->err)
+int prec_alloc(bo_prec* P);
+void prec_free(bo_prec* P);
+void launch_cpr(bo_prec* P, const double* v, void* z, int stage, const DevState* st);  // v internal FP64, z internal T
+void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  // FP64 values of At rebuilt on the fly
+
+// krylov.cu
+int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
+int krylov_alloc(bo_prec* P, int m);
+
+}  // namespace bo

@@ -1,0 +1,376 @@
+// C ABI entry points (declared in bosolve.h): argument checks, object
+// lifetimes, host <-> device staging and error mapping.  All arithmetic runs
+// in the kernels of layout.cu, precond.cu and krylov.cu.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "bo_internal.cuh"
+
+using namespace bo;
+
+namespace bo {
+std::atomic<long long> g_launches{0};
+}
+
+namespace {
+
+void ctx_release(bo_ctx* c) {
+  if (--c->refs > 0) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BO_OK;
+  if (e == cudaErrorMemoryAllocation) return BO_ERR_OOM;
+  return BO_ERR_CUDA;
+}
+
+bool grid_ok(const bo_grid* g) {
+  return g && g->nx >= 2 && g->ny >= 1 && g->nz >= 1 && (g->nx % 2) == 0 && g->ncontinua == 1 &&
+         (int64_t)g->nx * g->ny * g->nz <= ((int64_t)1 << 28);
+}
+
+int64_t nnzb_of(const bo_grid* g) {
+  const int64_t nx = g->nx, ny = g->ny, nz = g->nz;
+  return nx * ny * nz + 2 * ((nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1));
+}
+
+// read back and clear the matrix error flags; map to a status
+int mat_flags(bo_mat* m) {
+  cudaMemcpyAsync(m->h_flags, m->flags, sizeof(int), cudaMemcpyDeviceToHost, m->ctx->stream);
+  cudaError_t e = cudaStreamSynchronize(m->ctx->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int f = *m->h_flags;
+  cudaMemsetAsync(m->flags, 0, sizeof(int), m->ctx->stream);
+  if (f & kErrPattern) return BO_ERR_PATTERN;
+  if (f & kErrNonfinite) return BO_ERR_NONFINITE;
+  return BO_OK;
+}
+
+int load_values(bo_mat* m, const double* val, int mem) {
+  const size_t bytes = (m->kind == 0 ? 9 * (size_t)m->nnz : (size_t)m->nnz) * sizeof(double);
+  const double* dval = val;
+  if (mem == BO_MEM_HOST) {
+    cudaError_t e = cudaMemcpyAsync(m->stage, val, bytes, cudaMemcpyHostToDevice, m->ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    dval = m->stage;
+  }
+  int rc = m->kind == 0 ? ingest_bsr(m, dval) : ingest_csr(m, dval);
+  if (rc != BO_OK) return rc;
+  m->a32_valid = false;
+  return mat_flags(m);
+}
+
+void mat_free(bo_mat* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->ctx->stream);
+  cudaFree(m->rowptr);
+  cudaFree(m->col);
+  cudaFree(m->stage);
+  cudaFree(m->A);
+  cudaFree(m->A32);
+  cudaFree(m->flags);
+  cudaFreeHost(m->h_flags);
+  bo_ctx* c = m->ctx;
+  delete m;
+  ctx_release(c);
+}
+
+void mat_release(bo_mat* m) {
+  if (--m->refs == 0) mat_free(m);
+}
+
+int mat_create(bo_ctx* ctx, const bo_grid* grid, int kind, int64_t nrows, int64_t nnz, const int32_t* rowptr,
+               const int32_t* col, const double* val, int mem, bo_mat** out) {
+  if (!ctx || !out || !rowptr || !col || !val || !grid_ok(grid) || nnz <= 0 || nnz > INT32_MAX) return BO_ERR_ARG;
+  if (mem != BO_MEM_HOST && mem != BO_MEM_DEVICE) return BO_ERR_ARG;
+  const int64_t N = (int64_t)grid->nx * grid->ny * grid->nz;
+  if (nrows != (kind == 0 ? N : 3 * N)) return BO_ERR_ARG;
+  if (kind == 0 && nnz != nnzb_of(grid)) return BO_ERR_PATTERN;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return BO_ERR_CUDA;
+  if (mem == BO_MEM_HOST) {  // cheap host-side checks of the row pointers
+    if (rowptr[0] != 0 || rowptr[nrows] != nnz) return BO_ERR_PATTERN;
+    for (int64_t i = 0; i < nrows; ++i)
+      if (rowptr[i + 1] < rowptr[i]) return BO_ERR_PATTERN;
+  }
+  bo_mat* m = new (std::nothrow) bo_mat();
+  if (!m) return BO_ERR_OOM;
+  std::memset(m, 0, sizeof(*m));
+  m->ctx = ctx;
+  m->refs = 1;
+  ctx->refs++;
+  m->grid = *grid;
+  m->g = Geom{grid->nx, grid->ny, grid->nz, grid->nx / 2, N, N / 2};
+  m->kind = kind;
+  m->nnz = nnz;
+  cudaStream_t s = ctx->stream;
+  const size_t vbytes = (kind == 0 ? 9 * (size_t)nnz : (size_t)nnz) * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&m->rowptr, (nrows + 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&m->col, nnz * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&m->stage, vbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&m->A, (size_t)63 * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->flags, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&m->h_flags, sizeof(int));
+  if (e != cudaSuccess) {
+    mat_free(m);
+    return cuda_status(e);
+  }
+  const cudaMemcpyKind kd = mem == BO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyAsync(m->rowptr, rowptr, (nrows + 1) * sizeof(int32_t), kd, s);
+  cudaMemcpyAsync(m->col, col, nnz * sizeof(int32_t), kd, s);
+  cudaMemsetAsync(m->flags, 0, sizeof(int), s);
+  int rc = load_values(m, val, mem);
+  if (rc != BO_OK) {
+    mat_free(m);
+    return rc;
+  }
+  *out = m;
+  return BO_OK;
+}
+
+void prec_opts_fill(const bo_prec_opts* in, bo_prec_opts* o) {
+  bo_prec_opts_default(o);
+  if (in) *o = *in;
+}
+
+// set up values and read the error bits back
+int prec_refresh(bo_prec* P) {
+  cudaStream_t s = P->mat->ctx->stream;
+  cudaMemsetAsync(&P->st->err, 0, sizeof(int), s);
+  int rc = prec_values(P);
+  if (rc != BO_OK) return rc;
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(P->mat->h_flags, &P->st->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  err = *P->mat->h_flags;
+  cudaMemsetAsync(&P->st->err, 0, sizeof(int), s);
+  cudaMemsetAsync(&P->st->done, 0, sizeof(int), s);
+  if (err & kErrBreakdown) return BO_ERR_BREAKDOWN;
+  if (err & kErrNonfinite) return BO_ERR_NONFINITE;
+  return BO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bo_status_str(int s) {
+  switch (s) {
+    case BO_OK: return "ok";
+    case BO_ERR_ARG: return "invalid argument";
+    case BO_ERR_CUDA: return "CUDA error";
+    case BO_ERR_OOM: return "out of device memory";
+    case BO_ERR_PATTERN: return "pattern is not the grid's 7-point stencil";
+    case BO_ERR_NONFINITE: return "non-finite value in input";
+    case BO_ERR_BREAKDOWN: return "singular pivot (decoupling, ILU or AMG)";
+    case BO_ERR_NOT_CONVERGED: return "iteration limit reached";
+    case BO_ERR_TIMEOUT: return "device loop cap reached";
+    default: return "unknown status";
+  }
+}
+
+void bo_prec_opts_default(bo_prec_opts* o) {
+  if (!o) return;
+  o->precision = BO_PREC_FP64;
+  o->amg_nu1 = 1;
+  o->amg_nu2 = 1;
+  o->amg_overcorr = 1.0;
+  o->amg_coarse_max = 128;
+}
+
+void bo_solve_opts_default(bo_solve_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->restart = 30;
+  o->maxit = 500;
+  o->x0_is_zero = 0;
+  o->mem = BO_MEM_DEVICE;
+  o->profile = 0;
+}
+
+int bo_ctx_create(int device, void* cuda_stream, bo_ctx** out) {
+  if (!out) return BO_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return BO_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return BO_ERR_CUDA;
+  bo_ctx* c = new (std::nothrow) bo_ctx();
+  if (!c) return BO_ERR_OOM;
+  c->device = device;
+  c->refs = 1;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return BO_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return BO_OK;
+}
+
+int bo_ctx_destroy(bo_ctx* c) {
+  if (!c) return BO_ERR_ARG;
+  ctx_release(c);
+  return BO_OK;
+}
+
+int bo_mat_create_bsr(bo_ctx* ctx, const bo_grid* grid, int32_t nbrows, int64_t nnzb, const int32_t* rowptr,
+                      const int32_t* col, const double* val, int mem, bo_mat** out) {
+  return mat_create(ctx, grid, 0, nbrows, nnzb, rowptr, col, val, mem, out);
+}
+
+int bo_mat_create_csr(bo_ctx* ctx, const bo_grid* grid, int32_t nrows, int64_t nnz, const int32_t* rowptr,
+                      const int32_t* col, const double* val, int mem, bo_mat** out) {
+  return mat_create(ctx, grid, 1, nrows, nnz, rowptr, col, val, mem, out);
+}
+
+int bo_mat_update_values(bo_mat* m, const double* val, int mem) {
+  if (!m || !val || (mem != BO_MEM_HOST && mem != BO_MEM_DEVICE)) return BO_ERR_ARG;
+  return load_values(m, val, mem);
+}
+
+int bo_mat_spmv(bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
+  if (!m || !x || !y) return BO_ERR_ARG;
+  if (precision != BO_PREC_FP64 && precision != BO_PREC_FP32) return BO_ERR_ARG;
+  if (precision == BO_PREC_FP32 && !m->a32_valid) {
+    if (!m->A32 && cudaMalloc(&m->A32, (size_t)63 * m->g.N * sizeof(float)) != cudaSuccess) return BO_ERR_OOM;
+    launch_to_f32(m->A, m->A32, (size_t)63 * m->g.N, m->ctx->stream);
+    m->a32_valid = true;
+  }
+  launch_spmv_nat(m, alpha, x, beta, y, precision == BO_PREC_FP32);
+  return cuda_status(cudaGetLastError());
+}
+
+int bo_mat_destroy(bo_mat* m) {
+  if (!m) return BO_ERR_ARG;
+  mat_release(m);
+  return BO_OK;
+}
+
+int bo_prec_setup(bo_mat* m, const bo_prec_opts* opts, bo_prec** out) {
+  if (!m || !out) return BO_ERR_ARG;
+  bo_prec_opts o;
+  prec_opts_fill(opts, &o);
+  if ((o.precision != BO_PREC_FP64 && o.precision != BO_PREC_FP32) || o.amg_nu1 < 0 || o.amg_nu2 < 0 ||
+      o.amg_nu1 > 8 || o.amg_nu2 > 8 || o.amg_coarse_max < 1 || o.amg_coarse_max > 128 ||
+      !(o.amg_overcorr > 0.0 && o.amg_overcorr < 4.0))
+    return BO_ERR_ARG;
+  if (cudaSetDevice(m->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
+  bo_prec* P = new (std::nothrow) bo_prec();
+  if (!P) return BO_ERR_OOM;
+  std::memset(P, 0, sizeof(*P));
+  P->mat = m;
+  m->refs++;
+  P->opts = o;
+  P->fp32 = o.precision == BO_PREC_FP32;
+  P->tsize = P->fp32 ? sizeof(float) : sizeof(double);
+  int rc = prec_alloc(P);
+  if (rc == BO_OK) rc = krylov_alloc(P, 30);
+  if (rc == BO_OK) rc = prec_refresh(P);
+  if (rc != BO_OK) {
+    bo_prec_destroy(P);
+    return rc;
+  }
+  *out = P;
+  return BO_OK;
+}
+
+int bo_prec_update(bo_prec* P) {
+  if (!P) return BO_ERR_ARG;
+  return prec_refresh(P);
+}
+
+int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z) {
+  if (!P || !r || !z || stage < BO_STAGE_CPR || stage > BO_STAGE_CPR_DECOUPLED) return BO_ERR_ARG;
+  cudaStream_t s = P->mat->ctx->stream;
+  const Geom& g = P->mat->g;
+  cudaMemsetAsync(&P->st->done, 0, sizeof(int), s);
+  // r -> internal (xi as scratch), apply, z (precision T) -> FP64 internal -> natural
+  launch_gather(g, r, P->bi, s);
+  launch_cpr(P, P->bi, P->Z, stage, P->st);
+  if (P->fp32) {
+    launch_widen((const float*)P->Z, P->xi, (size_t)3 * g.N, s);
+    launch_scatter(g, P->xi, z, s);
+  } else {
+    launch_scatter(g, (const double*)P->Z, z, s);
+  }
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int bo_prec_spmv_decoupled(bo_prec* P, const double* x, double* y) {
+  if (!P || !x || !y) return BO_ERR_ARG;
+  cudaStream_t s = P->mat->ctx->stream;
+  const Geom& g = P->mat->g;
+  launch_gather(g, x, P->bi, s);
+  launch_spmv_decoupled_internal(P, P->bi, P->xi);
+  launch_scatter(g, P->xi, y, s);
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap) {
+  if (!P) return BO_ERR_ARG;
+  for (int l = 0; l < P->nlev && l < cap && dims; ++l) {
+    if (l == 0) {
+      dims[0] = P->mat->g.nx; dims[1] = P->mat->g.ny; dims[2] = P->mat->g.nz;
+    } else {
+      dims[3 * l] = P->lev[l].nx; dims[3 * l + 1] = P->lev[l].ny; dims[3 * l + 2] = P->lev[l].nz;
+    }
+  }
+  return P->nlev;
+}
+
+int bo_prec_destroy(bo_prec* P) {
+  if (!P) return BO_ERR_ARG;
+  cudaStreamSynchronize(P->mat->ctx->stream);
+  prec_free(P);
+  auto fr = [](void* p) { if (p) cudaFree(p); };
+  fr(P->V); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
+  fr(P->xi); fr(P->bi); fr(P->rk); fr(P->partials); fr(P->hostio);
+  if (P->h_st) cudaFreeHost(P->h_st);
+  if (P->ev[0]) cudaEventDestroy(P->ev[0]);
+  if (P->ev[1]) cudaEventDestroy(P->ev[1]);
+  if (P->prof_ready)
+    for (int i = 0; i < 2 * 512; ++i) cudaEventDestroy(P->prof_ev[i]);
+  delete[] P->hist;
+  bo_mat* m = P->mat;
+  delete P;
+  mat_release(m);
+  return BO_OK;
+}
+
+int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info) {
+  if (!P || !b || !x) return BO_ERR_ARG;
+  bo_solve_opts o;
+  bo_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 64 || o.maxit < 0 ||
+      (o.mem != BO_MEM_HOST && o.mem != BO_MEM_DEVICE))
+    return BO_ERR_ARG;
+  if (cudaSetDevice(P->mat->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
+  return fgmres(P, b, x, &o, info);
+}
+
+int bo_prec_residual_history(bo_prec* P, double* buf, int cap) {
+  if (!P || (!buf && cap > 0)) return BO_ERR_ARG;
+  const int n = P->nhist < cap ? P->nhist : cap;
+  for (int i = 0; i < n; ++i) buf[i] = P->hist[i];
+  return n;
+}
+
+int64_t bo_kernel_launches(void) { return g_launches.load(); }
+
+int bo_newton_update(bo_ctx* ctx, double* state, const double* dx, int64_t n) {
+  if (!ctx || !state || !dx || n < 0) return BO_ERR_ARG;
+  launch_newton_update(state, dx, n, ctx->stream);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,453 @@
+// Restarted flexible GMRES(m) in FP64 (paper Sec. 3.3 solver list; GMRES(30)
+// in Sec. 4), right preconditioned by CPR-FPF of the decoupled system, with
+// the paper's stopping rule ||b - A x|| <= tol ||b|| (Alg. 1) tested on the
+// recomputed FP64 residual of the original system.
+//
+// The Krylov space is that of D_QI^{-1} A preconditioned by CPR: with
+// M^{-1} = CPR o D_QI^{-1}, (A M^{-1})^k b = D_QI ((D_QI^{-1} A) CPR)^k D_QI^{-1} b,
+// so the iterates are those of the decoupled system and the minimised norm
+// is the original residual.
+//
+// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2), each pass
+// a multi-dot (one reduction for all j+1 coefficients) and a fused update.
+// Every reduction is two-stage with a fixed order (per-block partial sums,
+// then the last block to finish sums the partials), so results are bitwise
+// repeatable.  The Givens rotations run on the device in one thread; a flag
+// in device memory makes the rest of a cycle's kernels return at once after
+// convergence, so the host only polls with a lag of one iteration.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bo_internal.cuh"
+
+namespace bo {
+namespace {
+
+constexpr int kRedBlocks = 4 * 152;  // blocks of single reductions
+constexpr int kMaxM = 64;
+constexpr int kHistCap = 4096;
+
+// w = A z in FP64 on internal vectors (z in the preconditioner precision)
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const double* __restrict__ A,
+                                                          const TZ* __restrict__ z, double* __restrict__ w,
+                                                          const DevState* st) {
+  if (st->done) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int color = (int)(t / g.Nh);
+    const int64_t q = t - color * g.Nh;
+    const Cell c = decode(g, color, q);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      const int64_t nq = nbr(g, c, q, sl);
+      if (nq < 0) continue;
+      const int xc = (sl == kDiag) ? color : (color ^ 1);
+      const double x0 = (double)z[vidx(g, 0, xc, nq)], x1 = (double)z[vidx(g, 1, xc, nq)],
+                   x2 = (double)z[vidx(g, 2, xc, nq)];
+      const double* a = A + plane(g, color, sl, 0) + q;
+      const size_t P = (size_t)g.Nh;
+      a0 += ld_stream(a) * x0 + ld_stream(a + P) * x1 + ld_stream(a + 2 * P) * x2;
+      a1 += ld_stream(a + 3 * P) * x0 + ld_stream(a + 4 * P) * x1 + ld_stream(a + 5 * P) * x2;
+      a2 += ld_stream(a + 6 * P) * x0 + ld_stream(a + 7 * P) * x1 + ld_stream(a + 8 * P) * x2;
+    }
+    w[t] = a0;
+    w[g.N + t] = a1;
+    w[2 * g.N + t] = a2;
+  }
+}
+
+// sum of partials[0..np) in a fixed order by one block
+__device__ double reduce_partials(const double* partials, int np, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += __ldcg(partials + i);
+  return block_sum(s, sh);
+}
+
+// r = b - A x (FP64), ||r|| -> st->beta
+__global__ void __launch_bounds__(kThreads) k_true_residual(Geom g, const double* __restrict__ A,
+                                                           const double* __restrict__ b, const double* __restrict__ x,
+                                                           double* __restrict__ r, double* partials, DevState* st) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int color = (int)(t / g.Nh);
+    const int64_t q = t - color * g.Nh;
+    const Cell c = decode(g, color, q);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      const int64_t nq = nbr(g, c, q, sl);
+      if (nq < 0) continue;
+      const int xc = (sl == kDiag) ? color : (color ^ 1);
+      const double x0 = x[vidx(g, 0, xc, nq)], x1 = x[vidx(g, 1, xc, nq)], x2 = x[vidx(g, 2, xc, nq)];
+      const double* a = A + plane(g, color, sl, 0) + q;
+      const size_t P = (size_t)g.Nh;
+      a0 += ld_stream(a) * x0 + ld_stream(a + P) * x1 + ld_stream(a + 2 * P) * x2;
+      a1 += ld_stream(a + 3 * P) * x0 + ld_stream(a + 4 * P) * x1 + ld_stream(a + 5 * P) * x2;
+      a2 += ld_stream(a + 6 * P) * x0 + ld_stream(a + 7 * P) * x1 + ld_stream(a + 8 * P) * x2;
+    }
+    const double r0 = b[t] - a0, r1 = b[g.N + t] - a1, r2 = b[2 * g.N + t] - a2;
+    r[t] = r0;
+    r[g.N + t] = r1;
+    r[2 * g.N + t] = r2;
+    acc += r0 * r0 + r1 * r1 + r2 * r2;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (last_block(&st->counter[1], gridDim.x)) {
+    const double s = reduce_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      st->beta = sqrt(s);
+      st->counter[1] = 0;
+    }
+  }
+}
+
+// ||v|| -> st->bnorm
+__global__ void k_norm(int64_t n, const double* __restrict__ v, double* partials, DevState* st) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += v[i] * v[i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (last_block(&st->counter[2], gridDim.x)) {
+    const double s = reduce_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      st->bnorm = sqrt(s);
+      st->counter[2] = 0;
+    }
+  }
+}
+
+__global__ void k_set_target(DevState* st, double tol) {
+  st->target = tol * st->bnorm;
+  st->err = 0;
+}
+
+// start of a cycle: g = (beta, 0, ...), flags cleared
+__global__ void k_cycle_start(DevState* st, double* gv, int m) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) gv[i] = (i == 0) ? st->beta : 0.0;
+  if (threadIdx.x == 0) {
+    st->done = 0;
+    st->k = 0;
+    st->happy = 0;
+    st->est = st->beta;
+  }
+}
+
+// v = src * s with s = 1 / beta (which = 0) or 1 / hn (which = 1)
+__global__ void k_scale(int64_t n, const double* __restrict__ src, double* __restrict__ v, const DevState* st, int which,
+                        int check_done) {
+  if (check_done && st->done) return;
+  const double d = which == 0 ? st->beta : st->hn;
+  const double s = d > 0.0 ? 1.0 / d : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = src[i] * s;
+}
+
+// out[v] = <V_v, w> for v < nv; grid (chunks, nv)
+__global__ void __launch_bounds__(kThreads) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
+                                                  const double* __restrict__ w, double* partials, DevState* st,
+                                                  int out_off) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  const int nchunk = gridDim.x;
+  const int v = blockIdx.y;
+  const int64_t len = (n + nchunk - 1) / nchunk;
+  const int64_t i0 = blockIdx.x * len;
+  const int64_t i1 = min(n, i0 + len);
+  const double* Vv = V + (size_t)v * ldv;
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += Vv[i] * w[i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[(size_t)v * nchunk + blockIdx.x] = acc;
+  if (last_block(&st->counter[0], nchunk * nv)) {
+    for (int u = 0; u < nv; ++u) {
+      const double s = reduce_partials(partials + (size_t)u * nchunk, nchunk, sh);
+      if (threadIdx.x == 0) st->h[out_off + u] = s;
+    }
+    if (threadIdx.x == 0) st->counter[0] = 0;
+  }
+}
+
+// w -= sum_k h[k] V_k; with_norm: ||w|| -> st->hn
+__global__ void __launch_bounds__(kThreads) k_update(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
+                                                    double* __restrict__ w, int h_off, int with_norm,
+                                                    double* partials, DevState* st) {
+  __shared__ double sh[32];
+  __shared__ double hs[kMaxM + 1];
+  if (st->done) return;
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = st->h[h_off + k];
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int k = 0; k < nv; ++k) s -= hs[k] * V[(size_t)k * ldv + i];
+    w[i] = s;
+    acc += s * s;
+  }
+  if (!with_norm) return;
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (last_block(&st->counter[3], gridDim.x)) {
+    const double s = reduce_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      st->hn = sqrt(s);
+      st->counter[3] = 0;
+    }
+  }
+}
+
+// Hessenberg column j = h1 + h2 (both CGS passes) with h_{j+1,j} = hn;
+// previous rotations, a new one, the residual estimate and the stop flag.
+__global__ void k_givens(DevState* st, double* H, double* cs, double* sn, double* gv, int j, int m, int ldh,
+                         double* hist, int hist_at) {
+  if (st->done || threadIdx.x != 0) return;
+  double col[kMaxM + 1];
+  double nrm2 = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    col[i] = st->h[i] + st->h[kMaxM + i];
+    nrm2 += col[i] * col[i];
+  }
+  const double hn = st->hn;
+  const double wn0 = sqrt(nrm2 + hn * hn);
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j];
+  const double d = hypot(a, hn);
+  const double c = d > 0.0 ? a / d : 1.0, s = d > 0.0 ? hn / d : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = d;
+  for (int i = 0; i <= j; ++i) H[(size_t)i * ldh + j] = col[i];
+  gv[j + 1] = -s * gv[j];
+  gv[j] = c * gv[j];
+  st->k = j + 1;
+  st->est = fabs(gv[j + 1]);
+  st->happy = hn <= 1e-14 * wn0;
+  if (hist && hist_at < kHistCap) hist[hist_at] = st->est;
+  const bool bad = !isfinite(st->est) || !isfinite(d) || d == 0.0;
+  if (bad) atomicOr(&st->err, kErrNonfinite);
+  if (bad || st->est <= st->target || st->happy || j + 1 == m) st->done = 1;
+}
+
+// y = H(0:k, 0:k)^{-1} g (upper triangular after the rotations)
+__global__ void k_trisolve(DevState* st, const double* H, const double* gv, double* y, int ldh) {
+  if (threadIdx.x != 0) return;
+  if (st->err & kErrNonfinite) { st->k = 0; return; }
+  const int k = st->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gv[i];
+    for (int t = i + 1; t < k; ++t) s -= H[(size_t)i * ldh + t] * y[t];
+    y[i] = s / H[(size_t)i * ldh + i];
+  }
+}
+
+// x += sum_{l < k} y_l Z_l
+template <typename TZ>
+__global__ void k_xupdate(int64_t n, double* __restrict__ x, const TZ* __restrict__ Z, int64_t ldz,
+                          const double* __restrict__ y, const DevState* st) {
+  __shared__ double ys[kMaxM];
+  const int k = st->k;
+  for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = y[l];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int l = 0; l < k; ++l) s += ys[l] * (double)Z[(size_t)l * ldz + i];
+    x[i] = s;
+  }
+}
+
+template <typename TZ>
+void launch_arnoldi_spmv(bo_prec* P, const void* z, double* w) {
+  const Geom& g = P->mat->g;
+  (k_arnoldi_spmv<TZ><<<grid_for(g.N, kThreads, 152 * 64), kThreads, 0, P->mat->ctx->stream>>>(
+      g, P->mat->A, (const TZ*)z, w, P->st), note_launch());
+}
+
+int mdot_chunks(int64_t n) {
+  int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
+  if (c < 1) c = 1;
+  if (c > 2 * 152) c = 2 * 152;
+  return (int)c;
+}
+
+}  // namespace
+
+int krylov_alloc(bo_prec* P, int m) {
+  if (P->mcap >= m && P->V) return BO_OK;
+  const Geom& g = P->mat->g;
+  const int64_t n = 3 * g.N;
+  auto fr = [](void* p) { if (p) cudaFree(p); };
+  fr(P->V); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
+  P->V = nullptr; P->Z = nullptr;
+  bool ok = true;
+  auto al = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (ok && cudaMalloc(&p, bytes) != cudaSuccess) { ok = false; return nullptr; }
+    return p;
+  };
+  P->V = (double*)al((size_t)(m + 1) * n * sizeof(double));
+  P->Z = al((size_t)m * n * P->tsize);
+  P->H = (double*)al((size_t)(m + 1) * m * sizeof(double));
+  P->cs = (double*)al((size_t)m * sizeof(double));
+  P->sn = (double*)al((size_t)m * sizeof(double));
+  P->gvec = (double*)al((size_t)(m + 1) * sizeof(double));
+  P->y = (double*)al((size_t)m * sizeof(double));
+  if (!P->xi) {
+    P->xi = (double*)al((size_t)n * sizeof(double));
+    P->bi = (double*)al((size_t)n * sizeof(double));
+    P->rk = (double*)al((size_t)n * sizeof(double));
+    P->npartials = (int64_t)(kMaxM + 1) * 2 * 152 + 4096;
+    P->partials = (double*)al((size_t)P->npartials * sizeof(double));
+    P->hostio = (double*)al((size_t)2 * n * sizeof(double));
+    if (ok && cudaMallocHost(&P->h_st, 2 * sizeof(DevState)) != cudaSuccess) ok = false;
+    if (ok) {
+      cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming);
+    }
+    P->hist_cap = kHistCap;
+    P->hist = new double[kHistCap];
+  }
+  P->mcap = ok ? m : 0;
+  return ok ? BO_OK : BO_ERR_OOM;
+}
+
+int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  bo_mat* M = P->mat;
+  cudaStream_t s = M->ctx->stream;
+  const Geom& g = M->g;
+  const int64_t n = 3 * g.N;
+  const int m = o->restart;
+  int rc = krylov_alloc(P, m);
+  if (rc != BO_OK) return rc;
+  DevState* st = P->st;
+  double* dhist = nullptr;
+  // history on the device: reuse the partials tail
+  dhist = P->partials + (P->npartials - 4096);
+
+  const double* b_d = b_in;
+  double* x_d = x_in;
+  if (o->mem == BO_MEM_HOST) {
+    cudaMemcpyAsync(P->hostio, b_in, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    b_d = P->hostio;
+    x_d = P->hostio + n;
+    if (!o->x0_is_zero) cudaMemcpyAsync(x_d, x_in, n * sizeof(double), cudaMemcpyHostToDevice, s);
+  }
+  launch_gather(g, b_d, P->bi, s);
+  if (o->x0_is_zero) cudaMemsetAsync(P->xi, 0, n * sizeof(double), s);
+  else launch_gather(g, x_d, P->xi, s);
+  (k_norm<<<kRedBlocks, kThreads, 0, s>>>(n, P->bi, P->partials, st), note_launch());
+  (k_set_target<<<1, 1, 0, s>>>(st, o->tol), note_launch());
+  (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, M->A, P->bi, P->xi, P->rk, P->partials, st), note_launch());
+  cudaMemcpyAsync(P->h_st, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
+  const double bnorm = P->h_st[0].bnorm;
+  double beta = P->h_st[0].beta;
+  double est = beta;
+  int status = BO_OK;
+  int its = 0, restarts = 0;
+  P->nhist = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
+  if (o->profile && !P->prof_ready) {
+    for (int i = 0; i < 2 * 512; ++i) cudaEventCreate(&P->prof_ev[i]);
+    P->prof_ready = true;
+  }
+  if (!std::isfinite(bnorm) || !std::isfinite(beta)) {
+    status = BO_ERR_NONFINITE;
+  } else if (bnorm == 0.0) {
+    cudaMemsetAsync(P->xi, 0, n * sizeof(double), s);
+    beta = 0.0;
+  } else {
+    const double target = o->tol * bnorm;
+    const int64_t ldv = n;
+    while (beta > target && its < o->maxit) {
+      (k_cycle_start<<<1, 64, 0, s>>>(st, P->gvec, m), note_launch());
+      (k_scale<<<grid_for(n), kThreads, 0, s>>>(n, P->rk, P->V, st, 0, 0), note_launch());
+      int enq = 0;
+      for (int j = 0; j < m && its + j < o->maxit; ++j) {
+        double* vj = P->V + (size_t)j * ldv;
+        double* w = P->V + (size_t)(j + 1) * ldv;
+        void* zj = (char*)P->Z + (size_t)j * n * P->tsize;
+        launch_cpr(P, vj, zj, BO_STAGE_CPR, st);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (o->profile && prof.size() < 512) {
+          e0 = P->prof_ev[2 * prof.size()];
+          e1 = P->prof_ev[2 * prof.size() + 1];
+          cudaEventRecord(e0, s);
+        }
+        if (P->fp32) launch_arnoldi_spmv<float>(P, zj, w);
+        else launch_arnoldi_spmv<double>(P, zj, w);
+        if (e1) {
+          cudaEventRecord(e1, s);
+          prof.push_back({e0, e1});
+        }
+        dim3 gd(mdot_chunks(n), j + 1);
+        (k_mdot<<<gd, kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, P->partials, st, 0), note_launch());
+        (k_update<<<grid_for(n), kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, 0, 0, P->partials, st), note_launch());
+        (k_mdot<<<gd, kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, P->partials, st, kMaxM), note_launch());
+        (k_update<<<grid_for(n), kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, kMaxM, 1, P->partials, st), note_launch());
+        (k_givens<<<1, 32, 0, s>>>(st, P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j), note_launch());
+        (k_scale<<<grid_for(n), kThreads, 0, s>>>(n, w, w, st, 1, 1), note_launch());
+        cudaMemcpyAsync(&P->h_st[j & 1], st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(P->ev[j & 1], s);
+        ++enq;
+        if (j >= 1) {
+          if (cudaEventSynchronize(P->ev[(j - 1) & 1]) != cudaSuccess) return BO_ERR_CUDA;
+          if (P->h_st[(j - 1) & 1].done) break;
+        }
+      }
+      (k_trisolve<<<1, 32, 0, s>>>(st, P->H, P->gvec, P->y, m), note_launch());
+      if (P->fp32) (k_xupdate<float><<<grid_for(n), kThreads, 0, s>>>(n, P->xi, (const float*)P->Z, n, P->y, st), note_launch());
+      else (k_xupdate<double><<<grid_for(n), kThreads, 0, s>>>(n, P->xi, (const double*)P->Z, n, P->y, st), note_launch());
+      (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, M->A, P->bi, P->xi, P->rk, P->partials, st), note_launch());
+      cudaMemcpyAsync(P->h_st, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
+      const DevState& h = P->h_st[0];
+      ++restarts;
+      its += h.k;
+      beta = h.beta;
+      est = h.est;
+      if (h.err & kErrNonfinite) { status = BO_ERR_BREAKDOWN; break; }
+      if (h.k == 0) break;
+    }
+    if (status == BO_OK && beta > target) status = BO_ERR_NOT_CONVERGED;
+    const int nh = its < kHistCap ? its : kHistCap;
+    if (nh > 0) cudaMemcpy(P->hist, dhist, nh * sizeof(double), cudaMemcpyDeviceToHost);
+    for (int i = 0; i < nh; ++i) P->hist[i] /= bnorm;
+    P->nhist = nh;
+  }
+  // result back in natural order
+  launch_scatter(g, P->xi, x_d, s);
+  if (o->mem == BO_MEM_HOST) cudaMemcpyAsync(x_in, x_d, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
+  if (info) {
+    info->status = status;
+    info->iters = its;
+    info->restarts = restarts;
+    info->true_rel_res = bnorm > 0 ? beta / bnorm : beta;
+    info->est_rel_res = bnorm > 0 ? est / bnorm : est;
+    info->spmv_launches = 0;
+    info->spmv_ms = 0.0;
+    for (size_t i = 0; i < prof.size(); ++i) {
+      if ((int)i < its) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, prof[i].first, prof[i].second);
+        info->spmv_ms += ms;
+        info->spmv_launches++;
+      }
+    }
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+}  // namespace bo

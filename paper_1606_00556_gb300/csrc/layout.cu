@@ -1,0 +1,215 @@
+// Matrix ingest (BSR / CSR -> colour-split planes), the public BSR SpMV
+// (paper Sec. 3.3: y = alpha A x + beta y), natural <-> internal vector
+// permutations and the Newton update (paper Alg. 1: x^l = x^{l-1} + dx).
+#include "bo_internal.cuh"
+
+namespace bo {
+namespace {
+
+struct Nat {
+  int32_t i, j, k;
+  int color;
+  int64_t q;
+};
+
+__device__ __forceinline__ Nat decode_nat(const Geom& g, int64_t c) {
+  const int64_t r = c / g.nx;
+  Nat n;
+  n.i = (int32_t)(c - r * g.nx);
+  n.j = (int32_t)(r % g.ny);
+  n.k = (int32_t)(r / g.ny);
+  n.color = (n.i + n.j + n.k) & 1;
+  n.q = c >> 1;
+  return n;
+}
+
+// stencil slot of column offset d for a cell at (i, j, k), or -1
+__device__ __forceinline__ int slot_of(const Geom& g, const Nat& n, int64_t d) {
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  if (d == 0) return kDiag;
+  if (d == -1 && n.i > 0) return kXm;
+  if (d == 1 && n.i < g.nx - 1) return kXp;
+  if (d == -nxy && n.k > 0) return kZm;
+  if (d == nxy && n.k < g.nz - 1) return kZp;
+  if (d == -(int64_t)g.nx && n.j > 0) return kYm;
+  if (d == (int64_t)g.nx && n.j < g.ny - 1) return kYp;
+  return -1;
+}
+
+__device__ __forceinline__ unsigned valid_slots(const Geom& g, const Nat& n) {
+  unsigned m = 1u << kDiag;
+  if (n.k > 0) m |= 1u << kZm;
+  if (n.j > 0) m |= 1u << kYm;
+  if (n.i > 0) m |= 1u << kXm;
+  if (n.i < g.nx - 1) m |= 1u << kXp;
+  if (n.j < g.ny - 1) m |= 1u << kYp;
+  if (n.k < g.nz - 1) m |= 1u << kZp;
+  return m;
+}
+
+// One thread per cell: check the block row's pattern against the stencil
+// and scatter its 3x3 blocks into the colour-split planes.
+__global__ void k_ingest_bsr(Geom g, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, int64_t nnz, double* __restrict__ A, int* flags) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
+    const Nat n = decode_nat(g, c);
+    const unsigned valid = valid_slots(g, n);
+    const int32_t e0 = rowptr[c], e1 = rowptr[c + 1];
+    unsigned seen = 0;
+    int bad = e0 < 0 || e1 < e0 || e1 > nnz || (e1 - e0) != __popc(valid);
+    int nonfinite = 0;
+    for (int32_t e = e0; e < e1 && !bad; ++e) {
+      const int s = slot_of(g, n, (int64_t)col[e] - c);
+      if (s < 0 || ((seen >> s) & 1u)) { bad = 1; break; }
+      seen |= 1u << s;
+      const double* v = val + 9 * (size_t)e;
+#pragma unroll
+      for (int rc = 0; rc < 9; ++rc) {
+        const double a = v[rc];
+        nonfinite |= !isfinite(a);
+        A[plane(g, n.color, s, rc) + n.q] = a;
+      }
+    }
+    for (int s = 0; s < 7; ++s)
+      if (!((valid >> s) & 1u))
+        for (int rc = 0; rc < 9; ++rc) A[plane(g, n.color, s, rc) + n.q] = 0.0;
+    if (bad) atomicOr(flags, kErrPattern);
+    if (nonfinite) atomicOr(flags, kErrNonfinite);
+  }
+}
+
+// One thread per cell: zero the cell's blocks, then add every scalar entry
+// of its three CSR rows (row 3c+r, column 3c'+k) into block (c, c').
+__global__ void k_ingest_csr(Geom g, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, int64_t nnz, double* __restrict__ A, int* flags) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
+    const Nat n = decode_nat(g, c);
+    for (int s = 0; s < 7; ++s)
+      for (int rc = 0; rc < 9; ++rc) A[plane(g, n.color, s, rc) + n.q] = 0.0;
+    int bad = 0, nonfinite = 0;
+    for (int r = 0; r < 3; ++r) {
+      const int64_t row = 3 * c + r;
+      const int32_t e0 = rowptr[row], e1 = rowptr[row + 1];
+      if (e0 < 0 || e1 < e0 || e1 > nnz) { bad = 1; continue; }
+      for (int32_t e = e0; e < e1; ++e) {
+        if (col[e] < 0) { bad = 1; continue; }
+        const int64_t cc = col[e] / 3;
+        const int k = col[e] - 3 * (int32_t)cc;
+        const int s = slot_of(g, n, cc - c);
+        if (s < 0) { bad = 1; continue; }
+        const double a = val[e];
+        nonfinite |= !isfinite(a);
+        A[plane(g, n.color, s, 3 * r + k) + n.q] += a;
+      }
+    }
+    if (bad) atomicOr(flags, kErrPattern);
+    if (nonfinite) atomicOr(flags, kErrNonfinite);
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// y = alpha A x + beta y on natural-order interleaved vectors.  One thread
+// per cell; neighbouring lanes alternate colours, so each warp reads 16
+// consecutive values from each colour's plane per load instruction.
+template <typename TM>
+__global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restrict__ A, const double* __restrict__ x,
+                                                      double* __restrict__ y, double alpha, double beta) {
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
+    const Nat n = decode_nat(g, c);
+    const unsigned valid = valid_slots(g, n);
+    const int64_t off[7] = {-nxy, -(int64_t)g.nx, -1, 0, 1, (int64_t)g.nx, nxy};
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      if ((valid >> s) & 1u) {
+        const int64_t nc = c + off[s];
+        const double x0 = __ldg(x + 3 * nc), x1 = __ldg(x + 3 * nc + 1), x2 = __ldg(x + 3 * nc + 2);
+        const TM* a = A + plane(g, n.color, s, 0) + n.q;
+        const size_t P = (size_t)g.Nh;
+        acc0 += (double)ld_stream(a) * x0 + (double)ld_stream(a + P) * x1 + (double)ld_stream(a + 2 * P) * x2;
+        acc1 += (double)ld_stream(a + 3 * P) * x0 + (double)ld_stream(a + 4 * P) * x1 + (double)ld_stream(a + 5 * P) * x2;
+        acc2 += (double)ld_stream(a + 6 * P) * x0 + (double)ld_stream(a + 7 * P) * x1 + (double)ld_stream(a + 8 * P) * x2;
+      }
+    }
+    if (beta == 0.0) {
+      y[3 * c] = alpha * acc0;
+      y[3 * c + 1] = alpha * acc1;
+      y[3 * c + 2] = alpha * acc2;
+    } else {
+      y[3 * c] = alpha * acc0 + beta * y[3 * c];
+      y[3 * c + 1] = alpha * acc1 + beta * y[3 * c + 1];
+      y[3 * c + 2] = alpha * acc2 + beta * y[3 * c + 2];
+    }
+  }
+}
+
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+__global__ void k_gather(Geom g, const double* __restrict__ nat, double* __restrict__ in) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
+    const Nat n = decode_nat(g, c);
+    for (int k = 0; k < 3; ++k) in[vidx(g, k, n.color, n.q)] = nat[3 * c + k];
+  }
+}
+
+__global__ void k_scatter(Geom g, const double* __restrict__ in, double* __restrict__ nat) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
+    const Nat n = decode_nat(g, c);
+    for (int k = 0; k < 3; ++k) nat[3 * c + k] = in[vidx(g, k, n.color, n.q)];
+  }
+}
+
+__global__ void k_axpy1(double* __restrict__ s, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s[i] += d[i];
+}
+
+}  // namespace
+
+int ingest_bsr(bo_mat* m, const double* dval) {
+  (k_ingest_bsr<<<grid_for(m->g.N), kThreads, 0, m->ctx->stream>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
+  return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
+}
+
+int ingest_csr(bo_mat* m, const double* dval) {
+  (k_ingest_csr<<<grid_for(m->g.N), kThreads, 0, m->ctx->stream>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
+  return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
+}
+
+void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
+  (k_to_f32<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
+}
+
+void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, bool fp32) {
+  const int grid = grid_for(m->g.N, kThreads, 152 * 64);
+  if (fp32)
+    (k_spmv_nat<float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A32, x, y, alpha, beta), note_launch());
+  else
+    (k_spmv_nat<double><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A, x, y, alpha, beta), note_launch());
+}
+
+void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s) {
+  (k_widen<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
+}
+
+void launch_gather(const Geom& g, const double* nat, double* in, cudaStream_t s) {
+  (k_gather<<<grid_for(g.N), kThreads, 0, s>>>(g, nat, in), note_launch());
+}
+
+void launch_scatter(const Geom& g, const double* in, double* nat, cudaStream_t s) {
+  (k_scatter<<<grid_for(g.N), kThreads, 0, s>>>(g, in, nat), note_launch());
+}
+
+void launch_newton_update(double* state, const double* dx, int64_t n, cudaStream_t s) {
+  (k_axpy1<<<grid_for(n), kThreads, 0, s>>>(state, dx, n), note_launch());
+}
+
+}  // namespace bo

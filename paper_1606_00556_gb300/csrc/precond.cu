@@ -1,0 +1,985 @@
+// CPR-FPF preconditioner (paper Sec. 3.2, Alg. 2) on the colour-split
+// layout: Quasi-IMPES decoupling, red-black block ILU(0) as the local solver
+// R, an aggregation AMG V-cycle on the pressure block A_pp, and their
+// composition.
+//
+// Red-black block ILU(0).  With the red cells ordered first, red rows have
+// no lower part and black-black blocks lie off the pattern except on the
+// diagonal, so ILU(0) reduces to
+//     D_b' = D_b - sum_{r ~ b} A_br D_r^{-1} A_rb     (pivot blocks of black cells)
+// and (L U)^{-1} f is three stencil passes:
+//     t_r = D_r^{-1} f_r;   z_b = D_b'^{-1} (f_b - sum A_br t_r);
+//     z_r = t_r - D_r^{-1} sum A_rb z_b.
+//
+// AMG.  Level 0 is the (0,0) entry of every block of D_QI^{-1} A on the
+// colour-split grid; level l+1 aggregates the 2x2x2 boxes of level l
+// (piecewise-constant P, Galerkin P^T A P, still 7-point); coarsening stops
+// at <= coarse_max cells, whose dense inverse is formed once per setup.
+// V(nu1, nu2) with red-black Gauss-Seidel: red then black before the coarse
+// correction, black then red after it.  After a black half sweep only red
+// cells carry a residual, so restriction sums red residuals.  Levels of at
+// most kTailCells cells run inside one thread block (kernel k_tail).
+#include <cstdio>
+
+#include "bo_internal.cuh"
+
+namespace bo {
+namespace {
+
+constexpr int kTailThreads = 1024;
+constexpr int64_t kTailCells = 32768;
+constexpr int kCoarseMax = 128;
+
+// ---------------------------------------------------------------- 3x3 blocks
+// inverse by Gauss-Jordan elimination with partial pivoting; false if a
+// pivot is zero or the result is not finite
+__device__ bool inv3(const double a[9], double out[9]) {
+  double m[3][6];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      m[i][j] = a[3 * i + j];
+      m[i][3 + j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int k = 0; k < 3; ++k) {
+    int p = k;
+    for (int i = k + 1; i < 3; ++i)
+      if (fabs(m[i][k]) > fabs(m[p][k])) p = i;
+    if (m[p][k] == 0.0) return false;
+    if (p != k)
+      for (int j = 0; j < 6; ++j) { const double t = m[k][j]; m[k][j] = m[p][j]; m[p][j] = t; }
+    const double piv = m[k][k];
+    for (int j = 0; j < 6; ++j) m[k][j] /= piv;
+    for (int i = 0; i < 3; ++i) {
+      if (i == k) continue;
+      const double f = m[i][k];
+      for (int j = 0; j < 6; ++j) m[i][j] -= f * m[k][j];
+    }
+  }
+  bool ok = true;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      out[3 * i + j] = m[i][3 + j];
+      ok &= isfinite(out[3 * i + j]);
+    }
+  return ok;
+}
+
+// decoupled block (colour, slot) of the cell at half index q: row 0 becomes
+// row0 - w_w row1 - w_g row2 (paper Sec. 3.2, D_QI^{-1} A), FP64
+__device__ __forceinline__ void dec_block(const Geom& g, const double* __restrict__ A, const double* __restrict__ w,
+                                          int color, int slot, int64_t q, double b[9]) {
+  const double ww = w[vidx(g, 0, color, q)], wg = w[vidx(g, 1, color, q)];
+  double a[9];
+#pragma unroll
+  for (int rc = 0; rc < 9; ++rc) a[rc] = A[plane(g, color, slot, rc) + q];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    b[c] = a[c] - ww * a[3 + c] - wg * a[6 + c];
+    b[3 + c] = a[3 + c];
+    b[6 + c] = a[6 + c];
+  }
+}
+
+__device__ __forceinline__ void mul3(const double a[9], const double b[9], double c[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+
+// ---------------------------------------------------------------- setup kernels
+// Quasi-IMPES decoupling: weights and decoupled planes in precision T
+template <typename T>
+__global__ void k_decouple(Geom g, const double* __restrict__ A, T* __restrict__ At, double* __restrict__ w,
+                           DevState* st) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int color = (int)(t / g.Nh);
+    const int64_t q = t - color * g.Nh;
+    const double a11 = A[plane(g, color, kDiag, 4) + q], a22 = A[plane(g, color, kDiag, 8) + q];
+    double ww = 0.0, wg = 0.0;
+    if (a11 == 0.0 || a22 == 0.0 || !isfinite(a11) || !isfinite(a22)) {
+      atomicOr(&st->err, kErrBreakdown);
+    } else {
+      ww = A[plane(g, color, kDiag, 1) + q] / a11;
+      wg = A[plane(g, color, kDiag, 2) + q] / a22;
+    }
+    w[vidx(g, 0, color, q)] = ww;
+    w[vidx(g, 1, color, q)] = wg;
+    for (int s = 0; s < 7; ++s) {
+      double a[9];
+#pragma unroll
+      for (int rc = 0; rc < 9; ++rc) a[rc] = A[plane(g, color, s, rc) + q];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        At[plane(g, color, s, c) + q] = (T)(a[c] - ww * a[3 + c] - wg * a[6 + c]);
+        At[plane(g, color, s, 3 + c) + q] = (T)a[3 + c];
+        At[plane(g, color, s, 6 + c) + q] = (T)a[6 + c];
+      }
+      if (s == kDiag) {
+        const double app = a[0] - ww * a[3] - wg * a[6];
+        if (app == 0.0 || !isfinite(app)) atomicOr(&st->err, kErrBreakdown);
+      }
+    }
+  }
+}
+
+// red pivots: D_r^{-1} of the decoupled diagonal blocks
+__global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w,
+                          double* __restrict__ Dinv, DevState* st) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    double d[9], inv[9];
+    dec_block(g, A, w, 0, kDiag, q, d);
+    if (!inv3(d, inv)) {
+      atomicOr(&st->err, kErrBreakdown);
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
+    }
+    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + q] = inv[rc];
+  }
+}
+
+// black pivots: D_b' = D_b - sum_r A_br D_r^{-1} A_rb, stored inverted
+__global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* __restrict__ w,
+                            double* __restrict__ Dinv, DevState* st) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = decode(g, 1, q);
+    double S[9], inv[9];
+    dec_block(g, A, w, 1, kDiag, q, S);
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      if (s == kDiag) continue;
+      const int64_t nq = nbr(g, c, q, s);
+      if (nq < 0) continue;
+      double L[9], U[9], Dr[9], T1[9], T2[9];
+      dec_block(g, A, w, 1, s, q, L);
+      dec_block(g, A, w, 0, opposite(s), nq, U);
+      for (int rc = 0; rc < 9; ++rc) Dr[rc] = Dinv[(size_t)rc * g.N + nq];
+      mul3(L, Dr, T1);
+      mul3(T1, U, T2);
+      for (int rc = 0; rc < 9; ++rc) S[rc] -= T2[rc];
+    }
+    if (!inv3(S, inv)) {
+      atomicOr(&st->err, kErrBreakdown);
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
+    }
+    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = inv[rc];
+  }
+}
+
+template <typename T>
+__global__ void k_convert(const double* __restrict__ src, T* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+// ------------------------------------------------------------ AMG setup
+struct LevelDims {
+  int32_t nx, ny, nz;
+  int64_t n;
+};
+
+__device__ __forceinline__ int64_t nat_index(const LevelDims& L, int i, int j, int k) {
+  return i + (int64_t)L.nx * (j + (int64_t)L.ny * k);
+}
+
+// direction slot of the coarse neighbour (di, dj, dk), or kDiag
+__device__ __forceinline__ int dir_slot(int di, int dj, int dk) {
+  if (dk < 0) return kZm;
+  if (dk > 0) return kZp;
+  if (dj < 0) return kYm;
+  if (dj > 0) return kYp;
+  if (di < 0) return kXm;
+  if (di > 0) return kXp;
+  return kDiag;
+}
+
+// Galerkin level 1 from level 0 (the decoupled pressure block, FP64 from A
+// and the weights): coarse entry (I, J) = sum of fine a_ij, i in I, j in J.
+__global__ void k_galerkin0(Geom g, const double* __restrict__ A, const double* __restrict__ w, LevelDims C,
+                            double* __restrict__ c64, DevState* st) {
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
+          if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+          const int color = (i + j + k) & 1;
+          const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
+          const double ww = w[vidx(g, 0, color, q)], wg = w[vidx(g, 1, color, q)];
+          const int ni[7] = {i, i, i - 1, i, i + 1, i, i};
+          const int nj[7] = {j, j - 1, j, j, j, j + 1, j};
+          const int nk[7] = {k - 1, k, k, k, k, k, k + 1};
+          for (int s = 0; s < 7; ++s) {
+            if (ni[s] < 0 || ni[s] >= g.nx || nj[s] < 0 || nj[s] >= g.ny || nk[s] < 0 || nk[s] >= g.nz) continue;
+            const double a = A[plane(g, color, s, 0) + q] - ww * A[plane(g, color, s, 3) + q] -
+                             wg * A[plane(g, color, s, 6) + q];
+            const int cs = dir_slot(ni[s] / 2 - ci, nj[s] / 2 - cj, nk[s] / 2 - ck);
+            acc[cs] += a;
+          }
+        }
+    for (int s = 0; s < 7; ++s) c64[(size_t)s * C.n + I] = acc[s];
+    if (acc[kDiag] == 0.0 || !isfinite(acc[kDiag])) atomicOr(&st->err, kErrBreakdown);
+  }
+}
+
+// Galerkin level l+1 from natural-order level l
+__global__ void k_galerkinn(LevelDims F, const double* __restrict__ f64, LevelDims C, double* __restrict__ c64,
+                            DevState* st) {
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
+          if (i >= F.nx || j >= F.ny || k >= F.nz) continue;
+          const int64_t c = nat_index(F, i, j, k);
+          const int ni[7] = {i, i, i - 1, i, i + 1, i, i};
+          const int nj[7] = {j, j - 1, j, j, j, j + 1, j};
+          const int nk[7] = {k - 1, k, k, k, k, k, k + 1};
+          for (int s = 0; s < 7; ++s) {
+            if (ni[s] < 0 || ni[s] >= F.nx || nj[s] < 0 || nj[s] >= F.ny || nk[s] < 0 || nk[s] >= F.nz) continue;
+            acc[dir_slot(ni[s] / 2 - ci, nj[s] / 2 - cj, nk[s] / 2 - ck)] += f64[(size_t)s * F.n + c];
+          }
+        }
+    for (int s = 0; s < 7; ++s) c64[(size_t)s * C.n + I] = acc[s];
+    if (acc[kDiag] == 0.0 || !isfinite(acc[kDiag])) atomicOr(&st->err, kErrBreakdown);
+  }
+}
+
+// dense coarsest matrix: natural level (c64 given) or level 0 in the
+// colour-split index order (index = colour * N/2 + q)
+__global__ void k_dense_from_level(LevelDims L, const double* __restrict__ c64, Geom g, const double* __restrict__ A,
+                                   const double* __restrict__ w, int level0, double* __restrict__ M) {
+  const int64_t n = L.n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n; t += (int64_t)gridDim.x * blockDim.x)
+    M[t] = 0.0;
+  __syncthreads();
+  if (blockIdx.x != 0) return;
+  // one block fills the stencil entries (grid of at most 128 cells)
+  for (int64_t row = threadIdx.x; row < n; row += blockDim.x) {
+    int i, j, k;
+    if (level0) {
+      const int color = (int)(row / g.Nh);
+      const int64_t q = row - color * g.Nh;
+      const Cell c = decode(g, color, q);
+      i = c.i; j = c.j; k = c.k;
+    } else {
+      i = (int)(row % L.nx); j = (int)((row / L.nx) % L.ny); k = (int)(row / ((int64_t)L.nx * L.ny));
+    }
+    const int ni[7] = {i, i, i - 1, i, i + 1, i, i};
+    const int nj[7] = {j, j - 1, j, j, j, j + 1, j};
+    const int nk[7] = {k - 1, k, k, k, k, k, k + 1};
+    for (int s = 0; s < 7; ++s) {
+      if (ni[s] < 0 || ni[s] >= L.nx || nj[s] < 0 || nj[s] >= L.ny || nk[s] < 0 || nk[s] >= L.nz) continue;
+      double a;
+      int64_t colidx;
+      if (level0) {
+        const int color = (i + j + k) & 1;
+        const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
+        a = A[plane(g, color, s, 0) + q] - w[vidx(g, 0, color, q)] * A[plane(g, color, s, 3) + q] -
+            w[vidx(g, 1, color, q)] * A[plane(g, color, s, 6) + q];
+        const int ncol = (ni[s] + nj[s] + nk[s]) & 1;
+        colidx = ncol * g.Nh + ((ni[s] + (int64_t)g.nx * (nj[s] + (int64_t)g.ny * nk[s])) >> 1);
+      } else {
+        a = c64[(size_t)s * n + row];
+        colidx = nat_index(L, ni[s], nj[s], nk[s]);
+      }
+      M[row * n + colidx] += a;
+    }
+  }
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting of an n x n matrix
+// (n <= kCoarseMax) in shared memory by one thread block; the inverse is
+// written to Minv in precision T.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __restrict__ M, T* __restrict__ Minv, DevState* st) {
+  extern __shared__ double sm[];
+  double* a = sm;                 // n * n
+  int* perm = (int*)(a + n * n);  // n
+  __shared__ int piv;
+  __shared__ int fail;
+  __shared__ double fac[kCoarseMax];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = M[t];
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      for (int i = k + 1; i < n; ++i)
+        if (fabs(a[i * n + k]) > fabs(a[p * n + k])) p = i;
+      piv = p;
+      perm[k] = p;
+      if (a[p * n + k] == 0.0) fail = 1;
+    }
+    __syncthreads();
+    if (fail) break;
+    if (piv != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double t = a[k * n + j];
+        a[k * n + j] = a[piv * n + j];
+        a[piv * n + j] = t;
+      }
+    __syncthreads();
+    const double pv = a[k * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) / pv;
+    __syncthreads();
+    // eliminate column k from every other row; factors first, so that the
+    // row updates below read unmodified values
+    for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = a[i * n + k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, j = t - (t / n) * n;
+      if (i == k) continue;
+      const double base = (j == k) ? 0.0 : a[i * n + j];
+      a[i * n + j] = base - fac[i] * a[k * n + j];
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (threadIdx.x == 0) atomicOr(&st->err, kErrBreakdown);
+    return;
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t = a[i * n + k];
+        a[i * n + k] = a[i * n + p];
+        a[i * n + p] = t;
+      }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    Minv[t] = (T)a[t];
+    if (!isfinite(a[t])) atomicOr(&st->err, kErrBreakdown);
+  }
+}
+
+// ------------------------------------------------------------ apply kernels
+// f = D_QI^{-1} v (all cells), v FP64 internal, f precision T
+template <typename T>
+__global__ void k_decouple_vec(Geom g, const double* __restrict__ v, const double* __restrict__ w, T* __restrict__ f,
+                               const DevState* st) {
+  if (st->done) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const double v0 = v[t], v1 = v[g.N + t], v2 = v[2 * g.N + t];
+    f[t] = (T)(v0 - w[t] * v1 - w[g.N + t] * v2);
+    f[g.N + t] = (T)v1;
+    f[2 * g.N + t] = (T)v2;
+  }
+}
+
+template <typename T>
+__global__ void k_copy_vec(int64_t n, const double* __restrict__ v, T* __restrict__ f, const DevState* st) {
+  if (st->done) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    f[t] = (T)v[t];
+}
+
+// ILU pass 1 (red): t_r = D_r^{-1} src_r
+template <typename T>
+__global__ void k_ilu_r1(Geom g, const T* __restrict__ Dinv, const T* __restrict__ src, T* __restrict__ tv,
+                         const DevState* st) {
+  if (st->done) return;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    const T f0 = src[vidx(g, 0, 0, q)], f1 = src[vidx(g, 1, 0, q)], f2 = src[vidx(g, 2, 0, q)];
+    T d[9];
+#pragma unroll
+    for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + q];
+    tv[vidx(g, 0, 0, q)] = d[0] * f0 + d[1] * f1 + d[2] * f2;
+    tv[vidx(g, 1, 0, q)] = d[3] * f0 + d[4] * f1 + d[5] * f2;
+    tv[vidx(g, 2, 0, q)] = d[6] * f0 + d[7] * f1 + d[8] * f2;
+  }
+}
+
+// sum over the six off-diagonal blocks of a row of At times the other
+// colour's vector u: s = sum_s At[color][s] u[nbr]
+template <typename T>
+__device__ __forceinline__ void offdiag_sum(const Geom& g, const T* __restrict__ At, int color, int64_t q,
+                                            const Cell& c, const T* __restrict__ u, T s[3]) {
+  const int oc = color ^ 1;
+  s[0] = s[1] = s[2] = T(0);
+#pragma unroll
+  for (int sl = 0; sl < 7; ++sl) {
+    if (sl == kDiag) continue;
+    const int64_t nq = nbr(g, c, q, sl);
+    if (nq < 0) continue;
+    const T u0 = u[vidx(g, 0, oc, nq)], u1 = u[vidx(g, 1, oc, nq)], u2 = u[vidx(g, 2, oc, nq)];
+    const T* a = At + plane(g, color, sl, 0) + q;
+    const size_t P = (size_t)g.Nh;
+    s[0] += ld_stream(a) * u0 + ld_stream(a + P) * u1 + ld_stream(a + 2 * P) * u2;
+    s[1] += ld_stream(a + 3 * P) * u0 + ld_stream(a + 4 * P) * u1 + ld_stream(a + 5 * P) * u2;
+    s[2] += ld_stream(a + 6 * P) * u0 + ld_stream(a + 7 * P) * u1 + ld_stream(a + 8 * P) * u2;
+  }
+}
+
+// ILU pass 2 (black): u_b = D_b'^{-1} (src_b - sum A_br t_r).
+// ACC = false: z_b = u_b.  ACC = true: t_b = u_b, z_b += u_b (+ e_b on p).
+template <typename T, bool ACC>
+__global__ void k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ src,
+                        T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, const DevState* st) {
+  if (st->done) return;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = decode(g, 1, q);
+    T s[3];
+    offdiag_sum(g, At, 1, q, c, tv, s);
+    const T r0 = src[vidx(g, 0, 1, q)] - s[0], r1 = src[vidx(g, 1, 1, q)] - s[1], r2 = src[vidx(g, 2, 1, q)] - s[2];
+    T d[9];
+#pragma unroll
+    for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + g.Nh + q];
+    const T u0 = d[0] * r0 + d[1] * r1 + d[2] * r2;
+    const T u1 = d[3] * r0 + d[4] * r1 + d[5] * r2;
+    const T u2 = d[6] * r0 + d[7] * r1 + d[8] * r2;
+    if (ACC) {
+      tv[vidx(g, 0, 1, q)] = u0;
+      tv[vidx(g, 1, 1, q)] = u1;
+      tv[vidx(g, 2, 1, q)] = u2;
+      z[vidx(g, 0, 1, q)] += u0 + e[g.Nh + q];
+      z[vidx(g, 1, 1, q)] += u1;
+      z[vidx(g, 2, 1, q)] += u2;
+    } else {
+      z[vidx(g, 0, 1, q)] = u0;
+      z[vidx(g, 1, 1, q)] = u1;
+      z[vidx(g, 2, 1, q)] = u2;
+    }
+  }
+}
+
+// ILU pass 3 (red): corr = D_r^{-1} sum A_rb u_b, with u_b in `ub` (black half).
+// ACC = false: z_r = t_r - corr.  ACC = true: z_r += t_r - corr (+ e_r on p).
+template <typename T, bool ACC>
+__global__ void k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ tv,
+                         const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, const DevState* st) {
+  if (st->done) return;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = decode(g, 0, q);
+    T s[3];
+    offdiag_sum(g, At, 0, q, c, ub, s);
+    T d[9];
+#pragma unroll
+    for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + q];
+    const T c0 = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
+    const T c1 = d[3] * s[0] + d[4] * s[1] + d[5] * s[2];
+    const T c2 = d[6] * s[0] + d[7] * s[1] + d[8] * s[2];
+    const T t0 = tv[vidx(g, 0, 0, q)] - c0, t1 = tv[vidx(g, 1, 0, q)] - c1, t2 = tv[vidx(g, 2, 0, q)] - c2;
+    if (ACC) {
+      z[vidx(g, 0, 0, q)] += t0 + e[q];
+      z[vidx(g, 1, 0, q)] += t1;
+      z[vidx(g, 2, 0, q)] += t2;
+    } else {
+      z[vidx(g, 0, 0, q)] = t0;
+      z[vidx(g, 1, 0, q)] = t1;
+      z[vidx(g, 2, 0, q)] = t2;
+    }
+  }
+}
+
+// Residuals of the decoupled system in precision T.
+// ROWS = 1: out[t] = f_p - (At z)_p for all cells (the AMG right-hand side).
+// ROWS = 3: out = f - At (z + Pi_p e), all components.
+template <typename T, int ROWS>
+__global__ void k_cpr_residual(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
+                               const T* __restrict__ e, T* __restrict__ out, const DevState* st) {
+  if (st->done) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int color = (int)(t / g.Nh);
+    const int64_t q = t - color * g.Nh;
+    const Cell c = decode(g, color, q);
+    T acc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r] = T(0);
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      const int64_t nq = nbr(g, c, q, sl);
+      if (nq < 0) continue;
+      const int xc = (sl == kDiag) ? color : (color ^ 1);
+      T x0 = z[vidx(g, 0, xc, nq)];
+      if (ROWS == 3) x0 += e[(size_t)xc * g.Nh + nq];
+      const T x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
+      const T* a = At + plane(g, color, sl, 0) + q;
+      const size_t P = (size_t)g.Nh;
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+        acc[r] += ld_stream(a + 3 * r * P) * x0 + ld_stream(a + (3 * r + 1) * P) * x1 + ld_stream(a + (3 * r + 2) * P) * x2;
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) out[(size_t)r * g.N + t] = f[(size_t)r * g.N + t] - acc[r];
+  }
+}
+
+// ---- AMG level 0 (colour-split, coefficients = plane (colour, slot, 0) of At)
+template <typename T>
+__global__ void k_gs0(Geom g, const T* __restrict__ At, const T* __restrict__ f, T* __restrict__ x, int color,
+                      int zero_guess, const DevState* st) {
+  if (st->done) return;
+  const int oc = color ^ 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    T s = f[(size_t)color * g.Nh + q];
+    if (!zero_guess) {
+      const Cell c = decode(g, color, q);
+#pragma unroll
+      for (int sl = 0; sl < 7; ++sl) {
+        if (sl == kDiag) continue;
+        const int64_t nq = nbr(g, c, q, sl);
+        if (nq < 0) continue;
+        s -= At[plane(g, color, sl, 0) + q] * x[(size_t)oc * g.Nh + nq];
+      }
+    }
+    x[(size_t)color * g.Nh + q] = s / At[plane(g, color, kDiag, 0) + q];
+  }
+}
+
+// f1[I] = sum of level-0 residuals over aggregate I (red cells only when
+// the last half sweep was black)
+template <typename T>
+__global__ void k_restrict0(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ x,
+                            LevelDims C, T* __restrict__ fc, int red_only, const DevState* st) {
+  if (st->done) return;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+    T acc = T(0);
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
+          if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+          const int color = (i + j + k) & 1;
+          if (red_only && color == 1) continue;
+          const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
+          const Cell c{i, j, k, i & 1};
+          T r = f[(size_t)color * g.Nh + q];
+#pragma unroll
+          for (int sl = 0; sl < 7; ++sl) {
+            const int64_t nq = nbr(g, c, q, sl);
+            if (nq < 0) continue;
+            const int xc = (sl == kDiag) ? color : (color ^ 1);
+            r -= At[plane(g, color, sl, 0) + q] * x[(size_t)xc * g.Nh + nq];
+          }
+          acc += r;
+        }
+    fc[I] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_prolong0(Geom g, T* __restrict__ x, LevelDims C, const T* __restrict__ xc, T s, const DevState* st) {
+  if (st->done) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int color = (int)(t / g.Nh);
+    const int64_t q = t - color * g.Nh;
+    const Cell c = decode(g, color, q);
+    x[t] += s * xc[nat_index(C, c.i / 2, c.j / 2, c.k / 2)];
+  }
+}
+
+// ---- natural-order levels (device functions shared by the multi-block
+// kernels and the single-block tail)
+template <typename T>
+struct LevelView {
+  LevelDims d;
+  const T* c;  // 7 n coefficients
+  T* f;
+  T* x;
+};
+
+template <typename T>
+__device__ __forceinline__ void gs_cell(const LevelView<T>& L, int64_t cidx, int color, int zero_guess) {
+  const int i = (int)(cidx % L.d.nx), j = (int)((cidx / L.d.nx) % L.d.ny), k = (int)(cidx / ((int64_t)L.d.nx * L.d.ny));
+  if (((i + j + k) & 1) != color) return;
+  T s = L.f[cidx];
+  if (!zero_guess) {
+    const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
+    if (k > 0) s -= L.c[kZm * L.d.n + cidx] * L.x[cidx - nxy];
+    if (j > 0) s -= L.c[kYm * L.d.n + cidx] * L.x[cidx - L.d.nx];
+    if (i > 0) s -= L.c[kXm * L.d.n + cidx] * L.x[cidx - 1];
+    if (i < L.d.nx - 1) s -= L.c[kXp * L.d.n + cidx] * L.x[cidx + 1];
+    if (j < L.d.ny - 1) s -= L.c[kYp * L.d.n + cidx] * L.x[cidx + L.d.nx];
+    if (k < L.d.nz - 1) s -= L.c[kZp * L.d.n + cidx] * L.x[cidx + nxy];
+  }
+  L.x[cidx] = s / L.c[kDiag * L.d.n + cidx];
+}
+
+template <typename T>
+__device__ __forceinline__ T residual_cell(const LevelView<T>& L, int i, int j, int k) {
+  const int64_t cidx = nat_index(L.d, i, j, k);
+  const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
+  T r = L.f[cidx] - L.c[kDiag * L.d.n + cidx] * L.x[cidx];
+  if (k > 0) r -= L.c[kZm * L.d.n + cidx] * L.x[cidx - nxy];
+  if (j > 0) r -= L.c[kYm * L.d.n + cidx] * L.x[cidx - L.d.nx];
+  if (i > 0) r -= L.c[kXm * L.d.n + cidx] * L.x[cidx - 1];
+  if (i < L.d.nx - 1) r -= L.c[kXp * L.d.n + cidx] * L.x[cidx + 1];
+  if (j < L.d.ny - 1) r -= L.c[kYp * L.d.n + cidx] * L.x[cidx + L.d.nx];
+  if (k < L.d.nz - 1) r -= L.c[kZp * L.d.n + cidx] * L.x[cidx + nxy];
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T restrict_cell(const LevelView<T>& F, const LevelDims& C, int64_t I, int red_only) {
+  const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+  T acc = T(0);
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
+        if (i >= F.d.nx || j >= F.d.ny || k >= F.d.nz) continue;
+        if (red_only && ((i + j + k) & 1)) continue;
+        acc += residual_cell(F, i, j, k);
+      }
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_cell(const LevelView<T>& F, const LevelView<T>& C, int64_t cidx, T s) {
+  const int i = (int)(cidx % F.d.nx), j = (int)((cidx / F.d.nx) % F.d.ny), k = (int)(cidx / ((int64_t)F.d.nx * F.d.ny));
+  F.x[cidx] += s * C.x[nat_index(C.d, i / 2, j / 2, k / 2)];
+}
+
+template <typename T>
+__global__ void k_gsn(LevelView<T> L, int color, int zero_guess, const DevState* st) {
+  if (st->done) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.d.n; c += (int64_t)gridDim.x * blockDim.x)
+    gs_cell(L, c, color, zero_guess);
+}
+
+template <typename T>
+__global__ void k_restrictn(LevelView<T> F, LevelView<T> C, int red_only, const DevState* st) {
+  if (st->done) return;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.d.n; I += (int64_t)gridDim.x * blockDim.x)
+    C.f[I] = restrict_cell(F, C.d, I, red_only);
+}
+
+template <typename T>
+__global__ void k_prolongn(LevelView<T> F, LevelView<T> C, T s, const DevState* st) {
+  if (st->done) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < F.d.n; c += (int64_t)gridDim.x * blockDim.x)
+    prolong_cell(F, C, c, s);
+}
+
+template <typename T>
+struct TailArgs {
+  int first, last;  // levels first..last (last = coarsest)
+  int nu1, nu2;
+  T s;
+  LevelView<T> lv[24];
+  const T* inv;     // dense inverse of level `last`
+};
+
+// x_first = V-cycle(f_first) over levels first..last by one thread block
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const DevState* st) {
+  if (st->done) return;
+  const int nt = blockDim.x;
+  for (int l = a.first; l < a.last; ++l) {
+    const LevelView<T>& L = a.lv[l];
+    if (a.nu1 == 0) {
+      for (int64_t c = threadIdx.x; c < L.d.n; c += nt) L.x[c] = T(0);
+      __syncthreads();
+    }
+    for (int sw = 0; sw < a.nu1; ++sw)
+      for (int color = 0; color < 2; ++color) {
+        for (int64_t c = threadIdx.x; c < L.d.n; c += nt) gs_cell(L, c, color, sw == 0 && color == 0);
+        __syncthreads();
+      }
+    const LevelView<T>& C = a.lv[l + 1];
+    for (int64_t I = threadIdx.x; I < C.d.n; I += nt) C.f[I] = restrict_cell(L, C.d, I, a.nu1 > 0);
+    __syncthreads();
+  }
+  {
+    const LevelView<T>& C = a.lv[a.last];
+    const int64_t n = C.d.n;
+    for (int64_t i = threadIdx.x; i < n; i += nt) {
+      T s = T(0);
+      for (int64_t j = 0; j < n; ++j) s += a.inv[i * n + j] * C.f[j];
+      C.x[i] = s;
+    }
+    __syncthreads();
+  }
+  for (int l = a.last - 1; l >= a.first; --l) {
+    const LevelView<T>& L = a.lv[l];
+    const LevelView<T>& C = a.lv[l + 1];
+    for (int64_t c = threadIdx.x; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
+    __syncthreads();
+    for (int sw = 0; sw < a.nu2; ++sw)
+      for (int color = 1; color >= 0; --color) {
+        for (int64_t c = threadIdx.x; c < L.d.n; c += nt) gs_cell(L, c, color, 0);
+        __syncthreads();
+      }
+  }
+}
+
+// dense solve on level 0 when level 0 is the coarsest: x = inv f
+template <typename T>
+__global__ void k_dense0(int64_t n, const T* __restrict__ inv, const T* __restrict__ f, T* __restrict__ x,
+                         const DevState* st) {
+  if (st->done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t j = 0; j < n; ++j) s += inv[i * n + j] * f[j];
+    x[i] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_zero(int64_t n, T* __restrict__ x, const DevState* st) {
+  if (st->done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = T(0);
+}
+
+// z = Pi_p e (stage AMG alone)
+template <typename T>
+__global__ void k_place_p(Geom g, const T* __restrict__ e, T* __restrict__ z, const DevState* st) {
+  if (st->done) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    z[t] = e[t];
+    z[g.N + t] = T(0);
+    z[2 * g.N + t] = T(0);
+  }
+}
+
+// y = At x with At rebuilt in FP64 from A and the weights (parity checks)
+__global__ void k_spmv_dec64(Geom g, const double* __restrict__ A, const double* __restrict__ w,
+                             const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int color = (int)(t / g.Nh);
+    const int64_t q = t - color * g.Nh;
+    const Cell c = decode(g, color, q);
+    double acc[3] = {0, 0, 0};
+    for (int sl = 0; sl < 7; ++sl) {
+      const int64_t nq = nbr(g, c, q, sl);
+      if (nq < 0) continue;
+      const int xc = (sl == kDiag) ? color : (color ^ 1);
+      double b[9];
+      dec_block(g, A, w, color, sl, q, b);
+      for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) acc[r] += b[3 * r + k] * x[vidx(g, k, xc, nq)];
+    }
+    for (int r = 0; r < 3; ++r) y[vidx(g, r, color, q)] = acc[r];
+  }
+}
+
+// ---------------------------------------------------------------- host side
+template <typename T>
+LevelView<T> view(bo_prec* P, int l) {
+  const Level& L = P->lev[l];
+  return LevelView<T>{LevelDims{L.nx, L.ny, L.nz, L.n}, (const T*)L.c, (T*)L.f, (T*)L.x};
+}
+
+LevelDims dims_of(const Level& L) { return LevelDims{L.nx, L.ny, L.nz, L.n}; }
+
+template <typename T>
+void amg_vcycle(bo_prec* P, const DevState* st) {
+  cudaStream_t s = P->mat->ctx->stream;
+  const Geom& g = P->mat->g;
+  const T* At = (const T*)P->At;
+  T* f0 = (T*)P->f0;
+  T* x0 = (T*)P->e0;
+  const int nu1 = P->opts.amg_nu1, nu2 = P->opts.amg_nu2;
+  const T sc = (T)P->opts.amg_overcorr;
+  if (P->nlev == 1) {
+    (k_dense0<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, (const T*)P->coarse_inv, f0, x0, st), note_launch());
+    return;
+  }
+  const int ghalf = grid_for(g.Nh);
+  for (int sw = 0; sw < nu1; ++sw) {
+    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
+    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+  }
+  if (nu1 == 0) (k_zero<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, x0, st), note_launch());
+  (k_restrict0<T><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (T*)P->lev[1].f,
+                                                             nu1 > 0, st), note_launch());
+  // multi-block natural levels down to the tail
+  const int last = P->nlev - 1;
+  for (int l = 1; l < P->tail_from; ++l) {
+    LevelView<T> L = view<T>(P, l), C = view<T>(P, l + 1);
+    const int gl = grid_for(L.d.n);
+    for (int sw = 0; sw < nu1; ++sw) {
+      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 0, sw == 0, st), note_launch());
+      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+    }
+    if (nu1 == 0) (k_zero<T><<<gl, kThreads, 0, s>>>(L.d.n, L.x, st), note_launch());
+    (k_restrictn<T><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
+  }
+  TailArgs<T> ta;
+  ta.first = P->tail_from;
+  ta.last = last;
+  ta.nu1 = nu1;
+  ta.nu2 = nu2;
+  ta.s = sc;
+  for (int l = 1; l <= last; ++l) ta.lv[l] = view<T>(P, l);
+  ta.inv = (const T*)P->coarse_inv;
+  (k_tail<T><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+  for (int l = P->tail_from - 1; l >= 1; --l) {
+    LevelView<T> L = view<T>(P, l), C = view<T>(P, l + 1);
+    const int gl = grid_for(L.d.n);
+    (k_prolongn<T><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+    for (int sw = 0; sw < nu2; ++sw) {
+      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
+    }
+  }
+  (k_prolong0<T><<<grid_for(g.N), kThreads, 0, s>>>(g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st), note_launch());
+  for (int sw = 0; sw < nu2; ++sw) {
+    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, 0, st), note_launch());
+  }
+}
+
+template <typename T>
+void ilu_apply_first(bo_prec* P, const T* f, T* z, const DevState* st) {
+  cudaStream_t s = P->mat->ctx->stream;
+  const Geom& g = P->mat->g;
+  const int gh = grid_for(g.Nh);
+  const T* At = (const T*)P->At;
+  const T* D = (const T*)P->Dinv;
+  T* tv = (T*)P->t;
+  (k_ilu_r1<T><<<gh, kThreads, 0, s>>>(g, D, f, tv, st), note_launch());
+  (k_ilu_b<T, false><<<gh, kThreads, 0, s>>>(g, At, D, f, tv, z, nullptr, st), note_launch());
+  (k_ilu_r2<T, false><<<gh, kThreads, 0, s>>>(g, At, D, tv, z, z, nullptr, st), note_launch());
+}
+
+template <typename T>
+void cpr_apply(bo_prec* P, const double* v, T* z, int stage, const DevState* st) {
+  cudaStream_t s = P->mat->ctx->stream;
+  const Geom& g = P->mat->g;
+  const int gN = grid_for(g.N), gh = grid_for(g.Nh);
+  const T* At = (const T*)P->At;
+  const T* D = (const T*)P->Dinv;
+  T* f = (T*)P->f;
+  T* tv = (T*)P->t;
+  T* r = (T*)P->r;
+  T* e0 = (T*)P->e0;
+  T* f0 = (T*)P->f0;
+  if (stage == BO_STAGE_AMG) {
+    (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v, f0, st), note_launch());
+    amg_vcycle<T>(P, st);
+    (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, z, st), note_launch());
+    return;
+  }
+  if (stage == BO_STAGE_CPR)
+    (k_decouple_vec<T><<<gN, kThreads, 0, s>>>(g, v, P->w, f, st), note_launch());
+  else
+    (k_copy_vec<T><<<grid_for(3 * g.N), kThreads, 0, s>>>(3 * g.N, v, f, st), note_launch());
+  // x = R^{-1} f
+  ilu_apply_first<T>(P, f, z, st);
+  if (stage == BO_STAGE_ILU) return;
+  // x += Pi_p AMG(A_pp)^{-1} Pi_r (f - At x)
+  (k_cpr_residual<T, 1><<<gN, kThreads, 0, s>>>(g, At, f, z, nullptr, f0, st), note_launch());
+  amg_vcycle<T>(P, st);
+  // r = f - At x;  x += R^{-1} r  (the AMG correction e is added here too)
+  (k_cpr_residual<T, 3><<<gN, kThreads, 0, s>>>(g, At, f, z, e0, r, st), note_launch());
+  (k_ilu_r1<T><<<gh, kThreads, 0, s>>>(g, D, r, tv, st), note_launch());
+  (k_ilu_b<T, true><<<gh, kThreads, 0, s>>>(g, At, D, r, tv, z, e0, st), note_launch());
+  (k_ilu_r2<T, true><<<gh, kThreads, 0, s>>>(g, At, D, tv, tv, z, e0, st), note_launch());
+}
+
+template <typename T>
+int values_impl(bo_prec* P) {
+  bo_mat* m = P->mat;
+  cudaStream_t s = m->ctx->stream;
+  const Geom& g = m->g;
+  const int gN = grid_for(g.N), gh = grid_for(g.Nh);
+  (k_decouple<T><<<gN, kThreads, 0, s>>>(g, m->A, (T*)P->At, P->w, P->st), note_launch());
+  (k_ilu_red<<<gh, kThreads, 0, s>>>(g, m->A, P->w, P->Dinv64, P->st), note_launch());
+  (k_ilu_black<<<gh, kThreads, 0, s>>>(g, m->A, P->w, P->Dinv64, P->st), note_launch());
+  if (P->fp32) (k_convert<T><<<grid_for(9 * g.N), kThreads, 0, s>>>(P->Dinv64, (T*)P->Dinv, (size_t)9 * g.N), note_launch());
+  // AMG hierarchy values
+  for (int l = 1; l < P->nlev; ++l) {
+    Level& C = P->lev[l];
+    if (l == 1)
+      (k_galerkin0<<<grid_for(C.n), kThreads, 0, s>>>(g, m->A, P->w, dims_of(C), C.c64, P->st), note_launch());
+    else
+      (k_galerkinn<<<grid_for(C.n), kThreads, 0, s>>>(dims_of(P->lev[l - 1]), P->lev[l - 1].c64, dims_of(C), C.c64,
+                                                     P->st), note_launch());
+    (k_convert<T><<<grid_for(7 * C.n), kThreads, 0, s>>>(C.c64, (T*)C.c, (size_t)7 * C.n), note_launch());
+  }
+  const int last = P->nlev - 1;
+  LevelDims cd = last == 0 ? LevelDims{g.nx, g.ny, g.nz, g.N} : dims_of(P->lev[last]);
+  (k_dense_from_level<<<1, kThreads, 0, s>>>(cd, last == 0 ? nullptr : P->lev[last].c64, g, m->A, P->w, last == 0,
+                                            P->coarse64), note_launch());
+  const int n = (int)P->ncoarse;
+  const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
+  cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (k_gj_inverse<T><<<1, 1024, smem, s>>>(n, P->coarse64, (T*)P->coarse_inv, P->st), note_launch());
+  return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
+}
+
+}  // namespace
+
+int prec_alloc(bo_prec* P) {
+  const Geom& g = P->mat->g;
+  const size_t ts = P->tsize;
+  bool ok = true;
+  auto al = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (ok && cudaMalloc(&p, bytes) != cudaSuccess) { ok = false; return nullptr; }
+    return p;
+  };
+  P->At = al((size_t)63 * g.N * ts);
+  P->w = (double*)al((size_t)2 * g.N * sizeof(double));
+  P->Dinv64 = (double*)al((size_t)9 * g.N * sizeof(double));
+  P->Dinv = P->fp32 ? al((size_t)9 * g.N * ts) : (void*)P->Dinv64;
+  P->f = al((size_t)3 * g.N * ts);
+  P->t = al((size_t)3 * g.N * ts);
+  P->r = al((size_t)3 * g.N * ts);
+  P->e0 = al((size_t)g.N * ts);
+  P->f0 = al((size_t)g.N * ts);
+  // AMG hierarchy shape
+  int coarse_max = P->opts.amg_coarse_max;
+  if (coarse_max <= 0 || coarse_max > kCoarseMax) coarse_max = kCoarseMax;
+  P->nlev = 1;
+  int nx = g.nx, ny = g.ny, nz = g.nz;
+  int64_t n = g.N;
+  while (n > coarse_max && P->nlev < 24) {
+    nx = (nx + 1) / 2; ny = (ny + 1) / 2; nz = (nz + 1) / 2;
+    n = (int64_t)nx * ny * nz;
+    Level& L = P->lev[P->nlev];
+    L.nx = nx; L.ny = ny; L.nz = nz; L.n = n;
+    L.c64 = (double*)al((size_t)7 * n * sizeof(double));
+    L.c = al((size_t)7 * n * ts);
+    L.f = al((size_t)n * ts);
+    L.x = al((size_t)n * ts);
+    P->nlev++;
+  }
+  if (n > kCoarseMax) return BO_ERR_ARG;
+  P->ncoarse = n;
+  P->tail_from = P->nlev - 1;
+  for (int l = 1; l < P->nlev; ++l)
+    if (P->lev[l].n <= kTailCells) { P->tail_from = l; break; }
+  if (P->tail_from < 1) P->tail_from = 1;
+  P->coarse64 = (double*)al((size_t)n * n * sizeof(double));
+  P->coarse_inv = al((size_t)n * n * ts);
+  if (ok && cudaMalloc(&P->st, sizeof(DevState)) != cudaSuccess) ok = false;
+  if (ok) cudaMemsetAsync(P->st, 0, sizeof(DevState), P->mat->ctx->stream);
+  return ok ? BO_OK : BO_ERR_OOM;
+}
+
+void prec_free(bo_prec* P) {
+  auto fr = [](void* p) { if (p) cudaFree(p); };
+  fr(P->At); fr(P->w); fr(P->Dinv64);
+  if (P->fp32) fr(P->Dinv);
+  fr(P->f); fr(P->t); fr(P->r); fr(P->e0); fr(P->f0);
+  for (int l = 1; l < P->nlev; ++l) { fr(P->lev[l].c64); fr(P->lev[l].c); fr(P->lev[l].f); fr(P->lev[l].x); }
+  fr(P->coarse64); fr(P->coarse_inv); fr(P->st);
+}
+
+int prec_values(bo_prec* P) {
+  return P->fp32 ? values_impl<float>(P) : values_impl<double>(P);
+}
+
+void launch_cpr(bo_prec* P, const double* v, void* z, int stage, const DevState* st) {
+  if (P->fp32) cpr_apply<float>(P, v, (float*)z, stage, st);
+  else cpr_apply<double>(P, v, (double*)z, stage, st);
+}
+
+void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {
+  const Geom& g = P->mat->g;
+  (k_spmv_dec64<<<grid_for(g.N), kThreads, 0, P->mat->ctx->stream>>>(g, P->mat->A, P->w, x, y), note_launch());
+}
+
+}  // namespace bo

@@ -1,0 +1,336 @@
+"""GPU parity: every stage of the sm_103a solver against the FP64 oracle on
+the same seeded inputs, through the C ABI.
+
+Tolerances (derived from the arithmetic):
+  * FP64 SpMV: each output sums 21 products, so |y - y_ref| <= 21 eps
+    (|A| |x|)_i; tested at 1e-13 (|A| |x|)_i.
+  * FP32 matrix values: value rounding 2^-24 per entry -> <= 21 * 6e-8
+    (|A| |x|)_i; tested at 1e-5 (|A| |x|)_i.
+  * FP64 ILU / AMG / CPR applications: triangular and coarse solves amplify
+    rounding by the conditioning of the factors; tested at 1e-9 in norm.
+  * Solves (the spec bar): true FP64 residual ||b - A x|| / ||b|| <=
+    1e-8 checked by the oracle's compensated residual, and
+    ||x - x_ref|| / ||x_ref|| <= 1e-6 against the oracle solved to 1e-13.
+"""
+import numpy as np
+import pytest
+
+import bogen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bo():
+    import paper_1606_00556_gb300 as m
+    m.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(bo):
+    return bo.Context(0)
+
+
+def _sys(case):
+    a = bogen.assemble(case)
+    return a, oracle.BsrMatrix(a["rowptr"], a["col"], a["val"])
+
+
+def _random_bsr(nx, ny, nz, seed):
+    rng = np.random.default_rng(seed)
+    rowptr, col = bogen.pattern(nx, ny, nz)
+    val = rng.standard_normal((col.size, 3, 3))
+    for i in range(rowptr.size - 1):
+        for e in range(rowptr[i], rowptr[i + 1]):
+            if col[e] == i:
+                val[e] += 8 * np.eye(3)
+    return dict(rowptr=rowptr, col=col, val=val), oracle.BsrMatrix(rowptr, col, val)
+
+
+def _absprod(Ao, x):
+    return oracle.spmv(oracle.BsrMatrix(Ao.rowptr, Ao.col, np.abs(Ao.val)), np.abs(x))
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _mat(bo, ctx, dims, a):
+    return bo.Matrix.from_bsr(ctx, bo.grid(*dims), a["rowptr"], a["col"], a["val"])
+
+
+GRIDS = [(2, 1, 1), (4, 3, 2), (6, 5, 3), (20, 20, 5), (32, 7, 9)]
+
+
+# ------------------------------------------------------------------ SpMV
+@pytest.mark.parametrize("dims", GRIDS)
+def test_spmv_fp64_matches_oracle(bo, ctx, dims):
+    a, Ao = _random_bsr(*dims, seed=sum(dims))
+    A = _mat(bo, ctx, dims, a)
+    x = np.random.default_rng(1).standard_normal(Ao.n)
+    y = A.spmv(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = oracle.spmv(Ao, x)
+    assert np.all(np.abs(y - ref) <= 1e-13 * _absprod(Ao, x) + 1e-300)
+
+
+def test_spmv_fp32_and_alpha_beta(bo, ctx):
+    dims = (20, 20, 5)
+    a, Ao = _sys(bogen.tiny_case(0))
+    A = _mat(bo, ctx, dims, a)
+    x = np.random.default_rng(2).standard_normal(Ao.n)
+    y0 = np.random.default_rng(3).standard_normal(Ao.n)
+    ref = 2.0 * oracle.spmv(Ao, x) + 0.5 * y0
+    bound = 2.0 * _absprod(Ao, x) + 0.5 * np.abs(y0)
+    y = A.spmv(_dev(x), _dev(y0), alpha=2.0, beta=0.5).cpu().numpy()
+    assert np.all(np.abs(y - ref) <= 1e-13 * bound)
+    y32 = A.spmv(_dev(x), _dev(y0), alpha=2.0, beta=0.5, precision=bo.BO_PREC_FP32).cpu().numpy()
+    assert np.all(np.abs(y32 - ref) <= 1e-5 * bound)
+
+
+def test_spmv_beta_zero_ignores_nan_in_y(bo, ctx):
+    a, Ao = _random_bsr(4, 3, 2, 0)
+    A = _mat(bo, ctx, (4, 3, 2), a)
+    x = np.ones(Ao.n)
+    y = torch.full((Ao.n,), float("nan"), dtype=torch.float64, device="cuda")
+    assert np.all(np.isfinite(A.spmv(_dev(x), y).cpu().numpy()))
+
+
+def test_csr_input_equals_bsr_input(bo, ctx):
+    dims = (6, 5, 3)
+    a, Ao = _random_bsr(*dims, seed=4)
+    # scalar CSR with interleaved unknowns, entries shuffled within rows
+    rng = np.random.default_rng(5)
+    rows = [[] for _ in range(Ao.n)]
+    for i in range(Ao.nb):
+        for e in range(Ao.rowptr[i], Ao.rowptr[i + 1]):
+            j = Ao.col[e]
+            for r in range(3):
+                for k in range(3):
+                    rows[3 * i + r].append((3 * j + k, Ao.val[e][r, k]))
+    rp, cols, vals = [0], [], []
+    for r in rows:
+        rng.shuffle(r)
+        cols += [c for c, _ in r]
+        vals += [v for _, v in r]
+        rp.append(len(cols))
+    A = bo.Matrix.from_csr(ctx, bo.grid(*dims), np.array(rp, np.int32), np.array(cols, np.int32), np.array(vals))
+    x = rng.standard_normal(Ao.n)
+    y = A.spmv(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x))
+
+
+def test_device_inputs_and_value_update(bo, ctx):
+    dims = (20, 20, 5)
+    a0, _ = _sys(bogen.tiny_case(0))
+    a1, Ao1 = _sys(bogen.tiny_case(1))
+    A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), torch.tensor(a0["rowptr"], device="cuda"),
+                           torch.tensor(a0["col"], device="cuda"), _dev(a0["val"].ravel()))
+    A.update_values(a1["val"].ravel())
+    x = np.random.default_rng(6).standard_normal(Ao1.n)
+    y = A.spmv(_dev(x), torch.zeros(Ao1.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(Ao1, x)) <= 1e-13 * _absprod(Ao1, x))
+
+
+def test_input_errors_are_reported(bo, ctx):
+    dims = (4, 3, 2)
+    a, _ = _random_bsr(*dims, seed=7)
+    g = bo.grid(*dims)
+    # a wrong column inside the pattern's count
+    col = a["col"].copy()
+    col[5] = (col[5] + 7) % 24
+    with pytest.raises(bo.BoError) as e:
+        bo.Matrix.from_bsr(ctx, g, a["rowptr"], col, a["val"])
+    assert e.value.status == bo.BO_ERR_PATTERN
+    # NaN value
+    val = a["val"].copy()
+    val[3, 1, 2] = np.nan
+    with pytest.raises(bo.BoError) as e:
+        bo.Matrix.from_bsr(ctx, g, a["rowptr"], a["col"], val)
+    assert e.value.status == bo.BO_ERR_NONFINITE
+    # odd nx
+    with pytest.raises(bo.BoError) as e:
+        bo.Matrix.from_bsr(ctx, bo.grid(3, 2, 2), a["rowptr"], a["col"], a["val"])
+    assert e.value.status == bo.BO_ERR_ARG
+    # wrong block count
+    with pytest.raises(bo.BoError) as e:
+        bo.Matrix.from_bsr(ctx, g, a["rowptr"][:-1], a["col"][:-1], a["val"][:-1])
+    assert e.value.status in (bo.BO_ERR_PATTERN, bo.BO_ERR_ARG)
+
+
+# ------------------------------------------------------------------ stages
+def _cpr_pair(bo, ctx, case, dims, precision=0, overcorr=1.0):
+    a, Ao = _sys(case)
+    A = _mat(bo, ctx, dims, a)
+    P = bo.Preconditioner(A, precision=precision, overcorr=overcorr)
+    return a, Ao, A, P
+
+
+STAGE_DIMS = [(20, 20, 5), (6, 5, 3), (2, 2, 2)]
+
+
+@pytest.mark.parametrize("dims", STAGE_DIMS)
+def test_decoupled_spmv_matches_oracle(bo, ctx, dims):
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(3, *dims), dims)
+    At, _ = oracle.qi_decouple(Ao)
+    x = np.random.default_rng(8).standard_normal(Ao.n)
+    y = P.spmv_decoupled(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(At, x)) <= 1e-12 * _absprod(At, x) + 1e-300)
+
+
+@pytest.mark.parametrize("dims", STAGE_DIMS)
+@pytest.mark.parametrize("stage", ["ilu", "amg", "cpr_decoupled", "cpr"])
+def test_preconditioner_stages_match_oracle(bo, ctx, dims, stage):
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(4, *dims), dims)
+    st = {"ilu": (bo.BO_STAGE_ILU, oracle.STAGE_ILU), "amg": (bo.BO_STAGE_AMG, oracle.STAGE_AMG),
+          "cpr_decoupled": (bo.BO_STAGE_CPR_DECOUPLED, oracle.STAGE_CPR_DECOUPLED),
+          "cpr": (bo.BO_STAGE_CPR, oracle.STAGE_CPR)}[stage]
+    Po = oracle.cpr_prec(Ao, dims, ordering=oracle.ORDER_RED_BLACK,
+                         amg=oracle.AmgParams(coarse_max=128), stage=st[1])
+    r = np.random.default_rng(9).standard_normal(Ao.n)
+    z = P.apply(st[0], _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = Po.apply(r)
+    assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_amg_multilevel_with_tail_matches_oracle(bo, ctx):
+    # 96 x 96 x 40: level 1 (46,080 cells) runs on many blocks, levels from
+    # 23 x 24 x 10 down run in the single-block tail kernel
+    dims = (96, 96, 40)
+    case = bogen.waterflood_case(*dims, seed=11, corr=(8, 8, 1))
+    a, Ao, A, P = _cpr_pair(bo, ctx, case, dims)
+    lv = P.amg_levels()
+    assert lv[0] == dims and lv[1] == (48, 48, 20) and np.prod(lv[-1]) <= 128
+    Po = oracle.cpr_prec(Ao, dims, amg=oracle.AmgParams(coarse_max=128), stage=oracle.STAGE_AMG)
+    r = np.random.default_rng(10).standard_normal(Ao.n)
+    z = P.apply(bo.BO_STAGE_AMG, _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = Po.apply(r)
+    assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+# ------------------------------------------------------------------ solves
+def _xref(Ao, b):
+    x, info = oracle.gmres(Ao, b, tol=1e-13, maxit=5000, prec=oracle.ilu0_prec(Ao))
+    assert info["converged"]
+    return x
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_tiny_matches_oracle(bo, ctx, seed, precision):
+    dims = (20, 20, 5)
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(seed), dims, precision=precision)
+    b = _dev(a["b"])
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, tol=1e-8)
+    xg = x.cpu().numpy()
+    assert info["status"] == bo.BO_OK and info["iters"] > 0
+    assert oracle.rel_residual(Ao, a["b"], xg) <= 1e-8
+    assert info["true_rel_res"] <= 1e-8
+    xr = _xref(Ao, a["b"])
+    assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= 1e-6
+    hist = P.residual_history()
+    assert hist.size == info["iters"] and np.all(np.isfinite(hist))
+
+
+def test_solve_edge_cases(bo, ctx):
+    dims = (20, 20, 5)
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(0), dims)
+    n = Ao.n
+    # b = 0 -> x = 0
+    x = torch.ones(n, dtype=torch.float64, device="cuda")
+    info = P.solve(torch.zeros(n, dtype=torch.float64, device="cuda"), x, x0_is_zero=True)
+    assert info["status"] == 0 and float(x.abs().max()) == 0.0
+    # iteration cap -> NOT_CONVERGED, finite iterate, info filled
+    b = _dev(a["b"])
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, maxit=2)
+    assert info["status"] == bo.BO_ERR_NOT_CONVERGED and info["iters"] == 2
+    assert torch.isfinite(x).all() and info["true_rel_res"] < 1.0
+    # warm start from that iterate continues to the tolerance
+    info = P.solve(b, x, x0_is_zero=False)
+    assert info["status"] == 0 and oracle.rel_residual(Ao, a["b"], x.cpu().numpy()) <= 1e-8
+    # short restart cycles
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, restart=5, maxit=400)
+    assert info["status"] == 0 and info["restarts"] >= 2
+    assert oracle.rel_residual(Ao, a["b"], x.cpu().numpy()) <= 1e-8
+    # host buffers give the same answer as device buffers
+    xh = np.zeros(n)
+    info_h = P.solve(a["b"], xh)
+    xd = torch.zeros_like(b)
+    P.solve(b, xd)
+    assert info_h["status"] == 0 and np.array_equal(xh, xd.cpu().numpy())
+    # non-finite right-hand side
+    bn = b.clone()
+    bn[7] = float("nan")
+    info = P.solve(bn, torch.zeros_like(b), raise_on_error=False)
+    assert info["status"] == bo.BO_ERR_NONFINITE
+
+
+def test_solve_is_bitwise_repeatable(bo, ctx):
+    dims = (20, 20, 5)
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(2), dims)
+    b = _dev(a["b"])
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    i1 = P.solve(b, x1)
+    i2 = P.solve(b, x2)
+    assert i1["iters"] == i2["iters"] and torch.equal(x1, x2)
+
+
+def test_singular_pivot_is_breakdown(bo, ctx):
+    dims = (4, 4, 2)
+    a, _ = _sys(bogen.tiny_case(0, *dims))
+    val = a["val"].copy()
+    for e in range(a["rowptr"][5], a["rowptr"][6]):
+        if a["col"][e] == 5:
+            val[e][1, :] = 0.0   # water row of cell 5's diagonal block: a_11 = 0
+    A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), a["rowptr"], a["col"], val)
+    with pytest.raises(bo.BoError) as e:
+        bo.Preconditioner(A)
+    assert e.value.status == bo.BO_ERR_BREAKDOWN
+
+
+def test_prec_update_follows_new_values(bo, ctx):
+    dims = (20, 20, 5)
+    a0, _ = _sys(bogen.tiny_case(0))
+    a1, Ao1 = _sys(bogen.tiny_case(1))
+    A = _mat(bo, ctx, dims, a0)
+    P = bo.Preconditioner(A)
+    A.update_values(a1["val"])
+    P.update()
+    x = torch.zeros(Ao1.n, dtype=torch.float64, device="cuda")
+    info = P.solve(_dev(a1["b"]), x)
+    assert info["status"] == 0 and oracle.rel_residual(Ao1, a1["b"], x.cpu().numpy()) <= 1e-8
+
+
+def test_newton_update(bo, ctx):
+    s = torch.arange(30, dtype=torch.float64, device="cuda")
+    d = torch.full((30,), 0.5, dtype=torch.float64, device="cuda")
+    bo.bo_newton_update(ctx, s, d)
+    torch.cuda.synchronize()
+    assert torch.equal(s.cpu(), torch.arange(30, dtype=torch.float64) + 0.5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_waterflood_1m_cells(bo, ctx, precision):
+    # the benchmark workload: 128 x 128 x 64, 3.1M unknowns, launch sizes as
+    # timed; checked through the oracle's compensated FP64 residual
+    dims = (128, 128, 64)
+    a, Ao = _sys(bogen.waterflood_case(*dims, seed=42, day=0))
+    A = _mat(bo, ctx, dims, a)
+    P = bo.Preconditioner(A, precision=precision)
+    b = _dev(a["b"])
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, tol=1e-8, maxit=600)
+    assert info["status"] == 0, info
+    assert oracle.rel_residual(Ao, a["b"], x.cpu().numpy()) <= 1e-8
+    # sampled SpMV outputs at full size
+    xs = np.random.default_rng(12).standard_normal(Ao.n)
+    y = A.spmv(_dev(xs), torch.zeros_like(b)).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(Ao, xs)) <= 1e-13 * _absprod(Ao, xs))
