@@ -82,7 +82,7 @@ _VP = ctypes.c_void_p
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .buildlib import build as _b
     return _b(force=force)
 
 

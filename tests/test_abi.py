@@ -18,7 +18,7 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def libpath():
-    from paper_1606_00556_gb300.build import build
+    from paper_1606_00556_gb300.buildlib import build
     return build()
 
 
