@@ -170,6 +170,22 @@ int bo_newton_update(bo_ctx* ctx, double* state, const double* dx, int64_t n);
  * library has launched in the process so far. */
 int64_t bo_kernel_launches(void);
 
+/* Residual without device allocation (no counterpart in the paper).  For
+ * callers that must not call cudaMalloc when they check a residual: a
+ * framework's caching allocator may hold nearly all device memory, and
+ * cudaMalloc / cudaFree synchronise the whole device, which a serving loop
+ * or a caller that allocates only at start-up cannot afford.
+ *   r = b - A x and norms[0] = ||b - A x||_2, norms[1] = ||b||_2, in FP64;
+ *   b, x, r: device vectors of length 3 nx ny nz (natural interleaved order);
+ *   norms: device array of 2 doubles.  All are owned by the caller.
+ * Scratch lives in an array compiled into the library (256 KB per device
+ * that loads it, held until the process exits), shared by every call on the
+ * device: calls that overlap on the GPU race on it.  The first call on each
+ * device looks up that array's device address, so make it before any
+ * stream capture.  Grids of more than 4,194,304 cells give BO_ERR_ARG.
+ * Ordered on the context's stream; does not synchronise. */
+int bo_mat_residual_noalloc(bo_mat* A, const double* b, const double* x, double* r, double* norms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,7 @@ EXPORTS = (
     "bo_mat_create_bsr", "bo_mat_create_csr", "bo_mat_update_values", "bo_mat_spmv", "bo_mat_destroy",
     "bo_prec_setup", "bo_prec_update", "bo_prec_apply", "bo_prec_spmv_decoupled", "bo_prec_amg_levels",
     "bo_prec_destroy", "bo_solve", "bo_prec_residual_history", "bo_newton_update", "bo_kernel_launches",
+    "bo_mat_residual_noalloc",
 )
 
 
@@ -112,6 +113,7 @@ def lib():
         L.bo_solve.argtypes = [_VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
         L.bo_prec_residual_history.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.bo_newton_update.argtypes = [_VP, _VP, _VP, ctypes.c_int64]
+        L.bo_mat_residual_noalloc.argtypes = [_VP, _VP, _VP, _VP, _VP]
         L.bo_kernel_launches.restype = ctypes.c_int64
         L.bo_kernel_launches.argtypes = []
         L.bo_prec_opts_default.argtypes = [ctypes.POINTER(bo_prec_opts)]
@@ -319,6 +321,14 @@ class Preconditioner:
             self.close()
         except Exception:
             pass
+
+
+def bo_mat_residual_noalloc(mat: Matrix, b, x, r, norms):
+    """r = b - A x, norms[0:2] = (||r||, ||b||) on the device, with no device
+    allocation during the call (see include/bosolve.h)."""
+    _check(lib().bo_mat_residual_noalloc(mat.h, _VP(b.data_ptr()), _VP(x.data_ptr()), _VP(r.data_ptr()),
+                                         _VP(norms.data_ptr())), "bo_mat_residual_noalloc")
+    return r, norms
 
 
 def bo_kernel_launches() -> int:
