@@ -135,8 +135,8 @@ def oracle_sample(seed=SEED, maxit=400):
     return time.perf_counter() - t0, info
 
 
-def cpu_baseline_record(seconds, info):
-    scale = np.prod(DIMS) / np.prod(SAMPLE_DIMS)
+def cpu_baseline_record(seconds, info, dims=DIMS):
+    scale = float(np.prod(dims)) / float(np.prod(SAMPLE_DIMS))
     return {"value": seconds * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
             "sample": (f"oracle CPR-GMRES(30) (red-black block ILU(0) + AMG, FP64, one thread) on the "
                        f"{SAMPLE_DIMS[0]}x{SAMPLE_DIMS[1]}x{SAMPLE_DIMS[2]} waterflood Jacobian to 1e-8 "
@@ -165,11 +165,12 @@ def run_reference(args):
 
 
 def config_dict(args):
-    nx, ny, nz = DIMS
+    dims = tuple(getattr(args, "dims", DIMS))
+    nx, ny, nz = dims
     return {"workload": (f"waterflood black-oil Jacobians {nx}x{ny}x{nz} (3 unknowns/cell, 3x3 BSR 7-point), "
                          f"{args.jacobians} successive days, CPR-FGMRES({args.restart}) to 1e-8, "
                          f"preconditioner {args.precision}"),
-            "grid": list(DIMS), "unknowns": 3 * nx * ny * nz, "nnzb": _nnzb(*DIMS), "tol": 1e-8,
+            "grid": list(dims), "unknowns": 3 * nx * ny * nz, "nnzb": _nnzb(*dims), "tol": 1e-8,
             "restart": args.restart, "precision": args.precision, "seed": SEED, "jacobians": args.jacobians,
             "l2": "inputs larger than L2 (524 MB of matrix values per step, 10 Jacobians resident)"}
 
@@ -185,7 +186,11 @@ def main():
     ap.add_argument("--jacobians", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--secondary", default="fp32", choices=["fp32", "fp64", "none"],
+                    help="also time the other preconditioner precision on the same Jacobians")
     ap.add_argument("--dist-backend", default="nccl")
+    ap.add_argument("--dims", type=int, nargs=3, default=list(DIMS),
+                    help="grid (profiling runs only; the benchmark workload is 128 128 64)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -195,13 +200,14 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     # inputs first (spawned generator workers must start before CUDA)
-    jac = generate(DIMS, SEED + 1000 * rank, args.jacobians, procs=min(16, os.cpu_count() or 1))
+    dims = tuple(args.dims)
+    jac = generate(dims, SEED + 1000 * rank, args.jacobians, procs=min(16, os.cpu_count() or 1))
     cpu_rec = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         s, info = oracle_sample()
-        cpu_rec = cpu_baseline_record(s, info)
+        cpu_rec = cpu_baseline_record(s, info, dims)
 
     import torch
     import paper_1606_00556_gb300 as bo
@@ -225,15 +231,15 @@ def main():
     bo.lib()
     dev = torch.device("cuda", local)
     ctx = bo.Context(local)
-    nx, ny, nz = DIMS
+    nx, ny, nz = dims
     N = nx * ny * nz
     n = 3 * N
-    nnzb = _nnzb(*DIMS)
+    nnzb = _nnzb(*dims)
     rowptr, col = jac[0][0], jac[0][1]
     vals = [torch.from_numpy(j[2]).to(dev) for j in jac]
     bs = [torch.from_numpy(j[3]).to(dev) for j in jac]
     state = torch.from_numpy(jac[0][4]).to(dev)
-    g = bo.grid(*DIMS)
+    g = bo.grid(*dims)
     A = bo.Matrix.from_bsr(ctx, g, rowptr, col, jac[0][2])
     prec = bo.BO_PREC_FP32 if args.precision == "fp32" else bo.BO_PREC_FP64
     P = bo.Preconditioner(A, precision=prec)
@@ -269,13 +275,20 @@ def main():
     elapsed = e0.elapsed_time(e1)
     agg = aggregate(elapsed, args.steps, world, reduce_max)
 
-    # the dominant kernel, timed live inside the steps above: the FP64 Arnoldi SpMV
-    tz = 4 if args.precision == "fp32" else 8
-    spmv_bytes = 9 * 8 * nnzb + n * tz + n * 8
+    # the dominant kernel, timed live inside the steps above: the FP64 Arnoldi
+    # SpMV.  It does one FP64 FMA per 8 bytes it streams, and GB300 issues
+    # about 2 FP64 FMA per clock per SM, so it is bound by the FP64 pipe
+    # (ALU), not HBM: the roofline reports FP64 TFLOP/s against
+    # 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz, with the HBM view beside it.
+    spmv_bytes = 9 * 8 * nnzb + n * 8 + n * 8
+    spmv_flops = 2 * 9 * nnzb
     spmv_ms = sum(i["spmv_ms"] for i in infos)
     spmv_n = sum(i["spmv_launches"] for i in infos)
     hbm, peak_kind = peaks()
-    ach = spmv_bytes / (spmv_ms / spmv_n * 1e-3) / 1e9 if spmv_n else None
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    avg_s = spmv_ms / spmv_n * 1e-3 if spmv_n else None
+    ach = spmv_bytes / avg_s / 1e9 if avg_s else None
+    ach_tf = spmv_flops / avg_s / 1e12 if avg_s else None
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -302,6 +315,39 @@ def main():
         byts = 9 * vb * nnzb + 2 * n * 8
         sp[name] = {"us": us, "algorithmic_bytes": byts, "gbs": byts / (us * 1e-6) / 1e9,
                     "frac": byts / (us * 1e-6) / 1e9 / hbm}
+
+    # the mixed-precision form on the same Jacobians: FP32 preconditioner
+    # inside the FP64 FGMRES (Arnoldi, true residual and update in FP64)
+    second = None
+    if args.secondary != "none" and args.secondary != args.precision:
+        P2 = bo.Preconditioner(A, precision=bo.BO_PREC_FP32 if args.secondary == "fp32" else bo.BO_PREC_FP64)
+
+        def step2(k):
+            j = k % len(vals)
+            A.update_values(vals[j])
+            P2.update()
+            info = P2.solve(bs[j], x, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True)
+            if info["status"] != 0:
+                raise RuntimeError(f"solve failed: {info}")
+            bo.bo_newton_update(ctx, state, x)
+            return info
+
+        for k in range(args.warmup):
+            step2(k)
+        barrier()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        infos2 = [step2(args.warmup + k) for k in range(args.steps)]
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        agg2 = aggregate(f0.elapsed_time(f1), args.steps, world, reduce_max)
+        second = {"precision": args.secondary, "value": agg2["ms_per_solve"], "unit": "ms",
+                  "iters": [i["iters"] for i in infos2],
+                  "true_rel_res_max": max(i["true_rel_res"] for i in infos2)}
+        P2.close()
 
     # end to end through the C ABI with host buffers: matrix values, b and x
     # cross PCIe/C2C inside the timed region
@@ -331,12 +377,16 @@ def main():
             "warmup": args.warmup, "ms_per_step": agg["elapsed_ms"] / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic", "config": config_dict(args),
-            "roofline": {"bound": "hbm", "kernel": "k_arnoldi_spmv", "achieved": ach, "peak": hbm,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": (ach / hbm) if ach else None,
-                         "traffic": traffic, "algorithmic_bytes": spmv_bytes,
-                         "avg_us": spmv_ms / spmv_n * 1e3 if spmv_n else None, "launches": spmv_n},
-            "spmv": sp, "cpu_baseline": cpu_rec, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": "k_arnoldi_spmv (FP64)", "achieved": ach_tf,
+                         "peak": fp64_peak, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                         "unit": "TFLOP/s", "frac": (ach_tf / fp64_peak) if ach_tf else None,
+                         "traffic": traffic, "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
+                         "hbm": {"achieved": ach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                                 "frac": (ach / hbm) if ach else None},
+                         "avg_us": avg_s * 1e6 if avg_s else None, "launches": spmv_n},
+            "spmv": sp, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "iters": iters, "iters_mean": float(np.mean(iters)),
+            "true_rel_res_max": max(i["true_rel_res"] for i in infos),
             "solves_per_s": agg["solves_per_s"],
         }
         print(json.dumps(line), flush=True)

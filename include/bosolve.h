@@ -75,9 +75,9 @@ typedef struct {
 
 typedef struct {
   int32_t precision;      /* BO_PREC_FP64 or BO_PREC_FP32 (mixed precision)     */
-  int32_t amg_nu1;        /* red-black Gauss-Seidel pre-sweeps  (default 1)      */
-  int32_t amg_nu2;        /* post-sweeps (default 1)                             */
-  double amg_overcorr;    /* coarse correction scale s: x += s P x_c (default 1) */
+  int32_t amg_nu1;        /* red-black Gauss-Seidel pre-sweeps  (default 2)      */
+  int32_t amg_nu2;        /* post-sweeps (default 2)                             */
+  double amg_overcorr;    /* coarse correction scale s: x += s P x_c (default 1.3) */
   int32_t amg_coarse_max; /* coarsest level size, <= 128 (default 128)          */
 } bo_prec_opts;
 
@@ -102,7 +102,7 @@ typedef struct {
 } bo_solve_info;
 
 const char* bo_status_str(int status);
-/* Fill defaults: FP64, nu1 = nu2 = 1, overcorr 1, coarse_max 128 / tol 1e-8,
+/* Fill defaults: FP64, nu1 = nu2 = 2, overcorr 1.3, coarse_max 128 / tol 1e-8,
  * restart 30, maxit 500, device pointers. */
 void bo_prec_opts_default(bo_prec_opts* o);
 void bo_solve_opts_default(bo_solve_opts* o);

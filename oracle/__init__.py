@@ -185,7 +185,7 @@ def pressure_block(A: BsrMatrix):
 
 
 class AmgParams:
-    def __init__(self, smoother=SMOOTHER_RBGS, nu1=1, nu2=1, omega=2.0 / 3.0, overcorr=1.0, coarse_max=512,
+    def __init__(self, smoother=SMOOTHER_RBGS, nu1=2, nu2=2, omega=2.0 / 3.0, overcorr=1.3, coarse_max=128,
                  max_levels=20):
         self.smoother, self.nu1, self.nu2, self.omega = smoother, nu1, nu2, omega
         self.overcorr, self.coarse_max, self.max_levels = overcorr, coarse_max, max_levels

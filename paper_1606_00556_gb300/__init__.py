@@ -261,7 +261,7 @@ class Matrix:
 class Preconditioner:
     """bo_prec: CPR-FPF (decoupling + red-black block ILU(0) + AMG)."""
 
-    def __init__(self, mat: Matrix, precision=BO_PREC_FP64, nu1=1, nu2=1, overcorr=1.0, coarse_max=128):
+    def __init__(self, mat: Matrix, precision=BO_PREC_FP64, nu1=2, nu2=2, overcorr=1.3, coarse_max=128):
         o = bo_prec_opts(precision, nu1, nu2, overcorr, coarse_max)
         h = _VP()
         _check(lib().bo_prec_setup(mat.h, ctypes.byref(o), ctypes.byref(h)), "bo_prec_setup")

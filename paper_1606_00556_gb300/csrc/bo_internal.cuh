@@ -124,6 +124,9 @@ struct DevState {
   double bnorm;    // ||b||
   double wn0;      // ||w|| before orthogonalisation
   double hn;       // ||w|| after orthogonalisation
+  double wn2;      // ||w||^2 before the current Gram-Schmidt pass
+  double scale;    // 1 / h_{j+1,j}: normalisation of the new basis vector
+  int reorth;      // the current column needs a second Gram-Schmidt pass
   double h[136];   // coefficients of the column under construction: pass 1 at 0, pass 2 at 64
 };
 
@@ -138,6 +141,11 @@ inline int grid_for(int64_t n, int threads = kThreads, int max_blocks = 152 * 16
   if (b > max_blocks) b = max_blocks;
   return (int)b;
 }
+
+// Grid for a grid-stride loop over n items of a kernel launched with
+// kThreads threads: every SM gets as many blocks as can be resident at once
+// (one full wave, no partial last wave), capped by the work available.
+int occ_grid(const void* kernel, int64_t n, int threads = kThreads, size_t smem = 0);
 
 }  // namespace bo
 
@@ -190,8 +198,7 @@ struct bo_prec {
   size_t tsize;            // sizeof(preconditioner scalar)
   void* At;                // 63 N decoupled values (preconditioner precision)
   double* w;               // 2 N Quasi-IMPES weights (w_w, w_g) [2][N] internal order
-  double* Dinv64;          // 9 N inverted ILU pivot blocks, FP64 [rc][N]
-  void* Dinv;              // same in the preconditioner precision (aliases Dinv64 for FP64)
+  void* Dinv;              // 9 N inverted ILU pivot blocks [rc][N], preconditioner precision
   // AMG: level 0 = the pressure block of At (colour-split), levels 1.. natural order
   int nlev;
   bo::Level lev[24];
@@ -203,12 +210,13 @@ struct bo_prec {
   void* f;                 // 3N decoupled input
   void* t;                 // 3N ILU intermediates
   void* r;                 // 3N residual
+  void* z1;                // 3N first local solve x1 = R^{-1} f
   void* e0;                // N level-0 AMG correction
   void* f0;                // N level-0 AMG right-hand side
   // Krylov workspace (FP64 unless noted)
   int mcap;                // restart length the workspace was sized for
   double* V;               // (mcap+1) 3N
-  void* Z;                 // mcap 3N, precision T
+  double* Z;               // mcap 3N preconditioned vectors
   double* H;               // (mcap+1) mcap
   double* cs;
   double* sn;
@@ -247,7 +255,7 @@ void launch_newton_update(double* state, const double* dx, int64_t n, cudaStream
 int prec_values(bo_prec* P);   // decoupling + ILU + AMG values (stream-ordered, flags in st->err)
 int prec_alloc(bo_prec* P);
 void prec_free(bo_prec* P);
-void launch_cpr(bo_prec* P, const double* v, void* z, int stage, const DevState* st);  // v internal FP64, z internal T
+void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st);  // internal order, FP64 in and out
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  // FP64 values of At rebuilt on the fly
 
 // krylov.cu

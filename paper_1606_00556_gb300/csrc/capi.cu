@@ -3,7 +3,9 @@
 // in the kernels of layout.cu, precond.cu and krylov.cu.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include "bo_internal.cuh"
 
@@ -11,6 +13,29 @@ using namespace bo;
 
 namespace bo {
 std::atomic<long long> g_launches{0};
+
+int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(kernel);
+    if (it != cache.end()) per_sm = it->second;
+  }
+  if (per_sm == 0) {
+    int sms = 0, b = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem);
+    per_sm = (b > 0 ? b : 1) * (sms > 0 ? sms : 1);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[kernel] = per_sm;
+  }
+  const int64_t need = (n + threads - 1) / threads;
+  return (int)(need < 1 ? 1 : (need < per_sm ? need : per_sm));
+}
 }
 
 namespace {
@@ -177,9 +202,9 @@ const char* bo_status_str(int s) {
 void bo_prec_opts_default(bo_prec_opts* o) {
   if (!o) return;
   o->precision = BO_PREC_FP64;
-  o->amg_nu1 = 1;
-  o->amg_nu2 = 1;
-  o->amg_overcorr = 1.0;
+  o->amg_nu1 = 2;
+  o->amg_nu2 = 2;
+  o->amg_overcorr = 1.3;
   o->amg_coarse_max = 128;
 }
 
@@ -296,12 +321,7 @@ int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z) {
   // r -> internal (xi as scratch), apply, z (precision T) -> FP64 internal -> natural
   launch_gather(g, r, P->bi, s);
   launch_cpr(P, P->bi, P->Z, stage, P->st);
-  if (P->fp32) {
-    launch_widen((const float*)P->Z, P->xi, (size_t)3 * g.N, s);
-    launch_scatter(g, P->xi, z, s);
-  } else {
-    launch_scatter(g, (const double*)P->Z, z, s);
-  }
+  launch_scatter(g, P->Z, z, s);
   return cuda_status(cudaStreamSynchronize(s));
 }
 

@@ -8,12 +8,19 @@
 // so the iterates are those of the decoupled system and the minimised norm
 // is the original residual.
 //
-// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2), each pass
-// a multi-dot (one reduction for all j+1 coefficients) and a fused update.
+// Orthogonalisation: classical Gram-Schmidt with a selective second pass
+// ("twice is enough", Kahan-Parlett).  One pass computes the j+1
+// coefficients h = V^T w and ||w||^2 together; ||w - V h||^2 then follows
+// from Pythagoras as ||w||^2 - ||h||^2.  Unless that cancels to below
+// kReorthEta2 ||w||^2 the column is accepted and the update pass writes the
+// normalised v_{j+1} directly; otherwise a second pass re-orthogonalises.
+// On GB300 FP64 arithmetic, not HBM, bounds these passes, so every pass
+// saved is FP64 time saved.
+//
 // Every reduction is two-stage with a fixed order (per-block partial sums,
 // then the last block to finish sums the partials), so results are bitwise
-// repeatable.  The Givens rotations run on the device in one thread; a flag
-// in device memory makes the rest of a cycle's kernels return at once after
+// repeatable.  The Givens rotations run in that last block; a flag in device
+// memory makes the rest of a cycle's kernels return at once after
 // convergence, so the host only polls with a lag of one iteration.
 #include <chrono>
 #include <cmath>
@@ -28,11 +35,16 @@ namespace {
 constexpr int kRedBlocks = 4 * 152;  // blocks of single reductions
 constexpr int kMaxM = 64;
 constexpr int kHistCap = 4096;
+// Second pass only when ||w - V h|| < 1e-2 ||w||: above that the
+// Pythagorean norm is accurate to ~1e-12 and one classical pass loses at
+// most ~1e-12 of orthogonality, far below the 1e-8 target.  (A strongly
+// preconditioned w lies mostly in span(V), so the textbook threshold of
+// 1/sqrt(2) would request the second pass at every step.)
+constexpr double kReorthEta2 = 1e-4;
 
-// w = A z in FP64 on internal vectors (z in the preconditioner precision)
-template <typename TZ>
+// w = A z in FP64 on internal vectors
 __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const double* __restrict__ A,
-                                                          const TZ* __restrict__ z, double* __restrict__ w,
+                                                          const double* __restrict__ z, double* __restrict__ w,
                                                           const DevState* st) {
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -45,8 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const double*
       const int64_t nq = nbr(g, c, q, sl);
       if (nq < 0) continue;
       const int xc = (sl == kDiag) ? color : (color ^ 1);
-      const double x0 = (double)z[vidx(g, 0, xc, nq)], x1 = (double)z[vidx(g, 1, xc, nq)],
-                   x2 = (double)z[vidx(g, 2, xc, nq)];
+      const double x0 = z[vidx(g, 0, xc, nq)], x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
       const double* a = A + plane(g, color, sl, 0) + q;
       const size_t P = (size_t)g.Nh;
       a0 += ld_stream(a) * x0 + ld_stream(a + P) * x1 + ld_stream(a + 2 * P) * x2;
@@ -135,85 +146,25 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
     st->done = 0;
     st->k = 0;
     st->happy = 0;
+    st->reorth = 0;
     st->est = st->beta;
   }
 }
 
-// v = src * s with s = 1 / beta (which = 0) or 1 / hn (which = 1)
-__global__ void k_scale(int64_t n, const double* __restrict__ src, double* __restrict__ v, const DevState* st, int which,
-                        int check_done) {
-  if (check_done && st->done) return;
-  const double d = which == 0 ? st->beta : st->hn;
-  const double s = d > 0.0 ? 1.0 / d : 0.0;
+// v = src / beta
+__global__ void k_scale_beta(int64_t n, const double* __restrict__ src, double* __restrict__ v, const DevState* st) {
+  const double s = st->beta > 0.0 ? 1.0 / st->beta : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = src[i] * s;
 }
 
-// out[v] = <V_v, w> for v < nv; grid (chunks, nv)
-__global__ void __launch_bounds__(kThreads) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                                                  const double* __restrict__ w, double* partials, DevState* st,
-                                                  int out_off) {
-  __shared__ double sh[32];
-  if (st->done) return;
-  const int nchunk = gridDim.x;
-  const int v = blockIdx.y;
-  const int64_t len = (n + nchunk - 1) / nchunk;
-  const int64_t i0 = blockIdx.x * len;
-  const int64_t i1 = min(n, i0 + len);
-  const double* Vv = V + (size_t)v * ldv;
-  double acc = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += Vv[i] * w[i];
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[(size_t)v * nchunk + blockIdx.x] = acc;
-  if (last_block(&st->counter[0], nchunk * nv)) {
-    for (int u = 0; u < nv; ++u) {
-      const double s = reduce_partials(partials + (size_t)u * nchunk, nchunk, sh);
-      if (threadIdx.x == 0) st->h[out_off + u] = s;
-    }
-    if (threadIdx.x == 0) st->counter[0] = 0;
-  }
-}
-
-// w -= sum_k h[k] V_k; with_norm: ||w|| -> st->hn
-__global__ void __launch_bounds__(kThreads) k_update(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                                                    double* __restrict__ w, int h_off, int with_norm,
-                                                    double* partials, DevState* st) {
-  __shared__ double sh[32];
-  __shared__ double hs[kMaxM + 1];
-  if (st->done) return;
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = st->h[h_off + k];
-  __syncthreads();
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = w[i];
-    for (int k = 0; k < nv; ++k) s -= hs[k] * V[(size_t)k * ldv + i];
-    w[i] = s;
-    acc += s * s;
-  }
-  if (!with_norm) return;
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
-  if (last_block(&st->counter[3], gridDim.x)) {
-    const double s = reduce_partials(partials, gridDim.x, sh);
-    if (threadIdx.x == 0) {
-      st->hn = sqrt(s);
-      st->counter[3] = 0;
-    }
-  }
-}
-
-// Hessenberg column j = h1 + h2 (both CGS passes) with h_{j+1,j} = hn;
+// Hessenberg column j from the coefficients col[0..j] and h_{j+1,j} = hn:
 // previous rotations, a new one, the residual estimate and the stop flag.
-__global__ void k_givens(DevState* st, double* H, double* cs, double* sn, double* gv, int j, int m, int ldh,
-                         double* hist, int hist_at) {
-  if (st->done || threadIdx.x != 0) return;
-  double col[kMaxM + 1];
+// Runs in one thread.
+__device__ void givens_step(DevState* st, double* col, double hn, double* H, double* cs, double* sn, double* gv, int j,
+                            int m, int ldh, double* hist, int hist_at) {
   double nrm2 = 0.0;
-  for (int i = 0; i <= j; ++i) {
-    col[i] = st->h[i] + st->h[kMaxM + i];
-    nrm2 += col[i] * col[i];
-  }
-  const double hn = st->hn;
+  for (int i = 0; i <= j; ++i) nrm2 += col[i] * col[i];
   const double wn0 = sqrt(nrm2 + hn * hn);
   for (int i = 0; i < j; ++i) {
     const double a = col[i], b = col[i + 1];
@@ -232,10 +183,85 @@ __global__ void k_givens(DevState* st, double* H, double* cs, double* sn, double
   st->k = j + 1;
   st->est = fabs(gv[j + 1]);
   st->happy = hn <= 1e-14 * wn0;
+  st->hn = hn;
+  st->scale = hn > 0.0 ? 1.0 / hn : 0.0;
   if (hist && hist_at < kHistCap) hist[hist_at] = st->est;
   const bool bad = !isfinite(st->est) || !isfinite(d) || d == 0.0;
   if (bad) atomicOr(&st->err, kErrNonfinite);
   if (bad || st->est <= st->target || st->happy || j + 1 == m) st->done = 1;
+}
+
+struct ArnoldiArgs {
+  double* H;
+  double* cs;
+  double* sn;
+  double* gv;
+  int j, m, ldh;
+  double* hist;
+  int hist_at;
+};
+
+// Gram-Schmidt coefficient pass: h[u] = <V_u, w> for u <= j and ||w||^2
+// (grid y = j + 2).  Pass 0 decides from Pythagoras whether the column is
+// accepted (then it also applies the Givens step); pass 1 (run only when a
+// second pass was requested) finishes the column.
+__global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                     const double* __restrict__ w, double* partials, DevState* st,
+                                                     int pass, ArnoldiArgs aa) {
+  __shared__ double sh[32];
+  __shared__ double hs[kMaxM + 1];
+  if (st->done || (pass == 1 && !st->reorth)) return;
+  const int nv = aa.j + 1;
+  const int nchunk = gridDim.x;
+  const int v = blockIdx.y;
+  const int64_t len = (n + nchunk - 1) / nchunk;
+  const int64_t i0 = blockIdx.x * len;
+  const int64_t i1 = min(n, i0 + len);
+  const double* a = (v < nv) ? V + (size_t)v * ldv : w;
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += a[i] * w[i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[(size_t)v * nchunk + blockIdx.x] = acc;
+  if (!last_block(&st->counter[0], nchunk * (nv + 1))) return;
+  for (int u = 0; u <= nv; ++u) {
+    const double s = reduce_partials(partials + (size_t)u * nchunk, nchunk, sh);
+    if (threadIdx.x == 0) hs[u] = s;
+  }
+  if (threadIdx.x != 0) return;
+  st->counter[0] = 0;
+  const double wn2 = hs[nv];
+  double h2 = 0.0;
+  for (int u = 0; u < nv; ++u) {
+    st->h[pass * kMaxM + u] = hs[u];
+    h2 += hs[u] * hs[u];
+  }
+  const double rest = wn2 - h2;  // ||w - V h||^2 if V is orthonormal
+  if (pass == 0) {
+    st->reorth = !(rest >= kReorthEta2 * wn2);
+    if (st->reorth) return;  // keep h, orthogonalise once more before the Givens step
+  }
+  double col[kMaxM + 1];
+  for (int u = 0; u < nv; ++u) col[u] = st->h[u] + (pass == 1 ? st->h[kMaxM + u] : 0.0);
+  givens_step(st, col, sqrt(rest > 0.0 ? rest : 0.0), aa.H, aa.cs, aa.sn, aa.gv, aa.j, aa.m, aa.ldh, aa.hist,
+              aa.hist_at);
+}
+
+// Gram-Schmidt update pass: w -= V h; when the column is final (accepted
+// after this pass) the result is scaled to the unit vector v_{j+1}.
+__global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                       double* __restrict__ w, DevState* st, int pass, int nv) {
+  __shared__ double hs[kMaxM + 1];
+  __shared__ double scale;
+  if (st->done || (pass == 1 && !st->reorth)) return;
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = st->h[pass * kMaxM + k];
+  if (threadIdx.x == 0) scale = (pass == 0 && st->reorth) ? 1.0 : st->scale;
+  __syncthreads();
+  const double sc = scale;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int k = 0; k < nv; ++k) s -= hs[k] * V[(size_t)k * ldv + i];
+    w[i] = s * sc;
+  }
 }
 
 // y = H(0:k, 0:k)^{-1} g (upper triangular after the rotations)
@@ -251,8 +277,7 @@ __global__ void k_trisolve(DevState* st, const double* H, const double* gv, doub
 }
 
 // x += sum_{l < k} y_l Z_l
-template <typename TZ>
-__global__ void k_xupdate(int64_t n, double* __restrict__ x, const TZ* __restrict__ Z, int64_t ldz,
+__global__ void k_xupdate(int64_t n, double* __restrict__ x, const double* __restrict__ Z, int64_t ldz,
                           const double* __restrict__ y, const DevState* st) {
   __shared__ double ys[kMaxM];
   const int k = st->k;
@@ -260,19 +285,12 @@ __global__ void k_xupdate(int64_t n, double* __restrict__ x, const TZ* __restric
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = x[i];
-    for (int l = 0; l < k; ++l) s += ys[l] * (double)Z[(size_t)l * ldz + i];
+    for (int l = 0; l < k; ++l) s += ys[l] * Z[(size_t)l * ldz + i];
     x[i] = s;
   }
 }
 
-template <typename TZ>
-void launch_arnoldi_spmv(bo_prec* P, const void* z, double* w) {
-  const Geom& g = P->mat->g;
-  (k_arnoldi_spmv<TZ><<<grid_for(g.N, kThreads, 152 * 64), kThreads, 0, P->mat->ctx->stream>>>(
-      g, P->mat->A, (const TZ*)z, w, P->st), note_launch());
-}
-
-int mdot_chunks(int64_t n) {
+int gs_chunks(int64_t n) {
   int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
   if (c < 1) c = 1;
   if (c > 2 * 152) c = 2 * 152;
@@ -295,7 +313,7 @@ int krylov_alloc(bo_prec* P, int m) {
     return p;
   };
   P->V = (double*)al((size_t)(m + 1) * n * sizeof(double));
-  P->Z = al((size_t)m * n * P->tsize);
+  P->Z = (double*)al((size_t)m * n * sizeof(double));
   P->H = (double*)al((size_t)(m + 1) * m * sizeof(double));
   P->cs = (double*)al((size_t)m * sizeof(double));
   P->sn = (double*)al((size_t)m * sizeof(double));
@@ -305,7 +323,7 @@ int krylov_alloc(bo_prec* P, int m) {
     P->xi = (double*)al((size_t)n * sizeof(double));
     P->bi = (double*)al((size_t)n * sizeof(double));
     P->rk = (double*)al((size_t)n * sizeof(double));
-    P->npartials = (int64_t)(kMaxM + 1) * 2 * 152 + 4096;
+    P->npartials = (int64_t)(kMaxM + 2) * 2 * 152 + kHistCap;
     P->partials = (double*)al((size_t)P->npartials * sizeof(double));
     P->hostio = (double*)al((size_t)2 * n * sizeof(double));
     if (ok && cudaMallocHost(&P->h_st, 2 * sizeof(DevState)) != cudaSuccess) ok = false;
@@ -330,9 +348,8 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
   int rc = krylov_alloc(P, m);
   if (rc != BO_OK) return rc;
   DevState* st = P->st;
-  double* dhist = nullptr;
-  // history on the device: reuse the partials tail
-  dhist = P->partials + (P->npartials - 4096);
+  // residual-estimate history on the device: the tail of the partials buffer
+  double* dhist = P->partials + (P->npartials - kHistCap);
 
   const double* b_d = b_in;
   double* x_d = x_in;
@@ -369,14 +386,15 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
   } else {
     const double target = o->tol * bnorm;
     const int64_t ldv = n;
+    const int gn = grid_for(n);
+    const int gu = occ_grid((const void*)k_gs_update, n);
     while (beta > target && its < o->maxit) {
       (k_cycle_start<<<1, 64, 0, s>>>(st, P->gvec, m), note_launch());
-      (k_scale<<<grid_for(n), kThreads, 0, s>>>(n, P->rk, P->V, st, 0, 0), note_launch());
-      int enq = 0;
+      (k_scale_beta<<<gn, kThreads, 0, s>>>(n, P->rk, P->V, st), note_launch());
       for (int j = 0; j < m && its + j < o->maxit; ++j) {
         double* vj = P->V + (size_t)j * ldv;
         double* w = P->V + (size_t)(j + 1) * ldv;
-        void* zj = (char*)P->Z + (size_t)j * n * P->tsize;
+        double* zj = P->Z + (size_t)j * n;
         launch_cpr(P, vj, zj, BO_STAGE_CPR, st);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (o->profile && prof.size() < 512) {
@@ -384,30 +402,27 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
           e1 = P->prof_ev[2 * prof.size() + 1];
           cudaEventRecord(e0, s);
         }
-        if (P->fp32) launch_arnoldi_spmv<float>(P, zj, w);
-        else launch_arnoldi_spmv<double>(P, zj, w);
+        (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(g, M->A, zj, w, st),
+         note_launch());
         if (e1) {
           cudaEventRecord(e1, s);
           prof.push_back({e0, e1});
         }
-        dim3 gd(mdot_chunks(n), j + 1);
-        (k_mdot<<<gd, kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, P->partials, st, 0), note_launch());
-        (k_update<<<grid_for(n), kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, 0, 0, P->partials, st), note_launch());
-        (k_mdot<<<gd, kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, P->partials, st, kMaxM), note_launch());
-        (k_update<<<grid_for(n), kThreads, 0, s>>>(n, P->V, ldv, j + 1, w, kMaxM, 1, P->partials, st), note_launch());
-        (k_givens<<<1, 32, 0, s>>>(st, P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j), note_launch());
-        (k_scale<<<grid_for(n), kThreads, 0, s>>>(n, w, w, st, 1, 1), note_launch());
+        const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j};
+        const dim3 gd(gs_chunks(n), j + 2);
+        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, 0, aa), note_launch());
+        (k_gs_update<<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, st, 0, j + 1), note_launch());
+        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, 1, aa), note_launch());
+        (k_gs_update<<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, st, 1, j + 1), note_launch());
         cudaMemcpyAsync(&P->h_st[j & 1], st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         cudaEventRecord(P->ev[j & 1], s);
-        ++enq;
         if (j >= 1) {
           if (cudaEventSynchronize(P->ev[(j - 1) & 1]) != cudaSuccess) return BO_ERR_CUDA;
           if (P->h_st[(j - 1) & 1].done) break;
         }
       }
       (k_trisolve<<<1, 32, 0, s>>>(st, P->H, P->gvec, P->y, m), note_launch());
-      if (P->fp32) (k_xupdate<float><<<grid_for(n), kThreads, 0, s>>>(n, P->xi, (const float*)P->Z, n, P->y, st), note_launch());
-      else (k_xupdate<double><<<grid_for(n), kThreads, 0, s>>>(n, P->xi, (const double*)P->Z, n, P->y, st), note_launch());
+      (k_xupdate<<<gn, kThreads, 0, s>>>(n, P->xi, P->Z, n, P->y, st), note_launch());
       (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, M->A, P->bi, P->xi, P->rk, P->partials, st), note_launch());
       cudaMemcpyAsync(P->h_st, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;

@@ -27,31 +27,32 @@ namespace bo {
 namespace {
 
 constexpr int kTailThreads = 1024;
-constexpr int64_t kTailCells = 32768;
+constexpr int64_t kTailCells = 4096;
 constexpr int kCoarseMax = 128;
 
 // ---------------------------------------------------------------- 3x3 blocks
 // inverse by Gauss-Jordan elimination with partial pivoting; false if a
 // pivot is zero or the result is not finite
-__device__ bool inv3(const double a[9], double out[9]) {
-  double m[3][6];
+template <typename T>
+__device__ bool inv3(const T a[9], T out[9]) {
+  T m[3][6];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       m[i][j] = a[3 * i + j];
-      m[i][3 + j] = (i == j) ? 1.0 : 0.0;
+      m[i][3 + j] = (i == j) ? T(1) : T(0);
     }
   for (int k = 0; k < 3; ++k) {
     int p = k;
     for (int i = k + 1; i < 3; ++i)
       if (fabs(m[i][k]) > fabs(m[p][k])) p = i;
-    if (m[p][k] == 0.0) return false;
+    if (m[p][k] == T(0)) return false;
     if (p != k)
-      for (int j = 0; j < 6; ++j) { const double t = m[k][j]; m[k][j] = m[p][j]; m[p][j] = t; }
-    const double piv = m[k][k];
+      for (int j = 0; j < 6; ++j) { const T t = m[k][j]; m[k][j] = m[p][j]; m[p][j] = t; }
+    const T piv = m[k][k];
     for (int j = 0; j < 6; ++j) m[k][j] /= piv;
     for (int i = 0; i < 3; ++i) {
       if (i == k) continue;
-      const double f = m[i][k];
+      const T f = m[i][k];
       for (int j = 0; j < 6; ++j) m[i][j] -= f * m[k][j];
     }
   }
@@ -80,7 +81,8 @@ __device__ __forceinline__ void dec_block(const Geom& g, const double* __restric
   }
 }
 
-__device__ __forceinline__ void mul3(const double a[9], const double b[9], double c[9]) {
+template <typename T>
+__device__ __forceinline__ void mul3(const T a[9], const T b[9], T c[9]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -123,35 +125,43 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, T* __restrict__
   }
 }
 
-// red pivots: D_r^{-1} of the decoupled diagonal blocks
-__global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w,
-                          double* __restrict__ Dinv, DevState* st) {
+// block (colour, slot) of the decoupled planes at half index q
+template <typename T>
+__device__ __forceinline__ void load_block(const Geom& g, const T* __restrict__ At, int color, int slot, int64_t q,
+                                           T b[9]) {
+#pragma unroll
+  for (int rc = 0; rc < 9; ++rc) b[rc] = At[plane(g, color, slot, rc) + q];
+}
+
+// red pivots: D_r^{-1} of the decoupled diagonal blocks, in precision T
+template <typename T>
+__global__ void k_ilu_red(Geom g, const T* __restrict__ At, T* __restrict__ Dinv, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
-    double d[9], inv[9];
-    dec_block(g, A, w, 0, kDiag, q, d);
+    T d[9], inv[9];
+    load_block(g, At, 0, kDiag, q, d);
     if (!inv3(d, inv)) {
       atomicOr(&st->err, kErrBreakdown);
-      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = T(0);
     }
     for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + q] = inv[rc];
   }
 }
 
 // black pivots: D_b' = D_b - sum_r A_br D_r^{-1} A_rb, stored inverted
-__global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* __restrict__ w,
-                            double* __restrict__ Dinv, DevState* st) {
+template <typename T>
+__global__ void k_ilu_black(Geom g, const T* __restrict__ At, T* __restrict__ Dinv, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
-    double S[9], inv[9];
-    dec_block(g, A, w, 1, kDiag, q, S);
+    T S[9], inv[9];
+    load_block(g, At, 1, kDiag, q, S);
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       if (s == kDiag) continue;
       const int64_t nq = nbr(g, c, q, s);
       if (nq < 0) continue;
-      double L[9], U[9], Dr[9], T1[9], T2[9];
-      dec_block(g, A, w, 1, s, q, L);
-      dec_block(g, A, w, 0, opposite(s), nq, U);
+      T L[9], U[9], Dr[9], T1[9], T2[9];
+      load_block(g, At, 1, s, q, L);
+      load_block(g, At, 0, opposite(s), nq, U);
       for (int rc = 0; rc < 9; ++rc) Dr[rc] = Dinv[(size_t)rc * g.N + nq];
       mul3(L, Dr, T1);
       mul3(T1, U, T2);
@@ -159,7 +169,7 @@ __global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* 
     }
     if (!inv3(S, inv)) {
       atomicOr(&st->err, kErrBreakdown);
-      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = T(0);
     }
     for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = inv[rc];
   }
@@ -361,17 +371,35 @@ __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __rest
 }
 
 // ------------------------------------------------------------ apply kernels
-// f = D_QI^{-1} v (all cells), v FP64 internal, f precision T
-template <typename T>
-__global__ void k_decouple_vec(Geom g, const double* __restrict__ v, const double* __restrict__ w, T* __restrict__ f,
-                               const DevState* st) {
+// Entry of the preconditioner: f = D_QI^{-1} v (DEC) or f = v, in precision
+// T, fused with the first ILU pass on the red cells, t_r = D_r^{-1} f_r.
+template <typename T, bool DEC>
+__global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* __restrict__ w,
+                            const T* __restrict__ Dinv, T* __restrict__ f, T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const double v0 = v[t], v1 = v[g.N + t], v2 = v[2 * g.N + t];
-    f[t] = (T)(v0 - w[t] * v1 - w[g.N + t] * v2);
-    f[g.N + t] = (T)v1;
-    f[2 * g.N + t] = (T)v2;
+    const T f0 = DEC ? (T)(v0 - w[t] * v1 - w[g.N + t] * v2) : (T)v0;
+    const T f1 = (T)v1, f2 = (T)v2;
+    f[t] = f0;
+    f[g.N + t] = f1;
+    f[2 * g.N + t] = f2;
+    if (t < g.Nh) {
+      T d[9];
+#pragma unroll
+      for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + t];
+      tv[t] = d[0] * f0 + d[1] * f1 + d[2] * f2;
+      tv[g.N + t] = d[3] * f0 + d[4] * f1 + d[5] * f2;
+      tv[2 * g.N + t] = d[6] * f0 + d[7] * f1 + d[8] * f2;
+    }
   }
+}
+
+template <typename T>
+__global__ void k_widen_t(int64_t n, const T* __restrict__ a, double* __restrict__ b, const DevState* st) {
+  if (st->done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
 }
 
 template <typename T>
@@ -379,22 +407,6 @@ __global__ void k_copy_vec(int64_t n, const double* __restrict__ v, T* __restric
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     f[t] = (T)v[t];
-}
-
-// ILU pass 1 (red): t_r = D_r^{-1} src_r
-template <typename T>
-__global__ void k_ilu_r1(Geom g, const T* __restrict__ Dinv, const T* __restrict__ src, T* __restrict__ tv,
-                         const DevState* st) {
-  if (st->done) return;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
-    const T f0 = src[vidx(g, 0, 0, q)], f1 = src[vidx(g, 1, 0, q)], f2 = src[vidx(g, 2, 0, q)];
-    T d[9];
-#pragma unroll
-    for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + q];
-    tv[vidx(g, 0, 0, q)] = d[0] * f0 + d[1] * f1 + d[2] * f2;
-    tv[vidx(g, 1, 0, q)] = d[3] * f0 + d[4] * f1 + d[5] * f2;
-    tv[vidx(g, 2, 0, q)] = d[6] * f0 + d[7] * f1 + d[8] * f2;
-  }
 }
 
 // sum over the six off-diagonal blocks of a row of At times the other
@@ -419,10 +431,13 @@ __device__ __forceinline__ void offdiag_sum(const Geom& g, const T* __restrict__
 }
 
 // ILU pass 2 (black): u_b = D_b'^{-1} (src_b - sum A_br t_r).
-// ACC = false: z_b = u_b.  ACC = true: t_b = u_b, z_b += u_b (+ e_b on p).
-template <typename T, bool ACC>
-__global__ void k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ src,
-                        T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, const DevState* st) {
+// OUT = false: z_b = u_b (precision T).
+// OUT = true: t_b = u_b and the preconditioner's result on black cells,
+//   zo_b = z1_b + Pi_p e_b + u_b, in FP64.
+template <typename T, bool OUT>
+__global__ void __launch_bounds__(kThreads, 3) k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ src,
+                        T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
+                        const DevState* st) {
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
@@ -435,13 +450,13 @@ __global__ void k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ 
     const T u0 = d[0] * r0 + d[1] * r1 + d[2] * r2;
     const T u1 = d[3] * r0 + d[4] * r1 + d[5] * r2;
     const T u2 = d[6] * r0 + d[7] * r1 + d[8] * r2;
-    if (ACC) {
+    if (OUT) {
       tv[vidx(g, 0, 1, q)] = u0;
       tv[vidx(g, 1, 1, q)] = u1;
       tv[vidx(g, 2, 1, q)] = u2;
-      z[vidx(g, 0, 1, q)] += u0 + e[g.Nh + q];
-      z[vidx(g, 1, 1, q)] += u1;
-      z[vidx(g, 2, 1, q)] += u2;
+      zo[vidx(g, 0, 1, q)] = (double)(z[vidx(g, 0, 1, q)] + e[g.Nh + q] + u0);
+      zo[vidx(g, 1, 1, q)] = (double)(z[vidx(g, 1, 1, q)] + u1);
+      zo[vidx(g, 2, 1, q)] = (double)(z[vidx(g, 2, 1, q)] + u2);
     } else {
       z[vidx(g, 0, 1, q)] = u0;
       z[vidx(g, 1, 1, q)] = u1;
@@ -451,10 +466,12 @@ __global__ void k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ 
 }
 
 // ILU pass 3 (red): corr = D_r^{-1} sum A_rb u_b, with u_b in `ub` (black half).
-// ACC = false: z_r = t_r - corr.  ACC = true: z_r += t_r - corr (+ e_r on p).
-template <typename T, bool ACC>
-__global__ void k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ tv,
-                         const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, const DevState* st) {
+// OUT = false: z_r = t_r - corr (precision T).
+// OUT = true: zo_r = z1_r + Pi_p e_r + t_r - corr, in FP64.
+template <typename T, bool OUT>
+__global__ void __launch_bounds__(kThreads, 3) k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ tv,
+                         const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
+                         const DevState* st) {
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 0, q);
@@ -467,10 +484,10 @@ __global__ void k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__
     const T c1 = d[3] * s[0] + d[4] * s[1] + d[5] * s[2];
     const T c2 = d[6] * s[0] + d[7] * s[1] + d[8] * s[2];
     const T t0 = tv[vidx(g, 0, 0, q)] - c0, t1 = tv[vidx(g, 1, 0, q)] - c1, t2 = tv[vidx(g, 2, 0, q)] - c2;
-    if (ACC) {
-      z[vidx(g, 0, 0, q)] += t0 + e[q];
-      z[vidx(g, 1, 0, q)] += t1;
-      z[vidx(g, 2, 0, q)] += t2;
+    if (OUT) {
+      zo[vidx(g, 0, 0, q)] = (double)(z[vidx(g, 0, 0, q)] + e[q] + t0);
+      zo[vidx(g, 1, 0, q)] = (double)(z[vidx(g, 1, 0, q)] + t1);
+      zo[vidx(g, 2, 0, q)] = (double)(z[vidx(g, 2, 0, q)] + t2);
     } else {
       z[vidx(g, 0, 0, q)] = t0;
       z[vidx(g, 1, 0, q)] = t1;
@@ -481,10 +498,12 @@ __global__ void k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__
 
 // Residuals of the decoupled system in precision T.
 // ROWS = 1: out[t] = f_p - (At z)_p for all cells (the AMG right-hand side).
-// ROWS = 3: out = f - At (z + Pi_p e), all components.
+// ROWS = 3: out = f - At (z + Pi_p e), all components, fused with the first
+//   ILU pass of the second local solve on red cells: tv_r = D_r^{-1} out_r.
 template <typename T, int ROWS>
-__global__ void k_cpr_residual(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
-                               const T* __restrict__ e, T* __restrict__ out, const DevState* st) {
+__global__ void __launch_bounds__(kThreads, 4) k_cpr_residual(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
+                               const T* __restrict__ e, T* __restrict__ out, const T* __restrict__ Dinv,
+                               T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
@@ -507,8 +526,20 @@ __global__ void k_cpr_residual(Geom g, const T* __restrict__ At, const T* __rest
       for (int r = 0; r < ROWS; ++r)
         acc[r] += ld_stream(a + 3 * r * P) * x0 + ld_stream(a + (3 * r + 1) * P) * x1 + ld_stream(a + (3 * r + 2) * P) * x2;
     }
+    T res[ROWS];
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) out[(size_t)r * g.N + t] = f[(size_t)r * g.N + t] - acc[r];
+    for (int r = 0; r < ROWS; ++r) {
+      res[r] = f[(size_t)r * g.N + t] - acc[r];
+      out[(size_t)r * g.N + t] = res[r];
+    }
+    if (ROWS == 3 && color == 0) {
+      T d[9];
+#pragma unroll
+      for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + q];
+      tv[t] = d[0] * res[0] + d[1] * res[1 % ROWS] + d[2] * res[2 % ROWS];
+      tv[g.N + t] = d[3] * res[0] + d[4] * res[1 % ROWS] + d[5] * res[2 % ROWS];
+      tv[2 * g.N + t] = d[6] * res[0] + d[7] * res[1 % ROWS] + d[8] * res[2 % ROWS];
+    }
   }
 }
 
@@ -531,6 +562,31 @@ __global__ void k_gs0(Geom g, const T* __restrict__ At, const T* __restrict__ f,
       }
     }
     x[(size_t)color * g.Nh + q] = s / At[plane(g, color, kDiag, 0) + q];
+  }
+}
+
+// First post-smoothing half sweep (black cells) with the coarse correction
+// folded in: the red neighbours are read as x_r + s x_c(aggregate).  This
+// equals prolongating x += s P x_c on every cell and then sweeping the black
+// cells, because the black sweep overwrites x_b and the red sweep that
+// follows overwrites x_r without reading its old value.
+template <typename T>
+__global__ void k_gs0_prolong(Geom g, const T* __restrict__ At, const T* __restrict__ f, T* __restrict__ x,
+                              LevelDims C, const T* __restrict__ xc, T sc, const DevState* st) {
+  if (st->done) return;
+  const int di[7] = {0, 0, -1, 0, 1, 0, 0}, dj[7] = {0, -1, 0, 0, 0, 1, 0}, dk[7] = {-1, 0, 0, 0, 0, 0, 1};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = decode(g, 1, q);
+    T s = f[(size_t)g.Nh + q];
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      if (sl == kDiag) continue;
+      const int64_t nq = nbr(g, c, q, sl);
+      if (nq < 0) continue;
+      const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
+      s -= At[plane(g, 1, sl, 0) + q] * xv;
+    }
+    x[(size_t)g.Nh + q] = s / At[plane(g, 1, kDiag, 0) + q];
   }
 }
 
@@ -639,6 +695,33 @@ __device__ __forceinline__ void prolong_cell(const LevelView<T>& F, const LevelV
   F.x[cidx] += s * C.x[nat_index(C.d, i / 2, j / 2, k / 2)];
 }
 
+// black half sweep with the coarse correction of the red neighbours folded in
+// (the natural-order counterpart of k_gs0_prolong)
+template <typename T>
+__device__ __forceinline__ void gs_cell_prolong(const LevelView<T>& L, const LevelView<T>& C, int64_t cidx, T sc) {
+  const int i = (int)(cidx % L.d.nx), j = (int)((cidx / L.d.nx) % L.d.ny), k = (int)(cidx / ((int64_t)L.d.nx * L.d.ny));
+  if (((i + j + k) & 1) != 1) return;
+  const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
+  T s = L.f[cidx];
+  if (k > 0) s -= L.c[kZm * L.d.n + cidx] * (L.x[cidx - nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k - 1) / 2)]);
+  if (j > 0) s -= L.c[kYm * L.d.n + cidx] * (L.x[cidx - L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j - 1) / 2, k / 2)]);
+  if (i > 0) s -= L.c[kXm * L.d.n + cidx] * (L.x[cidx - 1] + sc * C.x[nat_index(C.d, (i - 1) / 2, j / 2, k / 2)]);
+  if (i < L.d.nx - 1)
+    s -= L.c[kXp * L.d.n + cidx] * (L.x[cidx + 1] + sc * C.x[nat_index(C.d, (i + 1) / 2, j / 2, k / 2)]);
+  if (j < L.d.ny - 1)
+    s -= L.c[kYp * L.d.n + cidx] * (L.x[cidx + L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j + 1) / 2, k / 2)]);
+  if (k < L.d.nz - 1)
+    s -= L.c[kZp * L.d.n + cidx] * (L.x[cidx + nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k + 1) / 2)]);
+  L.x[cidx] = s / L.c[kDiag * L.d.n + cidx];
+}
+
+template <typename T>
+__global__ void k_gsn_prolong(LevelView<T> L, LevelView<T> C, T sc, const DevState* st) {
+  if (st->done) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.d.n; c += (int64_t)gridDim.x * blockDim.x)
+    gs_cell_prolong(L, C, c, sc);
+}
+
 template <typename T>
 __global__ void k_gsn(LevelView<T> L, int color, int zero_guess, const DevState* st) {
   if (st->done) return;
@@ -702,11 +785,16 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const DevS
   for (int l = a.last - 1; l >= a.first; --l) {
     const LevelView<T>& L = a.lv[l];
     const LevelView<T>& C = a.lv[l + 1];
-    for (int64_t c = threadIdx.x; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
-    __syncthreads();
+    if (a.nu2 == 0) {
+      for (int64_t c = threadIdx.x; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
+      __syncthreads();
+    }
     for (int sw = 0; sw < a.nu2; ++sw)
       for (int color = 1; color >= 0; --color) {
-        for (int64_t c = threadIdx.x; c < L.d.n; c += nt) gs_cell(L, c, color, 0);
+        for (int64_t c = threadIdx.x; c < L.d.n; c += nt) {
+          if (sw == 0 && color == 1) gs_cell_prolong(L, C, c, a.s);
+          else gs_cell(L, c, color, 0);
+        }
         __syncthreads();
       }
   }
@@ -731,14 +819,14 @@ __global__ void k_zero(int64_t n, T* __restrict__ x, const DevState* st) {
     x[i] = T(0);
 }
 
-// z = Pi_p e (stage AMG alone)
+// z = Pi_p e (stage AMG alone), FP64 output
 template <typename T>
-__global__ void k_place_p(Geom g, const T* __restrict__ e, T* __restrict__ z, const DevState* st) {
+__global__ void k_place_p(Geom g, const T* __restrict__ e, double* __restrict__ z, const DevState* st) {
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
-    z[t] = e[t];
-    z[g.N + t] = T(0);
-    z[2 * g.N + t] = T(0);
+    z[t] = (double)e[t];
+    z[g.N + t] = 0.0;
+    z[2 * g.N + t] = 0.0;
   }
 }
 
@@ -817,34 +905,29 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   for (int l = P->tail_from - 1; l >= 1; --l) {
     LevelView<T> L = view<T>(P, l), C = view<T>(P, l + 1);
     const int gl = grid_for(L.d.n);
-    (k_prolongn<T><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+    if (nu2 == 0) (k_prolongn<T><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
     for (int sw = 0; sw < nu2; ++sw) {
-      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+      if (sw == 0) (k_gsn_prolong<T><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+      else (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
       (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
     }
   }
-  (k_prolong0<T><<<grid_for(g.N), kThreads, 0, s>>>(g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st), note_launch());
+  if (nu2 == 0)
+    (k_prolong0<T><<<grid_for(g.N), kThreads, 0, s>>>(g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
+     note_launch());
   for (int sw = 0; sw < nu2; ++sw) {
-    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+    if (sw == 0)
+      (k_gs0_prolong<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
+       note_launch());
+    else
+      (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
     (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, 0, st), note_launch());
   }
 }
 
+// z = CPR stage applied to v (FP64, internal order); result FP64 in zo
 template <typename T>
-void ilu_apply_first(bo_prec* P, const T* f, T* z, const DevState* st) {
-  cudaStream_t s = P->mat->ctx->stream;
-  const Geom& g = P->mat->g;
-  const int gh = grid_for(g.Nh);
-  const T* At = (const T*)P->At;
-  const T* D = (const T*)P->Dinv;
-  T* tv = (T*)P->t;
-  (k_ilu_r1<T><<<gh, kThreads, 0, s>>>(g, D, f, tv, st), note_launch());
-  (k_ilu_b<T, false><<<gh, kThreads, 0, s>>>(g, At, D, f, tv, z, nullptr, st), note_launch());
-  (k_ilu_r2<T, false><<<gh, kThreads, 0, s>>>(g, At, D, tv, z, z, nullptr, st), note_launch());
-}
-
-template <typename T>
-void cpr_apply(bo_prec* P, const double* v, T* z, int stage, const DevState* st) {
+void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevState* st) {
   cudaStream_t s = P->mat->ctx->stream;
   const Geom& g = P->mat->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
@@ -855,27 +938,47 @@ void cpr_apply(bo_prec* P, const double* v, T* z, int stage, const DevState* st)
   T* r = (T*)P->r;
   T* e0 = (T*)P->e0;
   T* f0 = (T*)P->f0;
+  T* z1 = (T*)P->z1;
   if (stage == BO_STAGE_AMG) {
     (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v, f0, st), note_launch());
     amg_vcycle<T>(P, st);
-    (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, z, st), note_launch());
+    (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo, st), note_launch());
     return;
   }
+  // x1 = R^{-1} f with f = D_QI^{-1} v (stage CPR) or f = v
   if (stage == BO_STAGE_CPR)
-    (k_decouple_vec<T><<<gN, kThreads, 0, s>>>(g, v, P->w, f, st), note_launch());
+    (k_cpr_entry<T, true><<<occ_grid((const void*)k_cpr_entry<T, true>, g.N), kThreads, 0, s>>>(g, v, P->w, D, f,
+                                                                                                  tv, st),
+     note_launch());
   else
-    (k_copy_vec<T><<<grid_for(3 * g.N), kThreads, 0, s>>>(3 * g.N, v, f, st), note_launch());
-  // x = R^{-1} f
-  ilu_apply_first<T>(P, f, z, st);
-  if (stage == BO_STAGE_ILU) return;
-  // x += Pi_p AMG(A_pp)^{-1} Pi_r (f - At x)
-  (k_cpr_residual<T, 1><<<gN, kThreads, 0, s>>>(g, At, f, z, nullptr, f0, st), note_launch());
+    (k_cpr_entry<T, false><<<occ_grid((const void*)k_cpr_entry<T, false>, g.N), kThreads, 0, s>>>(g, v, P->w, D, f,
+                                                                                                    tv, st),
+     note_launch());
+  (k_ilu_b<T, false><<<occ_grid((const void*)k_ilu_b<T, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
+                                                                                          nullptr, st),
+   note_launch());
+  (k_ilu_r2<T, false><<<occ_grid((const void*)k_ilu_r2<T, false>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, z1, z1,
+                                                                                            nullptr, nullptr, st),
+   note_launch());
+  if (stage == BO_STAGE_ILU) {
+    (k_widen_t<T><<<grid_for(3 * g.N), kThreads, 0, s>>>(3 * g.N, z1, zo, st), note_launch());
+    return;
+  }
+  // x2 = x1 + Pi_p AMG(A_pp)^{-1} Pi_r (f - At x1)
+  (k_cpr_residual<T, 1><<<occ_grid((const void*)k_cpr_residual<T, 1>, g.N), kThreads, 0, s>>>(
+       g, At, f, z1, nullptr, f0, nullptr, nullptr, st),
+   note_launch());
   amg_vcycle<T>(P, st);
-  // r = f - At x;  x += R^{-1} r  (the AMG correction e is added here too)
-  (k_cpr_residual<T, 3><<<gN, kThreads, 0, s>>>(g, At, f, z, e0, r, st), note_launch());
-  (k_ilu_r1<T><<<gh, kThreads, 0, s>>>(g, D, r, tv, st), note_launch());
-  (k_ilu_b<T, true><<<gh, kThreads, 0, s>>>(g, At, D, r, tv, z, e0, st), note_launch());
-  (k_ilu_r2<T, true><<<gh, kThreads, 0, s>>>(g, At, D, tv, tv, z, e0, st), note_launch());
+  // r = f - At x2 (with the red pass of R^{-1} r fused);  x3 = x2 + R^{-1} r
+  (k_cpr_residual<T, 3><<<occ_grid((const void*)k_cpr_residual<T, 3>, g.N), kThreads, 0, s>>>(g, At, f, z1, e0, r,
+                                                                                                D, tv, st),
+   note_launch());
+  (k_ilu_b<T, true><<<occ_grid((const void*)k_ilu_b<T, true>, g.Nh), kThreads, 0, s>>>(g, At, D, r, tv, z1, e0, zo,
+                                                                                        st),
+   note_launch());
+  (k_ilu_r2<T, true><<<occ_grid((const void*)k_ilu_r2<T, true>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, tv, z1, e0,
+                                                                                          zo, st),
+   note_launch());
 }
 
 template <typename T>
@@ -885,9 +988,8 @@ int values_impl(bo_prec* P) {
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
   (k_decouple<T><<<gN, kThreads, 0, s>>>(g, m->A, (T*)P->At, P->w, P->st), note_launch());
-  (k_ilu_red<<<gh, kThreads, 0, s>>>(g, m->A, P->w, P->Dinv64, P->st), note_launch());
-  (k_ilu_black<<<gh, kThreads, 0, s>>>(g, m->A, P->w, P->Dinv64, P->st), note_launch());
-  if (P->fp32) (k_convert<T><<<grid_for(9 * g.N), kThreads, 0, s>>>(P->Dinv64, (T*)P->Dinv, (size_t)9 * g.N), note_launch());
+  (k_ilu_red<T><<<gh, kThreads, 0, s>>>(g, (const T*)P->At, (T*)P->Dinv, P->st), note_launch());
+  (k_ilu_black<T><<<gh, kThreads, 0, s>>>(g, (const T*)P->At, (T*)P->Dinv, P->st), note_launch());
   // AMG hierarchy values
   for (int l = 1; l < P->nlev; ++l) {
     Level& C = P->lev[l];
@@ -922,11 +1024,11 @@ int prec_alloc(bo_prec* P) {
   };
   P->At = al((size_t)63 * g.N * ts);
   P->w = (double*)al((size_t)2 * g.N * sizeof(double));
-  P->Dinv64 = (double*)al((size_t)9 * g.N * sizeof(double));
-  P->Dinv = P->fp32 ? al((size_t)9 * g.N * ts) : (void*)P->Dinv64;
+  P->Dinv = al((size_t)9 * g.N * ts);
   P->f = al((size_t)3 * g.N * ts);
   P->t = al((size_t)3 * g.N * ts);
   P->r = al((size_t)3 * g.N * ts);
+  P->z1 = al((size_t)3 * g.N * ts);
   P->e0 = al((size_t)g.N * ts);
   P->f0 = al((size_t)g.N * ts);
   // AMG hierarchy shape
@@ -961,9 +1063,8 @@ int prec_alloc(bo_prec* P) {
 
 void prec_free(bo_prec* P) {
   auto fr = [](void* p) { if (p) cudaFree(p); };
-  fr(P->At); fr(P->w); fr(P->Dinv64);
-  if (P->fp32) fr(P->Dinv);
-  fr(P->f); fr(P->t); fr(P->r); fr(P->e0); fr(P->f0);
+  fr(P->At); fr(P->w); fr(P->Dinv);
+  fr(P->f); fr(P->t); fr(P->r); fr(P->z1); fr(P->e0); fr(P->f0);
   for (int l = 1; l < P->nlev; ++l) { fr(P->lev[l].c64); fr(P->lev[l].c); fr(P->lev[l].f); fr(P->lev[l].x); }
   fr(P->coarse64); fr(P->coarse_inv); fr(P->st);
 }
@@ -972,9 +1073,9 @@ int prec_values(bo_prec* P) {
   return P->fp32 ? values_impl<float>(P) : values_impl<double>(P);
 }
 
-void launch_cpr(bo_prec* P, const double* v, void* z, int stage, const DevState* st) {
-  if (P->fp32) cpr_apply<float>(P, v, (float*)z, stage, st);
-  else cpr_apply<double>(P, v, (double*)z, stage, st);
+void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st) {
+  if (P->fp32) cpr_apply<float>(P, v, z, stage, st);
+  else cpr_apply<double>(P, v, z, stage, st);
 }
 
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {

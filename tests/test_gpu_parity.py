@@ -164,11 +164,19 @@ def test_input_errors_are_reported(bo, ctx):
 
 
 # ------------------------------------------------------------------ stages
-def _cpr_pair(bo, ctx, case, dims, precision=0, overcorr=1.0):
+# AMG parameters given explicitly to both sides of every stage comparison
+AMG_NU, AMG_S = 2, 1.3
+
+
+def _cpr_pair(bo, ctx, case, dims, precision=0):
     a, Ao = _sys(case)
     A = _mat(bo, ctx, dims, a)
-    P = bo.Preconditioner(A, precision=precision, overcorr=overcorr)
+    P = bo.Preconditioner(A, precision=precision, nu1=AMG_NU, nu2=AMG_NU, overcorr=AMG_S)
     return a, Ao, A, P
+
+
+def _oracle_amg():
+    return oracle.AmgParams(coarse_max=128, nu1=AMG_NU, nu2=AMG_NU, overcorr=AMG_S)
 
 
 STAGE_DIMS = [(20, 20, 5), (6, 5, 3), (2, 2, 2)]
@@ -190,10 +198,25 @@ def test_preconditioner_stages_match_oracle(bo, ctx, dims, stage):
     st = {"ilu": (bo.BO_STAGE_ILU, oracle.STAGE_ILU), "amg": (bo.BO_STAGE_AMG, oracle.STAGE_AMG),
           "cpr_decoupled": (bo.BO_STAGE_CPR_DECOUPLED, oracle.STAGE_CPR_DECOUPLED),
           "cpr": (bo.BO_STAGE_CPR, oracle.STAGE_CPR)}[stage]
-    Po = oracle.cpr_prec(Ao, dims, ordering=oracle.ORDER_RED_BLACK,
-                         amg=oracle.AmgParams(coarse_max=128), stage=st[1])
+    Po = oracle.cpr_prec(Ao, dims, ordering=oracle.ORDER_RED_BLACK, amg=_oracle_amg(), stage=st[1])
     r = np.random.default_rng(9).standard_normal(Ao.n)
     z = P.apply(st[0], _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = Po.apply(r)
+    assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("nu1,nu2,s", [(1, 1, 1.0), (2, 2, 1.3), (1, 0, 1.0), (0, 2, 1.5), (3, 1, 1.7)])
+def test_amg_cycle_variants_match_oracle(bo, ctx, nu1, nu2, s):
+    # every smoothing/prolongation path: fused and explicit coarse correction,
+    # zero pre-smoothing (full restriction of the residual)
+    dims = (20, 20, 5)
+    a, Ao = _sys(bogen.tiny_case(6, *dims))
+    A = _mat(bo, ctx, dims, a)
+    P = bo.Preconditioner(A, nu1=nu1, nu2=nu2, overcorr=s)
+    Po = oracle.cpr_prec(Ao, dims, amg=oracle.AmgParams(coarse_max=128, nu1=nu1, nu2=nu2, overcorr=s),
+                         stage=oracle.STAGE_AMG)
+    r = np.random.default_rng(13).standard_normal(Ao.n)
+    z = P.apply(bo.BO_STAGE_AMG, _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
     ref = Po.apply(r)
     assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
 
@@ -206,7 +229,7 @@ def test_amg_multilevel_with_tail_matches_oracle(bo, ctx):
     a, Ao, A, P = _cpr_pair(bo, ctx, case, dims)
     lv = P.amg_levels()
     assert lv[0] == dims and lv[1] == (48, 48, 20) and np.prod(lv[-1]) <= 128
-    Po = oracle.cpr_prec(Ao, dims, amg=oracle.AmgParams(coarse_max=128), stage=oracle.STAGE_AMG)
+    Po = oracle.cpr_prec(Ao, dims, amg=_oracle_amg(), stage=oracle.STAGE_AMG)
     r = np.random.default_rng(10).standard_normal(Ao.n)
     z = P.apply(bo.BO_STAGE_AMG, _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
     ref = Po.apply(r)
