@@ -124,10 +124,9 @@ struct DevState {
   double bnorm;    // ||b||
   double wn0;      // ||w|| before orthogonalisation
   double hn;       // ||w|| after orthogonalisation
-  double wn2;      // ||w||^2 before the current Gram-Schmidt pass
   double scale;    // 1 / h_{j+1,j}: normalisation of the new basis vector
-  int reorth;      // the current column needs a second Gram-Schmidt pass
-  double h[136];   // coefficients of the column under construction: pass 1 at 0, pass 2 at 64
+  double vscale[72];  // 1 / ||V_k|| of the unnormalised basis vectors
+  double h[136];   // Gram-Schmidt coefficients of the column under construction: pass 1 at 0, pass 2 at 64
 };
 
 // Number of kernels this library has launched (reported by bo_kernel_launches).
@@ -255,7 +254,8 @@ void launch_newton_update(double* state, const double* dx, int64_t n, cudaStream
 int prec_values(bo_prec* P);   // decoupling + ILU + AMG values (stream-ordered, flags in st->err)
 int prec_alloc(bo_prec* P);
 void prec_free(bo_prec* P);
-void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st);  // internal order, FP64 in and out
+// z = stage(v * vs[0]) in internal order, FP64 in and out (vs may be NULL: scale 1)
+void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs = nullptr);
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  // FP64 values of At rebuilt on the fly
 
 // krylov.cu

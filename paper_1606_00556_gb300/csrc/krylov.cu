@@ -8,14 +8,16 @@
 // so the iterates are those of the decoupled system and the minimised norm
 // is the original residual.
 //
-// Orthogonalisation: classical Gram-Schmidt with a selective second pass
-// ("twice is enough", Kahan-Parlett).  One pass computes the j+1
-// coefficients h = V^T w and ||w||^2 together; ||w - V h||^2 then follows
-// from Pythagoras as ||w||^2 - ||h||^2.  Unless that cancels to below
-// kReorthEta2 ||w||^2 the column is accepted and the update pass writes the
-// normalised v_{j+1} directly; otherwise a second pass re-orthogonalises.
-// On GB300 FP64 arithmetic, not HBM, bounds these passes, so every pass
-// saved is FP64 time saved.
+// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2) for every
+// column: a multi-dot pass h1 = V^T w, an update pass w -= V h1, then the
+// same again, the second update also reducing ||w||^2 exactly and applying
+// the Givens step.  A second pass is necessary here: with a strong CPR
+// preconditioner A M^{-1} is close to the identity, so the new direction
+// cancels to 1e-6 of ||w|| and one classical pass alone loses all
+// orthogonality.  The basis vectors are stored unnormalised with their
+// scale 1/||v|| kept on the device; every reader applies it, so no pass is
+// spent normalising.  On GB300 these passes are bound jointly by FP64
+// arithmetic and HBM (one FMA per 8 bytes read).
 //
 // Every reduction is two-stage with a fixed order (per-block partial sums,
 // then the last block to finish sums the partials), so results are bitwise
@@ -24,6 +26,7 @@
 // convergence, so the host only polls with a lag of one iteration.
 #include <chrono>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -35,12 +38,7 @@ namespace {
 constexpr int kRedBlocks = 4 * 152;  // blocks of single reductions
 constexpr int kMaxM = 64;
 constexpr int kHistCap = 4096;
-// Second pass only when ||w - V h|| < 1e-2 ||w||: above that the
-// Pythagorean norm is accurate to ~1e-12 and one classical pass loses at
-// most ~1e-12 of orthogonality, far below the 1e-8 target.  (A strongly
-// preconditioned w lies mostly in span(V), so the textbook threshold of
-// 1/sqrt(2) would request the second pass at every step.)
-constexpr double kReorthEta2 = 1e-4;
+constexpr int kDotBlocks = 2 * 152;  // most chunks of the multi-dot pass
 
 // w = A z in FP64 on internal vectors
 __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const double* __restrict__ A,
@@ -146,8 +144,8 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
     st->done = 0;
     st->k = 0;
     st->happy = 0;
-    st->reorth = 0;
     st->est = st->beta;
+    st->vscale[0] = 1.0;
   }
 }
 
@@ -201,67 +199,77 @@ struct ArnoldiArgs {
   int hist_at;
 };
 
-// Gram-Schmidt coefficient pass: h[u] = <V_u, w> for u <= j and ||w||^2
-// (grid y = j + 2).  Pass 0 decides from Pythagoras whether the column is
-// accepted (then it also applies the Givens step); pass 1 (run only when a
-// second pass was requested) finishes the column.
+// Gram-Schmidt coefficient pass: h[off + u] = vscale[u] <V_u, w> for u <= j.
+// Grid (chunks, j + 1): block (c, u) sums column u over chunk c; the block
+// that finishes last reduces each column's partials with one warp per column.
 __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const double* __restrict__ V, int64_t ldv,
                                                      const double* __restrict__ w, double* partials, DevState* st,
-                                                     int pass, ArnoldiArgs aa) {
+                                                     int off) {
   __shared__ double sh[32];
-  __shared__ double hs[kMaxM + 1];
-  if (st->done || (pass == 1 && !st->reorth)) return;
-  const int nv = aa.j + 1;
+  if (st->done) return;
+  const int nv = gridDim.y;
   const int nchunk = gridDim.x;
-  const int v = blockIdx.y;
+  const int u = blockIdx.y;
   const int64_t len = (n + nchunk - 1) / nchunk;
   const int64_t i0 = blockIdx.x * len;
   const int64_t i1 = min(n, i0 + len);
-  const double* a = (v < nv) ? V + (size_t)v * ldv : w;
+  const double* a = V + (size_t)u * ldv;
   double acc = 0.0;
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += a[i] * w[i];
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[(size_t)v * nchunk + blockIdx.x] = acc;
-  if (!last_block(&st->counter[0], nchunk * (nv + 1))) return;
-  for (int u = 0; u <= nv; ++u) {
-    const double s = reduce_partials(partials + (size_t)u * nchunk, nchunk, sh);
-    if (threadIdx.x == 0) hs[u] = s;
+  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = acc;
+  if (!last_block(&st->counter[0], nchunk * nv)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < nv; r += kThreads / 32) {
+    double t = 0.0;
+    for (int b = lane; b < nchunk; b += 32) t += __ldcg(partials + (size_t)r * nchunk + b);
+    t = warp_sum(t);
+    if (lane == 0) st->h[off + r] = t * st->vscale[r];
   }
-  if (threadIdx.x != 0) return;
-  st->counter[0] = 0;
-  const double wn2 = hs[nv];
-  double h2 = 0.0;
-  for (int u = 0; u < nv; ++u) {
-    st->h[pass * kMaxM + u] = hs[u];
-    h2 += hs[u] * hs[u];
-  }
-  const double rest = wn2 - h2;  // ||w - V h||^2 if V is orthonormal
-  if (pass == 0) {
-    st->reorth = !(rest >= kReorthEta2 * wn2);
-    if (st->reorth) return;  // keep h, orthogonalise once more before the Givens step
-  }
-  double col[kMaxM + 1];
-  for (int u = 0; u < nv; ++u) col[u] = st->h[u] + (pass == 1 ? st->h[kMaxM + u] : 0.0);
-  givens_step(st, col, sqrt(rest > 0.0 ? rest : 0.0), aa.H, aa.cs, aa.sn, aa.gv, aa.j, aa.m, aa.ldh, aa.hist,
-              aa.hist_at);
+  if (threadIdx.x == 0) st->counter[0] = 0;
 }
 
-// Gram-Schmidt update pass: w -= V h; when the column is final (accepted
-// after this pass) the result is scaled to the unit vector v_{j+1}.
+// Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u.  In the
+// final pass (LAST) ||w||^2 is reduced exactly and the last block applies
+// the Givens step to h1 + h2 and stores 1/||w|| as the new column's scale
+// (w itself stays unnormalised).
+template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double* __restrict__ V, int64_t ldv,
-                                                       double* __restrict__ w, DevState* st, int pass, int nv) {
-  __shared__ double hs[kMaxM + 1];
-  __shared__ double scale;
-  if (st->done || (pass == 1 && !st->reorth)) return;
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = st->h[pass * kMaxM + k];
-  if (threadIdx.x == 0) scale = (pass == 0 && st->reorth) ? 1.0 : st->scale;
+                                                       double* __restrict__ w, double* partials, DevState* st,
+                                                       ArnoldiArgs aa) {
+  __shared__ double c[kMaxM + 1];
+  __shared__ double sh[32];
+  if (st->done) return;
+  const int nv = aa.j + 1;
+  const int off = LAST ? kMaxM : 0;
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = st->h[off + k] * st->vscale[k];
   __syncthreads();
-  const double sc = scale;
+  double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = w[i];
-    for (int k = 0; k < nv; ++k) s -= hs[k] * V[(size_t)k * ldv + i];
-    w[i] = s * sc;
+    for (int k = 0; k < nv; ++k) s -= c[k] * V[(size_t)k * ldv + i];
+    w[i] = s;
+    if (LAST) acc += s * s;
   }
+  if (!LAST) return;
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (!last_block(&st->counter[3], gridDim.x)) return;
+  const double hn2 = reduce_partials(partials, gridDim.x, sh);
+  if (threadIdx.x != 0) return;
+  st->counter[3] = 0;
+  double col[kMaxM + 1];
+  for (int u = 0; u < nv; ++u) col[u] = st->h[u] + st->h[kMaxM + u];
+  const double hn = sqrt(hn2);
+  givens_step(st, col, hn, aa.H, aa.cs, aa.sn, aa.gv, aa.j, aa.m, aa.ldh, aa.hist, aa.hist_at);
+  st->vscale[aa.j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+int gs_chunks(int64_t n) {
+  int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
+  if (c < 1) c = 1;
+  if (c > 2 * 152) c = 2 * 152;
+  return (int)c;
 }
 
 // y = H(0:k, 0:k)^{-1} g (upper triangular after the rotations)
@@ -290,12 +298,6 @@ __global__ void k_xupdate(int64_t n, double* __restrict__ x, const double* __res
   }
 }
 
-int gs_chunks(int64_t n) {
-  int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
-  if (c < 1) c = 1;
-  if (c > 2 * 152) c = 2 * 152;
-  return (int)c;
-}
 
 }  // namespace
 
@@ -323,7 +325,7 @@ int krylov_alloc(bo_prec* P, int m) {
     P->xi = (double*)al((size_t)n * sizeof(double));
     P->bi = (double*)al((size_t)n * sizeof(double));
     P->rk = (double*)al((size_t)n * sizeof(double));
-    P->npartials = (int64_t)(kMaxM + 2) * 2 * 152 + kHistCap;
+    P->npartials = (int64_t)(kMaxM + 2) * kDotBlocks + kHistCap;
     P->partials = (double*)al((size_t)P->npartials * sizeof(double));
     P->hostio = (double*)al((size_t)2 * n * sizeof(double));
     if (ok && cudaMallocHost(&P->h_st, 2 * sizeof(DevState)) != cudaSuccess) ok = false;
@@ -387,7 +389,7 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
     const double target = o->tol * bnorm;
     const int64_t ldv = n;
     const int gn = grid_for(n);
-    const int gu = occ_grid((const void*)k_gs_update, n);
+    const int gu = occ_grid((const void*)k_gs_update<true>, n);
     while (beta > target && its < o->maxit) {
       (k_cycle_start<<<1, 64, 0, s>>>(st, P->gvec, m), note_launch());
       (k_scale_beta<<<gn, kThreads, 0, s>>>(n, P->rk, P->V, st), note_launch());
@@ -395,7 +397,7 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
         double* vj = P->V + (size_t)j * ldv;
         double* w = P->V + (size_t)(j + 1) * ldv;
         double* zj = P->Z + (size_t)j * n;
-        launch_cpr(P, vj, zj, BO_STAGE_CPR, st);
+        launch_cpr(P, vj, zj, BO_STAGE_CPR, st, &st->vscale[j]);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (o->profile && prof.size() < 512) {
           e0 = P->prof_ev[2 * prof.size()];
@@ -409,11 +411,11 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
           prof.push_back({e0, e1});
         }
         const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j};
-        const dim3 gd(gs_chunks(n), j + 2);
-        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, 0, aa), note_launch());
-        (k_gs_update<<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, st, 0, j + 1), note_launch());
-        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, 1, aa), note_launch());
-        (k_gs_update<<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, st, 1, j + 1), note_launch());
+        const dim3 gd(gs_chunks(n), j + 1);
+        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, 0), note_launch());
+        (k_gs_update<false><<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, aa), note_launch());
+        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
+        (k_gs_update<true><<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, aa), note_launch());
         cudaMemcpyAsync(&P->h_st[j & 1], st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         cudaEventRecord(P->ev[j & 1], s);
         if (j >= 1) {

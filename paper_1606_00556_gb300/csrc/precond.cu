@@ -149,7 +149,7 @@ __global__ void k_ilu_red(Geom g, const T* __restrict__ At, T* __restrict__ Dinv
 
 // black pivots: D_b' = D_b - sum_r A_br D_r^{-1} A_rb, stored inverted
 template <typename T>
-__global__ void k_ilu_black(Geom g, const T* __restrict__ At, T* __restrict__ Dinv, DevState* st) {
+__global__ void __launch_bounds__(kThreads, 2) k_ilu_black(Geom g, const T* __restrict__ At, T* __restrict__ Dinv, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
     T S[9], inv[9];
@@ -374,11 +374,13 @@ __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __rest
 // Entry of the preconditioner: f = D_QI^{-1} v (DEC) or f = v, in precision
 // T, fused with the first ILU pass on the red cells, t_r = D_r^{-1} f_r.
 template <typename T, bool DEC>
-__global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* __restrict__ w,
-                            const T* __restrict__ Dinv, T* __restrict__ f, T* __restrict__ tv, const DevState* st) {
+__global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* __restrict__ vs,
+                            const double* __restrict__ w, const T* __restrict__ Dinv, T* __restrict__ f,
+                            T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
+  const double sc = vs ? *vs : 1.0;  // scale of an unnormalised Krylov vector
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
-    const double v0 = v[t], v1 = v[g.N + t], v2 = v[2 * g.N + t];
+    const double v0 = sc * v[t], v1 = sc * v[g.N + t], v2 = sc * v[2 * g.N + t];
     const T f0 = DEC ? (T)(v0 - w[t] * v1 - w[g.N + t] * v2) : (T)v0;
     const T f1 = (T)v1, f2 = (T)v2;
     f[t] = f0;
@@ -434,8 +436,15 @@ __device__ __forceinline__ void offdiag_sum(const Geom& g, const T* __restrict__
 // OUT = false: z_b = u_b (precision T).
 // OUT = true: t_b = u_b and the preconditioner's result on black cells,
 //   zo_b = z1_b + Pi_p e_b + u_b, in FP64.
+// blocks per SM the register budget is tuned for: the FP32 passes are
+// memory-latency bound and want more warps; the FP64 ones are FP64-bound
+template <typename T>
+constexpr int ilu_min_blocks() { return sizeof(T) == 4 ? 4 : 3; }
+template <typename T, int ROWS>
+constexpr int res_min_blocks() { return (sizeof(T) == 4 && ROWS == 1) ? 5 : 4; }
+
 template <typename T, bool OUT>
-__global__ void __launch_bounds__(kThreads, 3) k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ src,
+__global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ src,
                         T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
                         const DevState* st) {
   if (st->done) return;
@@ -469,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ilu_b(Geom g, const T* __restri
 // OUT = false: z_r = t_r - corr (precision T).
 // OUT = true: zo_r = z1_r + Pi_p e_r + t_r - corr, in FP64.
 template <typename T, bool OUT>
-__global__ void __launch_bounds__(kThreads, 3) k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ tv,
+__global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ tv,
                          const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
                          const DevState* st) {
   if (st->done) return;
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ilu_r2(Geom g, const T* __restr
 // ROWS = 3: out = f - At (z + Pi_p e), all components, fused with the first
 //   ILU pass of the second local solve on red cells: tv_r = D_r^{-1} out_r.
 template <typename T, int ROWS>
-__global__ void __launch_bounds__(kThreads, 4) k_cpr_residual(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
+__global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_residual(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
                                const T* __restrict__ e, T* __restrict__ out, const T* __restrict__ Dinv,
                                T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
@@ -927,7 +936,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
 
 // z = CPR stage applied to v (FP64, internal order); result FP64 in zo
 template <typename T>
-void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevState* st) {
+void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevState* st, const double* vs) {
   cudaStream_t s = P->mat->ctx->stream;
   const Geom& g = P->mat->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
@@ -939,7 +948,7 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
   T* e0 = (T*)P->e0;
   T* f0 = (T*)P->f0;
   T* z1 = (T*)P->z1;
-  if (stage == BO_STAGE_AMG) {
+  if (stage == BO_STAGE_AMG) {  // (v is a caller's vector here: vs is NULL)
     (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v, f0, st), note_launch());
     amg_vcycle<T>(P, st);
     (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo, st), note_launch());
@@ -947,12 +956,12 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
   }
   // x1 = R^{-1} f with f = D_QI^{-1} v (stage CPR) or f = v
   if (stage == BO_STAGE_CPR)
-    (k_cpr_entry<T, true><<<occ_grid((const void*)k_cpr_entry<T, true>, g.N), kThreads, 0, s>>>(g, v, P->w, D, f,
-                                                                                                  tv, st),
+    (k_cpr_entry<T, true><<<occ_grid((const void*)k_cpr_entry<T, true>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
+                                                                                                  f, tv, st),
      note_launch());
   else
-    (k_cpr_entry<T, false><<<occ_grid((const void*)k_cpr_entry<T, false>, g.N), kThreads, 0, s>>>(g, v, P->w, D, f,
-                                                                                                    tv, st),
+    (k_cpr_entry<T, false><<<occ_grid((const void*)k_cpr_entry<T, false>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
+                                                                                                    f, tv, st),
      note_launch());
   (k_ilu_b<T, false><<<occ_grid((const void*)k_ilu_b<T, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
                                                                                           nullptr, st),
@@ -1073,9 +1082,9 @@ int prec_values(bo_prec* P) {
   return P->fp32 ? values_impl<float>(P) : values_impl<double>(P);
 }
 
-void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st) {
-  if (P->fp32) cpr_apply<float>(P, v, z, stage, st);
-  else cpr_apply<double>(P, v, z, stage, st);
+void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs) {
+  if (P->fp32) cpr_apply<float>(P, v, z, stage, st, vs);
+  else cpr_apply<double>(P, v, z, stage, st, vs);
 }
 
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {
