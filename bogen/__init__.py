@@ -201,4 +201,4 @@ def relperm(fluid: Fluid, sw: float, sg: float):
     return out
 
 
-from .fields import tiny_case, waterflood_case, gaussian_field, uniform_case  # noqa: E402,F401
+from .fields import tiny_case, waterflood_case, gaussian_field, uniform_case, ensemble_specs, ensemble_case  # noqa: E402,F401,E501

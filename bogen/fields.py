@@ -105,3 +105,38 @@ def waterflood_case(nx: int = 128, ny: int = 128, nz: int = 64, seed: int = 42, 
     wells.append(Well(1, prod_bhp, _column(nx, ny, nz, nx // 2, ny // 2)))
     return Case(nx, ny, nz, 100.0, 100.0, 20.0, kh, kh.copy(), kv, np.full(N, 0.2),
                 depth, x, x.copy(), 1.0, wells, default_fluid())
+
+
+def ensemble_specs(n: int = 256, seed: int = 7, total_unknowns=(38e6, 42e6), max_draws: int = 10000):
+    """Grid sizes and parameters of a batch of realisations of uneven size.
+
+    nx, ny ~ log-uniform[32, 96] and nz ~ log-uniform[8, 24], rounded to
+    integers (nx then rounded up to even: the solver's red-black layout pairs
+    the cells of a grid row); the draw is repeated until the total number of
+    unknowns 3 sum(nx ny nz) lies in `total_unknowns`.  Each realisation gets
+    its own seed and a permeability sigma ~ U[0.5, 2.0].  Returns a list of
+    dicts (dims, sigma, seed)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = total_unknowns
+    for _ in range(max_draws):
+        nx = np.exp(rng.uniform(np.log(32), np.log(96), n)).round().astype(int)
+        nx += nx % 2
+        ny = np.exp(rng.uniform(np.log(32), np.log(96), n)).round().astype(int)
+        nz = np.exp(rng.uniform(np.log(8), np.log(24), n)).round().astype(int)
+        tot = 3 * int(np.sum(nx * ny * nz))
+        if lo <= tot <= hi:
+            sig = rng.uniform(0.5, 2.0, n)
+            seeds = rng.integers(0, 2 ** 31 - 1, n)
+            return [dict(dims=(int(a), int(b), int(c)), sigma=float(s), seed=int(q))
+                    for a, b, c, s, q in zip(nx, ny, nz, sig, seeds)]
+    raise RuntimeError("no draw within the unknown-count window")
+
+
+def ensemble_case(spec) -> Case:
+    """One realisation of the ensemble: the five-spot waterflood generator on
+    the realisation's grid, with correlation lengths and front radius scaled
+    to the grid (1/8 of the horizontal size, 1/8 of the layers)."""
+    nx, ny, nz = spec["dims"]
+    corr = (max(1.0, nx / 8), max(1.0, ny / 8), max(1.0, nz / 8))
+    return waterflood_case(nx, ny, nz, seed=spec["seed"], day=0, sigma=spec["sigma"], corr=corr,
+                           front0=0.3 * min(nx, ny), front_speed=0.0)

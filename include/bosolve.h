@@ -156,9 +156,19 @@ int bo_prec_destroy(bo_prec* P);
 /* Solve A x = b with FGMRES(m) + CPR to ||b - A x|| <= tol ||b|| (paper
  * Alg. 1 step "find dx").  b, x: length 3 nx ny nz, device or host memory
  * per opts->mem; x holds the initial guess unless x0_is_zero.  On
- * BO_ERR_NOT_CONVERGED x holds the last iterate and info is filled.  b = 0
- * returns x = 0.  info may be NULL. */
+ * BO_ERR_NOT_CONVERGED (maxit reached, or a whole restart cycle reduced the
+ * residual by less than 1%) x holds the last iterate and info is filled.
+ * b = 0 returns x = 0.  info may be NULL. */
 int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
+/* Solve nreal independent systems A_r x_r = b_r at once (an ensemble of
+ * realisations, possibly of different grid sizes; each P[r] a distinct
+ * preconditioner on the same device).  The solves run concurrently on a
+ * pool of streams driven by one host thread, each exactly as bo_solve
+ * would run it (same kernels, same results).  infos: nreal entries or
+ * NULL.  Returns BO_OK or the first failing status; each info holds its
+ * own.  Synchronises before returning. */
+int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x,
+                     const bo_solve_opts* opts, bo_solve_info* infos);
 /* Estimated relative residuals of the last solve, one per iteration; returns
  * how many were written (at most cap). */
 int bo_prec_residual_history(bo_prec* P, double* buf, int cap);

@@ -118,10 +118,12 @@ def spmv(A: BsrMatrix, x) -> np.ndarray:
 
 
 def qi_decouple(A: BsrMatrix):
-    """(D_QI^{-1} A, w) with w[i] = (a_01/a_11, a_02/a_22) of A_ii (paper
-    Sec. 3.2, Quasi-IMPES decoupling operator).  Raises on a zero pivot."""
+    """(D_QI^{-1} A, g): g[i] = the weights of the decoupled pressure row of
+    cell i, (1, -a_01/a_11, -a_02/a_22) of A_ii (paper Sec. 3.2, Quasi-IMPES),
+    or row 0 of A_ii^{-1} where Quasi-IMPES leaves a non-positive pressure
+    pivot.  Raises on a zero pivot."""
     out = np.zeros_like(A.val)
-    w = np.zeros((A.nb, 2))
+    w = np.zeros((A.nb, 3))
     rc = lib().or_qi_decouple(ctypes.c_int64(A.nb), _p(A.rowptr, _I32), _p(A.col, _I32), _p(A.val, _D),
                               _p(out, _D), _p(w, _D))
     if rc != 0:

@@ -423,7 +423,7 @@ struct IluPrec : Prec {
 // system it is applied to D_QI^{-1} v.
 struct CprPrec : Prec {
   Bsr At;
-  std::vector<double> w;  // per cell (w_w, w_g): D_QI^{-1} row 0 = e0 - w_w e1 - w_g e2
+  std::vector<double> w;  // per cell (g0, g1, g2): D_QI^{-1} row 0 = g0 e0 + g1 e1 + g2 e2
   IluPrec R;
   Amg amg;
   int stage = 0;  // 0 full CPR on D^{-1} v, 1 ILU only, 2 AMG only (Pi_p AMG Pi_r), 3 CPR on f as given
@@ -457,7 +457,7 @@ struct CprPrec : Prec {
     }
     if (stage == 3) { cpr_decoupled(v, z); return; }
     std::vector<double> f(v, v + 3 * nb);
-    for (int64_t i = 0; i < nb; ++i) f[3 * i] = v[3 * i] - w[2 * i] * v[3 * i + 1] - w[2 * i + 1] * v[3 * i + 2];
+    for (int64_t i = 0; i < nb; ++i) f[3 * i] = w[3 * i] * v[3 * i] + w[3 * i + 1] * v[3 * i + 1] + w[3 * i + 2] * v[3 * i + 2];
     cpr_decoupled(f.data(), z);
   }
 };
@@ -466,20 +466,34 @@ struct CprPrec : Prec {
 // [0, I, 0], [0, 0, I]] with D_ps = diag(A_ps), D_ss = diag(A_ss), read per
 // cell on its own diagonal block: the pressure equation is the oil row 0,
 // the saturation equations are rows 1 (water) and 2 (gas) against unknowns
-// Sw (column 1) and Sg (column 2).  So D_ps D_ss^{-1} on cell i is the row
-// (a_01 / a_11, a_02 / a_22) of A_ii, and D_QI^{-1} has its negative.
-int qi_decouple(const Bsr& A, Bsr& At, std::vector<double>& w) {
+// Sw (column 1) and Sg (column 2).  So D_QI^{-1} replaces row 0 of cell i by
+// g . (row0, row1, row2) with g = (1, -a_01/a_11, -a_02/a_22) from A_ii.
+// Where that leaves the cell's pressure pivot non-positive (injector cells
+// flooded to residual oil, where the oil row carries no pressure
+// information), the cell takes the exact local decoupling instead (the ABF
+// alternative the paper names): g = row 0 of A_ii^{-1}, pivot 1.  g holds
+// the three weights per cell.
+int qi_decouple(const Bsr& A, Bsr& At, std::vector<double>& g) {
   At = A;
-  w.assign(2 * A.nb, 0.0);
+  g.assign(3 * A.nb, 0.0);
   for (int64_t i = 0; i < A.nb; ++i) {
     const double* D = nullptr;
     for (int32_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
       if (A.col[e] == i) D = &A.val[(size_t)e * 9];
     if (!D || D[4] == 0.0 || D[8] == 0.0) return kBreakdown;
-    const double ww = D[1] / D[4], wg = D[2] / D[8];
-    w[2 * i] = ww;
-    w[2 * i + 1] = wg;
-    const double Dinv[9] = {1.0, -ww, -wg, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
+    double gi[3] = {1.0, -D[1] / D[4], -D[2] / D[8]};
+    const double pivot = gi[0] * D[0] + gi[1] * D[3] + gi[2] * D[6];
+    if (!(pivot > 0.0)) {
+      // row 0 of A_ii^{-1}: solve A_ii^T y = e_0
+      double Dt[9], e0[3] = {1.0, 0.0, 0.0};
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Dt[3 * r + c] = D[3 * c + r];
+      if (!block_solve(3, Dt, e0, gi)) return kBreakdown;
+    }
+    g[3 * i] = gi[0];
+    g[3 * i + 1] = gi[1];
+    g[3 * i + 2] = gi[2];
+    const double Dinv[9] = {gi[0], gi[1], gi[2], 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
     for (int32_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
       block_mul(3, Dinv, &A.val[(size_t)e * 9], &At.val[(size_t)e * 9]);
   }
@@ -534,7 +548,7 @@ void or_bsr_spmv(int64_t nb, int bs, const int32_t* rowptr, const int32_t* col, 
   A.spmv(x, y);
 }
 
-// out = D_QI^{-1} A (same pattern), w[2 nb] = (a_01/a_11, a_02/a_22) per cell
+// out = D_QI^{-1} A (same pattern), g[3 nb] = the row-0 weights of D_QI^{-1} per cell
 int or_qi_decouple(int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                    double* out, double* w) {
   Bsr A = make_bsr(nb, 3, rowptr, col, val), At;

@@ -42,7 +42,8 @@ EXPORTS = (
     "bo_status_str", "bo_prec_opts_default", "bo_solve_opts_default", "bo_ctx_create", "bo_ctx_destroy",
     "bo_mat_create_bsr", "bo_mat_create_csr", "bo_mat_update_values", "bo_mat_spmv", "bo_mat_destroy",
     "bo_prec_setup", "bo_prec_update", "bo_prec_apply", "bo_prec_spmv_decoupled", "bo_prec_amg_levels",
-    "bo_prec_destroy", "bo_solve", "bo_prec_residual_history", "bo_newton_update", "bo_kernel_launches",
+    "bo_prec_destroy", "bo_solve", "bo_solve_batched", "bo_prec_residual_history", "bo_newton_update",
+    "bo_kernel_launches",
     "bo_mat_residual_noalloc",
 )
 
@@ -111,6 +112,8 @@ def lib():
         L.bo_prec_amg_levels.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
         L.bo_prec_destroy.argtypes = [_VP]
         L.bo_solve.argtypes = [_VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
+        L.bo_solve_batched.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                       ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
         L.bo_prec_residual_history.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.bo_newton_update.argtypes = [_VP, _VP, _VP, ctypes.c_int64]
         L.bo_mat_residual_noalloc.argtypes = [_VP, _VP, _VP, _VP, _VP]
@@ -329,6 +332,25 @@ def bo_mat_residual_noalloc(mat: Matrix, b, x, r, norms):
     _check(lib().bo_mat_residual_noalloc(mat.h, _VP(b.data_ptr()), _VP(x.data_ptr()), _VP(r.data_ptr()),
                                          _VP(norms.data_ptr())), "bo_mat_residual_noalloc")
     return r, norms
+
+
+def bo_solve_batched(precs, bs, xs, tol=1e-8, restart=30, maxit=500, x0_is_zero=True):
+    """bo_solve_batched: solve every (precs[r], bs[r]) into xs[r] at once
+    (device tensors).  Returns (status, [info dict per system])."""
+    n = len(precs)
+    if not (len(bs) == len(xs) == n) or n == 0:
+        raise ValueError("one b and one x per preconditioner")
+    P = (_VP * n)(*[p.h for p in precs])
+    B = (_VP * n)(*[_VP(t.data_ptr()) for t in bs])
+    X = (_VP * n)(*[_VP(t.data_ptr()) for t in xs])
+    o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
+    infos = (bo_solve_info * n)()
+    rc = lib().bo_solve_batched(P, n, B, X, ctypes.byref(o), infos)
+    out = []
+    for i in infos:
+        d = i.as_dict()
+        out.append(d)
+    return rc, out
 
 
 def bo_kernel_launches() -> int:

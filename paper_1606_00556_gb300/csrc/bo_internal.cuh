@@ -192,11 +192,12 @@ struct Level {
 
 struct bo_prec {
   bo_mat* mat;
+  cudaStream_t stream;     // stream of all preconditioner work (the context's, or a batch stream)
   bo_prec_opts opts;
   bool fp32;               // preconditioner arithmetic FP32 (else FP64)
   size_t tsize;            // sizeof(preconditioner scalar)
   void* At;                // 63 N decoupled values (preconditioner precision)
-  double* w;               // 2 N Quasi-IMPES weights (w_w, w_g) [2][N] internal order
+  double* w;               // 3 N decoupling weights (g0, g1, g2) of row 0, [3][N] internal order
   void* Dinv;              // 9 N inverted ILU pivot blocks [rc][N], preconditioner precision
   // AMG: level 0 = the pressure block of At (colour-split), levels 1.. natural order
   int nlev;
@@ -228,8 +229,8 @@ struct bo_prec {
   int64_t npartials;
   double* hostio;          // device staging of host b / x
   bo::DevState* st;        // device state
-  bo::DevState* h_st;      // pinned host mirror (two slots)
-  cudaEvent_t ev[2];
+  bo::DevState* h_st;      // pinned host mirror (three column slots, one phase slot)
+  cudaEvent_t ev[4];
   cudaEvent_t prof_ev[2 * 512];
   bool prof_ready;
   double* hist;            // host residual history of the last solve
@@ -260,6 +261,8 @@ void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  //
 
 // krylov.cu
 int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
+int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
+                   bo_solve_info* infos);
 int krylov_alloc(bo_prec* P, int m);
 
 }  // namespace bo

@@ -6,6 +6,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <vector>
 
 #include "bo_internal.cuh"
 
@@ -164,7 +165,7 @@ void prec_opts_fill(const bo_prec_opts* in, bo_prec_opts* o) {
 
 // set up values and read the error bits back
 int prec_refresh(bo_prec* P) {
-  cudaStream_t s = P->mat->ctx->stream;
+  cudaStream_t s = P->stream;
   cudaMemsetAsync(&P->st->err, 0, sizeof(int), s);
   int rc = prec_values(P);
   if (rc != BO_OK) return rc;
@@ -293,6 +294,7 @@ int bo_prec_setup(bo_mat* m, const bo_prec_opts* opts, bo_prec** out) {
   if (!P) return BO_ERR_OOM;
   std::memset(P, 0, sizeof(*P));
   P->mat = m;
+  P->stream = m->ctx->stream;
   m->refs++;
   P->opts = o;
   P->fp32 = o.precision == BO_PREC_FP32;
@@ -315,7 +317,7 @@ int bo_prec_update(bo_prec* P) {
 
 int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z) {
   if (!P || !r || !z || stage < BO_STAGE_CPR || stage > BO_STAGE_CPR_DECOUPLED) return BO_ERR_ARG;
-  cudaStream_t s = P->mat->ctx->stream;
+  cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   cudaMemsetAsync(&P->st->done, 0, sizeof(int), s);
   // r -> internal (xi as scratch), apply, z (precision T) -> FP64 internal -> natural
@@ -327,7 +329,7 @@ int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z) {
 
 int bo_prec_spmv_decoupled(bo_prec* P, const double* x, double* y) {
   if (!P || !x || !y) return BO_ERR_ARG;
-  cudaStream_t s = P->mat->ctx->stream;
+  cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   launch_gather(g, x, P->bi, s);
   launch_spmv_decoupled_internal(P, P->bi, P->xi);
@@ -349,14 +351,14 @@ int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap) {
 
 int bo_prec_destroy(bo_prec* P) {
   if (!P) return BO_ERR_ARG;
-  cudaStreamSynchronize(P->mat->ctx->stream);
+  cudaStreamSynchronize(P->stream);
   prec_free(P);
   auto fr = [](void* p) { if (p) cudaFree(p); };
   fr(P->V); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
   fr(P->xi); fr(P->bi); fr(P->rk); fr(P->partials); fr(P->hostio);
   if (P->h_st) cudaFreeHost(P->h_st);
-  if (P->ev[0]) cudaEventDestroy(P->ev[0]);
-  if (P->ev[1]) cudaEventDestroy(P->ev[1]);
+  for (int e = 0; e < 4; ++e)
+    if (P->ev[e]) cudaEventDestroy(P->ev[e]);
   if (P->prof_ready)
     for (int i = 0; i < 2 * 512; ++i) cudaEventDestroy(P->prof_ev[i]);
   delete[] P->hist;
@@ -376,6 +378,61 @@ int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, 
     return BO_ERR_ARG;
   if (cudaSetDevice(P->mat->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   return fgmres(P, b, x, &o, info);
+}
+
+int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x,
+                     const bo_solve_opts* opts, bo_solve_info* infos) {
+  if (!P || !b || !x || nreal < 1) return BO_ERR_ARG;
+  bo_solve_opts o;
+  bo_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 64 || o.maxit < 0 ||
+      (o.mem != BO_MEM_HOST && o.mem != BO_MEM_DEVICE))
+    return BO_ERR_ARG;
+  const int dev = P[0] ? P[0]->mat->ctx->device : -1;
+  for (int r = 0; r < nreal; ++r) {
+    if (!P[r] || !b[r] || !x[r] || P[r]->mat->ctx->device != dev) return BO_ERR_ARG;
+    for (int q = 0; q < r; ++q)
+      if (P[q] == P[r]) return BO_ERR_ARG;  // each solve needs its own workspace
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
+  // a pool of streams per device, created once and kept for the process
+  constexpr int kPool = 16;
+  static std::mutex mu;
+  static std::unordered_map<int, std::vector<cudaStream_t>> pools;
+  std::vector<cudaStream_t> pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto& pl = pools[dev];
+    if (pl.empty())
+      for (int i = 0; i < kPool; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return BO_ERR_CUDA;
+        pl.push_back(st);
+      }
+    pool = pl;
+  }
+  // order the batch after everything already queued on the contexts' streams,
+  // and the contexts' streams after the batch
+  std::vector<cudaEvent_t> evs;
+  auto join = [&](cudaStream_t from, cudaStream_t to) {
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventRecord(e, from);
+    cudaStreamWaitEvent(to, e, 0);
+    evs.push_back(e);
+  };
+  const int S = nreal < kPool ? nreal : kPool;
+  for (int r = 0; r < nreal; ++r) join(P[r]->mat->ctx->stream, pool[r % S]);
+  for (int r = 0; r < nreal; ++r) P[r]->stream = pool[r % S];
+  const int rc = fgmres_batched(P, nreal, b, x, &o, infos);
+  for (int r = 0; r < nreal; ++r) {
+    join(pool[r % S], P[r]->mat->ctx->stream);
+    P[r]->stream = P[r]->mat->ctx->stream;
+  }
+  for (int r = 0; r < S; ++r) cudaStreamSynchronize(pool[r]);
+  for (auto e : evs) cudaEventDestroy(e);
+  return rc;
 }
 
 int bo_prec_residual_history(bo_prec* P, double* buf, int cap) {

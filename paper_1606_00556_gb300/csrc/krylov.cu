@@ -328,11 +328,9 @@ int krylov_alloc(bo_prec* P, int m) {
     P->npartials = (int64_t)(kMaxM + 2) * kDotBlocks + kHistCap;
     P->partials = (double*)al((size_t)P->npartials * sizeof(double));
     P->hostio = (double*)al((size_t)2 * n * sizeof(double));
-    if (ok && cudaMallocHost(&P->h_st, 2 * sizeof(DevState)) != cudaSuccess) ok = false;
-    if (ok) {
-      cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming);
-      cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming);
-    }
+    if (ok && cudaMallocHost(&P->h_st, 4 * sizeof(DevState)) != cudaSuccess) ok = false;
+    if (ok)
+      for (int e = 0; e < 4; ++e) cudaEventCreateWithFlags(&P->ev[e], cudaEventDisableTiming);
     P->hist_cap = kHistCap;
     P->hist = new double[kHistCap];
   }
@@ -340,130 +338,305 @@ int krylov_alloc(bo_prec* P, int m) {
   return ok ? BO_OK : BO_ERR_OOM;
 }
 
-int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
-  const auto t0 = std::chrono::steady_clock::now();
-  bo_mat* M = P->mat;
-  cudaStream_t s = M->ctx->stream;
-  const Geom& g = M->g;
-  const int64_t n = 3 * g.N;
-  const int m = o->restart;
-  int rc = krylov_alloc(P, m);
-  if (rc != BO_OK) return rc;
-  DevState* st = P->st;
-  // residual-estimate history on the device: the tail of the partials buffer
-  double* dhist = P->partials + (P->npartials - kHistCap);
+// One FGMRES solve as a resumable state machine.  advance() enqueues the
+// next piece of work on the preconditioner's stream and checks the events
+// of earlier pieces; with block = false it never waits, so many jobs on
+// different streams can be driven round-robin by one host thread
+// (bo_solve_batched); with block = true it waits on the oldest event it
+// needs, which gives the single-solve path its one-column polling lag.
+namespace {
 
-  const double* b_d = b_in;
-  double* x_d = x_in;
-  if (o->mem == BO_MEM_HOST) {
-    cudaMemcpyAsync(P->hostio, b_in, n * sizeof(double), cudaMemcpyHostToDevice, s);
-    b_d = P->hostio;
-    x_d = P->hostio + n;
-    if (!o->x0_is_zero) cudaMemcpyAsync(x_d, x_in, n * sizeof(double), cudaMemcpyHostToDevice, s);
-  }
-  launch_gather(g, b_d, P->bi, s);
-  if (o->x0_is_zero) cudaMemsetAsync(P->xi, 0, n * sizeof(double), s);
-  else launch_gather(g, x_d, P->xi, s);
-  (k_norm<<<kRedBlocks, kThreads, 0, s>>>(n, P->bi, P->partials, st), note_launch());
-  (k_set_target<<<1, 1, 0, s>>>(st, o->tol), note_launch());
-  (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, M->A, P->bi, P->xi, P->rk, P->partials, st), note_launch());
-  cudaMemcpyAsync(P->h_st, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
-  const double bnorm = P->h_st[0].bnorm;
-  double beta = P->h_st[0].beta;
-  double est = beta;
-  int status = BO_OK;
-  int its = 0, restarts = 0;
-  P->nhist = 0;
+constexpr int kRing = 3;        // status slots / events for columns
+constexpr int kPhaseSlot = 3;   // status slot / event for the other phases
+
+struct Job {
+  enum Phase { kStart, kInitWait, kColumns, kCycleWait, kFinalWait, kDone };
+  bo_prec* P = nullptr;
+  const double* b_in = nullptr;
+  double* x_in = nullptr;
+  bo_solve_opts o;
+  bo_solve_info* info = nullptr;
+  const double* b_d = nullptr;
+  double* x_d = nullptr;
+  Phase phase = kStart;
+  double bnorm = 0, beta = 0, est = 0, target = 0;
+  int status = BO_OK, its = 0, restarts = 0;
+  int j_enq = 0, j_polled = 0;
+  bool cycle_stop = false, profile = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
+  std::chrono::steady_clock::time_point t0;
+
+  cudaStream_t stream() const { return P->stream; }
+  const Geom& geom() const { return P->mat->g; }
+  int64_t n() const { return 3 * P->mat->g.N; }
+
+  bool ready(cudaEvent_t e, bool block) {
+    const cudaError_t r = block ? cudaEventSynchronize(e) : cudaEventQuery(e);
+    if (r == cudaSuccess) return true;
+    if (r != cudaErrorNotReady) fail(BO_ERR_CUDA);
+    return false;
+  }
+
+  void fail(int st) {
+    status = st;
+    phase = kDone;
+  }
+
+  void mark(int slot) {
+    cudaMemcpyAsync(&P->h_st[slot], P->st, sizeof(DevState), cudaMemcpyDeviceToHost, stream());
+    cudaEventRecord(P->ev[slot], stream());
+  }
+
+  void start() {
+    t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = stream();
+    const Geom& g = geom();
+    const int64_t nn = n();
+    DevState* st = P->st;
+    b_d = b_in;
+    x_d = x_in;
+    if (o.mem == BO_MEM_HOST) {
+      cudaMemcpyAsync(P->hostio, b_in, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+      b_d = P->hostio;
+      x_d = P->hostio + nn;
+      if (!o.x0_is_zero) cudaMemcpyAsync(x_d, x_in, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    launch_gather(g, b_d, P->bi, s);
+    if (o.x0_is_zero) cudaMemsetAsync(P->xi, 0, nn * sizeof(double), s);
+    else launch_gather(g, x_d, P->xi, s);
+    (k_norm<<<kRedBlocks, kThreads, 0, s>>>(nn, P->bi, P->partials, st), note_launch());
+    (k_set_target<<<1, 1, 0, s>>>(st, o.tol), note_launch());
+    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+     note_launch());
+    mark(kPhaseSlot);
+    P->nhist = 0;
+    phase = kInitWait;
+  }
+
+  void start_cycle() {
+    cudaStream_t s = stream();
+    (k_cycle_start<<<1, 64, 0, s>>>(P->st, P->gvec, o.restart), note_launch());
+    (k_scale_beta<<<grid_for(n()), kThreads, 0, s>>>(n(), P->rk, P->V, P->st), note_launch());
+    j_enq = j_polled = 0;
+    cycle_stop = false;
+    phase = kColumns;
+  }
+
+  void enqueue_column(int j) {
+    cudaStream_t s = stream();
+    const Geom& g = geom();
+    const int64_t nn = n(), ldv = nn;
+    const int m = o.restart;
+    DevState* st = P->st;
+    double* vj = P->V + (size_t)j * ldv;
+    double* w = P->V + (size_t)(j + 1) * ldv;
+    double* zj = P->Z + (size_t)j * nn;
+    double* dhist = P->partials + (P->npartials - kHistCap);
+    launch_cpr(P, vj, zj, BO_STAGE_CPR, st, &st->vscale[j]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profile && prof.size() < 512) {
+      e0 = P->prof_ev[2 * prof.size()];
+      e1 = P->prof_ev[2 * prof.size() + 1];
+      cudaEventRecord(e0, s);
+    }
+    (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(g, P->mat->A, zj, w, st),
+     note_launch());
+    if (e1) {
+      cudaEventRecord(e1, s);
+      prof.push_back({e0, e1});
+    }
+    const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j};
+    const dim3 gd(gs_chunks(nn), j + 1);
+    const int gu = occ_grid((const void*)k_gs_update<true>, nn);
+    (k_gs_dots<<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, 0), note_launch());
+    (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, aa), note_launch());
+    (k_gs_dots<<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
+    (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, aa), note_launch());
+    mark(j % kRing);
+  }
+
+  void end_cycle() {
+    cudaStream_t s = stream();
+    const int64_t nn = n();
+    const int gn = grid_for(nn);
+    (k_trisolve<<<1, 32, 0, s>>>(P->st, P->H, P->gvec, P->y, o.restart), note_launch());
+    (k_xupdate<<<gn, kThreads, 0, s>>>(nn, P->xi, P->Z, nn, P->y, P->st), note_launch());
+    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(geom(), P->mat->A, P->bi, P->xi, P->rk, P->partials, P->st),
+     note_launch());
+    mark(kPhaseSlot);
+    phase = kCycleWait;
+  }
+
+  void finish() {
+    cudaStream_t s = stream();
+    if (status == BO_OK && bnorm > 0 && beta > target) status = BO_ERR_NOT_CONVERGED;
+    launch_scatter(geom(), P->xi, x_d, s);
+    if (o.mem == BO_MEM_HOST) cudaMemcpyAsync(x_in, x_d, n() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(P->ev[kPhaseSlot], s);
+    phase = kFinalWait;
+  }
+
+  void done() {
+    const int nh = its < kHistCap ? its : kHistCap;
+    if (nh > 0 && bnorm > 0) {
+      cudaMemcpy(P->hist, P->partials + (P->npartials - kHistCap), nh * sizeof(double), cudaMemcpyDeviceToHost);
+      for (int i = 0; i < nh; ++i) P->hist[i] /= bnorm;
+    }
+    P->nhist = nh > 0 ? nh : 0;
+    if (info) {
+      info->status = status;
+      info->iters = its;
+      info->restarts = restarts;
+      info->true_rel_res = bnorm > 0 ? beta / bnorm : beta;
+      info->est_rel_res = bnorm > 0 ? est / bnorm : est;
+      info->spmv_launches = 0;
+      info->spmv_ms = 0.0;
+      for (size_t i = 0; i < prof.size(); ++i) {
+        if ((int)i < its) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, prof[i].first, prof[i].second);
+          info->spmv_ms += ms;
+          info->spmv_launches++;
+        }
+      }
+      info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    phase = kDone;
+  }
+
+  // one step of progress; returns whether anything happened
+  bool advance(bool block) {
+    switch (phase) {
+      case kStart:
+        start();
+        return true;
+      case kInitWait: {
+        if (!ready(P->ev[kPhaseSlot], block)) return false;
+        const DevState& h = P->h_st[kPhaseSlot];
+        bnorm = h.bnorm;
+        beta = est = h.beta;
+        if (!std::isfinite(bnorm) || !std::isfinite(beta)) {
+          status = BO_ERR_NONFINITE;
+          finish();
+        } else if (bnorm == 0.0) {
+          cudaMemsetAsync(P->xi, 0, n() * sizeof(double), stream());
+          beta = 0.0;
+          finish();
+        } else {
+          target = o.tol * bnorm;
+          if (beta <= target || its >= o.maxit) finish();
+          else start_cycle();
+        }
+        return true;
+      }
+      case kColumns: {
+        bool moved = false;
+        const int m = o.restart;
+        while (!cycle_stop && j_enq < m && its + j_enq < o.maxit && j_enq - j_polled < 2) {
+          enqueue_column(j_enq++);
+          moved = true;
+        }
+        while (j_polled < j_enq && !cycle_stop) {
+          // the single-solve path waits only for the column before the newest
+          const bool may_block = block && (j_enq - j_polled >= 2 || j_enq == m || its + j_enq >= o.maxit);
+          if (!ready(P->ev[j_polled % kRing], may_block)) break;
+          if (P->h_st[j_polled % kRing].done) cycle_stop = true;
+          ++j_polled;
+          moved = true;
+        }
+        if (phase == kDone) return true;
+        if (cycle_stop || j_enq == m || its + j_enq >= o.maxit) {
+          end_cycle();
+          moved = true;
+        }
+        return moved;
+      }
+      case kCycleWait: {
+        if (!ready(P->ev[kPhaseSlot], block)) return false;
+        const DevState& h = P->h_st[kPhaseSlot];
+        ++restarts;
+        its += h.k;
+        const double prev = beta;
+        beta = h.beta;
+        est = h.est;
+        if (h.err & kErrNonfinite) {
+          status = BO_ERR_BREAKDOWN;
+          finish();
+        } else if (h.k == 0 || beta <= target || its >= o.maxit) {
+          finish();
+        } else if (h.k == o.restart && beta > 0.99 * prev) {
+          finish();  // a full cycle gained under 1%: stagnation, report NOT_CONVERGED
+        } else {
+          start_cycle();
+        }
+        return true;
+      }
+      case kFinalWait:
+        if (!ready(P->ev[kPhaseSlot], block)) return false;
+        done();
+        return true;
+      case kDone:
+        return false;
+    }
+    return false;
+  }
+};
+
+}  // namespace
+
+int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
+  int rc = krylov_alloc(P, o->restart);
+  if (rc != BO_OK) return rc;
   if (o->profile && !P->prof_ready) {
     for (int i = 0; i < 2 * 512; ++i) cudaEventCreate(&P->prof_ev[i]);
     P->prof_ready = true;
   }
-  if (!std::isfinite(bnorm) || !std::isfinite(beta)) {
-    status = BO_ERR_NONFINITE;
-  } else if (bnorm == 0.0) {
-    cudaMemsetAsync(P->xi, 0, n * sizeof(double), s);
-    beta = 0.0;
-  } else {
-    const double target = o->tol * bnorm;
-    const int64_t ldv = n;
-    const int gn = grid_for(n);
-    const int gu = occ_grid((const void*)k_gs_update<true>, n);
-    while (beta > target && its < o->maxit) {
-      (k_cycle_start<<<1, 64, 0, s>>>(st, P->gvec, m), note_launch());
-      (k_scale_beta<<<gn, kThreads, 0, s>>>(n, P->rk, P->V, st), note_launch());
-      for (int j = 0; j < m && its + j < o->maxit; ++j) {
-        double* vj = P->V + (size_t)j * ldv;
-        double* w = P->V + (size_t)(j + 1) * ldv;
-        double* zj = P->Z + (size_t)j * n;
-        launch_cpr(P, vj, zj, BO_STAGE_CPR, st, &st->vscale[j]);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (o->profile && prof.size() < 512) {
-          e0 = P->prof_ev[2 * prof.size()];
-          e1 = P->prof_ev[2 * prof.size() + 1];
-          cudaEventRecord(e0, s);
-        }
-        (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(g, M->A, zj, w, st),
-         note_launch());
-        if (e1) {
-          cudaEventRecord(e1, s);
-          prof.push_back({e0, e1});
-        }
-        const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j};
-        const dim3 gd(gs_chunks(n), j + 1);
-        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, 0), note_launch());
-        (k_gs_update<false><<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, aa), note_launch());
-        (k_gs_dots<<<gd, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
-        (k_gs_update<true><<<gu, kThreads, 0, s>>>(n, P->V, ldv, w, P->partials, st, aa), note_launch());
-        cudaMemcpyAsync(&P->h_st[j & 1], st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(P->ev[j & 1], s);
-        if (j >= 1) {
-          if (cudaEventSynchronize(P->ev[(j - 1) & 1]) != cudaSuccess) return BO_ERR_CUDA;
-          if (P->h_st[(j - 1) & 1].done) break;
-        }
-      }
-      (k_trisolve<<<1, 32, 0, s>>>(st, P->H, P->gvec, P->y, m), note_launch());
-      (k_xupdate<<<gn, kThreads, 0, s>>>(n, P->xi, P->Z, n, P->y, st), note_launch());
-      (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, M->A, P->bi, P->xi, P->rk, P->partials, st), note_launch());
-      cudaMemcpyAsync(P->h_st, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-      if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
-      const DevState& h = P->h_st[0];
-      ++restarts;
-      its += h.k;
-      beta = h.beta;
-      est = h.est;
-      if (h.err & kErrNonfinite) { status = BO_ERR_BREAKDOWN; break; }
-      if (h.k == 0) break;
-    }
-    if (status == BO_OK && beta > target) status = BO_ERR_NOT_CONVERGED;
-    const int nh = its < kHistCap ? its : kHistCap;
-    if (nh > 0) cudaMemcpy(P->hist, dhist, nh * sizeof(double), cudaMemcpyDeviceToHost);
-    for (int i = 0; i < nh; ++i) P->hist[i] /= bnorm;
-    P->nhist = nh;
+  Job job;
+  job.P = P;
+  job.b_in = b_in;
+  job.x_in = x_in;
+  job.o = *o;
+  job.info = info;
+  job.profile = o->profile != 0;
+  while (job.phase != Job::kDone) job.advance(true);
+  if (job.status == BO_ERR_CUDA && info) info->status = BO_ERR_CUDA;
+  return job.status;
+}
+
+int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
+                   bo_solve_info* infos) {
+  for (int r = 0; r < nreal; ++r) {
+    const int rc = krylov_alloc(P[r], o->restart);
+    if (rc != BO_OK) return rc;
   }
-  // result back in natural order
-  launch_scatter(g, P->xi, x_d, s);
-  if (o->mem == BO_MEM_HOST) cudaMemcpyAsync(x_in, x_d, n * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
-  if (info) {
-    info->status = status;
-    info->iters = its;
-    info->restarts = restarts;
-    info->true_rel_res = bnorm > 0 ? beta / bnorm : beta;
-    info->est_rel_res = bnorm > 0 ? est / bnorm : est;
-    info->spmv_launches = 0;
-    info->spmv_ms = 0.0;
-    for (size_t i = 0; i < prof.size(); ++i) {
-      if ((int)i < its) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, prof[i].first, prof[i].second);
-        info->spmv_ms += ms;
-        info->spmv_launches++;
-      }
-    }
-    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  std::vector<Job> jobs(nreal);
+  for (int r = 0; r < nreal; ++r) {
+    jobs[r].P = P[r];
+    jobs[r].b_in = b[r];
+    jobs[r].x_in = x[r];
+    jobs[r].o = *o;
+    jobs[r].info = infos ? &infos[r] : nullptr;
   }
+  int remaining = nreal;
+  while (remaining > 0) {
+    bool moved = false;
+    remaining = 0;
+    for (auto& jb : jobs) {
+      if (jb.phase == Job::kDone) continue;
+      moved |= jb.advance(false);
+      if (jb.phase != Job::kDone) ++remaining;
+    }
+    if (!moved && remaining > 0) {  // nothing ready: wait on the first pending job
+      for (auto& jb : jobs)
+        if (jb.phase != Job::kDone) {
+          jb.advance(true);
+          break;
+        }
+    }
+  }
+  int status = BO_OK;
+  for (auto& jb : jobs)
+    if (jb.status != BO_OK && status == BO_OK) status = jb.status;
   return status;
 }
 

@@ -66,16 +66,17 @@ __device__ bool inv3(const T a[9], T out[9]) {
 }
 
 // decoupled block (colour, slot) of the cell at half index q: row 0 becomes
-// row0 - w_w row1 - w_g row2 (paper Sec. 3.2, D_QI^{-1} A), FP64
+// g0 row0 + g1 row1 + g2 row2 with the cell's weights (paper Sec. 3.2,
+// D_QI^{-1} A), FP64
 __device__ __forceinline__ void dec_block(const Geom& g, const double* __restrict__ A, const double* __restrict__ w,
                                           int color, int slot, int64_t q, double b[9]) {
-  const double ww = w[vidx(g, 0, color, q)], wg = w[vidx(g, 1, color, q)];
+  const double g0 = w[vidx(g, 0, color, q)], g1 = w[vidx(g, 1, color, q)], g2 = w[vidx(g, 2, color, q)];
   double a[9];
 #pragma unroll
   for (int rc = 0; rc < 9; ++rc) a[rc] = A[plane(g, color, slot, rc) + q];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    b[c] = a[c] - ww * a[3 + c] - wg * a[6 + c];
+    b[c] = g0 * a[c] + g1 * a[3 + c] + g2 * a[6 + c];
     b[3 + c] = a[3 + c];
     b[6 + c] = a[6 + c];
   }
@@ -90,88 +91,113 @@ __device__ __forceinline__ void mul3(const T a[9], const T b[9], T c[9]) {
 }
 
 // ---------------------------------------------------------------- setup kernels
-// Quasi-IMPES decoupling: weights and decoupled planes in precision T
+// Quasi-IMPES decoupling (paper Sec. 3.2): row 0 of each cell becomes
+// g . (row0, row1, row2) with g = (1, -a01/a11, -a02/a22) from the cell's
+// diagonal block.  Where that pressure pivot is not positive (injector cells
+// flooded to residual oil: the oil row carries no pressure information and
+// the water pivot is negative), the cell takes the exact local decoupling,
+// g = row 0 of A_ii^{-1} (pivot 1), which keeps the AMG operator's diagonal
+// positive for the Gauss-Seidel smoother.  Writes the weights [3][N] and the
+// decoupled planes in precision T.
 template <typename T>
 __global__ void k_decouple(Geom g, const double* __restrict__ A, T* __restrict__ At, double* __restrict__ w,
                            DevState* st) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
     const int64_t q = t - color * g.Nh;
-    const double a11 = A[plane(g, color, kDiag, 4) + q], a22 = A[plane(g, color, kDiag, 8) + q];
-    double ww = 0.0, wg = 0.0;
-    if (a11 == 0.0 || a22 == 0.0 || !isfinite(a11) || !isfinite(a22)) {
+    double D[9];
+#pragma unroll
+    for (int rc = 0; rc < 9; ++rc) D[rc] = A[plane(g, color, kDiag, rc) + q];
+    double g0 = 1.0, g1 = 0.0, g2 = 0.0;
+    if (D[4] == 0.0 || D[8] == 0.0 || !isfinite(D[4]) || !isfinite(D[8])) {
       atomicOr(&st->err, kErrBreakdown);
     } else {
-      ww = A[plane(g, color, kDiag, 1) + q] / a11;
-      wg = A[plane(g, color, kDiag, 2) + q] / a22;
+      g1 = -D[1] / D[4];
+      g2 = -D[2] / D[8];
+      if (!(g0 * D[0] + g1 * D[3] + g2 * D[6] > 0.0)) {
+        double inv[9];
+        if (inv3(D, inv)) {
+          g0 = inv[0];
+          g1 = inv[1];
+          g2 = inv[2];
+        } else {
+          atomicOr(&st->err, kErrBreakdown);
+        }
+      }
     }
-    w[vidx(g, 0, color, q)] = ww;
-    w[vidx(g, 1, color, q)] = wg;
+    w[vidx(g, 0, color, q)] = g0;
+    w[vidx(g, 1, color, q)] = g1;
+    w[vidx(g, 2, color, q)] = g2;
     for (int s = 0; s < 7; ++s) {
       double a[9];
 #pragma unroll
       for (int rc = 0; rc < 9; ++rc) a[rc] = A[plane(g, color, s, rc) + q];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        At[plane(g, color, s, c) + q] = (T)(a[c] - ww * a[3 + c] - wg * a[6 + c]);
+        At[plane(g, color, s, c) + q] = (T)(g0 * a[c] + g1 * a[3 + c] + g2 * a[6 + c]);
         At[plane(g, color, s, 3 + c) + q] = (T)a[3 + c];
         At[plane(g, color, s, 6 + c) + q] = (T)a[6 + c];
       }
       if (s == kDiag) {
-        const double app = a[0] - ww * a[3] - wg * a[6];
+        const double app = g0 * a[0] + g1 * a[3] + g2 * a[6];
         if (app == 0.0 || !isfinite(app)) atomicOr(&st->err, kErrBreakdown);
       }
     }
   }
 }
 
-// block (colour, slot) of the decoupled planes at half index q
-template <typename T>
-__device__ __forceinline__ void load_block(const Geom& g, const T* __restrict__ At, int color, int slot, int64_t q,
-                                           T b[9]) {
-#pragma unroll
-  for (int rc = 0; rc < 9; ++rc) b[rc] = At[plane(g, color, slot, rc) + q];
-}
+// Pivots are always factored in FP64 from the FP64 matrix and the
+// Quasi-IMPES weights, whatever precision they are stored in: the black
+// pivots are Schur complements D_b - sum A_br D_r^{-1} A_rb that cancel
+// strongly where the permeability contrast is high, and FP32 arithmetic there
+// can leave the local solver unstable.
 
-// red pivots: D_r^{-1} of the decoupled diagonal blocks, in precision T
+// red pivots: D_r^{-1} of the decoupled diagonal blocks, stored in precision
+// T and, for the black pass, in FP64 in `red64` ([rc][N/2])
 template <typename T>
-__global__ void k_ilu_red(Geom g, const T* __restrict__ At, T* __restrict__ Dinv, DevState* st) {
+__global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w, T* __restrict__ Dinv,
+                          double* __restrict__ red64, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
-    T d[9], inv[9];
-    load_block(g, At, 0, kDiag, q, d);
+    double d[9], inv[9];
+    dec_block(g, A, w, 0, kDiag, q, d);
     if (!inv3(d, inv)) {
       atomicOr(&st->err, kErrBreakdown);
-      for (int rc = 0; rc < 9; ++rc) inv[rc] = T(0);
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
     }
-    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + q] = inv[rc];
+    for (int rc = 0; rc < 9; ++rc) {
+      Dinv[(size_t)rc * g.N + q] = (T)inv[rc];
+      red64[(size_t)rc * g.Nh + q] = inv[rc];
+    }
   }
 }
 
-// black pivots: D_b' = D_b - sum_r A_br D_r^{-1} A_rb, stored inverted
+// black pivots: D_b' = D_b - sum_r A_br D_r^{-1} A_rb with the FP64 red
+// inverses, stored inverted in precision T
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_ilu_black(Geom g, const T* __restrict__ At, T* __restrict__ Dinv, DevState* st) {
+__global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* __restrict__ w,
+                            const double* __restrict__ red64, T* __restrict__ Dinv, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
-    T S[9], inv[9];
-    load_block(g, At, 1, kDiag, q, S);
+    double S[9], inv[9];
+    dec_block(g, A, w, 1, kDiag, q, S);
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       if (s == kDiag) continue;
       const int64_t nq = nbr(g, c, q, s);
       if (nq < 0) continue;
-      T L[9], U[9], Dr[9], T1[9], T2[9];
-      load_block(g, At, 1, s, q, L);
-      load_block(g, At, 0, opposite(s), nq, U);
-      for (int rc = 0; rc < 9; ++rc) Dr[rc] = Dinv[(size_t)rc * g.N + nq];
+      double L[9], U[9], Dr[9], T1[9], T2[9];
+      dec_block(g, A, w, 1, s, q, L);
+      dec_block(g, A, w, 0, opposite(s), nq, U);
+      for (int rc = 0; rc < 9; ++rc) Dr[rc] = red64[(size_t)rc * g.Nh + nq];
       mul3(L, Dr, T1);
       mul3(T1, U, T2);
       for (int rc = 0; rc < 9; ++rc) S[rc] -= T2[rc];
     }
     if (!inv3(S, inv)) {
       atomicOr(&st->err, kErrBreakdown);
-      for (int rc = 0; rc < 9; ++rc) inv[rc] = T(0);
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
     }
-    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = inv[rc];
+    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = (T)inv[rc];
   }
 }
 
@@ -216,14 +242,14 @@ __global__ void k_galerkin0(Geom g, const double* __restrict__ A, const double* 
           if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
           const int color = (i + j + k) & 1;
           const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
-          const double ww = w[vidx(g, 0, color, q)], wg = w[vidx(g, 1, color, q)];
+          const double g0 = w[vidx(g, 0, color, q)], g1 = w[vidx(g, 1, color, q)], g2 = w[vidx(g, 2, color, q)];
           const int ni[7] = {i, i, i - 1, i, i + 1, i, i};
           const int nj[7] = {j, j - 1, j, j, j, j + 1, j};
           const int nk[7] = {k - 1, k, k, k, k, k, k + 1};
           for (int s = 0; s < 7; ++s) {
             if (ni[s] < 0 || ni[s] >= g.nx || nj[s] < 0 || nj[s] >= g.ny || nk[s] < 0 || nk[s] >= g.nz) continue;
-            const double a = A[plane(g, color, s, 0) + q] - ww * A[plane(g, color, s, 3) + q] -
-                             wg * A[plane(g, color, s, 6) + q];
+            const double a = g0 * A[plane(g, color, s, 0) + q] + g1 * A[plane(g, color, s, 3) + q] +
+                             g2 * A[plane(g, color, s, 6) + q];
             const int cs = dir_slot(ni[s] / 2 - ci, nj[s] / 2 - cj, nk[s] / 2 - ck);
             acc[cs] += a;
           }
@@ -288,8 +314,8 @@ __global__ void k_dense_from_level(LevelDims L, const double* __restrict__ c64, 
       if (level0) {
         const int color = (i + j + k) & 1;
         const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
-        a = A[plane(g, color, s, 0) + q] - w[vidx(g, 0, color, q)] * A[plane(g, color, s, 3) + q] -
-            w[vidx(g, 1, color, q)] * A[plane(g, color, s, 6) + q];
+        a = w[vidx(g, 0, color, q)] * A[plane(g, color, s, 0) + q] + w[vidx(g, 1, color, q)] * A[plane(g, color, s, 3) + q] +
+            w[vidx(g, 2, color, q)] * A[plane(g, color, s, 6) + q];
         const int ncol = (ni[s] + nj[s] + nk[s]) & 1;
         colidx = ncol * g.Nh + ((ni[s] + (int64_t)g.nx * (nj[s] + (int64_t)g.ny * nk[s])) >> 1);
       } else {
@@ -381,7 +407,7 @@ __global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* 
   const double sc = vs ? *vs : 1.0;  // scale of an unnormalised Krylov vector
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const double v0 = sc * v[t], v1 = sc * v[g.N + t], v2 = sc * v[2 * g.N + t];
-    const T f0 = DEC ? (T)(v0 - w[t] * v1 - w[g.N + t] * v2) : (T)v0;
+    const T f0 = DEC ? (T)(w[t] * v0 + w[g.N + t] * v1 + w[2 * g.N + t] * v2) : (T)v0;
     const T f1 = (T)v1, f2 = (T)v2;
     f[t] = f0;
     f[g.N + t] = f1;
@@ -871,7 +897,7 @@ LevelDims dims_of(const Level& L) { return LevelDims{L.nx, L.ny, L.nz, L.n}; }
 
 template <typename T>
 void amg_vcycle(bo_prec* P, const DevState* st) {
-  cudaStream_t s = P->mat->ctx->stream;
+  cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   const T* At = (const T*)P->At;
   T* f0 = (T*)P->f0;
@@ -937,7 +963,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
 // z = CPR stage applied to v (FP64, internal order); result FP64 in zo
 template <typename T>
 void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevState* st, const double* vs) {
-  cudaStream_t s = P->mat->ctx->stream;
+  cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
   const T* At = (const T*)P->At;
@@ -993,12 +1019,14 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
 template <typename T>
 int values_impl(bo_prec* P) {
   bo_mat* m = P->mat;
-  cudaStream_t s = m->ctx->stream;
+  cudaStream_t s = P->stream;
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
   (k_decouple<T><<<gN, kThreads, 0, s>>>(g, m->A, (T*)P->At, P->w, P->st), note_launch());
-  (k_ilu_red<T><<<gh, kThreads, 0, s>>>(g, (const T*)P->At, (T*)P->Dinv, P->st), note_launch());
-  (k_ilu_black<T><<<gh, kThreads, 0, s>>>(g, (const T*)P->At, (T*)P->Dinv, P->st), note_launch());
+  // FP64 red inverses for the black pass: the Krylov basis is idle during setup
+  double* red64 = P->V;
+  (k_ilu_red<T><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (T*)P->Dinv, red64, P->st), note_launch());
+  (k_ilu_black<T><<<gh, kThreads, 0, s>>>(g, m->A, P->w, red64, (T*)P->Dinv, P->st), note_launch());
   // AMG hierarchy values
   for (int l = 1; l < P->nlev; ++l) {
     Level& C = P->lev[l];
@@ -1032,7 +1060,7 @@ int prec_alloc(bo_prec* P) {
     return p;
   };
   P->At = al((size_t)63 * g.N * ts);
-  P->w = (double*)al((size_t)2 * g.N * sizeof(double));
+  P->w = (double*)al((size_t)3 * g.N * sizeof(double));
   P->Dinv = al((size_t)9 * g.N * ts);
   P->f = al((size_t)3 * g.N * ts);
   P->t = al((size_t)3 * g.N * ts);
@@ -1066,7 +1094,7 @@ int prec_alloc(bo_prec* P) {
   P->coarse64 = (double*)al((size_t)n * n * sizeof(double));
   P->coarse_inv = al((size_t)n * n * ts);
   if (ok && cudaMalloc(&P->st, sizeof(DevState)) != cudaSuccess) ok = false;
-  if (ok) cudaMemsetAsync(P->st, 0, sizeof(DevState), P->mat->ctx->stream);
+  if (ok) cudaMemsetAsync(P->st, 0, sizeof(DevState), P->stream);
   return ok ? BO_OK : BO_ERR_OOM;
 }
 
@@ -1089,7 +1117,7 @@ void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevStat
 
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {
   const Geom& g = P->mat->g;
-  (k_spmv_dec64<<<grid_for(g.N), kThreads, 0, P->mat->ctx->stream>>>(g, P->mat->A, P->w, x, y), note_launch());
+  (k_spmv_dec64<<<grid_for(g.N), kThreads, 0, P->stream>>>(g, P->mat->A, P->w, x, y), note_launch());
 }
 
 }  // namespace bo

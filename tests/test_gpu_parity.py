@@ -360,3 +360,26 @@ def test_solve_waterflood_1m_cells(bo, ctx, precision):
     xs = np.random.default_rng(12).standard_normal(Ao.n)
     y = A.spmv(_dev(xs), torch.zeros_like(b)).cpu().numpy()
     assert np.all(np.abs(y - oracle.spmv(Ao, xs)) <= 1e-13 * _absprod(Ao, xs))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_flooded_injector_decoupling_matches_oracle(bo, ctx, precision):
+    # injector cells swept to residual oil take the exact local decoupling
+    # (Quasi-IMPES would give them a negative pressure pivot)
+    dims = (12, 12, 4)
+    case = bogen.waterflood_case(*dims, seed=3, day=0, corr=(2, 2, 1), front0=4.0)
+    a, Ao, A, P = _cpr_pair(bo, ctx, case, dims, precision=precision)
+    At, g = oracle.qi_decouple(Ao)
+    assert np.any(g[:, 0] != 1.0)
+    x = np.random.default_rng(14).standard_normal(Ao.n)
+    y = P.spmv_decoupled(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(At, x)) <= 1e-12 * _absprod(At, x) + 1e-300)
+    tol = 1e-9 if precision == 0 else 1e-4
+    for st, ost in [(bo.BO_STAGE_CPR, oracle.STAGE_CPR), (bo.BO_STAGE_AMG, oracle.STAGE_AMG)]:
+        Po = oracle.cpr_prec(Ao, dims, amg=_oracle_amg(), stage=ost)
+        z = P.apply(st, _dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+        ref = Po.apply(x)
+        assert np.linalg.norm(z - ref) <= tol * np.linalg.norm(ref)
+    xs = torch.zeros(Ao.n, dtype=torch.float64, device="cuda")
+    info = P.solve(_dev(a["b"]), xs, tol=1e-8)
+    assert info["status"] == 0 and oracle.rel_residual(Ao, a["b"], xs.cpu().numpy()) <= 1e-8

@@ -55,8 +55,34 @@ def test_qi_operator_multiplied_back_gives_A():
         blk = Ad[3 * i:3 * i + 3, 3 * i:3 * i + 3]
         D[3 * i, 3 * i + 1] = blk[0, 1] / blk[1, 1]
         D[3 * i, 3 * i + 2] = blk[0, 2] / blk[2, 2]
+        # the tiny case's pressure pivots stay positive: pure Quasi-IMPES
+        assert blk[0, 0] - D[3 * i, 3 * i + 1] * blk[1, 0] - D[3 * i, 3 * i + 2] * blk[2, 0] > 0
     assert np.allclose(D @ At.to_dense(), Ad, rtol=1e-13, atol=1e-10 * np.abs(Ad).max())
-    assert np.allclose(w[:, 0], np.diag(D, 1)[0::3])
+    assert np.allclose(w[:, 0], 1.0) and np.allclose(-w[:, 1], np.diag(D, 1)[0::3])
+
+
+def test_flooded_injector_cells_take_exact_local_decoupling():
+    # an injector cell swept to residual oil (So = s_orw): the oil row barely
+    # depends on pressure and the water pivot turns negative, so Quasi-IMPES
+    # would give a negative pressure pivot; there the decoupled row is row 0
+    # of A_ii^{-1} A, whose diagonal block row is exactly e_0
+    case = bogen.waterflood_case(12, 12, 4, seed=3, day=0, corr=(2, 2, 1), front0=4.0)
+    a = bogen.assemble(case)
+    A = BsrMatrix(a["rowptr"], a["col"], a["val"])
+    At, g = oracle.qi_decouple(A)
+    n_fallback = 0
+    for i in range(A.nb):
+        e = [e for e in range(A.rowptr[i], A.rowptr[i + 1]) if A.col[e] == i][0]
+        blk = A.val[e]
+        qi = blk[0, 0] - blk[0, 1] / blk[1, 1] * blk[1, 0] - blk[0, 2] / blk[2, 2] * blk[2, 0]
+        if qi > 0:
+            assert np.allclose(g[i], [1.0, -blk[0, 1] / blk[1, 1], -blk[0, 2] / blk[2, 2]])
+        else:
+            n_fallback += 1
+            assert np.allclose(g[i], np.linalg.inv(blk)[0], rtol=1e-12)
+            assert np.allclose(At.val[e][0], [1.0, 0.0, 0.0], atol=1e-12)
+        assert At.val[e][0, 0] > 0
+    assert n_fallback > 0
 
 
 def test_qi_removes_local_saturation_coupling_of_pressure_row():
@@ -349,7 +375,7 @@ def test_cpr_stages_compose_as_alg2():
     assert np.allclose(Cp.apply(f), x3, rtol=1e-12, atol=1e-14)
     # the full form decouples its input first: z = CPR(D_QI^{-1} v)
     fd = f.copy()
-    fd[0::3] = f[0::3] - w[:, 0] * f[1::3] - w[:, 1] * f[2::3]
+    fd[0::3] = w[:, 0] * f[0::3] + w[:, 1] * f[1::3] + w[:, 2] * f[2::3]
     assert np.allclose(Full.apply(f), Cp.apply(fd), rtol=1e-12, atol=1e-14)
 
 
