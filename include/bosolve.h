@@ -196,6 +196,81 @@ int64_t bo_kernel_launches(void);
  * Ordered on the context's stream; does not synchronise. */
 int bo_mat_residual_noalloc(bo_mat* A, const double* b, const double* x, double* r, double* norms);
 
+/* ---------------------------------------------------------------------------
+ * Learned Newton update.  No counterpart in the paper: an addition of this
+ * library that feeds the Krylov solve of Sec. 3 a predicted initial guess
+ * and a predicted coarse space; the architecture is this library's choice.
+ *
+ * A 3D convolutional network on the reservoir grid: an input convolution
+ * (16 -> 32 channels, ReLU), 6 residual blocks of two 32 -> 32 convolutions
+ * (ReLU; the second adds the block input before its ReLU) and an output
+ * convolution (32 -> 16, linear).  Every convolution is 3x3x3 with 'same'
+ * zero padding.  Output channel 0 is the predicted Newton pressure update dp
+ * of each cell, channels 1..2 optionally (dSw, dSg), in the caller's
+ * normalisation.
+ *
+ * Layouts (all device memory owned by the caller unless noted):
+ *   activations / inputs: BF16 bit patterns (uint16), NDHWC:
+ *     [batch][nz][ny][nx][C], voxel v = x + nx (y + ny z) (the solver's cell
+ *     index); the network input has C = 16 (features zero-padded);
+ *   weights: BF16 [27][Cout][Cin], tap t = 9 (dz+1) + 3 (dy+1) + (dx+1)
+ *     (cross-correlation: output v reads input v + (dx, dy, dz));
+ *   biases, gradients of activations, predictions: FP32;
+ *   predictions / targets: FP32 [batch][V][4] (channel 3 unused).
+ * Arithmetic: BF16 x BF16 products with FP32 accumulation on the tensor
+ * cores; hidden activations are stored in BF16; the loss is accumulated in
+ * FP64.  Every call is ordered on the context's stream.
+ * ------------------------------------------------------------------------- */
+typedef struct bo_cnn bo_cnn;
+
+/* Network for grids of nx x ny x nz voxels and up to max_batch samples;
+ * weights He-normal from `seed` (the second convolution of each block and the
+ * output convolution scaled by 0.1), biases zero.  Holds a reference on ctx.
+ * BO_ERR_ARG if max_batch nx ny nz > 2^31.  Synchronises. */
+int bo_cnn_create(bo_ctx* ctx, int nx, int ny, int nz, int max_batch, uint64_t seed, bo_cnn** out);
+int bo_cnn_destroy(bo_cnn* net);
+/* Number of FP32 parameters: per layer 27 Cout Cin weights then Cout biases. */
+int64_t bo_cnn_param_count(const bo_cnn* net);
+/* Copy the FP32 master parameters (or the gradients of the last backward
+ * pass) to / from HOST memory of at least bo_cnn_param_count floats;
+ * set_params also refreshes the BF16 copy.  Synchronise. */
+int bo_cnn_get_params(bo_cnn* net, float* host, int64_t cap);
+int bo_cnn_set_params(bo_cnn* net, const float* host, int64_t count);
+int bo_cnn_get_grads(bo_cnn* net, float* host, int64_t cap);
+/* pred[batch][V][4] = network(x); x: [batch][V][16] BF16. */
+int bo_cnn_forward(bo_cnn* net, const uint16_t* x, int batch, float* pred);
+/* Forward pass, loss = (1 / (batch V)) sum_v mask_v sum_{k < nout}
+ * (pred[v][k] - target[v][k])^2 (mask NULL: all ones; 1 <= nout <= 4) and
+ * the backward pass into the network's gradient buffer.  *loss (host, may be
+ * NULL) receives the loss; a non-NULL loss synchronises. */
+int bo_cnn_backward(bo_cnn* net, const uint16_t* x, const float* target, const float* mask, int nout, int batch,
+                    double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * FP32 master weights with the last gradients; refreshes the BF16 copy. */
+int bo_cnn_adam_step(bo_cnn* net, float lr);
+
+/* Single convolutions (the network's layers; also what the parity tests
+ * check).  Supported (cin, cout): forward (16, 32), (32, 32), (32, 16) as
+ * used by the network; modes by the non-NULL outputs:
+ *   y only, relu = 1           : y = ReLU(conv(x) + bias (+ residual)) BF16;
+ *   y and yf, relu = 0         : y = conv(x) + bias in BF16 and yf[v][0..3] =
+ *                                channels 0..3 in FP32 (cout = 16 only);
+ *   yf only, relu = 0          : yf[v][co] = conv(x) + bias in FP32.
+ * backward_data: dx[v][ci] = sum_t,co dy[v - off(t)][co] w[t][co][ci] (FP32),
+ *   dy BF16 [batch][V][cout];
+ * backward_weights: dw[t][co][ci] = sum_v dy[v][co] x[v + off(t)][ci] and
+ *   db[co] = sum_v dy[v][co] (FP32); dy FP32 [batch][V][cout] is rounded to
+ *   BF16 for the products.
+ * backward_data and backward_weights allocate and free scratch and
+ * synchronise.  BO_ERR_ARG on an unsupported (cin, cout) or mode. */
+int bo_conv3d_forward(bo_ctx* ctx, int nx, int ny, int nz, int batch, int cin, int cout, const uint16_t* x,
+                      const uint16_t* w, const float* bias, const uint16_t* residual, int relu, uint16_t* y,
+                      float* yf);
+int bo_conv3d_backward_data(bo_ctx* ctx, int nx, int ny, int nz, int batch, int cin, int cout, const uint16_t* dy,
+                            const uint16_t* w, float* dx);
+int bo_conv3d_backward_weights(bo_ctx* ctx, int nx, int ny, int nz, int batch, int cin, int cout, const uint16_t* x,
+                               const float* dy, float* dw, float* db);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,9 @@ EXPORTS = (
     "bo_prec_destroy", "bo_solve", "bo_solve_batched", "bo_prec_residual_history", "bo_newton_update",
     "bo_kernel_launches",
     "bo_mat_residual_noalloc",
+    "bo_cnn_create", "bo_cnn_destroy", "bo_cnn_param_count", "bo_cnn_get_params", "bo_cnn_set_params",
+    "bo_cnn_get_grads", "bo_cnn_forward", "bo_cnn_backward", "bo_cnn_adam_step",
+    "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
 )
 
 
@@ -121,6 +124,19 @@ def lib():
         L.bo_kernel_launches.argtypes = []
         L.bo_prec_opts_default.argtypes = [ctypes.POINTER(bo_prec_opts)]
         L.bo_solve_opts_default.argtypes = [ctypes.POINTER(bo_solve_opts)]
+        _i = ctypes.c_int
+        L.bo_cnn_create.argtypes = [_VP, _i, _i, _i, _i, ctypes.c_uint64, ctypes.POINTER(_VP)]
+        L.bo_cnn_destroy.argtypes = [_VP]
+        L.bo_cnn_param_count.restype = ctypes.c_int64
+        L.bo_cnn_param_count.argtypes = [_VP]
+        for f in (L.bo_cnn_get_params, L.bo_cnn_set_params, L.bo_cnn_get_grads):
+            f.argtypes = [_VP, _VP, ctypes.c_int64]
+        L.bo_cnn_forward.argtypes = [_VP, _VP, _i, _VP]
+        L.bo_cnn_backward.argtypes = [_VP, _VP, _VP, _VP, _i, _i, ctypes.POINTER(ctypes.c_double)]
+        L.bo_cnn_adam_step.argtypes = [_VP, ctypes.c_float]
+        L.bo_conv3d_forward.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP, _VP, _i, _VP, _VP]
+        L.bo_conv3d_backward_data.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP]
+        L.bo_conv3d_backward_weights.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP, _VP]
         _lib = L
     return _lib
 
@@ -362,3 +378,113 @@ def bo_newton_update(ctx: Context, state, dx):
     """state += dx on the device (paper Alg. 1 update)."""
     _check(lib().bo_newton_update(ctx.h, _VP(state.data_ptr()), _VP(dx.data_ptr()), state.numel()),
            "bo_newton_update")
+
+
+# ---------------------------------------------------------------- learned update
+def _dev(t, dtype_name, what):
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    if t is None:
+        return None
+    if not hasattr(t, "data_ptr") or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError(f"{what} must be {dtype_name}")
+    return _VP(t.data_ptr())
+
+
+def _bits(t):
+    """BF16 tensor -> the same storage as int16 bit patterns (no copy)."""
+    import torch
+    return t.view(torch.int16) if t.dtype == torch.bfloat16 else t
+
+
+class CNN:
+    """bo_cnn: the 3D convolutional network of the learned Newton update
+    (16 input channels, 32 hidden, 6 residual blocks; prediction [B, V, 4]
+    FP32).  Inputs are torch.bfloat16 [B, nz, ny, nx, 16] (or flat)."""
+
+    def __init__(self, ctx: Context, nx, ny, nz, max_batch=1, seed=0):
+        h = _VP()
+        _check(lib().bo_cnn_create(ctx.h, nx, ny, nz, max_batch, seed, ctypes.byref(h)), "bo_cnn_create")
+        self.h, self.ctx = h, ctx
+        self.dims = (nx, ny, nz)
+        self.V = nx * ny * nz
+        self.max_batch = max_batch
+
+    @property
+    def nparam(self) -> int:
+        return int(lib().bo_cnn_param_count(self.h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparam, np.float32)
+        _check(lib().bo_cnn_get_params(self.h, _VP(out.ctypes.data), out.size), "bo_cnn_get_params")
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().bo_cnn_set_params(self.h, _VP(p.ctypes.data), p.size), "bo_cnn_set_params")
+
+    def get_grads(self) -> np.ndarray:
+        out = np.zeros(self.nparam, np.float32)
+        _check(lib().bo_cnn_get_grads(self.h, _VP(out.ctypes.data), out.size), "bo_cnn_get_grads")
+        return out
+
+    def forward(self, x, pred):
+        B = x.shape[0]
+        _check(lib().bo_cnn_forward(self.h, _dev(_bits(x), "int16", "x"), B, _dev(pred, "float32", "pred")),
+               "bo_cnn_forward")
+        return pred
+
+    def backward(self, x, target, mask=None, nout=1, want_loss=True):
+        B = x.shape[0]
+        loss = ctypes.c_double(0.0)
+        _check(lib().bo_cnn_backward(self.h, _dev(_bits(x), "int16", "x"), _dev(target, "float32", "target"),
+                                     _dev(mask, "float32", "mask"), nout, B,
+                                     ctypes.byref(loss) if want_loss else None), "bo_cnn_backward")
+        return loss.value if want_loss else None
+
+    def adam_step(self, lr):
+        _check(lib().bo_cnn_adam_step(self.h, ctypes.c_float(lr)), "bo_cnn_adam_step")
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_cnn_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bo_conv3d_forward(ctx: Context, dims, x, w, bias, residual=None, relu=False, y=None, yf=None):
+    """One 3x3x3 convolution (see bo_conv3d_forward in include/bosolve.h).
+    dims = (nx, ny, nz); x [B, V, cin] bf16, w [27, cout, cin] bf16, bias
+    [cout] f32; y [B, V, cout] bf16 and/or yf f32."""
+    nx, ny, nz = dims
+    B = x.shape[0]
+    cin, cout = w.shape[2], w.shape[1]
+    _check(lib().bo_conv3d_forward(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(x), "int16", "x"),
+                                   _dev(_bits(w), "int16", "w"), _dev(bias, "float32", "bias"),
+                                   _dev(_bits(residual), "int16", "residual") if residual is not None else None,
+                                   int(relu), _dev(_bits(y), "int16", "y") if y is not None else None,
+                                   _dev(yf, "float32", "yf")), "bo_conv3d_forward")
+
+
+def bo_conv3d_backward_data(ctx: Context, dims, dy, w, dx):
+    nx, ny, nz = dims
+    B = dy.shape[0]
+    cin, cout = w.shape[2], w.shape[1]
+    _check(lib().bo_conv3d_backward_data(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(dy), "int16", "dy"),
+                                         _dev(_bits(w), "int16", "w"), _dev(dx, "float32", "dx")),
+           "bo_conv3d_backward_data")
+
+
+def bo_conv3d_backward_weights(ctx: Context, dims, x, dy, dw, db):
+    nx, ny, nz = dims
+    B = x.shape[0]
+    cout, cin = dw.shape[1], dw.shape[2]
+    _check(lib().bo_conv3d_backward_weights(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(x), "int16", "x"),
+                                            _dev(dy, "float32", "dy"), _dev(dw, "float32", "dw"),
+                                            _dev(db, "float32", "db")), "bo_conv3d_backward_weights")
