@@ -152,6 +152,28 @@ int bo_prec_spmv_decoupled(bo_prec* P, const double* x, double* y);
  * count (or a negative status). */
 int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap);
 int bo_prec_destroy(bo_prec* P);
+/* Learned coarse space (no counterpart in the paper; an addition to the
+ * CPR preconditioner of Sec. 3.3, Alg. 2).  dp: device array of nx ny nz
+ * doubles in natural cell order, a predicted pressure update; the grid is
+ * cut into tiles of tx x ty x tz cells (partial tiles at the far faces) and
+ * Z holds dp restricted to each tile as one column.  E = Z^T A~_pp Z, with
+ * A~_pp the quasi-IMPES-decoupled pressure block, is formed and inverted in
+ * FP64 now and again on every bo_prec_update; after each AMG V-cycle on a
+ * pressure residual f the pressure correction gains Z E^{-1} Z^T f (also in
+ * the BO_STAGE_AMG stage of bo_prec_apply).  dp is copied; NULL removes the
+ * space.  BO_ERR_ARG if a tile size is < 1 or there are more than 128
+ * tiles; BO_ERR_BREAKDOWN if E is singular (the space is then removed).
+ * Synchronises. */
+int bo_prec_set_coarse_space(bo_prec* P, const double* dp, int tx, int ty, int tz);
+/* Learned initial guess (no counterpart in the paper): x0[3c + k] =
+ * scale[k] pred[c][k] for k < ncomp (1..3), 0 for the other components,
+ * from a network prediction pred [nx ny nz][4] FP32 (device); natural
+ * order.  Falls back to x0 = 0 (and *used = 0) unless ||b - A x0|| < ||b||,
+ * so the guess never starts a solve further from the solution than the zero
+ * guess does.  b, x0: device, 3 nx ny nz doubles.  Uses P's Krylov
+ * workspace: not while a solve with P is in flight.  Synchronises. */
+int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const double* scale, int ncomp, double* x0,
+                     int* used);
 
 /* Solve A x = b with FGMRES(m) + CPR to ||b - A x|| <= tol ||b|| (paper
  * Alg. 1 step "find dx").  b, x: length 3 nx ny nz, device or host memory

@@ -62,6 +62,8 @@ def lib():
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
         L.or_prec_apply.argtypes = [ctypes.c_void_p, _D, _D]
+        L.or_prec_cpr_set_coarse.argtypes = [ctypes.c_void_p, _D] + [ctypes.c_int] * 6
+        L.or_prec_cpr_coarse_apply.argtypes = [ctypes.c_void_p, _D, _D]
         L.or_prec_destroy.argtypes = [ctypes.c_void_p]
         L.or_gmres.argtypes = [ctypes.c_int64, ctypes.c_int, _I32, _I32, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, ctypes.c_void_p, _D]
@@ -286,6 +288,28 @@ def cpr_prec(A: BsrMatrix, dims, ordering=ORDER_RED_BLACK, amg: AmgParams = None
     if st.value != 0:
         raise ArithmeticError("CPR setup breakdown")
     return p
+
+
+def cpr_set_coarse(prec: Prec, zc, dims, tile):
+    """Learned coarse space of a CPR preconditioner (no counterpart in the
+    paper): Z = tile restriction of the pressure field zc (natural order),
+    E = Z^T A~_pp Z; every pressure correction gains Z E^{-1} Z^T f.
+    zc None removes it."""
+    if zc is None:
+        lib().or_prec_cpr_set_coarse(prec.h, None, *dims, *tile)
+        return
+    zc = _d(zc)
+    prec._keep = prec._keep + (zc,)
+    if lib().or_prec_cpr_set_coarse(prec.h, _p(zc, _D), *dims, *tile) != 0:
+        raise ArithmeticError("singular learned coarse matrix")
+
+
+def cpr_coarse_apply(prec: Prec, fp):
+    """The learned coarse correction alone: Z E^{-1} Z^T fp."""
+    fp = _d(fp)
+    ep = np.zeros_like(fp)
+    lib().or_prec_cpr_coarse_apply(prec.h, _p(fp, _D), _p(ep, _D))
+    return ep
 
 
 def gmres(A: BsrMatrix, b, x0=None, m=30, maxit=1000, tol=1e-8, prec: Prec = None):

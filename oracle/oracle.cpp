@@ -427,6 +427,22 @@ struct CprPrec : Prec {
   IluPrec R;
   Amg amg;
   int stage = 0;  // 0 full CPR on D^{-1} v, 1 ILU only, 2 AMG only (Pi_p AMG Pi_r), 3 CPR on f as given
+  // Learned coarse space (no counterpart in the paper): Z has one column
+  // per tile holding the given pressure field zc on that tile's cells;
+  // E = Z^T A~_pp Z with A~_pp the decoupled pressure block.  Every pressure
+  // correction from the V-cycle gains Z E^{-1} Z^T fp.
+  std::vector<double> zc;
+  std::vector<int> tile;
+  int ntiles = 0;
+  DenseLU E;
+
+  void coarse_correct(const double* fp, double* ep) const {
+    if (ntiles == 0) return;
+    std::vector<double> y(ntiles, 0.0), u(ntiles);
+    for (size_t i = 0; i < zc.size(); ++i) y[tile[i]] += zc[i] * fp[i];
+    E.solve(y.data(), u.data());
+    for (size_t i = 0; i < zc.size(); ++i) ep[i] += zc[i] * u[tile[i]];
+  }
 
   void cpr_decoupled(const double* f, double* x) {
     const int64_t n = At.n(), nb = At.nb;
@@ -436,6 +452,7 @@ struct CprPrec : Prec {
     for (int64_t i = 0; i < n; ++i) r[i] = f[i] - Ax[i];
     for (int64_t i = 0; i < nb; ++i) fp[i] = r[3 * i];
     amg.vcycle(0, fp.data(), ep.data());
+    coarse_correct(fp.data(), ep.data());
     for (int64_t i = 0; i < nb; ++i) x[3 * i] += ep[i];
     At.spmv(x, Ax.data());
     for (int64_t i = 0; i < n; ++i) r[i] = f[i] - Ax[i];
@@ -451,6 +468,7 @@ struct CprPrec : Prec {
       std::vector<double> fp(nb), ep(nb);
       for (int64_t i = 0; i < nb; ++i) fp[i] = v[3 * i];
       amg.vcycle(0, fp.data(), ep.data());
+      coarse_correct(fp.data(), ep.data());
       for (int64_t i = 0; i < 3 * nb; ++i) z[i] = 0.0;
       for (int64_t i = 0; i < nb; ++i) z[3 * i] = ep[i];
       return;
@@ -671,6 +689,48 @@ void* or_prec_cpr_create(int64_t nb, const int32_t* rowptr, const int32_t* col, 
   ap.overcorr = overcorr; ap.coarse_max = coarse_max; ap.max_levels = max_levels;
   *status = p->amg.setup(pressure_block(p->At), nx, ny, nz, ap);
   return p;
+}
+
+// Learned coarse space of a CPR preconditioner from or_prec_cpr_create:
+// zc (one value per cell, natural order) restricted to tiles of tx x ty x tz
+// cells; tile t = a + ntx (b + nty c) for the tile at (a, b, c).  A tile
+// where zc vanishes gets E_tt = 1 (its column of Z is zero).  zc = NULL
+// removes the space.  Returns 0, or -5 if E is singular.
+int or_prec_cpr_set_coarse(void* h, const double* zc, int nx, int ny, int nz, int tx, int ty, int tz) {
+  auto* p = static_cast<CprPrec*>(h);
+  p->ntiles = 0;
+  p->zc.clear();
+  p->tile.clear();
+  if (!zc) return kOk;
+  const int ntx = (nx + tx - 1) / tx, nty = (ny + ty - 1) / ty, ntz = (nz + tz - 1) / tz;
+  const int nt = ntx * nty * ntz;
+  const int64_t n = (int64_t)nx * ny * nz;
+  std::vector<int> tile(n);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) tile[i + (int64_t)nx * (j + (int64_t)ny * k)] = i / tx + ntx * (j / ty + nty * (k / tz));
+  // E[s][t] = sum over cells c in s and pressure couplings (c, d) with d in t of zc_c A~_pp[c][d] zc_d
+  const Csr App = pressure_block(p->At);
+  std::vector<double> E((size_t)nt * nt, 0.0), zz(nt, 0.0);
+  for (int64_t c = 0; c < n; ++c) {
+    zz[tile[c]] += zc[c] * zc[c];
+    for (int32_t e = App.rowptr[c]; e < App.rowptr[c + 1]; ++e)
+      E[(size_t)tile[c] * nt + tile[App.col[e]]] += zc[c] * App.val[e] * zc[App.col[e]];
+  }
+  for (int t = 0; t < nt; ++t)
+    if (zz[t] == 0.0) E[(size_t)t * nt + t] = 1.0;
+  if (p->E.factor(nt, E.data()) != kOk) return kBreakdown;
+  p->zc.assign(zc, zc + n);
+  p->tile = tile;
+  p->ntiles = nt;
+  return kOk;
+}
+
+// The coarse correction alone: ep = Z E^{-1} Z^T fp (natural order)
+void or_prec_cpr_coarse_apply(void* h, const double* fp, double* ep) {
+  auto* p = static_cast<CprPrec*>(h);
+  for (size_t i = 0; i < p->zc.size(); ++i) ep[i] = 0.0;
+  p->coarse_correct(fp, ep);
 }
 
 void or_prec_apply(void* h, const double* r, double* z) { static_cast<Prec*>(h)->apply(r, z); }

@@ -48,6 +48,7 @@ EXPORTS = (
     "bo_cnn_create", "bo_cnn_destroy", "bo_cnn_param_count", "bo_cnn_get_params", "bo_cnn_set_params",
     "bo_cnn_get_grads", "bo_cnn_forward", "bo_cnn_backward", "bo_cnn_adam_step",
     "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
+    "bo_prec_set_coarse_space", "bo_learned_guess",
 )
 
 
@@ -137,6 +138,9 @@ def lib():
         L.bo_conv3d_forward.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP, _VP, _i, _VP, _VP]
         L.bo_conv3d_backward_data.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP]
         L.bo_conv3d_backward_weights.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP, _VP]
+        L.bo_prec_set_coarse_space.argtypes = [_VP, _VP, _i, _i, _i]
+        L.bo_learned_guess.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _i, _VP,
+                                       ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -324,6 +328,22 @@ class Preconditioner:
         d = info.as_dict()
         d["status"] = rc
         return d
+
+    def set_coarse_space(self, dp, tile=(16, 16, 8)):
+        """Learned coarse space from a predicted pressure update dp (device
+        float64, one value per cell, natural order); None removes it."""
+        ptr = _dev(dp, "float64", "dp") if dp is not None else None
+        _check(lib().bo_prec_set_coarse_space(self.h, ptr, *[int(t) for t in tile]), "bo_prec_set_coarse_space")
+
+    def learned_guess(self, b, pred, scale, ncomp, x0) -> bool:
+        """x0 from the network prediction pred [V, 4] (scaled per component);
+        falls back to zero unless it lowers the residual.  Returns whether the
+        guess was kept."""
+        sc = (ctypes.c_double * 3)(*[float(v) for v in scale])
+        used = ctypes.c_int(0)
+        _check(lib().bo_learned_guess(self.h, _dev(b, "float64", "b"), _dev(pred, "float32", "pred"), sc, int(ncomp),
+                                      _dev(x0, "float64", "x0"), ctypes.byref(used)), "bo_learned_guess")
+        return bool(used.value)
 
     def residual_history(self, cap=4096):
         buf = (ctypes.c_double * cap)()

@@ -233,6 +233,15 @@ struct bo_prec {
   cudaEvent_t ev[4];
   cudaEvent_t prof_ev[2 * 512];
   bool prof_ready;
+  // learned coarse space (Z = tile restriction of a predicted dp)
+  int lc_nt = 0;           // tiles (columns of Z); 0: off
+  int lc_tile[3] = {0, 0, 0};
+  int lc_ntile[3] = {0, 0, 0};
+  double* lc_z = nullptr;  // dp, colour-split order
+  double* lc_E = nullptr;  // Z^T A~_pp Z, nt x nt
+  double* lc_Einv = nullptr;
+  double* lc_y = nullptr;  // Z^T f
+  double* lc_u = nullptr;  // E^{-1} Z^T f
   double* hist;            // host residual history of the last solve
   int nhist;
   int hist_cap;
@@ -264,5 +273,11 @@ int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* 
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
                    bo_solve_info* infos);
 int krylov_alloc(bo_prec* P, int m);
+// dense FP64 inverse of an n x n matrix (n <= 128) by one block; sets
+// st->err on a zero pivot
+int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, cudaStream_t s);
+int learned_coarse_values(bo_prec* P);
+void learned_coarse_apply(bo_prec* P, const DevState* st);
+void learned_coarse_free(bo_prec* P);
 
 }  // namespace bo

@@ -977,6 +977,7 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
   if (stage == BO_STAGE_AMG) {  // (v is a caller's vector here: vs is NULL)
     (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v, f0, st), note_launch());
     amg_vcycle<T>(P, st);
+    learned_coarse_apply(P, st);
     (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo, st), note_launch());
     return;
   }
@@ -1004,6 +1005,7 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
        g, At, f, z1, nullptr, f0, nullptr, nullptr, st),
    note_launch());
   amg_vcycle<T>(P, st);
+  learned_coarse_apply(P, st);
   // r = f - At x2 (with the red pass of R^{-1} r fused);  x3 = x2 + R^{-1} r
   (k_cpr_residual<T, 3><<<occ_grid((const void*)k_cpr_residual<T, 3>, g.N), kThreads, 0, s>>>(g, At, f, z1, e0, r,
                                                                                                 D, tv, st),
@@ -1045,7 +1047,8 @@ int values_impl(bo_prec* P) {
   const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
   cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   (k_gj_inverse<T><<<1, 1024, smem, s>>>(n, P->coarse64, (T*)P->coarse_inv, P->st), note_launch());
-  return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return BO_ERR_CUDA;
+  return learned_coarse_values(P);
 }
 
 }  // namespace
@@ -1104,10 +1107,19 @@ void prec_free(bo_prec* P) {
   fr(P->f); fr(P->t); fr(P->r); fr(P->z1); fr(P->e0); fr(P->f0);
   for (int l = 1; l < P->nlev; ++l) { fr(P->lev[l].c64); fr(P->lev[l].c); fr(P->lev[l].f); fr(P->lev[l].x); }
   fr(P->coarse64); fr(P->coarse_inv); fr(P->st);
+  learned_coarse_free(P);
 }
 
 int prec_values(bo_prec* P) {
   return P->fp32 ? values_impl<float>(P) : values_impl<double>(P);
+}
+
+int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, cudaStream_t s) {
+  if (n < 1 || n > kCoarseMax) return BO_ERR_ARG;
+  const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
+  cudaFuncSetAttribute(k_gj_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (k_gj_inverse<double><<<1, 1024, smem, s>>>(n, M, Minv, st), note_launch());
+  return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
 void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs) {

@@ -203,3 +203,29 @@ def test_tiny_case_is_seeded_and_nonsingular():
     a3 = bogen.assemble(bogen.tiny_case(1))
     assert not np.array_equal(a1["b"], a3["b"])
     assert np.all(np.isfinite(a1["val"]))
+
+
+def test_learned_case_recipe():
+    from bogen import learned as L
+    c = L.learned_case(3, 32, 32, 16)
+    c2 = L.learned_case(3, 32, 32, 16)
+    assert np.array_equal(c.kx, c2.kx) and np.array_equal(c.x, c2.x)  # seeded
+    inj, prod = c.wells
+    assert inj.kind == 0 and prod.kind == 1 and inj.cells.size == 16 and prod.cells.size == 16
+    ci, cp = int(inj.cells[0]), int(prod.cells[0])
+    assert np.hypot(ci % 32 - cp % 32, ci // 32 - cp // 32) >= 16
+    assert 3500 <= inj.bhp <= 4500 and 1500 <= prod.bhp <= 2500
+    assert np.all((c.x[1::3] >= 0.1 - 1e-12) & (c.x[1::3] <= 0.85 + 1e-12))
+    assert np.allclose(c.kz, 0.1 * c.kx)
+    f = L.features(c)
+    assert f.shape == (c.N, 16) and f.dtype == np.float32 and np.all(f[:, 6:] == 0)
+    # well features only on perforated cells, signed by well type
+    wells = np.zeros(c.N, bool)
+    wells[inj.cells] = wells[prod.cells] = True
+    assert np.all(f[~wells, 4] == 0) and np.all(f[inj.cells, 4] > 0) and np.all(f[prod.cells, 4] < 0)
+    np.testing.assert_allclose(f[inj.cells, 5], (inj.bhp - c.x[0::3][inj.cells]) / 1000.0, rtol=1e-6)
+    dx = np.arange(3 * c.N, dtype=np.float64)
+    t = L.targets(dx)
+    np.testing.assert_allclose(t[:, 0] * L.TARGET_SCALE[0], dx[0::3], rtol=1e-6)
+    np.testing.assert_allclose(t[:, 2] * L.TARGET_SCALE[2], dx[2::3], rtol=1e-6)
+    assert np.all(t[:, 3] == 0)
