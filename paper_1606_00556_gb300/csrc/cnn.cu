@@ -36,7 +36,6 @@ namespace {
 using bf16 = __nv_bfloat16;
 constexpr int kConvThreads = 256;
 constexpr int kVoxPerBlock = 128;   // 8 warps x 16 voxels
-constexpr int kWgChunks = 96;       // voxel chunks of the weight gradient
 constexpr int kOutF32 = 4;          // FP32 prediction channels (dp, then optionally dSw, dSg)
 
 __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
@@ -159,127 +158,156 @@ __global__ void k_flip_transpose(const bf16* __restrict__ W, bf16* __restrict__ 
   }
 }
 
-// channel-major copy: T[b][c][v] = X[b][v][c]
-__global__ void k_to_channel_major(const bf16* __restrict__ X, bf16* __restrict__ T, int V, int C, int B) {
-  const int64_t n = (int64_t)B * V * C;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / ((int64_t)V * C);
-    const int64_t rem = i - b * V * C;
-    const int64_t c = rem / V, v = rem - c * V;
-    T[i] = X[(b * V + v) * C + c];
-  }
+// ldmatrix of four 8x8 b16 blocks, transposed: lanes 8i..8i+7 give the 16-byte
+// rows of block i; register i receives block i in the mma fragment layout
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
 }
 
-// Weight gradient partials: for tap = blockIdx.y and the voxel chunk
-// blockIdx.x, P[chunk][tap][co][ci] = sum_v dY[v][co] X[v + off(tap)][ci]
-// as an mma GEMM with M = co (rows >= COUT are zero), N = ci, K = voxels,
-// from channel-major copies Xt[b][ci][v], Dt[b][co][v].
+// Weight gradient dW[t][co][ci] = sum_v dY[v][co] X[v + off(t)][ci] as a
+// persistent implicit GEMM (M = co, N = ci, K = voxels) over bricks of
+// 8 x 8 x 4 voxels.  Per brick the block stages dY (256 voxels) and X with
+// a one-voxel halo (10 x 10 x 6) in shared memory, rows padded by 16 bytes so
+// that the 8 rows of an ldmatrix fall in distinct banks; ldmatrix.trans
+// turns the voxel-major tiles into the K-major mma fragments, for every tap
+// (the tap only moves the X row addresses).  Warps own (tap, 16-row co tile)
+// units and keep their accumulators in registers across all bricks of the
+// block; at the end each block writes its partial sums
+// part[block][tap][co][ci], summed in a fixed order by k_wgrad_reduce.
+// Voxels of a brick outside the grid have dY = 0, so they add nothing.
+constexpr int kBrickX = 8, kBrickY = 8, kBrickZ = 4, kBrick = 256;
+constexpr int kHaloX = 10, kHaloY = 10, kHalo = 600;
+constexpr int kWgMaxBlocks = 304;
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) k_conv3d_wgrad(int nx, int ny, int nz, int B,
-                                                              const bf16* __restrict__ Xt,
-                                                              const bf16* __restrict__ Dt, float* __restrict__ part) {
-  constexpr int MT = (COUT + 15) / 16;  // m16 tiles over co
-  constexpr int NT = CIN / 8;           // n8 tiles over ci
-  __shared__ float red[COUT][CIN];
+constexpr size_t wgrad_smem() {
+  return (size_t)(kHalo * (CIN + 8) + kBrick * (COUT + 8)) * sizeof(bf16);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_wgrad(int nx, int ny, int nz, int B,
+                                                                 const bf16* __restrict__ X,
+                                                                 const bf16* __restrict__ D, float* __restrict__ part) {
+  constexpr int XS = CIN + 8, DS = COUT + 8;  // shared row strides (bf16)
+  constexpr int MT = COUT / 16, NT = CIN / 8;
+  constexpr int kUnits = (27 * MT + 7) / 8;   // (tap, co tile) units per warp
+  extern __shared__ __align__(16) bf16 sm[];
+  bf16* xs = sm;                // [kHalo][XS]
+  bf16* ds = sm + kHalo * XS;   // [kBrick][DS]
   const int V = nx * ny * nz;
-  const int tap = blockIdx.y;
-  int dx, dy, dz;
-  tap_offset(tap, dx, dy, dz);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  for (int i = threadIdx.x; i < COUT * CIN; i += blockDim.x) red[i / CIN][i % CIN] = 0.f;
-  __syncthreads();
-  float acc[MT][NT][4];
+  const int mi = lane >> 3, r = lane & 7;
+  const int bxn = (nx + kBrickX - 1) / kBrickX, byn = (ny + kBrickY - 1) / kBrickY,
+            bzn = (nz + kBrickZ - 1) / kBrickZ;
+  const int nbricks = bxn * byn * bzn * B;
+  float acc[kUnits][NT][4];
 #pragma unroll
-  for (int m = 0; m < MT; ++m)
+  for (int u = 0; u < kUnits; ++u)
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
-  const int64_t total = (int64_t)B * V;
-  const int64_t per = ((total + gridDim.x - 1) / gridDim.x + 15) / 16 * 16;
-  const int64_t k0 = blockIdx.x * per, k1 = min(total, k0 + per);
-  const bf16 zero = __float2bfloat16_rn(0.f);
-  for (int64_t ks = k0 + warp * 16; ks < k1; ks += 16 * (kConvThreads / 32)) {
-    // the 16 voxels of this step: k = ks + 2c, 2c+1, 2c+8, 2c+9
-    int64_t kk[4] = {ks + 2 * c, ks + 2 * c + 1, ks + 2 * c + 8, ks + 2 * c + 9};
-    bf16 xv[NT][4];  // B operand rows: X at the shifted voxel, per ci = n*8 + g
-    bf16 dv[MT][2][4];  // A operand: dY at voxel, rows co = m*16 + g (+8)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int64_t k = kk[e];
-      bool valid = k < k1;
-      int64_t bb = 0, v = 0, nvx = 0;
-      bool inb = false;
-      if (valid) {
-        bb = k / V;
-        v = k - bb * V;
-        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
-        inb = x + dx >= 0 && x + dx < nx && y + dy >= 0 && y + dy < ny && z + dz >= 0 && z + dz < nz;
-        nvx = v + dx + (int64_t)nx * (dy + (int64_t)ny * dz);
-      }
-#pragma unroll
-      for (int n = 0; n < NT; ++n)
-        xv[n][e] = (valid && inb) ? Xt[(bb * CIN + n * 8 + g) * V + nvx] : zero;
-#pragma unroll
-      for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int co = m * 16 + g + 8 * h;
-          dv[m][h][e] = (valid && co < COUT) ? Dt[(bb * COUT + co) * V + v] : zero;
-        }
+    for (int n = 0; n < NT; ++n) acc[u][n][0] = acc[u][n][1] = acc[u][n][2] = acc[u][n][3] = 0.f;
+  for (int br = blockIdx.x; br < nbricks; br += gridDim.x) {
+    int t = br;
+    const int bx = t % bxn; t /= bxn;
+    const int by = t % byn; t /= byn;
+    const int bz = t % bzn;
+    const int b = t / bzn;
+    const int x0 = bx * kBrickX, y0 = by * kBrickY, z0 = bz * kBrickZ;
+    const bf16* Xb = X + (size_t)b * V * CIN;
+    const bf16* Db = D + (size_t)b * V * COUT;
+    __syncthreads();  // the previous brick's fragments are read
+    for (int i = threadIdx.x; i < kHalo * (CIN / 8); i += blockDim.x) {
+      const int row = i / (CIN / 8), ch = i - row * (CIN / 8);
+      const int gx = x0 + row % kHaloX - 1, gy = y0 + (row / kHaloX) % kHaloY - 1, gz = z0 + row / (kHaloX * kHaloY) - 1;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+        v = *reinterpret_cast<const uint4*>(Xb + (size_t)(gx + nx * (gy + ny * gz)) * CIN + ch * 8);
+      *reinterpret_cast<uint4*>(xs + row * XS + ch * 8) = v;
     }
-#pragma unroll
-    for (int m = 0; m < MT; ++m) {
-      uint32_t a[4];
-      a[0] = (uint32_t)__bfloat16_as_ushort(dv[m][0][0]) | ((uint32_t)__bfloat16_as_ushort(dv[m][0][1]) << 16);
-      a[1] = (uint32_t)__bfloat16_as_ushort(dv[m][1][0]) | ((uint32_t)__bfloat16_as_ushort(dv[m][1][1]) << 16);
-      a[2] = (uint32_t)__bfloat16_as_ushort(dv[m][0][2]) | ((uint32_t)__bfloat16_as_ushort(dv[m][0][3]) << 16);
-      a[3] = (uint32_t)__bfloat16_as_ushort(dv[m][1][2]) | ((uint32_t)__bfloat16_as_ushort(dv[m][1][3]) << 16);
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const uint32_t b0 = (uint32_t)__bfloat16_as_ushort(xv[n][0]) | ((uint32_t)__bfloat16_as_ushort(xv[n][1]) << 16);
-        const uint32_t b1 = (uint32_t)__bfloat16_as_ushort(xv[n][2]) | ((uint32_t)__bfloat16_as_ushort(xv[n][3]) << 16);
-        mma_bf16(acc[m][n], a, b0, b1);
-      }
-    }
-  }
-  // sum the warps' tiles in a fixed order (one warp at a time)
-  for (int w = 0; w < kConvThreads / 32; ++w) {
-    if (warp == w) {
-#pragma unroll
-      for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int n = 0; n < NT; ++n)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int co = m * 16 + g + 8 * h, ci = n * 8 + 2 * c;
-            if (co < COUT) {
-              red[co][ci] += acc[m][n][2 * h];
-              red[co][ci + 1] += acc[m][n][2 * h + 1];
-            }
-          }
+    for (int i = threadIdx.x; i < kBrick * (COUT / 8); i += blockDim.x) {
+      const int row = i / (COUT / 8), ch = i - row * (COUT / 8);
+      const int gx = x0 + row % kBrickX, gy = y0 + (row / kBrickX) % kBrickY, gz = z0 + row / (kBrickX * kBrickY);
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (gx < nx && gy < ny && gz < nz)
+        v = *reinterpret_cast<const uint4*>(Db + (size_t)(gx + nx * (gy + ny * gz)) * COUT + ch * 8);
+      *reinterpret_cast<uint4*>(ds + row * DS + ch * 8) = v;
     }
     __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kUnits; ++u) {
+      const int unit = warp + 8 * u;
+      if (unit >= 27 * MT) break;  // warp-uniform
+      const int tap = unit / MT, mt = unit - tap * MT;
+      int dx, dy, dz;
+      tap_offset(tap, dx, dy, dz);
+#pragma unroll 2
+      for (int ks = 0; ks < kBrick; ks += 16) {
+        uint32_t a[4];
+        ldsm_x4_t(a, ds + (ks + r + ((mi >> 1) << 3)) * DS + mt * 16 + ((mi & 1) << 3));
+        const int v = ks + r + ((mi & 1) << 3);
+        const int hrow = ((v & 7) + 1 + dx) + kHaloX * ((((v >> 3) & 7) + 1 + dy) + kHaloY * ((v >> 6) + 1 + dz));
+#pragma unroll
+        for (int np = 0; np < NT / 2; ++np) {
+          uint32_t bq[4];
+          ldsm_x4_t(bq, xs + hrow * XS + (2 * np + (mi >> 1)) * 8);
+          mma_bf16(acc[u][2 * np], a, bq[0], bq[1]);
+          mma_bf16(acc[u][2 * np + 1], a, bq[2], bq[3]);
+        }
+      }
+    }
   }
-  for (int i = threadIdx.x; i < COUT * CIN; i += blockDim.x)
-    part[((size_t)blockIdx.x * 27 + tap) * COUT * CIN + i] = red[i / CIN][i % CIN];
+#pragma unroll
+  for (int u = 0; u < kUnits; ++u) {
+    const int unit = warp + 8 * u;
+    if (unit >= 27 * MT) break;
+    const int tap = unit / MT, mt = unit - tap * MT;
+    float* P = part + ((size_t)blockIdx.x * 27 + tap) * COUT * CIN;
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int co = mt * 16 + g + 8 * h, ci = n * 8 + 2 * c;
+        P[co * CIN + ci] = acc[u][n][2 * h];
+        P[co * CIN + ci + 1] = acc[u][n][2 * h + 1];
+      }
+  }
 }
 
-// dW[t][co][ci] = sum over chunks of the partials (fixed order)
-__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ dW, int n, int chunks) {
+// out[i] = sum over k < chunks of part[k n + i] (fixed order, FP64 sum)
+__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ out, int n, int chunks) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
+    double s = 0.0;
     for (int k = 0; k < chunks; ++k) s += part[(size_t)k * n + i];
-    dW[i] = s;
+    out[i] = (float)s;
   }
 }
 
-// db[co] = sum_v dY[v][co] (one block per channel, fixed order)
-__global__ void k_bias_grad(const float* __restrict__ dY, float* __restrict__ db, int64_t nvox, int C) {
-  __shared__ double sh[32];
-  const int co = blockIdx.x;
+// Per-block bias-gradient partials: part[block][co] = sum over this block's
+// voxels of dY[v][co] (FP64).  Threads take consecutive (voxel, channel)
+// pairs, so the loads are coalesced; C divides the block size.
+__global__ void k_bias_partial(const float* __restrict__ dY, double* __restrict__ part, int64_t nvox, int C) {
+  __shared__ double sh[kThreads];
+  const int per = blockDim.x / C;
+  const int co = threadIdx.x % C, sub = threadIdx.x / C;
   double s = 0.0;
-  for (int64_t v = threadIdx.x; v < nvox; v += blockDim.x) s += dY[v * C + co];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) db[co] = (float)s;
+  for (int64_t v = blockIdx.x * (int64_t)per + sub; v < nvox; v += (int64_t)gridDim.x * per) s += dY[v * C + co];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < C) {
+    double t = 0.0;
+    for (int k = 0; k < per; ++k) t += sh[k * C + threadIdx.x];
+    part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_bias_reduce(const double* __restrict__ part, float* __restrict__ db, int C, int chunks) {
+  const int co = threadIdx.x;
+  if (co >= C) return;
+  double s = 0.0;
+  for (int k = 0; k < chunks; ++k) s += part[(size_t)k * C + co];
+  db[co] = (float)s;
 }
 
 // dpre = dpost * (post > 0); also the BF16 copy used as the next mma input
@@ -382,20 +410,27 @@ int launch_fwd(int cin, int cout, FwdMode mode, int nx, int ny, int nz, int B, c
 }
 
 template <int CIN, int COUT>
-int launch_wgrad_t(int nx, int ny, int nz, int B, const bf16* Xt, const bf16* Dt, float* part, float* dW,
+int launch_wgrad_t(int nx, int ny, int nz, int B, const bf16* X, const bf16* D, float* part, float* dW,
                    cudaStream_t s) {
-  (k_conv3d_wgrad<CIN, COUT><<<dim3(kWgChunks, 27), kConvThreads, 0, s>>>(nx, ny, nz, B, Xt, Dt, part),
-   note_launch());
+  auto k = k_conv3d_wgrad<CIN, COUT>;
+  constexpr size_t smem = wgrad_smem<CIN, COUT>();
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return BO_ERR_CUDA;
+  const int64_t nbricks = (int64_t)((nx + kBrickX - 1) / kBrickX) * ((ny + kBrickY - 1) / kBrickY) *
+                          ((nz + kBrickZ - 1) / kBrickZ) * B;
+  int grid = occ_grid((const void*)k, nbricks * kConvThreads, kConvThreads, smem);
+  if (grid > kWgMaxBlocks) grid = kWgMaxBlocks;
+  (k<<<grid, kConvThreads, smem, s>>>(nx, ny, nz, B, X, D, part), note_launch());
   const int n = 27 * CIN * COUT;
-  (k_wgrad_reduce<<<grid_for(n), kThreads, 0, s>>>(part, dW, n, kWgChunks), note_launch());
+  (k_wgrad_reduce<<<grid_for(n), kThreads, 0, s>>>(part, dW, n, grid), note_launch());
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
-int launch_wgrad(int cin, int cout, int nx, int ny, int nz, int B, const bf16* Xt, const bf16* Dt, float* part,
+int launch_wgrad(int cin, int cout, int nx, int ny, int nz, int B, const bf16* X, const bf16* D, float* part,
                  float* dW, cudaStream_t s) {
-  if (cin == 16 && cout == 32) return launch_wgrad_t<16, 32>(nx, ny, nz, B, Xt, Dt, part, dW, s);
-  if (cin == 32 && cout == 32) return launch_wgrad_t<32, 32>(nx, ny, nz, B, Xt, Dt, part, dW, s);
-  if (cin == 32 && cout == 16) return launch_wgrad_t<32, 16>(nx, ny, nz, B, Xt, Dt, part, dW, s);
+  if (cin == 16 && cout == 32) return launch_wgrad_t<16, 32>(nx, ny, nz, B, X, D, part, dW, s);
+  if (cin == 32 && cout == 32) return launch_wgrad_t<32, 32>(nx, ny, nz, B, X, D, part, dW, s);
+  if (cin == 32 && cout == 16) return launch_wgrad_t<32, 16>(nx, ny, nz, B, X, D, part, dW, s);
   return BO_ERR_ARG;
 }
 
@@ -407,16 +442,17 @@ int launch_dgrad(int cin, int cout, int nx, int ny, int nz, int B, const bf16* d
   return launch_fwd(cout, cin, kLinearF32All, nx, ny, nz, B, dY, wd, zero_bias, nullptr, nullptr, dX, s);
 }
 
-// Weight and bias gradients of a layer from its input X (BF16) and dY (FP32)
+// Weight and bias gradients of a layer from its input X (BF16) and dY
+// (FP32; its BF16 copy dY16 is made here unless have16)
 int launch_layer_wgrad(int cin, int cout, int nx, int ny, int nz, int B, const bf16* X, const float* dY, bf16* dY16,
-                       bf16* xt, bf16* dt, float* part, float* dW, float* db, cudaStream_t s) {
+                       bool have16, float* part, double* bpart, float* dW, float* db, cudaStream_t s) {
   const int64_t V = (int64_t)nx * ny * nz, BV = B * V;
-  (k_f32_to_bf16<<<grid_for(BV * cout), kThreads, 0, s>>>(dY, dY16, BV * cout), note_launch());
-  (k_to_channel_major<<<grid_for(BV * cin), kThreads, 0, s>>>(X, xt, (int)V, cin, B), note_launch());
-  (k_to_channel_major<<<grid_for(BV * cout), kThreads, 0, s>>>(dY16, dt, (int)V, cout, B), note_launch());
-  const int rc = launch_wgrad(cin, cout, nx, ny, nz, B, xt, dt, part, dW, s);
+  if (!have16) (k_f32_to_bf16<<<grid_for(BV * cout), kThreads, 0, s>>>(dY, dY16, BV * cout), note_launch());
+  const int rc = launch_wgrad(cin, cout, nx, ny, nz, B, X, dY16, part, dW, s);
   if (rc != BO_OK) return rc;
-  (k_bias_grad<<<cout, kThreads, 0, s>>>(dY, db, BV, cout), note_launch());
+  const int gb = grid_for(BV * cout, kThreads, kWgMaxBlocks);
+  (k_bias_partial<<<gb, kThreads, 0, s>>>(dY, bpart, BV, cout), note_launch());
+  (k_bias_reduce<<<1, 32, 0, s>>>(bpart, db, cout, gb), note_launch());
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
@@ -462,8 +498,7 @@ struct bo_cnn {
   float* gB = nullptr;
   float* gC = nullptr;
   bf16* g16 = nullptr;
-  bf16* xt = nullptr;
-  bf16* dt = nullptr;
+  double* bpart = nullptr;  // bias-gradient partials
   int64_t step = 0;
 };
 
@@ -473,7 +508,7 @@ void cnn_free(bo_cnn* n) {
   auto fr = [](void* q) { if (q) cudaFree(q); };
   fr(n->p); fr(n->gr); fr(n->m); fr(n->v); fr(n->p16); fr(n->wd); fr(n->zero_bias); fr(n->part); fr(n->loss_part);
   for (auto a : n->act) fr(a);
-  fr(n->outf); fr(n->gA); fr(n->gB); fr(n->gC); fr(n->g16); fr(n->xt); fr(n->dt);
+  fr(n->outf); fr(n->gA); fr(n->gB); fr(n->gC); fr(n->g16); fr(n->bpart);
   if (n->h_loss) cudaFreeHost(n->h_loss);
 }
 
@@ -492,7 +527,7 @@ int cnn_alloc(bo_cnn* n) {
   n->p16 = (bf16*)al(n->nparam * 2);
   n->wd = (bf16*)al((size_t)27 * 32 * 32 * 2);
   n->zero_bias = (float*)al(32 * 4);
-  n->part = (float*)al((size_t)bo::kWgChunks * 27 * 32 * 32 * 4);
+  n->part = (float*)al((size_t)bo::kWgMaxBlocks * 27 * 32 * 32 * 4);
   n->loss_part = (double*)al(4096 * sizeof(double));
   if (ok && cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess) ok = false;
   n->act.assign(n->layers.size() + 1, nullptr);
@@ -503,8 +538,7 @@ int cnn_alloc(bo_cnn* n) {
   n->gB = (float*)al(BV * 32 * 4);
   n->gC = (float*)al(BV * 32 * 4);
   n->g16 = (bf16*)al(BV * 32 * 2);
-  n->xt = (bf16*)al(BV * 32 * 2);
-  n->dt = (bf16*)al(BV * 32 * 2);
+  n->bpart = (double*)al((size_t)bo::kWgMaxBlocks * 32 * sizeof(double));
   if (!ok) return BO_ERR_OOM;
   cudaStream_t s = n->ctx->stream;
   cudaMemsetAsync(n->m, 0, n->nparam * 4, s);
@@ -547,8 +581,8 @@ int cnn_backward(bo_cnn* n, const bf16* x, const float* target, const float* mas
    bo::note_launch());
   // output layer (linear)
   const Layer& Lo = n->layers[nl - 1];
-  rc = bo::launch_layer_wgrad(Lo.cin, Lo.cout, n->nx, n->ny, n->nz, B, n->act[nl - 1], n->gA, n->g16, n->xt, n->dt,
-                              n->part, n->gr + Lo.woff, n->gr + Lo.boff, s);
+  rc = bo::launch_layer_wgrad(Lo.cin, Lo.cout, n->nx, n->ny, n->nz, B, n->act[nl - 1], n->gA, n->g16, false,
+                              n->part, n->bpart, n->gr + Lo.woff, n->gr + Lo.boff, s);
   if (rc != BO_OK) return rc;
   rc = bo::launch_dgrad(Lo.cin, Lo.cout, n->nx, n->ny, n->nz, B, n->g16, n->p16 + Lo.woff, n->wd, n->zero_bias,
                         n->gB, s);  // gB = d act[nl-1] (output of the last block)
@@ -561,8 +595,8 @@ int cnn_backward(bo_cnn* n, const bf16* x, const float* target, const float* mas
     // dpre_b = d out * (out > 0) -> gA
     (bo::k_relu_bwd<<<bo::grid_for(cnt), bo::kThreads, 0, s>>>(n->gB, n->act[l + 1], n->gA, n->g16, cnt),
      bo::note_launch());
-    rc = bo::launch_layer_wgrad(Lb.cin, Lb.cout, n->nx, n->ny, n->nz, B, n->act[l], n->gA, n->g16, n->xt, n->dt,
-                                n->part, n->gr + Lb.woff, n->gr + Lb.boff, s);
+    rc = bo::launch_layer_wgrad(Lb.cin, Lb.cout, n->nx, n->ny, n->nz, B, n->act[l], n->gA, n->g16, true,
+                                n->part, n->bpart, n->gr + Lb.woff, n->gr + Lb.boff, s);
     if (rc != BO_OK) return rc;
     rc = bo::launch_dgrad(Lb.cin, Lb.cout, n->nx, n->ny, n->nz, B, n->g16, n->p16 + Lb.woff, n->wd, n->zero_bias,
                           n->gC, s);  // gC = d act[l] (output of conv a)
@@ -571,8 +605,8 @@ int cnn_backward(bo_cnn* n, const bf16* x, const float* target, const float* mas
     cudaMemcpyAsync(n->gB, n->gA, cnt * 4, cudaMemcpyDeviceToDevice, s);
     (bo::k_relu_bwd<<<bo::grid_for(cnt), bo::kThreads, 0, s>>>(n->gC, n->act[l], n->gA, n->g16, cnt),
      bo::note_launch());
-    rc = bo::launch_layer_wgrad(La.cin, La.cout, n->nx, n->ny, n->nz, B, n->act[l - 1], n->gA, n->g16, n->xt, n->dt,
-                                n->part, n->gr + La.woff, n->gr + La.boff, s);
+    rc = bo::launch_layer_wgrad(La.cin, La.cout, n->nx, n->ny, n->nz, B, n->act[l - 1], n->gA, n->g16, true,
+                                n->part, n->bpart, n->gr + La.woff, n->gr + La.boff, s);
     if (rc != BO_OK) return rc;
     rc = bo::launch_dgrad(La.cin, La.cout, n->nx, n->ny, n->nz, B, n->g16, n->p16 + La.woff, n->wd, n->zero_bias,
                           n->gC, s);
@@ -583,8 +617,8 @@ int cnn_backward(bo_cnn* n, const bf16* x, const float* target, const float* mas
   const Layer& Li = n->layers[0];
   (bo::k_relu_bwd<<<bo::grid_for(BV * 32), bo::kThreads, 0, s>>>(n->gB, n->act[1], n->gA, n->g16, BV * 32),
    bo::note_launch());
-  rc = bo::launch_layer_wgrad(Li.cin, Li.cout, n->nx, n->ny, n->nz, B, n->act[0], n->gA, n->g16, n->xt, n->dt,
-                              n->part, n->gr + Li.woff, n->gr + Li.boff, s);
+  rc = bo::launch_layer_wgrad(Li.cin, Li.cout, n->nx, n->ny, n->nz, B, n->act[0], n->gA, n->g16, true,
+                              n->part, n->bpart, n->gr + Li.woff, n->gr + Li.boff, s);
   if (rc != BO_OK) return rc;
   if (loss) {
     std::vector<double> lp(lgrid);
@@ -750,16 +784,17 @@ int bo_conv3d_backward_weights(bo_ctx* ctx, int nx, int ny, int nz, int batch, i
     return BO_ERR_ARG;
   if (!((cin == 16 && cout == 32) || (cin == 32 && cout == 32) || (cin == 32 && cout == 16))) return BO_ERR_ARG;
   const int64_t BV = (int64_t)batch * nx * ny * nz;
-  bf16 *d16 = nullptr, *xt = nullptr, *dt = nullptr;
+  bf16* d16 = nullptr;
   float* part = nullptr;
-  bool ok = cudaMalloc(&d16, BV * cout * 2) == cudaSuccess && cudaMalloc(&xt, BV * cin * 2) == cudaSuccess &&
-            cudaMalloc(&dt, BV * cout * 2) == cudaSuccess &&
-            cudaMalloc(&part, (size_t)bo::kWgChunks * 27 * cin * cout * 4) == cudaSuccess;
-  int rc = ok ? bo::launch_layer_wgrad(cin, cout, nx, ny, nz, batch, reinterpret_cast<const bf16*>(x), dy, d16, xt,
-                                       dt, part, dw, db, ctx->stream)
+  double* bpart = nullptr;
+  bool ok = cudaMalloc(&d16, BV * cout * 2) == cudaSuccess &&
+            cudaMalloc(&part, (size_t)bo::kWgMaxBlocks * 27 * cin * cout * 4) == cudaSuccess &&
+            cudaMalloc(&bpart, (size_t)bo::kWgMaxBlocks * cout * sizeof(double)) == cudaSuccess;
+  int rc = ok ? bo::launch_layer_wgrad(cin, cout, nx, ny, nz, batch, reinterpret_cast<const bf16*>(x), dy, d16, false,
+                                       part, bpart, dw, db, ctx->stream)
               : BO_ERR_OOM;
   cudaStreamSynchronize(ctx->stream);
-  cudaFree(d16); cudaFree(xt); cudaFree(dt); cudaFree(part);
+  cudaFree(d16); cudaFree(part); cudaFree(bpart);
   return rc;
 }
 
