@@ -249,6 +249,138 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def _conv_flops(V):
+    """Forward and training (forward + weight and data gradients, no data
+    gradient for the input layer) FLOPs of the network on V voxels."""
+    layers = [(16, 32)] + [(32, 32)] * 12 + [(32, 16)]
+    f = [2 * 27 * V * ci * co for ci, co in layers]
+    return sum(f), 3 * sum(f) - f[0]
+
+
+def run_learned(args):
+    """The learned Newton update on 64x64x32 realisations (one injector, one
+    producer): targets from this solver's FP64 CPR-FGMRES solves to 1e-8,
+    training with the BF16 tensor-core kernels, then held-out solves from
+    the zero guess and from the network's prediction (pressure only, all
+    three components, and all three plus the learned coarse space)."""
+    import bogen
+    from bogen import learned as L
+    bogen.build()
+    import torch
+    import paper_1606_00556_gb300 as bo
+    from paper_1606_00556_gb300 import learned
+    dims = (64, 64, 32)
+    V = int(np.prod(dims))
+    dev = torch.device("cuda", 0)
+    ctx = bo.Context(0)
+    procs = min(16, os.cpu_count() or 1)
+    stream = torch.cuda.current_stream(dev)
+    X = torch.empty(args.train, V, 16, dtype=torch.bfloat16, device=dev)
+    Y = torch.empty(args.train, V, 4, dtype=torch.float32, device=dev)
+    A = P = None
+    t0 = time.perf_counter()
+    gen_iters = []
+    for i, (f, a) in enumerate(L.samples(range(1000, 1000 + args.train), dims, processes=procs)):
+        if A is None:
+            A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), a["rowptr"], a["col"], a["val"])
+            P = bo.Preconditioner(A)
+        else:
+            A.update_values(a["val"])
+            P.update()
+        b = torch.from_numpy(a["b"]).to(dev)
+        x = torch.zeros_like(b)
+        info = P.solve(b, x, tol=1e-8, restart=args.restart, maxit=1000, raise_on_error=False)
+        gen_iters.append(info["iters"])
+        X[i] = torch.from_numpy(f).to(dev).to(torch.bfloat16)
+        Y[i] = torch.from_numpy(L.targets(x.cpu().numpy())).to(dev)
+    gen_s = time.perf_counter() - t0
+    net = bo.CNN(ctx, *dims, max_batch=args.batch, seed=0)
+    steps = args.epochs * args.train // args.batch
+    learned.train(net, X, Y, 3, args.batch, lr=args.lr, nout=3)  # warm-up (3 steps), then a fresh network
+    net.close()
+    net = bo.CNN(ctx, *dims, max_batch=args.batch, seed=0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    l0 = bo.bo_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = learned.train(net, X, Y, steps, args.batch, lr=args.lr, nout=3, log_every=max(1, steps // 10))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    train_launches = bo.bo_kernel_launches() - l0
+    train_ms = e0.elapsed_time(e1)
+    fwd_flops, train_flops = _conv_flops(V)
+    # forward-only throughput of the inference pass (batch 1) and of one conv layer
+    pred = torch.empty(args.batch, V, 4, device=dev)
+    for _ in range(3):
+        net.forward(X[:args.batch], pred)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(10):
+        net.forward(X[:args.batch], pred)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / 10
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16_peak, peak_kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        bf16_peak, peak_kind = 1900.0, "fallback"
+    del X, Y
+    # held-out evaluation
+    modes = {"zero": None, "learned_p": (1, None), "learned_pss": (3, None), "learned_pss_coarse": (3, (16, 16, 8))}
+    res = {m: {"iters": [], "ms": [], "kept": []} for m in modes}
+    xf = torch.empty(1, V, 16, dtype=torch.bfloat16, device=dev)
+    pred1 = torch.empty(1, V, 4, device=dev)
+    for f, a in L.samples(range(5000, 5000 + args.test), dims, processes=procs):
+        A.update_values(a["val"])
+        P.update()
+        b = torch.from_numpy(a["b"]).to(dev)
+        xf[0] = torch.from_numpy(f).to(dev).to(torch.bfloat16)
+        for m, opt in modes.items():
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            if opt is None:
+                info = P.solve(b, x, tol=1e-8, restart=args.restart, maxit=1000, raise_on_error=False)
+                info["guess_used"] = False
+            else:
+                info = learned.learned_solve(P, net, xf, b, x, L.TARGET_SCALE, opt[0], coarse_tile=opt[1],
+                                             restart=args.restart, pred=pred1)
+            torch.cuda.synchronize()
+            res[m]["ms"].append((time.perf_counter() - ta) * 1e3)
+            if info["status"] != 0 or info["true_rel_res"] > 1e-8:
+                raise RuntimeError(f"held-out solve failed in mode {m}: {info}")
+            res[m]["iters"].append(info["iters"])
+            res[m]["kept"].append(bool(info["guess_used"]))
+    summ = {m: {"iters_mean": float(np.mean(r["iters"])), "ms_mean": float(np.mean(r["ms"])),
+                "guess_kept": float(np.mean(r["kept"]))} for m, r in res.items()}
+    ach = train_flops * args.batch * steps / (train_ms * 1e-3) / 1e12
+    line = {"metric": "learned Newton update: training throughput and held-out iterations to 1e-8 (64x64x32)",
+            "workload": "learned", "value": summ["learned_pss"]["iters_mean"], "unit": "iterations",
+            "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": 3,
+            "ms_per_step": train_ms / steps, "dtype": "bf16", "data": "synthetic",
+            "config": {"grid": list(dims), "train": args.train, "test": args.test, "epochs": args.epochs,
+                       "batch": args.batch, "lr": args.lr,
+                       "network": "conv 16->32, 6 residual blocks of 2 conv 32->32, conv 32->16; 3x3x3, ReLU",
+                       "seeds": "train 1000.., test 5000..", "l2": "activations > L2 (4 x 131072 x 32 x 2 B per layer)"},
+            "training": {"ms": train_ms, "samples_per_s": args.batch * steps / (train_ms * 1e-3),
+                         "tflops": ach, "loss_first": losses[0][1], "loss_last": losses[-1][1],
+                         "losses": losses, "gpu_launches": train_launches},
+            "roofline": {"bound": "tensor", "kernel": "network training step (fwd + dgrad + wgrad)",
+                         "achieved": ach, "peak": bf16_peak, "peak_kind": peak_kind, "unit": "TFLOP/s",
+                         "frac": ach / bf16_peak, "traffic": None,
+                         "forward_tflops": fwd_flops * args.batch / (fwd_ms * 1e-3) / 1e12,
+                         "forward_ms_batch": fwd_ms},
+            "heldout": summ, "generation": {"seconds": gen_s, "iters_mean": float(np.mean(gen_iters))},
+            "clocks": clk, "gpu_launches": train_launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,7 +395,12 @@ def main():
     ap.add_argument("--secondary", default="fp32", choices=["fp32", "fp64", "none"],
                     help="also time the other preconditioner precision on the same Jacobians")
     ap.add_argument("--dist-backend", default="nccl")
-    ap.add_argument("--workload", default="jacobian", choices=["jacobian", "ensemble"])
+    ap.add_argument("--workload", default="jacobian", choices=["jacobian", "ensemble", "learned"])
+    ap.add_argument("--train", type=int, default=2000, help="training realisations of the learned workload")
+    ap.add_argument("--test", type=int, default=200, help="held-out realisations of the learned workload")
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--ensemble", type=int, default=256, help="realisations of the ensemble workload")
     ap.add_argument("--dims", type=int, nargs=3, default=list(DIMS),
                     help="grid (profiling runs only; the benchmark workload is 128 128 64)")
@@ -272,6 +409,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "learned":
+        return run_learned(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
