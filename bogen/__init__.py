@@ -203,3 +203,4 @@ def relperm(fluid: Fluid, sw: float, sg: float):
 
 from .fields import tiny_case, waterflood_case, gaussian_field, uniform_case, ensemble_specs, ensemble_case  # noqa: E402,F401,E501
 from . import learned  # noqa: E402,F401
+from . import dual  # noqa: E402,F401

@@ -194,6 +194,93 @@ struct Assembler {
   }
 };
 
+
+// Flux into node a from node b through a connection of transmissibility T,
+// computed once and added with opposite signs to both nodes' residuals and
+// Jacobian rows.  za, zb: depths of the two nodes.
+void add_face(Assembler& as, const std::vector<Props>& P, const double* x, double za, double zb, int64_t a,
+              int64_t b, double T, double* R) {
+  const Props& A = P[a];
+  const Props& B = P[b];
+  Dual<6> pa = Dual<6>::var(x[3 * a], 0), pb = Dual<6>::var(x[3 * b], 3);
+  const double dz = zb - za;
+  // phase potential differences Phi_b - Phi_a, face density = mean of the two nodes
+  Dual<6> dphi_o = (pb - pa) - 0.5 * (lift(A.go, 0) + lift(B.go, 3)) * dz;
+  Dual<6> dphi_w = (pb - pa) - 0.5 * (lift(A.gw, 0) + lift(B.gw, 3)) * dz;
+  Dual<6> dphi_g = (pb - pa) - 0.5 * (lift(A.gg, 0) + lift(B.gg, 3)) * dz;
+  // upstream node: b if the potential of b is higher; on a tie the lower index
+  auto up = [&](const Dual<6>& d, const Dual<3>& qa, const Dual<3>& qb) {
+    if (d.v > 0) return lift(qb, 3);
+    if (d.v < 0) return lift(qa, 0);
+    return a < b ? lift(qa, 0) : lift(qb, 3);
+  };
+  Dual<6> fo = T * up(dphi_o, A.lo, B.lo) * dphi_o;
+  Dual<6> fw = T * up(dphi_w, A.lw, B.lw) * dphi_w;
+  Dual<6> fg = T * (up(dphi_o, A.rs * A.lo, B.rs * B.lo) * dphi_o + up(dphi_g, A.lg, B.lg) * dphi_g);
+  const Dual<6>* F[3] = {&fo, &fw, &fg};
+  double ba[3][3], bb[3][3];
+  for (int comp = 0; comp < 3; ++comp) {
+    R[3 * a + comp] -= F[comp]->v;
+    R[3 * b + comp] += F[comp]->v;
+    for (int u = 0; u < 3; ++u) { ba[comp][u] = F[comp]->d[u]; bb[comp][u] = F[comp]->d[3 + u]; }
+  }
+  double m[3][3];
+  for (int r = 0; r < 3; ++r) for (int u = 0; u < 3; ++u) m[r][u] = -ba[r][u];
+  as.add_block(a, a, m);
+  for (int r = 0; r < 3; ++r) for (int u = 0; u < 3; ++u) m[r][u] = -bb[r][u];
+  as.add_block(a, b, m);
+  as.add_block(b, a, ba);
+  as.add_block(b, b, bb);
+}
+
+// accumulation of node c: V / (5.615 dt) (M(x) - M(x_n))
+void add_accumulation(Assembler& as, const bg_fluid& f, const Props& Pc, double phi0, const double* xn_c, double V,
+                      double dt, int64_t c, double* R) {
+  const double s = V / (kBblFt3 * dt);
+  const Dual<3>* m[3] = {&Pc.mo, &Pc.mw, &Pc.mg};
+  double blk[3][3];
+  for (int comp = 0; comp < 3; ++comp) {
+    const double mn = cell_mass_value(f, phi0, xn_c[0], xn_c[1], xn_c[2], comp);
+    R[3 * c + comp] += s * (m[comp]->v - mn);
+    for (int u = 0; u < 3; ++u) blk[comp][u] = s * m[comp]->d[u];
+  }
+  as.add_block(c, c, blk);
+}
+
+// wells under fixed bottom-hole pressure (paper Eq. 4) on the perforated nodes:
+// the rate into node c is WI * mobility * (p_h - p - rho g (z_h - z))
+void add_wells(Assembler& as, const std::vector<Props>& P, const double* x, const double* depth, int32_t nw,
+               const int32_t* wtype, const double* bhp, const double* dref, const int32_t* perf_ptr,
+               const int32_t* perf_cells, const double* perf_wi, double* R) {
+  for (int32_t w = 0; w < nw; ++w) {
+    for (int32_t e = perf_ptr[w]; e < perf_ptr[w + 1]; ++e) {
+      const int64_t c = perf_cells[e];
+      const Props& C = P[c];
+      const double WI = perf_wi[e];
+      Dual<3> p = Dual<3>::var(x[3 * c], 0);
+      const double dzh = dref[w] - depth[c];
+      Dual<3> dpo = bhp[w] - p - C.go * dzh;
+      Dual<3> dpw = bhp[w] - p - C.gw * dzh;
+      Dual<3> dpg = bhp[w] - p - C.gg * dzh;
+      Dual<3> qo(0.0), qw(0.0), qg(0.0);
+      if (wtype[w] == 0) {
+        qw = WI * C.lt_res_w * dpw;  // water injector: total mobility
+      } else {
+        qo = WI * C.lo * dpo;
+        qw = WI * C.lw * dpw;
+        qg = WI * (C.rs * C.lo * dpo + C.lg * dpg);
+      }
+      const Dual<3>* Q[3] = {&qo, &qw, &qg};
+      double blk[3][3];
+      for (int comp = 0; comp < 3; ++comp) {
+        R[3 * c + comp] -= Q[comp]->v;
+        for (int u = 0; u < 3; ++u) blk[comp][u] = -Q[comp]->d[u];
+      }
+      as.add_block(c, c, blk);
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -275,53 +362,10 @@ int bg_assemble(const bg_grid* g, const bg_fluid* f,
   }
 
   // accumulation
-  for (int64_t c = 0; c < N; ++c) {
-    const double s = V / (kBblFt3 * dt);
-    const Dual<3>* m[3] = {&P[c].mo, &P[c].mw, &P[c].mg};
-    double blk[3][3];
-    for (int comp = 0; comp < 3; ++comp) {
-      const double mn = cell_mass_value(*f, phi0[c], xn[3 * c], xn[3 * c + 1], xn[3 * c + 2], comp);
-      R[3 * c + comp] += s * (m[comp]->v - mn);
-      for (int u = 0; u < 3; ++u) blk[comp][u] = s * m[comp]->d[u];
-    }
-    as.add_block(c, c, blk);
-  }
+  for (int64_t c = 0; c < N; ++c) add_accumulation(as, *f, P[c], phi0[c], xn + 3 * c, V, dt, c, R);
 
-  // interior faces: flux into cell a from cell b, computed once per face and
-  // added with opposite signs to both cells (no-flow on the outer faces)
-  auto face = [&](int64_t a, int64_t b, double T) {
-    const Props& A = P[a];
-    const Props& B = P[b];
-    Dual<6> pa = Dual<6>::var(x[3 * a], 0), pb = Dual<6>::var(x[3 * b], 3);
-    const double dz = depth[b] - depth[a];
-    // phase potential differences Phi_b - Phi_a, face density = mean of the two cells
-    Dual<6> dphi_o = (pb - pa) - 0.5 * (lift(A.go, 0) + lift(B.go, 3)) * dz;
-    Dual<6> dphi_w = (pb - pa) - 0.5 * (lift(A.gw, 0) + lift(B.gw, 3)) * dz;
-    Dual<6> dphi_g = (pb - pa) - 0.5 * (lift(A.gg, 0) + lift(B.gg, 3)) * dz;
-    // upstream cell: b if the potential of b is higher; on a tie the lower index
-    auto up = [&](const Dual<6>& d, const Dual<3>& qa, const Dual<3>& qb) {
-      if (d.v > 0) return lift(qb, 3);
-      if (d.v < 0) return lift(qa, 0);
-      return a < b ? lift(qa, 0) : lift(qb, 3);
-    };
-    Dual<6> fo = T * up(dphi_o, A.lo, B.lo) * dphi_o;
-    Dual<6> fw = T * up(dphi_w, A.lw, B.lw) * dphi_w;
-    Dual<6> fg = T * (up(dphi_o, A.rs * A.lo, B.rs * B.lo) * dphi_o + up(dphi_g, A.lg, B.lg) * dphi_g);
-    const Dual<6>* F[3] = {&fo, &fw, &fg};
-    double ba[3][3], bb[3][3];
-    for (int comp = 0; comp < 3; ++comp) {
-      R[3 * a + comp] -= F[comp]->v;
-      R[3 * b + comp] += F[comp]->v;
-      for (int u = 0; u < 3; ++u) { ba[comp][u] = F[comp]->d[u]; bb[comp][u] = F[comp]->d[3 + u]; }
-    }
-    double m[3][3];
-    for (int r = 0; r < 3; ++r) for (int u = 0; u < 3; ++u) m[r][u] = -ba[r][u];
-    as.add_block(a, a, m);
-    for (int r = 0; r < 3; ++r) for (int u = 0; u < 3; ++u) m[r][u] = -bb[r][u];
-    as.add_block(a, b, m);
-    as.add_block(b, a, ba);
-    as.add_block(b, b, bb);
-  };
+  // interior faces (no-flow on the outer faces)
+  auto face = [&](int64_t a, int64_t b, double T) { add_face(as, P, x, depth[a], depth[b], a, b, T, R); };
 
   auto tpfa = [&](double area, double h, double k1, double k2) {
     return kDarcy * area * 2.0 / (h / k1 + h / k2);
@@ -357,35 +401,83 @@ int bg_assemble(const bg_grid* g, const bg_fluid* f,
         }
   }
 
-  // wells under fixed bottom-hole pressure (paper Eq. 4): the rate into the
-  // cell is WI * mobility * (p_h - p - rho g (z_h - z))
-  for (int32_t w = 0; w < nw; ++w) {
-    for (int32_t e = perf_ptr[w]; e < perf_ptr[w + 1]; ++e) {
-      const int64_t c = perf_cells[e];
-      const Props& C = P[c];
-      const double WI = perf_wi[e];
-      Dual<3> p = Dual<3>::var(x[3 * c], 0);
-      const double dzh = dref[w] - depth[c];
-      Dual<3> dpo = bhp[w] - p - C.go * dzh;
-      Dual<3> dpw = bhp[w] - p - C.gw * dzh;
-      Dual<3> dpg = bhp[w] - p - C.gg * dzh;
-      Dual<3> qo(0.0), qw(0.0), qg(0.0);
-      if (wtype[w] == 0) {
-        qw = WI * C.lt_res_w * dpw;  // water injector: total mobility
-      } else {
-        qo = WI * C.lo * dpo;
-        qw = WI * C.lw * dpw;
-        qg = WI * (C.rs * C.lo * dpo + C.lg * dpg);
-      }
-      const Dual<3>* Q[3] = {&qo, &qw, &qg};
-      double blk[3][3];
-      for (int comp = 0; comp < 3; ++comp) {
-        R[3 * c + comp] -= Q[comp]->v;
-        for (int u = 0; u < 3; ++u) blk[comp][u] = -Q[comp]->d[u];
-      }
-      as.add_block(c, c, blk);
-    }
+  add_wells(as, P, x, depth, nw, wtype, bhp, dref, perf_ptr, perf_cells, perf_wi, R);
+  return 0;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Block pattern of the dual-porosity system (paper Sec. 2.1's dual-porosity
+// model): 2N block rows, node c < N the fracture continuum of cell c and node
+// N + c its matrix continuum.  Fracture row c holds its 7-point fracture
+// neighbours and its matrix node (ascending columns); matrix row N + c holds
+// (c, N + c).  nnzb = nnzb(7-point) + 3 N.
+int64_t bg_dual_nnzb(const bg_grid* g) {
+  const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+  return bg_nnzb(g) + 3 * N;
+}
+
+void bg_dual_pattern(const bg_grid* g, int32_t* rowptr, int32_t* col) {
+  const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+  std::vector<int32_t> rp(N + 1), cl(bg_nnzb(g));
+  bg_pattern(g, rp.data(), cl.data());
+  int64_t e = 0;
+  rowptr[0] = 0;
+  for (int64_t c = 0; c < N; ++c) {
+    for (int32_t k = rp[c]; k < rp[c + 1]; ++k) col[e++] = cl[k];
+    col[e++] = (int32_t)(N + c);
+    rowptr[c + 1] = (int32_t)e;
   }
+  for (int64_t c = 0; c < N; ++c) {
+    col[e++] = (int32_t)c;
+    col[e++] = (int32_t)(N + c);
+    rowptr[N + c + 1] = (int32_t)e;
+  }
+}
+
+// Dual-porosity residual and Jacobian.  Per cell c: a fracture node (porosity
+// phif, permeabilities kx, ky, kz, 7-point flow among fracture nodes, wells)
+// and a matrix node (porosity phim, no matrix-matrix flow) exchanging fluid
+// with its fracture node through the Warren-Root transfer
+// tau = 0.001127 sigma km V lambda_up (Phi_f - Phi_m) (same depth, so the
+// potential difference is the pressure difference).  x, xn: 6N (fracture
+// nodes' (p, Sw, Sg) first, then the matrix nodes').  Returns 0 or -1.
+int bg_assemble_dual(const bg_grid* g, const bg_fluid* f,
+                     const double* kx, const double* ky, const double* kz, const double* km,
+                     const double* phif, const double* phim, const double* depth,
+                     const double* x, const double* xn, double dt, double sigma,
+                     int32_t nw, const int32_t* wtype, const double* bhp, const double* dref,
+                     const int32_t* perf_ptr, const int32_t* perf_cells, const double* perf_wi,
+                     const int32_t* rowptr, const int32_t* col, double* R, double* val) {
+  const int64_t nx = g->nx, ny = g->ny, nz = g->nz, N = nx * ny * nz;
+  const double V = g->dx * g->dy * g->dz;
+  std::memset(R, 0, sizeof(double) * 6 * N);
+  if (val) std::memset(val, 0, sizeof(double) * 9 * (size_t)rowptr[2 * N]);
+  Assembler as{*g, *f, 2 * N, rowptr, col, R, val};
+  std::vector<Props> P(2 * N);
+  for (int64_t c = 0; c < 2 * N; ++c) {
+    const double ph = c < N ? phif[c] : phim[c - N];
+    P[c] = cell_props(*f, ph, x[3 * c], x[3 * c + 1], x[3 * c + 2]);
+    if (P[c].phi.v <= 0 || P[c].bw.v <= 0 || P[c].bo.v <= 0 || P[c].bg.v <= 0) return -1;
+  }
+  for (int64_t c = 0; c < 2 * N; ++c)
+    add_accumulation(as, *f, P[c], c < N ? phif[c] : phim[c - N], xn + 3 * c, V, dt, c, R);
+  auto tpfa = [&](double area, double h, double k1, double k2) { return kDarcy * area * 2.0 / (h / k1 + h / k2); };
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        const int64_t c = i + nx * (j + ny * k);
+        if (i < nx - 1) add_face(as, P, x, depth[c], depth[c + 1], c, c + 1, tpfa(g->dy * g->dz, g->dx, kx[c], kx[c + 1]), R);
+        if (j < ny - 1)
+          add_face(as, P, x, depth[c], depth[c + nx], c, c + nx, tpfa(g->dx * g->dz, g->dy, ky[c], ky[c + nx]), R);
+        if (k < nz - 1)
+          add_face(as, P, x, depth[c], depth[c + nx * ny], c, c + nx * ny,
+                   tpfa(g->dx * g->dy, g->dz, kz[c], kz[c + nx * ny]), R);
+      }
+  for (int64_t c = 0; c < N; ++c) add_face(as, P, x, depth[c], depth[c], c, N + c, kDarcy * sigma * km[c] * V, R);
+  add_wells(as, P, x, depth, nw, wtype, bhp, dref, perf_ptr, perf_cells, perf_wi, R);
   return 0;
 }
 

@@ -66,7 +66,8 @@ enum {
 };
 
 /* Structured grid (paper Sec. 3.3).  nx must be even (the red-black layout
- * pairs neighbouring cells of a grid row); ncontinua must be 1. */
+ * pairs neighbouring cells of a grid row); ncontinua must be 1 for a bo_mat
+ * and 2 for a bo_dp (dual porosity). */
 typedef struct {
   int32_t nx, ny, nz;
   double dx, dy, dz;
@@ -217,6 +218,46 @@ int64_t bo_kernel_launches(void);
  * stream capture.  Grids of more than 4,194,304 cells give BO_ERR_ARG.
  * Ordered on the context's stream; does not synchronise. */
 int bo_mat_residual_noalloc(bo_mat* A, const double* b, const double* x, double* r, double* norms);
+
+/* ---------------------------------------------------------------------------
+ * Dual-porosity systems (paper Sec. 2.1, the dual-porosity model: fracture
+ * and matrix continua per cell with a transfer term between them).
+ *
+ * Input: a BSR matrix of nbrows = 2 nx ny nz block rows (3x3, row-major,
+ * columns (p, Sw, Sg)); block row c < N is the fracture node of cell c with
+ * its 7-point fracture neighbours and column N + c; block row N + c is the
+ * matrix node of cell c with exactly the columns c and N + c (any order
+ * within a row).  Vectors have 6N doubles, the fracture nodes' (p, Sw, Sg)
+ * first.  grid->ncontinua must be 2; other rules as for bo_mat_create_bsr.
+ *
+ * The matrix unknowns are eliminated exactly per cell (they couple only to
+ * their own fracture node): S = A_ff - A_fm A_mm^{-1} A_mf is a 7-point
+ * system on the fracture nodes, solved by the single-porosity CPR-FGMRES;
+ * x_m = A_mm^{-1} (b_m - A_mf x_f) is recovered afterwards.  Convergence is
+ * judged on the full system's FP64 residual ||b - A x|| / ||b||.
+ * ------------------------------------------------------------------------- */
+typedef struct bo_dp bo_dp;
+
+/* Copies the pattern and values (host or device per mem), checks the
+ * pattern (BO_ERR_PATTERN), forms S and A_mm^{-1} (BO_ERR_BREAKDOWN on a
+ * singular A_mm, BO_ERR_NONFINITE on NaN/Inf).  Holds a reference on ctx.
+ * Synchronises. */
+int bo_dp_create(bo_ctx* ctx, const bo_grid* grid, int32_t nbrows, int64_t nnzb, const int32_t* rowptr,
+                 const int32_t* col, const double* val, int mem, bo_dp** out);
+/* New values on the same pattern; S changes in place, so a preconditioner on
+ * it needs bo_prec_update afterwards.  Synchronises. */
+int bo_dp_update_values(bo_dp* dp, const double* val, int mem);
+/* The condensed fracture system S (owned by dp, valid until bo_dp_destroy):
+ * set up the preconditioner on it with bo_prec_setup. */
+bo_mat* bo_dp_fracture_matrix(bo_dp* dp);
+/* Solve A x = b (device vectors of 6N doubles) to ||b - A x|| <= tol ||b||
+ * with P set up on bo_dp_fracture_matrix(dp): condense, CPR-FGMRES on S,
+ * recover the matrix unknowns, check the full residual in FP64 and refine
+ * (up to two more passes) if rounding left it above tol.  info sums the
+ * passes' iterations and reports the full system's true_rel_res; returns
+ * BO_OK or BO_ERR_NOT_CONVERGED (x then holds the last iterate). */
+int bo_dp_solve(bo_dp* dp, bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
+int bo_dp_destroy(bo_dp* dp);
 
 /* ---------------------------------------------------------------------------
  * Learned Newton update.  No counterpart in the paper: an addition of this

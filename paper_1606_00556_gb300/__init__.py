@@ -49,6 +49,7 @@ EXPORTS = (
     "bo_cnn_get_grads", "bo_cnn_forward", "bo_cnn_backward", "bo_cnn_adam_step",
     "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
     "bo_prec_set_coarse_space", "bo_learned_guess",
+    "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
 )
 
 
@@ -139,6 +140,13 @@ def lib():
         L.bo_conv3d_backward_data.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP]
         L.bo_conv3d_backward_weights.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP, _VP]
         L.bo_prec_set_coarse_space.argtypes = [_VP, _VP, _i, _i, _i]
+        L.bo_dp_create.argtypes = [_VP, ctypes.POINTER(bo_grid), ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, _i,
+                                   ctypes.POINTER(_VP)]
+        L.bo_dp_update_values.argtypes = [_VP, _VP, _i]
+        L.bo_dp_fracture_matrix.restype = _VP
+        L.bo_dp_fracture_matrix.argtypes = [_VP]
+        L.bo_dp_solve.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
+        L.bo_dp_destroy.argtypes = [_VP]
         L.bo_learned_guess.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _i, _VP,
                                        ctypes.POINTER(ctypes.c_int)]
         _lib = L
@@ -272,6 +280,58 @@ class Matrix:
     def close(self):
         if self.h and _alive():
             lib().bo_mat_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DualPorosity:
+    """bo_dp: a dual-porosity system (2N block rows; fracture nodes first).
+    `fracture_matrix` is the condensed fracture system to build the
+    Preconditioner on; `solve` solves the full system."""
+
+    def __init__(self, ctx: Context, nx, ny, nz, rowptr, col, val, dx=100.0, dy=100.0, dz=20.0):
+        g = bo_grid(nx, ny, nz, dx, dy, dz, 2)
+        rowptr = rowptr if hasattr(rowptr, "data_ptr") else np.ascontiguousarray(rowptr, np.int32)
+        col = col if hasattr(col, "data_ptr") else np.ascontiguousarray(col, np.int32)
+        val = _f64(val)
+        rp, m1 = _ptr(rowptr)
+        cp, m2 = _ptr(col)
+        vp, m3 = _ptr(val)
+        if len({m1, m2, m3}) != 1:
+            raise ValueError("rowptr, col and val must all be host or all device")
+        h = _VP()
+        N = nx * ny * nz
+        _check(lib().bo_dp_create(ctx.h, ctypes.byref(g), 2 * N, int(col.shape[0]), rp, cp, vp, m1, ctypes.byref(h)),
+               "bo_dp_create")
+        self.h, self.ctx, self.N = h, ctx, N
+        self._keep = (rowptr, col, val)
+        # a borrowed handle: the bo_dp owns the condensed matrix
+        self.fracture_matrix = Matrix(ctx, bo_grid(nx, ny, nz, dx, dy, dz, 1), _VP(lib().bo_dp_fracture_matrix(h)), ())
+        self.fracture_matrix.close = lambda: None
+
+    def update_values(self, val):
+        val = _f64(val)
+        vp, mem = _ptr(val)
+        _check(lib().bo_dp_update_values(self.h, vp, mem), "bo_dp_update_values")
+
+    def solve(self, P: "Preconditioner", b, x, tol=1e-8, restart=30, maxit=500, x0_is_zero=True,
+              raise_on_error=True):
+        o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
+        info = bo_solve_info()
+        rc = lib().bo_dp_solve(self.h, P.h, _dev(b, "float64", "b"), _dev(x, "float64", "x"), ctypes.byref(o),
+                               ctypes.byref(info))
+        if raise_on_error and rc != BO_OK:
+            raise BoError(rc, "bo_dp_solve")
+        return info.as_dict()
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_dp_destroy(self.h)
         self.h = None
 
     def __del__(self):

@@ -229,3 +229,63 @@ def test_learned_case_recipe():
     np.testing.assert_allclose(t[:, 0] * L.TARGET_SCALE[0], dx[0::3], rtol=1e-6)
     np.testing.assert_allclose(t[:, 2] * L.TARGET_SCALE[2], dx[2::3], rtol=1e-6)
     assert np.all(t[:, 3] == 0)
+
+
+# ---------------------------------------------------------------- dual porosity
+def test_dual_pattern_shape():
+    from bogen import dual as D
+    nx, ny, nz = 4, 3, 2
+    N = nx * ny * nz
+    rp, col = D.dual_pattern(nx, ny, nz)
+    rp7, col7 = bogen.pattern(nx, ny, nz)
+    assert rp.size == 2 * N + 1 and col.size == col7.size + 3 * N
+    for c in range(N):
+        row = list(col[rp[c]:rp[c + 1]])
+        assert row == list(col7[rp7[c]:rp7[c + 1]]) + [N + c]
+        assert sorted(col[rp[N + c]:rp[N + c + 1]]) == [c, N + c]
+
+
+def test_dual_mass_balance_and_transfer_cancel():
+    # summed over both continua, fluxes and the fracture-matrix transfer cancel:
+    # sum R = accumulation of all 2N nodes (no wells)
+    from bogen import dual as D
+    c = D.dual_case(1, 6, 4, 3)
+    c.wells = []
+    rng = np.random.default_rng(2)
+    N = c.N
+    c.x = c.xn * rng.uniform(0.97, 1.03, 6 * N)
+    a = D.assemble_dual(c)
+    V = c.dx * c.dy * c.dz
+    acc = np.zeros(3)
+    for node in range(2 * N):
+        phi = c.phif[node] if node < N else c.phim[node - N]
+        for comp in range(3):
+            m1 = bogen.cell_mass(c.fluid, phi, *c.x[3 * node:3 * node + 3], comp)
+            m0 = bogen.cell_mass(c.fluid, phi, *c.xn[3 * node:3 * node + 3], comp)
+            acc[comp] += V / (5.615 * c.dt) * (m1 - m0)
+    tot = a["R"].reshape(2 * N, 3).sum(axis=0)
+    assert np.allclose(tot, acc, rtol=1e-10, atol=1e-9 * np.abs(a["R"]).max())
+    # the transfer moves fluid between the continua: per cell, the matrix
+    # node's residual is its accumulation minus the inflow from its fracture
+    assert np.abs(a["R"][3 * N:]).max() > 0
+
+
+def test_dual_without_transfer_is_single_porosity_plus_storage():
+    # shape factor 0: the fracture rows equal the single-porosity assembly of
+    # the fracture continuum, and each matrix row holds only its accumulation block
+    from bogen import dual as D
+    c = D.dual_case(3, 6, 4, 3, shape_factor=0.0)
+    N = c.N
+    a = D.assemble_dual(c)
+    sc = bogen.Case(c.nx, c.ny, c.nz, c.dx, c.dy, c.dz, c.kx, c.ky, c.kz, c.phif, c.depth, c.x[:3 * N].copy(),
+                    c.xn[:3 * N].copy(), c.dt, c.wells, c.fluid)
+    s = bogen.assemble(sc)
+    rp, col = a["rowptr"], a["col"]
+    for i in range(N):
+        blocks = {int(col[e]): a["val"][e] for e in range(rp[i], rp[i + 1])}
+        for e in range(s["rowptr"][i], s["rowptr"][i + 1]):
+            np.testing.assert_array_equal(blocks[int(s["col"][e])], s["val"][e])
+        assert np.all(blocks[N + i] == 0.0)
+        mblocks = {int(col[e]): a["val"][e] for e in range(rp[N + i], rp[N + i + 1])}
+        assert np.all(mblocks[i] == 0.0)
+    np.testing.assert_array_equal(a["R"][:3 * N], s["R"])
