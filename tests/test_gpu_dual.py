@@ -1,7 +1,11 @@
 """GPU parity of the dual-porosity solve against the FP64 oracle (plain
 GMRES + ILU(0) on the full 2N-block-row system, or dense LU), through the C
-ABI: the full system's true FP64 residual <= 1e-8 (checked by the oracle's
-compensated residual) and the oracle's solution to 1e-6."""
+ABI.  At tol 1e-8 the full system's true FP64 residual must be <= 1e-8
+(checked by the oracle's compensated residual).  The error bound that
+residual gives is kappa * 1e-8, and these systems are worse conditioned than
+the single-porosity ones (the matrix continuum stores fluid that moves
+through the far more conductive fractures), so the solution is compared
+with the oracle's to 1e-6 after a solve to 1e-11."""
 import numpy as np
 import pytest
 
@@ -51,6 +55,11 @@ def test_dual_solve_matches_oracle(bo, ctx, dims, precision):
     assert info["status"] == bo.BO_OK and info["iters"] > 0
     assert oracle.rel_residual(Ao, a["b"], xg) <= 1e-8
     assert info["true_rel_res"] <= 1e-8
+    x.zero_()
+    info = dp.solve(P, b, x, tol=1e-11)
+    xg = x.cpu().numpy()
+    assert info["status"] == bo.BO_OK
+    assert oracle.rel_residual(Ao, a["b"], xg) <= 1e-11
     assert np.linalg.norm(xg - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
     # the matrix continuum is recovered, not left at zero
     N = int(np.prod(dims))
@@ -67,7 +76,7 @@ def test_dual_update_values(bo, ctx):
     P.update()
     b = torch.tensor(a1["b"], device="cuda")
     x = torch.zeros_like(b)
-    info = dp.solve(P, b, x)
+    info = dp.solve(P, b, x, tol=1e-11)
     Ao, x_ref = _oracle_solution(a1)
     assert info["status"] == bo.BO_OK
     assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
