@@ -206,6 +206,14 @@ def run_ensemble(args):
         xs.append(torch.zeros(b.size, dtype=torch.float64, device=dev))
 
     fallback = {}
+    tuned = None
+    if args.launch == "graph":
+        for P in precs:
+            P.set_launch_mode(bo.BO_LAUNCH_GRAPH)
+    elif args.launch == "auto":
+        cache = os.path.join(ROOT, "paper_1606_00556_gb300", "_build", "tune_cache.json")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tuned = bo.bo_autotune_batched(precs, bs, xs, cache_path=cache, restart=args.restart, maxit=1000)
 
     def step():
         for A, P, v in zip(mats, precs, vals):
@@ -228,10 +236,15 @@ def run_ensemble(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = bo.bo_kernel_launches()
     t0 = time.perf_counter()
     all_infos = [step() for _ in range(args.steps)]
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    launches = bo.bo_kernel_launches() - l0
+    clk = clocks.stop()
     per = sorted(i["solve_ms"] for infos in all_infos for i in infos)
     its = [i["iters"] for i in all_infos[-1]]
     unknowns = sum(3 * int(np.prod(sp["dims"])) for sp in specs)
@@ -245,7 +258,8 @@ def run_ensemble(args):
             "iters": {"min": min(its), "mean": float(np.mean(its)), "max": max(its)},
             "true_rel_res_max": max(i["true_rel_res"] for infos in all_infos for i in infos),
             "failed": sum(i["status"] != 0 for infos in all_infos for i in infos),
-            "promoted_to_fp64": sorted(fallback.keys())}
+            "promoted_to_fp64": sorted(fallback.keys()), "launch": args.launch, "tuned": tuned,
+            "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -402,6 +416,8 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--ensemble", type=int, default=256, help="realisations of the ensemble workload")
+    ap.add_argument("--launch", default="auto", choices=["stream", "graph", "auto"],
+                    help="ensemble: per-kernel launches, per-column CUDA graphs, or the autotuner's choice")
     ap.add_argument("--dims", type=int, nargs=3, default=list(DIMS),
                     help="grid (profiling runs only; the benchmark workload is 128 128 64)")
     args = ap.parse_args()

@@ -57,6 +57,10 @@ typedef enum {
 enum { BO_MEM_HOST = 0, BO_MEM_DEVICE = 1 };
 /* arithmetic of the preconditioner (and of bo_mat_spmv's matrix values) */
 enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1 };
+/* How bo_solve issues the kernels of each Arnoldi column: one launch per
+ * kernel on the stream, or one CUDA-graph launch per column (captured on
+ * first use and replayed; no per-column SpMV timing then). */
+enum { BO_LAUNCH_STREAM = 0, BO_LAUNCH_GRAPH = 1 };
 /* stages of the preconditioner that bo_prec_apply can run on their own */
 enum {
   BO_STAGE_CPR = 0,           /* z = CPR(D_QI^{-1} r): the preconditioner FGMRES uses */
@@ -153,6 +157,35 @@ int bo_prec_spmv_decoupled(bo_prec* P, const double* x, double* y);
  * count (or a negative status). */
 int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap);
 int bo_prec_destroy(bo_prec* P);
+/* Launch mode of P's solves (BO_LAUNCH_STREAM default, BO_LAUNCH_GRAPH).
+ * Graph mode captures the kernels of each Arnoldi column once per restart
+ * length and replays them; the graphs are rebuilt after a change of restart
+ * length or of the learned coarse space.  No counterpart in the paper: a
+ * launch-overhead measure for batches of small systems. */
+int bo_prec_set_launch_mode(bo_prec* P, int mode);
+
+/* Streams bo_solve_batched spreads its systems over (1..16, default 16). */
+int bo_set_batch_streams(int n);
+
+typedef struct {
+  int32_t launch_mode;   /* chosen BO_LAUNCH_* */
+  int32_t streams;       /* chosen stream-pool width */
+  double best_ms;        /* wall time of the chosen configuration's batch */
+  int32_t from_cache;    /* 1: taken from the cache without timing */
+  double trial_ms[6];    /* stream x {4, 8, 16}, then graph x {4, 8, 16} */
+} bo_tune_result;
+
+/* Autotuner for bo_solve_batched (no counterpart in the paper).  Times the
+ * caller's batch (same arguments as bo_solve_batched; x is overwritten,
+ * solves start from zero) under every launch mode and stream-pool width of
+ * 4, 8 and 16, two passes each (the first untimed), applies the fastest to
+ * all P and to the pool, and records it in the JSON file cache_path (NULL:
+ * no cache) under a key of the batch's shape (count, total and largest cell
+ * counts as powers of two, FP32 preconditioners, restart).  With an entry
+ * for the key already present it applies that entry without timing.  Returns
+ * BO_ERR_ARG if the cache cannot be written. */
+int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x,
+                        const bo_solve_opts* opts, const char* cache_path, bo_tune_result* out);
 /* Learned coarse space (no counterpart in the paper; an addition to the
  * CPR preconditioner of Sec. 3.3, Alg. 2).  dp: device array of nx ny nz
  * doubles in natural cell order, a predicted pressure update; the grid is

@@ -36,6 +36,8 @@ BO_STAGE_CPR = 0
 BO_STAGE_ILU = 1
 BO_STAGE_AMG = 2
 BO_STAGE_CPR_DECOUPLED = 3
+BO_LAUNCH_STREAM = 0
+BO_LAUNCH_GRAPH = 1
 
 # every symbol include/bosolve.h declares
 EXPORTS = (
@@ -50,6 +52,7 @@ EXPORTS = (
     "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
     "bo_prec_set_coarse_space", "bo_learned_guess",
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
+    "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched",
 )
 
 
@@ -73,6 +76,11 @@ class bo_prec_opts(ctypes.Structure):
 class bo_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("x0_is_zero", ctypes.c_int32), ("mem", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class bo_tune_result(ctypes.Structure):
+    _fields_ = [("launch_mode", ctypes.c_int32), ("streams", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("from_cache", ctypes.c_int32), ("trial_ms", ctypes.c_double * 6)]
 
 
 class bo_solve_info(ctypes.Structure):
@@ -147,6 +155,10 @@ def lib():
         L.bo_dp_fracture_matrix.argtypes = [_VP]
         L.bo_dp_solve.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
         L.bo_dp_destroy.argtypes = [_VP]
+        L.bo_prec_set_launch_mode.argtypes = [_VP, _i]
+        L.bo_set_batch_streams.argtypes = [_i]
+        L.bo_autotune_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                          ctypes.POINTER(bo_solve_opts), ctypes.c_char_p, ctypes.POINTER(bo_tune_result)]
         L.bo_learned_guess.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _i, _VP,
                                        ctypes.POINTER(ctypes.c_int)]
         _lib = L
@@ -389,6 +401,10 @@ class Preconditioner:
         d["status"] = rc
         return d
 
+    def set_launch_mode(self, mode):
+        """BO_LAUNCH_STREAM or BO_LAUNCH_GRAPH (per-column CUDA graphs)."""
+        _check(lib().bo_prec_set_launch_mode(self.h, int(mode)), "bo_prec_set_launch_mode")
+
     def set_coarse_space(self, dp, tile=(16, 16, 8)):
         """Learned coarse space from a predicted pressure update dp (device
         float64, one value per cell, natural order); None removes it."""
@@ -447,6 +463,25 @@ def bo_solve_batched(precs, bs, xs, tol=1e-8, restart=30, maxit=500, x0_is_zero=
         d = i.as_dict()
         out.append(d)
     return rc, out
+
+
+def bo_set_batch_streams(n: int):
+    _check(lib().bo_set_batch_streams(int(n)), "bo_set_batch_streams")
+
+
+def bo_autotune_batched(precs, bs, xs, cache_path=None, tol=1e-8, restart=30, maxit=500):
+    """bo_autotune_batched: pick (launch mode, stream-pool width) for this
+    batch by timing, or from the JSON cache; returns a dict of the result."""
+    n = len(precs)
+    P = (_VP * n)(*[p.h for p in precs])
+    B = (_VP * n)(*[_VP(t.data_ptr()) for t in bs])
+    X = (_VP * n)(*[_VP(t.data_ptr()) for t in xs])
+    o = bo_solve_opts(tol, restart, maxit, 1, BO_MEM_DEVICE, 0)
+    res = bo_tune_result()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().bo_autotune_batched(P, n, B, X, ctypes.byref(o), path, ctypes.byref(res)), "bo_autotune_batched")
+    return {"launch_mode": res.launch_mode, "streams": res.streams, "best_ms": res.best_ms,
+            "from_cache": bool(res.from_cache), "trial_ms": list(res.trial_ms)}
 
 
 def bo_kernel_launches() -> int:

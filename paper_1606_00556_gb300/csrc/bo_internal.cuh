@@ -117,6 +117,7 @@ struct DevState {
   int k;           // Arnoldi steps completed in the current cycle
   int happy;       // happy breakdown in the current cycle
   int err;         // kErr* bits from setup and apply kernels
+  int hist_base;   // Arnoldi steps of the finished cycles of this solve (residual-history offset)
   unsigned counter[8];
   double est;      // Arnoldi estimate of ||b - A x|| after k steps
   double target;   // tol * ||b||
@@ -131,6 +132,9 @@ struct DevState {
 
 // Number of kernels this library has launched (reported by bo_kernel_launches).
 extern std::atomic<long long> g_launches;
+// streams of the batched solve's pool in use (1..kMaxPoolStreams)
+constexpr int kMaxPoolStreams = 16;
+extern std::atomic<int> g_pool_width;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // grid size for a grid-stride loop over n items
@@ -242,6 +246,13 @@ struct bo_prec {
   double* lc_Einv = nullptr;
   double* lc_y = nullptr;  // Z^T f
   double* lc_u = nullptr;  // E^{-1} Z^T f
+  // CUDA-graph launch of the Arnoldi columns (BO_LAUNCH_GRAPH): one
+  // instantiated graph per column index, captured for restart length graph_m
+  int launch_mode = 0;
+  int graph_m = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t col_exec[64] = {};
+  long long col_nodes[64] = {};
   double* hist;            // host residual history of the last solve
   int nhist;
   int hist_cap;
@@ -273,6 +284,7 @@ int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* 
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
                    bo_solve_info* infos);
 int krylov_alloc(bo_prec* P, int m);
+void graphs_reset(bo_prec* P);
 // dense FP64 inverse of an n x n matrix (n <= 128) by one block; sets
 // st->err on a zero pivot
 int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, cudaStream_t s);

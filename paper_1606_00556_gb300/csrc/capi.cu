@@ -1,6 +1,7 @@
 // C ABI entry points (declared in bosolve.h): argument checks, object
 // lifetimes, host <-> device staging and error mapping.  All arithmetic runs
 // in the kernels of layout.cu, precond.cu and krylov.cu.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -14,6 +15,7 @@ using namespace bo;
 
 namespace bo {
 std::atomic<long long> g_launches{0};
+std::atomic<int> g_pool_width{kMaxPoolStreams};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
   static std::mutex mu;
@@ -396,8 +398,9 @@ int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, doubl
       if (P[q] == P[r]) return BO_ERR_ARG;  // each solve needs its own workspace
   }
   if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
-  // a pool of streams per device, created once and kept for the process
-  constexpr int kPool = 16;
+  // a pool of streams per device, created once and kept for the process;
+  // the batch uses the first g_pool_width of them
+  constexpr int kPool = kMaxPoolStreams;
   static std::mutex mu;
   static std::unordered_map<int, std::vector<cudaStream_t>> pools;
   std::vector<cudaStream_t> pool;
@@ -422,7 +425,8 @@ int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, doubl
     cudaStreamWaitEvent(to, e, 0);
     evs.push_back(e);
   };
-  const int S = nreal < kPool ? nreal : kPool;
+  const int width = std::min(kPool, std::max(1, g_pool_width.load()));
+  const int S = nreal < width ? nreal : width;
   for (int r = 0; r < nreal; ++r) join(P[r]->mat->ctx->stream, pool[r % S]);
   for (int r = 0; r < nreal; ++r) P[r]->stream = pool[r % S];
   const int rc = fgmres_batched(P, nreal, b, x, &o, infos);
@@ -443,6 +447,12 @@ int bo_prec_residual_history(bo_prec* P, double* buf, int cap) {
 }
 
 int64_t bo_kernel_launches(void) { return g_launches.load(); }
+
+int bo_prec_set_launch_mode(bo_prec* P, int mode) {
+  if (!P || (mode != BO_LAUNCH_STREAM && mode != BO_LAUNCH_GRAPH)) return BO_ERR_ARG;
+  P->launch_mode = mode;
+  return BO_OK;
+}
 
 int bo_newton_update(bo_ctx* ctx, double* state, const double* dx, int64_t n) {
   if (!ctx || !state || !dx || n < 0) return BO_ERR_ARG;

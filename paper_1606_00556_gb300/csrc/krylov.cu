@@ -135,6 +135,8 @@ __global__ void k_norm(int64_t n, const double* __restrict__ v, double* partials
 __global__ void k_set_target(DevState* st, double tol) {
   st->target = tol * st->bnorm;
   st->err = 0;
+  st->k = 0;
+  st->hist_base = 0;
 }
 
 // start of a cycle: g = (beta, 0, ...), flags cleared
@@ -142,6 +144,7 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
   for (int i = threadIdx.x; i <= m; i += blockDim.x) gv[i] = (i == 0) ? st->beta : 0.0;
   if (threadIdx.x == 0) {
     st->done = 0;
+    st->hist_base += st->k;
     st->k = 0;
     st->happy = 0;
     st->est = st->beta;
@@ -160,7 +163,7 @@ __global__ void k_scale_beta(int64_t n, const double* __restrict__ src, double* 
 // previous rotations, a new one, the residual estimate and the stop flag.
 // Runs in one thread.
 __device__ void givens_step(DevState* st, double* col, double hn, double* H, double* cs, double* sn, double* gv, int j,
-                            int m, int ldh, double* hist, int hist_at) {
+                            int m, int ldh, double* hist) {
   double nrm2 = 0.0;
   for (int i = 0; i <= j; ++i) nrm2 += col[i] * col[i];
   const double wn0 = sqrt(nrm2 + hn * hn);
@@ -183,6 +186,7 @@ __device__ void givens_step(DevState* st, double* col, double hn, double* H, dou
   st->happy = hn <= 1e-14 * wn0;
   st->hn = hn;
   st->scale = hn > 0.0 ? 1.0 / hn : 0.0;
+  const int hist_at = st->hist_base + j;
   if (hist && hist_at < kHistCap) hist[hist_at] = st->est;
   const bool bad = !isfinite(st->est) || !isfinite(d) || d == 0.0;
   if (bad) atomicOr(&st->err, kErrNonfinite);
@@ -196,7 +200,6 @@ struct ArnoldiArgs {
   double* gv;
   int j, m, ldh;
   double* hist;
-  int hist_at;
 };
 
 // Gram-Schmidt coefficient pass: h[off + u] = vscale[u] <V_u, w> for u <= j.
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double*
   double col[kMaxM + 1];
   for (int u = 0; u < nv; ++u) col[u] = st->h[u] + st->h[kMaxM + u];
   const double hn = sqrt(hn2);
-  givens_step(st, col, hn, aa.H, aa.cs, aa.sn, aa.gv, aa.j, aa.m, aa.ldh, aa.hist, aa.hist_at);
+  givens_step(st, col, hn, aa.H, aa.cs, aa.sn, aa.gv, aa.j, aa.m, aa.ldh, aa.hist);
   st->vscale[aa.j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
 }
 
@@ -301,8 +304,18 @@ __global__ void k_xupdate(int64_t n, double* __restrict__ x, const double* __res
 
 }  // namespace
 
+void graphs_reset(bo_prec* P) {
+  for (int j = 0; j < 64; ++j)
+    if (P->col_exec[j]) {
+      cudaGraphExecDestroy(P->col_exec[j]);
+      P->col_exec[j] = nullptr;
+    }
+  P->graph_m = 0;
+}
+
 int krylov_alloc(bo_prec* P, int m) {
   if (P->mcap >= m && P->V) return BO_OK;
+  graphs_reset(P);
   const Geom& g = P->mat->g;
   const int64_t n = 3 * g.N;
   auto fr = [](void* p) { if (p) cudaFree(p); };
@@ -422,7 +435,8 @@ struct Job {
     phase = kColumns;
   }
 
-  void enqueue_column(int j) {
+  // the kernels of Arnoldi column j on the preconditioner's stream
+  void enqueue_column_kernels(int j, bool timed) {
     cudaStream_t s = stream();
     const Geom& g = geom();
     const int64_t nn = n(), ldv = nn;
@@ -434,7 +448,7 @@ struct Job {
     double* dhist = P->partials + (P->npartials - kHistCap);
     launch_cpr(P, vj, zj, BO_STAGE_CPR, st, &st->vscale[j]);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (profile && prof.size() < 512) {
+    if (timed && prof.size() < 512) {
       e0 = P->prof_ev[2 * prof.size()];
       e1 = P->prof_ev[2 * prof.size() + 1];
       cudaEventRecord(e0, s);
@@ -445,13 +459,64 @@ struct Job {
       cudaEventRecord(e1, s);
       prof.push_back({e0, e1});
     }
-    const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist, its + j};
+    const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
     const dim3 gd(gs_chunks(nn), j + 1);
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
     (k_gs_dots<<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, 0), note_launch());
     (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, aa), note_launch());
     (k_gs_dots<<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
     (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, aa), note_launch());
+  }
+
+  // Column j's kernels captured once into a CUDA graph (on a private stream,
+  // since the preconditioner's stream may be the legacy default stream) and
+  // instantiated; valid while the workspace and restart length stay put.
+  bool ensure_graph(int j) {
+    const int m = o.restart;
+    if (P->graph_m != m) {
+      graphs_reset(P);
+      P->graph_m = m;
+    }
+    if (P->col_exec[j]) return true;
+    if (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    cudaStream_t saved = P->stream;
+    P->stream = P->cap_stream;
+    const long long l0 = g_launches.load();
+    if (cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      P->stream = saved;
+      return false;
+    }
+    enqueue_column_kernels(j, false);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(P->cap_stream, &gr);
+    P->stream = saved;
+    const long long nodes = g_launches.load() - l0;
+    g_launches.fetch_sub(nodes);  // captured, not run: counted at each replay instead
+    if (e != cudaSuccess || !gr) return false;
+    const cudaError_t ei = cudaGraphInstantiate(&P->col_exec[j], gr, 0);
+    cudaGraphDestroy(gr);
+    if (ei != cudaSuccess) {
+      P->col_exec[j] = nullptr;
+      return false;
+    }
+    P->col_nodes[j] = nodes;
+    return true;
+  }
+
+  void enqueue_column(int j) {
+    if (P->launch_mode == BO_LAUNCH_GRAPH && !profile) {
+      if (!ensure_graph(j)) {
+        fail(BO_ERR_CUDA);
+        return;
+      }
+      if (cudaGraphLaunch(P->col_exec[j], stream()) != cudaSuccess) {
+        fail(BO_ERR_CUDA);
+        return;
+      }
+      g_launches.fetch_add(P->col_nodes[j]);
+    } else {
+      enqueue_column_kernels(j, profile);
+    }
     mark(j % kRing);
   }
 

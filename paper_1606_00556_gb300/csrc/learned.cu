@@ -207,6 +207,7 @@ int bo_prec_set_coarse_space(bo_prec* P, const double* dp, int tx, int ty, int t
   if (cudaSetDevice(P->mat->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   cudaStreamSynchronize(P->stream);
   bo::learned_coarse_free(P);
+  bo::graphs_reset(P);  // captured columns hold the old preconditioner sequence
   if (!dp) return BO_OK;
   const bo::Geom& g = P->mat->g;
   if (tx < 1 || ty < 1 || tz < 1) return BO_ERR_ARG;

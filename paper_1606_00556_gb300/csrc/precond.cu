@@ -1108,6 +1108,9 @@ void prec_free(bo_prec* P) {
   for (int l = 1; l < P->nlev; ++l) { fr(P->lev[l].c64); fr(P->lev[l].c); fr(P->lev[l].f); fr(P->lev[l].x); }
   fr(P->coarse64); fr(P->coarse_inv); fr(P->st);
   learned_coarse_free(P);
+  graphs_reset(P);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  P->cap_stream = nullptr;
 }
 
 int prec_values(bo_prec* P) {

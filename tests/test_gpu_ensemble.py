@@ -54,3 +54,85 @@ def test_batched_rejects_shared_workspace():
         bo.bo_solve_batched([P], [b], [])
     rc, _ = bo.bo_solve_batched([P, P], [b, b], [torch.zeros_like(b), torch.zeros_like(b)])
     assert rc == bo.BO_ERR_ARG
+
+
+def _ensemble(bo, ctx, precision=0, specs=SPECS):
+    precs, bs, sys, mats = [], [], [], []
+    for sp in specs:
+        a = bogen.assemble(bogen.ensemble_case(sp))
+        A = bo.Matrix.from_bsr(ctx, bo.grid(*sp["dims"]), a["rowptr"], a["col"], a["val"])
+        mats.append(A)
+        precs.append(bo.Preconditioner(A, precision=precision))
+        bs.append(torch.tensor(a["b"], dtype=torch.float64, device="cuda"))
+        sys.append((oracle.BsrMatrix(a["rowptr"], a["col"], a["val"]), a["b"]))
+    return mats, precs, bs, sys
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_launch_is_bitwise_equal_to_stream_launch(precision):
+    # the captured columns run the same kernels in the same order
+    import paper_1606_00556_gb300 as bo
+    ctx = bo.Context(0)
+    mats, precs, bs, sys = _ensemble(bo, ctx, precision)
+    ref = []
+    for P, b in zip(precs, bs):
+        x = torch.zeros_like(b)
+        info = P.solve(b, x, tol=1e-8)
+        ref.append((x, info["iters"], P.residual_history()))
+    for P in precs:
+        P.set_launch_mode(bo.BO_LAUNCH_GRAPH)
+    for rep in range(2):  # the second run replays the graphs captured by the first
+        for (P, b), (xr, it, hist) in zip(zip(precs, bs), ref):
+            x = torch.zeros_like(b)
+            info = P.solve(b, x, tol=1e-8)
+            assert info["iters"] == it and torch.equal(x, xr)
+            np.testing.assert_array_equal(P.residual_history(), hist)
+        xs = [torch.zeros_like(b) for b in bs]
+        rc, infos = bo.bo_solve_batched(precs, bs, xs, tol=1e-8)
+        assert rc == bo.BO_OK
+        for x, (xr, it, _), info in zip(xs, ref, infos):
+            assert info["iters"] == it and torch.equal(x, xr)
+
+
+def test_graph_launch_follows_restart_and_coarse_space_changes():
+    import paper_1606_00556_gb300 as bo
+    ctx = bo.Context(0)
+    mats, precs, bs, sys = _ensemble(bo, ctx, 0, SPECS[1:2])
+    P, b, (Ao, bh) = precs[0], bs[0], sys[0]
+    P.set_launch_mode(bo.BO_LAUNCH_GRAPH)
+    for restart in (30, 10, 30):
+        x = torch.zeros_like(b)
+        info = P.solve(b, x, tol=1e-8, restart=restart)
+        assert info["status"] == 0 and oracle.rel_residual(Ao, bh, x.cpu().numpy()) <= 1e-8
+    x_ref = x.cpu().numpy()
+    P.set_coarse_space(torch.tensor(x_ref[0::3], device="cuda"), (10, 10, 5))
+    x = torch.zeros_like(b)
+    info = P.solve(b, x, tol=1e-8)
+    assert info["status"] == 0 and oracle.rel_residual(Ao, bh, x.cpu().numpy()) <= 1e-8
+    P.set_launch_mode(bo.BO_LAUNCH_STREAM)
+    x2 = torch.zeros_like(b)
+    P.solve(b, x2, tol=1e-8)
+    assert torch.equal(x, x2)
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    import paper_1606_00556_gb300 as bo
+    ctx = bo.Context(0)
+    mats, precs, bs, sys = _ensemble(bo, ctx, 0)
+    xs = [torch.zeros_like(b) for b in bs]
+    path = str(tmp_path / "tune.json")
+    r1 = bo.bo_autotune_batched(precs, bs, xs, cache_path=path)
+    assert not r1["from_cache"] and r1["launch_mode"] in (0, 1) and r1["streams"] in (4, 8, 16)
+    assert all(t > 0 for t in r1["trial_ms"]) and r1["best_ms"] == min(r1["trial_ms"])
+    r2 = bo.bo_autotune_batched(precs, bs, xs, cache_path=path)
+    assert r2["from_cache"] and (r2["launch_mode"], r2["streams"]) == (r1["launch_mode"], r1["streams"])
+    import json
+    with open(path) as f:
+        assert len(json.load(f)) == 1
+    # the tuned configuration still solves the batch correctly
+    xs = [torch.zeros_like(b) for b in bs]
+    rc, infos = bo.bo_solve_batched(precs, bs, xs, tol=1e-8)
+    assert rc == bo.BO_OK
+    for x, (Ao, bh) in zip(xs, sys):
+        assert oracle.rel_residual(Ao, bh, x.cpu().numpy()) <= 1e-8
+    bo.bo_set_batch_streams(16)
