@@ -216,9 +216,7 @@ def run_ensemble(args):
         tuned = bo.bo_autotune_batched(precs, bs, xs, cache_path=cache, restart=args.restart, maxit=1000)
 
     def step():
-        for A, P, v in zip(mats, precs, vals):
-            A.update_values(v)
-            P.update()
+        bo.bo_update_batched(precs, vals)
         rc, infos = bo.bo_solve_batched(precs, bs, xs, tol=1e-8, restart=args.restart, maxit=1000)
         # mixed precision with promotion: a realisation whose FP32-preconditioned
         # solve stagnates is solved again with an FP64 preconditioner

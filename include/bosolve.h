@@ -164,6 +164,15 @@ int bo_prec_destroy(bo_prec* P);
  * launch-overhead measure for batches of small systems. */
 int bo_prec_set_launch_mode(bo_prec* P, int mode);
 
+/* New values for many systems at once: for each r, the values val[r]
+ * (host or device per mem; NULL keeps the matrix's values) go into P[r]'s
+ * matrix as bo_mat_update_values does, then P[r] is refreshed as
+ * bo_prec_update does, the systems spread over the stream pool, with one
+ * synchronisation for the whole batch instead of two per system.  Each P[r]
+ * needs its own matrix.  Returns the first error found (pattern, non-finite
+ * value or singular pivot), after all systems were processed. */
+int bo_update_batched(bo_prec* const* P, int nreal, const double* const* val, int mem);
+
 /* Streams bo_solve_batched spreads its systems over (1..16, default 16). */
 int bo_set_batch_streams(int n);
 

@@ -52,7 +52,7 @@ EXPORTS = (
     "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
     "bo_prec_set_coarse_space", "bo_learned_guess",
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
-    "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched",
+    "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
 )
 
 
@@ -157,6 +157,7 @@ def lib():
         L.bo_dp_destroy.argtypes = [_VP]
         L.bo_prec_set_launch_mode.argtypes = [_VP, _i]
         L.bo_set_batch_streams.argtypes = [_i]
+        L.bo_update_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), _i]
         L.bo_autotune_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                           ctypes.POINTER(bo_solve_opts), ctypes.c_char_p, ctypes.POINTER(bo_tune_result)]
         L.bo_learned_guess.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _i, _VP,
@@ -463,6 +464,18 @@ def bo_solve_batched(precs, bs, xs, tol=1e-8, restart=30, maxit=500, x0_is_zero=
         d = i.as_dict()
         out.append(d)
     return rc, out
+
+
+def bo_update_batched(precs, vals=None):
+    """bo_update_batched: new values (device tensors, or None to keep) for
+    every preconditioner's matrix, then refresh them all, one sync in all."""
+    n = len(precs)
+    P = (_VP * n)(*[p.h for p in precs])
+    if vals is None:
+        V = None
+    else:
+        V = (_VP * n)(*[_VP(_dev(v, "float64", "val").value) if v is not None else None for v in vals])
+    _check(lib().bo_update_batched(P, n, V, BO_MEM_DEVICE), "bo_update_batched")
 
 
 def bo_set_batch_streams(n: int):

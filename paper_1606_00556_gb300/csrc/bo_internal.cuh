@@ -262,8 +262,8 @@ struct bo_prec {
 namespace bo {
 
 // layout.cu
-int ingest_bsr(bo_mat* m, const double* dval);
-int ingest_csr(bo_mat* m, const double* dval);
+int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s);
+int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s);
 void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
 void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s);
 void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, bool fp32);

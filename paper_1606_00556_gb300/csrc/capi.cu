@@ -86,7 +86,7 @@ int load_values(bo_mat* m, const double* val, int mem) {
     if (e != cudaSuccess) return cuda_status(e);
     dval = m->stage;
   }
-  int rc = m->kind == 0 ? ingest_bsr(m, dval) : ingest_csr(m, dval);
+  int rc = m->kind == 0 ? ingest_bsr(m, dval, m->ctx->stream) : ingest_csr(m, dval, m->ctx->stream);
   if (rc != BO_OK) return rc;
   m->a32_valid = false;
   return mat_flags(m);
@@ -158,6 +158,23 @@ int mat_create(bo_ctx* ctx, const bo_grid* grid, int kind, int64_t nrows, int64_
   }
   *out = m;
   return BO_OK;
+}
+
+// a pool of streams per device, created once and kept for the process;
+// batched calls use the first g_pool_width of them
+bool stream_pool(int dev, std::vector<cudaStream_t>& pool) {
+  static std::mutex mu;
+  static std::unordered_map<int, std::vector<cudaStream_t>> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  auto& pl = pools[dev];
+  if (pl.empty())
+    for (int i = 0; i < kMaxPoolStreams; ++i) {
+      cudaStream_t st;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
+      pl.push_back(st);
+    }
+  pool = pl;
+  return true;
 }
 
 void prec_opts_fill(const bo_prec_opts* in, bo_prec_opts* o) {
@@ -398,23 +415,9 @@ int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, doubl
       if (P[q] == P[r]) return BO_ERR_ARG;  // each solve needs its own workspace
   }
   if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
-  // a pool of streams per device, created once and kept for the process;
-  // the batch uses the first g_pool_width of them
-  constexpr int kPool = kMaxPoolStreams;
-  static std::mutex mu;
-  static std::unordered_map<int, std::vector<cudaStream_t>> pools;
   std::vector<cudaStream_t> pool;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    auto& pl = pools[dev];
-    if (pl.empty())
-      for (int i = 0; i < kPool; ++i) {
-        cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return BO_ERR_CUDA;
-        pl.push_back(st);
-      }
-    pool = pl;
-  }
+  if (!stream_pool(dev, pool)) return BO_ERR_CUDA;
+  constexpr int kPool = kMaxPoolStreams;
   // order the batch after everything already queued on the contexts' streams,
   // and the contexts' streams after the batch
   std::vector<cudaEvent_t> evs;
@@ -436,6 +439,71 @@ int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, doubl
   }
   for (int r = 0; r < S; ++r) cudaStreamSynchronize(pool[r]);
   for (auto e : evs) cudaEventDestroy(e);
+  return rc;
+}
+
+int bo_update_batched(bo_prec* const* P, int nreal, const double* const* val, int mem) {
+  if (!P || nreal < 1 || (mem != BO_MEM_HOST && mem != BO_MEM_DEVICE)) return BO_ERR_ARG;
+  const int dev = P[0] ? P[0]->mat->ctx->device : -1;
+  for (int r = 0; r < nreal; ++r) {
+    if (!P[r] || P[r]->mat->ctx->device != dev) return BO_ERR_ARG;
+    for (int q = 0; q < r; ++q)
+      if (P[q] == P[r] || P[q]->mat == P[r]->mat) return BO_ERR_ARG;
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
+  std::vector<cudaStream_t> pool;
+  if (!stream_pool(dev, pool)) return BO_ERR_CUDA;
+  const int width = std::min(kMaxPoolStreams, std::max(1, g_pool_width.load()));
+  const int S = nreal < width ? nreal : width;
+  int* hflags = nullptr;
+  if (cudaMallocHost(&hflags, 2 * (size_t)nreal * sizeof(int)) != cudaSuccess) return BO_ERR_OOM;
+  std::vector<cudaEvent_t> evs;
+  auto join = [&](cudaStream_t from, cudaStream_t to) {
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventRecord(e, from);
+    cudaStreamWaitEvent(to, e, 0);
+    evs.push_back(e);
+  };
+  int rc = BO_OK;
+  for (int r = 0; r < nreal && rc == BO_OK; ++r) {
+    bo_prec* p = P[r];
+    bo_mat* m = p->mat;
+    cudaStream_t s = pool[r % S];
+    join(m->ctx->stream, s);
+    p->stream = s;
+    cudaMemsetAsync(&p->st->err, 0, sizeof(int), s);
+    if (val && val[r]) {
+      const double* dval = val[r];
+      const size_t bytes = (m->kind == 0 ? 9 * (size_t)m->nnz : (size_t)m->nnz) * sizeof(double);
+      if (mem == BO_MEM_HOST) {
+        if (cudaMemcpyAsync(m->stage, val[r], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = BO_ERR_CUDA;
+        dval = m->stage;
+      }
+      if (rc == BO_OK) rc = m->kind == 0 ? ingest_bsr(m, dval, s) : ingest_csr(m, dval, s);
+      m->a32_valid = false;
+    }
+    if (rc == BO_OK) rc = prec_values(p);
+    cudaMemcpyAsync(&hflags[2 * r], m->flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&hflags[2 * r + 1], &p->st->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemsetAsync(m->flags, 0, sizeof(int), s);
+    cudaMemsetAsync(&p->st->err, 0, sizeof(int), s);
+    cudaMemsetAsync(&p->st->done, 0, sizeof(int), s);
+  }
+  for (int r = 0; r < nreal; ++r) {
+    join(P[r]->stream, P[r]->mat->ctx->stream);
+    P[r]->stream = P[r]->mat->ctx->stream;
+  }
+  for (int r = 0; r < S; ++r)
+    if (cudaStreamSynchronize(pool[r]) != cudaSuccess) rc = BO_ERR_CUDA;
+  for (auto e : evs) cudaEventDestroy(e);
+  for (int r = 0; r < nreal && rc == BO_OK; ++r) {
+    const int f = hflags[2 * r] | hflags[2 * r + 1];
+    if (f & kErrPattern) rc = BO_ERR_PATTERN;
+    else if (f & kErrNonfinite) rc = BO_ERR_NONFINITE;
+    else if (f & kErrBreakdown) rc = BO_ERR_BREAKDOWN;
+  }
+  cudaFreeHost(hflags);
   return rc;
 }
 

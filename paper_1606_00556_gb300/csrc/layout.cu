@@ -174,13 +174,13 @@ __global__ void k_axpy1(double* __restrict__ s, const double* __restrict__ d, in
 
 }  // namespace
 
-int ingest_bsr(bo_mat* m, const double* dval) {
-  (k_ingest_bsr<<<grid_for(m->g.N), kThreads, 0, m->ctx->stream>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
+int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s) {
+  (k_ingest_bsr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
-int ingest_csr(bo_mat* m, const double* dval) {
-  (k_ingest_csr<<<grid_for(m->g.N), kThreads, 0, m->ctx->stream>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
+int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s) {
+  (k_ingest_csr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 

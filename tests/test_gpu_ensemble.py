@@ -136,3 +136,33 @@ def test_autotuner_picks_and_caches(tmp_path):
     for x, (Ao, bh) in zip(xs, sys):
         assert oracle.rel_residual(Ao, bh, x.cpu().numpy()) <= 1e-8
     bo.bo_set_batch_streams(16)
+
+
+def test_batched_update_equals_individual_updates():
+    import paper_1606_00556_gb300 as bo
+    ctx = bo.Context(0)
+    specs2 = [dict(sp, seed=sp["seed"] + 100) for sp in SPECS]
+    mats, precs, bs, _ = _ensemble(bo, ctx, 0)
+    mats2, precs2, bs2, _ = _ensemble(bo, ctx, 0)
+    new_vals, sys = [], []
+    for sp in specs2:
+        a = bogen.assemble(bogen.ensemble_case(sp))
+        new_vals.append(torch.tensor(a["val"].reshape(-1), device="cuda"))
+        sys.append((oracle.BsrMatrix(a["rowptr"], a["col"], a["val"]), a["b"]))
+    bo.bo_update_batched(precs, new_vals)
+    for A, P, v in zip(mats2, precs2, new_vals):
+        A.update_values(v)
+        P.update()
+    for P, P2, (Ao, bh) in zip(precs, precs2, sys):
+        b = torch.tensor(bh, device="cuda")
+        x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+        P.solve(b, x1, tol=1e-8)
+        P2.solve(b, x2, tol=1e-8)
+        assert torch.equal(x1, x2)
+        assert oracle.rel_residual(Ao, bh, x1.cpu().numpy()) <= 1e-8
+    # errors are reported: a NaN in one system's values
+    bad = [v.clone() for v in new_vals]
+    bad[2][7] = float("nan")
+    with pytest.raises(bo.BoError) as e:
+        bo.bo_update_batched(precs, bad)
+    assert e.value.status == bo.BO_ERR_NONFINITE
