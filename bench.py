@@ -393,6 +393,68 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_conv(args):
+    """One 32 -> 32 3x3x3 convolution layer of the learned update at
+    64x64x32 voxels, batch 16 (input 134 MB > L2): forward (ReLU) on each
+    engine, data gradient and weight gradient, CUDA-event timed."""
+    import torch
+    import paper_1606_00556_gb300 as bo
+    nx, ny, nz = args.dims if tuple(args.dims) != DIMS else (64, 64, 32)
+    B = args.batch if args.batch != 4 else 16
+    V = nx * ny * nz
+    dev = torch.device("cuda", 0)
+    ctx = bo.Context(0)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev).manual_seed(SEED)
+    x = (torch.randn(B, V, 32, device=dev, generator=g) * 0.5).to(torch.bfloat16)
+    w = (torch.randn(27, 32, 32, device=dev, generator=g) * 0.05).to(torch.bfloat16)
+    bias = torch.zeros(32, device=dev)
+    y = torch.empty(B, V, 32, device=dev, dtype=torch.bfloat16)
+    dx = torch.empty(B, V, 32, device=dev)
+    dy = torch.randn(B, V, 32, device=dev, generator=g)
+    dw = torch.empty(27, 32, 32, device=dev)
+    db = torch.empty(32, device=dev)
+    flops = 2 * 27 * 32 * 32 * V * B
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    res = {}
+    for eng in (0, 1):
+        bo.bo_set_conv_engine(eng)
+        ms = timed(lambda: bo.bo_conv3d_forward(ctx, (nx, ny, nz), x, w, bias, relu=True, y=y))
+        res[f"forward_engine{eng}"] = {"ms": ms, "tflops": flops / ms / 1e9}
+        ms = timed(lambda: bo.bo_conv3d_backward_data(ctx, (nx, ny, nz), y, w, dx))
+        res[f"dgrad_engine{eng}"] = {"ms": ms, "tflops": flops / ms / 1e9, "note": "includes the primitive's scratch alloc"}
+    bo.bo_set_conv_engine(0)
+    tc_ok = bo.bo_tc_status() == bo.BO_OK
+    ms = timed(lambda: bo.bo_conv3d_backward_weights(ctx, (nx, ny, nz), x, dy, dw, db))
+    res["wgrad"] = {"ms": ms, "tflops": flops / ms / 1e9, "note": "includes the primitive's scratch alloc"}
+    best = max(res["forward_engine0"]["tflops"], res["forward_engine1"]["tflops"])
+    line = {"metric": "3x3x3 conv 32->32 forward TFLOP/s (64x64x32, batch 16)", "workload": "conv", "value": best,
+            "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "bf16", "data": "synthetic", "config": {"grid": [nx, ny, nz], "batch": B, "flops": flops,
+                                                            "l2": "input 134 MB > L2"},
+            "roofline": {"bound": "tensor", "kernel": "k_conv3d_tc / k_conv3d_fwd", "achieved": best, "peak": peak,
+                         "peak_kind": kind, "unit": "TFLOP/s", "frac": best / peak, "traffic": None},
+            "kernels": res, "tc_status_ok": tc_ok}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,7 +469,7 @@ def main():
     ap.add_argument("--secondary", default="fp32", choices=["fp32", "fp64", "none"],
                     help="also time the other preconditioner precision on the same Jacobians")
     ap.add_argument("--dist-backend", default="nccl")
-    ap.add_argument("--workload", default="jacobian", choices=["jacobian", "ensemble", "learned"])
+    ap.add_argument("--workload", default="jacobian", choices=["jacobian", "ensemble", "learned", "conv"])
     ap.add_argument("--train", type=int, default=2000, help="training realisations of the learned workload")
     ap.add_argument("--test", type=int, default=200, help="held-out realisations of the learned workload")
     ap.add_argument("--epochs", type=int, default=8)
@@ -425,6 +487,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "conv":
+        return run_conv(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -53,6 +53,7 @@ EXPORTS = (
     "bo_prec_set_coarse_space", "bo_learned_guess",
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
+    "bo_set_conv_engine", "bo_tc_status",
 )
 
 
@@ -157,6 +158,8 @@ def lib():
         L.bo_dp_destroy.argtypes = [_VP]
         L.bo_prec_set_launch_mode.argtypes = [_VP, _i]
         L.bo_set_batch_streams.argtypes = [_i]
+        L.bo_set_conv_engine.argtypes = [_i]
+        L.bo_tc_status.argtypes = []
         L.bo_update_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), _i]
         L.bo_autotune_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                           ctypes.POINTER(bo_solve_opts), ctypes.c_char_p, ctypes.POINTER(bo_tune_result)]
@@ -476,6 +479,15 @@ def bo_update_batched(precs, vals=None):
     else:
         V = (_VP * n)(*[_VP(_dev(v, "float64", "val").value) if v is not None else None for v in vals])
     _check(lib().bo_update_batched(P, n, V, BO_MEM_DEVICE), "bo_update_batched")
+
+
+def bo_set_conv_engine(engine: int):
+    """0: mma.sync, 1: tcgen05 for the 32 -> 32 convolutions."""
+    _check(lib().bo_set_conv_engine(int(engine)), "bo_set_conv_engine")
+
+
+def bo_tc_status() -> int:
+    return int(lib().bo_tc_status())
 
 
 def bo_set_batch_streams(n: int):

@@ -17,6 +17,7 @@
 // Column indices are implied by the stencil and never stored.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -135,6 +136,8 @@ extern std::atomic<long long> g_launches;
 // streams of the batched solve's pool in use (1..kMaxPoolStreams)
 constexpr int kMaxPoolStreams = 16;
 extern std::atomic<int> g_pool_width;
+// convolution engine of the 32 -> 32 layers: 0 mma.sync, 1 tcgen05 (conv_tc.cu)
+extern std::atomic<int> g_conv_engine;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // grid size for a grid-stride loop over n items
@@ -285,6 +288,10 @@ int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double*
                    bo_solve_info* infos);
 int krylov_alloc(bo_prec* P, int m);
 void graphs_reset(bo_prec* P);
+// tcgen05 convolution for 32 -> 32 layers; mode 0 ReLU, 1 ReLU + residual,
+// 2 linear FP32 output.  BO_ERR_ARG where it does not apply.
+int launch_conv_tc(int nx, int ny, int nz, int B, const __nv_bfloat16* X, const __nv_bfloat16* W, const float* bias,
+                   const __nv_bfloat16* R, __nv_bfloat16* Y, float* Yf, int mode, cudaStream_t s);
 // dense FP64 inverse of an n x n matrix (n <= 128) by one block; sets
 // st->err on a zero pivot
 int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, cudaStream_t s);

@@ -16,6 +16,7 @@ using namespace bo;
 namespace bo {
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_pool_width{kMaxPoolStreams};
+std::atomic<int> g_conv_engine{0};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
   static std::mutex mu;
@@ -515,6 +516,12 @@ int bo_prec_residual_history(bo_prec* P, double* buf, int cap) {
 }
 
 int64_t bo_kernel_launches(void) { return g_launches.load(); }
+
+int bo_set_conv_engine(int engine) {
+  if (engine != 0 && engine != 1) return BO_ERR_ARG;
+  g_conv_engine.store(engine);
+  return BO_OK;
+}
 
 int bo_prec_set_launch_mode(bo_prec* P, int mode) {
   if (!P || (mode != BO_LAUNCH_STREAM && mode != BO_LAUNCH_GRAPH)) return BO_ERR_ARG;

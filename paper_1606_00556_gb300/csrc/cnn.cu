@@ -392,6 +392,12 @@ enum FwdMode { kReluBf16, kReluResBf16, kLinearOut, kLinearF32All };
 
 int launch_fwd(int cin, int cout, FwdMode mode, int nx, int ny, int nz, int B, const bf16* X, const bf16* W,
                const float* bias, const bf16* R, bf16* Y, float* Yf, cudaStream_t s) {
+  if (g_conv_engine.load() == 1 && cin == 32 && cout == 32 &&
+      (mode == kReluBf16 || mode == kReluResBf16 || mode == kLinearF32All)) {
+    const int tm = mode == kReluBf16 ? 0 : mode == kReluResBf16 ? 1 : 2;
+    const int rc = launch_conv_tc(nx, ny, nz, B, X, W, bias, R, Y, Yf, tm, s);
+    if (rc != BO_ERR_ARG) return rc;  // else: the mma.sync kernel below
+  }
   if (mode == kReluBf16 && cin == 16 && cout == 32)
     return launch_fwd_t<16, 32, true, false, 0>(nx, ny, nz, B, X, W, bias, R, Y, Yf, s);
   if (mode == kReluBf16 && cin == 32 && cout == 32)

@@ -216,3 +216,50 @@ def test_adam_step_matches_oracle(ctx):
     p1 = net.get_params().astype(np.float64)
     ref, _, _ = O.adam_step(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, 1e-3)
     np.testing.assert_allclose(p1, ref, rtol=1e-6, atol=1e-7)
+
+
+# ---------------------------------------------------------------- tcgen05 engine
+@pytest.fixture
+def tc_engine():
+    bo.bo_set_conv_engine(1)
+    yield
+    assert bo.bo_tc_status() == bo.BO_OK  # no tcgen05 CTA gave up on a barrier
+    bo.bo_set_conv_engine(0)
+
+
+@pytest.mark.parametrize("dims", DIMS + [(64, 64, 8), (16, 16, 3)])
+@pytest.mark.parametrize("mode", ["relu", "relu_res", "f32"])
+def test_tc_conv_forward(ctx, tc_engine, dims, mode):
+    # the tcgen05 kernel against the oracle, with the same tolerances as the mma.sync kernel
+    test_conv_forward(ctx, dims, 32, 32, mode)
+
+
+@pytest.mark.parametrize("dims", DIMS + [(64, 64, 8)])
+def test_tc_conv_backward_data(ctx, tc_engine, dims):
+    test_conv_backward_data(ctx, dims, 32, 32)
+
+
+def test_tc_conv_equals_mma_sync_to_accumulation_order(ctx):
+    # both engines sum the same BF16 products in FP32: FP32 outputs agree to rounding
+    rng = np.random.default_rng(3)
+    dims = (24, 20, 12)
+    nx, ny, nz = dims
+    V, B = nx * ny * nz, 3
+    x = _bf16(rng, (B, V, 32)).cuda()
+    w = _bf16(rng, (27, 32, 32), 0.1).cuda()
+    bias = torch.from_numpy(rng.standard_normal(32) * 0.1).float().cuda()
+    out = []
+    for eng in (0, 1):
+        bo.bo_set_conv_engine(eng)
+        yf = torch.full((B, V, 32), float("nan"), device="cuda")
+        bo.bo_conv3d_forward(ctx, dims, x, w, bias, yf=yf)
+        torch.cuda.synchronize()
+        out.append(yf.cpu().numpy().astype(np.float64))
+    bo.bo_set_conv_engine(0)
+    assert bo.bo_tc_status() == bo.BO_OK
+    mag = O.conv3d(np.abs(_vol(_np(x), dims)), np.abs(_np(w))).reshape(B, V, 32) + np.abs(_np(bias))
+    assert np.all(np.abs(out[0] - out[1]) <= 2e-5 * mag + 1e-30)
+
+
+def test_tc_network_gradient(ctx, tc_engine):
+    test_network_forward_and_gradient(ctx)
