@@ -9,8 +9,14 @@ block-ILU(0) factorisation and AMG setup, CPR-FGMRES(30) to
 ten seeded Jacobians (successive days of a synthetic five-spot waterflood),
 524 MB of matrix values each, so every step's inputs are larger than L2.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
   python bench.py --impl reference ...   # the FP64 CPU oracle, timed alone
+  python bench.py --workload ensemble|learned|conv ...
+
+The default preconditioner precision is the mixed form: FP32 decoupling,
+ILU and AMG inside the FP64 flexible GMRES (Arnoldi, true residual and the
+Newton update in FP64); the FP64 preconditioner is timed beside it
+("secondary").
 
 One JSON line is printed by rank 0.
 """
@@ -461,12 +467,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
+                    help="preconditioner precision: fp32 (mixed: FP32 CPR inside FP64 FGMRES) or fp64")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--jacobians", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="fp32", choices=["fp32", "fp64", "none"],
+    ap.add_argument("--secondary", default="fp64", choices=["fp32", "fp64", "none"],
                     help="also time the other preconditioner precision on the same Jacobians")
     ap.add_argument("--dist-backend", default="nccl")
     ap.add_argument("--workload", default="jacobian", choices=["jacobian", "ensemble", "learned", "conv"])

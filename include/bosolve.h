@@ -377,7 +377,8 @@ int bo_conv3d_backward_weights(bo_ctx* ctx, int nx, int ny, int nz, int batch, i
                                const float* dy, float* dw, float* db);
 /* Convolution engine for the 32 -> 32 layers (forward and data gradient;
  * process-wide): 0 = mma.sync kernel, 1 = tcgen05 kernel (tensor memory
- * accumulator, TMA-fetched tiles).  The other layers always use mma.sync. */
+ * accumulator, TMA-fetched tiles; the default).  The other layers always use
+ * mma.sync. */
 int bo_set_conv_engine(int engine);
 /* BO_ERR_TIMEOUT if a tcgen05 convolution gave up waiting on one of its
  * barriers since the last call (its output is then incomplete), else BO_OK;

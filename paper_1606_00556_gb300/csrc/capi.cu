@@ -16,7 +16,7 @@ using namespace bo;
 namespace bo {
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_pool_width{kMaxPoolStreams};
-std::atomic<int> g_conv_engine{0};
+std::atomic<int> g_conv_engine{1};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
   static std::mutex mu;

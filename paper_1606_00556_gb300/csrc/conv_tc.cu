@@ -42,7 +42,7 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 160;  // warp 0: TMA + MMA issue; warps 1-4: epilogue
 constexpr int kTileX = 8, kTileY = 16;
 constexpr int kHX = 10, kHY = 18, kHZ = 3;
 constexpr int kHaloRows = kHX * kHY * kHZ;                       // 540
@@ -52,8 +52,9 @@ constexpr int kHaloBuf = 4 * kChunkStride;                        // 34816
 constexpr int kWBytes = 27 * 2048;                                // weights, 27 taps x (32 x 32 bf16)
 constexpr int kOffW = 0;
 constexpr int kOffHalo = kWBytes;                                 // 55296 (128-B aligned)
-constexpr int kOffBar = kOffHalo + 2 * kHaloBuf;                  // 124928
-constexpr int kSmemBytes = kOffBar + 64 + 128 + 1024;             // barriers, bias, base-alignment slack
+constexpr int kStages = 3;                                        // halo buffers
+constexpr int kOffBar = kOffHalo + kStages * kHaloBuf;            // 159744
+constexpr int kSmemBytes = kOffBar + 256 + 1024;                  // barriers, TMEM slot, flag, bias; base-alignment slack
 constexpr long kSpinLimit = 1l << 26;
 constexpr uint32_t kTxBytes = 4 * kChunkBytes;
 
@@ -111,7 +112,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// OUT 0: Y = ReLU(conv + bias (+ R)) in BF16;  OUT 1: Yf = conv + bias in FP32
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+
+// OUT 0: Y = ReLU(conv + bias (+ R)) in BF16;  OUT 1: Yf = conv + bias in FP32.
+// Warp 0 (one elected thread) feeds TMA and issues the MMAs of tile k into
+// TMEM accumulator k & 1 while warps 1-4 drain the other accumulator
+// (warp w reads TMEM lanes 32 (w % 4) ..).  Tile k's halo sits in buffer
+// k % 3: the TMA for tile k + 2 goes out right after tile k's MMAs are
+// queued, once tile k - 1's MMAs (queued earlier) have released its buffer,
+// so the tensor pipe never drains while waiting for a copy.  mbarriers:
+//   full[b]     TMA bytes of halo buffer b landed          (TMA -> MMA)
+//   empty[b]    the MMAs reading halo buffer b finished     (MMA -> TMA)
+//   accfull[a]  the MMAs into accumulator a finished        (MMA -> epilogue)
+//   accempty[a] the epilogue finished reading accumulator a (epilogue -> MMA, 4 arrivals)
+// The n-th completion of a barrier has parity n & 1; each side counts the
+// completions it has waited for.
 template <bool RES, int OUT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_constant__ CUtensorMap xmap, int nx, int ny,
                                                            int nz, int B, const bf16* __restrict__ W,
@@ -119,9 +140,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
                                                            bf16* __restrict__ Y, float* __restrict__ Yf) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);  // full[0], full[1], mma
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffBar + 32);
-  float* sbias = reinterpret_cast<float*>(sm + kOffBar + 64);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);  // full[3], empty[3], accfull[2], accempty[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffBar + 80);
+  volatile int* sfail = reinterpret_cast<volatile int*>(sm + kOffBar + 84);
+  float* sbias = reinterpret_cast<float*>(sm + kOffBar + 128);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int V = nx * ny * nz;
   const int ntx = (nx + kTileX - 1) / kTileX, nty = (ny + kTileY - 1) / kTileY;
@@ -133,17 +155,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
     *reinterpret_cast<uint4*>(sm + kOffW + t * 2048 + kc * 512 + co * 16) = w;
   }
   if (tid < 32) sbias[tid] = bias[tid];
-  const uint32_t bar_full0 = smem_u32(&bars[0]), bar_full1 = smem_u32(&bars[1]), bar_mma = smem_u32(&bars[2]);
+  uint32_t full[kStages], empty[kStages], accfull[2], accempty[2];
+  for (int i = 0; i < kStages; ++i) {
+    full[i] = smem_u32(&bars[i]);
+    empty[i] = smem_u32(&bars[kStages + i]);
+  }
+  for (int i = 0; i < 2; ++i) {
+    accfull[i] = smem_u32(&bars[2 * kStages + i]);
+    accempty[i] = smem_u32(&bars[2 * kStages + 2 + i]);
+  }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_full0));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_full1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_mma));
+    for (int i = 0; i < kStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full[i]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty[i]));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accfull[i]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(accempty[i]));
+    }
+    *sfail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(smem_u32(tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -162,35 +198,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
     x0 = tx * kTileX;
     y0 = ty * kTileY;
   };
-  // prefetch the first two tiles; fills / uses count each buffer's TMA
-  // completions issued and consumed (thread 0's bookkeeping)
-  int fills[2] = {0, 0}, uses[2] = {0, 0};
-  bool mma_pending = false;
-  if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      const int t = blockIdx.x + s * gridDim.x;
-      if (t < ntiles) {
+  const int first = blockIdx.x, step = gridDim.x;
+  const int mine = first < ntiles ? (ntiles - 1 - first) / step + 1 : 0;  // tiles of this CTA
+  if (warp == 0) {
+    if (lane == 0) {
+      int fills[kStages] = {0, 0, 0}, uses[kStages] = {0, 0, 0}, commits[kStages] = {0, 0, 0},
+          freed[kStages] = {0, 0, 0};
+      int acc_waits[2] = {0, 0};
+      bool ok = true;
+      for (int s = 0; s < 2 && s < mine; ++s) {
         int x0, y0, z, b;
-        tile_xyzb(t, x0, y0, z, b);
-        tma_halo(&xmap, hbase + s * kHaloBuf, s ? bar_full1 : bar_full0, x0, y0, z, b);
+        tile_xyzb(first + s * step, x0, y0, z, b);
+        tma_halo(&xmap, hbase + s * kHaloBuf, full[s], x0, y0, z, b);
         ++fills[s];
       }
-    }
-  }
-  __shared__ int s_fail;
-  if (tid == 0) s_fail = 0;
-  __syncthreads();
-  int k = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-    const int buf = k & 1;
-    const uint32_t bar_full = buf ? bar_full1 : bar_full0;
-    if (tid == 0) {
-      if (!mbar_wait(bar_full, uses[buf] & 1)) {
-        s_fail = 1;
-      } else {
-        ++uses[buf];
+      for (int k = 0; k < mine && ok; ++k) {
+        const int bf = k % kStages, a = k & 1;
+        if (*sfail) { ok = false; break; }
+        ok = mbar_wait(full[bf], uses[bf] & 1);
+        if (!ok) break;
+        ++uses[bf];
+        if (k >= 2) {  // tile k - 2's epilogue is done with accumulator a
+          ok = mbar_wait(accempty[a], acc_waits[a] & 1);
+          if (!ok) break;
+          ++acc_waits[a];
+        }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t hb = hbase + buf * kHaloBuf;
+        const uint32_t hb = hbase + bf * kHaloBuf;
+        const uint32_t dacc = tmem + (uint32_t)(a * 32);
         for (int tap = 0; tap < 27; ++tap) {
           const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
           const uint32_t rowoff = ((1 + dz) * kHY + (1 + dy)) * kHX + (1 + dx);
@@ -201,97 +236,108 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
             const uint32_t acc = (tap | ks) ? 1u : 0u;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
                 "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
                 : "memory");
           }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_mma)
-                     : "memory");
-        mma_pending = true;
+        umma_commit(empty[bf]);
+        umma_commit(accfull[a]);
+        ++commits[bf];
+        // tile k + 2 goes into the buffer tile k - 1 used, once its MMAs are done
+        if (k + 2 < mine) {
+          const int nb = (k + 2) % kStages;
+          if (commits[nb] > freed[nb]) {
+            ok = mbar_wait(empty[nb], freed[nb] & 1);
+            if (!ok) break;
+            ++freed[nb];
+          }
+          int x0, y0, z, b;
+          tile_xyzb(first + (k + 2) * step, x0, y0, z, b);
+          tma_halo(&xmap, hbase + nb * kHaloBuf, full[nb], x0, y0, z, b);
+          ++fills[nb];
+        }
+      }
+      if (!ok) {
+        *sfail = 1;
+        atomicExch(&g_tc_err, 1);
+        // copies and MMAs in flight finish before shared and tensor memory go away
+        for (int i = 0; i < kStages; ++i) {
+          if (fills[i] > uses[i]) mbar_wait(full[i], uses[i] & 1);
+          while (commits[i] > freed[i] && mbar_wait(empty[i], freed[i] & 1)) ++freed[i];
+        }
       }
     }
-    __syncthreads();
-    if (s_fail) break;
-    if (!mbar_wait(bar_mma, k & 1)) s_fail = 1;  // every thread observes the MMAs' completion
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (s_fail) break;
-    mma_pending = false;
-    // the buffer is free again: fetch tile k + 2 into it
-    if (tid == 0 && t + 2 * gridDim.x < ntiles) {
+    __syncwarp();
+  } else {
+    // epilogue warps: TMEM lane quarter of warp w is w % 4
+    const int quarter = warp & 3;
+    for (int k = 0; k < mine; ++k) {
+      const int a = k & 1;
+      if (!mbar_wait(accfull[a], (k >> 1) & 1)) {
+        *sfail = 1;
+        atomicExch(&g_tc_err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      float acc[32];
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * 32), acc);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accempty[a]);
       int x0, y0, z, b;
-      tile_xyzb(t + 2 * gridDim.x, x0, y0, z, b);
-      tma_halo(&xmap, hbase + buf * kHaloBuf, bar_full, x0, y0, z, b);
-      ++fills[buf];
-    }
-    // epilogue: warp w holds rows 32 w .. 32 w + 31 (row m = x + 8 y of the tile)
-    float acc[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    int x0, y0, z, b;
-    tile_xyzb(t, x0, y0, z, b);
-    const int m = warp * 32 + lane;
-    const int x = x0 + (m & 7), y = y0 + (m >> 3);
-    if (x < nx && y < ny) {
-      const size_t o = ((size_t)b * V + x + (size_t)nx * (y + (size_t)ny * z)) * 32;
-      if (OUT == 0) {
-        float rr[32];
-        if (RES) {
+      tile_xyzb(first + k * step, x0, y0, z, b);
+      const int m = quarter * 32 + lane;
+      const int x = x0 + (m & 7), y = y0 + (m >> 3);
+      if (x < nx && y < ny) {
+        const size_t o = ((size_t)b * V + x + (size_t)nx * (y + (size_t)ny * z)) * 32;
+        if (OUT == 0) {
+          float rr[32];
+          if (RES) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint4 u = *reinterpret_cast<const uint4*>(R + o + 8 * q);
+              const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                rr[8 * q + 2 * e] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[e] & 0xffffu)));
+                rr[8 * q + 2 * e + 1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[e] >> 16)));
+              }
+            }
+          }
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const uint4 u = *reinterpret_cast<const uint4*>(R + o + 8 * q);
-            const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+            uint32_t pk[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              rr[8 * q + 2 * e] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[e] & 0xffffu)));
-              rr[8 * q + 2 * e + 1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[e] >> 16)));
+              const int c0 = 8 * q + 2 * e;
+              float y0v = acc[c0] + sbias[c0], y1v = acc[c0 + 1] + sbias[c0 + 1];
+              if (RES) {
+                y0v += rr[c0];
+                y1v += rr[c0 + 1];
+              }
+              y0v = fmaxf(y0v, 0.f);
+              y1v = fmaxf(y1v, 0.f);
+              pk[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y0v)) |
+                      ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y1v)) << 16);
             }
+            *reinterpret_cast<uint4*>(Y + o + 8 * q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(Yf + o + 4 * q) =
+                make_float4(acc[4 * q] + sbias[4 * q], acc[4 * q + 1] + sbias[4 * q + 1],
+                            acc[4 * q + 2] + sbias[4 * q + 2], acc[4 * q + 3] + sbias[4 * q + 3]);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint32_t pk[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c0 = 8 * q + 2 * e;
-            float y0v = acc[c0] + sbias[c0], y1v = acc[c0 + 1] + sbias[c0 + 1];
-            if (RES) {
-              y0v += rr[c0];
-              y1v += rr[c0 + 1];
-            }
-            y0v = fmaxf(y0v, 0.f);
-            y1v = fmaxf(y1v, 0.f);
-            pk[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y0v)) |
-                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y1v)) << 16);
-          }
-          *reinterpret_cast<uint4*>(Y + o + 8 * q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(Yf + o + 4 * q) =
-              make_float4(acc[4 * q] + sbias[4 * q], acc[4 * q + 1] + sbias[4 * q + 1], acc[4 * q + 2] + sbias[4 * q + 2],
-                          acc[4 * q + 3] + sbias[4 * q + 3]);
       }
+      if (*sfail) break;
     }
-    __syncthreads();  // TMEM reads done before the next tile's MMAs overwrite the accumulator
-  }
-  if (s_fail) {
-    if (tid == 0) {
-      atomicExch(&g_tc_err, 1);
-      // copies and MMAs still in flight finish before the CTA's shared and
-      // tensor memory go away (each wait bounded again)
-      if (fills[0] > uses[0]) mbar_wait(bar_full0, uses[0] & 1);
-      if (fills[1] > uses[1]) mbar_wait(bar_full1, uses[1] & 1);
-      if (mma_pending) mbar_wait(bar_mma, k & 1);
-    }
-    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {

@@ -25,6 +25,7 @@ DIMS = [(10, 7, 5), (24, 20, 12)]  # 350 voxels (3 blocks of 128, ragged tail); 
 def ctx():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    bo.bo_set_conv_engine(0)  # the mma.sync kernels; the tcgen05 tests switch engines themselves
     return bo.Context(0)
 
 
