@@ -602,7 +602,7 @@ def main():
     xs = torch.randn(n, dtype=torch.float64, device=dev)
     ys = torch.zeros_like(xs)
     sp = {}
-    for name, pr, vb in (("fp64", bo.BO_PREC_FP64, 8), ("fp32", bo.BO_PREC_FP32, 4)):
+    for name, pr, vb in (("fp64", bo.BO_PREC_FP64, 8), ("fp32", bo.BO_PREC_FP32, 4), ("bf16", bo.BO_PREC_BF16, 2)):
         for _ in range(3):
             A.spmv(xs, ys, precision=pr)
         s0 = torch.cuda.Event(enable_timing=True)

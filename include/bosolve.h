@@ -56,7 +56,7 @@ typedef enum {
 
 enum { BO_MEM_HOST = 0, BO_MEM_DEVICE = 1 };
 /* arithmetic of the preconditioner (and of bo_mat_spmv's matrix values) */
-enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1 };
+enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1, BO_PREC_BF16 = 2 /* bo_mat_spmv only */ };
 /* How bo_solve issues the kernels of each Arnoldi column: one launch per
  * kernel on the stream, or one CUDA-graph launch per column (captured on
  * first use and replayed; no per-column SpMV timing then). */
@@ -136,9 +136,11 @@ int bo_mat_create_csr(bo_ctx* ctx, const bo_grid* grid, int32_t nrows, int64_t n
 /* New values on the pattern given at create (the next Newton Jacobian). */
 int bo_mat_update_values(bo_mat* A, const double* val, int mem);
 /* y = alpha A x + beta y (paper Sec. 3.3 first basic operation); x, y
- * device vectors of length 3 nx ny nz.  precision BO_PREC_FP32 uses an FP32
- * copy of the values (FP64 vectors, FP32 products, FP64 accumulation is not
- * promised: the sum runs in FP32).  beta = 0 never reads y. */
+ * device vectors of length 3 nx ny nz.  precision BO_PREC_FP64: FP64 values
+ * and sums.  BO_PREC_FP32 / BO_PREC_BF16: a reduced-precision copy of the
+ * values (made on first use after each value update), x rounded to FP32 on
+ * load, products and sums in FP32, y written in FP64 (the reduced-storage
+ * matrix form of the mixed-precision path).  beta = 0 never reads y. */
 int bo_mat_spmv(bo_mat* A, double alpha, const double* x, double beta, double* y, int precision);
 int bo_mat_destroy(bo_mat* A);
 

@@ -32,6 +32,7 @@ BO_MEM_HOST = 0
 BO_MEM_DEVICE = 1
 BO_PREC_FP64 = 0
 BO_PREC_FP32 = 1
+BO_PREC_BF16 = 2
 BO_STAGE_CPR = 0
 BO_STAGE_ILU = 1
 BO_STAGE_AMG = 2

@@ -81,6 +81,9 @@ __host__ __device__ __forceinline__ size_t vidx(const Geom& g, int comp, int col
 // streaming (evict-first) loads for matrix values that are read once per pass
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16* p) {
+  return __ushort_as_bfloat16(__ldcs(reinterpret_cast<const unsigned short*>(p)));
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -179,6 +182,8 @@ struct bo_mat {
   double* A;           // 63 N FP64 values, colour-split planes
   float* A32;          // FP32 copy for bo_mat_spmv(..., BO_PREC_FP32)
   bool a32_valid;
+  __nv_bfloat16* A16;  // BF16 copy for bo_mat_spmv(..., BO_PREC_BF16)
+  bool a16_valid;
   int* flags;          // device error bits
   int* h_flags;        // pinned host copy
 };
@@ -269,7 +274,8 @@ int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s);
 int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s);
 void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
 void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s);
-void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, bool fp32);
+void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision);
+void launch_to_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t s);
 void launch_gather(const Geom& g, const double* nat, double* in, cudaStream_t s);
 void launch_scatter(const Geom& g, const double* in, double* nat, cudaStream_t s);
 void launch_newton_update(double* state, const double* dx, int64_t n, cudaStream_t s);

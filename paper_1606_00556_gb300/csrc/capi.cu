@@ -90,6 +90,7 @@ int load_values(bo_mat* m, const double* val, int mem) {
   int rc = m->kind == 0 ? ingest_bsr(m, dval, m->ctx->stream) : ingest_csr(m, dval, m->ctx->stream);
   if (rc != BO_OK) return rc;
   m->a32_valid = false;
+  m->a16_valid = false;
   return mat_flags(m);
 }
 
@@ -101,6 +102,7 @@ void mat_free(bo_mat* m) {
   cudaFree(m->stage);
   cudaFree(m->A);
   cudaFree(m->A32);
+  cudaFree(m->A16);
   cudaFree(m->flags);
   cudaFreeHost(m->h_flags);
   bo_ctx* c = m->ctx;
@@ -285,13 +287,18 @@ int bo_mat_update_values(bo_mat* m, const double* val, int mem) {
 
 int bo_mat_spmv(bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
   if (!m || !x || !y) return BO_ERR_ARG;
-  if (precision != BO_PREC_FP64 && precision != BO_PREC_FP32) return BO_ERR_ARG;
+  if (precision != BO_PREC_FP64 && precision != BO_PREC_FP32 && precision != BO_PREC_BF16) return BO_ERR_ARG;
   if (precision == BO_PREC_FP32 && !m->a32_valid) {
     if (!m->A32 && cudaMalloc(&m->A32, (size_t)63 * m->g.N * sizeof(float)) != cudaSuccess) return BO_ERR_OOM;
     launch_to_f32(m->A, m->A32, (size_t)63 * m->g.N, m->ctx->stream);
     m->a32_valid = true;
   }
-  launch_spmv_nat(m, alpha, x, beta, y, precision == BO_PREC_FP32);
+  if (precision == BO_PREC_BF16 && !m->a16_valid) {
+    if (!m->A16 && cudaMalloc(&m->A16, (size_t)63 * m->g.N * sizeof(__nv_bfloat16)) != cudaSuccess) return BO_ERR_OOM;
+    launch_to_bf16(m->A, m->A16, (size_t)63 * m->g.N, m->ctx->stream);
+    m->a16_valid = true;
+  }
+  launch_spmv_nat(m, alpha, x, beta, y, precision);
   return cuda_status(cudaGetLastError());
 }
 
@@ -483,6 +490,7 @@ int bo_update_batched(bo_prec* const* P, int nreal, const double* const* val, in
       }
       if (rc == BO_OK) rc = m->kind == 0 ? ingest_bsr(m, dval, s) : ingest_csr(m, dval, s);
       m->a32_valid = false;
+      m->a16_valid = false;
     }
     if (rc == BO_OK) rc = prec_values(p);
     cudaMemcpyAsync(&hflags[2 * r], m->flags, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -227,6 +227,7 @@ int dp_condense(bo_dp* d) {
   (k_dp_condense<<<grid_for(d->N), kThreads, 0, s>>>(d->g, d->val, d->fmap, d->mmap, d->S->A, d->minv, d->flags),
    note_launch());
   d->S->a32_valid = false;
+  d->S->a16_valid = false;
   cudaMemcpyAsync(d->h_flags, d->flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
   if (*d->h_flags & kErrNonfinite) return BO_ERR_NONFINITE;

@@ -116,6 +116,14 @@ __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst
 // per cell; neighbouring lanes alternate colours, so each warp reads 16
 // consecutive values from each colour's plane per load instruction.
 template <typename TM>
+__device__ __forceinline__ float to_f(TM v) { return (float)v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// TA: accumulation type.  FP64 values accumulate in FP64; FP32 and BF16
+// values (the reduced-precision copies) multiply and accumulate in FP32, so
+// they are bound by the bytes they move rather than by the FP64 rate.
+template <typename TM, typename TA>
 __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restrict__ A, const double* __restrict__ x,
                                                       double* __restrict__ y, double alpha, double beta) {
   const int64_t nxy = (int64_t)g.nx * g.ny;
@@ -123,29 +131,40 @@ __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restr
     const Nat n = decode_nat(g, c);
     const unsigned valid = valid_slots(g, n);
     const int64_t off[7] = {-nxy, -(int64_t)g.nx, -1, 0, 1, (int64_t)g.nx, nxy};
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    TA acc0 = 0, acc1 = 0, acc2 = 0;
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       if ((valid >> s) & 1u) {
         const int64_t nc = c + off[s];
-        const double x0 = __ldg(x + 3 * nc), x1 = __ldg(x + 3 * nc + 1), x2 = __ldg(x + 3 * nc + 2);
+        const TA x0 = (TA)__ldg(x + 3 * nc), x1 = (TA)__ldg(x + 3 * nc + 1), x2 = (TA)__ldg(x + 3 * nc + 2);
         const TM* a = A + plane(g, n.color, s, 0) + n.q;
         const size_t P = (size_t)g.Nh;
-        acc0 += (double)ld_stream(a) * x0 + (double)ld_stream(a + P) * x1 + (double)ld_stream(a + 2 * P) * x2;
-        acc1 += (double)ld_stream(a + 3 * P) * x0 + (double)ld_stream(a + 4 * P) * x1 + (double)ld_stream(a + 5 * P) * x2;
-        acc2 += (double)ld_stream(a + 6 * P) * x0 + (double)ld_stream(a + 7 * P) * x1 + (double)ld_stream(a + 8 * P) * x2;
+        if constexpr (sizeof(TA) == 8) {
+          acc0 += (TA)ld_stream(a) * x0 + (TA)ld_stream(a + P) * x1 + (TA)ld_stream(a + 2 * P) * x2;
+          acc1 += (TA)ld_stream(a + 3 * P) * x0 + (TA)ld_stream(a + 4 * P) * x1 + (TA)ld_stream(a + 5 * P) * x2;
+          acc2 += (TA)ld_stream(a + 6 * P) * x0 + (TA)ld_stream(a + 7 * P) * x1 + (TA)ld_stream(a + 8 * P) * x2;
+        } else {
+          acc0 += to_f(ld_stream(a)) * x0 + to_f(ld_stream(a + P)) * x1 + to_f(ld_stream(a + 2 * P)) * x2;
+          acc1 += to_f(ld_stream(a + 3 * P)) * x0 + to_f(ld_stream(a + 4 * P)) * x1 + to_f(ld_stream(a + 5 * P)) * x2;
+          acc2 += to_f(ld_stream(a + 6 * P)) * x0 + to_f(ld_stream(a + 7 * P)) * x1 + to_f(ld_stream(a + 8 * P)) * x2;
+        }
       }
     }
     if (beta == 0.0) {
-      y[3 * c] = alpha * acc0;
-      y[3 * c + 1] = alpha * acc1;
-      y[3 * c + 2] = alpha * acc2;
+      y[3 * c] = alpha * (double)acc0;
+      y[3 * c + 1] = alpha * (double)acc1;
+      y[3 * c + 2] = alpha * (double)acc2;
     } else {
-      y[3 * c] = alpha * acc0 + beta * y[3 * c];
-      y[3 * c + 1] = alpha * acc1 + beta * y[3 * c + 1];
-      y[3 * c + 2] = alpha * acc2 + beta * y[3 * c + 2];
+      y[3 * c] = alpha * (double)acc0 + beta * y[3 * c];
+      y[3 * c + 1] = alpha * (double)acc1 + beta * y[3 * c + 1];
+      y[3 * c + 2] = alpha * (double)acc2 + beta * y[3 * c + 2];
     }
   }
+}
+
+__global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn((float)src[i]);
 }
 
 __global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
@@ -188,12 +207,19 @@ void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
   (k_to_f32<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
 }
 
-void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, bool fp32) {
+void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
   const int grid = grid_for(m->g.N, kThreads, 152 * 64);
-  if (fp32)
-    (k_spmv_nat<float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A32, x, y, alpha, beta), note_launch());
+  if (precision == BO_PREC_FP32)
+    (k_spmv_nat<float, float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A32, x, y, alpha, beta), note_launch());
+  else if (precision == BO_PREC_BF16)
+    (k_spmv_nat<__nv_bfloat16, float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A16, x, y, alpha, beta),
+     note_launch());
   else
-    (k_spmv_nat<double><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A, x, y, alpha, beta), note_launch());
+    (k_spmv_nat<double, double><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A, x, y, alpha, beta), note_launch());
+}
+
+void launch_to_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t s) {
+  (k_to_bf16<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
 }
 
 void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s) {

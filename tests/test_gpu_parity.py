@@ -91,6 +91,18 @@ def test_spmv_fp32_and_alpha_beta(bo, ctx):
     assert np.all(np.abs(y - ref) <= 1e-13 * bound)
     y32 = A.spmv(_dev(x), _dev(y0), alpha=2.0, beta=0.5, precision=bo.BO_PREC_FP32).cpu().numpy()
     assert np.all(np.abs(y32 - ref) <= 1e-5 * bound)
+    # BF16 values (relative rounding 2^-9 per entry), x in FP32, FP32 sums of 21 terms
+    y16 = A.spmv(_dev(x), _dev(y0), alpha=2.0, beta=0.5, precision=bo.BO_PREC_BF16).cpu().numpy()
+    assert np.all(np.abs(y16 - ref) <= 2.0 ** -8 * bound)
+    assert np.abs(y16 - ref).max() > 0  # the copy really is reduced precision
+    # the reduced copies follow value updates
+    a2, Ao2 = _sys(bogen.tiny_case(1))
+    A.update_values(a2["val"])
+    ref2 = oracle.spmv(Ao2, x)
+    b2 = _absprod(Ao2, x)
+    for prec, tol in ((bo.BO_PREC_FP32, 1e-5), (bo.BO_PREC_BF16, 2.0 ** -8)):
+        y2 = A.spmv(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda"), precision=prec).cpu().numpy()
+        assert np.all(np.abs(y2 - ref2) <= tol * b2)
 
 
 def test_spmv_beta_zero_ignores_nan_in_y(bo, ctx):
