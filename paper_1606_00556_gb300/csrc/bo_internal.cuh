@@ -85,6 +85,15 @@ __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16* p) {
   return __ushort_as_bfloat16(__ldcs(reinterpret_cast<const unsigned short*>(p)));
 }
 
+// acc + a0 x0 + a1 x1 + a2 x2 as a chain of three fused multiply-adds (one
+// FP64 instruction per product: the FP64 kernels are bound by FP64 issue)
+__device__ __forceinline__ double fma3(double acc, double a0, double x0, double a1, double x1, double a2, double x2) {
+  return fma(a2, x2, fma(a1, x1, fma(a0, x0, acc)));
+}
+__device__ __forceinline__ float fma3(float acc, float a0, float x0, float a1, float x1, float a2, float x2) {
+  return fmaf(a2, x2, fmaf(a1, x1, fmaf(a0, x0, acc)));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

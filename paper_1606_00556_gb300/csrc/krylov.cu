@@ -58,9 +58,9 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const double*
       const double x0 = z[vidx(g, 0, xc, nq)], x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
       const double* a = A + plane(g, color, sl, 0) + q;
       const size_t P = (size_t)g.Nh;
-      a0 += ld_stream(a) * x0 + ld_stream(a + P) * x1 + ld_stream(a + 2 * P) * x2;
-      a1 += ld_stream(a + 3 * P) * x0 + ld_stream(a + 4 * P) * x1 + ld_stream(a + 5 * P) * x2;
-      a2 += ld_stream(a + 6 * P) * x0 + ld_stream(a + 7 * P) * x1 + ld_stream(a + 8 * P) * x2;
+      a0 = fma3(a0, ld_stream(a), x0, ld_stream(a + P), x1, ld_stream(a + 2 * P), x2);
+      a1 = fma3(a1, ld_stream(a + 3 * P), x0, ld_stream(a + 4 * P), x1, ld_stream(a + 5 * P), x2);
+      a2 = fma3(a2, ld_stream(a + 6 * P), x0, ld_stream(a + 7 * P), x1, ld_stream(a + 8 * P), x2);
     }
     w[t] = a0;
     w[g.N + t] = a1;
@@ -94,9 +94,9 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(Geom g, const double
       const double x0 = x[vidx(g, 0, xc, nq)], x1 = x[vidx(g, 1, xc, nq)], x2 = x[vidx(g, 2, xc, nq)];
       const double* a = A + plane(g, color, sl, 0) + q;
       const size_t P = (size_t)g.Nh;
-      a0 += ld_stream(a) * x0 + ld_stream(a + P) * x1 + ld_stream(a + 2 * P) * x2;
-      a1 += ld_stream(a + 3 * P) * x0 + ld_stream(a + 4 * P) * x1 + ld_stream(a + 5 * P) * x2;
-      a2 += ld_stream(a + 6 * P) * x0 + ld_stream(a + 7 * P) * x1 + ld_stream(a + 8 * P) * x2;
+      a0 = fma3(a0, ld_stream(a), x0, ld_stream(a + P), x1, ld_stream(a + 2 * P), x2);
+      a1 = fma3(a1, ld_stream(a + 3 * P), x0, ld_stream(a + 4 * P), x1, ld_stream(a + 5 * P), x2);
+      a2 = fma3(a2, ld_stream(a + 6 * P), x0, ld_stream(a + 7 * P), x1, ld_stream(a + 8 * P), x2);
     }
     const double r0 = b[t] - a0, r1 = b[g.N + t] - a1, r2 = b[2 * g.N + t] - a2;
     r[t] = r0;

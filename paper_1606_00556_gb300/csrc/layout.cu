@@ -140,13 +140,15 @@ __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restr
         const TM* a = A + plane(g, n.color, s, 0) + n.q;
         const size_t P = (size_t)g.Nh;
         if constexpr (sizeof(TA) == 8) {
-          acc0 += (TA)ld_stream(a) * x0 + (TA)ld_stream(a + P) * x1 + (TA)ld_stream(a + 2 * P) * x2;
-          acc1 += (TA)ld_stream(a + 3 * P) * x0 + (TA)ld_stream(a + 4 * P) * x1 + (TA)ld_stream(a + 5 * P) * x2;
-          acc2 += (TA)ld_stream(a + 6 * P) * x0 + (TA)ld_stream(a + 7 * P) * x1 + (TA)ld_stream(a + 8 * P) * x2;
+          acc0 = fma3(acc0, (TA)ld_stream(a), x0, (TA)ld_stream(a + P), x1, (TA)ld_stream(a + 2 * P), x2);
+          acc1 = fma3(acc1, (TA)ld_stream(a + 3 * P), x0, (TA)ld_stream(a + 4 * P), x1, (TA)ld_stream(a + 5 * P), x2);
+          acc2 = fma3(acc2, (TA)ld_stream(a + 6 * P), x0, (TA)ld_stream(a + 7 * P), x1, (TA)ld_stream(a + 8 * P), x2);
         } else {
-          acc0 += to_f(ld_stream(a)) * x0 + to_f(ld_stream(a + P)) * x1 + to_f(ld_stream(a + 2 * P)) * x2;
-          acc1 += to_f(ld_stream(a + 3 * P)) * x0 + to_f(ld_stream(a + 4 * P)) * x1 + to_f(ld_stream(a + 5 * P)) * x2;
-          acc2 += to_f(ld_stream(a + 6 * P)) * x0 + to_f(ld_stream(a + 7 * P)) * x1 + to_f(ld_stream(a + 8 * P)) * x2;
+          acc0 = fma3(acc0, to_f(ld_stream(a)), x0, to_f(ld_stream(a + P)), x1, to_f(ld_stream(a + 2 * P)), x2);
+          acc1 = fma3(acc1, to_f(ld_stream(a + 3 * P)), x0, to_f(ld_stream(a + 4 * P)), x1, to_f(ld_stream(a + 5 * P)),
+                      x2);
+          acc2 = fma3(acc2, to_f(ld_stream(a + 6 * P)), x0, to_f(ld_stream(a + 7 * P)), x1, to_f(ld_stream(a + 8 * P)),
+                      x2);
         }
       }
     }

@@ -452,9 +452,9 @@ __device__ __forceinline__ void offdiag_sum(const Geom& g, const T* __restrict__
     const T u0 = u[vidx(g, 0, oc, nq)], u1 = u[vidx(g, 1, oc, nq)], u2 = u[vidx(g, 2, oc, nq)];
     const T* a = At + plane(g, color, sl, 0) + q;
     const size_t P = (size_t)g.Nh;
-    s[0] += ld_stream(a) * u0 + ld_stream(a + P) * u1 + ld_stream(a + 2 * P) * u2;
-    s[1] += ld_stream(a + 3 * P) * u0 + ld_stream(a + 4 * P) * u1 + ld_stream(a + 5 * P) * u2;
-    s[2] += ld_stream(a + 6 * P) * u0 + ld_stream(a + 7 * P) * u1 + ld_stream(a + 8 * P) * u2;
+    s[0] = fma3(s[0], ld_stream(a), u0, ld_stream(a + P), u1, ld_stream(a + 2 * P), u2);
+    s[1] = fma3(s[1], ld_stream(a + 3 * P), u0, ld_stream(a + 4 * P), u1, ld_stream(a + 5 * P), u2);
+    s[2] = fma3(s[2], ld_stream(a + 6 * P), u0, ld_stream(a + 7 * P), u1, ld_stream(a + 8 * P), u2);
   }
 }
 
@@ -559,7 +559,8 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
       const size_t P = (size_t)g.Nh;
 #pragma unroll
       for (int r = 0; r < ROWS; ++r)
-        acc[r] += ld_stream(a + 3 * r * P) * x0 + ld_stream(a + (3 * r + 1) * P) * x1 + ld_stream(a + (3 * r + 2) * P) * x2;
+        acc[r] = fma3(acc[r], ld_stream(a + 3 * r * P), x0, ld_stream(a + (3 * r + 1) * P), x1,
+                      ld_stream(a + (3 * r + 2) * P), x2);
     }
     T res[ROWS];
 #pragma unroll
