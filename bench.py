@@ -201,7 +201,7 @@ def run_ensemble(args):
     import paper_1606_00556_gb300 as bo
     dev = torch.device("cuda", 0)
     ctx = bo.Context(0)
-    prec = bo.BO_PREC_FP32 if args.precision == "fp32" else bo.BO_PREC_FP64
+    prec = {"fp32": bo.BO_PREC_FP32, "bf16": bo.BO_PREC_BF16}.get(args.precision, bo.BO_PREC_FP64)
     mats, precs, vals, bs, xs = [], [], [], [], []
     for sp, (rp, cl, v, b) in zip(specs, data):
         A = bo.Matrix.from_bsr(ctx, bo.grid(*sp["dims"]), rp, cl, v)
@@ -255,7 +255,7 @@ def run_ensemble(args):
     line = {"metric": "ensemble solves/s (batched CPR-FGMRES to 1e-8)", "workload": "ensemble",
             "value": len(specs) * args.steps / el, "unit": "solves/s", "higher_is_better": True,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
-            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.precision], "data": "synthetic",
             "config": {"realisations": len(specs), "unknowns": unknowns, "precision": args.precision,
                        "grids": "nx,ny in 32..96 (nx even), nz in 8..24, sigma 0.5..2.0, seed 7"},
             "per_realisation_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
@@ -467,13 +467,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
-                    help="preconditioner precision: fp32 (mixed: FP32 CPR inside FP64 FGMRES) or fp64")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"],
+                    help="preconditioner precision: fp32 (mixed: FP32 CPR inside FP64 FGMRES), bf16 (BF16 "
+                         "storage of the preconditioner, FP32 arithmetic) or fp64")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--jacobians", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="fp64", choices=["fp32", "fp64", "none"],
+    ap.add_argument("--secondary", default="fp64", choices=["fp32", "fp64", "bf16", "none"],
                     help="also time the other preconditioner precision on the same Jacobians")
     ap.add_argument("--dist-backend", default="nccl")
     ap.add_argument("--workload", default="jacobian", choices=["jacobian", "ensemble", "learned", "conv"])
@@ -543,7 +544,7 @@ def main():
     state = torch.from_numpy(jac[0][4]).to(dev)
     g = bo.grid(*dims)
     A = bo.Matrix.from_bsr(ctx, g, rowptr, col, jac[0][2])
-    prec = bo.BO_PREC_FP32 if args.precision == "fp32" else bo.BO_PREC_FP64
+    prec = {"fp32": bo.BO_PREC_FP32, "bf16": bo.BO_PREC_BF16}.get(args.precision, bo.BO_PREC_FP64)
     P = bo.Preconditioner(A, precision=prec)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -622,7 +623,8 @@ def main():
     # inside the FP64 FGMRES (Arnoldi, true residual and update in FP64)
     second = None
     if args.secondary != "none" and args.secondary != args.precision:
-        P2 = bo.Preconditioner(A, precision=bo.BO_PREC_FP32 if args.secondary == "fp32" else bo.BO_PREC_FP64)
+        P2 = bo.Preconditioner(A, precision={"fp32": bo.BO_PREC_FP32, "bf16": bo.BO_PREC_BF16}.get(args.secondary,
+                                                                                                  bo.BO_PREC_FP64))
 
         def step2(k):
             j = k % len(vals)
@@ -677,7 +679,7 @@ def main():
         line = {
             "metric": METRIC, "value": agg["ms_per_solve"], "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": agg["elapsed_ms"] / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.precision],
             "data": "synthetic", "config": config_dict(args),
             "roofline": {"bound": "alu", "kernel": "k_arnoldi_spmv (FP64)", "achieved": ach_tf,
                          "peak": fp64_peak, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",

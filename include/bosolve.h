@@ -56,7 +56,12 @@ typedef enum {
 
 enum { BO_MEM_HOST = 0, BO_MEM_DEVICE = 1 };
 /* arithmetic of the preconditioner (and of bo_mat_spmv's matrix values) */
-enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1, BO_PREC_BF16 = 2 /* bo_mat_spmv only */ };
+/* Preconditioner / reduced-copy precision.  BO_PREC_FP32: the preconditioner
+ * stores and computes in FP32 (mixed precision inside FP64 FGMRES).
+ * BO_PREC_BF16: the preconditioner stores its decoupled matrix, ILU pivot
+ * inverses and AMG coefficients in BF16 and computes in FP32; for
+ * bo_mat_spmv, a BF16 copy of the values with FP32 sums. */
+enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1, BO_PREC_BF16 = 2 };
 /* How bo_solve issues the kernels of each Arnoldi column: one launch per
  * kernel on the stream, or one CUDA-graph launch per column (captured on
  * first use and replayed; no per-column SpMV timing then). */
@@ -79,7 +84,7 @@ typedef struct {
 } bo_grid;
 
 typedef struct {
-  int32_t precision;      /* BO_PREC_FP64 or BO_PREC_FP32 (mixed precision)     */
+  int32_t precision;      /* BO_PREC_FP64, BO_PREC_FP32 or BO_PREC_BF16         */
   int32_t amg_nu1;        /* red-black Gauss-Seidel pre-sweeps  (default 2)      */
   int32_t amg_nu2;        /* post-sweeps (default 2)                             */
   double amg_overcorr;    /* coarse correction scale s: x += s P x_c (default 1.3) */

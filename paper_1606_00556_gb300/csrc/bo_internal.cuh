@@ -216,7 +216,9 @@ struct bo_prec {
   cudaStream_t stream;     // stream of all preconditioner work (the context's, or a batch stream)
   bo_prec_opts opts;
   bool fp32;               // preconditioner arithmetic FP32 (else FP64)
-  size_t tsize;            // sizeof(preconditioner scalar)
+  size_t tsize;            // sizeof(preconditioner vector scalar / arithmetic)
+  size_t ssize;            // sizeof(stored matrix, pivot and AMG coefficient)
+  bool bf16;               // BF16 storage of those (arithmetic FP32)
   void* At;                // 63 N decoupled values (preconditioner precision)
   double* w;               // 3 N decoupling weights (g0, g1, g2) of row 0, [3][N] internal order
   void* Dinv;              // 9 N inverted ILU pivot blocks [rc][N], preconditioner precision

@@ -312,7 +312,8 @@ int bo_prec_setup(bo_mat* m, const bo_prec_opts* opts, bo_prec** out) {
   if (!m || !out) return BO_ERR_ARG;
   bo_prec_opts o;
   prec_opts_fill(opts, &o);
-  if ((o.precision != BO_PREC_FP64 && o.precision != BO_PREC_FP32) || o.amg_nu1 < 0 || o.amg_nu2 < 0 ||
+  if ((o.precision != BO_PREC_FP64 && o.precision != BO_PREC_FP32 && o.precision != BO_PREC_BF16) ||
+      o.amg_nu1 < 0 || o.amg_nu2 < 0 ||
       o.amg_nu1 > 8 || o.amg_nu2 > 8 || o.amg_coarse_max < 1 || o.amg_coarse_max > 128 ||
       !(o.amg_overcorr > 0.0 && o.amg_overcorr < 4.0))
     return BO_ERR_ARG;
@@ -324,8 +325,10 @@ int bo_prec_setup(bo_mat* m, const bo_prec_opts* opts, bo_prec** out) {
   P->stream = m->ctx->stream;
   m->refs++;
   P->opts = o;
-  P->fp32 = o.precision == BO_PREC_FP32;
+  P->fp32 = o.precision != BO_PREC_FP64;
+  P->bf16 = o.precision == BO_PREC_BF16;
   P->tsize = P->fp32 ? sizeof(float) : sizeof(double);
+  P->ssize = P->bf16 ? sizeof(__nv_bfloat16) : P->tsize;
   int rc = prec_alloc(P);
   if (rc == BO_OK) rc = krylov_alloc(P, 30);
   if (rc == BO_OK) rc = prec_refresh(P);

@@ -90,6 +90,20 @@ __device__ __forceinline__ void mul3(const T a[9], const T b[9], T c[9]) {
     for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
 }
 
+// Storage and arithmetic types.  S is the storage type of the matrix-like
+// arrays (decoupled matrix, ILU pivot inverses, AMG coefficients, coarse
+// inverse): double, float or BF16; vectors and arithmetic use T (double for
+// S = double, float otherwise).  cv converts a stored value to T, to_store
+// an FP64 value to S.
+template <typename T, typename S>
+__device__ __forceinline__ T cv(S v) { return (T)v; }
+template <>
+__device__ __forceinline__ float cv<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename S>
+__device__ __forceinline__ S to_store(double v) { return (S)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+
 // ---------------------------------------------------------------- setup kernels
 // Quasi-IMPES decoupling (paper Sec. 3.2): row 0 of each cell becomes
 // g . (row0, row1, row2) with g = (1, -a01/a11, -a02/a22) from the cell's
@@ -98,9 +112,9 @@ __device__ __forceinline__ void mul3(const T a[9], const T b[9], T c[9]) {
 // the water pivot is negative), the cell takes the exact local decoupling,
 // g = row 0 of A_ii^{-1} (pivot 1), which keeps the AMG operator's diagonal
 // positive for the Gauss-Seidel smoother.  Writes the weights [3][N] and the
-// decoupled planes in precision T.
-template <typename T>
-__global__ void k_decouple(Geom g, const double* __restrict__ A, T* __restrict__ At, double* __restrict__ w,
+// decoupled planes in storage type S.
+template <typename S>
+__global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__ At, double* __restrict__ w,
                            DevState* st) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
@@ -134,9 +148,9 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, T* __restrict__
       for (int rc = 0; rc < 9; ++rc) a[rc] = A[plane(g, color, s, rc) + q];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        At[plane(g, color, s, c) + q] = (T)(g0 * a[c] + g1 * a[3 + c] + g2 * a[6 + c]);
-        At[plane(g, color, s, 3 + c) + q] = (T)a[3 + c];
-        At[plane(g, color, s, 6 + c) + q] = (T)a[6 + c];
+        At[plane(g, color, s, c) + q] = to_store<S>(g0 * a[c] + g1 * a[3 + c] + g2 * a[6 + c]);
+        At[plane(g, color, s, 3 + c) + q] = to_store<S>(a[3 + c]);
+        At[plane(g, color, s, 6 + c) + q] = to_store<S>(a[6 + c]);
       }
       if (s == kDiag) {
         const double app = g0 * a[0] + g1 * a[3] + g2 * a[6];
@@ -152,10 +166,10 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, T* __restrict__
 // strongly where the permeability contrast is high, and FP32 arithmetic there
 // can leave the local solver unstable.
 
-// red pivots: D_r^{-1} of the decoupled diagonal blocks, stored in precision
-// T and, for the black pass, in FP64 in `red64` ([rc][N/2])
-template <typename T>
-__global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w, T* __restrict__ Dinv,
+// red pivots: D_r^{-1} of the decoupled diagonal blocks, stored in type S
+// and, for the black pass, in FP64 in `red64` ([rc][N/2])
+template <typename S>
+__global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w, S* __restrict__ Dinv,
                           double* __restrict__ red64, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     double d[9], inv[9];
@@ -165,21 +179,21 @@ __global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __
       for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
     }
     for (int rc = 0; rc < 9; ++rc) {
-      Dinv[(size_t)rc * g.N + q] = (T)inv[rc];
+      Dinv[(size_t)rc * g.N + q] = to_store<S>(inv[rc]);
       red64[(size_t)rc * g.Nh + q] = inv[rc];
     }
   }
 }
 
 // black pivots: D_b' = D_b - sum_r A_br D_r^{-1} A_rb with the FP64 red
-// inverses, stored inverted in precision T
-template <typename T>
+// inverses, stored inverted in type S
+template <typename S>
 __global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* __restrict__ w,
-                            const double* __restrict__ red64, T* __restrict__ Dinv, DevState* st) {
+                            const double* __restrict__ red64, S* __restrict__ Dinv, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
-    double S[9], inv[9];
-    dec_block(g, A, w, 1, kDiag, q, S);
+    double Sc[9], inv[9];
+    dec_block(g, A, w, 1, kDiag, q, Sc);
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       if (s == kDiag) continue;
@@ -191,20 +205,20 @@ __global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* 
       for (int rc = 0; rc < 9; ++rc) Dr[rc] = red64[(size_t)rc * g.Nh + nq];
       mul3(L, Dr, T1);
       mul3(T1, U, T2);
-      for (int rc = 0; rc < 9; ++rc) S[rc] -= T2[rc];
+      for (int rc = 0; rc < 9; ++rc) Sc[rc] -= T2[rc];
     }
-    if (!inv3(S, inv)) {
+    if (!inv3(Sc, inv)) {
       atomicOr(&st->err, kErrBreakdown);
       for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
     }
-    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = (T)inv[rc];
+    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = to_store<S>(inv[rc]);
   }
 }
 
-template <typename T>
-__global__ void k_convert(const double* __restrict__ src, T* __restrict__ dst, size_t n) {
+template <typename S>
+__global__ void k_convert(const double* __restrict__ src, S* __restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = (T)src[i];
+    dst[i] = to_store<S>(src[i]);
 }
 
 // ------------------------------------------------------------ AMG setup
@@ -329,9 +343,9 @@ __global__ void k_dense_from_level(LevelDims L, const double* __restrict__ c64, 
 
 // In-place Gauss-Jordan inversion with partial pivoting of an n x n matrix
 // (n <= kCoarseMax) in shared memory by one thread block; the inverse is
-// written to Minv in precision T.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __restrict__ M, T* __restrict__ Minv, DevState* st) {
+// written to Minv in type S.
+template <typename S>
+__global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __restrict__ M, S* __restrict__ Minv, DevState* st) {
   extern __shared__ double sm[];
   double* a = sm;                 // n * n
   int* perm = (int*)(a + n * n);  // n
@@ -391,7 +405,7 @@ __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __rest
     __syncthreads();
   }
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    Minv[t] = (T)a[t];
+    Minv[t] = to_store<S>(a[t]);
     if (!isfinite(a[t])) atomicOr(&st->err, kErrBreakdown);
   }
 }
@@ -399,9 +413,9 @@ __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __rest
 // ------------------------------------------------------------ apply kernels
 // Entry of the preconditioner: f = D_QI^{-1} v (DEC) or f = v, in precision
 // T, fused with the first ILU pass on the red cells, t_r = D_r^{-1} f_r.
-template <typename T, bool DEC>
+template <typename T, typename S, bool DEC>
 __global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* __restrict__ vs,
-                            const double* __restrict__ w, const T* __restrict__ Dinv, T* __restrict__ f,
+                            const double* __restrict__ w, const S* __restrict__ Dinv, T* __restrict__ f,
                             T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
   const double sc = vs ? *vs : 1.0;  // scale of an unnormalised Krylov vector
@@ -415,7 +429,7 @@ __global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* 
     if (t < g.Nh) {
       T d[9];
 #pragma unroll
-      for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + t];
+      for (int rc = 0; rc < 9; ++rc) d[rc] = cv<T>(Dinv[(size_t)rc * g.N + t]);
       tv[t] = d[0] * f0 + d[1] * f1 + d[2] * f2;
       tv[g.N + t] = d[3] * f0 + d[4] * f1 + d[5] * f2;
       tv[2 * g.N + t] = d[6] * f0 + d[7] * f1 + d[8] * f2;
@@ -439,8 +453,8 @@ __global__ void k_copy_vec(int64_t n, const double* __restrict__ v, T* __restric
 
 // sum over the six off-diagonal blocks of a row of At times the other
 // colour's vector u: s = sum_s At[color][s] u[nbr]
-template <typename T>
-__device__ __forceinline__ void offdiag_sum(const Geom& g, const T* __restrict__ At, int color, int64_t q,
+template <typename T, typename S>
+__device__ __forceinline__ void offdiag_sum(const Geom& g, const S* __restrict__ At, int color, int64_t q,
                                             const Cell& c, const T* __restrict__ u, T s[3]) {
   const int oc = color ^ 1;
   s[0] = s[1] = s[2] = T(0);
@@ -450,11 +464,11 @@ __device__ __forceinline__ void offdiag_sum(const Geom& g, const T* __restrict__
     const int64_t nq = nbr(g, c, q, sl);
     if (nq < 0) continue;
     const T u0 = u[vidx(g, 0, oc, nq)], u1 = u[vidx(g, 1, oc, nq)], u2 = u[vidx(g, 2, oc, nq)];
-    const T* a = At + plane(g, color, sl, 0) + q;
+    const S* a = At + plane(g, color, sl, 0) + q;
     const size_t P = (size_t)g.Nh;
-    s[0] = fma3(s[0], ld_stream(a), u0, ld_stream(a + P), u1, ld_stream(a + 2 * P), u2);
-    s[1] = fma3(s[1], ld_stream(a + 3 * P), u0, ld_stream(a + 4 * P), u1, ld_stream(a + 5 * P), u2);
-    s[2] = fma3(s[2], ld_stream(a + 6 * P), u0, ld_stream(a + 7 * P), u1, ld_stream(a + 8 * P), u2);
+    s[0] = fma3(s[0], cv<T>(ld_stream(a)), u0, cv<T>(ld_stream(a + P)), u1, cv<T>(ld_stream(a + 2 * P)), u2);
+    s[1] = fma3(s[1], cv<T>(ld_stream(a + 3 * P)), u0, cv<T>(ld_stream(a + 4 * P)), u1, cv<T>(ld_stream(a + 5 * P)), u2);
+    s[2] = fma3(s[2], cv<T>(ld_stream(a + 6 * P)), u0, cv<T>(ld_stream(a + 7 * P)), u1, cv<T>(ld_stream(a + 8 * P)), u2);
   }
 }
 
@@ -469,8 +483,8 @@ constexpr int ilu_min_blocks() { return sizeof(T) == 4 ? 4 : 3; }
 template <typename T, int ROWS>
 constexpr int res_min_blocks() { return (sizeof(T) == 4 && ROWS == 1) ? 5 : 4; }
 
-template <typename T, bool OUT>
-__global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ src,
+template <typename T, typename S, bool OUT>
+__global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g, const S* __restrict__ At, const S* __restrict__ Dinv, const T* __restrict__ src,
                         T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
                         const DevState* st) {
   if (st->done) return;
@@ -481,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g,
     const T r0 = src[vidx(g, 0, 1, q)] - s[0], r1 = src[vidx(g, 1, 1, q)] - s[1], r2 = src[vidx(g, 2, 1, q)] - s[2];
     T d[9];
 #pragma unroll
-    for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + g.Nh + q];
+    for (int rc = 0; rc < 9; ++rc) d[rc] = cv<T>(Dinv[(size_t)rc * g.N + g.Nh + q]);
     const T u0 = d[0] * r0 + d[1] * r1 + d[2] * r2;
     const T u1 = d[3] * r0 + d[4] * r1 + d[5] * r2;
     const T u2 = d[6] * r0 + d[7] * r1 + d[8] * r2;
@@ -503,8 +517,8 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g,
 // ILU pass 3 (red): corr = D_r^{-1} sum A_rb u_b, with u_b in `ub` (black half).
 // OUT = false: z_r = t_r - corr (precision T).
 // OUT = true: zo_r = z1_r + Pi_p e_r + t_r - corr, in FP64.
-template <typename T, bool OUT>
-__global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g, const T* __restrict__ At, const T* __restrict__ Dinv, const T* __restrict__ tv,
+template <typename T, typename S, bool OUT>
+__global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g, const S* __restrict__ At, const S* __restrict__ Dinv, const T* __restrict__ tv,
                          const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
                          const DevState* st) {
   if (st->done) return;
@@ -514,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g
     offdiag_sum(g, At, 0, q, c, ub, s);
     T d[9];
 #pragma unroll
-    for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + q];
+    for (int rc = 0; rc < 9; ++rc) d[rc] = cv<T>(Dinv[(size_t)rc * g.N + q]);
     const T c0 = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
     const T c1 = d[3] * s[0] + d[4] * s[1] + d[5] * s[2];
     const T c2 = d[6] * s[0] + d[7] * s[1] + d[8] * s[2];
@@ -535,9 +549,9 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g
 // ROWS = 1: out[t] = f_p - (At z)_p for all cells (the AMG right-hand side).
 // ROWS = 3: out = f - At (z + Pi_p e), all components, fused with the first
 //   ILU pass of the second local solve on red cells: tv_r = D_r^{-1} out_r.
-template <typename T, int ROWS>
-__global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_residual(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
-                               const T* __restrict__ e, T* __restrict__ out, const T* __restrict__ Dinv,
+template <typename T, typename S, int ROWS>
+__global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_residual(Geom g, const S* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
+                               const T* __restrict__ e, T* __restrict__ out, const S* __restrict__ Dinv,
                                T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -555,12 +569,12 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
       T x0 = z[vidx(g, 0, xc, nq)];
       if (ROWS == 3) x0 += e[(size_t)xc * g.Nh + nq];
       const T x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
-      const T* a = At + plane(g, color, sl, 0) + q;
+      const S* a = At + plane(g, color, sl, 0) + q;
       const size_t P = (size_t)g.Nh;
 #pragma unroll
       for (int r = 0; r < ROWS; ++r)
-        acc[r] = fma3(acc[r], ld_stream(a + 3 * r * P), x0, ld_stream(a + (3 * r + 1) * P), x1,
-                      ld_stream(a + (3 * r + 2) * P), x2);
+        acc[r] = fma3(acc[r], cv<T>(ld_stream(a + 3 * r * P)), x0, cv<T>(ld_stream(a + (3 * r + 1) * P)), x1,
+                      cv<T>(ld_stream(a + (3 * r + 2) * P)), x2);
     }
     T res[ROWS];
 #pragma unroll
@@ -571,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
     if (ROWS == 3 && color == 0) {
       T d[9];
 #pragma unroll
-      for (int rc = 0; rc < 9; ++rc) d[rc] = Dinv[(size_t)rc * g.N + q];
+      for (int rc = 0; rc < 9; ++rc) d[rc] = cv<T>(Dinv[(size_t)rc * g.N + q]);
       tv[t] = d[0] * res[0] + d[1] * res[1 % ROWS] + d[2] * res[2 % ROWS];
       tv[g.N + t] = d[3] * res[0] + d[4] * res[1 % ROWS] + d[5] * res[2 % ROWS];
       tv[2 * g.N + t] = d[6] * res[0] + d[7] * res[1 % ROWS] + d[8] * res[2 % ROWS];
@@ -580,8 +594,8 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
 }
 
 // ---- AMG level 0 (colour-split, coefficients = plane (colour, slot, 0) of At)
-template <typename T>
-__global__ void k_gs0(Geom g, const T* __restrict__ At, const T* __restrict__ f, T* __restrict__ x, int color,
+template <typename T, typename S>
+__global__ void k_gs0(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x, int color,
                       int zero_guess, const DevState* st) {
   if (st->done) return;
   const int oc = color ^ 1;
@@ -594,10 +608,10 @@ __global__ void k_gs0(Geom g, const T* __restrict__ At, const T* __restrict__ f,
         if (sl == kDiag) continue;
         const int64_t nq = nbr(g, c, q, sl);
         if (nq < 0) continue;
-        s -= At[plane(g, color, sl, 0) + q] * x[(size_t)oc * g.Nh + nq];
+        s -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)oc * g.Nh + nq];
       }
     }
-    x[(size_t)color * g.Nh + q] = s / At[plane(g, color, kDiag, 0) + q];
+    x[(size_t)color * g.Nh + q] = s / cv<T>(At[plane(g, color, kDiag, 0) + q]);
   }
 }
 
@@ -606,8 +620,8 @@ __global__ void k_gs0(Geom g, const T* __restrict__ At, const T* __restrict__ f,
 // equals prolongating x += s P x_c on every cell and then sweeping the black
 // cells, because the black sweep overwrites x_b and the red sweep that
 // follows overwrites x_r without reading its old value.
-template <typename T>
-__global__ void k_gs0_prolong(Geom g, const T* __restrict__ At, const T* __restrict__ f, T* __restrict__ x,
+template <typename T, typename S>
+__global__ void k_gs0_prolong(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x,
                               LevelDims C, const T* __restrict__ xc, T sc, const DevState* st) {
   if (st->done) return;
   const int di[7] = {0, 0, -1, 0, 1, 0, 0}, dj[7] = {0, -1, 0, 0, 0, 1, 0}, dk[7] = {-1, 0, 0, 0, 0, 0, 1};
@@ -620,16 +634,16 @@ __global__ void k_gs0_prolong(Geom g, const T* __restrict__ At, const T* __restr
       const int64_t nq = nbr(g, c, q, sl);
       if (nq < 0) continue;
       const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
-      s -= At[plane(g, 1, sl, 0) + q] * xv;
+      s -= cv<T>(At[plane(g, 1, sl, 0) + q]) * xv;
     }
-    x[(size_t)g.Nh + q] = s / At[plane(g, 1, kDiag, 0) + q];
+    x[(size_t)g.Nh + q] = s / cv<T>(At[plane(g, 1, kDiag, 0) + q]);
   }
 }
 
 // f1[I] = sum of level-0 residuals over aggregate I (red cells only when
 // the last half sweep was black)
-template <typename T>
-__global__ void k_restrict0(Geom g, const T* __restrict__ At, const T* __restrict__ f, const T* __restrict__ x,
+template <typename T, typename S>
+__global__ void k_restrict0(Geom g, const S* __restrict__ At, const T* __restrict__ f, const T* __restrict__ x,
                             LevelDims C, T* __restrict__ fc, int red_only, const DevState* st) {
   if (st->done) return;
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
@@ -650,7 +664,7 @@ __global__ void k_restrict0(Geom g, const T* __restrict__ At, const T* __restric
             const int64_t nq = nbr(g, c, q, sl);
             if (nq < 0) continue;
             const int xc = (sl == kDiag) ? color : (color ^ 1);
-            r -= At[plane(g, color, sl, 0) + q] * x[(size_t)xc * g.Nh + nq];
+            r -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)xc * g.Nh + nq];
           }
           acc += r;
         }
@@ -671,47 +685,48 @@ __global__ void k_prolong0(Geom g, T* __restrict__ x, LevelDims C, const T* __re
 
 // ---- natural-order levels (device functions shared by the multi-block
 // kernels and the single-block tail)
-template <typename T>
+template <typename T, typename S = T>
 struct LevelView {
   LevelDims d;
-  const T* c;  // 7 n coefficients
+  const S* c;  // 7 n coefficients (storage type)
   T* f;
   T* x;
+  __device__ __forceinline__ T cc(int slot, int64_t cidx) const { return cv<T>(c[slot * d.n + cidx]); }
 };
 
-template <typename T>
-__device__ __forceinline__ void gs_cell(const LevelView<T>& L, int64_t cidx, int color, int zero_guess) {
+template <typename T, typename S>
+__device__ __forceinline__ void gs_cell(const LevelView<T, S>& L, int64_t cidx, int color, int zero_guess) {
   const int i = (int)(cidx % L.d.nx), j = (int)((cidx / L.d.nx) % L.d.ny), k = (int)(cidx / ((int64_t)L.d.nx * L.d.ny));
   if (((i + j + k) & 1) != color) return;
   T s = L.f[cidx];
   if (!zero_guess) {
     const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-    if (k > 0) s -= L.c[kZm * L.d.n + cidx] * L.x[cidx - nxy];
-    if (j > 0) s -= L.c[kYm * L.d.n + cidx] * L.x[cidx - L.d.nx];
-    if (i > 0) s -= L.c[kXm * L.d.n + cidx] * L.x[cidx - 1];
-    if (i < L.d.nx - 1) s -= L.c[kXp * L.d.n + cidx] * L.x[cidx + 1];
-    if (j < L.d.ny - 1) s -= L.c[kYp * L.d.n + cidx] * L.x[cidx + L.d.nx];
-    if (k < L.d.nz - 1) s -= L.c[kZp * L.d.n + cidx] * L.x[cidx + nxy];
+    if (k > 0) s -= L.cc(kZm, cidx) * L.x[cidx - nxy];
+    if (j > 0) s -= L.cc(kYm, cidx) * L.x[cidx - L.d.nx];
+    if (i > 0) s -= L.cc(kXm, cidx) * L.x[cidx - 1];
+    if (i < L.d.nx - 1) s -= L.cc(kXp, cidx) * L.x[cidx + 1];
+    if (j < L.d.ny - 1) s -= L.cc(kYp, cidx) * L.x[cidx + L.d.nx];
+    if (k < L.d.nz - 1) s -= L.cc(kZp, cidx) * L.x[cidx + nxy];
   }
-  L.x[cidx] = s / L.c[kDiag * L.d.n + cidx];
+  L.x[cidx] = s / L.cc(kDiag, cidx);
 }
 
-template <typename T>
-__device__ __forceinline__ T residual_cell(const LevelView<T>& L, int i, int j, int k) {
+template <typename T, typename S>
+__device__ __forceinline__ T residual_cell(const LevelView<T, S>& L, int i, int j, int k) {
   const int64_t cidx = nat_index(L.d, i, j, k);
   const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-  T r = L.f[cidx] - L.c[kDiag * L.d.n + cidx] * L.x[cidx];
-  if (k > 0) r -= L.c[kZm * L.d.n + cidx] * L.x[cidx - nxy];
-  if (j > 0) r -= L.c[kYm * L.d.n + cidx] * L.x[cidx - L.d.nx];
-  if (i > 0) r -= L.c[kXm * L.d.n + cidx] * L.x[cidx - 1];
-  if (i < L.d.nx - 1) r -= L.c[kXp * L.d.n + cidx] * L.x[cidx + 1];
-  if (j < L.d.ny - 1) r -= L.c[kYp * L.d.n + cidx] * L.x[cidx + L.d.nx];
-  if (k < L.d.nz - 1) r -= L.c[kZp * L.d.n + cidx] * L.x[cidx + nxy];
+  T r = L.f[cidx] - L.cc(kDiag, cidx) * L.x[cidx];
+  if (k > 0) r -= L.cc(kZm, cidx) * L.x[cidx - nxy];
+  if (j > 0) r -= L.cc(kYm, cidx) * L.x[cidx - L.d.nx];
+  if (i > 0) r -= L.cc(kXm, cidx) * L.x[cidx - 1];
+  if (i < L.d.nx - 1) r -= L.cc(kXp, cidx) * L.x[cidx + 1];
+  if (j < L.d.ny - 1) r -= L.cc(kYp, cidx) * L.x[cidx + L.d.nx];
+  if (k < L.d.nz - 1) r -= L.cc(kZp, cidx) * L.x[cidx + nxy];
   return r;
 }
 
-template <typename T>
-__device__ __forceinline__ T restrict_cell(const LevelView<T>& F, const LevelDims& C, int64_t I, int red_only) {
+template <typename T, typename S>
+__device__ __forceinline__ T restrict_cell(const LevelView<T, S>& F, const LevelDims& C, int64_t I, int red_only) {
   const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
   T acc = T(0);
   for (int dk = 0; dk < 2; ++dk)
@@ -725,76 +740,76 @@ __device__ __forceinline__ T restrict_cell(const LevelView<T>& F, const LevelDim
   return acc;
 }
 
-template <typename T>
-__device__ __forceinline__ void prolong_cell(const LevelView<T>& F, const LevelView<T>& C, int64_t cidx, T s) {
+template <typename T, typename S>
+__device__ __forceinline__ void prolong_cell(const LevelView<T, S>& F, const LevelView<T, S>& C, int64_t cidx, T s) {
   const int i = (int)(cidx % F.d.nx), j = (int)((cidx / F.d.nx) % F.d.ny), k = (int)(cidx / ((int64_t)F.d.nx * F.d.ny));
   F.x[cidx] += s * C.x[nat_index(C.d, i / 2, j / 2, k / 2)];
 }
 
 // black half sweep with the coarse correction of the red neighbours folded in
 // (the natural-order counterpart of k_gs0_prolong)
-template <typename T>
-__device__ __forceinline__ void gs_cell_prolong(const LevelView<T>& L, const LevelView<T>& C, int64_t cidx, T sc) {
+template <typename T, typename S>
+__device__ __forceinline__ void gs_cell_prolong(const LevelView<T, S>& L, const LevelView<T, S>& C, int64_t cidx, T sc) {
   const int i = (int)(cidx % L.d.nx), j = (int)((cidx / L.d.nx) % L.d.ny), k = (int)(cidx / ((int64_t)L.d.nx * L.d.ny));
   if (((i + j + k) & 1) != 1) return;
   const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
   T s = L.f[cidx];
-  if (k > 0) s -= L.c[kZm * L.d.n + cidx] * (L.x[cidx - nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k - 1) / 2)]);
-  if (j > 0) s -= L.c[kYm * L.d.n + cidx] * (L.x[cidx - L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j - 1) / 2, k / 2)]);
-  if (i > 0) s -= L.c[kXm * L.d.n + cidx] * (L.x[cidx - 1] + sc * C.x[nat_index(C.d, (i - 1) / 2, j / 2, k / 2)]);
+  if (k > 0) s -= L.cc(kZm, cidx) * (L.x[cidx - nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k - 1) / 2)]);
+  if (j > 0) s -= L.cc(kYm, cidx) * (L.x[cidx - L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j - 1) / 2, k / 2)]);
+  if (i > 0) s -= L.cc(kXm, cidx) * (L.x[cidx - 1] + sc * C.x[nat_index(C.d, (i - 1) / 2, j / 2, k / 2)]);
   if (i < L.d.nx - 1)
-    s -= L.c[kXp * L.d.n + cidx] * (L.x[cidx + 1] + sc * C.x[nat_index(C.d, (i + 1) / 2, j / 2, k / 2)]);
+    s -= L.cc(kXp, cidx) * (L.x[cidx + 1] + sc * C.x[nat_index(C.d, (i + 1) / 2, j / 2, k / 2)]);
   if (j < L.d.ny - 1)
-    s -= L.c[kYp * L.d.n + cidx] * (L.x[cidx + L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j + 1) / 2, k / 2)]);
+    s -= L.cc(kYp, cidx) * (L.x[cidx + L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j + 1) / 2, k / 2)]);
   if (k < L.d.nz - 1)
-    s -= L.c[kZp * L.d.n + cidx] * (L.x[cidx + nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k + 1) / 2)]);
-  L.x[cidx] = s / L.c[kDiag * L.d.n + cidx];
+    s -= L.cc(kZp, cidx) * (L.x[cidx + nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k + 1) / 2)]);
+  L.x[cidx] = s / L.cc(kDiag, cidx);
 }
 
-template <typename T>
-__global__ void k_gsn_prolong(LevelView<T> L, LevelView<T> C, T sc, const DevState* st) {
+template <typename T, typename S>
+__global__ void k_gsn_prolong(LevelView<T, S> L, LevelView<T, S> C, T sc, const DevState* st) {
   if (st->done) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.d.n; c += (int64_t)gridDim.x * blockDim.x)
     gs_cell_prolong(L, C, c, sc);
 }
 
-template <typename T>
-__global__ void k_gsn(LevelView<T> L, int color, int zero_guess, const DevState* st) {
+template <typename T, typename S>
+__global__ void k_gsn(LevelView<T, S> L, int color, int zero_guess, const DevState* st) {
   if (st->done) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.d.n; c += (int64_t)gridDim.x * blockDim.x)
     gs_cell(L, c, color, zero_guess);
 }
 
-template <typename T>
-__global__ void k_restrictn(LevelView<T> F, LevelView<T> C, int red_only, const DevState* st) {
+template <typename T, typename S>
+__global__ void k_restrictn(LevelView<T, S> F, LevelView<T, S> C, int red_only, const DevState* st) {
   if (st->done) return;
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.d.n; I += (int64_t)gridDim.x * blockDim.x)
     C.f[I] = restrict_cell(F, C.d, I, red_only);
 }
 
-template <typename T>
-__global__ void k_prolongn(LevelView<T> F, LevelView<T> C, T s, const DevState* st) {
+template <typename T, typename S>
+__global__ void k_prolongn(LevelView<T, S> F, LevelView<T, S> C, T s, const DevState* st) {
   if (st->done) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < F.d.n; c += (int64_t)gridDim.x * blockDim.x)
     prolong_cell(F, C, c, s);
 }
 
-template <typename T>
+template <typename T, typename S>
 struct TailArgs {
   int first, last;  // levels first..last (last = coarsest)
   int nu1, nu2;
   T s;
-  LevelView<T> lv[24];
-  const T* inv;     // dense inverse of level `last`
+  LevelView<T, S> lv[24];
+  const S* inv;     // dense inverse of level `last`
 };
 
 // x_first = V-cycle(f_first) over levels first..last by one thread block
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const DevState* st) {
+template <typename T, typename S>
+__global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T, S> a, const DevState* st) {
   if (st->done) return;
   const int nt = blockDim.x;
   for (int l = a.first; l < a.last; ++l) {
-    const LevelView<T>& L = a.lv[l];
+    const LevelView<T, S>& L = a.lv[l];
     if (a.nu1 == 0) {
       for (int64_t c = threadIdx.x; c < L.d.n; c += nt) L.x[c] = T(0);
       __syncthreads();
@@ -804,23 +819,23 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const DevS
         for (int64_t c = threadIdx.x; c < L.d.n; c += nt) gs_cell(L, c, color, sw == 0 && color == 0);
         __syncthreads();
       }
-    const LevelView<T>& C = a.lv[l + 1];
+    const LevelView<T, S>& C = a.lv[l + 1];
     for (int64_t I = threadIdx.x; I < C.d.n; I += nt) C.f[I] = restrict_cell(L, C.d, I, a.nu1 > 0);
     __syncthreads();
   }
   {
-    const LevelView<T>& C = a.lv[a.last];
+    const LevelView<T, S>& C = a.lv[a.last];
     const int64_t n = C.d.n;
     for (int64_t i = threadIdx.x; i < n; i += nt) {
       T s = T(0);
-      for (int64_t j = 0; j < n; ++j) s += a.inv[i * n + j] * C.f[j];
+      for (int64_t j = 0; j < n; ++j) s += cv<T>(a.inv[i * n + j]) * C.f[j];
       C.x[i] = s;
     }
     __syncthreads();
   }
   for (int l = a.last - 1; l >= a.first; --l) {
-    const LevelView<T>& L = a.lv[l];
-    const LevelView<T>& C = a.lv[l + 1];
+    const LevelView<T, S>& L = a.lv[l];
+    const LevelView<T, S>& C = a.lv[l + 1];
     if (a.nu2 == 0) {
       for (int64_t c = threadIdx.x; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
       __syncthreads();
@@ -837,13 +852,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a, const DevS
 }
 
 // dense solve on level 0 when level 0 is the coarsest: x = inv f
-template <typename T>
-__global__ void k_dense0(int64_t n, const T* __restrict__ inv, const T* __restrict__ f, T* __restrict__ x,
+template <typename T, typename S>
+__global__ void k_dense0(int64_t n, const S* __restrict__ inv, const T* __restrict__ f, T* __restrict__ x,
                          const DevState* st) {
   if (st->done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
-    for (int64_t j = 0; j < n; ++j) s += inv[i * n + j] * f[j];
+    for (int64_t j = 0; j < n; ++j) s += cv<T>(inv[i * n + j]) * f[j];
     x[i] = s;
   }
 }
@@ -888,64 +903,64 @@ __global__ void k_spmv_dec64(Geom g, const double* __restrict__ A, const double*
 }
 
 // ---------------------------------------------------------------- host side
-template <typename T>
-LevelView<T> view(bo_prec* P, int l) {
+template <typename T, typename S>
+LevelView<T, S> view(bo_prec* P, int l) {
   const Level& L = P->lev[l];
-  return LevelView<T>{LevelDims{L.nx, L.ny, L.nz, L.n}, (const T*)L.c, (T*)L.f, (T*)L.x};
+  return LevelView<T, S>{LevelDims{L.nx, L.ny, L.nz, L.n}, (const S*)L.c, (T*)L.f, (T*)L.x};
 }
 
 LevelDims dims_of(const Level& L) { return LevelDims{L.nx, L.ny, L.nz, L.n}; }
 
-template <typename T>
+template <typename T, typename S>
 void amg_vcycle(bo_prec* P, const DevState* st) {
   cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
-  const T* At = (const T*)P->At;
+  const S* At = (const S*)P->At;
   T* f0 = (T*)P->f0;
   T* x0 = (T*)P->e0;
   const int nu1 = P->opts.amg_nu1, nu2 = P->opts.amg_nu2;
   const T sc = (T)P->opts.amg_overcorr;
   if (P->nlev == 1) {
-    (k_dense0<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, (const T*)P->coarse_inv, f0, x0, st), note_launch());
+    (k_dense0<T, S><<<grid_for(g.N), kThreads, 0, s>>>(g.N, (const S*)P->coarse_inv, f0, x0, st), note_launch());
     return;
   }
   const int ghalf = grid_for(g.Nh);
   for (int sw = 0; sw < nu1; ++sw) {
-    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
-    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+    (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
+    (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
   }
   if (nu1 == 0) (k_zero<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, x0, st), note_launch());
-  (k_restrict0<T><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (T*)P->lev[1].f,
+  (k_restrict0<T, S><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (T*)P->lev[1].f,
                                                              nu1 > 0, st), note_launch());
   // multi-block natural levels down to the tail
   const int last = P->nlev - 1;
   for (int l = 1; l < P->tail_from; ++l) {
-    LevelView<T> L = view<T>(P, l), C = view<T>(P, l + 1);
+    LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
     const int gl = grid_for(L.d.n);
     for (int sw = 0; sw < nu1; ++sw) {
-      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 0, sw == 0, st), note_launch());
-      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+      (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, sw == 0, st), note_launch());
+      (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
     }
     if (nu1 == 0) (k_zero<T><<<gl, kThreads, 0, s>>>(L.d.n, L.x, st), note_launch());
-    (k_restrictn<T><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
+    (k_restrictn<T, S><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
   }
-  TailArgs<T> ta;
+  TailArgs<T, S> ta;
   ta.first = P->tail_from;
   ta.last = last;
   ta.nu1 = nu1;
   ta.nu2 = nu2;
   ta.s = sc;
-  for (int l = 1; l <= last; ++l) ta.lv[l] = view<T>(P, l);
-  ta.inv = (const T*)P->coarse_inv;
-  (k_tail<T><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+  for (int l = 1; l <= last; ++l) ta.lv[l] = view<T, S>(P, l);
+  ta.inv = (const S*)P->coarse_inv;
+  (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
   for (int l = P->tail_from - 1; l >= 1; --l) {
-    LevelView<T> L = view<T>(P, l), C = view<T>(P, l + 1);
+    LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
     const int gl = grid_for(L.d.n);
-    if (nu2 == 0) (k_prolongn<T><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+    if (nu2 == 0) (k_prolongn<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
     for (int sw = 0; sw < nu2; ++sw) {
-      if (sw == 0) (k_gsn_prolong<T><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
-      else (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
-      (k_gsn<T><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
+      if (sw == 0) (k_gsn_prolong<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+      else (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+      (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
     }
   }
   if (nu2 == 0)
@@ -953,22 +968,22 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
      note_launch());
   for (int sw = 0; sw < nu2; ++sw) {
     if (sw == 0)
-      (k_gs0_prolong<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
+      (k_gs0_prolong<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
        note_launch());
     else
-      (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
-    (k_gs0<T><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, 0, st), note_launch());
+      (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+    (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, 0, st), note_launch());
   }
 }
 
 // z = CPR stage applied to v (FP64, internal order); result FP64 in zo
-template <typename T>
+template <typename T, typename S>
 void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevState* st, const double* vs) {
   cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
-  const T* At = (const T*)P->At;
-  const T* D = (const T*)P->Dinv;
+  const S* At = (const S*)P->At;
+  const S* D = (const S*)P->Dinv;
   T* f = (T*)P->f;
   T* tv = (T*)P->t;
   T* r = (T*)P->r;
@@ -977,24 +992,24 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
   T* z1 = (T*)P->z1;
   if (stage == BO_STAGE_AMG) {  // (v is a caller's vector here: vs is NULL)
     (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v, f0, st), note_launch());
-    amg_vcycle<T>(P, st);
+    amg_vcycle<T, S>(P, st);
     learned_coarse_apply(P, st);
     (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo, st), note_launch());
     return;
   }
   // x1 = R^{-1} f with f = D_QI^{-1} v (stage CPR) or f = v
   if (stage == BO_STAGE_CPR)
-    (k_cpr_entry<T, true><<<occ_grid((const void*)k_cpr_entry<T, true>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
+    (k_cpr_entry<T, S, true><<<occ_grid((const void*)k_cpr_entry<T, S, true>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
                                                                                                   f, tv, st),
      note_launch());
   else
-    (k_cpr_entry<T, false><<<occ_grid((const void*)k_cpr_entry<T, false>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
+    (k_cpr_entry<T, S, false><<<occ_grid((const void*)k_cpr_entry<T, S, false>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
                                                                                                     f, tv, st),
      note_launch());
-  (k_ilu_b<T, false><<<occ_grid((const void*)k_ilu_b<T, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
+  (k_ilu_b<T, S, false><<<occ_grid((const void*)k_ilu_b<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
                                                                                           nullptr, st),
    note_launch());
-  (k_ilu_r2<T, false><<<occ_grid((const void*)k_ilu_r2<T, false>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, z1, z1,
+  (k_ilu_r2<T, S, false><<<occ_grid((const void*)k_ilu_r2<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, z1, z1,
                                                                                             nullptr, nullptr, st),
    note_launch());
   if (stage == BO_STAGE_ILU) {
@@ -1002,34 +1017,34 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
     return;
   }
   // x2 = x1 + Pi_p AMG(A_pp)^{-1} Pi_r (f - At x1)
-  (k_cpr_residual<T, 1><<<occ_grid((const void*)k_cpr_residual<T, 1>, g.N), kThreads, 0, s>>>(
+  (k_cpr_residual<T, S, 1><<<occ_grid((const void*)k_cpr_residual<T, S, 1>, g.N), kThreads, 0, s>>>(
        g, At, f, z1, nullptr, f0, nullptr, nullptr, st),
    note_launch());
-  amg_vcycle<T>(P, st);
+  amg_vcycle<T, S>(P, st);
   learned_coarse_apply(P, st);
   // r = f - At x2 (with the red pass of R^{-1} r fused);  x3 = x2 + R^{-1} r
-  (k_cpr_residual<T, 3><<<occ_grid((const void*)k_cpr_residual<T, 3>, g.N), kThreads, 0, s>>>(g, At, f, z1, e0, r,
+  (k_cpr_residual<T, S, 3><<<occ_grid((const void*)k_cpr_residual<T, S, 3>, g.N), kThreads, 0, s>>>(g, At, f, z1, e0, r,
                                                                                                 D, tv, st),
    note_launch());
-  (k_ilu_b<T, true><<<occ_grid((const void*)k_ilu_b<T, true>, g.Nh), kThreads, 0, s>>>(g, At, D, r, tv, z1, e0, zo,
+  (k_ilu_b<T, S, true><<<occ_grid((const void*)k_ilu_b<T, S, true>, g.Nh), kThreads, 0, s>>>(g, At, D, r, tv, z1, e0, zo,
                                                                                         st),
    note_launch());
-  (k_ilu_r2<T, true><<<occ_grid((const void*)k_ilu_r2<T, true>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, tv, z1, e0,
+  (k_ilu_r2<T, S, true><<<occ_grid((const void*)k_ilu_r2<T, S, true>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, tv, z1, e0,
                                                                                           zo, st),
    note_launch());
 }
 
-template <typename T>
+template <typename S>
 int values_impl(bo_prec* P) {
   bo_mat* m = P->mat;
   cudaStream_t s = P->stream;
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
-  (k_decouple<T><<<gN, kThreads, 0, s>>>(g, m->A, (T*)P->At, P->w, P->st), note_launch());
+  (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, (S*)P->At, P->w, P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
-  (k_ilu_red<T><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (T*)P->Dinv, red64, P->st), note_launch());
-  (k_ilu_black<T><<<gh, kThreads, 0, s>>>(g, m->A, P->w, red64, (T*)P->Dinv, P->st), note_launch());
+  (k_ilu_red<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
+  (k_ilu_black<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, red64, (S*)P->Dinv, P->st), note_launch());
   // AMG hierarchy values
   for (int l = 1; l < P->nlev; ++l) {
     Level& C = P->lev[l];
@@ -1038,7 +1053,7 @@ int values_impl(bo_prec* P) {
     else
       (k_galerkinn<<<grid_for(C.n), kThreads, 0, s>>>(dims_of(P->lev[l - 1]), P->lev[l - 1].c64, dims_of(C), C.c64,
                                                      P->st), note_launch());
-    (k_convert<T><<<grid_for(7 * C.n), kThreads, 0, s>>>(C.c64, (T*)C.c, (size_t)7 * C.n), note_launch());
+    (k_convert<S><<<grid_for(7 * C.n), kThreads, 0, s>>>(C.c64, (S*)C.c, (size_t)7 * C.n), note_launch());
   }
   const int last = P->nlev - 1;
   LevelDims cd = last == 0 ? LevelDims{g.nx, g.ny, g.nz, g.N} : dims_of(P->lev[last]);
@@ -1046,8 +1061,8 @@ int values_impl(bo_prec* P) {
                                             P->coarse64), note_launch());
   const int n = (int)P->ncoarse;
   const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
-  cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  (k_gj_inverse<T><<<1, 1024, smem, s>>>(n, P->coarse64, (T*)P->coarse_inv, P->st), note_launch());
+  cudaFuncSetAttribute(k_gj_inverse<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (k_gj_inverse<S><<<1, 1024, smem, s>>>(n, P->coarse64, (S*)P->coarse_inv, P->st), note_launch());
   if (cudaGetLastError() != cudaSuccess) return BO_ERR_CUDA;
   return learned_coarse_values(P);
 }
@@ -1063,9 +1078,10 @@ int prec_alloc(bo_prec* P) {
     if (ok && cudaMalloc(&p, bytes) != cudaSuccess) { ok = false; return nullptr; }
     return p;
   };
-  P->At = al((size_t)63 * g.N * ts);
+  const size_t ss = P->ssize;  // storage of the matrix-like arrays
+  P->At = al((size_t)63 * g.N * ss);
   P->w = (double*)al((size_t)3 * g.N * sizeof(double));
-  P->Dinv = al((size_t)9 * g.N * ts);
+  P->Dinv = al((size_t)9 * g.N * ss);
   P->f = al((size_t)3 * g.N * ts);
   P->t = al((size_t)3 * g.N * ts);
   P->r = al((size_t)3 * g.N * ts);
@@ -1084,7 +1100,7 @@ int prec_alloc(bo_prec* P) {
     Level& L = P->lev[P->nlev];
     L.nx = nx; L.ny = ny; L.nz = nz; L.n = n;
     L.c64 = (double*)al((size_t)7 * n * sizeof(double));
-    L.c = al((size_t)7 * n * ts);
+    L.c = al((size_t)7 * n * ss);
     L.f = al((size_t)n * ts);
     L.x = al((size_t)n * ts);
     P->nlev++;
@@ -1096,7 +1112,7 @@ int prec_alloc(bo_prec* P) {
     if (P->lev[l].n <= kTailCells) { P->tail_from = l; break; }
   if (P->tail_from < 1) P->tail_from = 1;
   P->coarse64 = (double*)al((size_t)n * n * sizeof(double));
-  P->coarse_inv = al((size_t)n * n * ts);
+  P->coarse_inv = al((size_t)n * n * ss);
   if (ok && cudaMalloc(&P->st, sizeof(DevState)) != cudaSuccess) ok = false;
   if (ok) cudaMemsetAsync(P->st, 0, sizeof(DevState), P->stream);
   return ok ? BO_OK : BO_ERR_OOM;
@@ -1115,6 +1131,7 @@ void prec_free(bo_prec* P) {
 }
 
 int prec_values(bo_prec* P) {
+  if (P->bf16) return values_impl<__nv_bfloat16>(P);
   return P->fp32 ? values_impl<float>(P) : values_impl<double>(P);
 }
 
@@ -1127,8 +1144,9 @@ int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, c
 }
 
 void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs) {
-  if (P->fp32) cpr_apply<float>(P, v, z, stage, st, vs);
-  else cpr_apply<double>(P, v, z, stage, st, vs);
+  if (P->bf16) cpr_apply<float, __nv_bfloat16>(P, v, z, stage, st, vs);
+  else if (P->fp32) cpr_apply<float, float>(P, v, z, stage, st, vs);
+  else cpr_apply<double, double>(P, v, z, stage, st, vs);
 }
 
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {

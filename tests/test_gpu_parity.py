@@ -256,7 +256,7 @@ def _xref(Ao, b):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_tiny_matches_oracle(bo, ctx, seed, precision):
     dims = (20, 20, 5)
     a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(seed), dims, precision=precision)
@@ -352,7 +352,7 @@ def test_newton_update(bo, ctx):
     assert torch.equal(s.cpu(), torch.arange(30, dtype=torch.float64) + 0.5)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_waterflood_1m_cells(bo, ctx, precision):
     # the benchmark workload: 128 x 128 x 64, 3.1M unknowns, launch sizes as
     # timed; checked through the oracle's compensated FP64 residual
@@ -367,14 +367,15 @@ def test_solve_waterflood_1m_cells(bo, ctx, precision):
     assert oracle.rel_residual(Ao, a["b"], x.cpu().numpy()) <= 1e-8
     # the oracle's own CPR-GMRES(30) (same AMG, modified Gram-Schmidt) needs
     # 20 iterations on this Jacobian; a loss of orthogonality shows here first
-    assert info["iters"] <= 26, info
+    # (BF16 storage of the preconditioner weakens it: a looser budget there)
+    assert info["iters"] <= (26 if precision < 2 else 60), info
     # sampled SpMV outputs at full size
     xs = np.random.default_rng(12).standard_normal(Ao.n)
     y = A.spmv(_dev(xs), torch.zeros_like(b)).cpu().numpy()
     assert np.all(np.abs(y - oracle.spmv(Ao, xs)) <= 1e-13 * _absprod(Ao, xs))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_flooded_injector_decoupling_matches_oracle(bo, ctx, precision):
     # injector cells swept to residual oil take the exact local decoupling
     # (Quasi-IMPES would give them a negative pressure pivot)
@@ -386,7 +387,7 @@ def test_flooded_injector_decoupling_matches_oracle(bo, ctx, precision):
     x = np.random.default_rng(14).standard_normal(Ao.n)
     y = P.spmv_decoupled(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
     assert np.all(np.abs(y - oracle.spmv(At, x)) <= 1e-12 * _absprod(At, x) + 1e-300)
-    tol = 1e-9 if precision == 0 else 1e-4
+    tol = {0: 1e-9, 1: 1e-4, 2: 5e-2}[precision]
     for st, ost in [(bo.BO_STAGE_CPR, oracle.STAGE_CPR), (bo.BO_STAGE_AMG, oracle.STAGE_AMG)]:
         Po = oracle.cpr_prec(Ao, dims, amg=_oracle_amg(), stage=ost)
         z = P.apply(st, _dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
@@ -395,3 +396,23 @@ def test_flooded_injector_decoupling_matches_oracle(bo, ctx, precision):
     xs = torch.zeros(Ao.n, dtype=torch.float64, device="cuda")
     info = P.solve(_dev(a["b"]), xs, tol=1e-8)
     assert info["status"] == 0 and oracle.rel_residual(Ao, a["b"], xs.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("stage", ["ilu", "amg", "cpr"])
+def test_bf16_storage_stages_track_oracle(bo, ctx, stage):
+    # BF16 storage (relative rounding 2^-9 per stored value) with FP32
+    # arithmetic: each stage's output stays within a few percent of the FP64
+    # oracle's, and is not bitwise the FP32-storage result
+    dims = (20, 20, 5)
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(4, *dims), dims, precision=2)
+    _, _, _, P32 = _cpr_pair(bo, ctx, bogen.tiny_case(4, *dims), dims, precision=1)
+    st = {"ilu": (bo.BO_STAGE_ILU, oracle.STAGE_ILU), "amg": (bo.BO_STAGE_AMG, oracle.STAGE_AMG),
+          "cpr": (bo.BO_STAGE_CPR, oracle.STAGE_CPR)}[stage]
+    Po = oracle.cpr_prec(Ao, dims, ordering=oracle.ORDER_RED_BLACK, amg=_oracle_amg(), stage=st[1])
+    r = np.random.default_rng(9).standard_normal(Ao.n)
+    z16 = P.apply(st[0], _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    z32 = P32.apply(st[0], _dev(r), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = Po.apply(r)
+    assert np.linalg.norm(z16 - ref) <= 5e-2 * np.linalg.norm(ref)
+    assert np.linalg.norm(z32 - ref) <= 1e-4 * np.linalg.norm(ref)
+    assert not np.array_equal(z16, z32)
