@@ -29,6 +29,7 @@ namespace {
 constexpr int kTailThreads = 1024;
 constexpr int64_t kTailCells = 4096;
 constexpr int kCoarseMax = 128;
+constexpr size_t kTailSmemMax = 200 * 1024;  // stage the tail levels in shared memory up to this size
 
 // ---------------------------------------------------------------- 3x3 blocks
 // inverse by Gauss-Jordan elimination with partial pivoting; false if a
@@ -805,8 +806,7 @@ struct TailArgs {
 
 // x_first = V-cycle(f_first) over levels first..last by one thread block
 template <typename T, typename S>
-__global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T, S> a, const DevState* st) {
-  if (st->done) return;
+__device__ void tail_cycle(const TailArgs<T, S>& a) {
   const int nt = blockDim.x;
   for (int l = a.first; l < a.last; ++l) {
     const LevelView<T, S>& L = a.lv[l];
@@ -849,6 +849,66 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T, S> a, const D
         __syncthreads();
       }
   }
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T, S> a, const DevState* st) {
+  if (st->done) return;
+  tail_cycle(a);
+}
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// shared-memory bytes that k_tail_smem needs for levels first..last
+template <typename T, typename S>
+__host__ __device__ size_t tail_smem_bytes(const TailArgs<T, S>& a) {
+  size_t b = 0;
+  for (int l = a.first; l <= a.last; ++l)
+    b += align16(7 * a.lv[l].d.n * sizeof(S)) + 2 * align16(a.lv[l].d.n * sizeof(T));
+  return b + align16((size_t)a.lv[a.last].d.n * a.lv[a.last].d.n * sizeof(S));
+}
+
+// The same V-cycle with the tail levels staged in shared memory: their
+// coefficients, right-hand sides and iterates, and the coarse inverse, are
+// copied in once, every sweep then reads shared memory instead of L2, and
+// only the first tail level's iterate (read by the next finer level's
+// prolongation) is copied back.
+template <typename T, typename S>
+__global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, const DevState* st) {
+  if (st->done) return;
+  extern __shared__ __align__(16) uint8_t tsm[];
+  __shared__ TailArgs<T, S> b;
+  if (threadIdx.x == 0) {
+    b = a;
+    size_t off = 0;
+    for (int l = a.first; l <= a.last; ++l) {
+      const int64_t n = a.lv[l].d.n;
+      b.lv[l].c = reinterpret_cast<const S*>(tsm + off);
+      off += align16(7 * n * sizeof(S));
+      b.lv[l].f = reinterpret_cast<T*>(tsm + off);
+      off += align16(n * sizeof(T));
+      b.lv[l].x = reinterpret_cast<T*>(tsm + off);
+      off += align16(n * sizeof(T));
+    }
+    b.inv = reinterpret_cast<const S*>(tsm + off);
+  }
+  __syncthreads();
+  for (int l = a.first; l <= a.last; ++l) {
+    const int64_t n = a.lv[l].d.n;
+    S* c = const_cast<S*>(b.lv[l].c);
+    for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = a.lv[l].c[i];
+  }
+  {
+    const int64_t n = a.lv[a.first].d.n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.lv[a.first].f[i] = a.lv[a.first].f[i];
+    const int64_t nc = a.lv[a.last].d.n;
+    S* inv = const_cast<S*>(b.inv);
+    for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = a.inv[i];
+  }
+  __syncthreads();
+  tail_cycle(b);
+  const int64_t n = a.lv[a.first].d.n;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a.lv[a.first].x[i] = b.lv[a.first].x[i];
 }
 
 // dense solve on level 0 when level 0 is the coarsest: x = inv f
@@ -952,7 +1012,13 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   ta.s = sc;
   for (int l = 1; l <= last; ++l) ta.lv[l] = view<T, S>(P, l);
   ta.inv = (const S*)P->coarse_inv;
-  (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+  const size_t tb = tail_smem_bytes(ta);
+  if (tb <= kTailSmemMax) {
+    cudaFuncSetAttribute(k_tail_smem<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);
+    (k_tail_smem<T, S><<<1, kTailThreads, tb, s>>>(ta, st), note_launch());
+  } else {
+    (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+  }
   for (int l = P->tail_from - 1; l >= 1; --l) {
     LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
     const int gl = grid_for(L.d.n);
