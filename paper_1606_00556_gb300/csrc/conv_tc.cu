@@ -42,7 +42,7 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kTcThreads = 160;  // warp 0: TMA + MMA issue; warps 1-4: epilogue
+constexpr int kTcThreads = 288;  // warp 0: TMA + MMA issue; warps 1-8: epilogue
 constexpr int kTileX = 8, kTileY = 16;
 constexpr int kHX = 10, kHY = 18, kHZ = 3;
 constexpr int kHaloRows = kHX * kHY * kHZ;                       // 540
@@ -120,17 +120,29 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // OUT 0: Y = ReLU(conv + bias (+ R)) in BF16;  OUT 1: Yf = conv + bias in FP32.
 // Warp 0 (one elected thread) feeds TMA and issues the MMAs of tile k into
-// TMEM accumulator k & 1 while warps 1-4 drain the other accumulator
-// (warp w reads TMEM lanes 32 (w % 4) ..).  Tile k's halo sits in buffer
+// TMEM accumulator k & 1 while warps 1-8 drain the other accumulator
+// (warp w reads TMEM lanes 32 (w % 4) .. and output channels 16 ((w - 1) / 4) ..).  Tile k's halo sits in buffer
 // k % 3: the TMA for tile k + 2 goes out right after tile k's MMAs are
 // queued, once tile k - 1's MMAs (queued earlier) have released its buffer,
 // so the tensor pipe never drains while waiting for a copy.  mbarriers:
 //   full[b]     TMA bytes of halo buffer b landed          (TMA -> MMA)
 //   empty[b]    the MMAs reading halo buffer b finished     (MMA -> TMA)
 //   accfull[a]  the MMAs into accumulator a finished        (MMA -> epilogue)
-//   accempty[a] the epilogue finished reading accumulator a (epilogue -> MMA, 4 arrivals)
+//   accempty[a] the epilogue finished reading accumulator a (epilogue -> MMA, 8 arrivals)
 // The n-th completion of a barrier has parity n & 1; each side counts the
 // completions it has waited for.
 template <bool RES, int OUT>
@@ -171,7 +183,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
     }
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accfull[i]));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(accempty[i]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(accempty[i]));
     }
     *sfail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -270,8 +282,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
     }
     __syncwarp();
   } else {
-    // epilogue warps: TMEM lane quarter of warp w is w % 4
-    const int quarter = warp & 3;
+    // epilogue warps: TMEM lane quarter w % 4, output channels 16 ((w - 1) / 4) .. + 15
+    const int quarter = warp & 3, ch0 = 16 * ((warp - 1) >> 2);
     for (int k = 0; k < mine; ++k) {
       const int a = k & 1;
       if (!mbar_wait(accfull[a], (k >> 1) & 1)) {
@@ -280,8 +292,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      float acc[32];
-      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * 32), acc);
+      float acc[16];
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * 32 + ch0), acc);
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(accempty[a]);
@@ -290,12 +302,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
       const int m = quarter * 32 + lane;
       const int x = x0 + (m & 7), y = y0 + (m >> 3);
       if (x < nx && y < ny) {
-        const size_t o = ((size_t)b * V + x + (size_t)nx * (y + (size_t)ny * z)) * 32;
+        const size_t o = ((size_t)b * V + x + (size_t)nx * (y + (size_t)ny * z)) * 32 + ch0;
         if (OUT == 0) {
-          float rr[32];
+          float rr[16];
           if (RES) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
               const uint4 u = *reinterpret_cast<const uint4*>(R + o + 8 * q);
               const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -306,12 +318,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
             }
           }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 2; ++q) {
             uint32_t pk[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int c0 = 8 * q + 2 * e;
-              float y0v = acc[c0] + sbias[c0], y1v = acc[c0 + 1] + sbias[c0 + 1];
+              float y0v = acc[c0] + sbias[ch0 + c0], y1v = acc[c0 + 1] + sbias[ch0 + c0 + 1];
               if (RES) {
                 y0v += rr[c0];
                 y1v += rr[c0 + 1];
@@ -325,10 +337,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
+          for (int q = 0; q < 4; ++q)
             *reinterpret_cast<float4*>(Yf + o + 4 * q) =
-                make_float4(acc[4 * q] + sbias[4 * q], acc[4 * q + 1] + sbias[4 * q + 1],
-                            acc[4 * q + 2] + sbias[4 * q + 2], acc[4 * q + 3] + sbias[4 * q + 3]);
+                make_float4(acc[4 * q] + sbias[ch0 + 4 * q], acc[4 * q + 1] + sbias[ch0 + 4 * q + 1],
+                            acc[4 * q + 2] + sbias[ch0 + 4 * q + 2], acc[4 * q + 3] + sbias[ch0 + 4 * q + 3]);
         }
       }
       if (*sfail) break;
