@@ -120,6 +120,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def make_reduce_max(dist, device):
+    """max over ranks of a host float (identity without a process group)."""
+    def reduce_max(v):
+        if dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return reduce_max
+
+
+def rank_seed(rank):
+    """Each rank of a multi-GPU run solves its own seeded Jacobians (replicas)."""
+    return SEED + 1000 * rank
+
+
 def aggregate(elapsed_ms, units, world, reduce_max):
     """Whole-job numbers: the max elapsed time over ranks; every rank solved
     `units` Jacobians, so the job solved units * world in that time."""
@@ -504,7 +521,7 @@ def main():
 
     # inputs first (spawned generator workers must start before CUDA)
     dims = tuple(args.dims)
-    jac = generate(dims, SEED + 1000 * rank, args.jacobians, procs=min(16, os.cpu_count() or 1))
+    jac = generate(dims, rank_seed(rank), args.jacobians, procs=min(16, os.cpu_count() or 1))
     cpu_rec = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -524,12 +541,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def reduce_max(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda" if args.dist_backend == "nccl" else "cpu")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    reduce_max = make_reduce_max(dist, "cuda" if args.dist_backend == "nccl" else "cpu")
 
     bo.lib()
     dev = torch.device("cuda", local)
