@@ -120,6 +120,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def bind_near_gpu(index):
+    """Run on the CPUs next to the GPU (its PCI device's local_cpulist), so
+    that pinned host buffers allocated afterwards are first touched on the
+    GPU's own memory node; returns the CPU list, or None where unknown."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, bus, rest = out.lower().split(":")
+        path = f"/sys/bus/pci/devices/{dom[-4:]}:{bus}:{rest}/local_cpulist"
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if cpus and len(cpus) < len(os.sched_getaffinity(0)):
+            os.sched_setaffinity(0, cpus)
+            return sorted(cpus)
+    except Exception:
+        pass
+    return None
+
+
 def make_reduce_max(dist, device):
     """max over ranks of a host float (identity without a process group)."""
     def reduce_max(v):
@@ -532,6 +556,7 @@ def main():
     import torch
     import paper_1606_00556_gb300 as bo
     torch.cuda.set_device(local)
+    numa_cpus = bind_near_gpu(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -684,7 +709,8 @@ def main():
         te = (time.perf_counter() - t0) * 1e3
         te = reduce_max(te)
         e2e = {"value": te / (args.e2e_steps * world), "unit": "ms", "h2d_bytes_per_step": 9 * 8 * nnzb + n * 8,
-               "d2h_bytes_per_step": n * 8}
+               "d2h_bytes_per_step": n * 8,
+               "host_cpus": f"{len(numa_cpus)} CPUs local to the GPU" if numa_cpus else "unbound"}
 
     if rank == 0:
         iters = [i["iters"] for i in infos]

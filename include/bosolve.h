@@ -387,6 +387,15 @@ int bo_conv3d_backward_weights(bo_ctx* ctx, int nx, int ny, int nz, int batch, i
  * accumulator, TMA-fetched tiles; the default).  The other layers always use
  * mma.sync. */
 int bo_set_conv_engine(int engine);
+/* How the AMG V-cycle launches its multi-block levels (process-wide):
+ * 1 (the default) = two cooperative launches per V-cycle, a down leg and an
+ * up leg, whose blocks meet at grid-wide barriers between the Gauss-Seidel
+ * half sweeps of paper Sec. 3.2's pressure AMG stage; 0 = one kernel per half
+ * sweep, restriction and prolongation.  Both compute the same V-cycle.
+ * Inside stream capture (CUDA-graph launch mode) the per-kernel form is used
+ * whatever the setting.  A barrier that waits too long ends the launch and
+ * the solve returns BO_ERR_TIMEOUT.  BO_ERR_ARG for another mode. */
+int bo_set_amg_cooperative(int on);
 /* BO_ERR_TIMEOUT if a tcgen05 convolution gave up waiting on one of its
  * barriers since the last call (its output is then incomplete), else BO_OK;
  * clears the flag.  Synchronises the device. */

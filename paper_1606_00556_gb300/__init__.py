@@ -54,7 +54,7 @@ EXPORTS = (
     "bo_prec_set_coarse_space", "bo_learned_guess",
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
-    "bo_set_conv_engine", "bo_tc_status",
+    "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative",
 )
 
 
@@ -160,6 +160,7 @@ def lib():
         L.bo_prec_set_launch_mode.argtypes = [_VP, _i]
         L.bo_set_batch_streams.argtypes = [_i]
         L.bo_set_conv_engine.argtypes = [_i]
+        L.bo_set_amg_cooperative.argtypes = [_i]
         L.bo_tc_status.argtypes = []
         L.bo_update_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), _i]
         L.bo_autotune_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -480,6 +481,12 @@ def bo_update_batched(precs, vals=None):
     else:
         V = (_VP * n)(*[_VP(_dev(v, "float64", "val").value) if v is not None else None for v in vals])
     _check(lib().bo_update_batched(P, n, V, BO_MEM_DEVICE), "bo_update_batched")
+
+
+def bo_set_amg_cooperative(on: int):
+    """1: the AMG's multi-block levels as two cooperative launches per
+    V-cycle (grid barriers between half sweeps); 0: one kernel per sweep."""
+    _check(lib().bo_set_amg_cooperative(int(on)), "bo_set_amg_cooperative")
 
 
 def bo_set_conv_engine(engine: int):

@@ -78,6 +78,16 @@ __host__ __device__ __forceinline__ size_t vidx(const Geom& g, int comp, int col
   return (size_t)comp * (size_t)g.N + (size_t)color * (size_t)g.Nh + (size_t)q;
 }
 
+// Split copy of the matrix (A2, read by the Arnoldi product) in a tiled
+// layout: the 63 values of 32 consecutive half indices of one colour form a
+// contiguous 16 KB tile, [colour][q / 32][slot * 9 + rc][q % 32], so the 63
+// loads of a warp stream one contiguous region instead of 63 planes.
+__host__ __device__ __forceinline__ int64_t a2_tiles(const Geom& g) { return (g.Nh + 31) / 32; }
+__host__ __device__ __forceinline__ size_t a2_size(const Geom& g) { return (size_t)2 * a2_tiles(g) * 63 * 32; }
+__host__ __device__ __forceinline__ size_t a2_index(const Geom& g, int color, int v, int64_t q) {
+  return (((size_t)color * a2_tiles(g) + (size_t)(q >> 5)) * 63 + (size_t)v) * 32 + (size_t)(q & 31);
+}
+
 // streaming (evict-first) loads for matrix values that are read once per pass
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
@@ -92,6 +102,93 @@ __device__ __forceinline__ double fma3(double acc, double a0, double x0, double 
 }
 __device__ __forceinline__ float fma3(float acc, float a0, float x0, float a1, float x1, float a2, float x2) {
   return fmaf(a2, x2, fmaf(a1, x1, fmaf(a0, x0, acc)));
+}
+
+// ---- split FP32 pairs for the Krylov vectors and the Arnoldi product
+// A value is the unevaluated sum hi + lo of two floats with |lo| at most
+// half an ulp of hi (Dekker's double-length arithmetic, Numer. Math. 18,
+// 1971): 48 significant bits, 2^-47 relative rounding, with FP32's exponent
+// range.  The error-free transformations are Knuth's TwoSum and the FMA
+// form of Dekker's TwoProduct.  GB300 issues 128 FP32 operations per clock
+// per SM against about 2 FP64 FMAs, so a split multiply-add (about 15 FP32
+// operations) is several times cheaper than one FP64 FMA, and the kernels
+// built from it are bound by HBM instead of the FP64 pipe.  The _rn
+// intrinsics are never contracted into FMAs, which the transformations rely
+// on.
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df{s, e};
+}
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  const df s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+// acc + a b, renormalised
+__device__ __forceinline__ df df_fma(df acc, df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
+  const df s = df_two_sum(acc.hi, p);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, pe)));
+}
+// acc + a b for a long sum: the low parts of the products and of the
+// running sum collect in acc.lo without renormalising each step (the sum is
+// renormalised once, by df_norm, before it is used)
+__device__ __forceinline__ df df_fma_acc(df acc, df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
+  const df s = df_two_sum(acc.hi, p);
+  return df{s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, pe))};
+}
+__device__ __forceinline__ df df_norm(df a) { return df_fast_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ df df_from(double v) {
+  const float h = __double2float_rn(v);
+  return df{h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+// The same split by integer operations on the bit pattern (no FP64
+// instruction): hi keeps the leading 24 significant bits, lo the next 24
+// (both truncated), so |a - hi - lo| < 2^-46 |a|.  Below 2^-74 the low part
+// would be subnormal and is dropped; *bad is set where |a| > 2^126 or
+// 0 < |a| < 2^-120 (outside what the split form represents) or a is not
+// finite.
+__device__ __forceinline__ float2 df_split_bits(double a, int* bad) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int E = (int)((u >> 52) & 0x7ff);
+  const unsigned long long M = u & 0xFFFFFFFFFFFFFull;
+  if (E == 0) {
+    *bad |= (M != 0);
+    return make_float2(__uint_as_float(sign), __uint_as_float(sign));
+  }
+  const int e = E - 1023;
+  if (e > 126 || e < -120) {
+    *bad = 1;
+    return make_float2(__double2float_rn(a), 0.f);
+  }
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(M >> 29));
+  const unsigned R = (unsigned)(M & 0x1FFFFFFFu);
+  const int lz = __clz(R);
+  const int fe = e - 52 + (31 - lz) + 127;
+  if (R == 0 || fe < 1) return make_float2(hi, __uint_as_float(sign));
+  const unsigned mant = (unsigned)((((unsigned long long)R) << (lz + 1)) & 0xFFFFFFFFull) >> 9;
+  return make_float2(hi, __uint_as_float(sign | ((unsigned)fe << 23) | mant));
+}
+__device__ __forceinline__ df df_shfl_xor(df a, int o) {
+  return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -112,6 +209,35 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = l < nw ? sh[l] : 0.0;
   return warp_sum(v);
 }
+
+// Sum of split values over the thread block in a fixed order: warps reduce
+// in split arithmetic, the warp sums are added in FP64.  The result is valid
+// in thread 0.  `sh` must hold 32 doubles.
+__device__ __forceinline__ double block_sum_df(df v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = df_to_double(v);
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) s += sh[k];
+  return s;
+}
+
+// A preconditioner input or output vector of 3N entries in internal order:
+// FP64 (d) or split pairs (f: hi plane, then the lo plane at f + n).
+struct InV {
+  const double* d;
+  const float* f;
+  int64_t n;
+};
+struct OutV {
+  double* d;
+  float* f;
+  int64_t n;
+};
 
 // Ticket of the "last block done" pattern: true in the block that finished
 // last among `total`.  Partials written before the call are visible to it.
@@ -150,6 +276,8 @@ constexpr int kMaxPoolStreams = 16;
 extern std::atomic<int> g_pool_width;
 // convolution engine of the 32 -> 32 layers: 0 mma.sync, 1 tcgen05 (conv_tc.cu)
 extern std::atomic<int> g_conv_engine;
+// AMG multi-block levels: 1 cooperative down/up launches, 0 one kernel per sweep
+extern std::atomic<int> g_amg_coop;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // grid size for a grid-stride loop over n items
@@ -193,6 +321,9 @@ struct bo_mat {
   bool a32_valid;
   __nv_bfloat16* A16;  // BF16 copy for bo_mat_spmv(..., BO_PREC_BF16)
   bool a16_valid;
+  float2* A2;          // split (hi, lo) copy of A for the Arnoldi product, tiled (a2_index)
+  bool a2_valid;
+  int* a2_range;       // device flag: a value lies outside the split form's range
   int* flags;          // device error bits
   int* h_flags;        // pinned host copy
 };
@@ -221,6 +352,7 @@ struct bo_prec {
   bool bf16;               // BF16 storage of those (arithmetic FP32)
   void* At;                // 63 N decoupled values (preconditioner precision)
   double* w;               // 3 N decoupling weights (g0, g1, g2) of row 0, [3][N] internal order
+  float* wf;               // the same weights rounded to FP32 (FP32 arithmetic), else NULL
   void* Dinv;              // 9 N inverted ILU pivot blocks [rc][N], preconditioner precision
   // AMG: level 0 = the pressure block of At (colour-split), levels 1.. natural order
   int nlev;
@@ -238,8 +370,8 @@ struct bo_prec {
   void* f0;                // N level-0 AMG right-hand side
   // Krylov workspace (FP64 unless noted)
   int mcap;                // restart length the workspace was sized for
-  double* V;               // (mcap+1) 3N
-  double* Z;               // mcap 3N preconditioned vectors
+  double* V;               // (mcap+1) 3N basis
+  double* Z;               // mcap 3N preconditioned vectors as split pairs: per vector a hi plane, then a lo plane
   double* H;               // (mcap+1) mcap
   double* cs;
   double* sn;
@@ -297,6 +429,10 @@ int prec_alloc(bo_prec* P);
 void prec_free(bo_prec* P);
 // z = stage(v * vs[0]) in internal order, FP64 in and out (vs may be NULL: scale 1)
 void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs = nullptr);
+// the CPR stage with its output as split pairs (FP64 basis vector in, preconditioned vector out)
+void launch_cpr_split(bo_prec* P, const double* v, float* z, const DevState* st, const double* vs);
+// A2 = split copy of A, flagging values outside FP32's normal range
+void launch_split_matrix(bo_mat* m, cudaStream_t s);
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  // FP64 values of At rebuilt on the fly
 
 // krylov.cu

@@ -17,6 +17,7 @@ namespace bo {
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_pool_width{kMaxPoolStreams};
 std::atomic<int> g_conv_engine{1};
+std::atomic<int> g_amg_coop{1};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
   static std::mutex mu;
@@ -103,6 +104,8 @@ void mat_free(bo_mat* m) {
   cudaFree(m->A);
   cudaFree(m->A32);
   cudaFree(m->A16);
+  cudaFree(m->A2);
+  cudaFree(m->a2_range);
   cudaFree(m->flags);
   cudaFreeHost(m->h_flags);
   bo_ctx* c = m->ctx;
@@ -144,6 +147,8 @@ int mat_create(bo_ctx* ctx, const bo_grid* grid, int kind, int64_t nrows, int64_
   if (e == cudaSuccess) e = cudaMalloc(&m->col, nnz * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&m->stage, vbytes);
   if (e == cudaSuccess) e = cudaMalloc(&m->A, (size_t)63 * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->A2, a2_size(m->g) * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&m->a2_range, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&m->flags, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&m->h_flags, sizeof(int));
   if (e != cudaSuccess) {
@@ -527,6 +532,12 @@ int bo_prec_residual_history(bo_prec* P, double* buf, int cap) {
 }
 
 int64_t bo_kernel_launches(void) { return g_launches.load(); }
+
+int bo_set_amg_cooperative(int on) {
+  if (on != 0 && on != 1) return BO_ERR_ARG;
+  g_amg_coop.store(on);
+  return BO_OK;
+}
 
 int bo_set_conv_engine(int engine) {
   if (engine != 0 && engine != 1) return BO_ERR_ARG;

@@ -65,8 +65,8 @@ __device__ bool inv3d(const double a[9], double out[9]) {
     if (m[p][k] == 0.0) return false;
     if (p != k)
       for (int j = 0; j < 6; ++j) { const double t = m[k][j]; m[k][j] = m[p][j]; m[p][j] = t; }
-    const double piv = m[k][k];
-    for (int j = 0; j < 6; ++j) m[k][j] /= piv;
+    const double rp = 1.0 / m[k][k];  // one FP64 division per pivot
+    for (int j = 0; j < 6; ++j) m[k][j] *= rp;
     for (int i = 0; i < 3; ++i) {
       if (i == k) continue;
       const double f = m[i][k];
@@ -228,6 +228,7 @@ int dp_condense(bo_dp* d) {
    note_launch());
   d->S->a32_valid = false;
   d->S->a16_valid = false;
+  launch_split_matrix(d->S, s);
   cudaMemcpyAsync(d->h_flags, d->flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
   if (*d->h_flags & kErrNonfinite) return BO_ERR_NONFINITE;

@@ -19,6 +19,15 @@
 // spent normalising.  On GB300 these passes are bound jointly by FP64
 // arithmetic and HBM (one FMA per 8 bytes read).
 //
+// The Arnoldi product w = A z_j reads a split copy of A (each value as an
+// unevaluated sum hi + lo of two floats, 48 significant bits; see df in
+// bo_internal.cuh) in a tiled layout, and the preconditioned vectors Z are
+// stored as split pairs too (a hi plane, then a lo plane; exact for the FP32
+// preconditioner's output).  The product is formed with FP32 instructions,
+// so it is bound by HBM rather than by GB300's FP64 rate; w is written in
+// FP64.  The true residual b - A x, which decides convergence, is FP64 on
+// the original FP64 matrix.
+//
 // Every reduction is two-stage with a fixed order (per-block partial sums,
 // then the last block to finish sums the partials), so results are bitwise
 // repeatable.  The Givens rotations run in that last block; a flag in device
@@ -40,31 +49,67 @@ constexpr int kMaxM = 64;
 constexpr int kHistCap = 4096;
 constexpr int kDotBlocks = 2 * 152;  // most chunks of the multi-dot pass
 
-// w = A z in FP64 on internal vectors
-__global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const double* __restrict__ A,
-                                                          const double* __restrict__ z, double* __restrict__ w,
+// acc + a0 x0 + a1 x1 + a2 x2 in split arithmetic (low parts collected lazily)
+__device__ __forceinline__ df dfma3(df acc, float2 a0, df x0, float2 a1, df x1, float2 a2, df x2) {
+  acc = df_fma_acc(acc, df{a0.x, a0.y}, x0);
+  acc = df_fma_acc(acc, df{a1.x, a1.y}, x1);
+  return df_fma_acc(acc, df{a2.x, a2.y}, x2);
+}
+
+// w = A z on internal vectors: z split pairs (planes of n = 3N), w FP64.
+// A2 is the split copy of A; where it could not hold every value (*range)
+// the product is formed in FP64 from A instead.
+__global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2* __restrict__ A2,
+                                                          const double* __restrict__ A, const int* __restrict__ range,
+                                                          const float* __restrict__ z, double* __restrict__ w,
                                                           const DevState* st) {
   if (st->done) return;
+  const int64_t n = 3 * g.N;
+  const bool fp64 = *range != 0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
     const int64_t q = t - color * g.Nh;
     const Cell c = decode(g, color, q);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const size_t P = (size_t)g.Nh;
+    double r0, r1, r2;
+    if (!fp64) {
+      df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f};
 #pragma unroll
-    for (int sl = 0; sl < 7; ++sl) {
-      const int64_t nq = nbr(g, c, q, sl);
-      if (nq < 0) continue;
-      const int xc = (sl == kDiag) ? color : (color ^ 1);
-      const double x0 = z[vidx(g, 0, xc, nq)], x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
-      const double* a = A + plane(g, color, sl, 0) + q;
-      const size_t P = (size_t)g.Nh;
-      a0 = fma3(a0, ld_stream(a), x0, ld_stream(a + P), x1, ld_stream(a + 2 * P), x2);
-      a1 = fma3(a1, ld_stream(a + 3 * P), x0, ld_stream(a + 4 * P), x1, ld_stream(a + 5 * P), x2);
-      a2 = fma3(a2, ld_stream(a + 6 * P), x0, ld_stream(a + 7 * P), x1, ld_stream(a + 8 * P), x2);
+      for (int sl = 0; sl < 7; ++sl) {
+        const int64_t nq = nbr(g, c, q, sl);
+        if (nq < 0) continue;
+        const int xc = (sl == kDiag) ? color : (color ^ 1);
+        const size_t i0 = vidx(g, 0, xc, nq), i1 = vidx(g, 1, xc, nq), i2 = vidx(g, 2, xc, nq);
+        const df x0{z[i0], z[n + i0]}, x1{z[i1], z[n + i1]}, x2{z[i2], z[n + i2]};
+        const float2* a = A2 + a2_index(g, color, sl * 9, q);
+        a0 = dfma3(a0, __ldcs(a), x0, __ldcs(a + 32), x1, __ldcs(a + 64), x2);
+        a1 = dfma3(a1, __ldcs(a + 96), x0, __ldcs(a + 128), x1, __ldcs(a + 160), x2);
+        a2 = dfma3(a2, __ldcs(a + 192), x0, __ldcs(a + 224), x1, __ldcs(a + 256), x2);
+      }
+      r0 = df_to_double(df_norm(a0));
+      r1 = df_to_double(df_norm(a1));
+      r2 = df_to_double(df_norm(a2));
+    } else {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int sl = 0; sl < 7; ++sl) {
+        const int64_t nq = nbr(g, c, q, sl);
+        if (nq < 0) continue;
+        const int xc = (sl == kDiag) ? color : (color ^ 1);
+        const size_t i0 = vidx(g, 0, xc, nq), i1 = vidx(g, 1, xc, nq), i2 = vidx(g, 2, xc, nq);
+        const double x0 = (double)z[i0] + (double)z[n + i0], x1 = (double)z[i1] + (double)z[n + i1],
+                     x2 = (double)z[i2] + (double)z[n + i2];
+        const double* a = A + plane(g, color, sl, 0) + q;
+        a0 = fma3(a0, a[0], x0, a[P], x1, a[2 * P], x2);
+        a1 = fma3(a1, a[3 * P], x0, a[4 * P], x1, a[5 * P], x2);
+        a2 = fma3(a2, a[6 * P], x0, a[7 * P], x1, a[8 * P], x2);
+      }
+      r0 = a0;
+      r1 = a1;
+      r2 = a2;
     }
-    w[t] = a0;
-    w[g.N + t] = a1;
-    w[2 * g.N + t] = a2;
+    w[t] = r0;
+    w[g.N + t] = r1;
+    w[2 * g.N + t] = r2;
   }
 }
 
@@ -132,9 +177,13 @@ __global__ void k_norm(int64_t n, const double* __restrict__ v, double* partials
   }
 }
 
+// zero initial guess: r0 = b, so ||r0|| = ||b||
+__global__ void k_beta_is_bnorm(DevState* st) { st->beta = st->bnorm; }
+
 __global__ void k_set_target(DevState* st, double tol) {
   st->target = tol * st->bnorm;
   st->err = 0;
+  st->counter[5] = 0;  // arrivals of the AMG's grid barrier
   st->k = 0;
   st->hist_base = 0;
 }
@@ -190,7 +239,7 @@ __device__ void givens_step(DevState* st, double* col, double hn, double* H, dou
   if (hist && hist_at < kHistCap) hist[hist_at] = st->est;
   const bool bad = !isfinite(st->est) || !isfinite(d) || d == 0.0;
   if (bad) atomicOr(&st->err, kErrNonfinite);
-  if (bad || st->est <= st->target || st->happy || j + 1 == m) st->done = 1;
+  if (bad || (st->err & kErrTimeout) || st->est <= st->target || st->happy || j + 1 == m) st->done = 1;
 }
 
 struct ArnoldiArgs {
@@ -287,20 +336,38 @@ __global__ void k_trisolve(DevState* st, const double* H, const double* gv, doub
   }
 }
 
-// x += sum_{l < k} y_l Z_l
-__global__ void k_xupdate(int64_t n, double* __restrict__ x, const double* __restrict__ Z, int64_t ldz,
-                          const double* __restrict__ y, const DevState* st) {
-  __shared__ double ys[kMaxM];
-  const int k = st->k;
-  for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = y[l];
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = x[i];
-    for (int l = 0; l < k; ++l) s += ys[l] * Z[(size_t)l * ldz + i];
-    x[i] = s;
+// sum_{k < nv} c_k V_k[i] in split arithmetic (nv <= NU), in batches of B
+// columns: each batch is unrolled with the bound as a predicate, so its 2 B
+// loads are in flight at once
+template <int NU, int B = NU>
+__device__ __forceinline__ df lincomb(const df* c, const float* __restrict__ V, int64_t ldv, int64_t n, int64_t i,
+                                      int nv) {
+  df s{0.f, 0.f};
+#pragma unroll 1
+  for (int k0 = 0; k0 < NU; k0 += B) {
+    if (k0 >= nv) break;
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (k0 + k < nv) {
+        const float* a = V + (size_t)(k0 + k) * ldv;
+        s = df_fma_acc(s, c[k0 + k], df{a[i], a[n + i]});
+      }
   }
+  return df_norm(s);
 }
 
+// x += sum_{l < k} y_l Z_l: the sum in split arithmetic (Z split pairs,
+// ldz floats apart), added to the FP64 iterate
+template <int NU>
+__global__ void __launch_bounds__(kThreads, 2) k_xupdate(int64_t n, double* __restrict__ x, const float* __restrict__ Z, int64_t ldz,
+                          const double* __restrict__ y, const DevState* st) {
+  __shared__ df ys[kMaxM];
+  const int k = st->k;
+  for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = df_from(y[l]);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += df_to_double(lincomb<NU, 16>(ys, Z, ldz, n, i, k));
+}
 
 }  // namespace
 
@@ -403,6 +470,7 @@ struct Job {
   void start() {
     t0 = std::chrono::steady_clock::now();
     cudaStream_t s = stream();
+    if (!P->mat->a2_valid) launch_split_matrix(P->mat, s);
     const Geom& g = geom();
     const int64_t nn = n();
     DevState* st = P->st;
@@ -419,8 +487,13 @@ struct Job {
     else launch_gather(g, x_d, P->xi, s);
     (k_norm<<<kRedBlocks, kThreads, 0, s>>>(nn, P->bi, P->partials, st), note_launch());
     (k_set_target<<<1, 1, 0, s>>>(st, o.tol), note_launch());
-    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
-     note_launch());
+    if (o.x0_is_zero) {  // r0 = b: no pass over the matrix
+      cudaMemcpyAsync(P->rk, P->bi, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      (k_beta_is_bnorm<<<1, 1, 0, s>>>(st), note_launch());
+    } else {
+      (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+       note_launch());
+    }
     mark(kPhaseSlot);
     P->nhist = 0;
     phase = kInitWait;
@@ -444,16 +517,17 @@ struct Job {
     DevState* st = P->st;
     double* vj = P->V + (size_t)j * ldv;
     double* w = P->V + (size_t)(j + 1) * ldv;
-    double* zj = P->Z + (size_t)j * nn;
+    float* zj = (float*)P->Z + (size_t)j * 2 * nn;  // split pairs: hi plane, lo plane
     double* dhist = P->partials + (P->npartials - kHistCap);
-    launch_cpr(P, vj, zj, BO_STAGE_CPR, st, &st->vscale[j]);
+    launch_cpr_split(P, vj, zj, st, &st->vscale[j]);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed && prof.size() < 512) {
       e0 = P->prof_ev[2 * prof.size()];
       e1 = P->prof_ev[2 * prof.size() + 1];
       cudaEventRecord(e0, s);
     }
-    (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(g, P->mat->A, zj, w, st),
+    (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(
+         g, P->mat->A2, P->mat->A, P->mat->a2_range, zj, w, st),
      note_launch());
     if (e1) {
       cudaEventRecord(e1, s);
@@ -525,7 +599,10 @@ struct Job {
     const int64_t nn = n();
     const int gn = grid_for(nn);
     (k_trisolve<<<1, 32, 0, s>>>(P->st, P->H, P->gvec, P->y, o.restart), note_launch());
-    (k_xupdate<<<gn, kThreads, 0, s>>>(nn, P->xi, P->Z, nn, P->y, P->st), note_launch());
+    const float* Z = (const float*)P->Z;
+    if (o.restart <= 16) (k_xupdate<16><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
+    else if (o.restart <= 32) (k_xupdate<32><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
+    else (k_xupdate<kMaxM><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
     (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(geom(), P->mat->A, P->bi, P->xi, P->rk, P->partials, P->st),
      note_launch());
     mark(kPhaseSlot);
@@ -624,7 +701,10 @@ struct Job {
         const double prev = beta;
         beta = h.beta;
         est = h.est;
-        if (h.err & kErrNonfinite) {
+        if (h.err & kErrTimeout) {
+          status = BO_ERR_TIMEOUT;
+          finish();
+        } else if (h.err & kErrNonfinite) {
           status = BO_ERR_BREAKDOWN;
           finish();
         } else if (h.k == 0 || beta <= target || its >= o.maxit) {

@@ -48,9 +48,12 @@ __device__ __forceinline__ unsigned valid_slots(const Geom& g, const Nat& n) {
 }
 
 // One thread per cell: check the block row's pattern against the stencil
-// and scatter its 3x3 blocks into the colour-split planes.
+// and scatter its 3x3 blocks into the colour-split planes, in FP64 (A) and
+// as split pairs (A2, read by the Arnoldi product).
 __global__ void k_ingest_bsr(Geom g, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ val, int64_t nnz, double* __restrict__ A, int* flags) {
+                             const double* __restrict__ val, int64_t nnz, double* __restrict__ A,
+                             float2* __restrict__ A2, int* flags, int* range) {
+  int split_bad = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Nat n = decode_nat(g, c);
     const unsigned valid = valid_slots(g, n);
@@ -68,20 +71,27 @@ __global__ void k_ingest_bsr(Geom g, const int32_t* __restrict__ rowptr, const i
         const double a = v[rc];
         nonfinite |= !isfinite(a);
         A[plane(g, n.color, s, rc) + n.q] = a;
+        A2[a2_index(g, n.color, s * 9 + rc, n.q)] = df_split_bits(a, &split_bad);
       }
     }
     for (int s = 0; s < 7; ++s)
       if (!((valid >> s) & 1u))
-        for (int rc = 0; rc < 9; ++rc) A[plane(g, n.color, s, rc) + n.q] = 0.0;
+        for (int rc = 0; rc < 9; ++rc) {
+          A[plane(g, n.color, s, rc) + n.q] = 0.0;
+          A2[a2_index(g, n.color, s * 9 + rc, n.q)] = make_float2(0.f, 0.f);
+        }
     if (bad) atomicOr(flags, kErrPattern);
     if (nonfinite) atomicOr(flags, kErrNonfinite);
   }
+  if (__any_sync(0xffffffffu, split_bad) && (threadIdx.x & 31) == 0) atomicOr(range, 1);
 }
 
 // One thread per cell: zero the cell's blocks, then add every scalar entry
 // of its three CSR rows (row 3c+r, column 3c'+k) into block (c, c').
 __global__ void k_ingest_csr(Geom g, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ val, int64_t nnz, double* __restrict__ A, int* flags) {
+                             const double* __restrict__ val, int64_t nnz, double* __restrict__ A,
+                             float2* __restrict__ A2, int* flags, int* range) {
+  int split_bad = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Nat n = decode_nat(g, c);
     for (int s = 0; s < 7; ++s)
@@ -102,9 +112,13 @@ __global__ void k_ingest_csr(Geom g, const int32_t* __restrict__ rowptr, const i
         A[plane(g, n.color, s, 3 * r + k) + n.q] += a;
       }
     }
+    for (int s = 0; s < 7; ++s)
+      for (int rc = 0; rc < 9; ++rc)
+        A2[a2_index(g, n.color, s * 9 + rc, n.q)] = df_split_bits(A[plane(g, n.color, s, rc) + n.q], &split_bad);
     if (bad) atomicOr(flags, kErrPattern);
     if (nonfinite) atomicOr(flags, kErrNonfinite);
   }
+  if (__any_sync(0xffffffffu, split_bad) && (threadIdx.x & 31) == 0) atomicOr(range, 1);
 }
 
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
@@ -164,6 +178,19 @@ __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restr
   }
 }
 
+// split (hi, lo) copy of the matrix values for the Arnoldi product, in the
+// tiled layout; *range flags values the split form cannot hold
+__global__ void k_split_matrix(Geom g, const double* __restrict__ src, float2* __restrict__ dst, int* range) {
+  int bad = 0;
+  const size_t n = (size_t)126 * g.Nh;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i / g.Nh);  // plane: colour * 63 + slot * 9 + rc
+    const int64_t q = (int64_t)(i - (size_t)p * g.Nh);
+    dst[a2_index(g, p / 63, p % 63, q)] = df_split_bits(src[i], &bad);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(range, 1);
+}
+
 __global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = __float2bfloat16_rn((float)src[i]);
@@ -196,12 +223,18 @@ __global__ void k_axpy1(double* __restrict__ s, const double* __restrict__ d, in
 }  // namespace
 
 int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s) {
-  (k_ingest_bsr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
+  cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
+  (k_ingest_bsr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
+                                                      m->a2_range), note_launch());
+  m->a2_valid = true;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
 int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s) {
-  (k_ingest_csr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->flags), note_launch());
+  cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
+  (k_ingest_csr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
+                                                      m->a2_range), note_launch());
+  m->a2_valid = true;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
@@ -218,6 +251,12 @@ void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta
      note_launch());
   else
     (k_spmv_nat<double, double><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A, x, y, alpha, beta), note_launch());
+}
+
+void launch_split_matrix(bo_mat* m, cudaStream_t s) {
+  cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
+  (k_split_matrix<<<grid_for((int64_t)63 * m->g.N), kThreads, 0, s>>>(m->g, m->A, m->A2, m->a2_range), note_launch());
+  m->a2_valid = true;
 }
 
 void launch_to_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t s) {

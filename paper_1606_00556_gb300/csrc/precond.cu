@@ -33,7 +33,9 @@ constexpr size_t kTailSmemMax = 200 * 1024;  // stage the tail levels in shared 
 
 // ---------------------------------------------------------------- 3x3 blocks
 // inverse by Gauss-Jordan elimination with partial pivoting; false if a
-// pivot is zero or the result is not finite
+// pivot is zero or the result is not finite.  Each pivot row is scaled by
+// one reciprocal: on GB300 an FP64 division is a long sequence of FP64
+// instructions, and six of them per pivot made the ILU setup FP64-bound.
 template <typename T>
 __device__ bool inv3(const T a[9], T out[9]) {
   T m[3][6];
@@ -49,8 +51,8 @@ __device__ bool inv3(const T a[9], T out[9]) {
     if (m[p][k] == T(0)) return false;
     if (p != k)
       for (int j = 0; j < 6; ++j) { const T t = m[k][j]; m[k][j] = m[p][j]; m[p][j] = t; }
-    const T piv = m[k][k];
-    for (int j = 0; j < 6; ++j) m[k][j] /= piv;
+    const T rp = T(1) / m[k][k];
+    for (int j = 0; j < 6; ++j) m[k][j] *= rp;
     for (int i = 0; i < 3; ++i) {
       if (i == k) continue;
       const T f = m[i][k];
@@ -116,7 +118,7 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { ret
 // decoupled planes in storage type S.
 template <typename S>
 __global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__ At, double* __restrict__ w,
-                           DevState* st) {
+                           float* __restrict__ wf, DevState* st) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
     const int64_t q = t - color * g.Nh;
@@ -143,6 +145,12 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__
     w[vidx(g, 0, color, q)] = g0;
     w[vidx(g, 1, color, q)] = g1;
     w[vidx(g, 2, color, q)] = g2;
+    if (wf) {
+      wf[vidx(g, 0, color, q)] = (float)g0;
+      wf[vidx(g, 1, color, q)] = (float)g1;
+      wf[vidx(g, 2, color, q)] = (float)g2;
+    }
+#pragma unroll
     for (int s = 0; s < 7; ++s) {
       double a[9];
 #pragma unroll
@@ -414,16 +422,33 @@ __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __rest
 // ------------------------------------------------------------ apply kernels
 // Entry of the preconditioner: f = D_QI^{-1} v (DEC) or f = v, in precision
 // T, fused with the first ILU pass on the red cells, t_r = D_r^{-1} f_r.
+// v is FP64 or split pairs; sc the scale of an unnormalised Krylov vector.
+// FP32 arithmetic reads the split input's high part (the low part lies
+// below FP32's rounding) and the FP32 copy of the weights, so the FP32
+// preconditioner issues no FP64 instruction here.
+template <typename T>
+__device__ __forceinline__ T in_get(const InV& v, size_t i, double sc) {
+  if (v.f) {
+    if constexpr (sizeof(T) == 4) return (float)sc * v.f[i];
+    else return sc * ((double)v.f[i] + (double)v.f[v.n + i]);
+  }
+  return (T)(sc * v.d[i]);
+}
+
 template <typename T, typename S, bool DEC>
-__global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* __restrict__ vs,
-                            const double* __restrict__ w, const S* __restrict__ Dinv, T* __restrict__ f,
+__global__ void k_cpr_entry(Geom g, InV v, const double* __restrict__ vs, const double* __restrict__ w,
+                            const float* __restrict__ wf, const S* __restrict__ Dinv, T* __restrict__ f,
                             T* __restrict__ tv, const DevState* st) {
   if (st->done) return;
   const double sc = vs ? *vs : 1.0;  // scale of an unnormalised Krylov vector
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
-    const double v0 = sc * v[t], v1 = sc * v[g.N + t], v2 = sc * v[2 * g.N + t];
-    const T f0 = DEC ? (T)(w[t] * v0 + w[g.N + t] * v1 + w[2 * g.N + t] * v2) : (T)v0;
-    const T f1 = (T)v1, f2 = (T)v2;
+    const T v0 = in_get<T>(v, t, sc), v1 = in_get<T>(v, g.N + t, sc), v2 = in_get<T>(v, 2 * g.N + t, sc);
+    T f0 = v0;
+    if (DEC) {
+      if constexpr (sizeof(T) == 4) f0 = fma3(0.f, wf[t], v0, wf[g.N + t], v1, wf[2 * g.N + t], v2);
+      else f0 = fma3(0.0, w[t], v0, w[g.N + t], v1, w[2 * g.N + t], v2);
+    }
+    const T f1 = v1, f2 = v2;
     f[t] = f0;
     f[g.N + t] = f1;
     f[2 * g.N + t] = f2;
@@ -435,6 +460,23 @@ __global__ void k_cpr_entry(Geom g, const double* __restrict__ v, const double* 
       tv[g.N + t] = d[3] * f0 + d[4] * f1 + d[5] * f2;
       tv[2 * g.N + t] = d[6] * f0 + d[7] * f1 + d[8] * f2;
     }
+  }
+}
+
+// preconditioner output: FP64, or split pairs (exact for FP32 values)
+template <typename T>
+__device__ __forceinline__ void out_put(const OutV& o, size_t i, T v) {
+  if (o.f) {
+    if constexpr (sizeof(T) == 4) {
+      o.f[i] = v;
+      o.f[o.n + i] = 0.f;
+    } else {
+      const df d = df_from(v);
+      o.f[i] = d.hi;
+      o.f[o.n + i] = d.lo;
+    }
+  } else {
+    o.d[i] = (double)v;
   }
 }
 
@@ -486,7 +528,7 @@ constexpr int res_min_blocks() { return (sizeof(T) == 4 && ROWS == 1) ? 5 : 4; }
 
 template <typename T, typename S, bool OUT>
 __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g, const S* __restrict__ At, const S* __restrict__ Dinv, const T* __restrict__ src,
-                        T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
+                        T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, OutV zo,
                         const DevState* st) {
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
@@ -504,9 +546,9 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g,
       tv[vidx(g, 0, 1, q)] = u0;
       tv[vidx(g, 1, 1, q)] = u1;
       tv[vidx(g, 2, 1, q)] = u2;
-      zo[vidx(g, 0, 1, q)] = (double)(z[vidx(g, 0, 1, q)] + e[g.Nh + q] + u0);
-      zo[vidx(g, 1, 1, q)] = (double)(z[vidx(g, 1, 1, q)] + u1);
-      zo[vidx(g, 2, 1, q)] = (double)(z[vidx(g, 2, 1, q)] + u2);
+      out_put<T>(zo, vidx(g, 0, 1, q), z[vidx(g, 0, 1, q)] + e[g.Nh + q] + u0);
+      out_put<T>(zo, vidx(g, 1, 1, q), z[vidx(g, 1, 1, q)] + u1);
+      out_put<T>(zo, vidx(g, 2, 1, q), z[vidx(g, 2, 1, q)] + u2);
     } else {
       z[vidx(g, 0, 1, q)] = u0;
       z[vidx(g, 1, 1, q)] = u1;
@@ -520,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g,
 // OUT = true: zo_r = z1_r + Pi_p e_r + t_r - corr, in FP64.
 template <typename T, typename S, bool OUT>
 __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g, const S* __restrict__ At, const S* __restrict__ Dinv, const T* __restrict__ tv,
-                         const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, double* __restrict__ zo,
+                         const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, OutV zo,
                          const DevState* st) {
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
@@ -535,9 +577,9 @@ __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g
     const T c2 = d[6] * s[0] + d[7] * s[1] + d[8] * s[2];
     const T t0 = tv[vidx(g, 0, 0, q)] - c0, t1 = tv[vidx(g, 1, 0, q)] - c1, t2 = tv[vidx(g, 2, 0, q)] - c2;
     if (OUT) {
-      zo[vidx(g, 0, 0, q)] = (double)(z[vidx(g, 0, 0, q)] + e[q] + t0);
-      zo[vidx(g, 1, 0, q)] = (double)(z[vidx(g, 1, 0, q)] + t1);
-      zo[vidx(g, 2, 0, q)] = (double)(z[vidx(g, 2, 0, q)] + t2);
+      out_put<T>(zo, vidx(g, 0, 0, q), z[vidx(g, 0, 0, q)] + e[q] + t0);
+      out_put<T>(zo, vidx(g, 1, 0, q), z[vidx(g, 1, 0, q)] + t1);
+      out_put<T>(zo, vidx(g, 2, 0, q), z[vidx(g, 2, 0, q)] + t2);
     } else {
       z[vidx(g, 0, 0, q)] = t0;
       z[vidx(g, 1, 0, q)] = t1;
@@ -595,25 +637,31 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
 }
 
 // ---- AMG level 0 (colour-split, coefficients = plane (colour, slot, 0) of At)
+// One cell of a level-0 Gauss-Seidel half sweep.
+template <typename T, typename S>
+__device__ __forceinline__ void gs0_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                         T* __restrict__ x, int color, int zero_guess, int64_t q) {
+  const int oc = color ^ 1;
+  T s = f[(size_t)color * g.Nh + q];
+  if (!zero_guess) {
+    const Cell c = decode(g, color, q);
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      if (sl == kDiag) continue;
+      const int64_t nq = nbr(g, c, q, sl);
+      if (nq < 0) continue;
+      s -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)oc * g.Nh + nq];
+    }
+  }
+  x[(size_t)color * g.Nh + q] = s / cv<T>(At[plane(g, color, kDiag, 0) + q]);
+}
+
 template <typename T, typename S>
 __global__ void k_gs0(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x, int color,
                       int zero_guess, const DevState* st) {
   if (st->done) return;
-  const int oc = color ^ 1;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
-    T s = f[(size_t)color * g.Nh + q];
-    if (!zero_guess) {
-      const Cell c = decode(g, color, q);
-#pragma unroll
-      for (int sl = 0; sl < 7; ++sl) {
-        if (sl == kDiag) continue;
-        const int64_t nq = nbr(g, c, q, sl);
-        if (nq < 0) continue;
-        s -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)oc * g.Nh + nq];
-      }
-    }
-    x[(size_t)color * g.Nh + q] = s / cv<T>(At[plane(g, color, kDiag, 0) + q]);
-  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x)
+    gs0_cell<T, S>(g, At, f, x, color, zero_guess, q);
 }
 
 // First post-smoothing half sweep (black cells) with the coarse correction
@@ -622,66 +670,82 @@ __global__ void k_gs0(Geom g, const S* __restrict__ At, const T* __restrict__ f,
 // cells, because the black sweep overwrites x_b and the red sweep that
 // follows overwrites x_r without reading its old value.
 template <typename T, typename S>
+__device__ __forceinline__ void gs0_prolong_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                                 T* __restrict__ x, const LevelDims& C, const T* __restrict__ xc,
+                                                 T sc, int64_t q) {
+  const int di[7] = {0, 0, -1, 0, 1, 0, 0}, dj[7] = {0, -1, 0, 0, 0, 1, 0}, dk[7] = {-1, 0, 0, 0, 0, 0, 1};
+  const Cell c = decode(g, 1, q);
+  T s = f[(size_t)g.Nh + q];
+#pragma unroll
+  for (int sl = 0; sl < 7; ++sl) {
+    if (sl == kDiag) continue;
+    const int64_t nq = nbr(g, c, q, sl);
+    if (nq < 0) continue;
+    const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
+    s -= cv<T>(At[plane(g, 1, sl, 0) + q]) * xv;
+  }
+  x[(size_t)g.Nh + q] = s / cv<T>(At[plane(g, 1, kDiag, 0) + q]);
+}
+
+template <typename T, typename S>
 __global__ void k_gs0_prolong(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x,
                               LevelDims C, const T* __restrict__ xc, T sc, const DevState* st) {
   if (st->done) return;
-  const int di[7] = {0, 0, -1, 0, 1, 0, 0}, dj[7] = {0, -1, 0, 0, 0, 1, 0}, dk[7] = {-1, 0, 0, 0, 0, 0, 1};
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
-    const Cell c = decode(g, 1, q);
-    T s = f[(size_t)g.Nh + q];
-#pragma unroll
-    for (int sl = 0; sl < 7; ++sl) {
-      if (sl == kDiag) continue;
-      const int64_t nq = nbr(g, c, q, sl);
-      if (nq < 0) continue;
-      const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
-      s -= cv<T>(At[plane(g, 1, sl, 0) + q]) * xv;
-    }
-    x[(size_t)g.Nh + q] = s / cv<T>(At[plane(g, 1, kDiag, 0) + q]);
-  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x)
+    gs0_prolong_cell<T, S>(g, At, f, x, C, xc, sc, q);
 }
 
-// f1[I] = sum of level-0 residuals over aggregate I (red cells only when
-// the last half sweep was black)
+// Sum of level-0 residuals over aggregate I (red cells only when the last
+// half sweep was black)
+template <typename T, typename S>
+__device__ __forceinline__ T restrict0_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                            const T* __restrict__ x, const LevelDims& C, int64_t I, int red_only) {
+  const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+  T acc = T(0);
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
+        if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
+        const int color = (i + j + k) & 1;
+        if (red_only && color == 1) continue;
+        const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
+        const Cell c{i, j, k, i & 1};
+        T r = f[(size_t)color * g.Nh + q];
+#pragma unroll
+        for (int sl = 0; sl < 7; ++sl) {
+          const int64_t nq = nbr(g, c, q, sl);
+          if (nq < 0) continue;
+          const int xc = (sl == kDiag) ? color : (color ^ 1);
+          r -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)xc * g.Nh + nq];
+        }
+        acc += r;
+      }
+  return acc;
+}
+
 template <typename T, typename S>
 __global__ void k_restrict0(Geom g, const S* __restrict__ At, const T* __restrict__ f, const T* __restrict__ x,
                             LevelDims C, T* __restrict__ fc, int red_only, const DevState* st) {
   if (st->done) return;
-  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
-    T acc = T(0);
-    for (int dk = 0; dk < 2; ++dk)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int di = 0; di < 2; ++di) {
-          const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
-          if (i >= g.nx || j >= g.ny || k >= g.nz) continue;
-          const int color = (i + j + k) & 1;
-          if (red_only && color == 1) continue;
-          const int64_t q = (i + (int64_t)g.nx * (j + (int64_t)g.ny * k)) >> 1;
-          const Cell c{i, j, k, i & 1};
-          T r = f[(size_t)color * g.Nh + q];
-#pragma unroll
-          for (int sl = 0; sl < 7; ++sl) {
-            const int64_t nq = nbr(g, c, q, sl);
-            if (nq < 0) continue;
-            const int xc = (sl == kDiag) ? color : (color ^ 1);
-            r -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)xc * g.Nh + nq];
-          }
-          acc += r;
-        }
-    fc[I] = acc;
-  }
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x)
+    fc[I] = restrict0_cell<T, S>(g, At, f, x, C, I, red_only);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong0_cell(const Geom& g, T* __restrict__ x, const LevelDims& C,
+                                              const T* __restrict__ xc, T s, int64_t t) {
+  const int color = (int)(t / g.Nh);
+  const int64_t q = t - color * g.Nh;
+  const Cell c = decode(g, color, q);
+  x[t] += s * xc[nat_index(C, c.i / 2, c.j / 2, c.k / 2)];
 }
 
 template <typename T>
 __global__ void k_prolong0(Geom g, T* __restrict__ x, LevelDims C, const T* __restrict__ xc, T s, const DevState* st) {
   if (st->done) return;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
-    const int color = (int)(t / g.Nh);
-    const int64_t q = t - color * g.Nh;
-    const Cell c = decode(g, color, q);
-    x[t] += s * xc[nat_index(C, c.i / 2, c.j / 2, c.k / 2)];
-  }
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x)
+    prolong0_cell<T>(g, x, C, xc, s, t);
 }
 
 // ---- natural-order levels (device functions shared by the multi-block
@@ -896,6 +960,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
   for (int l = a.first; l <= a.last; ++l) {
     const int64_t n = a.lv[l].d.n;
     S* c = const_cast<S*>(b.lv[l].c);
+#pragma unroll 8
     for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = a.lv[l].c[i];
   }
   {
@@ -903,12 +968,143 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.lv[a.first].f[i] = a.lv[a.first].f[i];
     const int64_t nc = a.lv[a.last].d.n;
     S* inv = const_cast<S*>(b.inv);
+#pragma unroll 8
     for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = a.inv[i];
   }
   __syncthreads();
   tail_cycle(b);
   const int64_t n = a.lv[a.first].d.n;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a.lv[a.first].x[i] = b.lv[a.first].x[i];
+}
+
+// ---- the multi-block AMG levels in two cooperative launches
+// Grid-wide barrier of a cooperative launch (all blocks resident): one
+// arrival counter and one generation word in the device state.  The wait is
+// bounded; if it runs out (which needs a block that never arrives) the
+// barrier records kErrTimeout, and every later barrier of the launch fails
+// at once, so the kernel returns and the solve reports BO_ERR_TIMEOUT.
+constexpr unsigned kBarrierSpins = 1u << 22;
+
+__device__ __forceinline__ bool grid_barrier(DevState* st) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &st->counter[6];
+    volatile int* err = &st->err;
+    int good = !(*err & kErrTimeout);
+    if (good) {
+      const unsigned g0 = *gen;
+      __threadfence();
+      if (atomicAdd(&st->counter[5], 1u) == gridDim.x - 1) {
+        st->counter[5] = 0;
+        __threadfence();
+        atomicAdd(&st->counter[6], 1u);
+      } else {
+        unsigned it = 0;
+        while (*gen == g0) {
+          if (++it > kBarrierSpins || (*err & kErrTimeout)) {
+            atomicOr(&st->err, kErrTimeout);
+            good = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok;
+}
+
+template <typename T, typename S>
+struct CycleArgs {
+  Geom g;
+  const S* At;
+  T* f0;
+  T* x0;
+  int tail_from;  // first level of the single-block tail
+  int nu1, nu2;
+  T s;
+  LevelView<T, S> lv[24];
+};
+
+// Down leg: level-0 pre-smoothing and restriction, then the same for the
+// natural-order levels 1 .. tail_from - 1, a grid barrier after every half
+// sweep (the kernel-per-half-sweep form launches each separately).
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads) k_amg_down(CycleArgs<T, S> a, DevState* st) {
+  if (st->done) return;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  const Geom& g = a.g;
+  for (int sw = 0; sw < a.nu1; ++sw)
+    for (int color = 0; color < 2; ++color) {
+      for (int64_t q = t0; q < g.Nh; q += nt) gs0_cell<T, S>(g, a.At, a.f0, a.x0, color, sw == 0 && color == 0, q);
+      if (!grid_barrier(st)) return;
+    }
+  if (a.nu1 == 0) {
+    for (int64_t t = t0; t < g.N; t += nt) a.x0[t] = T(0);
+    if (!grid_barrier(st)) return;
+  }
+  {
+    const LevelView<T, S>& C = a.lv[1];
+    for (int64_t I = t0; I < C.d.n; I += nt) C.f[I] = restrict0_cell<T, S>(g, a.At, a.f0, a.x0, C.d, I, a.nu1 > 0);
+  }
+  for (int l = 1; l < a.tail_from; ++l) {
+    if (!grid_barrier(st)) return;
+    const LevelView<T, S>& L = a.lv[l];
+    for (int sw = 0; sw < a.nu1; ++sw)
+      for (int color = 0; color < 2; ++color) {
+        for (int64_t c = t0; c < L.d.n; c += nt) gs_cell(L, c, color, sw == 0 && color == 0);
+        if (!grid_barrier(st)) return;
+      }
+    if (a.nu1 == 0) {
+      for (int64_t c = t0; c < L.d.n; c += nt) L.x[c] = T(0);
+      if (!grid_barrier(st)) return;
+    }
+    const LevelView<T, S>& C = a.lv[l + 1];
+    for (int64_t I = t0; I < C.d.n; I += nt) C.f[I] = restrict_cell(L, C.d, I, a.nu1 > 0);
+  }
+}
+
+// Up leg: post-smoothing of levels tail_from - 1 .. 1 and then level 0, the
+// first (black) half sweep of each level reading the coarse correction
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads) k_amg_up(CycleArgs<T, S> a, DevState* st) {
+  if (st->done) return;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  const Geom& g = a.g;
+  for (int l = a.tail_from - 1; l >= 1; --l) {
+    const LevelView<T, S>& L = a.lv[l];
+    const LevelView<T, S>& C = a.lv[l + 1];
+    if (a.nu2 == 0) {
+      for (int64_t c = t0; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
+      if (!grid_barrier(st)) return;
+    }
+    for (int sw = 0; sw < a.nu2; ++sw)
+      for (int color = 1; color >= 0; --color) {
+        for (int64_t c = t0; c < L.d.n; c += nt) {
+          if (sw == 0 && color == 1) gs_cell_prolong(L, C, c, a.s);
+          else gs_cell(L, c, color, 0);
+        }
+        if (!grid_barrier(st)) return;
+      }
+  }
+  const LevelView<T, S>& C1 = a.lv[1];
+  if (a.nu2 == 0) {
+    for (int64_t t = t0; t < g.N; t += nt) prolong0_cell<T>(g, a.x0, C1.d, C1.x, a.s, t);
+    return;
+  }
+  for (int sw = 0; sw < a.nu2; ++sw) {
+    for (int64_t q = t0; q < g.Nh; q += nt) {
+      if (sw == 0) gs0_prolong_cell<T, S>(g, a.At, a.f0, a.x0, C1.d, C1.x, a.s, q);
+      else gs0_cell<T, S>(g, a.At, a.f0, a.x0, 1, 0, q);
+    }
+    if (!grid_barrier(st)) return;
+    for (int64_t q = t0; q < g.Nh; q += nt) gs0_cell<T, S>(g, a.At, a.f0, a.x0, 0, 0, q);
+    if (sw + 1 < a.nu2 && !grid_barrier(st)) return;
+  }
 }
 
 // dense solve on level 0 when level 0 is the coarsest: x = inv f
@@ -985,6 +1181,33 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     return;
   }
   const int ghalf = grid_for(g.Nh);
+  const int last = P->nlev - 1;
+  // The multi-block levels as two cooperative launches (down leg, up leg)
+  // with grid barriers between half sweeps; inside stream capture, or if a
+  // cooperative launch is refused, one kernel per half sweep instead.
+  CycleArgs<T, S> ca;
+  ca.g = g;
+  ca.At = At;
+  ca.f0 = f0;
+  ca.x0 = x0;
+  ca.tail_from = P->tail_from;
+  ca.nu1 = nu1;
+  ca.nu2 = nu2;
+  ca.s = sc;
+  for (int l = 1; l <= last; ++l) ca.lv[l] = view<T, S>(P, l);
+  DevState* stw = const_cast<DevState*>(st);
+  void* cargs[] = {&ca, &stw};
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool coop = g_amg_coop.load() != 0 && cap == cudaStreamCaptureStatusNone;
+  bool down_done = false;
+  if (coop) {
+    const int gd = occ_grid((const void*)k_amg_down<T, S>, g.Nh);
+    down_done = cudaLaunchCooperativeKernel((const void*)k_amg_down<T, S>, gd, kThreads, cargs, 0, s) == cudaSuccess;
+    if (down_done) note_launch();
+    else cudaGetLastError();
+  }
+  if (!down_done) {
   for (int sw = 0; sw < nu1; ++sw) {
     (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
     (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
@@ -993,7 +1216,6 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   (k_restrict0<T, S><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (T*)P->lev[1].f,
                                                              nu1 > 0, st), note_launch());
   // multi-block natural levels down to the tail
-  const int last = P->nlev - 1;
   for (int l = 1; l < P->tail_from; ++l) {
     LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
     const int gl = grid_for(L.d.n);
@@ -1003,6 +1225,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     }
     if (nu1 == 0) (k_zero<T><<<gl, kThreads, 0, s>>>(L.d.n, L.x, st), note_launch());
     (k_restrictn<T, S><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
+  }
   }
   TailArgs<T, S> ta;
   ta.first = P->tail_from;
@@ -1018,6 +1241,14 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     (k_tail_smem<T, S><<<1, kTailThreads, tb, s>>>(ta, st), note_launch());
   } else {
     (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+  }
+  if (coop) {
+    const int gu = occ_grid((const void*)k_amg_up<T, S>, g.Nh);
+    if (cudaLaunchCooperativeKernel((const void*)k_amg_up<T, S>, gu, kThreads, cargs, 0, s) == cudaSuccess) {
+      note_launch();
+      return;
+    }
+    cudaGetLastError();
   }
   for (int l = P->tail_from - 1; l >= 1; --l) {
     LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
@@ -1044,7 +1275,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
 
 // z = CPR stage applied to v (FP64, internal order); result FP64 in zo
 template <typename T, typename S>
-void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevState* st, const double* vs) {
+void cpr_apply(bo_prec* P, InV v, OutV zo, int stage, const DevState* st, const double* vs) {
   cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
@@ -1056,30 +1287,30 @@ void cpr_apply(bo_prec* P, const double* v, double* zo, int stage, const DevStat
   T* e0 = (T*)P->e0;
   T* f0 = (T*)P->f0;
   T* z1 = (T*)P->z1;
-  if (stage == BO_STAGE_AMG) {  // (v is a caller's vector here: vs is NULL)
-    (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v, f0, st), note_launch());
+  if (stage == BO_STAGE_AMG) {  // (v is a caller's FP64 vector here: vs is NULL)
+    (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v.d, f0, st), note_launch());
     amg_vcycle<T, S>(P, st);
     learned_coarse_apply(P, st);
-    (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo, st), note_launch());
+    (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo.d, st), note_launch());
     return;
   }
   // x1 = R^{-1} f with f = D_QI^{-1} v (stage CPR) or f = v
   if (stage == BO_STAGE_CPR)
-    (k_cpr_entry<T, S, true><<<occ_grid((const void*)k_cpr_entry<T, S, true>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
-                                                                                                  f, tv, st),
+    (k_cpr_entry<T, S, true><<<occ_grid((const void*)k_cpr_entry<T, S, true>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, P->wf,
+                                                                                                  D, f, tv, st),
      note_launch());
   else
-    (k_cpr_entry<T, S, false><<<occ_grid((const void*)k_cpr_entry<T, S, false>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, D,
-                                                                                                    f, tv, st),
+    (k_cpr_entry<T, S, false><<<occ_grid((const void*)k_cpr_entry<T, S, false>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, P->wf,
+                                                                                                    D, f, tv, st),
      note_launch());
   (k_ilu_b<T, S, false><<<occ_grid((const void*)k_ilu_b<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
-                                                                                          nullptr, st),
+                                                                                          OutV{}, st),
    note_launch());
   (k_ilu_r2<T, S, false><<<occ_grid((const void*)k_ilu_r2<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, z1, z1,
-                                                                                            nullptr, nullptr, st),
+                                                                                            nullptr, OutV{}, st),
    note_launch());
   if (stage == BO_STAGE_ILU) {
-    (k_widen_t<T><<<grid_for(3 * g.N), kThreads, 0, s>>>(3 * g.N, z1, zo, st), note_launch());
+    (k_widen_t<T><<<grid_for(3 * g.N), kThreads, 0, s>>>(3 * g.N, z1, zo.d, st), note_launch());
     return;
   }
   // x2 = x1 + Pi_p AMG(A_pp)^{-1} Pi_r (f - At x1)
@@ -1106,7 +1337,7 @@ int values_impl(bo_prec* P) {
   cudaStream_t s = P->stream;
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
-  (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, (S*)P->At, P->w, P->st), note_launch());
+  (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, (S*)P->At, P->w, P->wf, P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
   (k_ilu_red<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
@@ -1147,6 +1378,7 @@ int prec_alloc(bo_prec* P) {
   const size_t ss = P->ssize;  // storage of the matrix-like arrays
   P->At = al((size_t)63 * g.N * ss);
   P->w = (double*)al((size_t)3 * g.N * sizeof(double));
+  P->wf = ts == sizeof(float) ? (float*)al((size_t)3 * g.N * sizeof(float)) : nullptr;
   P->Dinv = al((size_t)9 * g.N * ss);
   P->f = al((size_t)3 * g.N * ts);
   P->t = al((size_t)3 * g.N * ts);
@@ -1186,7 +1418,7 @@ int prec_alloc(bo_prec* P) {
 
 void prec_free(bo_prec* P) {
   auto fr = [](void* p) { if (p) cudaFree(p); };
-  fr(P->At); fr(P->w); fr(P->Dinv);
+  fr(P->At); fr(P->w); fr(P->wf); fr(P->Dinv);
   fr(P->f); fr(P->t); fr(P->r); fr(P->z1); fr(P->e0); fr(P->f0);
   for (int l = 1; l < P->nlev; ++l) { fr(P->lev[l].c64); fr(P->lev[l].c); fr(P->lev[l].f); fr(P->lev[l].x); }
   fr(P->coarse64); fr(P->coarse_inv); fr(P->st);
@@ -1210,9 +1442,21 @@ int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, c
 }
 
 void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs) {
-  if (P->bf16) cpr_apply<float, __nv_bfloat16>(P, v, z, stage, st, vs);
-  else if (P->fp32) cpr_apply<float, float>(P, v, z, stage, st, vs);
-  else cpr_apply<double, double>(P, v, z, stage, st, vs);
+  const int64_t n = 3 * P->mat->g.N;
+  const InV in{v, nullptr, n};
+  const OutV out{z, nullptr, n};
+  if (P->bf16) cpr_apply<float, __nv_bfloat16>(P, in, out, stage, st, vs);
+  else if (P->fp32) cpr_apply<float, float>(P, in, out, stage, st, vs);
+  else cpr_apply<double, double>(P, in, out, stage, st, vs);
+}
+
+void launch_cpr_split(bo_prec* P, const double* v, float* z, const DevState* st, const double* vs) {
+  const int64_t n = 3 * P->mat->g.N;
+  const InV in{v, nullptr, n};
+  const OutV out{nullptr, z, n};
+  if (P->bf16) cpr_apply<float, __nv_bfloat16>(P, in, out, BO_STAGE_CPR, st, vs);
+  else if (P->fp32) cpr_apply<float, float>(P, in, out, BO_STAGE_CPR, st, vs);
+  else cpr_apply<double, double>(P, in, out, BO_STAGE_CPR, st, vs);
 }
 
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {

@@ -217,8 +217,16 @@ def test_preconditioner_stages_match_oracle(bo, ctx, dims, stage):
     assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+@pytest.fixture(params=[1, 0], ids=["cooperative", "per_kernel"])
+def amg_launch(bo, request):
+    # both launch forms of the AMG's multi-block levels compute the same V-cycle
+    bo.bo_set_amg_cooperative(request.param)
+    yield request.param
+    bo.bo_set_amg_cooperative(1)
+
+
 @pytest.mark.parametrize("nu1,nu2,s", [(1, 1, 1.0), (2, 2, 1.3), (1, 0, 1.0), (0, 2, 1.5), (3, 1, 1.7)])
-def test_amg_cycle_variants_match_oracle(bo, ctx, nu1, nu2, s):
+def test_amg_cycle_variants_match_oracle(bo, ctx, nu1, nu2, s, amg_launch):
     # every smoothing/prolongation path: fused and explicit coarse correction,
     # zero pre-smoothing (full restriction of the residual)
     dims = (20, 20, 5)
@@ -233,7 +241,7 @@ def test_amg_cycle_variants_match_oracle(bo, ctx, nu1, nu2, s):
     assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
-def test_amg_multilevel_with_tail_matches_oracle(bo, ctx):
+def test_amg_multilevel_with_tail_matches_oracle(bo, ctx, amg_launch):
     # 96 x 96 x 40: level 1 (46,080 cells) runs on many blocks, levels from
     # 23 x 24 x 10 down run in the single-block tail kernel
     dims = (96, 96, 40)

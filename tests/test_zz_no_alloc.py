@@ -43,7 +43,10 @@ def test_residual_noalloc_matches_existing_entry_points():
         assert np.all(np.abs(r.cpu().numpy() - r_ref.cpu().numpy()) <= bound)
         nr, nb = norms.cpu().numpy()
         assert nb == pytest.approx(np.linalg.norm(a["b"]), rel=1e-13)
-        assert nr == pytest.approx(float(torch.linalg.norm(r_ref)), rel=1e-10)
+        # | ||r|| - ||r_ref|| | <= ||r - r_ref|| <= ||bound|| (triangle inequality),
+        # plus the rounding of the two norms' own sums
+        nref = float(torch.linalg.norm(r_ref))
+        assert abs(nr - nref) <= np.linalg.norm(bound) + 1e-12 * nref
         # the solve reports the same relative residual from its own reduction
         assert nr / nb == pytest.approx(info["true_rel_res"], rel=1e-6)
     # missing arguments are rejected, not dereferenced
