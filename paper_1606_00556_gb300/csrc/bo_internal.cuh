@@ -46,11 +46,14 @@ struct Cell {
 
 __host__ __device__ __forceinline__ int opposite(int slot) { return 6 - slot; }
 
+// (half indices are below 2^31 for any grid that fits one GPU: 32-bit
+// division is several times cheaper than 64-bit)
 __device__ __forceinline__ Cell decode(const Geom& g, int color, int64_t q) {
-  const int64_t r = q / g.hx;
-  const int32_t ih = (int32_t)(q - r * g.hx);
-  const int32_t j = (int32_t)(r % g.ny);
-  const int32_t k = (int32_t)(r / g.ny);
+  const uint32_t qu = (uint32_t)q, hx = (uint32_t)g.hx, ny = (uint32_t)g.ny;
+  const uint32_t r = qu / hx;
+  const int32_t ih = (int32_t)(qu - r * hx);
+  const int32_t j = (int32_t)(r % ny);
+  const int32_t k = (int32_t)(r / ny);
   const int32_t s = (color ^ j ^ k) & 1;
   return Cell{2 * ih + s, j, k, s};
 }
@@ -159,6 +162,18 @@ __device__ __forceinline__ df df_from(double v) {
   return df{h, __double2float_rn(v - (double)h)};
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+// The leading 24 significant bits of a as a float (truncated), by integer
+// operations on the bit pattern: no FP64 instruction.  Magnitudes beyond
+// FP32's normal range go to 0 or +-FLT_MAX.
+__device__ __forceinline__ float df_hi_bits(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff) - 1023;
+  if (e < -126) return __uint_as_float(sign);
+  if (e > 127) return __uint_as_float(sign | 0x7f7fffffu);
+  return __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+}
+
 // The same split by integer operations on the bit pattern (no FP64
 // instruction): hi keeps the leading 24 significant bits, lo the next 24
 // (both truncated), so |a - hi - lo| < 2^-46 |a|.  Below 2^-74 the low part
@@ -371,6 +386,7 @@ struct bo_prec {
   // Krylov workspace (FP64 unless noted)
   int mcap;                // restart length the workspace was sized for
   double* V;               // (mcap+1) 3N basis
+  float* Vs;               // (mcap+1) 3N FP32 shadow of the basis (first Gram-Schmidt pass)
   double* Z;               // mcap 3N preconditioned vectors as split pairs: per vector a hi plane, then a lo plane
   double* H;               // (mcap+1) mcap
   double* cs;

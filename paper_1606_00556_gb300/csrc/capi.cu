@@ -389,7 +389,7 @@ int bo_prec_destroy(bo_prec* P) {
   cudaStreamSynchronize(P->stream);
   prec_free(P);
   auto fr = [](void* p) { if (p) cudaFree(p); };
-  fr(P->V); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
+  fr(P->V); fr(P->Vs); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
   fr(P->xi); fr(P->bi); fr(P->rk); fr(P->partials); fr(P->hostio);
   if (P->h_st) cudaFreeHost(P->h_st);
   for (int e = 0; e < 4; ++e)

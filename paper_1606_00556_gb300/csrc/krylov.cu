@@ -19,6 +19,13 @@
 // spent normalising.  On GB300 these passes are bound jointly by FP64
 // arithmetic and HBM (one FMA per 8 bytes read).
 //
+// The first coefficient pass reads an FP32 shadow of the basis (each basis
+// vector's leading 24 bits, written beside it) and sums in FP32: CGS2's
+// second pass, in FP64, removes whatever the first left in span(V), and the
+// FP64 updates subtract exactly the coefficients they are given, so the
+// Arnoldi relation A z_j = V h_j holds to FP64 rounding whatever the first
+// pass's error.  That takes a quarter of the FP64 work out of each column.
+//
 // The Arnoldi product w = A z_j reads a split copy of A (each value as an
 // unevaluated sum hi + lo of two floats, 48 significant bits; see df in
 // bo_internal.cuh) in a tiled layout, and the preconditioned vectors Z are
@@ -47,7 +54,7 @@ namespace {
 constexpr int kRedBlocks = 4 * 152;  // blocks of single reductions
 constexpr int kMaxM = 64;
 constexpr int kHistCap = 4096;
-constexpr int kDotBlocks = 2 * 152;  // most chunks of the multi-dot pass
+constexpr int kDotBlocks = 2 * 152;  // most chunks of a coefficient pass (partials per column)
 
 // acc + a0 x0 + a1 x1 + a2 x2 in split arithmetic (low parts collected lazily)
 __device__ __forceinline__ df dfma3(df acc, float2 a0, df x0, float2 a1, df x1, float2 a2, df x2) {
@@ -62,7 +69,7 @@ __device__ __forceinline__ df dfma3(df acc, float2 a0, df x0, float2 a1, df x1, 
 __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2* __restrict__ A2,
                                                           const double* __restrict__ A, const int* __restrict__ range,
                                                           const float* __restrict__ z, double* __restrict__ w,
-                                                          const DevState* st) {
+                                                          float* __restrict__ ws, const DevState* st) {
   if (st->done) return;
   const int64_t n = 3 * g.N;
   const bool fp64 = *range != 0;
@@ -72,6 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
     const Cell c = decode(g, color, q);
     const size_t P = (size_t)g.Nh;
     double r0, r1, r2;
+    float h0, h1, h2;  // FP32 shadow of w for the first Gram-Schmidt pass
     if (!fp64) {
       df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f};
 #pragma unroll
@@ -86,9 +94,13 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
         a1 = dfma3(a1, __ldcs(a + 96), x0, __ldcs(a + 128), x1, __ldcs(a + 160), x2);
         a2 = dfma3(a2, __ldcs(a + 192), x0, __ldcs(a + 224), x1, __ldcs(a + 256), x2);
       }
-      r0 = df_to_double(df_norm(a0));
-      r1 = df_to_double(df_norm(a1));
-      r2 = df_to_double(df_norm(a2));
+      const df n0 = df_norm(a0), n1 = df_norm(a1), n2 = df_norm(a2);
+      r0 = df_to_double(n0);
+      r1 = df_to_double(n1);
+      r2 = df_to_double(n2);
+      h0 = n0.hi;
+      h1 = n1.hi;
+      h2 = n2.hi;
     } else {
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int sl = 0; sl < 7; ++sl) {
@@ -106,10 +118,16 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
       r0 = a0;
       r1 = a1;
       r2 = a2;
+      h0 = (float)a0;
+      h1 = (float)a1;
+      h2 = (float)a2;
     }
     w[t] = r0;
     w[g.N + t] = r1;
     w[2 * g.N + t] = r2;
+    ws[t] = h0;
+    ws[g.N + t] = h1;
+    ws[2 * g.N + t] = h2;
   }
 }
 
@@ -201,11 +219,15 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
   }
 }
 
-// v = src / beta
-__global__ void k_scale_beta(int64_t n, const double* __restrict__ src, double* __restrict__ v, const DevState* st) {
+// v = src / beta, and its FP32 shadow
+__global__ void k_scale_beta(int64_t n, const double* __restrict__ src, double* __restrict__ v,
+                             float* __restrict__ vs, const DevState* st) {
   const double s = st->beta > 0.0 ? 1.0 / st->beta : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = src[i] * s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = src[i] * s;
+    v[i] = t;
+    vs[i] = df_hi_bits(t);
+  }
 }
 
 // Hessenberg column j from the coefficients col[0..j] and h_{j+1,j} = hn:
@@ -252,10 +274,14 @@ struct ArnoldiArgs {
 };
 
 // Gram-Schmidt coefficient pass: h[off + u] = vscale[u] <V_u, w> for u <= j.
-// Grid (chunks, j + 1): block (c, u) sums column u over chunk c; the block
-// that finishes last reduces each column's partials with one warp per column.
-__global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const double* __restrict__ V, int64_t ldv,
-                                                     const double* __restrict__ w, double* partials, DevState* st,
+// Grid (chunks, j + 1): block (c, u) sums column u over chunk c (products
+// and the per-thread sum in R, the block sum in FP64); the block that
+// finishes last reduces each column's partials with one warp per column.
+// R = float: the first pass, on the FP32 shadows of V and w (ldv floats
+// apart); R = double: the second pass, on V and w in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const R* __restrict__ V, int64_t ldv,
+                                                     const R* __restrict__ w, double* partials, DevState* st,
                                                      int off) {
   __shared__ double sh[32];
   if (st->done) return;
@@ -265,11 +291,11 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const double* _
   const int64_t len = (n + nchunk - 1) / nchunk;
   const int64_t i0 = blockIdx.x * len;
   const int64_t i1 = min(n, i0 + len);
-  const double* a = V + (size_t)u * ldv;
-  double acc = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += a[i] * w[i];
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = acc;
+  const R* a = V + (size_t)u * ldv;
+  R acc = R(0);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fma(a[i], w[i], acc);
+  const double sum = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
   if (!last_block(&st->counter[0], nchunk * nv)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = warp; r < nv; r += kThreads / 32) {
@@ -287,8 +313,8 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const double* _
 // (w itself stays unnormalised).
 template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double* __restrict__ V, int64_t ldv,
-                                                       double* __restrict__ w, double* partials, DevState* st,
-                                                       ArnoldiArgs aa) {
+                                                       double* __restrict__ w, float* __restrict__ ws,
+                                                       double* partials, DevState* st, ArnoldiArgs aa) {
   __shared__ double c[kMaxM + 1];
   __shared__ double sh[32];
   if (st->done) return;
@@ -301,7 +327,10 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double*
     double s = w[i];
     for (int k = 0; k < nv; ++k) s -= c[k] * V[(size_t)k * ldv + i];
     w[i] = s;
-    if (LAST) acc += s * s;
+    if (LAST) {
+      acc += s * s;
+      ws[i] = df_hi_bits(s);  // the new basis vector's FP32 shadow (integer operations)
+    }
   }
   if (!LAST) return;
   acc = block_sum(acc, sh);
@@ -320,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double*
 int gs_chunks(int64_t n) {
   int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
   if (c < 1) c = 1;
-  if (c > 2 * 152) c = 2 * 152;
+  if (c > kDotBlocks) c = kDotBlocks;
   return (int)c;
 }
 
@@ -386,8 +415,8 @@ int krylov_alloc(bo_prec* P, int m) {
   const Geom& g = P->mat->g;
   const int64_t n = 3 * g.N;
   auto fr = [](void* p) { if (p) cudaFree(p); };
-  fr(P->V); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
-  P->V = nullptr; P->Z = nullptr;
+  fr(P->V); fr(P->Vs); fr(P->Z); fr(P->H); fr(P->cs); fr(P->sn); fr(P->gvec); fr(P->y);
+  P->V = nullptr; P->Vs = nullptr; P->Z = nullptr;
   bool ok = true;
   auto al = [&](size_t bytes) -> void* {
     void* p = nullptr;
@@ -395,6 +424,7 @@ int krylov_alloc(bo_prec* P, int m) {
     return p;
   };
   P->V = (double*)al((size_t)(m + 1) * n * sizeof(double));
+  P->Vs = (float*)al((size_t)(m + 1) * n * sizeof(float));
   P->Z = (double*)al((size_t)m * n * sizeof(double));
   P->H = (double*)al((size_t)(m + 1) * m * sizeof(double));
   P->cs = (double*)al((size_t)m * sizeof(double));
@@ -502,7 +532,7 @@ struct Job {
   void start_cycle() {
     cudaStream_t s = stream();
     (k_cycle_start<<<1, 64, 0, s>>>(P->st, P->gvec, o.restart), note_launch());
-    (k_scale_beta<<<grid_for(n()), kThreads, 0, s>>>(n(), P->rk, P->V, P->st), note_launch());
+    (k_scale_beta<<<grid_for(n()), kThreads, 0, s>>>(n(), P->rk, P->V, P->Vs, P->st), note_launch());
     j_enq = j_polled = 0;
     cycle_stop = false;
     phase = kColumns;
@@ -526,20 +556,22 @@ struct Job {
       e1 = P->prof_ev[2 * prof.size() + 1];
       cudaEventRecord(e0, s);
     }
+    float* ws = P->Vs + (size_t)(j + 1) * ldv;
     (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(
-         g, P->mat->A2, P->mat->A, P->mat->a2_range, zj, w, st),
+         g, P->mat->A2, P->mat->A, P->mat->a2_range, zj, w, ws, st),
      note_launch());
     if (e1) {
       cudaEventRecord(e1, s);
       prof.push_back({e0, e1});
     }
     const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
-    const dim3 gd(gs_chunks(nn), j + 1);
+    const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
-    (k_gs_dots<<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, 0), note_launch());
-    (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, aa), note_launch());
-    (k_gs_dots<<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
-    (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, aa), note_launch());
+    const dim3 gd(gs_chunks(nn), nv);
+    (k_gs_dots<float><<<gd, kThreads, 0, s>>>(nn, P->Vs, ldv, ws, P->partials, st, 0), note_launch());
+    (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, ws, P->partials, st, aa), note_launch());
+    (k_gs_dots<double><<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
+    (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, ws, P->partials, st, aa), note_launch());
   }
 
   // Column j's kernels captured once into a CUDA graph (on a private stream,

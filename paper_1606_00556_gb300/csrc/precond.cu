@@ -236,6 +236,16 @@ struct LevelDims {
   int64_t n;
 };
 
+// (i, j, k) of natural index c of a level (c < 2^31), by 32-bit division
+struct Ijk {
+  int i, j, k;
+};
+__device__ __forceinline__ Ijk ijk_of(const LevelDims& L, int64_t c) {
+  const uint32_t cu = (uint32_t)c, nx = (uint32_t)L.nx, ny = (uint32_t)L.ny;
+  const uint32_t r = cu / nx;
+  return Ijk{(int)(cu - r * nx), (int)(r % ny), (int)(r / ny)};
+}
+
 __device__ __forceinline__ int64_t nat_index(const LevelDims& L, int i, int j, int k) {
   return i + (int64_t)L.nx * (j + (int64_t)L.ny * k);
 }
@@ -256,7 +266,8 @@ __device__ __forceinline__ int dir_slot(int di, int dj, int dk) {
 __global__ void k_galerkin0(Geom g, const double* __restrict__ A, const double* __restrict__ w, LevelDims C,
                             double* __restrict__ c64, DevState* st) {
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+    const Ijk cc = ijk_of(C, I);
+  const int ci = cc.i, cj = cc.j, ck = cc.k;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
@@ -286,7 +297,8 @@ __global__ void k_galerkin0(Geom g, const double* __restrict__ A, const double* 
 __global__ void k_galerkinn(LevelDims F, const double* __restrict__ f64, LevelDims C, double* __restrict__ c64,
                             DevState* st) {
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+    const Ijk cc = ijk_of(C, I);
+  const int ci = cc.i, cj = cc.j, ck = cc.k;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
@@ -700,7 +712,8 @@ __global__ void k_gs0_prolong(Geom g, const S* __restrict__ At, const T* __restr
 template <typename T, typename S>
 __device__ __forceinline__ T restrict0_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
                                             const T* __restrict__ x, const LevelDims& C, int64_t I, int red_only) {
-  const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+  const Ijk cc = ijk_of(C, I);
+  const int ci = cc.i, cj = cc.j, ck = cc.k;
   T acc = T(0);
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj)
@@ -761,7 +774,8 @@ struct LevelView {
 
 template <typename T, typename S>
 __device__ __forceinline__ void gs_cell(const LevelView<T, S>& L, int64_t cidx, int color, int zero_guess) {
-  const int i = (int)(cidx % L.d.nx), j = (int)((cidx / L.d.nx) % L.d.ny), k = (int)(cidx / ((int64_t)L.d.nx * L.d.ny));
+  const Ijk p = ijk_of(L.d, cidx);
+  const int i = p.i, j = p.j, k = p.k;
   if (((i + j + k) & 1) != color) return;
   T s = L.f[cidx];
   if (!zero_guess) {
@@ -792,7 +806,8 @@ __device__ __forceinline__ T residual_cell(const LevelView<T, S>& L, int i, int 
 
 template <typename T, typename S>
 __device__ __forceinline__ T restrict_cell(const LevelView<T, S>& F, const LevelDims& C, int64_t I, int red_only) {
-  const int ci = (int)(I % C.nx), cj = (int)((I / C.nx) % C.ny), ck = (int)(I / ((int64_t)C.nx * C.ny));
+  const Ijk cc = ijk_of(C, I);
+  const int ci = cc.i, cj = cc.j, ck = cc.k;
   T acc = T(0);
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj)
@@ -807,7 +822,8 @@ __device__ __forceinline__ T restrict_cell(const LevelView<T, S>& F, const Level
 
 template <typename T, typename S>
 __device__ __forceinline__ void prolong_cell(const LevelView<T, S>& F, const LevelView<T, S>& C, int64_t cidx, T s) {
-  const int i = (int)(cidx % F.d.nx), j = (int)((cidx / F.d.nx) % F.d.ny), k = (int)(cidx / ((int64_t)F.d.nx * F.d.ny));
+  const Ijk p = ijk_of(F.d, cidx);
+  const int i = p.i, j = p.j, k = p.k;
   F.x[cidx] += s * C.x[nat_index(C.d, i / 2, j / 2, k / 2)];
 }
 
@@ -815,7 +831,8 @@ __device__ __forceinline__ void prolong_cell(const LevelView<T, S>& F, const Lev
 // (the natural-order counterpart of k_gs0_prolong)
 template <typename T, typename S>
 __device__ __forceinline__ void gs_cell_prolong(const LevelView<T, S>& L, const LevelView<T, S>& C, int64_t cidx, T sc) {
-  const int i = (int)(cidx % L.d.nx), j = (int)((cidx / L.d.nx) % L.d.ny), k = (int)(cidx / ((int64_t)L.d.nx * L.d.ny));
+  const Ijk p = ijk_of(L.d, cidx);
+  const int i = p.i, j = p.j, k = p.k;
   if (((i + j + k) & 1) != 1) return;
   const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
   T s = L.f[cidx];
@@ -984,6 +1001,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
 // barrier records kErrTimeout, and every later barrier of the launch fails
 // at once, so the kernel returns and the solve reports BO_ERR_TIMEOUT.
 constexpr unsigned kBarrierSpins = 1u << 22;
+// one block of 1024 threads per SM: a quarter of the arrivals at each
+// barrier of four 256-thread blocks, for the same threads
+constexpr int kCoopThreads = 1024;
 
 __device__ __forceinline__ bool grid_barrier(DevState* st) {
   __shared__ int ok;
@@ -1034,7 +1054,7 @@ struct CycleArgs {
 // natural-order levels 1 .. tail_from - 1, a grid barrier after every half
 // sweep (the kernel-per-half-sweep form launches each separately).
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads) k_amg_down(CycleArgs<T, S> a, DevState* st) {
+__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a, DevState* st) {
   if (st->done) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
   const Geom& g = a.g;
@@ -1071,7 +1091,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_down(CycleArgs<T, S> a, DevSta
 // Up leg: post-smoothing of levels tail_from - 1 .. 1 and then level 0, the
 // first (black) half sweep of each level reading the coarse correction
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads) k_amg_up(CycleArgs<T, S> a, DevState* st) {
+__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, DevState* st) {
   if (st->done) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
   const Geom& g = a.g;
@@ -1202,8 +1222,9 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   const bool coop = g_amg_coop.load() != 0 && cap == cudaStreamCaptureStatusNone;
   bool down_done = false;
   if (coop) {
-    const int gd = occ_grid((const void*)k_amg_down<T, S>, g.Nh);
-    down_done = cudaLaunchCooperativeKernel((const void*)k_amg_down<T, S>, gd, kThreads, cargs, 0, s) == cudaSuccess;
+    const int gd = occ_grid((const void*)k_amg_down<T, S>, g.Nh, kCoopThreads);
+    down_done =
+        cudaLaunchCooperativeKernel((const void*)k_amg_down<T, S>, gd, kCoopThreads, cargs, 0, s) == cudaSuccess;
     if (down_done) note_launch();
     else cudaGetLastError();
   }
@@ -1243,8 +1264,8 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
   }
   if (coop) {
-    const int gu = occ_grid((const void*)k_amg_up<T, S>, g.Nh);
-    if (cudaLaunchCooperativeKernel((const void*)k_amg_up<T, S>, gu, kThreads, cargs, 0, s) == cudaSuccess) {
+    const int gu = occ_grid((const void*)k_amg_up<T, S>, g.Nh, kCoopThreads);
+    if (cudaLaunchCooperativeKernel((const void*)k_amg_up<T, S>, gu, kCoopThreads, cargs, 0, s) == cudaSuccess) {
       note_launch();
       return;
     }
