@@ -651,8 +651,8 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
 // ---- AMG level 0 (colour-split, coefficients = plane (colour, slot, 0) of At)
 // One cell of a level-0 Gauss-Seidel half sweep.
 template <typename T, typename S>
-__device__ __forceinline__ void gs0_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
-                                         T* __restrict__ x, int color, int zero_guess, int64_t q) {
+__device__ __forceinline__ T gs0_value(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                      const T* __restrict__ x, int color, int zero_guess, int64_t q) {
   const int oc = color ^ 1;
   T s = f[(size_t)color * g.Nh + q];
   if (!zero_guess) {
@@ -665,7 +665,34 @@ __device__ __forceinline__ void gs0_cell(const Geom& g, const S* __restrict__ At
       s -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)oc * g.Nh + nq];
     }
   }
-  x[(size_t)color * g.Nh + q] = s / cv<T>(At[plane(g, color, kDiag, 0) + q]);
+  return s / cv<T>(At[plane(g, color, kDiag, 0) + q]);
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ void gs0_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                         T* __restrict__ x, int color, int zero_guess, int64_t q) {
+  x[(size_t)color * g.Nh + q] = gs0_value<T, S>(g, At, f, x, color, zero_guess, q);
+}
+
+// A level-0 half sweep over a grid-stride range, B cells per thread at a
+// time: the loads of all B cells are issued before any store (the stores go
+// to this colour's half of x, which no cell of the sweep reads), so a
+// thread's cells overlap their memory latency instead of queueing it.
+template <int B, typename T, typename F>
+__device__ __forceinline__ void sweep_batched(int64_t t0, int64_t nt, int64_t n, T* __restrict__ out, F value) {
+  for (int64_t q0 = t0; q0 < n; q0 += (int64_t)B * nt) {
+    T v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int64_t q = q0 + b * nt;
+      v[b] = q < n ? value(q) : T(0);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int64_t q = q0 + b * nt;
+      if (q < n) out[q] = v[b];
+    }
+  }
 }
 
 template <typename T, typename S>
@@ -682,9 +709,9 @@ __global__ void k_gs0(Geom g, const S* __restrict__ At, const T* __restrict__ f,
 // cells, because the black sweep overwrites x_b and the red sweep that
 // follows overwrites x_r without reading its old value.
 template <typename T, typename S>
-__device__ __forceinline__ void gs0_prolong_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
-                                                 T* __restrict__ x, const LevelDims& C, const T* __restrict__ xc,
-                                                 T sc, int64_t q) {
+__device__ __forceinline__ T gs0_prolong_value(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                              const T* __restrict__ x, const LevelDims& C, const T* __restrict__ xc,
+                                              T sc, int64_t q) {
   const int di[7] = {0, 0, -1, 0, 1, 0, 0}, dj[7] = {0, -1, 0, 0, 0, 1, 0}, dk[7] = {-1, 0, 0, 0, 0, 0, 1};
   const Cell c = decode(g, 1, q);
   T s = f[(size_t)g.Nh + q];
@@ -696,7 +723,14 @@ __device__ __forceinline__ void gs0_prolong_cell(const Geom& g, const S* __restr
     const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
     s -= cv<T>(At[plane(g, 1, sl, 0) + q]) * xv;
   }
-  x[(size_t)g.Nh + q] = s / cv<T>(At[plane(g, 1, kDiag, 0) + q]);
+  return s / cv<T>(At[plane(g, 1, kDiag, 0) + q]);
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ void gs0_prolong_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
+                                                 T* __restrict__ x, const LevelDims& C, const T* __restrict__ xc,
+                                                 T sc, int64_t q) {
+  x[(size_t)g.Nh + q] = gs0_prolong_value<T, S>(g, At, f, x, C, xc, sc, q);
 }
 
 template <typename T, typename S>
@@ -1060,7 +1094,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
   const Geom& g = a.g;
   for (int sw = 0; sw < a.nu1; ++sw)
     for (int color = 0; color < 2; ++color) {
-      for (int64_t q = t0; q < g.Nh; q += nt) gs0_cell<T, S>(g, a.At, a.f0, a.x0, color, sw == 0 && color == 0, q);
+      const int zero = sw == 0 && color == 0;
+      sweep_batched<4>(t0, nt, g.Nh, a.x0 + (size_t)color * g.Nh,
+                       [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, color, zero, q); });
       if (!grid_barrier(st)) return;
     }
   if (a.nu1 == 0) {
@@ -1117,12 +1153,15 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
     return;
   }
   for (int sw = 0; sw < a.nu2; ++sw) {
-    for (int64_t q = t0; q < g.Nh; q += nt) {
-      if (sw == 0) gs0_prolong_cell<T, S>(g, a.At, a.f0, a.x0, C1.d, C1.x, a.s, q);
-      else gs0_cell<T, S>(g, a.At, a.f0, a.x0, 1, 0, q);
-    }
+    if (sw == 0)
+      sweep_batched<4>(t0, nt, g.Nh, a.x0 + g.Nh, [&](int64_t q) {
+        return gs0_prolong_value<T, S>(g, a.At, a.f0, a.x0, C1.d, C1.x, a.s, q);
+      });
+    else
+      sweep_batched<4>(t0, nt, g.Nh, a.x0 + g.Nh,
+                       [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 1, 0, q); });
     if (!grid_barrier(st)) return;
-    for (int64_t q = t0; q < g.Nh; q += nt) gs0_cell<T, S>(g, a.At, a.f0, a.x0, 0, 0, q);
+    sweep_batched<4>(t0, nt, g.Nh, a.x0, [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 0, 0, q); });
     if (sw + 1 < a.nu2 && !grid_barrier(st)) return;
   }
 }
