@@ -91,6 +91,12 @@ __host__ __device__ __forceinline__ size_t a2_index(const Geom& g, int color, in
   return (((size_t)color * a2_tiles(g) + (size_t)(q >> 5)) * 63 + (size_t)v) * 32 + (size_t)(q & 31);
 }
 
+// The decoupled matrix of the preconditioner uses the same tiles (its
+// kernels read a block's entries 32 apart).
+__host__ __device__ __forceinline__ size_t at_index(const Geom& g, int color, int v, int64_t q) {
+  return a2_index(g, color, v, q);
+}
+
 // streaming (evict-first) loads for matrix values that are read once per pass
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
@@ -365,7 +371,7 @@ struct bo_prec {
   size_t tsize;            // sizeof(preconditioner vector scalar / arithmetic)
   size_t ssize;            // sizeof(stored matrix, pivot and AMG coefficient)
   bool bf16;               // BF16 storage of those (arithmetic FP32)
-  void* At;                // 63 N decoupled values (preconditioner precision)
+  void* At;                // 63 N decoupled values (preconditioner precision), tiled (at_index)
   double* w;               // 3 N decoupling weights (g0, g1, g2) of row 0, [3][N] internal order
   float* wf;               // the same weights rounded to FP32 (FP32 arithmetic), else NULL
   void* Dinv;              // 9 N inverted ILU pivot blocks [rc][N], preconditioner precision

@@ -126,9 +126,14 @@ __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst
     dst[i] = (float)src[i];
 }
 
-// y = alpha A x + beta y on natural-order interleaved vectors.  One thread
-// per cell; neighbouring lanes alternate colours, so each warp reads 16
-// consecutive values from each colour's plane per load instruction.
+// y = alpha A x + beta y on natural-order interleaved vectors.
+// FP64 values: one thread per pair of cells (2q, 2q+1) of a grid row (nx is
+// even); the two cells have the two colours and the same half index q, so a
+// warp reads 32 consecutive values of each plane of each colour per load
+// instruction, and writes the pair's six consecutive outputs.  FP32 and BF16
+// values: one thread per cell; neighbouring lanes alternate colours, and the
+// warp's gathers of x stay within fewer lines, which matters more once the
+// matrix bytes are halved or quartered.
 template <typename TM>
 __device__ __forceinline__ float to_f(TM v) { return (float)v; }
 template <>
@@ -140,42 +145,54 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return _
 template <typename TM, typename TA>
 __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restrict__ A, const double* __restrict__ x,
                                                       double* __restrict__ y, double alpha, double beta) {
+  constexpr int H = sizeof(TA) == 8 ? 2 : 1;  // cells per thread
   const int64_t nxy = (int64_t)g.nx * g.ny;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
-    const Nat n = decode_nat(g, c);
-    const unsigned valid = valid_slots(g, n);
-    const int64_t off[7] = {-nxy, -(int64_t)g.nx, -1, 0, 1, (int64_t)g.nx, nxy};
-    TA acc0 = 0, acc1 = 0, acc2 = 0;
+  const int64_t off[7] = {-nxy, -(int64_t)g.nx, -1, 0, 1, (int64_t)g.nx, nxy};
+  const int64_t nu = g.N / H;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nu; q += (int64_t)gridDim.x * blockDim.x) {
+    TA acc[H][3];
 #pragma unroll
-    for (int s = 0; s < 7; ++s) {
-      if ((valid >> s) & 1u) {
-        const int64_t nc = c + off[s];
-        const TA x0 = (TA)__ldg(x + 3 * nc), x1 = (TA)__ldg(x + 3 * nc + 1), x2 = (TA)__ldg(x + 3 * nc + 2);
-        const TM* a = A + plane(g, n.color, s, 0) + n.q;
-        const size_t P = (size_t)g.Nh;
-        if constexpr (sizeof(TA) == 8) {
-          acc0 = fma3(acc0, (TA)ld_stream(a), x0, (TA)ld_stream(a + P), x1, (TA)ld_stream(a + 2 * P), x2);
-          acc1 = fma3(acc1, (TA)ld_stream(a + 3 * P), x0, (TA)ld_stream(a + 4 * P), x1, (TA)ld_stream(a + 5 * P), x2);
-          acc2 = fma3(acc2, (TA)ld_stream(a + 6 * P), x0, (TA)ld_stream(a + 7 * P), x1, (TA)ld_stream(a + 8 * P), x2);
-        } else {
-          acc0 = fma3(acc0, to_f(ld_stream(a)), x0, to_f(ld_stream(a + P)), x1, to_f(ld_stream(a + 2 * P)), x2);
-          acc1 = fma3(acc1, to_f(ld_stream(a + 3 * P)), x0, to_f(ld_stream(a + 4 * P)), x1, to_f(ld_stream(a + 5 * P)),
-                      x2);
-          acc2 = fma3(acc2, to_f(ld_stream(a + 6 * P)), x0, to_f(ld_stream(a + 7 * P)), x1, to_f(ld_stream(a + 8 * P)),
-                      x2);
+    for (int h = 0; h < H; ++h) {
+      const int64_t c = H * q + h;
+      const Nat n = decode_nat(g, c);
+      const unsigned valid = valid_slots(g, n);
+      TA acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        if ((valid >> s) & 1u) {
+          const int64_t nc = c + off[s];
+          const TA x0 = (TA)__ldg(x + 3 * nc), x1 = (TA)__ldg(x + 3 * nc + 1), x2 = (TA)__ldg(x + 3 * nc + 2);
+          const TM* a = A + plane(g, n.color, s, 0) + n.q;
+          const size_t P = (size_t)g.Nh;
+          if constexpr (sizeof(TA) == 8) {
+            acc0 = fma3(acc0, (TA)ld_stream(a), x0, (TA)ld_stream(a + P), x1, (TA)ld_stream(a + 2 * P), x2);
+            acc1 = fma3(acc1, (TA)ld_stream(a + 3 * P), x0, (TA)ld_stream(a + 4 * P), x1, (TA)ld_stream(a + 5 * P), x2);
+            acc2 = fma3(acc2, (TA)ld_stream(a + 6 * P), x0, (TA)ld_stream(a + 7 * P), x1, (TA)ld_stream(a + 8 * P), x2);
+          } else {
+            acc0 = fma3(acc0, to_f(ld_stream(a)), x0, to_f(ld_stream(a + P)), x1, to_f(ld_stream(a + 2 * P)), x2);
+            acc1 = fma3(acc1, to_f(ld_stream(a + 3 * P)), x0, to_f(ld_stream(a + 4 * P)), x1,
+                        to_f(ld_stream(a + 5 * P)), x2);
+            acc2 = fma3(acc2, to_f(ld_stream(a + 6 * P)), x0, to_f(ld_stream(a + 7 * P)), x1,
+                        to_f(ld_stream(a + 8 * P)), x2);
+          }
         }
       }
+      acc[h][0] = acc0;
+      acc[h][1] = acc1;
+      acc[h][2] = acc2;
     }
-    if (beta == 0.0) {
-      y[3 * c] = alpha * (double)acc0;
-      y[3 * c + 1] = alpha * (double)acc1;
-      y[3 * c + 2] = alpha * (double)acc2;
-    } else {
-      y[3 * c] = alpha * (double)acc0 + beta * y[3 * c];
-      y[3 * c + 1] = alpha * (double)acc1 + beta * y[3 * c + 1];
-      y[3 * c + 2] = alpha * (double)acc2 + beta * y[3 * c + 2];
+    double* yo = y + 3 * H * q;
+#pragma unroll
+    for (int r = 0; r < 3 * H; ++r) {
+      const double v = alpha * (double)acc[r / 3][r % 3];
+      yo[r] = beta == 0.0 ? v : v + beta * yo[r];
     }
   }
+}
+
+__global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn((float)src[i]);
 }
 
 // split (hi, lo) copy of the matrix values for the Arnoldi product, in the
@@ -189,11 +206,6 @@ __global__ void k_split_matrix(Geom g, const double* __restrict__ src, float2* _
     dst[a2_index(g, p / 63, p % 63, q)] = df_split_bits(src[i], &bad);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(range, 1);
-}
-
-__global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = __float2bfloat16_rn((float)src[i]);
 }
 
 __global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
@@ -243,7 +255,7 @@ void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
 }
 
 void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
-  const int grid = grid_for(m->g.N, kThreads, 152 * 64);
+  const int grid = grid_for(precision == BO_PREC_FP64 ? m->g.Nh : m->g.N, kThreads, 152 * 64);
   if (precision == BO_PREC_FP32)
     (k_spmv_nat<float, float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A32, x, y, alpha, beta), note_launch());
   else if (precision == BO_PREC_BF16)

@@ -157,9 +157,9 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__
       for (int rc = 0; rc < 9; ++rc) a[rc] = A[plane(g, color, s, rc) + q];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        At[plane(g, color, s, c) + q] = to_store<S>(g0 * a[c] + g1 * a[3 + c] + g2 * a[6 + c]);
-        At[plane(g, color, s, 3 + c) + q] = to_store<S>(a[3 + c]);
-        At[plane(g, color, s, 6 + c) + q] = to_store<S>(a[6 + c]);
+        At[at_index(g, color, s * 9 + c, q)] = to_store<S>(g0 * a[c] + g1 * a[3 + c] + g2 * a[6 + c]);
+        At[at_index(g, color, s * 9 + 3 + c, q)] = to_store<S>(a[3 + c]);
+        At[at_index(g, color, s * 9 + 6 + c, q)] = to_store<S>(a[6 + c]);
       }
       if (s == kDiag) {
         const double app = g0 * a[0] + g1 * a[3] + g2 * a[6];
@@ -519,8 +519,8 @@ __device__ __forceinline__ void offdiag_sum(const Geom& g, const S* __restrict__
     const int64_t nq = nbr(g, c, q, sl);
     if (nq < 0) continue;
     const T u0 = u[vidx(g, 0, oc, nq)], u1 = u[vidx(g, 1, oc, nq)], u2 = u[vidx(g, 2, oc, nq)];
-    const S* a = At + plane(g, color, sl, 0) + q;
-    const size_t P = (size_t)g.Nh;
+    const S* a = At + at_index(g, color, sl * 9, q);
+    constexpr size_t P = 32;  // entries (rc) of a block lie 32 apart in a tile
     s[0] = fma3(s[0], cv<T>(ld_stream(a)), u0, cv<T>(ld_stream(a + P)), u1, cv<T>(ld_stream(a + 2 * P)), u2);
     s[1] = fma3(s[1], cv<T>(ld_stream(a + 3 * P)), u0, cv<T>(ld_stream(a + 4 * P)), u1, cv<T>(ld_stream(a + 5 * P)), u2);
     s[2] = fma3(s[2], cv<T>(ld_stream(a + 6 * P)), u0, cv<T>(ld_stream(a + 7 * P)), u1, cv<T>(ld_stream(a + 8 * P)), u2);
@@ -624,8 +624,8 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
       T x0 = z[vidx(g, 0, xc, nq)];
       if (ROWS == 3) x0 += e[(size_t)xc * g.Nh + nq];
       const T x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
-      const S* a = At + plane(g, color, sl, 0) + q;
-      const size_t P = (size_t)g.Nh;
+      const S* a = At + at_index(g, color, sl * 9, q);
+      constexpr size_t P = 32;  // entries (rc) of a block lie 32 apart in a tile
 #pragma unroll
       for (int r = 0; r < ROWS; ++r)
         acc[r] = fma3(acc[r], cv<T>(ld_stream(a + 3 * r * P)), x0, cv<T>(ld_stream(a + (3 * r + 1) * P)), x1,
@@ -662,10 +662,10 @@ __device__ __forceinline__ T gs0_value(const Geom& g, const S* __restrict__ At, 
       if (sl == kDiag) continue;
       const int64_t nq = nbr(g, c, q, sl);
       if (nq < 0) continue;
-      s -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)oc * g.Nh + nq];
+      s -= cv<T>(At[at_index(g, color, sl * 9, q)]) * x[(size_t)oc * g.Nh + nq];
     }
   }
-  return s / cv<T>(At[plane(g, color, kDiag, 0) + q]);
+  return s / cv<T>(At[at_index(g, color, kDiag * 9, q)]);
 }
 
 template <typename T, typename S>
@@ -721,9 +721,9 @@ __device__ __forceinline__ T gs0_prolong_value(const Geom& g, const S* __restric
     const int64_t nq = nbr(g, c, q, sl);
     if (nq < 0) continue;
     const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
-    s -= cv<T>(At[plane(g, 1, sl, 0) + q]) * xv;
+    s -= cv<T>(At[at_index(g, 1, sl * 9, q)]) * xv;
   }
-  return s / cv<T>(At[plane(g, 1, kDiag, 0) + q]);
+  return s / cv<T>(At[at_index(g, 1, kDiag * 9, q)]);
 }
 
 template <typename T, typename S>
@@ -764,7 +764,7 @@ __device__ __forceinline__ T restrict0_cell(const Geom& g, const S* __restrict__
           const int64_t nq = nbr(g, c, q, sl);
           if (nq < 0) continue;
           const int xc = (sl == kDiag) ? color : (color ^ 1);
-          r -= cv<T>(At[plane(g, color, sl, 0) + q]) * x[(size_t)xc * g.Nh + nq];
+          r -= cv<T>(At[at_index(g, color, sl * 9, q)]) * x[(size_t)xc * g.Nh + nq];
         }
         acc += r;
       }
@@ -1072,6 +1072,12 @@ __device__ __forceinline__ bool grid_barrier(DevState* st) {
   return ok;
 }
 
+// (i + j + k) even at a natural-order level
+__device__ __forceinline__ bool red_cell(const LevelDims& L, int64_t c) {
+  const Ijk p = ijk_of(L, c);
+  return ((p.i + p.j + p.k) & 1) == 0;
+}
+
 template <typename T, typename S>
 struct CycleArgs {
   Geom g;
@@ -1103,16 +1109,25 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
     for (int64_t t = t0; t < g.N; t += nt) a.x0[t] = T(0);
     if (!grid_barrier(st)) return;
   }
+  // The first pre-smoothing half sweep of a multi-block level starts from
+  // zero, x_r = f_r / a_rr: the thread that restricts a red cell's
+  // right-hand side computes it at once, which saves that sweep's barrier.
   {
     const LevelView<T, S>& C = a.lv[1];
-    for (int64_t I = t0; I < C.d.n; I += nt) C.f[I] = restrict0_cell<T, S>(g, a.At, a.f0, a.x0, C.d, I, a.nu1 > 0);
+    const bool fold = a.nu1 > 0 && 1 < a.tail_from;
+    for (int64_t I = t0; I < C.d.n; I += nt) {
+      const T fI = restrict0_cell<T, S>(g, a.At, a.f0, a.x0, C.d, I, a.nu1 > 0);
+      C.f[I] = fI;
+      if (fold && red_cell(C.d, I)) C.x[I] = fI / C.cc(kDiag, I);
+    }
   }
   for (int l = 1; l < a.tail_from; ++l) {
     if (!grid_barrier(st)) return;
     const LevelView<T, S>& L = a.lv[l];
     for (int sw = 0; sw < a.nu1; ++sw)
       for (int color = 0; color < 2; ++color) {
-        for (int64_t c = t0; c < L.d.n; c += nt) gs_cell(L, c, color, sw == 0 && color == 0);
+        if (sw == 0 && color == 0) continue;  // done with the restriction
+        for (int64_t c = t0; c < L.d.n; c += nt) gs_cell(L, c, color, 0);
         if (!grid_barrier(st)) return;
       }
     if (a.nu1 == 0) {
@@ -1120,7 +1135,12 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
       if (!grid_barrier(st)) return;
     }
     const LevelView<T, S>& C = a.lv[l + 1];
-    for (int64_t I = t0; I < C.d.n; I += nt) C.f[I] = restrict_cell(L, C.d, I, a.nu1 > 0);
+    const bool fold = a.nu1 > 0 && l + 1 < a.tail_from;
+    for (int64_t I = t0; I < C.d.n; I += nt) {
+      const T fI = restrict_cell(L, C.d, I, a.nu1 > 0);
+      C.f[I] = fI;
+      if (fold && red_cell(C.d, I)) C.x[I] = fI / C.cc(kDiag, I);
+    }
   }
 }
 
@@ -1436,7 +1456,7 @@ int prec_alloc(bo_prec* P) {
     return p;
   };
   const size_t ss = P->ssize;  // storage of the matrix-like arrays
-  P->At = al((size_t)63 * g.N * ss);
+  P->At = al(a2_size(g) * ss);  // tiled like the split copy of A (at_index)
   P->w = (double*)al((size_t)3 * g.N * sizeof(double));
   P->wf = ts == sizeof(float) ? (float*)al((size_t)3 * g.N * sizeof(float)) : nullptr;
   P->Dinv = al((size_t)9 * g.N * ss);
