@@ -176,8 +176,9 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__
 // can leave the local solver unstable.
 
 // red pivots: D_r^{-1} of the decoupled diagonal blocks, stored in type S
-// and, for the black pass, in FP64 in `red64` ([rc][N/2])
-template <typename S>
+// and, for the black pass, in FP64 in `red64` ([rc][N/2]); with SPLIT the
+// black pass takes them as split pairs instead (red64 read as float2)
+template <typename S, bool SPLIT>
 __global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w, S* __restrict__ Dinv,
                           double* __restrict__ red64, DevState* st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
@@ -187,10 +188,127 @@ __global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __
       atomicOr(&st->err, kErrBreakdown);
       for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
     }
+    int bad = 0;
     for (int rc = 0; rc < 9; ++rc) {
       Dinv[(size_t)rc * g.N + q] = to_store<S>(inv[rc]);
-      red64[(size_t)rc * g.Nh + q] = inv[rc];
+      if (SPLIT) reinterpret_cast<float2*>(red64)[(size_t)rc * g.Nh + q] = df_split_bits(inv[rc], &bad);
+      else red64[(size_t)rc * g.Nh + q] = inv[rc];
     }
+  }
+}
+
+// The black pivots of a preconditioner stored in FP32 or BF16, formed in
+// split FP32 pairs (48 significant bits, FP32 instructions) instead of FP64:
+// the six products L D_r^{-1} U per cell are 324 multiply-adds, which on
+// GB300's FP64 rate made this the slowest setup kernel.  The decoupled blocks
+// come from the split copy of A and split weights; the Schur complement is
+// summed in split pairs and inverted in FP64.  (An FP64-stored
+// preconditioner keeps the FP64 kernel below.)
+__device__ __forceinline__ void dec_block_split(const Geom& g, const float2* __restrict__ A2, const df wq[3],
+                                                int color, int slot, int64_t q, df b[9]) {
+  df a[9];
+#pragma unroll
+  for (int rc = 0; rc < 9; ++rc) {
+    const float2 v = A2[a2_index(g, color, slot * 9 + rc, q)];
+    a[rc] = df{v.x, v.y};
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    df r = df_fma_acc(df{0.f, 0.f}, wq[0], a[c]);
+    r = df_fma_acc(r, wq[1], a[3 + c]);
+    r = df_fma_acc(r, wq[2], a[6 + c]);
+    b[c] = df_norm(r);
+    b[3 + c] = a[3 + c];
+    b[6 + c] = a[6 + c];
+  }
+}
+
+__device__ __forceinline__ void weights_split(const Geom& g, const double* __restrict__ w, int color, int64_t q,
+                                              df wq[3]) {
+  int bad = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 v = df_split_bits(w[vidx(g, k, color, q)], &bad);
+    wq[k] = df{v.x, v.y};
+  }
+}
+
+__device__ __forceinline__ void mul3_split(const df a[9], const df b[9], df c[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      df r = df_fma_acc(df{0.f, 0.f}, a[3 * i], b[j]);
+      r = df_fma_acc(r, a[3 * i + 1], b[3 + j]);
+      r = df_fma_acc(r, a[3 * i + 2], b[6 + j]);
+      c[3 * i + j] = df_norm(r);
+    }
+}
+
+template <typename S>
+__global__ void k_ilu_black_split(Geom g, const float2* __restrict__ A2, const double* __restrict__ A,
+                                  const int* __restrict__ range, const double* __restrict__ w,
+                                  const float2* __restrict__ red2, S* __restrict__ Dinv, DevState* st) {
+  if (*range) {  // a value outside the split form's range: the FP64 products, from A
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+      const Cell c = decode(g, 1, q);
+      double Sc[9], inv[9];
+      dec_block(g, A, w, 1, kDiag, q, Sc);
+      for (int s = 0; s < 7; ++s) {
+        if (s == kDiag) continue;
+        const int64_t nq = nbr(g, c, q, s);
+        if (nq < 0) continue;
+        double L[9], U[9], Dr[9], T1[9], T2[9];
+        dec_block(g, A, w, 1, s, q, L);
+        dec_block(g, A, w, 0, opposite(s), nq, U);
+        for (int rc = 0; rc < 9; ++rc) {
+          const float2 v = red2[(size_t)rc * g.Nh + nq];
+          Dr[rc] = (double)v.x + (double)v.y;
+        }
+        mul3(L, Dr, T1);
+        mul3(T1, U, T2);
+        for (int rc = 0; rc < 9; ++rc) Sc[rc] -= T2[rc];
+      }
+      if (!inv3(Sc, inv)) {
+        atomicOr(&st->err, kErrBreakdown);
+        for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
+      }
+      for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = to_store<S>(inv[rc]);
+    }
+    return;
+  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
+    const Cell c = decode(g, 1, q);
+    df wb[3], Sc[9];
+    weights_split(g, w, 1, q, wb);
+    dec_block_split(g, A2, wb, 1, kDiag, q, Sc);
+#pragma unroll 1
+    for (int s = 0; s < 7; ++s) {
+      if (s == kDiag) continue;
+      const int64_t nq = nbr(g, c, q, s);
+      if (nq < 0) continue;
+      df wr[3], L[9], U[9], Dr[9], T1[9], T2[9];
+      weights_split(g, w, 0, nq, wr);
+      dec_block_split(g, A2, wb, 1, s, q, L);
+      dec_block_split(g, A2, wr, 0, opposite(s), nq, U);
+#pragma unroll
+      for (int rc = 0; rc < 9; ++rc) {
+        const float2 v = red2[(size_t)rc * g.Nh + nq];
+        Dr[rc] = df{v.x, v.y};
+      }
+      mul3_split(L, Dr, T1);
+      mul3_split(T1, U, T2);
+#pragma unroll
+      for (int rc = 0; rc < 9; ++rc) Sc[rc] = df_add(Sc[rc], df_neg(T2[rc]));
+    }
+    double S64[9], inv[9];
+#pragma unroll
+    for (int rc = 0; rc < 9; ++rc) S64[rc] = df_to_double(Sc[rc]);
+    if (!inv3(S64, inv)) {
+      atomicOr(&st->err, kErrBreakdown);
+      for (int rc = 0; rc < 9; ++rc) inv[rc] = 0.0;
+    }
+    for (int rc = 0; rc < 9; ++rc) Dinv[(size_t)rc * g.N + g.Nh + q] = to_store<S>(inv[rc]);
   }
 }
 
@@ -1420,8 +1538,17 @@ int values_impl(bo_prec* P) {
   (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, (S*)P->At, P->w, P->wf, P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
-  (k_ilu_red<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
-  (k_ilu_black<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, red64, (S*)P->Dinv, P->st), note_launch());
+  if (sizeof(S) < sizeof(double) && m->a2_valid) {
+    // black pivots in split arithmetic (the kernel takes the FP64 products
+    // itself where the split copy of A could not hold every value)
+    (k_ilu_red<S, true><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
+    (k_ilu_black_split<S><<<gh, kThreads, 0, s>>>(g, m->A2, m->A, m->a2_range, P->w,
+                                                 reinterpret_cast<const float2*>(red64), (S*)P->Dinv, P->st),
+     note_launch());
+  } else {
+    (k_ilu_red<S, false><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
+    (k_ilu_black<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, red64, (S*)P->Dinv, P->st), note_launch());
+  }
   // AMG hierarchy values
   for (int l = 1; l < P->nlev; ++l) {
     Level& C = P->lev[l];
