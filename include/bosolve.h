@@ -230,7 +230,15 @@ int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const doubl
  * per opts->mem; x holds the initial guess unless x0_is_zero.  On
  * BO_ERR_NOT_CONVERGED (maxit reached, or a whole restart cycle reduced the
  * residual by less than 1%) x holds the last iterate and info is filled.
- * b = 0 returns x = 0.  info may be NULL. */
+ * b = 0 returns x = 0.  info may be NULL.
+ * Precision: the Krylov basis, Gram-Schmidt (second pass), updates and the
+ * true residual that decides convergence are FP64.  The Arnoldi product
+ * A z_j uses a copy of A split into two floats per value (48 significant
+ * bits for |a| >= 2^-74, 24 below), and the preconditioned vectors z_j are
+ * stored the same way; a matrix with a value outside [2^-120, 2^126] makes
+ * the product use the FP64 matrix instead.  The split vectors keep FP32's
+ * exponent range: a system scaled so that z_j = M^{-1} v_j (|v_j| = 1)
+ * leaves that range overflows and the solve returns BO_ERR_BREAKDOWN. */
 int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
 /* Solve nreal independent systems A_r x_r = b_r at once (an ensemble of
  * realisations, possibly of different grid sizes; each P[r] a distinct
