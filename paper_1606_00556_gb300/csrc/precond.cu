@@ -1037,12 +1037,41 @@ struct TailArgs {
   const S* inv;     // dense inverse of level `last`
 };
 
-// x_first = V-cycle(f_first) over levels first..last by one thread block
+// Dynamic shared memory of the single-block tail (one symbol for the whole
+// translation unit).
+extern __shared__ __align__(16) uint8_t g_tail_smem[];
+
+// Views of the tail levels: in global memory (the kernel's arguments), or
+// staged in the tail's shared memory.  The shared-memory views are rebuilt
+// from offsets into g_tail_smem at each use, so the compiler sees shared
+// addresses and issues shared-memory loads (pointers read back from a
+// shared struct would be generic and take the slower generic path).
 template <typename T, typename S>
-__device__ void tail_cycle(const TailArgs<T, S>& a) {
+struct TailGlobalViews {
+  const TailArgs<T, S>* a;
+  __device__ LevelView<T, S> lv(int l) const { return a->lv[l]; }
+  __device__ const S* inv() const { return a->inv; }
+};
+template <typename T, typename S>
+struct TailSharedViews {
+  const TailArgs<T, S>* a;
+  const uint32_t* off;  // per level: coefficient, right-hand side and iterate offsets; the inverse at off[72]
+  __device__ LevelView<T, S> lv(int l) const {
+    LevelView<T, S> v = a->lv[l];
+    v.c = reinterpret_cast<const S*>(g_tail_smem + off[3 * l]);
+    v.f = reinterpret_cast<T*>(g_tail_smem + off[3 * l + 1]);
+    v.x = reinterpret_cast<T*>(g_tail_smem + off[3 * l + 2]);
+    return v;
+  }
+  __device__ const S* inv() const { return reinterpret_cast<const S*>(g_tail_smem + off[72]); }
+};
+
+// x_first = V-cycle(f_first) over levels first..last by one thread block
+template <typename T, typename S, typename Views>
+__device__ void tail_cycle(const TailArgs<T, S>& a, const Views& vw) {
   const int nt = blockDim.x;
   for (int l = a.first; l < a.last; ++l) {
-    const LevelView<T, S>& L = a.lv[l];
+    const LevelView<T, S> L = vw.lv(l);
     if (a.nu1 == 0) {
       for (int64_t c = threadIdx.x; c < L.d.n; c += nt) L.x[c] = T(0);
       __syncthreads();
@@ -1052,23 +1081,24 @@ __device__ void tail_cycle(const TailArgs<T, S>& a) {
         for (int64_t c = threadIdx.x; c < L.d.n; c += nt) gs_cell(L, c, color, sw == 0 && color == 0);
         __syncthreads();
       }
-    const LevelView<T, S>& C = a.lv[l + 1];
+    const LevelView<T, S> C = vw.lv(l + 1);
     for (int64_t I = threadIdx.x; I < C.d.n; I += nt) C.f[I] = restrict_cell(L, C.d, I, a.nu1 > 0);
     __syncthreads();
   }
   {
-    const LevelView<T, S>& C = a.lv[a.last];
+    const LevelView<T, S> C = vw.lv(a.last);
+    const S* inv = vw.inv();
     const int64_t n = C.d.n;
     for (int64_t i = threadIdx.x; i < n; i += nt) {
       T s = T(0);
-      for (int64_t j = 0; j < n; ++j) s += cv<T>(a.inv[i * n + j]) * C.f[j];
+      for (int64_t j = 0; j < n; ++j) s += cv<T>(inv[i * n + j]) * C.f[j];
       C.x[i] = s;
     }
     __syncthreads();
   }
   for (int l = a.last - 1; l >= a.first; --l) {
-    const LevelView<T, S>& L = a.lv[l];
-    const LevelView<T, S>& C = a.lv[l + 1];
+    const LevelView<T, S> L = vw.lv(l);
+    const LevelView<T, S> C = vw.lv(l + 1);
     if (a.nu2 == 0) {
       for (int64_t c = threadIdx.x; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
       __syncthreads();
@@ -1087,7 +1117,7 @@ __device__ void tail_cycle(const TailArgs<T, S>& a) {
 template <typename T, typename S>
 __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T, S> a, const DevState* st) {
   if (st->done) return;
-  tail_cycle(a);
+  tail_cycle(a, TailGlobalViews<T, S>{&a});
 }
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -1109,41 +1139,43 @@ __host__ __device__ size_t tail_smem_bytes(const TailArgs<T, S>& a) {
 template <typename T, typename S>
 __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, const DevState* st) {
   if (st->done) return;
-  extern __shared__ __align__(16) uint8_t tsm[];
-  __shared__ TailArgs<T, S> b;
+  __shared__ uint32_t off[73];
   if (threadIdx.x == 0) {
-    b = a;
-    size_t off = 0;
+    uint32_t o = 0;
     for (int l = a.first; l <= a.last; ++l) {
-      const int64_t n = a.lv[l].d.n;
-      b.lv[l].c = reinterpret_cast<const S*>(tsm + off);
-      off += align16(7 * n * sizeof(S));
-      b.lv[l].f = reinterpret_cast<T*>(tsm + off);
-      off += align16(n * sizeof(T));
-      b.lv[l].x = reinterpret_cast<T*>(tsm + off);
-      off += align16(n * sizeof(T));
+      const uint32_t n = (uint32_t)a.lv[l].d.n;
+      off[3 * l] = o;
+      o += (uint32_t)align16(7 * n * sizeof(S));
+      off[3 * l + 1] = o;
+      o += (uint32_t)align16(n * sizeof(T));
+      off[3 * l + 2] = o;
+      o += (uint32_t)align16(n * sizeof(T));
     }
-    b.inv = reinterpret_cast<const S*>(tsm + off);
+    off[72] = o;
   }
   __syncthreads();
+  const TailSharedViews<T, S> vw{&a, off};
   for (int l = a.first; l <= a.last; ++l) {
     const int64_t n = a.lv[l].d.n;
-    S* c = const_cast<S*>(b.lv[l].c);
+    S* c = const_cast<S*>(vw.lv(l).c);
+    const S* src = a.lv[l].c;
 #pragma unroll 8
-    for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = a.lv[l].c[i];
+    for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = src[i];
   }
   {
     const int64_t n = a.lv[a.first].d.n;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b.lv[a.first].f[i] = a.lv[a.first].f[i];
+    T* f = vw.lv(a.first).f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = a.lv[a.first].f[i];
     const int64_t nc = a.lv[a.last].d.n;
-    S* inv = const_cast<S*>(b.inv);
+    S* inv = const_cast<S*>(vw.inv());
 #pragma unroll 8
     for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = a.inv[i];
   }
   __syncthreads();
-  tail_cycle(b);
+  tail_cycle(a, vw);
   const int64_t n = a.lv[a.first].d.n;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a.lv[a.first].x[i] = b.lv[a.first].x[i];
+  const T* x = vw.lv(a.first).x;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a.lv[a.first].x[i] = x[i];
 }
 
 // ---- the multi-block AMG levels in two cooperative launches
