@@ -114,16 +114,17 @@ __device__ __forceinline__ float fma3(float acc, float a0, float x0, float a1, f
 }
 
 // ---- split FP32 pairs for the Krylov vectors and the Arnoldi product
-// A value is the unevaluated sum hi + lo of two floats with |lo| at most
-// half an ulp of hi (Dekker's double-length arithmetic, Numer. Math. 18,
-// 1971): 48 significant bits, 2^-47 relative rounding, with FP32's exponent
-// range.  The error-free transformations are Knuth's TwoSum and the FMA
-// form of Dekker's TwoProduct.  GB300 issues 128 FP32 operations per clock
-// per SM against about 2 FP64 FMAs, so a split multiply-add (about 15 FP32
+// A value is the unevaluated sum hi + lo of two floats with |lo| below one
+// ulp of hi (Dekker's double-length arithmetic, Numer. Math. 18, 1971):
+// about 48 significant bits (2^-46 relative) with FP32's exponent range.
+// The error-free transformations are Knuth's TwoSum and the FMA form of
+// Dekker's TwoProduct.  GB300 issues 128 FP32 operations per clock per SM
+// against about 2 FP64 FMAs, so a split multiply-add (about 12 FP32
 // operations) is several times cheaper than one FP64 FMA, and the kernels
-// built from it are bound by HBM instead of the FP64 pipe.  The _rn
-// intrinsics are never contracted into FMAs, which the transformations rely
-// on.
+// built from it (the Arnoldi product, the black ILU pivots of a
+// reduced-precision preconditioner) are bound by memory instead of the FP64
+// pipe.  The _rn intrinsics are never contracted into FMAs, which the
+// transformations rely on.
 struct df {
   float hi, lo;
 };
@@ -144,14 +145,6 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-// acc + a b, renormalised
-__device__ __forceinline__ df df_fma(df acc, df a, df b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float pe = __fmaf_rn(a.hi, b.hi, -p);
-  pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
-  const df s = df_two_sum(acc.hi, p);
-  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, pe)));
-}
 // acc + a b for a long sum: the low parts of the products and of the
 // running sum collect in acc.lo without renormalising each step (the sum is
 // renormalised once, by df_norm, before it is used)
@@ -208,9 +201,6 @@ __device__ __forceinline__ float2 df_split_bits(double a, int* bad) {
   const unsigned mant = (unsigned)((((unsigned long long)R) << (lz + 1)) & 0xFFFFFFFFull) >> 9;
   return make_float2(hi, __uint_as_float(sign | ((unsigned)fe << 23) | mant));
 }
-__device__ __forceinline__ df df_shfl_xor(df a, int o) {
-  return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -229,22 +219,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int nw = (blockDim.x + 31) >> 5;
   v = l < nw ? sh[l] : 0.0;
   return warp_sum(v);
-}
-
-// Sum of split values over the thread block in a fixed order: warps reduce
-// in split arithmetic, the warp sums are added in FP64.  The result is valid
-// in thread 0.  `sh` must hold 32 doubles.
-__device__ __forceinline__ double block_sum_df(df v, double* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = df_to_double(v);
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) s += sh[k];
-  return s;
 }
 
 // A preconditioner input or output vector of 3N entries in internal order:
