@@ -115,10 +115,26 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { ret
 // the water pivot is negative), the cell takes the exact local decoupling,
 // g = row 0 of A_ii^{-1} (pivot 1), which keeps the AMG operator's diagonal
 // positive for the Gauss-Seidel smoother.  Writes the weights [3][N] and the
-// decoupled planes in storage type S.
+// decoupled blocks in storage type S.  The weights are formed in FP64; for
+// FP32 or BF16 storage the decoupled rows are formed from the split copy of
+// A in split FP32 pairs (FP32 instructions; the result rounded once to S),
+// unless the split copy could not hold every value (*range).
 template <typename S>
-__global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__ At, double* __restrict__ w,
+__device__ __forceinline__ S store_split(df v) {
+  return to_store<S>((double)__fadd_rn(v.hi, v.lo));
+}
+template <>
+__device__ __forceinline__ float store_split<float>(df v) { return __fadd_rn(v.hi, v.lo); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_split<__nv_bfloat16>(df v) {
+  return __float2bfloat16_rn(__fadd_rn(v.hi, v.lo));
+}
+
+template <typename S>
+__global__ void k_decouple(Geom g, const double* __restrict__ A, const float2* __restrict__ A2,
+                           const int* __restrict__ range, S* __restrict__ At, double* __restrict__ w,
                            float* __restrict__ wf, DevState* st) {
+  const bool split = sizeof(S) < sizeof(double) && A2 && !*range;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
     const int64_t q = t - color * g.Nh;
@@ -149,6 +165,31 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, S* __restrict__
       wf[vidx(g, 0, color, q)] = (float)g0;
       wf[vidx(g, 1, color, q)] = (float)g1;
       wf[vidx(g, 2, color, q)] = (float)g2;
+    }
+    if (split) {
+      int bad = 0;
+      const float2 g0p = df_split_bits(g0, &bad), g1p = df_split_bits(g1, &bad), g2p = df_split_bits(g2, &bad);
+      const df gs0{g0p.x, g0p.y}, gs1{g1p.x, g1p.y}, gs2{g2p.x, g2p.y};
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        df a[9];
+#pragma unroll
+        for (int rc = 0; rc < 9; ++rc) {
+          const float2 v = A2[a2_index(g, color, s * 9 + rc, q)];
+          a[rc] = df{v.x, v.y};
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          df r = df_fma_acc(df{0.f, 0.f}, gs0, a[c]);
+          r = df_fma_acc(r, gs1, a[3 + c]);
+          r = df_norm(df_fma_acc(r, gs2, a[6 + c]));
+          At[at_index(g, color, s * 9 + c, q)] = store_split<S>(r);
+          At[at_index(g, color, s * 9 + 3 + c, q)] = store_split<S>(a[3 + c]);
+          At[at_index(g, color, s * 9 + 6 + c, q)] = store_split<S>(a[6 + c]);
+          if (s == kDiag && c == 0 && (r.hi == 0.f || !isfinite(r.hi))) atomicOr(&st->err, kErrBreakdown);
+        }
+      }
+      continue;
     }
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
@@ -1567,7 +1608,8 @@ int values_impl(bo_prec* P) {
   cudaStream_t s = P->stream;
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
-  (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, (S*)P->At, P->w, P->wf, P->st), note_launch());
+  (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, m->a2_valid ? m->A2 : nullptr, m->a2_range, (S*)P->At, P->w, P->wf,
+                                         P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
   if (sizeof(S) < sizeof(double) && m->a2_valid) {
