@@ -201,7 +201,7 @@ __global__ void k_beta_is_bnorm(DevState* st) { st->beta = st->bnorm; }
 __global__ void k_set_target(DevState* st, double tol) {
   st->target = tol * st->bnorm;
   st->err = 0;
-  st->counter[5] = 0;  // arrivals of the AMG's grid barrier
+  st->counter[5] = 0;  // the AMG grid barrier's word (its low 31 bits must start at 0)
   st->k = 0;
   st->hist_base = 0;
 }

@@ -1234,26 +1234,25 @@ __device__ __forceinline__ bool grid_barrier(DevState* st) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = &st->counter[6];
+    volatile unsigned* word = &st->counter[5];
     volatile int* err = &st->err;
     int good = !(*err & kErrTimeout);
     if (good) {
-      const unsigned g0 = *gen;
+      // One word per barrier round: block 0 adds 2^31 - (blocks - 1) and
+      // every other block adds 1, so the round's arrivals sum to 2^31 and
+      // the last one flips the word's top bit; a block has passed when the
+      // top bit differs from the one its own addition saw.
+      const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
       __threadfence();
-      if (atomicAdd(&st->counter[5], 1u) == gridDim.x - 1) {
-        st->counter[5] = 0;
-        __threadfence();
-        atomicAdd(&st->counter[6], 1u);
-      } else {
-        unsigned it = 0;
-        while (*gen == g0) {
-          if (++it > kBarrierSpins || (*err & kErrTimeout)) {
-            atomicOr(&st->err, kErrTimeout);
-            good = 0;
-            break;
-          }
-          __nanosleep(32);
+      const unsigned old = atomicAdd(&st->counter[5], inc);
+      unsigned it = 0;
+      while (((*word ^ old) & 0x80000000u) == 0) {
+        if (++it > kBarrierSpins || (*err & kErrTimeout)) {
+          atomicOr(&st->err, kErrTimeout);
+          good = 0;
+          break;
         }
+        __nanosleep(32);
       }
       __threadfence();
     }
