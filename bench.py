@@ -120,6 +120,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def parse_cpulist(spec):
+    """CPU numbers of a sysfs cpulist such as "0-3,8,10-11"."""
+    cpus = set()
+    for part in spec.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
 def bind_near_gpu(index):
     """Run on the CPUs next to the GPU (its PCI device's local_cpulist), so
     that pinned host buffers allocated afterwards are first touched on the
@@ -130,11 +141,7 @@ def bind_near_gpu(index):
         dom, bus, rest = out.lower().split(":")
         path = f"/sys/bus/pci/devices/{dom[-4:]}:{bus}:{rest}/local_cpulist"
         with open(path) as f:
-            spec = f.read().strip()
-        cpus = set()
-        for part in spec.split(","):
-            lo, _, hi = part.partition("-")
-            cpus.update(range(int(lo), int(hi or lo) + 1))
+            cpus = parse_cpulist(f.read())
         cpus &= os.sched_getaffinity(0)
         if cpus and len(cpus) < len(os.sched_getaffinity(0)):
             os.sched_setaffinity(0, cpus)

@@ -58,3 +58,15 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     class A:
         warmup, steps, gpus = 1, 1, 2
     assert bench.run_reference(A()) is None and not called
+
+
+def test_cpulist_parser():
+    # the benchmark binds itself to the CPUs that sysfs lists next to the GPU
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()
+    with pytest.raises(ValueError):
+        bench.parse_cpulist("a-b")
