@@ -67,6 +67,8 @@ def lib():
         L.or_prec_destroy.argtypes = [ctypes.c_void_p]
         L.or_gmres.argtypes = [ctypes.c_int64, ctypes.c_int, _I32, _I32, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, ctypes.c_void_p, _D]
+        L.or_bicgstab.argtypes = [ctypes.c_int64, ctypes.c_int, _I32, _I32, _D, _D, _D, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_void_p, _D]
         _lib = L
     return _lib
 
@@ -320,3 +322,15 @@ def gmres(A: BsrMatrix, b, x0=None, m=30, maxit=1000, tol=1e-8, prec: Prec = Non
     info = np.zeros(4)
     rc = lib().or_gmres(*A.args(), _p(b, _D), _p(x, _D), m, maxit, tol, prec.h if prec else None, _p(info, _D))
     return x, dict(iters=int(info[0]), relres=float(info[1]), restarts=int(info[2]), converged=(rc == 0))
+
+
+def bicgstab(A: BsrMatrix, b, x0=None, maxit=1000, tol=1e-8, prec: Prec = None):
+    """Right-preconditioned BiCGSTAB (two preconditioner applications and two
+    products per iteration).  Returns (x, info) with info = dict(iters,
+    relres, restarts, converged, breakdown)."""
+    b = _d(b)
+    x = np.zeros(b.size) if x0 is None else _d(x0).copy()
+    info = np.zeros(4)
+    rc = lib().or_bicgstab(*A.args(), _p(b, _D), _p(x, _D), maxit, tol, prec.h if prec else None, _p(info, _D))
+    return x, dict(iters=int(info[0]), relres=float(info[1]), restarts=int(info[2]), converged=(rc == 0),
+                   breakdown=(rc == -6))

@@ -15,6 +15,8 @@
 //   or_cpr_*               CPR-FPF                     (Sec. 3.2, Alg. 2)
 //   or_gmres               restarted right-preconditioned GMRES(m), MGS
 //                                                       (Sec. 3.3 solver list; GMRES(30) in Sec. 4)
+//   or_bicgstab            right-preconditioned BiCGSTAB (Sec. 3.3 solver list; the
+//                                                       solver of Sec. 4's scalability runs)
 //   or_rel_residual        ||b - A x|| / ||b||, compensated sums (Alg. 1 criterion)
 //
 // Layout conventions: BSR with bs x bs blocks stored row-major inside a
@@ -830,6 +832,95 @@ int or_gmres(int64_t nb, int bs, const int32_t* rowptr, const int32_t* col, cons
   info[1] = relres;
   info[2] = restarts;
   return beta <= target ? kOk : kNotConverged;
+}
+
+// Right-preconditioned BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput.
+// 13, 1992), preconditioner `prec` (NULL: none).  Each iteration applies the
+// preconditioner twice and A twice: the BiCG step p -> v = A M^{-1} p with
+// alpha = rho / (rt, v), then the minimal-residual step s -> t = A M^{-1} s
+// with omega = (t, s) / (t, t).  When the recursive residual meets
+// tol ||b|| the true residual b - A x is recomputed; if it does not meet the
+// tolerance, or a scalar of the recurrence vanishes, the iteration restarts
+// from the true residual with a new shadow vector rt = r.  x holds the
+// initial guess on entry.  info = {iterations, true relative residual,
+// restarts}.  Returns 0, -7 when maxit was reached first, -6 on a breakdown
+// right after a restart.
+int or_bicgstab(int64_t nb, int bs, const int32_t* rowptr, const int32_t* col, const double* val,
+                const double* b, double* x, int maxit, double tol, void* prec, double* info) {
+  Bsr A = make_bsr(nb, bs, rowptr, col, val);
+  Prec* P = static_cast<Prec*>(prec);
+  const int64_t n = A.n();
+  std::vector<double> r(n), rt(n), p(n), v(n), s(n), t(n), ph(n), sh(n);
+  const double bnorm = std::sqrt(dot(n, b, b));
+  const double target = tol * (bnorm > 0 ? bnorm : 1.0);
+  auto apply_prec = [&](const double* in, double* out) {
+    if (P) P->apply(in, out);
+    else std::copy(in, in + n, out);
+  };
+  auto true_residual = [&]() {
+    A.spmv(x, v.data());
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - v[i];
+    return std::sqrt(dot(n, r.data(), r.data()));
+  };
+  int its = 0, restarts = 0, status = kNotConverged;
+  double rnorm = true_residual();
+  bool fresh = true;  // no iteration since the last (re)start
+  while (rnorm > target && its < maxit) {
+    // (re)start: shadow vector rt = r, p = v = 0, rho_prev = alpha = omega = 1
+    rt = r;
+    std::fill(p.begin(), p.end(), 0.0);
+    std::fill(v.begin(), v.end(), 0.0);
+    double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    bool restart = false;
+    while (!restart && its < maxit) {
+      const double rho = dot(n, rt.data(), r.data());
+      if (rho == 0.0) { restart = true; break; }
+      const double beta = (rho / rho_prev) * (alpha / omega);
+      for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+      apply_prec(p.data(), ph.data());
+      A.spmv(ph.data(), v.data());
+      const double rtv = dot(n, rt.data(), v.data());
+      if (rtv == 0.0) { restart = true; break; }
+      alpha = rho / rtv;
+      for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+      ++its;
+      fresh = false;
+      if (std::sqrt(dot(n, s.data(), s.data())) <= target) {
+        for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i];
+        restart = true;  // recompute the true residual below
+        break;
+      }
+      apply_prec(s.data(), sh.data());
+      A.spmv(sh.data(), t.data());
+      const double tt = dot(n, t.data(), t.data());
+      if (tt == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i];
+        restart = true;
+        break;
+      }
+      omega = dot(n, t.data(), s.data()) / tt;
+      for (int64_t i = 0; i < n; ++i) {
+        x[i] += alpha * ph[i] + omega * sh[i];
+        r[i] = s[i] - omega * t[i];
+      }
+      rho_prev = rho;
+      if (omega == 0.0 || std::sqrt(dot(n, r.data(), r.data())) <= target) restart = true;
+    }
+    const double prev = rnorm;
+    rnorm = true_residual();
+    ++restarts;
+    if (rnorm <= target) break;
+    if (fresh && rnorm >= prev) {  // broke down before any progress
+      status = kBreakdown;
+      break;
+    }
+    fresh = true;
+  }
+  if (rnorm <= target) status = kOk;
+  info[0] = its;
+  info[1] = rnorm / (bnorm > 0 ? bnorm : 1.0);
+  info[2] = restarts;
+  return status;
 }
 
 }  // extern "C"

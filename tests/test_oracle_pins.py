@@ -3,7 +3,7 @@ its code: dense products and LAPACK solves, the defining property of ILU(0)
 ((L U)_ij = A_ij on the pattern), exactness of ILU(0) on block-tridiagonal
 matrices, the paper's form of the Quasi-IMPES operator multiplied back,
 Galerkin coarse operators against explicit P^T A P, symmetry of a symmetric
-V-cycle, and GMRES identities."""
+V-cycle, and GMRES and BiCGSTAB identities."""
 import numpy as np
 import pytest
 
@@ -235,6 +235,74 @@ def test_gmres_tiny_case_true_residual():
     A, b = _tiny_system(0)
     P = oracle.ilu0_prec(A)
     x, info = oracle.gmres(A, b, tol=1e-8, prec=P)
+    assert info["converged"] and oracle.rel_residual(A, b, x) <= 1e-8
+
+
+# ----------------------------------------------------------------- BiCGSTAB
+def test_bicgstab_identity_one_iteration():
+    nb = 10
+    rowptr = np.arange(nb + 1, dtype=np.int32)
+    col = np.arange(nb, dtype=np.int32)
+    I = BsrMatrix(rowptr, col, np.tile(np.eye(3), (nb, 1, 1)))
+    b = np.random.default_rng(0).standard_normal(3 * nb)
+    x, info = oracle.bicgstab(I, b, tol=1e-12)
+    assert info["converged"] and info["iters"] == 1 and np.allclose(x, b, rtol=1e-15)
+
+
+def test_bicgstab_exact_preconditioner_one_iteration():
+    # ILU(0) of a block-tridiagonal column is its exact LU: with M = A the
+    # first BiCG half step gives alpha = 1 and s = 0
+    A = _random_bsr(1, 1, 9, 7, diag_boost=1.0)
+    b = np.random.default_rng(2).standard_normal(A.n)
+    x, info = oracle.bicgstab(A, b, tol=1e-12, prec=oracle.ilu0_prec(A))
+    assert info["converged"] and info["iters"] == 1
+    assert np.allclose(x, np.linalg.solve(A.to_dense(), b), rtol=1e-11, atol=1e-12)
+
+
+def test_bicgstab_zero_budget_and_zero_rhs():
+    A, b = _tiny_system(0, (4, 4, 2))
+    x0 = np.random.default_rng(1).standard_normal(A.n)
+    x, info = oracle.bicgstab(A, b, x0=x0, maxit=0)
+    assert np.array_equal(x, x0) and info["iters"] == 0 and not info["converged"]
+    x, info = oracle.bicgstab(A, np.zeros(A.n))
+    assert info["converged"] and info["iters"] == 0 and not x.any()
+
+
+@pytest.mark.parametrize("prec", ["none", "ilu0", "cpr"])
+def test_bicgstab_matches_lapack_on_small_black_oil(prec):
+    dims = (6, 5, 4)
+    A, b = _tiny_system(2, dims)
+    if prec == "none":
+        A = _random_bsr(*dims, 2)
+    P = None
+    if prec == "ilu0":
+        P = oracle.ilu0_prec(A)
+    elif prec == "cpr":
+        P = oracle.cpr_prec(A, dims)
+    x, info = oracle.bicgstab(A, b, tol=1e-13, maxit=2000, prec=P)
+    ref = np.linalg.solve(A.to_dense(), b)
+    assert info["converged"]
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+def test_bicgstab_skew_matrix_reports_breakdown():
+    # for a skew-symmetric A and shadow vector r0, (r0, A r0) = 0: the BiCG
+    # step cannot be taken, and a restart cannot change that
+    S = np.array([[0.0, 1.0, 2.0, 0.5, 0.0, 1.0], [-1.0, 0.0, 1.0, 0.0, 2.0, 0.0],
+                  [-2.0, -1.0, 0.0, 1.0, 0.0, 3.0], [-0.5, 0.0, -1.0, 0.0, 1.0, 0.0],
+                  [0.0, -2.0, 0.0, -1.0, 0.0, 1.0], [-1.0, 0.0, -3.0, 0.0, -1.0, 0.0]])
+    assert abs(np.linalg.det(S)) > 1e-3
+    rowptr = np.array([0, 2, 4], dtype=np.int32)
+    col = np.array([0, 1, 0, 1], dtype=np.int32)
+    val = np.stack([S[0:3, 0:3], S[0:3, 3:6], S[3:6, 0:3], S[3:6, 3:6]])
+    A = BsrMatrix(rowptr, col, val)
+    x, info = oracle.bicgstab(A, np.arange(1.0, 7.0), maxit=50)
+    assert info["breakdown"] and not info["converged"] and info["iters"] == 0
+
+
+def test_cpr_bicgstab_reaches_paper_tolerance_tiny_case():
+    A, b = _tiny_system(0)
+    x, info = oracle.bicgstab(A, b, tol=1e-8, prec=oracle.cpr_prec(A, (20, 20, 5)))
     assert info["converged"] and oracle.rel_residual(A, b, x) <= 1e-8
 
 
