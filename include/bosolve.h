@@ -240,6 +240,16 @@ int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const doubl
  * exponent range: a system scaled so that z_j = M^{-1} v_j (|v_j| = 1)
  * leaves that range overflows and the solve returns BO_ERR_BREAKDOWN. */
 int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
+/* Solve A x = b with BiCGSTAB (van der Vorst 1992) right preconditioned by
+ * the same CPR as bo_solve: the solver of the paper's scalability
+ * experiments (Sec. 3.3 solver list, Sec. 4).  Same arguments, tolerance rule
+ * (||b - A x|| <= tol ||b|| on the recomputed FP64 residual) and info as
+ * bo_solve; opts->restart is ignored (it only sizes the workspace shared
+ * with bo_solve).  One iteration applies the preconditioner twice.  When a
+ * scalar of the recurrence vanishes the iteration restarts from the true
+ * residual; BO_ERR_BREAKDOWN if it vanishes right after such a restart.  No
+ * residual history is recorded. */
+int bo_solve_bicgstab(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
 /* Solve nreal independent systems A_r x_r = b_r at once (an ensemble of
  * realisations, possibly of different grid sizes; each P[r] a distinct
  * preconditioner on the same device).  The solves run concurrently on a

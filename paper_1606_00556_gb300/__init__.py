@@ -45,7 +45,7 @@ EXPORTS = (
     "bo_status_str", "bo_prec_opts_default", "bo_solve_opts_default", "bo_ctx_create", "bo_ctx_destroy",
     "bo_mat_create_bsr", "bo_mat_create_csr", "bo_mat_update_values", "bo_mat_spmv", "bo_mat_destroy",
     "bo_prec_setup", "bo_prec_update", "bo_prec_apply", "bo_prec_spmv_decoupled", "bo_prec_amg_levels",
-    "bo_prec_destroy", "bo_solve", "bo_solve_batched", "bo_prec_residual_history", "bo_newton_update",
+    "bo_prec_destroy", "bo_solve", "bo_solve_bicgstab", "bo_solve_batched", "bo_prec_residual_history", "bo_newton_update",
     "bo_kernel_launches",
     "bo_mat_residual_noalloc",
     "bo_cnn_create", "bo_cnn_destroy", "bo_cnn_param_count", "bo_cnn_get_params", "bo_cnn_set_params",
@@ -127,6 +127,7 @@ def lib():
         L.bo_prec_amg_levels.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
         L.bo_prec_destroy.argtypes = [_VP]
         L.bo_solve.argtypes = [_VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
+        L.bo_solve_bicgstab.argtypes = [_VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
         L.bo_solve_batched.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                        ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
         L.bo_prec_residual_history.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
@@ -403,6 +404,22 @@ class Preconditioner:
         rc = lib().bo_solve(self.h, bp, xp, ctypes.byref(o), ctypes.byref(info))
         if raise_on_error and rc not in (BO_OK, BO_ERR_NOT_CONVERGED):
             raise BoError(rc, "bo_solve")
+        d = info.as_dict()
+        d["status"] = rc
+        return d
+
+    def solve_bicgstab(self, b, x, tol=1e-8, maxit=500, x0_is_zero=True, raise_on_error=True):
+        """bo_solve_bicgstab: BiCGSTAB + CPR to ||b - A x|| <= tol ||b||
+        (same arguments and result as solve)."""
+        bp, m1 = _ptr(b)
+        xp, m2 = _ptr(x)
+        if m1 != m2:
+            raise ValueError("b and x must both be host or both device")
+        o = bo_solve_opts(tol, 30, maxit, int(x0_is_zero), m1, 0)
+        info = bo_solve_info()
+        rc = lib().bo_solve_bicgstab(self.h, bp, xp, ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error and rc not in (BO_OK, BO_ERR_NOT_CONVERGED):
+            raise BoError(rc, "bo_solve_bicgstab")
         d = info.as_dict()
         d["status"] = rc
         return d

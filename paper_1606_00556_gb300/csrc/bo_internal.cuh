@@ -433,6 +433,7 @@ void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  //
 
 // krylov.cu
 int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
+int bicgstab(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
                    bo_solve_info* infos);
 int krylov_alloc(bo_prec* P, int m);

@@ -415,6 +415,17 @@ int bo_solve(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, 
   return fgmres(P, b, x, &o, info);
 }
 
+int bo_solve_bicgstab(bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info) {
+  if (!P || !b || !x) return BO_ERR_ARG;
+  bo_solve_opts o;
+  bo_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.maxit < 0 || (o.mem != BO_MEM_HOST && o.mem != BO_MEM_DEVICE)) return BO_ERR_ARG;
+  if (o.restart < 1 || o.restart > 64) o.restart = 30;  // sizes the shared workspace only
+  if (cudaSetDevice(P->mat->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
+  return bicgstab(P, b, x, &o, info);
+}
+
 int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x,
                      const bo_solve_opts* opts, bo_solve_info* infos) {
   if (!P || !b || !x || nreal < 1) return BO_ERR_ARG;

@@ -780,6 +780,303 @@ int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o,
   return job.status;
 }
 
+// ---------------------------------------------------------------- BiCGSTAB
+// Right-preconditioned BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput.
+// 13, 1992) with the same CPR preconditioner: the solver of the paper's
+// scalability experiments (Sec. 4).  Each iteration takes the BiCG step
+// p -> v = A M^{-1} p with alpha = rho / (rt, v) and the minimal-residual
+// step s -> t = A M^{-1} s with omega = (t, s) / (t, t).  The recurrence
+// vectors and scalars are FP64; the preconditioned vectors are the CPR's
+// split-pair output and the products use the Arnoldi SpMV.  The scalars
+// live in the device state and the host polls one iteration behind, as in
+// FGMRES.  When the recursive residual meets tol ||b||, or a scalar of the
+// recurrence vanishes, the cycle ends: the true FP64 residual is recomputed
+// and, if it is above the target, the iteration restarts from it with a new
+// shadow vector.
+namespace {
+
+// scalar slots of DevState::h used by BiCGSTAB
+enum : int { kBcRho = 0, kBcRhoPrev, kBcAlpha, kBcOmega, kBcBeta, kBcRtv, kBcSs, kBcTs, kBcTt, kBcRr, kBcReason };
+// why a cycle stopped (h[kBcReason])
+enum : int { kBcGoing = 0, kBcSDone = 1, kBcRDone = 2, kBcBroke = 3 };
+
+// h[o1] = a . b and, with c, h[o2] = c . d; per-block partials reduced in a
+// fixed order by the block that finishes last
+__global__ void __launch_bounds__(kThreads) k_bc_dots(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, const double* __restrict__ c,
+                                                     const double* __restrict__ d, double* partials, DevState* st,
+                                                     int o1, int o2) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s1 = fma(a[i], b[i], s1);
+    if (c) s2 = fma(c[i], d[i], s2);
+  }
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s1;
+    partials[gridDim.x + blockIdx.x] = s2;
+  }
+  if (!last_block(&st->counter[4], gridDim.x)) return;
+  const double t1 = reduce_partials(partials, gridDim.x, sh);
+  const double t2 = reduce_partials(partials + gridDim.x, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    st->h[o1] = t1;
+    if (o2 >= 0) st->h[o2] = t2;
+    st->counter[4] = 0;
+  }
+}
+
+// the scalar steps of an iteration (one thread)
+template <int PHASE>
+__global__ void k_bc_scalar(DevState* st) {
+  if (st->done) return;
+  double* h = st->h;
+  auto stop = [&](int why) {
+    h[kBcReason] = why;
+    st->done = 1;
+  };
+  if (PHASE == 0) {  // rho = (rt, r) -> beta
+    if (h[kBcRho] == 0.0 || !isfinite(h[kBcRho])) return stop(kBcBroke);
+    h[kBcBeta] = (h[kBcRho] / h[kBcRhoPrev]) * (h[kBcAlpha] / h[kBcOmega]);
+  } else if (PHASE == 1) {  // (rt, v) -> alpha
+    if (h[kBcRtv] == 0.0 || !isfinite(h[kBcRtv])) return stop(kBcBroke);
+    h[kBcAlpha] = h[kBcRho] / h[kBcRtv];
+  } else if (PHASE == 2) {  // ||s||: the BiCG half step counts as the iteration
+    st->k += 1;
+    if (!isfinite(h[kBcSs])) return stop(kBcBroke);
+    if (sqrt(h[kBcSs]) <= st->target) return stop(kBcSDone);
+  } else if (PHASE == 3) {  // omega = (t, s) / (t, t)
+    if (h[kBcTt] == 0.0 || !isfinite(h[kBcTt])) return stop(kBcSDone);  // t = 0: keep the half step
+    h[kBcOmega] = h[kBcTs] / h[kBcTt];
+  } else {  // ||r||
+    h[kBcRhoPrev] = h[kBcRho];
+    if (!isfinite(h[kBcRr])) return stop(kBcBroke);
+    if (sqrt(h[kBcRr]) <= st->target || h[kBcOmega] == 0.0) return stop(kBcRDone);
+  }
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bc_p(int64_t n, const double* __restrict__ r, double* __restrict__ p, const double* __restrict__ v,
+                       const DevState* st) {
+  if (st->done) return;
+  const double beta = st->h[kBcBeta], omega = st->h[kBcOmega];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+
+// s = r - alpha v and h[kBcSs] = ||s||^2
+__global__ void __launch_bounds__(kThreads) k_bc_s(int64_t n, const double* __restrict__ r,
+                                                  const double* __restrict__ v, double* __restrict__ s,
+                                                  double* partials, DevState* st) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  const double alpha = st->h[kBcAlpha];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = r[i] - alpha * v[i];
+    s[i] = t;
+    acc = fma(t, t, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (!last_block(&st->counter[4], gridDim.x)) return;
+  const double tot = reduce_partials(partials, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    st->h[kBcSs] = tot;
+    st->counter[4] = 0;
+  }
+}
+
+__device__ __forceinline__ double split_at(const float* z, int64_t n, int64_t i) {
+  return (double)z[i] + (double)z[n + i];
+}
+
+// x += alpha p^ + omega s^, r = s - omega t and h[kBcRr] = ||r||^2 (p^, s^
+// split pairs)
+__global__ void __launch_bounds__(kThreads) k_bc_xr(int64_t n, double* __restrict__ x, const float* __restrict__ ph,
+                                                   const float* __restrict__ shs, const double* __restrict__ s,
+                                                   const double* __restrict__ t, double* __restrict__ r,
+                                                   double* partials, DevState* st) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  const double alpha = st->h[kBcAlpha], omega = st->h[kBcOmega];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * split_at(ph, n, i) + omega * split_at(shs, n, i);
+    const double ri = s[i] - omega * t[i];
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (!last_block(&st->counter[4], gridDim.x)) return;
+  const double tot = reduce_partials(partials, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    st->h[kBcRr] = tot;
+    st->counter[4] = 0;
+  }
+}
+
+// the cycle stopped after a BiCG half step whose residual met the target:
+// x += alpha p^ (runs after the stop, so not gated by it)
+__global__ void k_bc_xs(int64_t n, double* __restrict__ x, const float* __restrict__ ph, const DevState* st) {
+  if (st->h[kBcReason] != kBcSDone) return;
+  const double alpha = st->h[kBcAlpha];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += alpha * split_at(ph, n, i);
+}
+
+// start of a cycle from the true residual rk: r = rt = rk, p = v = 0
+__global__ void k_bc_start_vec(int64_t n, const double* __restrict__ rk, double* __restrict__ r,
+                               double* __restrict__ rt, double* __restrict__ p, double* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    r[i] = rk[i];
+    rt[i] = rk[i];
+    p[i] = 0.0;
+    v[i] = 0.0;
+  }
+}
+
+__global__ void k_bc_start(DevState* st) {
+  st->h[kBcRhoPrev] = st->h[kBcAlpha] = st->h[kBcOmega] = 1.0;
+  st->h[kBcReason] = kBcGoing;
+  st->done = 0;
+  st->k = 0;
+}
+
+}  // namespace
+
+int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
+  int rc = krylov_alloc(P, std::max(o->restart, 8));  // six FP64 recurrence vectors, two split ones
+  if (rc != BO_OK) return rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = P->stream;
+  const Geom& g = P->mat->g;
+  const int64_t nn = 3 * g.N;
+  DevState* st = P->st;
+  if (!P->mat->a2_valid) launch_split_matrix(P->mat, s);
+  const double* b_d = b_in;
+  double* x_d = x_in;
+  if (o->mem == BO_MEM_HOST) {
+    cudaMemcpyAsync(P->hostio, b_in, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    b_d = P->hostio;
+    x_d = P->hostio + nn;
+    if (!o->x0_is_zero) cudaMemcpyAsync(x_d, x_in, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+  }
+  launch_gather(g, b_d, P->bi, s);
+  if (o->x0_is_zero) cudaMemsetAsync(P->xi, 0, nn * sizeof(double), s);
+  else launch_gather(g, x_d, P->xi, s);
+  (k_norm<<<kRedBlocks, kThreads, 0, s>>>(nn, P->bi, P->partials, st), note_launch());
+  (k_set_target<<<1, 1, 0, s>>>(st, o->tol), note_launch());
+  if (o->x0_is_zero) {
+    cudaMemcpyAsync(P->rk, P->bi, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    (k_beta_is_bnorm<<<1, 1, 0, s>>>(st), note_launch());
+  } else {
+    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+     note_launch());
+  }
+  auto read_state = [&](int slot) -> bool {
+    cudaMemcpyAsync(&P->h_st[slot], st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(P->ev[slot], s);
+    return cudaEventSynchronize(P->ev[slot]) == cudaSuccess;
+  };
+  int status = BO_OK;
+  if (!read_state(3)) return BO_ERR_CUDA;
+  const double bnorm = P->h_st[3].bnorm;
+  double beta = P->h_st[3].beta;
+  const double target = o->tol * bnorm;
+  int its = 0, restarts = 0;
+  if (!std::isfinite(bnorm) || !std::isfinite(beta)) status = BO_ERR_NONFINITE;
+  // recurrence vectors in the Krylov workspace
+  double* r = P->V;
+  double* rt = P->V + nn;
+  double* p = P->V + 2 * nn;
+  double* v = P->V + 3 * nn;
+  double* sv = P->V + 4 * nn;
+  double* tv = P->V + 5 * nn;
+  float* ph = (float*)P->Z;             // M^{-1} p as split pairs
+  float* shs = (float*)P->Z + 2 * nn;   // M^{-1} s as split pairs
+  float* ws = P->Vs;                    // shadow written by the SpMV, unused here
+  const int gn = grid_for(nn);
+  const int gs = occ_grid((const void*)k_arnoldi_spmv, g.N);
+  auto enqueue_iteration = [&]() {
+    (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, rt, r, nullptr, nullptr, P->partials, st, kBcRho, -1),
+     note_launch());
+    (k_bc_scalar<0><<<1, 1, 0, s>>>(st), note_launch());
+    (k_bc_p<<<gn, kThreads, 0, s>>>(nn, r, p, v, st), note_launch());
+    launch_cpr_split(P, p, ph, st, nullptr);
+    (k_arnoldi_spmv<<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, ph, v, ws, st),
+     note_launch());
+    (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, rt, v, nullptr, nullptr, P->partials, st, kBcRtv, -1),
+     note_launch());
+    (k_bc_scalar<1><<<1, 1, 0, s>>>(st), note_launch());
+    (k_bc_s<<<kRedBlocks, kThreads, 0, s>>>(nn, r, v, sv, P->partials, st), note_launch());
+    (k_bc_scalar<2><<<1, 1, 0, s>>>(st), note_launch());
+    launch_cpr_split(P, sv, shs, st, nullptr);
+    (k_arnoldi_spmv<<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, shs, tv, ws, st),
+     note_launch());
+    (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, tv, sv, tv, tv, P->partials, st, kBcTs, kBcTt), note_launch());
+    (k_bc_scalar<3><<<1, 1, 0, s>>>(st), note_launch());
+    (k_bc_xr<<<kRedBlocks, kThreads, 0, s>>>(nn, P->xi, ph, shs, sv, tv, r, P->partials, st), note_launch());
+    (k_bc_scalar<4><<<1, 1, 0, s>>>(st), note_launch());
+  };
+  while (status == BO_OK && bnorm > 0.0 && beta > target && its < o->maxit) {
+    (k_bc_start_vec<<<gn, kThreads, 0, s>>>(nn, P->rk, r, rt, p, v), note_launch());
+    (k_bc_start<<<1, 1, 0, s>>>(st), note_launch());
+    // iterations, polled one behind: a stop leaves the queued iteration's kernels idle
+    int enq = 0, polled = 0;
+    bool stop = false;
+    while (!stop && polled < enq + 1) {
+      while (!stop && its + enq < o->maxit && enq - polled < 2) {
+        enqueue_iteration();
+        cudaMemcpyAsync(&P->h_st[enq % 2], st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(P->ev[enq % 2], s);
+        ++enq;
+      }
+      if (polled == enq) break;
+      if (cudaEventSynchronize(P->ev[polled % 2]) != cudaSuccess) return BO_ERR_CUDA;
+      if (P->h_st[polled % 2].done) stop = true;
+      ++polled;
+    }
+    (k_bc_xs<<<gn, kThreads, 0, s>>>(nn, P->xi, ph, st), note_launch());
+    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+     note_launch());
+    if (!read_state(3)) return BO_ERR_CUDA;
+    const DevState& h = P->h_st[3];
+    its += h.k;
+    ++restarts;
+    beta = h.beta;
+    if (!std::isfinite(beta)) {
+      status = BO_ERR_BREAKDOWN;
+    } else if ((int)h.h[kBcReason] == kBcBroke && h.k == 0) {
+      status = BO_ERR_BREAKDOWN;  // the recurrence cannot start from this residual
+    }
+  }
+  if (status == BO_OK && bnorm > 0.0 && beta > target) status = BO_ERR_NOT_CONVERGED;
+  if (bnorm == 0.0) {
+    cudaMemsetAsync(P->xi, 0, nn * sizeof(double), s);
+    beta = 0.0;
+  }
+  launch_scatter(g, P->xi, x_d, s);
+  if (o->mem == BO_MEM_HOST) cudaMemcpyAsync(x_in, x_d, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
+  P->nhist = 0;
+  if (info) {
+    info->status = status;
+    info->iters = its;
+    info->restarts = restarts;
+    info->true_rel_res = bnorm > 0 ? beta / bnorm : beta;
+    info->est_rel_res = info->true_rel_res;
+    info->spmv_launches = 0;
+    info->spmv_ms = 0.0;
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
                    bo_solve_info* infos) {
   for (int r = 0; r < nreal; ++r) {
