@@ -68,3 +68,32 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(bo, "_lib", None)
     with pytest.raises(RuntimeError):
         bo.lib()
+
+
+def test_host_side_contract_without_a_gpu(libpath):
+    # the parts of the boundary that touch no device: status strings, option
+    # defaults, process-wide switches and the rejection of missing arguments
+    import ctypes
+
+    import paper_1606_00556_gb300 as bo
+    L = bo.lib()
+    for code in range(0, -9, -1):
+        s = L.bo_status_str(code)
+        assert isinstance(s, bytes) and len(s) > 0
+    po = bo.bo_prec_opts()
+    L.bo_prec_opts_default(ctypes.byref(po))
+    assert (po.precision, po.amg_nu1, po.amg_nu2, po.amg_coarse_max) == (bo.BO_PREC_FP64, 2, 2, 128)
+    assert po.amg_overcorr == 1.3
+    so = bo.bo_solve_opts()
+    L.bo_solve_opts_default(ctypes.byref(so))
+    assert (so.tol, so.restart, so.maxit, so.mem) == (1e-8, 30, 500, bo.BO_MEM_DEVICE)
+    assert L.bo_set_amg_cooperative(2) == bo.BO_ERR_ARG and L.bo_set_amg_cooperative(1) == bo.BO_OK
+    assert L.bo_set_conv_engine(7) == bo.BO_ERR_ARG
+    for f in ("bo_solve", "bo_solve_bicgstab"):
+        assert getattr(L, f)(None, None, None, None, None) == bo.BO_ERR_ARG
+    assert L.bo_solve_batched(None, 0, None, None, None, None) == bo.BO_ERR_ARG
+    assert L.bo_prec_update(None) == bo.BO_ERR_ARG
+    assert L.bo_prec_destroy(None) == bo.BO_ERR_ARG and L.bo_mat_destroy(None) == bo.BO_ERR_ARG
+    assert L.bo_prec_apply(None, 0, None, None) == bo.BO_ERR_ARG
+    assert L.bo_newton_update(None, None, None, 0) == bo.BO_ERR_ARG
+    assert L.bo_ctx_create(0, None, None) == bo.BO_ERR_ARG
