@@ -8,7 +8,8 @@ marshals numpy arrays.
 
 Pinned by tests/test_oracle_pins.py against dense linear algebra, textbook
 characterisations and closed forms; see the docstring of each function for
-the paper passage it follows.
+the paper passage it follows.  ``newton.py`` holds the inexact Newton method
+(Alg. 1) on top of these solvers, pinned by tests/test_oracle_newton_pins.py.
 """
 from __future__ import annotations
 
