@@ -323,9 +323,8 @@ int bo_prec_setup(bo_mat* m, const bo_prec_opts* opts, bo_prec** out) {
       !(o.amg_overcorr > 0.0 && o.amg_overcorr < 4.0))
     return BO_ERR_ARG;
   if (cudaSetDevice(m->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
-  bo_prec* P = new (std::nothrow) bo_prec();
+  bo_prec* P = new (std::nothrow) bo_prec();  // value-initialised: every member zero or its default
   if (!P) return BO_ERR_OOM;
-  std::memset(P, 0, sizeof(*P));
   P->mat = m;
   P->stream = m->ctx->stream;
   m->refs++;

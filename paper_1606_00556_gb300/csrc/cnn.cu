@@ -368,11 +368,6 @@ __global__ void k_f32_to_bf16(const float* __restrict__ a, bf16* __restrict__ b,
     b[i] = __float2bfloat16_rn(a[i]);
 }
 
-__global__ void k_widen_bf16(const bf16* __restrict__ a, float* __restrict__ b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = __bfloat162float(a[i]);
-}
-
 // ------------------------------------------------------------ dispatch
 template <int CIN, int COUT, bool RELU, bool RES, int F32>
 int launch_fwd_t(int nx, int ny, int nz, int B, const bf16* X, const bf16* W, const float* bias, const bf16* R, bf16* Y,

@@ -1576,6 +1576,7 @@ void cpr_apply(bo_prec* P, InV v, OutV zo, int stage, const DevState* st, const 
   (k_ilu_b<T, S, false><<<occ_grid((const void*)k_ilu_b<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
                                                                                           OutV{}, st),
    note_launch());
+  // (ub and z are both z1: the pass reads its black half and writes its red half)
   (k_ilu_r2<T, S, false><<<occ_grid((const void*)k_ilu_r2<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, z1, z1,
                                                                                             nullptr, OutV{}, st),
    note_launch());
