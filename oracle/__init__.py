@@ -20,7 +20,9 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# BO_ORACLE_LIB names a prebuilt oracle library to load instead (the pin
+# tests' planted-mistake checks compile altered copies of oracle.cpp)
+_LIB_PATH = os.environ.get("BO_ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -33,6 +35,8 @@ SMOOTHER_JACOBI = 1
 
 def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "oracle.cpp")
+    if os.environ.get("BO_ORACLE_LIB"):
+        return _LIB_PATH
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", src, "-o", _LIB_PATH])
     return _LIB_PATH

@@ -1,0 +1,115 @@
+"""Planted mistakes: each case compiles a copy of oracle.cpp with one
+plausible error (a flipped sign, a transposed index, a wrong update) and runs
+the pin that should catch it against that copy; the pin must fail.  The
+unaltered source, compiled the same way, must pass the same pins.  This
+checks that the pins constrain the oracle rather than restate it."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
+
+# (what is wrong, exact source text, altered text, pin file, pin tests that must fail)
+P = "test_oracle_pins.py"
+L = "test_oracle_learned_pins.py"
+MUTATIONS = [
+    ("BSR SpMV reads the block transposed",
+     "s += val[(size_t)e * bs * bs + bs * r + c] * x[(size_t)col[e] * bs + c];",
+     "s += val[(size_t)e * bs * bs + bs * c + r] * x[(size_t)col[e] * bs + c];",
+     P, "test_spmv_matches_dense_product"),
+    ("Quasi-IMPES weight of the water row has the wrong sign",
+     "{1.0, -D[1] / D[4], -D[2] / D[8]}", "{1.0, D[1] / D[4], -D[2] / D[8]}",
+     P, "test_qi_operator_multiplied_back_gives_A"),
+    ("Exact local decoupling takes a column of A_ii^{-1} instead of row 0",
+     "Dt[3 * r + c] = D[3 * c + r];", "Dt[3 * r + c] = D[3 * r + c];",
+     P, "test_flooded_injector_cells_take_exact_local_decoupling"),
+    ("ILU(0) elimination adds instead of subtracts",
+     "lu[(size_t)f * b2 + t] -= prod[t];", "lu[(size_t)f * b2 + t] += prod[t];",
+     P, "test_ilu0_defining_property"),
+    ("ILU(0) backward substitution adds the upper blocks",
+     "s[rr] -= lu[(size_t)e * b2 + bs * rr + c] * z[k * bs + c];",
+     "s[rr] += lu[(size_t)e * b2 + bs * rr + c] * z[k * bs + c];",
+     P, "test_ilu0_exact_on_block_tridiagonal_column"),
+    ("Permutation inverted the wrong way",
+     "inv[perm[i]] = i;", "inv[i] = perm[i];",
+     P, "test_permute_matches_dense_permutation"),
+    ("Dense LU forgets the row interchanges in the solve",
+     "for (int k = 0; k < n; ++k) std::swap(y[k], y[piv[k]]);", "",
+     P, "test_dense_solve_matches_lapack"),
+    ("Relative residual adds A x instead of subtracting it",
+     "s.add(-val[(size_t)e * bs * bs + bs * r + c] * x[(size_t)col[e] * bs + c]);",
+     "s.add(val[(size_t)e * bs * bs + bs * r + c] * x[(size_t)col[e] * bs + c]);",
+     P, "test_rel_residual_matches_numpy"),
+    ("Galerkin coarse operator transposed",
+     "rows[f.agg[i]][f.agg[f.A.col[e]]] += f.A.val[e];", "rows[f.agg[f.A.col[e]]][f.agg[i]] += f.A.val[e];",
+     P, "test_amg_galerkin_on_a_nonsymmetric_matrix"),
+    ("Restriction keeps one residual per aggregate instead of the sum",
+     "fc[L.agg[i]] += r;", "fc[L.agg[i]] = r;",
+     P, "test_amg_two_level_without_smoothing_is_scaled_coarse_correction"),
+    ("Over-correction factor dropped",
+     "x[i] += prm.overcorr * xc[L.agg[i]];", "x[i] += xc[L.agg[i]];",
+     P, "test_amg_two_level_without_smoothing_is_scaled_coarse_correction"),
+    ("Jacobi sweep undamped",
+     "xn[i] = x[i] + prm.omega * s / d;", "xn[i] = x[i] + s / d;",
+     P, "test_amg_two_level_jacobi_cycle_closed_form"),
+    ("Post-smoothing repeats the red-black order",
+     "gs_half(L, pre ? 0 : 1, f, x);\n        gs_half(L, pre ? 1 : 0, f, x);",
+     "gs_half(L, 0, f, x);\n        gs_half(L, 1, f, x);",
+     P, "test_amg_two_level_gauss_seidel_cycle_closed_form or test_amg_symmetric_vcycle_is_symmetric_operator"),
+    ("CPR places the pressure correction on the water unknown",
+     "for (int64_t i = 0; i < nb; ++i) x[3 * i] += ep[i];",
+     "for (int64_t i = 0; i < nb; ++i) x[3 * i + 1] += ep[i];",
+     P, "test_cpr_stages_compose_as_alg2"),
+    ("CPR decouples the input with the wrong gas entry",
+     "w[3 * i + 2] * v[3 * i + 2];", "w[3 * i + 2] * v[3 * i + 1];",
+     P, "test_cpr_stages_compose_as_alg2"),
+    ("GMRES Givens rotation with the wrong sine",
+     "sn[j] = c / d;", "sn[j] = -c / d;",
+     P, "test_gmres_matches_lapack_on_small_black_oil"),
+    ("GMRES Gram-Schmidt adds the projection",
+     "for (int64_t t = 0; t < n; ++t) w[t] -= h * V[i][t];",
+     "for (int64_t t = 0; t < n; ++t) w[t] += h * V[i][t];",
+     P, "test_gmres_matches_lapack_on_small_black_oil"),
+    ("BiCGSTAB update subtracts the minimal-residual step",
+     "x[i] += alpha * ph[i] + omega * sh[i];", "x[i] += alpha * ph[i] - omega * sh[i];",
+     P, "test_bicgstab_matches_lapack_on_small_black_oil"),
+    ("BiCGSTAB search direction without the omega term",
+     "p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];",
+     P, "test_bicgstab_matches_lapack_on_small_black_oil"),
+    ("Learned coarse operator uses zc of the row cell twice",
+     "zc[c] * App.val[e] * zc[App.col[e]];", "zc[c] * App.val[e] * zc[c];",
+     L, "test_galerkin_orthogonality"),
+]
+
+
+def _compile(tmp_path, name, text):
+    src = tmp_path / f"{name}.cpp"
+    src.write_text(text)
+    so = tmp_path / f"lib{name}.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", str(src), "-o", str(so)])
+    return str(so)
+
+
+def _run_pins(lib, files, tests):
+    env = dict(os.environ, BO_ORACLE_LIB=lib)
+    cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+           *[os.path.join(ROOT, "tests", f) for f in sorted(set(files))], "-k", tests]
+    return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+
+
+def test_unaltered_oracle_passes_the_pins(tmp_path):
+    lib = _compile(tmp_path, "original", open(SRC).read())
+    r = _run_pins(lib, [m[3] for m in MUTATIONS], " or ".join(m[4] for m in MUTATIONS))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("what,orig,bad,pinfile,pin", MUTATIONS, ids=[f"m{i:02d}" for i in range(len(MUTATIONS))])
+def test_planted_mistake_is_caught(tmp_path, what, orig, bad, pinfile, pin):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site not unique or missing: {orig}"
+    lib = _compile(tmp_path, "mutant", text.replace(orig, bad))
+    r = _run_pins(lib, [pinfile], pin)
+    assert r.returncode != 0, f"{what}: the pin {pin} still passed"

@@ -364,6 +364,27 @@ def test_amg_galerkin_equals_explicit_triple_product():
     assert np.allclose(A1, P.T @ A0 @ P, rtol=1e-13, atol=1e-13)
 
 
+def test_amg_galerkin_on_a_nonsymmetric_matrix():
+    # the decoupled pressure matrix is not symmetric (upwinded mobilities and
+    # the Quasi-IMPES weights), so P^T A P must not come out as P^T A^T P
+    dims = (6, 5, 3)
+    rp, c, v = _laplacian(*dims)
+    rng = np.random.default_rng(11)
+    v = v.copy()
+    for i in range(rp.size - 1):
+        off = [e for e in range(rp[i], rp[i + 1]) if c[e] != i]
+        v[off] *= np.exp(rng.normal(0.0, 0.5, len(off)))
+        for e in range(rp[i], rp[i + 1]):
+            if c[e] == i:
+                v[e] = -v[off].sum() + 0.2
+    A0 = _csr_dense(rp, c, v)
+    assert not np.allclose(A0, A0.T)
+    amg = oracle.Amg(rp, c, v, dims, oracle.AmgParams(coarse_max=8))
+    P = _aggregation_P(*dims)
+    A1 = _csr_dense(*amg.level_matrix(1))
+    assert np.allclose(A1, P.T @ A0 @ P, rtol=1e-13, atol=1e-13)
+
+
 def test_amg_coarse_laplacian_keeps_zero_row_sums_and_symmetry():
     dims = (8, 8, 4)
     rp, c, v = _laplacian(*dims)
@@ -395,6 +416,59 @@ def test_amg_symmetric_vcycle_is_symmetric_operator(overcorr):
     n = 144
     M = np.stack([amg.vcycle(np.eye(n)[i]) for i in range(n)], axis=1)
     assert np.allclose(M, M.T, rtol=1e-11, atol=1e-13)
+
+
+def _two_level(dims, nu1, nu2, smoother, overcorr):
+    rp, c, v = _laplacian(*dims, coef=lambda r: np.exp(r.normal(0, 1)), shift=0.2)
+    ncoarse = np.prod([(d + 1) // 2 for d in dims])
+    prm = oracle.AmgParams(smoother=smoother, nu1=nu1, nu2=nu2, overcorr=overcorr, coarse_max=int(ncoarse))
+    amg = oracle.Amg(rp, c, v, dims, prm)
+    assert amg.nlevels == 2
+    A = _csr_dense(rp, c, v)
+    P = _aggregation_P(*dims)
+    return amg, A, P, prm
+
+
+def test_amg_two_level_without_smoothing_is_scaled_coarse_correction():
+    # with no sweeps a two-level cycle is x = s P (P^T A P)^{-1} P^T f
+    dims = (6, 5, 4)
+    amg, A, P, prm = _two_level(dims, 0, 0, oracle.SMOOTHER_RBGS, 1.6)
+    f = np.random.default_rng(8).standard_normal(A.shape[0])
+    ref = prm.overcorr * P @ np.linalg.solve(P.T @ A @ P, P.T @ f)
+    assert np.allclose(amg.vcycle(f), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_amg_two_level_jacobi_cycle_closed_form():
+    # one damped-Jacobi pre-sweep from zero, then the coarse correction:
+    # x1 = w D^{-1} f;  x = x1 + s P A_c^{-1} P^T (f - A x1)
+    dims = (5, 4, 4)
+    amg, A, P, prm = _two_level(dims, 1, 0, oracle.SMOOTHER_JACOBI, 1.3)
+    f = np.random.default_rng(9).standard_normal(A.shape[0])
+    x1 = prm.omega * f / np.diag(A)
+    ref = x1 + prm.overcorr * P @ np.linalg.solve(P.T @ A @ P, P.T @ (f - A @ x1))
+    assert np.allclose(amg.vcycle(f), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_amg_two_level_gauss_seidel_cycle_closed_form():
+    # one red-black Gauss-Seidel pre-sweep and one black-red post-sweep: each
+    # half sweep solves its colour's rows exactly with the other colour fixed
+    dims = (4, 4, 3)
+    amg, A, P, prm = _two_level(dims, 1, 1, oracle.SMOOTHER_RBGS, 1.3)
+    n = A.shape[0]
+    red = np.array([((c % 4) + (c // 4) % 4 + c // 16) % 2 == 0 for c in range(n)])
+
+    def half(x, f, colour):
+        x = x.copy()
+        S = colour
+        O = ~colour
+        x[S] = (f[S] - A[np.ix_(S, O)] @ x[O]) / np.diag(A)[S]
+        return x
+
+    f = np.random.default_rng(10).standard_normal(n)
+    x = half(half(np.zeros(n), f, red), f, ~red)
+    x = x + prm.overcorr * P @ np.linalg.solve(P.T @ A @ P, P.T @ (f - A @ x))
+    x = half(half(x, f, ~red), f, red)
+    assert np.allclose(amg.vcycle(f), x, rtol=1e-12, atol=1e-14)
 
 
 def test_amg_vcycle_iteration_converges_to_solution():
