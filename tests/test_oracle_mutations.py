@@ -85,6 +85,39 @@ MUTATIONS = [
 ]
 
 
+# The same for the oracle's Python modules: (what is wrong, module, exact
+# source text, altered text, pin file, pin tests that must fail)
+C = "test_oracle_cnn_pins.py"
+N = "test_oracle_newton_pins.py"
+PY_MUTATIONS = [
+    ("Convolution instead of correlation (taps mirrored)",
+     "cnn.py", "y += _window(xp, dx, dy, dz, nz, ny, nx) @ w[t].T", "y += _window(xp, dx, dy, dz, nz, ny, nx) @ w[26 - t].T",
+     C, "test_single_channel_matches_scipy_correlate or test_brute_force_small"),
+    ("Data gradient scatters through the unmirrored offset",
+     "cnn.py", "_window(dxp, dx, dyy, dz, nz, ny, nx)[...] += dy @ w[t]",
+     "_window(dxp, -dx, -dyy, -dz, nz, ny, nx)[...] += dy @ w[t]",
+     C, "test_backward_data_is_adjoint"),
+    ("Bias gradient averaged instead of summed",
+     "cnn.py", "return dw, d2.sum(axis=0)", "return dw, d2.mean(axis=0)",
+     C, "test_backward_weights_is_adjoint or test_gradient_matches_finite_differences"),
+    ("Residual block adds the wrong activation",
+     "cnn.py", "y = y + acts[l - 1]", "y = y + acts[l]",
+     C, "test_zero_second_conv_makes_block_pass_through"),
+    ("Backward pass drops the skip connection",
+     "cnn.py", "g = g + skip  #", "g = g  #",
+     C, "test_gradient_matches_finite_differences"),
+    ("Adam without bias correction",
+     "cnn.py", "mh = m / (1.0 - b1 ** t)", "mh = m",
+     C, "test_adam_first_steps_closed_form"),
+    ("Newton step damped by one half (linear, not quadratic, convergence)",
+     "newton.py", "x = x + dx", "x = x + 0.5 * dx",
+     N, "test_exact_newton_converges_quadratically"),
+    ("Linear residual of the Newton step with the wrong sign",
+     "newton.py", "r = b - spmv(A, dx)", "r = b + spmv(A, dx)",
+     N, "test_forcing_terms_reach_the_same_solution_with_fewer_linear_iterations"),
+]
+
+
 def _compile(tmp_path, name, text):
     src = tmp_path / f"{name}.cpp"
     src.write_text(text)
@@ -100,8 +133,13 @@ def _run_pins(lib, files, tests):
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
 
 
-def test_unaltered_oracle_passes_the_pins(tmp_path):
-    lib = _compile(tmp_path, "original", open(SRC).read())
+@pytest.fixture(scope="module")
+def original_lib(tmp_path_factory):
+    return _compile(tmp_path_factory.mktemp("oracle"), "original", open(SRC).read())
+
+
+def test_unaltered_oracle_passes_the_pins(original_lib):
+    lib = original_lib
     r = _run_pins(lib, [m[3] for m in MUTATIONS], " or ".join(m[4] for m in MUTATIONS))
     assert r.returncode == 0, r.stdout[-2000:]
 
@@ -112,4 +150,32 @@ def test_planted_mistake_is_caught(tmp_path, what, orig, bad, pinfile, pin):
     assert text.count(orig) == 1, f"mutation site not unique or missing: {orig}"
     lib = _compile(tmp_path, "mutant", text.replace(orig, bad))
     r = _run_pins(lib, [pinfile], pin)
+    assert r.returncode != 0, f"{what}: the pin {pin} still passed"
+
+
+def _oracle_copy(tmp_path, module, orig, bad):
+    import shutil
+    dst = tmp_path / "pkg" / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst, ignore=shutil.ignore_patterns("__pycache__", "*.so"))
+    text = (dst / module).read_text()
+    assert text.count(orig) == 1, f"mutation site not unique or missing: {orig}"
+    (dst / module).write_text(text.replace(orig, bad))
+    return str(tmp_path / "pkg")
+
+
+@pytest.mark.parametrize("what,module,orig,bad,pinfile,pin", PY_MUTATIONS,
+                         ids=[f"py{i:02d}" for i in range(len(PY_MUTATIONS))])
+def test_planted_mistake_in_python_oracle_is_caught(tmp_path, original_lib, what, module, orig, bad, pinfile, pin):
+    lib = original_lib
+    pkg = _oracle_copy(tmp_path, module, orig, orig)
+    env = dict(os.environ, BO_ORACLE_LIB=lib, BO_ORACLE_PATH=pkg)
+    cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+           os.path.join(ROOT, "tests", pinfile), "-k", pin]
+    # the unaltered copy passes, so a failure below is the planted mistake's
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout[-2000:]
+    import shutil
+    shutil.rmtree(os.path.join(pkg, "oracle"))
+    pkg = _oracle_copy(tmp_path, module, orig, bad)
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
     assert r.returncode != 0, f"{what}: the pin {pin} still passed"
