@@ -122,6 +122,12 @@ void bo_solve_opts_default(bo_solve_opts* o);
  * default stream, or NULL for a new non-blocking stream owned by the
  * context.  The context must outlive the matrices made with it. */
 int bo_ctx_create(int device, void* cuda_stream, bo_ctx** out);
+/* Lifetimes are reference counted: a matrix holds its context, a
+ * preconditioner its matrix, a dual-porosity system and a network their
+ * context.  A *_destroy call drops the caller's reference; the object is
+ * freed (after synchronising its stream; an owned stream is destroyed) when
+ * the last reference goes, so objects may be destroyed in any order.
+ * BO_ERR_ARG for NULL. */
 int bo_ctx_destroy(bo_ctx* ctx);
 
 /* Jacobian from BSR arrays (paper Sec. 3.3 matrix of rows; Sec. 3.2 block
@@ -138,7 +144,12 @@ int bo_mat_create_bsr(bo_ctx* ctx, const bo_grid* grid, int32_t nbrows, int64_t 
 int bo_mat_create_csr(bo_ctx* ctx, const bo_grid* grid, int32_t nrows, int64_t nnz,
                       const int32_t* rowptr, const int32_t* col, const double* val,
                       int mem, bo_mat** out);
-/* New values on the pattern given at create (the next Newton Jacobian). */
+/* New values on the pattern given at create (the next Newton Jacobian):
+ * val[9 nnzb] (BSR) or val[nnz] (CSR) in the order of the arrays given at
+ * create, host or device per mem, copied.  Invalidates the reduced-precision
+ * copies; preconditioners on A keep their old values until bo_prec_update.
+ * BO_ERR_NONFINITE for NaN/Inf (the matrix then holds the new values and must
+ * not be solved with); BO_ERR_ARG for NULL or a bad mem. */
 int bo_mat_update_values(bo_mat* A, const double* val, int mem);
 /* y = alpha A x + beta y (paper Sec. 3.3 first basic operation); x, y
  * device vectors of length 3 nx ny nz.  precision BO_PREC_FP64: FP64 values
@@ -147,6 +158,7 @@ int bo_mat_update_values(bo_mat* A, const double* val, int mem);
  * load, products and sums in FP32, y written in FP64 (the reduced-storage
  * matrix form of the mixed-precision path).  beta = 0 never reads y. */
 int bo_mat_spmv(bo_mat* A, double alpha, const double* x, double beta, double* y, int precision);
+/* BO_ERR_ARG for NULL; see bo_ctx_destroy for lifetimes. */
 int bo_mat_destroy(bo_mat* A);
 
 /* Decoupling, ILU(0) factorisation and AMG hierarchy for the current values
@@ -154,15 +166,22 @@ int bo_mat_destroy(bo_mat* A);
  * BO_ERR_BREAKDOWN: zero saturation pivot in Quasi-IMPES, singular ILU
  * pivot block, zero AMG diagonal or singular coarsest matrix. */
 int bo_prec_setup(bo_mat* A, const bo_prec_opts* opts, bo_prec** out);
-/* Recompute all preconditioner values after bo_mat_update_values. */
+/* Recompute all preconditioner values after bo_mat_update_values (same
+ * options, no reallocation).  Errors as bo_prec_setup; on error P must be
+ * updated again before it is used.  Synchronises. */
 int bo_prec_update(bo_prec* P);
-/* z = stage(r), r and z device vectors of length 3 nx ny nz (FP64). */
+/* z = stage(r), r and z device vectors of length 3 nx ny nz (FP64), owned by
+ * the caller; stage one of BO_STAGE_* (else BO_ERR_ARG).  Uses P's Krylov
+ * workspace: not while a solve with P is in flight.  Synchronises. */
 int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z);
-/* y = (D_QI^{-1} A) x in FP64, device vectors (paper Sec. 3.2 decoupled system). */
+/* y = (D_QI^{-1} A) x in FP64, device vectors of length 3 nx ny nz (paper
+ * Sec. 3.2 decoupled system).  Uses P's Krylov workspace.  Synchronises. */
 int bo_prec_spmv_decoupled(bo_prec* P, const double* x, double* y);
 /* AMG level sizes: writes up to cap triples (nx, ny, nz), returns the level
  * count (or a negative status). */
 int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap);
+/* Synchronises P's stream and frees its workspace; drops P's reference on
+ * its matrix.  BO_ERR_ARG for NULL. */
 int bo_prec_destroy(bo_prec* P);
 /* Launch mode of P's solves (BO_LAUNCH_STREAM default, BO_LAUNCH_GRAPH).
  * Graph mode captures the kernels of each Arnoldi column once per restart
@@ -259,11 +278,15 @@ int bo_solve_bicgstab(bo_prec* P, const double* b, double* x, const bo_solve_opt
  * own.  Synchronises before returning. */
 int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x,
                      const bo_solve_opts* opts, bo_solve_info* infos);
-/* Estimated relative residuals of the last solve, one per iteration; returns
- * how many were written (at most cap). */
+/* Estimated relative residuals of the last bo_solve with P, one per
+ * iteration, into host memory buf[cap]; returns how many were written (at
+ * most cap), or BO_ERR_ARG for a NULL P or a NULL buf with cap > 0. */
 int bo_prec_residual_history(bo_prec* P, double* buf, int cap);
 
-/* state += dx on the device in FP64 (paper Alg. 1, x^l = x^{l-1} + dx). */
+/* state += dx on the device in FP64 (paper Alg. 1, x^l = x^{l-1} + dx):
+ * state, dx device arrays of n doubles owned by the caller, in the solver's
+ * natural interleaved order.  n = 0 does nothing; BO_ERR_ARG for NULL or
+ * n < 0.  Ordered on the context's stream; does not synchronise. */
 int bo_newton_update(bo_ctx* ctx, double* state, const double* dx, int64_t n);
 
 /* Diagnostics (no counterpart in the paper): the number of CUDA kernels this
