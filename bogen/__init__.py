@@ -16,13 +16,17 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libbogen.so")
+# BO_BOGEN_LIB names a prebuilt library to load instead (the generator pins'
+# planted-mistake checks compile altered copies of assembly.cpp)
+_LIB_PATH = os.environ.get("BO_BOGEN_LIB") or os.path.join(_HERE, "libbogen.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile assembly.cpp into libbogen.so (plain g++, no arch flags)."""
     src = os.path.join(_HERE, "assembly.cpp")
+    if os.environ.get("BO_BOGEN_LIB"):
+        return _LIB_PATH
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", src, "-o", _LIB_PATH])
     return _LIB_PATH

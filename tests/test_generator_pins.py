@@ -196,6 +196,68 @@ def test_peaceman_equivalent_radius_square_cell():
     assert wi == pytest.approx(0.001127 * 2 * np.pi * k * dz / np.log(ro / rw), rel=1e-14)
 
 
+def _mobilities(fl, sw, sg):
+    # at p = pref every formation volume factor is its reference value
+    krw, kro, krg = bogen.relperm(fl, sw, sg)
+    return krw / (fl.muw * fl.bw0), kro / (fl.muo * fl.bo0), krg / (fl.mug * fl.bg0), (krw, kro, krg)
+
+
+@pytest.mark.parametrize("high", [0, 1])
+def test_flux_is_upwinded_by_phase_potential(high):
+    # two cells side by side, no gravity, x = x^n (no accumulation): each
+    # phase flows with the mobility of the cell of higher potential, so cell 0
+    # gets R = -T lambda_up (p_1 - p_0) per component (gas: dissolved plus free)
+    fl = incompressible_fluid()
+    c = bogen.uniform_case(2, 1, 1, fluid=fl)
+    sat = [(0.6, 0.05), (0.2, 0.15)]
+    p = [3000.0, 3000.0]
+    p[high] = 3100.0
+    c.x = np.array([p[0], *sat[0], p[1], *sat[1]])
+    c.xn = c.x.copy()
+    R = bogen.assemble(c, jacobian=False)["R"]
+    T = 0.001127 * (c.dy * c.dz) * 100.0 / c.dx  # k = 100 mD in both cells
+    lw, lo, lg, _ = _mobilities(fl, *sat[high])
+    R0 = -T * (p[1] - p[0]) * np.array([lo, lw, fl.rs0 * lo + lg])
+    assert np.allclose(R[0:3], R0, rtol=1e-12) and np.allclose(R[3:6], -R0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_well_rates_closed_form(kind):
+    # one cell at p = pref with one well (reference depth at the cell): R = -Q
+    # with Q = WI lambda (p_bhp - p); the water injector uses the total
+    # mobility over B_w, a producer each phase's own (gas: Rs lambda_o + lambda_g)
+    fl = default_fluid()
+    bhp = 3500.0 if kind == 0 else 2500.0
+    c = bogen.uniform_case(1, 1, 1, p=3000.0, sw=0.3, sg=0.1, fluid=fl,
+                           wells=[Well(kind, bhp, np.array([0], np.int32))])
+    R = bogen.assemble(c, jacobian=False)["R"]
+    wi = bogen.well_index(c, 0)
+    lw, lo, lg, (krw, kro, krg) = _mobilities(fl, 0.3, 0.1)
+    if kind == 0:
+        q = np.array([0.0, (krw / fl.muw + kro / fl.muo + krg / fl.mug) / fl.bw0, 0.0])
+    else:
+        q = np.array([lo, lw, fl.rs0 * lo + lg])
+    assert np.allclose(R, -wi * q * (bhp - 3000.0), rtol=1e-12, atol=0)
+
+
+def test_oil_column_in_hydrostatic_equilibrium_has_no_oil_flow():
+    # constant oil density rho_o and p = p_top + rho_o (D - D_top) / 144 make
+    # every vertical oil potential difference vanish (Phi = p - rho g D / 144);
+    # water and gas are lighter or heavier and still flow
+    fl = incompressible_fluid(gravity=1.0)
+    c = bogen.uniform_case(1, 1, 6, fluid=fl)
+    rho_o = (fl.rhoo_sc * 5.615 + fl.rs0 * 1000.0 * fl.rhog_sc) / (5.615 * fl.bo0)
+    c.x[0::3] = 3000.0 + rho_o * (c.depth - c.depth[0]) / 144.0
+    c.xn = c.x.copy()
+    R = bogen.assemble(c, jacobian=False)["R"]
+    assert np.abs(R[1::3]).max() > 1e-3
+    # against the oil flux one layer's gravity head would drive (rounding of
+    # p ~ 3000 psi leaves about 1e-13 of it)
+    _, lo, _, _ = _mobilities(fl, 0.2, 0.05)
+    head_flux = 0.001127 * (c.dx * c.dy) * 100.0 / c.dz * lo * rho_o * c.dz / 144.0
+    assert np.abs(R[0::3]).max() <= 1e-11 * head_flux
+
+
 def test_tiny_case_is_seeded_and_nonsingular():
     a1 = bogen.assemble(bogen.tiny_case(0))
     a2 = bogen.assemble(bogen.tiny_case(0))

@@ -118,6 +118,49 @@ PY_MUTATIONS = [
 ]
 
 
+# The seeded Jacobian generator the oracle's inputs come from, against its
+# physics pins: (what is wrong, exact source text, altered text, pin tests)
+G = "test_generator_pins.py"
+GEN_SRC = os.path.join(ROOT, "bogen", "assembly.cpp")
+GEN_MUTATIONS = [
+    ("Quotient rule with the wrong sign",
+     "r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);", "r.d[i] = (a.d[i] * b.v + a.v * b.d[i]) / (b.v * b.v);",
+     "test_exact_jacobian_matches_central_differences"),
+    ("Arithmetic instead of harmonic face permeability",
+     "    return kDarcy * area * 2.0 / (h / k1 + h / k2);\n  };",
+     "    return kDarcy * area * (k1 + k2) / (2.0 * h);\n  };",
+     "test_face_transmissibility_is_harmonic or test_linear_pressure_profile_layered_harmonic"),
+    ("Flux added to the neighbour with the wrong sign",
+     "R[3 * b + comp] += F[comp]->v;", "R[3 * b + comp] -= F[comp]->v;",
+     "test_component_mass_balance"),
+    ("Upwinding takes the downstream cell",
+     "if (d.v > 0) return lift(qb, 3);\n    if (d.v < 0) return lift(qa, 0);",
+     "if (d.v > 0) return lift(qa, 0);\n    if (d.v < 0) return lift(qb, 3);",
+     "test_flux_is_upwinded_by_phase_potential"),
+    ("Accumulation adds the previous mass",
+     "R[3 * c + comp] += s * (m[comp]->v - mn);", "R[3 * c + comp] += s * (m[comp]->v + mn);",
+     "test_component_mass_balance"),
+    ("Water injector with the water mobility instead of the total",
+     "qw = WI * C.lt_res_w * dpw;", "qw = WI * C.lw * dpw;",
+     "test_well_rates_closed_form"),
+    ("Gravity term of the oil potential with the wrong sign",
+     "Dual<6> dphi_o = (pb - pa) - 0.5 *", "Dual<6> dphi_o = (pb - pa) + 0.5 *",
+     "test_oil_column_in_hydrostatic_equilibrium_has_no_oil_flow"),
+    ("Stone II without the gas term",
+     "(krog / krocw + krg) - krw - krg));", "(krog / krocw + krg) - krw));",
+     "test_stone2_endpoint_identities"),
+    ("Peaceman radius with the wrong constant",
+     "const double ro = 0.28 *", "const double ro = 0.14 *",
+     "test_peaceman_equivalent_radius_square_cell"),
+    ("Pattern lists the wrong y neighbour",
+     "if (j < ny - 1) col[e++] = (int32_t)(c + nx);", "if (j < ny - 1) col[e++] = (int32_t)(c + ny);",
+     "test_pattern_is_seven_point_sorted"),
+    ("Dirichlet face transmissibility over a whole cell",
+     "kx[c] / (0.5 * g->dx);", "kx[c] / g->dx;",
+     "test_linear_pressure_profile_homogeneous"),
+]
+
+
 def _compile(tmp_path, name, text):
     src = tmp_path / f"{name}.cpp"
     src.write_text(text)
@@ -178,4 +221,30 @@ def test_planted_mistake_in_python_oracle_is_caught(tmp_path, original_lib, what
     shutil.rmtree(os.path.join(pkg, "oracle"))
     pkg = _oracle_copy(tmp_path, module, orig, bad)
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+    assert r.returncode != 0, f"{what}: the pin {pin} still passed"
+
+
+@pytest.fixture(scope="module")
+def original_gen_lib(tmp_path_factory):
+    return _compile(tmp_path_factory.mktemp("bogen"), "bogen_original", open(GEN_SRC).read())
+
+
+def _run_gen_pins(lib, tests):
+    env = dict(os.environ, BO_BOGEN_LIB=lib)
+    cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+           os.path.join(ROOT, "tests", G), "-k", tests]
+    return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+
+
+def test_unaltered_generator_passes_the_pins(original_gen_lib):
+    r = _run_gen_pins(original_gen_lib, " or ".join(m[3] for m in GEN_MUTATIONS))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("what,orig,bad,pin", GEN_MUTATIONS, ids=[f"gen{i:02d}" for i in range(len(GEN_MUTATIONS))])
+def test_planted_mistake_in_generator_is_caught(tmp_path, what, orig, bad, pin):
+    text = open(GEN_SRC).read()
+    assert text.count(orig) == 1, f"mutation site not unique or missing: {orig}"
+    lib = _compile(tmp_path, "bogen_mutant", text.replace(orig, bad))
+    r = _run_gen_pins(lib, pin)
     assert r.returncode != 0, f"{what}: the pin {pin} still passed"
