@@ -307,6 +307,23 @@ def test_dual_pattern_shape():
         assert sorted(col[rp[N + c]:rp[N + c + 1]]) == [c, N + c]
 
 
+def test_dual_transfer_closed_form():
+    # one cell, x = x^n, no wells: only the Warren-Root transfer remains,
+    # tau = 0.001127 sigma k_m V lambda_up (Phi_f - Phi_m) out of the fracture
+    # node (upstream: the node of higher pressure, here the fracture)
+    from bogen import dual as D
+    fl = incompressible_fluid()
+    one = lambda v: np.array([float(v)])
+    xf, xm = [3100.0, 0.5, 0.05], [3000.0, 0.2, 0.1]
+    x = np.array(xf + xm)
+    c = D.DualCase(1, 1, 1, 100.0, 100.0, 20.0, one(500), one(500), one(50), one(50), one(0.04), one(0.14),
+                   one(8000.0), x, x.copy(), 1.0, sigma=0.1, wells=[], fluid=fl)
+    R = D.assemble_dual(c)["R"]
+    lw, lo, lg, _ = _mobilities(fl, xf[1], xf[2])
+    tau = 0.001127 * 0.1 * 50.0 * (100.0 * 100.0 * 20.0) * (xf[0] - xm[0]) * np.array([lo, lw, fl.rs0 * lo + lg])
+    assert np.allclose(R[0:3], tau, rtol=1e-12) and np.allclose(R[3:6], -tau, rtol=1e-12)
+
+
 def test_dual_mass_balance_and_transfer_cancel():
     # summed over both continua, fluxes and the fracture-matrix transfer cancel:
     # sum R = accumulation of all 2N nodes (no wells)

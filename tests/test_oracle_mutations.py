@@ -155,6 +155,9 @@ GEN_MUTATIONS = [
     ("Pattern lists the wrong y neighbour",
      "if (j < ny - 1) col[e++] = (int32_t)(c + nx);", "if (j < ny - 1) col[e++] = (int32_t)(c + ny);",
      "test_pattern_is_seven_point_sorted"),
+    ("Dual-porosity transfer without the bulk volume",
+     "kDarcy * sigma * km[c] * V, R);", "kDarcy * sigma * km[c], R);",
+     "test_dual_transfer_closed_form"),
     ("Dirichlet face transmissibility over a whole cell",
      "kx[c] / (0.5 * g->dx);", "kx[c] / g->dx;",
      "test_linear_pressure_profile_homogeneous"),
