@@ -97,3 +97,50 @@ def test_host_side_contract_without_a_gpu(libpath):
     assert L.bo_prec_apply(None, 0, None, None) == bo.BO_ERR_ARG
     assert L.bo_newton_update(None, None, None, 0) == bo.BO_ERR_ARG
     assert L.bo_ctx_create(0, None, None) == bo.BO_ERR_ARG
+
+
+def test_every_entry_point_rejects_missing_handles(libpath):
+    # no call dereferences a NULL handle or pointer: each returns BO_ERR_ARG
+    # before it touches the device (so this runs without a GPU)
+    import ctypes
+
+    import paper_1606_00556_gb300 as bo
+    L = bo.lib()
+    N = None
+    calls = {
+        "bo_mat_create_bsr": (N, N, 0, 0, N, N, N, 0, N),
+        "bo_mat_create_csr": (N, N, 0, 0, N, N, N, 0, N),
+        "bo_mat_update_values": (N, N, 0),
+        "bo_mat_spmv": (N, 1.0, N, 0.0, N, 0),
+        "bo_mat_residual_noalloc": (N, N, N, N, N),
+        "bo_prec_setup": (N, N, N),
+        "bo_prec_spmv_decoupled": (N, N, N),
+        "bo_prec_amg_levels": (N, N, 0),
+        "bo_prec_set_launch_mode": (N, 0),
+        "bo_prec_set_coarse_space": (N, N, 1, 1, 1),
+        "bo_prec_residual_history": (N, N, 0),
+        "bo_learned_guess": (N, N, N, N, 1, N, N),
+        "bo_update_batched": (N, 0, N, 0),
+        "bo_autotune_batched": (N, 0, N, N, N, N, N),
+        "bo_dp_create": (N, N, 0, 0, N, N, N, 0, N),
+        "bo_dp_update_values": (N, N, 0),
+        "bo_dp_solve": (N, N, N, N, N, N),
+        "bo_dp_destroy": (N,),
+        "bo_cnn_create": (N, 8, 8, 8, 1, ctypes.c_uint64(0), N),
+        "bo_cnn_destroy": (N,),
+        "bo_cnn_get_params": (N, N, 0),
+        "bo_cnn_set_params": (N, N, 0),
+        "bo_cnn_get_grads": (N, N, 0),
+        "bo_cnn_forward": (N, N, 1, N),
+        "bo_cnn_backward": (N, N, N, N, 1, 1, N),
+        "bo_cnn_adam_step": (N, ctypes.c_float(1e-3)),
+        "bo_conv3d_forward": (N, 8, 8, 8, 1, 32, 32, N, N, N, N, 1, N, N),
+        "bo_conv3d_backward_data": (N, 8, 8, 8, 1, 32, 32, N, N, N),
+        "bo_conv3d_backward_weights": (N, 8, 8, 8, 1, 32, 32, N, N, N, N),
+        "bo_ctx_destroy": (N,),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == bo.BO_ERR_ARG, name
+    assert L.bo_dp_fracture_matrix(None) is None
+    # the stream pool is 1..16 wide
+    assert L.bo_set_batch_streams(0) == bo.BO_ERR_ARG and L.bo_set_batch_streams(17) == bo.BO_ERR_ARG
