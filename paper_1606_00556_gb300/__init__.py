@@ -64,6 +64,15 @@ class BoError(RuntimeError):
         super().__init__(f"{where}: {_status_str(status)} ({status})")
 
 
+class BoArgError(BoError, ValueError, TypeError):
+    """An argument the binding rejects before the call (status BO_ERR_ARG):
+    a wrong dtype, length, layout or device.  The C ABI takes plain pointers
+    and cannot check what they point to, so the binding does."""
+
+    def __init__(self, where):
+        super().__init__(BO_ERR_ARG, where)
+
+
 class bo_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
@@ -188,7 +197,7 @@ def _ptr(a):
     """(pointer, mem kind) of a torch tensor or numpy array."""
     if hasattr(a, "data_ptr"):
         if not a.is_contiguous():
-            raise ValueError("tensor must be contiguous")
+            raise BoArgError("tensor must be contiguous")
         return _VP(a.data_ptr()), (BO_MEM_DEVICE if a.is_cuda else BO_MEM_HOST)
     a = np.ascontiguousarray(a)
     return _VP(a.ctypes.data), BO_MEM_HOST
@@ -198,9 +207,68 @@ def _f64(a):
     if hasattr(a, "data_ptr"):
         import torch
         if a.dtype != torch.float64:
-            raise TypeError("vectors must be float64")
+            raise BoArgError("vectors must be float64")
         return a
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a, what):
+    """A host int32 copy of an index array, or the torch tensor itself if it
+    is already int32."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.int32:
+            raise BoArgError(f"{what} must be int32, not {a.dtype}")
+        return a
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _count(a):
+    return int(a.numel()) if hasattr(a, "numel") else int(np.size(a))
+
+
+def _need(a, n, what):
+    if _count(a) != n:
+        raise BoArgError(f"{what} must have {n} entries, not {_count(a)}")
+
+
+def _on_device(t, ctx, what):
+    if ctx is not None and t.is_cuda and t.get_device() != ctx.device:
+        raise BoArgError(f"{what} is on cuda:{t.get_device()}, the context on cuda:{ctx.device}")
+
+
+def _vec(t, n, what, ctx=None, host=False, out=False):
+    """(pointer, mem kind, object to keep alive) of a float64 vector of
+    exactly n entries: a contiguous torch tensor on the context's device, or
+    where `host` is allowed a CPU tensor or a numpy array.  A numpy input is
+    converted to a contiguous float64 copy; a numpy output (`out`) is written
+    in place, so it must already be one."""
+    if hasattr(t, "data_ptr"):
+        import torch
+        if t.dtype != torch.float64:
+            raise BoArgError(f"{what} must be float64, not {t.dtype}")
+        if not t.is_contiguous():
+            raise BoArgError(f"{what} must be contiguous")
+        if not t.is_cuda and not host:
+            raise BoArgError(f"{what} must be a CUDA tensor")
+        _on_device(t, ctx, what)
+        _need(t, n, what)
+        return _VP(t.data_ptr()), (BO_MEM_DEVICE if t.is_cuda else BO_MEM_HOST), t
+    if not host:
+        raise BoArgError(f"{what} must be a CUDA tensor")
+    if out:
+        if not (isinstance(t, np.ndarray) and t.dtype == np.float64 and t.flags.c_contiguous and t.flags.writeable):
+            raise BoArgError(f"{what} must be a writeable C-contiguous float64 array (it is written in place)")
+        a = t
+    else:
+        a = np.ascontiguousarray(t, dtype=np.float64)
+    _need(a, n, what)
+    return _VP(a.ctypes.data), BO_MEM_HOST, a
+
+
+def _dvec(t, n, what, ctx=None):
+    """Device pointer of a contiguous float64 CUDA vector of n entries."""
+    return _vec(t, n, what, ctx)[0]
 
 
 _CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
@@ -248,52 +316,61 @@ def grid(nx, ny, nz, dx=100.0, dy=100.0, dz=20.0) -> bo_grid:
 class Matrix:
     """bo_mat: one Jacobian on a structured grid."""
 
-    def __init__(self, ctx: Context, g: bo_grid, h, keep):
+    def __init__(self, ctx: Context, g: bo_grid, h, keep, nval=None):
         self.ctx, self.grid, self.h, self._keep = ctx, g, h, keep
         self.n = 3 * g.nx * g.ny * g.nz
+        self.nval = nval  # values bo_mat_update_values reads (None: not updatable here)
 
     @classmethod
     def from_bsr(cls, ctx, g: bo_grid, rowptr, col, val):
         """bo_mat_create_bsr; arrays on host (numpy) or device (torch)."""
-        rowptr = rowptr if hasattr(rowptr, "data_ptr") else np.ascontiguousarray(rowptr, np.int32)
-        col = col if hasattr(col, "data_ptr") else np.ascontiguousarray(col, np.int32)
-        val = _f64(val)
+        rowptr, col, val = _i32(rowptr, "rowptr"), _i32(col, "col"), _f64(val)
         rp, m1 = _ptr(rowptr)
         cp, m2 = _ptr(col)
         vp, m3 = _ptr(val)
         if len({m1, m2, m3}) != 1:
-            raise ValueError("rowptr, col and val must all be host or all device")
+            raise BoArgError("rowptr, col and val must all be host or all device")
         h = _VP()
         nb = g.nx * g.ny * g.nz
-        nnzb = int(col.shape[0])
+        nnzb = _count(col)
+        _need(rowptr, nb + 1, "rowptr")
+        _need(val, 9 * nnzb, "val")
         _check(lib().bo_mat_create_bsr(ctx.h, ctypes.byref(g), nb, nnzb, rp, cp, vp, m1, ctypes.byref(h)),
                "bo_mat_create_bsr")
-        return cls(ctx, g, h, (rowptr, col, val))
+        return cls(ctx, g, h, (rowptr, col, val), 9 * nnzb)
 
     @classmethod
     def from_csr(cls, ctx, g: bo_grid, rowptr, col, val):
         """bo_mat_create_csr (scalar CSR, interleaved unknowns)."""
-        rowptr = rowptr if hasattr(rowptr, "data_ptr") else np.ascontiguousarray(rowptr, np.int32)
-        col = col if hasattr(col, "data_ptr") else np.ascontiguousarray(col, np.int32)
-        val = _f64(val)
+        rowptr, col, val = _i32(rowptr, "rowptr"), _i32(col, "col"), _f64(val)
         rp, m1 = _ptr(rowptr)
-        cp, _ = _ptr(col)
-        vp, _ = _ptr(val)
+        cp, m2 = _ptr(col)
+        vp, m3 = _ptr(val)
+        if len({m1, m2, m3}) != 1:
+            raise BoArgError("rowptr, col and val must all be host or all device")
         h = _VP()
-        _check(lib().bo_mat_create_csr(ctx.h, ctypes.byref(g), 3 * g.nx * g.ny * g.nz, int(col.shape[0]), rp, cp, vp,
-                                       m1, ctypes.byref(h)), "bo_mat_create_csr")
-        return cls(ctx, g, h, (rowptr, col, val))
+        nrows = 3 * g.nx * g.ny * g.nz
+        nnz = _count(col)
+        _need(rowptr, nrows + 1, "rowptr")
+        _need(val, nnz, "val")
+        _check(lib().bo_mat_create_csr(ctx.h, ctypes.byref(g), nrows, nnz, rp, cp, vp, m1, ctypes.byref(h)),
+               "bo_mat_create_csr")
+        return cls(ctx, g, h, (rowptr, col, val), nnz)
 
     def update_values(self, val):
         """bo_mat_update_values."""
         val = _f64(val)
+        if self.nval is not None:
+            _need(val, self.nval, "val")
         vp, mem = _ptr(val)
+        if mem == BO_MEM_DEVICE:
+            _on_device(val, self.ctx, "val")
         _check(lib().bo_mat_update_values(self.h, vp, mem), "bo_mat_update_values")
 
     def spmv(self, x, y, alpha=1.0, beta=0.0, precision=BO_PREC_FP64):
         """bo_mat_spmv: y = alpha A x + beta y (device tensors)."""
-        _check(lib().bo_mat_spmv(self.h, alpha, _VP(x.data_ptr()), beta, _VP(y.data_ptr()), precision),
-               "bo_mat_spmv")
+        _check(lib().bo_mat_spmv(self.h, alpha, _dvec(x, self.n, "x", self.ctx), beta, _dvec(y, self.n, "y", self.ctx),
+                                 precision), "bo_mat_spmv")
         return y
 
     def close(self):
@@ -315,19 +392,20 @@ class DualPorosity:
 
     def __init__(self, ctx: Context, nx, ny, nz, rowptr, col, val, dx=100.0, dy=100.0, dz=20.0):
         g = bo_grid(nx, ny, nz, dx, dy, dz, 2)
-        rowptr = rowptr if hasattr(rowptr, "data_ptr") else np.ascontiguousarray(rowptr, np.int32)
-        col = col if hasattr(col, "data_ptr") else np.ascontiguousarray(col, np.int32)
-        val = _f64(val)
+        rowptr, col, val = _i32(rowptr, "rowptr"), _i32(col, "col"), _f64(val)
         rp, m1 = _ptr(rowptr)
         cp, m2 = _ptr(col)
         vp, m3 = _ptr(val)
         if len({m1, m2, m3}) != 1:
-            raise ValueError("rowptr, col and val must all be host or all device")
+            raise BoArgError("rowptr, col and val must all be host or all device")
         h = _VP()
         N = nx * ny * nz
-        _check(lib().bo_dp_create(ctx.h, ctypes.byref(g), 2 * N, int(col.shape[0]), rp, cp, vp, m1, ctypes.byref(h)),
+        nnzb = _count(col)
+        _need(rowptr, 2 * N + 1, "rowptr")
+        _need(val, 9 * nnzb, "val")
+        _check(lib().bo_dp_create(ctx.h, ctypes.byref(g), 2 * N, nnzb, rp, cp, vp, m1, ctypes.byref(h)),
                "bo_dp_create")
-        self.h, self.ctx, self.N = h, ctx, N
+        self.h, self.ctx, self.N, self.nval = h, ctx, N, 9 * nnzb
         self._keep = (rowptr, col, val)
         # a borrowed handle: the bo_dp owns the condensed matrix
         self.fracture_matrix = Matrix(ctx, bo_grid(nx, ny, nz, dx, dy, dz, 1), _VP(lib().bo_dp_fracture_matrix(h)), ())
@@ -335,14 +413,18 @@ class DualPorosity:
 
     def update_values(self, val):
         val = _f64(val)
+        _need(val, self.nval, "val")
         vp, mem = _ptr(val)
+        if mem == BO_MEM_DEVICE:
+            _on_device(val, self.ctx, "val")
         _check(lib().bo_dp_update_values(self.h, vp, mem), "bo_dp_update_values")
 
     def solve(self, P: "Preconditioner", b, x, tol=1e-8, restart=30, maxit=500, x0_is_zero=True,
               raise_on_error=True):
         o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
         info = bo_solve_info()
-        rc = lib().bo_dp_solve(self.h, P.h, _dev(b, "float64", "b"), _dev(x, "float64", "x"), ctypes.byref(o),
+        n = 6 * self.N
+        rc = lib().bo_dp_solve(self.h, P.h, _dvec(b, n, "b", self.ctx), _dvec(x, n, "x", self.ctx), ctypes.byref(o),
                                ctypes.byref(info))
         if raise_on_error and rc != BO_OK:
             raise BoError(rc, "bo_dp_solve")
@@ -373,14 +455,17 @@ class Preconditioner:
         """bo_prec_update (after Matrix.update_values)."""
         _check(lib().bo_prec_update(self.h), "bo_prec_update")
 
+    def _d(self, t, what):
+        return _dvec(t, self.mat.n, what, self.mat.ctx)
+
     def apply(self, stage, r, z):
         """bo_prec_apply: z = stage(r)."""
-        _check(lib().bo_prec_apply(self.h, stage, _VP(r.data_ptr()), _VP(z.data_ptr())), "bo_prec_apply")
+        _check(lib().bo_prec_apply(self.h, stage, self._d(r, "r"), self._d(z, "z")), "bo_prec_apply")
         return z
 
     def spmv_decoupled(self, x, y):
         """bo_prec_spmv_decoupled: y = D_QI^{-1} A x."""
-        _check(lib().bo_prec_spmv_decoupled(self.h, _VP(x.data_ptr()), _VP(y.data_ptr())), "bo_prec_spmv_decoupled")
+        _check(lib().bo_prec_spmv_decoupled(self.h, self._d(x, "x"), self._d(y, "y")), "bo_prec_spmv_decoupled")
         return y
 
     def amg_levels(self):
@@ -395,10 +480,10 @@ class Preconditioner:
         """bo_solve: FGMRES(restart) + CPR to ||b - A x|| <= tol ||b||.
         b, x: torch CUDA tensors (device) or numpy arrays (host).  Returns
         the bo_solve_info fields as a dict."""
-        bp, m1 = _ptr(b)
-        xp, m2 = _ptr(x)
+        bp, m1, _kb = _vec(b, self.mat.n, "b", self.mat.ctx, host=True)
+        xp, m2, _kx = _vec(x, self.mat.n, "x", self.mat.ctx, host=True, out=True)
         if m1 != m2:
-            raise ValueError("b and x must both be host or both device")
+            raise BoArgError("b and x must both be host or both device")
         o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), m1, int(profile))
         info = bo_solve_info()
         rc = lib().bo_solve(self.h, bp, xp, ctypes.byref(o), ctypes.byref(info))
@@ -411,10 +496,10 @@ class Preconditioner:
     def solve_bicgstab(self, b, x, tol=1e-8, maxit=500, x0_is_zero=True, raise_on_error=True):
         """bo_solve_bicgstab: BiCGSTAB + CPR to ||b - A x|| <= tol ||b||
         (same arguments and result as solve)."""
-        bp, m1 = _ptr(b)
-        xp, m2 = _ptr(x)
+        bp, m1, _kb = _vec(b, self.mat.n, "b", self.mat.ctx, host=True)
+        xp, m2, _kx = _vec(x, self.mat.n, "x", self.mat.ctx, host=True, out=True)
         if m1 != m2:
-            raise ValueError("b and x must both be host or both device")
+            raise BoArgError("b and x must both be host or both device")
         o = bo_solve_opts(tol, 30, maxit, int(x0_is_zero), m1, 0)
         info = bo_solve_info()
         rc = lib().bo_solve_bicgstab(self.h, bp, xp, ctypes.byref(o), ctypes.byref(info))
@@ -431,7 +516,7 @@ class Preconditioner:
     def set_coarse_space(self, dp, tile=(16, 16, 8)):
         """Learned coarse space from a predicted pressure update dp (device
         float64, one value per cell, natural order); None removes it."""
-        ptr = _dev(dp, "float64", "dp") if dp is not None else None
+        ptr = _dvec(dp, self.mat.n // 3, "dp", self.mat.ctx) if dp is not None else None
         _check(lib().bo_prec_set_coarse_space(self.h, ptr, *[int(t) for t in tile]), "bo_prec_set_coarse_space")
 
     def learned_guess(self, b, pred, scale, ncomp, x0) -> bool:
@@ -440,8 +525,9 @@ class Preconditioner:
         guess was kept."""
         sc = (ctypes.c_double * 3)(*[float(v) for v in scale])
         used = ctypes.c_int(0)
-        _check(lib().bo_learned_guess(self.h, _dev(b, "float64", "b"), _dev(pred, "float32", "pred"), sc, int(ncomp),
-                                      _dev(x0, "float64", "x0"), ctypes.byref(used)), "bo_learned_guess")
+        V = self.mat.n // 3
+        _check(lib().bo_learned_guess(self.h, self._d(b, "b"), _dev(pred, "float32", "pred", 4 * V), sc, int(ncomp),
+                                      self._d(x0, "x0"), ctypes.byref(used)), "bo_learned_guess")
         return bool(used.value)
 
     def residual_history(self, cap=4096):
@@ -464,8 +550,9 @@ class Preconditioner:
 def bo_mat_residual_noalloc(mat: Matrix, b, x, r, norms):
     """r = b - A x, norms[0:2] = (||r||, ||b||) on the device, with no device
     allocation during the call (see include/bosolve.h)."""
-    _check(lib().bo_mat_residual_noalloc(mat.h, _VP(b.data_ptr()), _VP(x.data_ptr()), _VP(r.data_ptr()),
-                                         _VP(norms.data_ptr())), "bo_mat_residual_noalloc")
+    d = lambda t, w: _dvec(t, mat.n, w, mat.ctx)
+    _check(lib().bo_mat_residual_noalloc(mat.h, d(b, "b"), d(x, "x"), d(r, "r"), _dvec(norms, 2, "norms", mat.ctx)),
+           "bo_mat_residual_noalloc")
     return r, norms
 
 
@@ -476,8 +563,8 @@ def bo_solve_batched(precs, bs, xs, tol=1e-8, restart=30, maxit=500, x0_is_zero=
     if not (len(bs) == len(xs) == n) or n == 0:
         raise ValueError("one b and one x per preconditioner")
     P = (_VP * n)(*[p.h for p in precs])
-    B = (_VP * n)(*[_VP(t.data_ptr()) for t in bs])
-    X = (_VP * n)(*[_VP(t.data_ptr()) for t in xs])
+    B = (_VP * n)(*[p._d(t, f"b[{i}]") for i, (p, t) in enumerate(zip(precs, bs))])
+    X = (_VP * n)(*[p._d(t, f"x[{i}]") for i, (p, t) in enumerate(zip(precs, xs))])
     o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
     infos = (bo_solve_info * n)()
     rc = lib().bo_solve_batched(P, n, B, X, ctypes.byref(o), infos)
@@ -496,6 +583,11 @@ def bo_update_batched(precs, vals=None):
     if vals is None:
         V = None
     else:
+        if len(vals) != n:
+            raise BoArgError("one value array (or None) per preconditioner")
+        for i, (p, v) in enumerate(zip(precs, vals)):
+            if v is not None and p.mat.nval is not None:
+                _need(v, p.mat.nval, f"vals[{i}]")
         V = (_VP * n)(*[_VP(_dev(v, "float64", "val").value) if v is not None else None for v in vals])
     _check(lib().bo_update_batched(P, n, V, BO_MEM_DEVICE), "bo_update_batched")
 
@@ -523,9 +615,11 @@ def bo_autotune_batched(precs, bs, xs, cache_path=None, tol=1e-8, restart=30, ma
     """bo_autotune_batched: pick (launch mode, stream-pool width) for this
     batch by timing, or from the JSON cache; returns a dict of the result."""
     n = len(precs)
+    if not (len(bs) == len(xs) == n) or n == 0:
+        raise BoArgError("one b and one x per preconditioner")
     P = (_VP * n)(*[p.h for p in precs])
-    B = (_VP * n)(*[_VP(t.data_ptr()) for t in bs])
-    X = (_VP * n)(*[_VP(t.data_ptr()) for t in xs])
+    B = (_VP * n)(*[p._d(t, f"b[{i}]") for i, (p, t) in enumerate(zip(precs, bs))])
+    X = (_VP * n)(*[p._d(t, f"x[{i}]") for i, (p, t) in enumerate(zip(precs, xs))])
     o = bo_solve_opts(tol, restart, maxit, 1, BO_MEM_DEVICE, 0)
     res = bo_tune_result()
     path = cache_path.encode() if cache_path else None
@@ -541,19 +635,23 @@ def bo_kernel_launches() -> int:
 
 def bo_newton_update(ctx: Context, state, dx):
     """state += dx on the device (paper Alg. 1 update)."""
-    _check(lib().bo_newton_update(ctx.h, _VP(state.data_ptr()), _VP(dx.data_ptr()), state.numel()),
+    n = _count(state)
+    _check(lib().bo_newton_update(ctx.h, _dvec(state, n, "state", ctx), _dvec(dx, n, "dx", ctx), n),
            "bo_newton_update")
 
 
 # ---------------------------------------------------------------- learned update
-def _dev(t, dtype_name, what):
-    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+def _dev(t, dtype_name, what, n=None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (and,
+    if n is given, of exactly n entries)."""
     if t is None:
         return None
     if not hasattr(t, "data_ptr") or not t.is_cuda or not t.is_contiguous():
-        raise ValueError(f"{what} must be a contiguous CUDA tensor")
+        raise BoArgError(f"{what} must be a contiguous CUDA tensor")
     if str(t.dtype) != "torch." + dtype_name:
-        raise TypeError(f"{what} must be {dtype_name}")
+        raise BoArgError(f"{what} must be {dtype_name}")
+    if n is not None:
+        _need(t, n, what)
     return _VP(t.data_ptr())
 
 
@@ -596,15 +694,16 @@ class CNN:
 
     def forward(self, x, pred):
         B = x.shape[0]
-        _check(lib().bo_cnn_forward(self.h, _dev(_bits(x), "int16", "x"), B, _dev(pred, "float32", "pred")),
-               "bo_cnn_forward")
+        _check(lib().bo_cnn_forward(self.h, _dev(_bits(x), "int16", "x", 16 * B * self.V), B,
+                                    _dev(pred, "float32", "pred", 4 * B * self.V)), "bo_cnn_forward")
         return pred
 
     def backward(self, x, target, mask=None, nout=1, want_loss=True):
         B = x.shape[0]
         loss = ctypes.c_double(0.0)
-        _check(lib().bo_cnn_backward(self.h, _dev(_bits(x), "int16", "x"), _dev(target, "float32", "target"),
-                                     _dev(mask, "float32", "mask"), nout, B,
+        _check(lib().bo_cnn_backward(self.h, _dev(_bits(x), "int16", "x", 16 * B * self.V),
+                                     _dev(target, "float32", "target", 4 * B * self.V),
+                                     _dev(mask, "float32", "mask", B * self.V), nout, B,
                                      ctypes.byref(loss) if want_loss else None), "bo_cnn_backward")
         return loss.value if want_loss else None
 
@@ -630,26 +729,33 @@ def bo_conv3d_forward(ctx: Context, dims, x, w, bias, residual=None, relu=False,
     nx, ny, nz = dims
     B = x.shape[0]
     cin, cout = w.shape[2], w.shape[1]
-    _check(lib().bo_conv3d_forward(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(x), "int16", "x"),
-                                   _dev(_bits(w), "int16", "w"), _dev(bias, "float32", "bias"),
-                                   _dev(_bits(residual), "int16", "residual") if residual is not None else None,
-                                   int(relu), _dev(_bits(y), "int16", "y") if y is not None else None,
-                                   _dev(yf, "float32", "yf")), "bo_conv3d_forward")
+    BV = B * nx * ny * nz
+    # with y given, yf holds output channels 0..3 only (the network's prediction)
+    nyf = BV * (4 if y is not None else cout)
+    _check(lib().bo_conv3d_forward(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(x), "int16", "x", BV * cin),
+                                   _dev(_bits(w), "int16", "w", 27 * cout * cin),
+                                   _dev(bias, "float32", "bias", cout),
+                                   _dev(_bits(residual), "int16", "residual", BV * cout) if residual is not None else None,
+                                   int(relu), _dev(_bits(y), "int16", "y", BV * cout) if y is not None else None,
+                                   _dev(yf, "float32", "yf", nyf)), "bo_conv3d_forward")
 
 
 def bo_conv3d_backward_data(ctx: Context, dims, dy, w, dx):
     nx, ny, nz = dims
     B = dy.shape[0]
     cin, cout = w.shape[2], w.shape[1]
-    _check(lib().bo_conv3d_backward_data(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(dy), "int16", "dy"),
-                                         _dev(_bits(w), "int16", "w"), _dev(dx, "float32", "dx")),
-           "bo_conv3d_backward_data")
+    BV = B * nx * ny * nz
+    _check(lib().bo_conv3d_backward_data(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(dy), "int16", "dy", BV * cout),
+                                         _dev(_bits(w), "int16", "w", 27 * cout * cin),
+                                         _dev(dx, "float32", "dx", BV * cin)), "bo_conv3d_backward_data")
 
 
 def bo_conv3d_backward_weights(ctx: Context, dims, x, dy, dw, db):
     nx, ny, nz = dims
     B = x.shape[0]
     cout, cin = dw.shape[1], dw.shape[2]
-    _check(lib().bo_conv3d_backward_weights(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(x), "int16", "x"),
-                                            _dev(dy, "float32", "dy"), _dev(dw, "float32", "dw"),
-                                            _dev(db, "float32", "db")), "bo_conv3d_backward_weights")
+    BV = B * nx * ny * nz
+    _check(lib().bo_conv3d_backward_weights(ctx.h, nx, ny, nz, B, cin, cout, _dev(_bits(x), "int16", "x", BV * cin),
+                                            _dev(dy, "float32", "dy", BV * cout),
+                                            _dev(dw, "float32", "dw", 27 * cout * cin),
+                                            _dev(db, "float32", "db", cout)), "bo_conv3d_backward_weights")
