@@ -10,6 +10,9 @@ Pinned by tests/test_oracle_pins.py against dense linear algebra, textbook
 characterisations and closed forms; see the docstring of each function for
 the paper passage it follows.  ``newton.py`` holds the inexact Newton method
 (Alg. 1) on top of these solvers, pinned by tests/test_oracle_newton_pins.py.
+tests/test_oracle_mutations.py compiles altered copies of oracle.cpp and
+loads them through the BO_ORACLE_LIB variable to show that the pins fail on
+each planted mistake.
 """
 from __future__ import annotations
 
