@@ -368,3 +368,21 @@ def test_dual_without_transfer_is_single_porosity_plus_storage():
         mblocks = {int(col[e]): a["val"][e] for e in range(rp[N + i], rp[N + i + 1])}
         assert np.all(mblocks[i] == 0.0)
     np.testing.assert_array_equal(a["R"][:3 * N], s["R"])
+
+
+def test_ensemble_recipe():
+    # 256 seeded realisations of uneven size: nx, ny in [32, 96] (nx even for
+    # the red-black layout), nz in [8, 24], sigma in [0.5, 2], and the total
+    # unknown count inside the 38M-42M window
+    s1, s2 = bogen.ensemble_specs(), bogen.ensemble_specs()
+    assert s1 == s2 and len(s1) == 256
+    d = np.array([sp["dims"] for sp in s1])
+    assert np.all(d[:, 0] % 2 == 0)
+    assert d[:, 0].min() >= 32 and d[:, 0].max() <= 96 and d[:, 1].min() >= 32 and d[:, 1].max() <= 96
+    assert d[:, 2].min() >= 8 and d[:, 2].max() <= 24
+    assert 38e6 <= 3 * int(np.prod(d, axis=1).sum()) <= 42e6
+    assert all(0.5 <= sp["sigma"] <= 2.0 for sp in s1)
+    assert len({sp["seed"] for sp in s1}) == 256
+    # the sizes really are uneven
+    cells = np.prod(d, axis=1)
+    assert cells.max() > 5 * cells.min()
