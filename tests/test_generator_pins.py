@@ -386,3 +386,34 @@ def test_ensemble_recipe():
     # the sizes really are uneven
     cells = np.prod(d, axis=1)
     assert cells.max() > 5 * cells.min()
+
+
+def test_waterflood_recipe():
+    # the bench's Jacobian recipe at a reduced size: ln k_h = 4 + 1.5 g with g
+    # of zero mean and unit variance, correlated over ~16 cells in x and ~2
+    # layers in z (Gaussian filter of std s: lag-1 correlation exp(-1/(4 s^2)),
+    # 0.999 and 0.94); k_v = 0.1 k_h; a water front around the four corner
+    # injectors that grows with the day; BHP wells on whole columns
+    nx, ny, nz = 64, 64, 16
+    c0 = bogen.waterflood_case(nx, ny, nz, seed=42, day=0)
+    c9 = bogen.waterflood_case(nx, ny, nz, seed=42, day=9)
+    L = np.log(c0.kx).reshape(nz, ny, nx)
+    assert abs(L.mean() - 4.0) < 1e-9 and abs(L.std() - 1.5) < 1e-9
+    lag = lambda a, b: np.corrcoef(a.ravel(), b.ravel())[0, 1]
+    assert lag(L[:, :, :-1], L[:, :, 1:]) > 0.99
+    assert 0.85 < lag(L[:-1], L[1:]) < 0.97
+    assert np.array_equal(c0.kx, c0.ky) and np.allclose(c0.kz, 0.1 * c0.kx, rtol=1e-15)
+    assert np.array_equal(c0.kx, c9.kx)  # the day moves the front only
+    sw0, sw9 = c0.x[1::3], c9.x[1::3]
+    assert sw0.min() >= 0.1 and sw0.max() <= 0.85
+    assert sw9.mean() > sw0.mean()
+    assert np.all(c0.x[2::3] == 0.05) and np.array_equal(c0.x, c0.xn)
+    assert np.allclose(c0.x[0::3], 3000.0 + 0.35 * (c0.depth - c0.depth.min() + 10.0))
+    inj = [w for w in c0.wells if w.kind == 0]
+    prod = [w for w in c0.wells if w.kind == 1]
+    assert len(inj) == 4 and len(prod) == 1
+    assert all(w.bhp == 4000.0 and w.cells.size == nz for w in inj) and prod[0].bhp == 2000.0
+    corners = {(int(w.cells[0]) % nx, int(w.cells[0]) // nx) for w in inj}
+    assert corners == {(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1)}
+    assert int(prod[0].cells[0]) == nx // 2 + nx * (ny // 2)
+    assert not np.array_equal(c0.kx, bogen.waterflood_case(nx, ny, nz, seed=43).kx)
