@@ -417,3 +417,27 @@ def test_waterflood_recipe():
     assert corners == {(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1)}
     assert int(prod[0].cells[0]) == nx // 2 + nx * (ny // 2)
     assert not np.array_equal(c0.kx, bogen.waterflood_case(nx, ny, nz, seed=43).kx)
+
+
+def test_dual_porosity_recipe():
+    # fracture permeability 10 k_m with ln k_m = 4 + sigma g (sigma in
+    # [0.5, 2]), porosities 0.04 / 0.14, shape factor 0.1 ft^-2; the matrix
+    # lags the fractures: p_m <= p_f, Sw_m = 0.1 + 0.5 (Sw_f - 0.1); wells on
+    # the fracture columns at (0, 0) and (nx-1, ny-1)
+    from bogen import dual as D
+    nx, ny, nz = 12, 10, 4
+    c = D.dual_case(5, nx, ny, nz)
+    N = nx * ny * nz
+    Lm = np.log(c.km)
+    assert abs(Lm.mean() - 4.0) < 1e-9 and 0.5 - 1e-9 <= Lm.std() <= 2.0 + 1e-9
+    assert np.allclose(c.kx, 10.0 * c.km, rtol=1e-15) and np.array_equal(c.kx, c.kz)
+    assert np.all(c.phif == 0.04) and np.all(c.phim == 0.14) and c.sigma == 0.1
+    xf, xm = c.x[:3 * N], c.x[3 * N:]
+    assert np.all(xm[0::3] <= xf[0::3])
+    assert np.allclose(xm[1::3], 0.1 + 0.5 * (xf[1::3] - 0.1), rtol=0, atol=1e-15)
+    assert np.all(xf[2::3] == 0.05) and np.all(xm[2::3] == 0.05) and np.array_equal(c.x, c.xn)
+    assert xf[1::3].min() >= 0.1 and xf[1::3].max() <= 0.85
+    inj, prod = c.wells
+    assert (inj.kind, inj.bhp, int(inj.cells[0])) == (0, 4000.0, 0)
+    assert (prod.kind, prod.bhp, int(prod.cells[0])) == (1, 2000.0, nx - 1 + nx * (ny - 1))
+    assert inj.cells.size == prod.cells.size == nz and np.all(inj.cells < N)
