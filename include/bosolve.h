@@ -234,13 +234,21 @@ int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, do
  * tiles; BO_ERR_BREAKDOWN if E is singular (the space is then removed).
  * Synchronises. */
 int bo_prec_set_coarse_space(bo_prec* P, const double* dp, int tx, int ty, int tz);
+/* The same coarse space built straight from a network prediction: dp[c] =
+ * scale * pred[c][0], pred [nx ny nz][4] FP32 on the device (natural order,
+ * channel 0 the pressure update in the network's normalisation), so the
+ * caller does no arithmetic on the prediction.  NULL removes the space;
+ * BO_ERR_ARG also for a non-finite scale; otherwise as
+ * bo_prec_set_coarse_space. */
+int bo_learned_coarse_space(bo_prec* P, const float* pred, double scale, int tx, int ty, int tz);
 /* Learned initial guess (no counterpart in the paper): x0[3c + k] =
  * scale[k] pred[c][k] for k < ncomp (1..3), 0 for the other components,
  * from a network prediction pred [nx ny nz][4] FP32 (device); natural
  * order.  Falls back to x0 = 0 (and *used = 0) unless ||b - A x0|| < ||b||,
  * so the guess never starts a solve further from the solution than the zero
- * guess does.  b, x0: device, 3 nx ny nz doubles.  Uses P's Krylov
- * workspace: not while a solve with P is in flight.  Synchronises. */
+ * guess does (both norms reduced in FP64 in P's own workspace, any grid
+ * size).  b, x0: device, 3 nx ny nz doubles.  Uses P's Krylov workspace: not
+ * while a solve with P is in flight.  Synchronises. */
 int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const double* scale, int ncomp, double* x0,
                      int* used);
 
@@ -301,6 +309,8 @@ int64_t bo_kernel_launches(void);
  *   r = b - A x and norms[0] = ||b - A x||_2, norms[1] = ||b||_2, in FP64;
  *   b, x, r: device vectors of length 3 nx ny nz (natural interleaved order);
  *   norms: device array of 2 doubles.  All are owned by the caller.
+ *   r must not overlap b or x (each thread reads x at its six neighbours
+ *   while others write r): BO_ERR_ARG if it does.
  * Scratch lives in an array compiled into the library (256 KB per device
  * that loads it, held until the process exits), shared by every call on the
  * device: calls that overlap on the GPU race on it.  The first call on each
@@ -437,6 +447,14 @@ int bo_set_conv_engine(int engine);
  * whatever the setting.  A barrier that waits too long ends the launch and
  * the solve returns BO_ERR_TIMEOUT.  BO_ERR_ARG for another mode. */
 int bo_set_amg_cooperative(int on);
+/* Polls of a grid barrier of the cooperative AMG legs before it gives up
+ * (process-wide; read at each V-cycle launch).  0 restores the default,
+ * 2^22 polls of about 30 ns.  A lower limit makes a barrier give up while
+ * other blocks are still on their way: the launch then ends early and the
+ * solve returns BO_ERR_TIMEOUT with x holding the last iterate; the next
+ * solve starts clean.  No counterpart in the paper: it exists so the bounded
+ * waits' error path can be exercised without hanging a GPU. */
+int bo_set_amg_barrier_spins(uint32_t spins);
 /* BO_ERR_TIMEOUT if a tcgen05 convolution gave up waiting on one of its
  * barriers since the last call (its output is then incomplete), else BO_OK;
  * clears the flag.  Synchronises the device. */

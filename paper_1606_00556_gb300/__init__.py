@@ -51,10 +51,10 @@ EXPORTS = (
     "bo_cnn_create", "bo_cnn_destroy", "bo_cnn_param_count", "bo_cnn_get_params", "bo_cnn_set_params",
     "bo_cnn_get_grads", "bo_cnn_forward", "bo_cnn_backward", "bo_cnn_adam_step",
     "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
-    "bo_prec_set_coarse_space", "bo_learned_guess",
+    "bo_prec_set_coarse_space", "bo_learned_coarse_space", "bo_learned_guess",
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
-    "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative",
+    "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins",
 )
 
 
@@ -160,6 +160,7 @@ def lib():
         L.bo_conv3d_backward_data.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP]
         L.bo_conv3d_backward_weights.argtypes = [_VP, _i, _i, _i, _i, _i, _i, _VP, _VP, _VP, _VP]
         L.bo_prec_set_coarse_space.argtypes = [_VP, _VP, _i, _i, _i]
+        L.bo_learned_coarse_space.argtypes = [_VP, _VP, ctypes.c_double, _i, _i, _i]
         L.bo_dp_create.argtypes = [_VP, ctypes.POINTER(bo_grid), ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, _i,
                                    ctypes.POINTER(_VP)]
         L.bo_dp_update_values.argtypes = [_VP, _VP, _i]
@@ -171,6 +172,7 @@ def lib():
         L.bo_set_batch_streams.argtypes = [_i]
         L.bo_set_conv_engine.argtypes = [_i]
         L.bo_set_amg_cooperative.argtypes = [_i]
+        L.bo_set_amg_barrier_spins.argtypes = [ctypes.c_uint32]
         L.bo_tc_status.argtypes = []
         L.bo_update_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), _i]
         L.bo_autotune_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -519,6 +521,14 @@ class Preconditioner:
         ptr = _dvec(dp, self.mat.n // 3, "dp", self.mat.ctx) if dp is not None else None
         _check(lib().bo_prec_set_coarse_space(self.h, ptr, *[int(t) for t in tile]), "bo_prec_set_coarse_space")
 
+    def learned_coarse_space(self, pred, scale, tile=(16, 16, 8)):
+        """Learned coarse space from the network prediction pred [V, 4]
+        (device float32; channel 0 times scale is the pressure update)."""
+        V = self.mat.n // 3
+        ptr = _dev(pred, "float32", "pred", 4 * V) if pred is not None else None
+        _check(lib().bo_learned_coarse_space(self.h, ptr, float(scale), *[int(t) for t in tile]),
+               "bo_learned_coarse_space")
+
     def learned_guess(self, b, pred, scale, ncomp, x0) -> bool:
         """x0 from the network prediction pred [V, 4] (scaled per component);
         falls back to zero unless it lowers the residual.  Returns whether the
@@ -596,6 +606,11 @@ def bo_set_amg_cooperative(on: int):
     """1: the AMG's multi-block levels as two cooperative launches per
     V-cycle (grid barriers between half sweeps); 0: one kernel per sweep."""
     _check(lib().bo_set_amg_cooperative(int(on)), "bo_set_amg_cooperative")
+
+
+def bo_set_amg_barrier_spins(spins: int):
+    """Polls of an AMG grid barrier before it gives up (0: the default)."""
+    _check(lib().bo_set_amg_barrier_spins(int(spins)), "bo_set_amg_barrier_spins")
 
 
 def bo_set_conv_engine(engine: int):

@@ -73,6 +73,66 @@ __device__ __forceinline__ int64_t nbr(const Geom& g, const Cell& c, int64_t q, 
   }
 }
 
+// A cell in natural order c = i + nx (j + ny k): its coordinates, colour
+// and half index.  Kernels that read or write the caller's natural-order
+// vectors (ingest, the public SpMV, the allocation-free residual) decode
+// cells with these helpers, so the natural-to-colour-plane mapping is
+// written once.
+struct Nat {
+  int32_t i, j, k;
+  int color;
+  int64_t q;
+};
+
+__device__ __forceinline__ Nat decode_nat(const Geom& g, int64_t c) {
+  const int64_t r = c / g.nx;
+  Nat n;
+  n.i = (int32_t)(c - r * g.nx);
+  n.j = (int32_t)(r % g.ny);
+  n.k = (int32_t)(r / g.ny);
+  n.color = (n.i + n.j + n.k) & 1;
+  n.q = c >> 1;
+  return n;
+}
+
+// stencil slot of column offset d for a cell at (i, j, k), or -1
+__device__ __forceinline__ int slot_of(const Geom& g, const Nat& n, int64_t d) {
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  if (d == 0) return kDiag;
+  if (d == -1 && n.i > 0) return kXm;
+  if (d == 1 && n.i < g.nx - 1) return kXp;
+  if (d == -nxy && n.k > 0) return kZm;
+  if (d == nxy && n.k < g.nz - 1) return kZp;
+  if (d == -(int64_t)g.nx && n.j > 0) return kYm;
+  if (d == (int64_t)g.nx && n.j < g.ny - 1) return kYp;
+  return -1;
+}
+
+__device__ __forceinline__ unsigned valid_slots(const Geom& g, const Nat& n) {
+  unsigned m = 1u << kDiag;
+  if (n.k > 0) m |= 1u << kZm;
+  if (n.j > 0) m |= 1u << kYm;
+  if (n.i > 0) m |= 1u << kXm;
+  if (n.i < g.nx - 1) m |= 1u << kXp;
+  if (n.j < g.ny - 1) m |= 1u << kYp;
+  if (n.k < g.nz - 1) m |= 1u << kZp;
+  return m;
+}
+
+// natural-order offset c' - c of the neighbour at `slot`
+__device__ __forceinline__ int64_t nat_offset(const Geom& g, int slot) {
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  switch (slot) {
+    case kZm: return -nxy;
+    case kYm: return -(int64_t)g.nx;
+    case kXm: return -1;
+    case kDiag: return 0;
+    case kXp: return 1;
+    case kYp: return (int64_t)g.nx;
+    default: return nxy;
+  }
+}
+
 __host__ __device__ __forceinline__ size_t plane(const Geom& g, int color, int slot, int rc) {
   return ((size_t)(color * 7 + slot) * 9 + rc) * (size_t)g.Nh;
 }
@@ -273,6 +333,9 @@ extern std::atomic<int> g_pool_width;
 extern std::atomic<int> g_conv_engine;
 // AMG multi-block levels: 1 cooperative down/up launches, 0 one kernel per sweep
 extern std::atomic<int> g_amg_coop;
+// polls of an AMG grid barrier before it gives up (default 2^22, about 0.1 s)
+constexpr unsigned kAmgSpinsDefault = 1u << 22;
+extern std::atomic<unsigned> g_amg_spins;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // grid size for a grid-stride loop over n items

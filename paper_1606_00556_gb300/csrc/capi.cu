@@ -18,6 +18,7 @@ std::atomic<long long> g_launches{0};
 std::atomic<int> g_pool_width{kMaxPoolStreams};
 std::atomic<int> g_conv_engine{1};
 std::atomic<int> g_amg_coop{1};
+std::atomic<unsigned> g_amg_spins{kAmgSpinsDefault};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
   static std::mutex mu;
@@ -546,6 +547,11 @@ int64_t bo_kernel_launches(void) { return g_launches.load(); }
 int bo_set_amg_cooperative(int on) {
   if (on != 0 && on != 1) return BO_ERR_ARG;
   g_amg_coop.store(on);
+  return BO_OK;
+}
+
+int bo_set_amg_barrier_spins(uint32_t spins) {
+  g_amg_spins.store(spins == 0 ? kAmgSpinsDefault : spins);
   return BO_OK;
 }
 

@@ -21,11 +21,14 @@
 // 32-column TMEM accumulator.  The weights (N = 32 rows, K = 27 x 32) sit
 // in shared memory for the whole persistent CTA.
 //
-// One CTA of 128 threads per SM, persistent over tiles; two halo buffers:
-// the TMA for tile k + 2 is issued as soon as tile k's MMAs have read its
-// buffer, so it overlaps tile k + 1.  Thread 0 issues TMA and MMAs; the
-// four warps read their 32 TMEM lanes each (tcgen05.ld 32x32b) for the
-// epilogue (bias, residual, ReLU, BF16 or FP32 store).  Every wait on an
+// One CTA of 288 threads (nine warps) per SM, persistent over tiles.  Warp
+// 0 issues the TMA copies and the MMAs (one elected thread); three halo
+// buffers let the copies of the next tiles overlap the MMAs of the current
+// one, and two 32-column TMEM accumulators let the MMAs of one tile overlap
+// the epilogue of the previous one.  Warps 1-8 form the epilogue: warp w
+// reads TMEM lane quarter w % 4 (the 32 lanes its warp may access) for
+// output channels 16 ((w - 1) / 4) .. + 15 with tcgen05.ld, then applies
+// bias, residual and ReLU and stores BF16 or FP32.  Every wait on an
 // mbarrier is bounded: on expiry the CTA records an error, waits (bounded)
 // for its copies in flight, frees its TMEM and returns.
 #include <cuda.h>

@@ -6,47 +6,6 @@
 namespace bo {
 namespace {
 
-struct Nat {
-  int32_t i, j, k;
-  int color;
-  int64_t q;
-};
-
-__device__ __forceinline__ Nat decode_nat(const Geom& g, int64_t c) {
-  const int64_t r = c / g.nx;
-  Nat n;
-  n.i = (int32_t)(c - r * g.nx);
-  n.j = (int32_t)(r % g.ny);
-  n.k = (int32_t)(r / g.ny);
-  n.color = (n.i + n.j + n.k) & 1;
-  n.q = c >> 1;
-  return n;
-}
-
-// stencil slot of column offset d for a cell at (i, j, k), or -1
-__device__ __forceinline__ int slot_of(const Geom& g, const Nat& n, int64_t d) {
-  const int64_t nxy = (int64_t)g.nx * g.ny;
-  if (d == 0) return kDiag;
-  if (d == -1 && n.i > 0) return kXm;
-  if (d == 1 && n.i < g.nx - 1) return kXp;
-  if (d == -nxy && n.k > 0) return kZm;
-  if (d == nxy && n.k < g.nz - 1) return kZp;
-  if (d == -(int64_t)g.nx && n.j > 0) return kYm;
-  if (d == (int64_t)g.nx && n.j < g.ny - 1) return kYp;
-  return -1;
-}
-
-__device__ __forceinline__ unsigned valid_slots(const Geom& g, const Nat& n) {
-  unsigned m = 1u << kDiag;
-  if (n.k > 0) m |= 1u << kZm;
-  if (n.j > 0) m |= 1u << kYm;
-  if (n.i > 0) m |= 1u << kXm;
-  if (n.i < g.nx - 1) m |= 1u << kXp;
-  if (n.j < g.ny - 1) m |= 1u << kYp;
-  if (n.k < g.nz - 1) m |= 1u << kZp;
-  return m;
-}
-
 // One thread per cell: check the block row's pattern against the stencil
 // and scatter its 3x3 blocks into the colour-split planes, in FP64 (A) and
 // as split pairs (A2, read by the Arnoldi product).

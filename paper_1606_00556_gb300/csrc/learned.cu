@@ -34,10 +34,13 @@ __device__ __forceinline__ int tile_of(const Tiles& T, int i, int j, int k) {
 }
 
 // z[colour-split] = dp[natural]
-__global__ void k_lc_perm(Geom g, const double* __restrict__ dp, double* __restrict__ z) {
+// z (colour-split order) = scale * dp[c * stride] (natural order): an FP64
+// field (stride 1) or channel 0 of a network prediction [N][4] (stride 4)
+template <typename T>
+__global__ void k_lc_perm(Geom g, const T* __restrict__ dp, int stride, double scale, double* __restrict__ z) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
-    z[((i + j + k) & 1) * g.Nh + (c >> 1)] = dp[c];
+    z[((i + j + k) & 1) * g.Nh + (c >> 1)] = scale * (double)dp[c * stride];
   }
 }
 
@@ -150,6 +153,55 @@ __global__ void k_guess(int64_t N, const float* __restrict__ pred, double s0, do
   }
 }
 
+// ||b - A x0||^2 and ||b||^2 on natural-order vectors (FP64), into out[0..1]:
+// per-block partials in the preconditioner's reduction memory, summed in a
+// fixed order by the block that finishes last (counter 6 of the device state)
+__global__ void __launch_bounds__(kThreads) k_guess_norms(Geom g, const double* __restrict__ A,
+                                                         const double* __restrict__ b,
+                                                         const double* __restrict__ x, double* partials,
+                                                         DevState* st, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double rr = 0.0, bb = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
+    const Nat n = decode_nat(g, c);
+    const unsigned valid = valid_slots(g, n);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      if (!((valid >> s) & 1u)) continue;
+      const int64_t nc = c + nat_offset(g, s);
+      const double* a = A + plane(g, n.color, s, 0) + n.q;
+      const size_t P = (size_t)g.Nh;
+      a0 = fma3(a0, a[0], x[3 * nc], a[P], x[3 * nc + 1], a[2 * P], x[3 * nc + 2]);
+      a1 = fma3(a1, a[3 * P], x[3 * nc], a[4 * P], x[3 * nc + 1], a[5 * P], x[3 * nc + 2]);
+      a2 = fma3(a2, a[6 * P], x[3 * nc], a[7 * P], x[3 * nc + 1], a[8 * P], x[3 * nc + 2]);
+    }
+    const double b0 = b[3 * c], b1 = b[3 * c + 1], b2 = b[3 * c + 2];
+    const double r0 = b0 - a0, r1 = b1 - a1, r2 = b2 - a2;
+    rr += r0 * r0 + r1 * r1 + r2 * r2;
+    bb += b0 * b0 + b1 * b1 + b2 * b2;
+  }
+  rr = block_sum(rr, sh);
+  bb = block_sum(bb, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = rr;
+    partials[2 * blockIdx.x + 1] = bb;
+  }
+  if (!last_block(&st->counter[6], gridDim.x)) return;
+  double sr = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sr += __ldcg(partials + 2 * i);
+    sb += __ldcg(partials + 2 * i + 1);
+  }
+  sr = block_sum(sr, sh);
+  sb = block_sum(sb, sh);
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(sr);
+    out[1] = sqrt(sb);
+    st->counter[6] = 0;
+  }
+}
+
 __global__ void k_zero64(int64_t n, double* __restrict__ x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = 0.0;
@@ -200,27 +252,30 @@ void learned_coarse_free(bo_prec* P) {
 
 }  // namespace bo
 
-extern "C" {
+namespace bo {
+namespace {
 
-int bo_prec_set_coarse_space(bo_prec* P, const double* dp, int tx, int ty, int tz) {
+// the coarse space from dp (FP64, stride 1) or a prediction (FP32, stride 4)
+template <typename T>
+int set_coarse_space(bo_prec* P, const T* dp, int stride, double scale, int tx, int ty, int tz) {
   if (!P) return BO_ERR_ARG;
   if (cudaSetDevice(P->mat->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   cudaStreamSynchronize(P->stream);
-  bo::learned_coarse_free(P);
-  bo::graphs_reset(P);  // captured columns hold the old preconditioner sequence
+  learned_coarse_free(P);
+  graphs_reset(P);  // captured columns hold the old preconditioner sequence
   if (!dp) return BO_OK;
-  const bo::Geom& g = P->mat->g;
-  if (tx < 1 || ty < 1 || tz < 1) return BO_ERR_ARG;
+  const Geom& g = P->mat->g;
+  if (tx < 1 || ty < 1 || tz < 1 || !std::isfinite(scale)) return BO_ERR_ARG;
   const int ntx = (g.nx + tx - 1) / tx, nty = (g.ny + ty - 1) / ty, ntz = (g.nz + tz - 1) / tz;
   const int64_t nt = (int64_t)ntx * nty * ntz;
-  if (nt > bo::kMaxTiles) return BO_ERR_ARG;
+  if (nt > kMaxTiles) return BO_ERR_ARG;
   bool ok = cudaMalloc(&P->lc_z, g.N * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&P->lc_E, nt * nt * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&P->lc_Einv, nt * nt * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&P->lc_y, nt * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&P->lc_u, nt * sizeof(double)) == cudaSuccess;
   if (!ok) {
-    bo::learned_coarse_free(P);
+    learned_coarse_free(P);
     return BO_ERR_OOM;
   }
   P->lc_tile[0] = tx; P->lc_tile[1] = ty; P->lc_tile[2] = tz;
@@ -228,15 +283,28 @@ int bo_prec_set_coarse_space(bo_prec* P, const double* dp, int tx, int ty, int t
   P->lc_nt = (int)nt;
   cudaStream_t s = P->stream;
   cudaMemsetAsync(&P->st->err, 0, sizeof(P->st->err), s);
-  (bo::k_lc_perm<<<bo::grid_for(g.N), bo::kThreads, 0, s>>>(g, dp, P->lc_z), bo::note_launch());
-  int rc = bo::learned_coarse_values(P);
-  bo::DevState h;
+  (k_lc_perm<T><<<grid_for(g.N), kThreads, 0, s>>>(g, dp, stride, scale, P->lc_z), note_launch());
+  int rc = learned_coarse_values(P);
+  DevState h;
   if (cudaMemcpyAsync(&h, P->st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     rc = BO_ERR_CUDA;
   if (rc == BO_OK && h.err) rc = BO_ERR_BREAKDOWN;
-  if (rc != BO_OK) bo::learned_coarse_free(P);
+  if (rc != BO_OK) learned_coarse_free(P);
   return rc;
+}
+
+}  // namespace
+}  // namespace bo
+
+extern "C" {
+
+int bo_prec_set_coarse_space(bo_prec* P, const double* dp, int tx, int ty, int tz) {
+  return bo::set_coarse_space<double>(P, dp, 1, 1.0, tx, ty, tz);
+}
+
+int bo_learned_coarse_space(bo_prec* P, const float* pred, double scale, int tx, int ty, int tz) {
+  return bo::set_coarse_space<float>(P, pred, 4, scale, tx, ty, tz);
 }
 
 int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const double* scale, int ncomp, double* x0,
@@ -247,12 +315,11 @@ int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const doubl
   cudaStream_t s = P->mat->ctx->stream;
   (bo::k_guess<<<bo::grid_for(g.N), bo::kThreads, 0, s>>>(g.N, pred, scale[0], scale[1], scale[2], ncomp, x0),
    bo::note_launch());
-  // ||b - A x0|| against ||b||, with column 0 of the idle Krylov basis as r
-  // and the start of column 1 for the two norms
-  double* r = P->V;
-  double* norms = P->V + 3 * g.N;
-  int rc = bo_mat_residual_noalloc(P->mat, b, x0, r, norms);
-  if (rc != BO_OK) return rc;
+  // ||b - A x0|| against ||b||: partial sums in the preconditioner's own
+  // reduction memory, the two norms at the start of the idle Krylov basis
+  double* norms = P->V;
+  (bo::k_guess_norms<<<bo::grid_for(g.N), bo::kThreads, 0, s>>>(g, P->mat->A, b, x0, P->partials, P->st, norms),
+   bo::note_launch());
   double h[2];
   if (cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

@@ -37,23 +37,6 @@ double* g_na_ptr[kNaMaxDevices];
 cudaError_t g_na_rc[kNaMaxDevices];
 std::once_flag g_na_once[kNaMaxDevices];
 
-struct NatCell {
-  int32_t i, j, k;
-  int color;
-  int64_t q;
-};
-
-__device__ __forceinline__ NatCell na_decode(const Geom& g, int64_t c) {
-  const int64_t r = c / g.nx;
-  NatCell n;
-  n.i = (int32_t)(c - r * g.nx);
-  n.j = (int32_t)(r % g.ny);
-  n.k = (int32_t)(r / g.ny);
-  n.color = (n.i + n.j + n.k) & 1;
-  n.q = c >> 1;
-  return n;
-}
-
 // One thread per cell (natural order); one pair of partial sums per block,
 // summed in a fixed order by the block that finishes last.
 __global__ void __launch_bounds__(kNaThreads) k_residual_noalloc(Geom g, const double* __restrict__ A,
@@ -65,15 +48,13 @@ __global__ void __launch_bounds__(kNaThreads) k_residual_noalloc(Geom g, const d
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double rr = 0.0, bb = 0.0;
   if (c < g.N) {
-    const NatCell n = na_decode(g, c);
-    const int64_t nxy = (int64_t)g.nx * g.ny;
-    const bool valid[7] = {n.k > 0, n.j > 0, n.i > 0, true, n.i < g.nx - 1, n.j < g.ny - 1, n.k < g.nz - 1};
-    const int64_t off[7] = {-nxy, -(int64_t)g.nx, -1, 0, 1, (int64_t)g.nx, nxy};
+    const Nat n = decode_nat(g, c);
+    const unsigned valid = valid_slots(g, n);
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
-      if (!valid[s]) continue;
-      const int64_t nc = c + off[s];
+      if (!((valid >> s) & 1u)) continue;
+      const int64_t nc = c + nat_offset(g, s);
       const double x0 = x[3 * nc], x1 = x[3 * nc + 1], x2 = x[3 * nc + 2];
       const double* a = A + plane(g, n.color, s, 0) + n.q;
       const size_t P = (size_t)g.Nh;
@@ -118,6 +99,15 @@ __global__ void __launch_bounds__(kNaThreads) k_residual_noalloc(Geom g, const d
 extern "C" int bo_mat_residual_noalloc(bo_mat* m, const double* b, const double* x, double* r, double* norms) {
   using namespace bo;
   if (!m || !b || !x || !r || !norms) return BO_ERR_ARG;
+  // r is written while other threads still read b and x (x at six
+  // neighbours): it must not overlap either of them
+  const size_t bytes = (size_t)3 * (size_t)m->g.N * sizeof(double);
+  auto overlap = [bytes](const void* p, const void* q) {
+    const char* a = (const char*)p;
+    const char* c = (const char*)q;
+    return a < c + bytes && c < a + bytes;
+  };
+  if (overlap(r, x) || overlap(r, b)) return BO_ERR_ARG;
   const int64_t blocks = (m->g.N + kNaThreads - 1) / kNaThreads;
   if (blocks > kNaMaxBlocks) return BO_ERR_ARG;  // more than 4,194,304 cells
   const int dev = m->ctx->device;

@@ -1225,12 +1225,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
 // bounded; if it runs out (which needs a block that never arrives) the
 // barrier records kErrTimeout, and every later barrier of the launch fails
 // at once, so the kernel returns and the solve reports BO_ERR_TIMEOUT.
-constexpr unsigned kBarrierSpins = 1u << 22;
+// (the limit is a launch argument: bo_set_amg_barrier_spins lowers it)
 // one block of 1024 threads per SM: a quarter of the arrivals at each
 // barrier of four 256-thread blocks, for the same threads
 constexpr int kCoopThreads = 1024;
 
-__device__ __forceinline__ bool grid_barrier(DevState* st) {
+__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned spins) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1247,7 +1247,7 @@ __device__ __forceinline__ bool grid_barrier(DevState* st) {
       const unsigned old = atomicAdd(&st->counter[5], inc);
       unsigned it = 0;
       while (((*word ^ old) & 0x80000000u) == 0) {
-        if (++it > kBarrierSpins || (*err & kErrTimeout)) {
+        if (++it > spins || (*err & kErrTimeout)) {
           atomicOr(&st->err, kErrTimeout);
           good = 0;
           break;
@@ -1277,6 +1277,7 @@ struct CycleArgs {
   int tail_from;  // first level of the single-block tail
   int nu1, nu2;
   T s;
+  unsigned spins;  // polls of a grid barrier before it gives up (BO_ERR_TIMEOUT)
   LevelView<T, S> lv[24];
 };
 
@@ -1293,11 +1294,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
       const int zero = sw == 0 && color == 0;
       sweep_batched<4>(t0, nt, g.Nh, a.x0 + (size_t)color * g.Nh,
                        [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, color, zero, q); });
-      if (!grid_barrier(st)) return;
+      if (!grid_barrier(st, a.spins)) return;
     }
   if (a.nu1 == 0) {
     for (int64_t t = t0; t < g.N; t += nt) a.x0[t] = T(0);
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, a.spins)) return;
   }
   // The first pre-smoothing half sweep of a multi-block level starts from
   // zero, x_r = f_r / a_rr: the thread that restricts a red cell's
@@ -1312,17 +1313,17 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
     }
   }
   for (int l = 1; l < a.tail_from; ++l) {
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, a.spins)) return;
     const LevelView<T, S>& L = a.lv[l];
     for (int sw = 0; sw < a.nu1; ++sw)
       for (int color = 0; color < 2; ++color) {
         if (sw == 0 && color == 0) continue;  // done with the restriction
         for (int64_t c = t0; c < L.d.n; c += nt) gs_cell(L, c, color, 0);
-        if (!grid_barrier(st)) return;
+        if (!grid_barrier(st, a.spins)) return;
       }
     if (a.nu1 == 0) {
       for (int64_t c = t0; c < L.d.n; c += nt) L.x[c] = T(0);
-      if (!grid_barrier(st)) return;
+      if (!grid_barrier(st, a.spins)) return;
     }
     const LevelView<T, S>& C = a.lv[l + 1];
     const bool fold = a.nu1 > 0 && l + 1 < a.tail_from;
@@ -1346,7 +1347,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
     const LevelView<T, S>& C = a.lv[l + 1];
     if (a.nu2 == 0) {
       for (int64_t c = t0; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
-      if (!grid_barrier(st)) return;
+      if (!grid_barrier(st, a.spins)) return;
     }
     for (int sw = 0; sw < a.nu2; ++sw)
       for (int color = 1; color >= 0; --color) {
@@ -1354,7 +1355,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
           if (sw == 0 && color == 1) gs_cell_prolong(L, C, c, a.s);
           else gs_cell(L, c, color, 0);
         }
-        if (!grid_barrier(st)) return;
+        if (!grid_barrier(st, a.spins)) return;
       }
   }
   const LevelView<T, S>& C1 = a.lv[1];
@@ -1370,9 +1371,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
     else
       sweep_batched<4>(t0, nt, g.Nh, a.x0 + g.Nh,
                        [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 1, 0, q); });
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, a.spins)) return;
     sweep_batched<4>(t0, nt, g.Nh, a.x0, [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 0, 0, q); });
-    if (sw + 1 < a.nu2 && !grid_barrier(st)) return;
+    if (sw + 1 < a.nu2 && !grid_barrier(st, a.spins)) return;
   }
 }
 
@@ -1463,6 +1464,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   ca.nu1 = nu1;
   ca.nu2 = nu2;
   ca.s = sc;
+  ca.spins = g_amg_spins.load();
   for (int l = 1; l <= last; ++l) ca.lv[l] = view<T, S>(P, l);
   DevState* stw = const_cast<DevState*>(st);
   void* cargs[] = {&ca, &stw};

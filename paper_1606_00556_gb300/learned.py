@@ -62,8 +62,7 @@ def learned_solve(P: Preconditioner, net: CNN, x_feat, b, x, scale, ncomp: int =
         pred = torch.empty(1, V, 4, dtype=torch.float32, device=b.device)
     net.forward(x_feat, pred)
     if coarse_tile is not None:
-        dp = pred[0, :, 0].double().mul_(scale[0]).contiguous()
-        P.set_coarse_space(dp, coarse_tile)
+        P.learned_coarse_space(pred[0], scale[0], coarse_tile)
     used = P.learned_guess(b, pred[0], scale, ncomp, x)
     info = P.solve(b, x, tol=tol, restart=restart, maxit=maxit, x0_is_zero=not used, raise_on_error=False)
     info["guess_used"] = used

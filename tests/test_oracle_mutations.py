@@ -113,8 +113,36 @@ PY_MUTATIONS = [
      "newton.py", "x = x + dx", "x = x + 0.5 * dx",
      N, "test_exact_newton_converges_quadratically"),
     ("Linear residual of the Newton step with the wrong sign",
-     "newton.py", "r = b - spmv(A, dx)", "r = b + spmv(A, dx)",
+     "newton.py", "r = b - matvec(A, dx)", "r = b + matvec(A, dx)",
      N, "test_forcing_terms_reach_the_same_solution_with_fewer_linear_iterations"),
+    ("First forcing term with numerator and denominator swapped",
+     "newton.py", "return float(np.linalg.norm(b_new - r)) / nb_old",
+     "return nb_old / float(np.linalg.norm(b_new - r))",
+     N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("First forcing term with the old residual in place of the linear residual",
+     "newton.py", "return float(np.linalg.norm(b_new - r)) / nb_old",
+     "return float(np.linalg.norm(b_new + r)) / nb_old",
+     N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("Second forcing term with numerator and denominator swapped",
+     "newton.py", "return abs(float(np.linalg.norm(b_new)) - float(np.linalg.norm(r))) / nb_old",
+     "return nb_old / abs(float(np.linalg.norm(b_new)) - float(np.linalg.norm(r)))",
+     N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("Second forcing term without the absolute value",
+     "newton.py", "return abs(float(np.linalg.norm(b_new)) - float(np.linalg.norm(r))) / nb_old",
+     "return (float(np.linalg.norm(b_new)) - float(np.linalg.norm(r))) / nb_old",
+     N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("Third forcing term with the ratio inverted",
+     "newton.py", "return gamma * (float(np.linalg.norm(b_new)) / nb_old) ** beta",
+     "return gamma * (nb_old / float(np.linalg.norm(b_new))) ** beta",
+     N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("Third forcing term without gamma",
+     "newton.py", "return gamma * (float(np.linalg.norm(b_new)) / nb_old) ** beta",
+     "return (float(np.linalg.norm(b_new)) / nb_old) ** beta",
+     N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("Safeguard clips at theta_min only",
+     "newton.py", "theta = min(max(forcing_term(forcing, b_new, nb_old, r, gamma, beta), theta_min), theta_max)",
+     "theta = max(forcing_term(forcing, b_new, nb_old, r, gamma, beta), theta_min)",
+     N, "test_forcing_term_safeguards"),
 ]
 
 
