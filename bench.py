@@ -39,7 +39,9 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-8 rel. residual, 1M-cell 3-phase Jacobian; BSR SpMV HBM GB/s"
 DIMS = (128, 128, 64)
 SEED = 42
-SAMPLE_DIMS = (64, 64, 32)  # oracle sample: 1/8 of the cells
+SAMPLE_DIMS = (64, 64, 32)  # the reference arm's warm-up sample
+MIXED_DIMS = (256, 256, 128)  # the 8.4M-cell mixed-precision Jacobian
+REF_TOL = 1e-13  # the oracle's reference solutions for the error report
 
 
 def _nnzb(nx, ny, nz):
@@ -175,29 +177,100 @@ def aggregate(elapsed_ms, units, world, reduce_max):
     return {"elapsed_ms": t, "ms_per_solve": t / (units * world), "solves_per_s": units * world / (t / 1e3)}
 
 
-def oracle_sample(seed=SEED, maxit=400):
-    """The FP64 oracle (single thread) on the 64x64x32 sample Jacobian: CPR-FGMRES
-    to 1e-8 from zero; returns (seconds, iterations)."""
+def host_cores():
+    """(CPUs of the machine, CPUs this process may run on)."""
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except Exception:
+        aff = os.cpu_count() or 1
+    return os.cpu_count() or aff, aff
+
+
+def oracle_solve(a, dims, tol=1e-8, x0=None, prec=None, maxit=600):
+    """The FP64 oracle (one thread): CPR (red-black block ILU(0) + AMG) set up
+    on the Jacobian a (unless given) and GMRES(30) to tol; returns
+    (x, info, seconds, prec)."""
+    import oracle
+    A = oracle.BsrMatrix(a["rowptr"], a["col"], np.asarray(a["val"]).reshape(-1, 3, 3))
+    t0 = time.perf_counter()
+    P = prec or oracle.cpr_prec(A, dims, amg=oracle.AmgParams(coarse_max=128))
+    x, info = oracle.gmres(A, a["b"], x0=x0, tol=tol, maxit=maxit, prec=P)
+    return x, info, time.perf_counter() - t0, P
+
+
+def oracle_sample(seed=SEED):
+    """The oracle on the 64x64x32 waterflood Jacobian (the reference arm's
+    warm-up): seconds of setup + solve to 1e-8."""
+    import bogen
+    a = bogen.assemble(bogen.waterflood_case(*SAMPLE_DIMS, seed=seed, day=0))
+    _, info, sec, _ = oracle_solve(a, SAMPLE_DIMS)
+    return sec, info
+
+
+def oracle_full(dims=DIMS, seed=SEED):
+    """The oracle on the benchmark's first Jacobian itself (128x128x64, day
+    0): seconds of setup + solve to 1e-8."""
+    import bogen
+    a = bogen.assemble(bogen.waterflood_case(*dims, seed=seed, day=0))
+    _, info, sec, _ = oracle_solve(a, dims)
+    return sec, info
+
+
+def oracle_reference_job(args):
+    """Spawned worker of the CPU leg: the oracle's reference solution of a
+    seeded Jacobian (GMRES(30) + CPR to REF_TOL from zero), for the error
+    report of the GPU solves; returns (x_ref, info, seconds)."""
+    dims, seed, day, tol = args
     import bogen
     import oracle
-    case = bogen.waterflood_case(*SAMPLE_DIMS, seed=seed, day=0)
-    a = bogen.assemble(case)
-    A = oracle.BsrMatrix(a["rowptr"], a["col"], a["val"])
+    oracle.build()
+    a = bogen.assemble(bogen.waterflood_case(*dims, seed=seed, day=day))
+    x, info, sec, _ = oracle_solve(a, dims, tol=tol)
+    return x, info, sec
+
+
+def cpu_baseline_record(seconds, info, dims=DIMS, what="the benchmark's first Jacobian (day 0)"):
+    total, aff = host_cores()
+    return {"value": seconds * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+            "host_cores": total, "affinity_cores": aff,
+            "sample": (f"oracle CPR-GMRES(30) (red-black block ILU(0) + AMG, FP64, one thread) on {what}, "
+                       f"{dims[0]}x{dims[1]}x{dims[2]} waterflood, setup + solve to 1e-8 from zero "
+                       f"({info['iters']} its, {seconds:.2f} s)")}
+
+
+def cpu_spmv_record(a, threads, reps=10):
+    """The CPU's BSR SpMV bandwidth: the oracle's threaded y = A x over the
+    process's CPUs, algorithmic bytes as for the GPU SpMV."""
+    import oracle
+    A = oracle.BsrMatrix(a["rowptr"], a["col"], np.asarray(a["val"]).reshape(-1, 3, 3))
+    x = np.random.default_rng(1).standard_normal(A.n)
+    y = np.zeros(A.n)
+    for _ in range(2):
+        oracle.spmv_threads(A, x, threads, y)
     t0 = time.perf_counter()
-    P = oracle.cpr_prec(A, SAMPLE_DIMS, amg=oracle.AmgParams(coarse_max=128))
-    x, info = oracle.gmres(A, a["b"], tol=1e-8, maxit=maxit, prec=P)
-    return time.perf_counter() - t0, info
+    for _ in range(reps):
+        oracle.spmv_threads(A, x, threads, y)
+    sec = (time.perf_counter() - t0) / reps
+    byts = 9 * 8 * A.col.size + 2 * A.n * 8
+    return {"us": sec * 1e6, "algorithmic_bytes": byts, "gbs": byts / sec / 1e9, "threads": threads,
+            "kind": "oracle BSR SpMV over host threads (FP64)"}
 
 
-def cpu_baseline_record(seconds, info, dims=DIMS):
-    scale = float(np.prod(dims)) / float(np.prod(SAMPLE_DIMS))
-    return {"value": seconds * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle CPR-GMRES(30) (red-black block ILU(0) + AMG, FP64, one thread) on the "
-                       f"{SAMPLE_DIMS[0]}x{SAMPLE_DIMS[1]}x{SAMPLE_DIMS[2]} waterflood Jacobian to 1e-8 "
-                       f"({info['iters']} its, {seconds:.2f} s), scaled by the cell ratio x{scale:.0f}")}
+def solution_errors(x, xr):
+    """||x - x_ref|| / ||x_ref||, overall and per component (p, Sw, Sg)."""
+    x = np.asarray(x, dtype=np.float64)
+    xr = np.asarray(xr, dtype=np.float64)
+    out = {"all": float(np.linalg.norm(x - xr) / np.linalg.norm(xr))}
+    for k, nm in enumerate(("p", "sw", "sg")):
+        out[nm] = float(np.linalg.norm(x[k::3] - xr[k::3]) / np.linalg.norm(xr[k::3]))
+    return out
 
 
 def run_reference(args):
+    """The FP64 oracle as the reference arm: every timed step is the
+    oracle's setup and CPR-GMRES(30) solve of the benchmark's first
+    128x128x64 Jacobian to 1e-8 (one thread); the warm-up steps run the
+    64x64x32 sample, which exercises the same code."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -205,11 +278,14 @@ def run_reference(args):
     oracle.build()
     for _ in range(args.warmup):
         oracle_sample()
+    import bogen
+    a = bogen.assemble(bogen.waterflood_case(*DIMS, seed=SEED, day=0))
     times, info = [], None
     for _ in range(args.steps):
-        s, info = oracle_sample()
-        times.append(s)
+        _, info, sec, _ = oracle_solve(a, DIMS)
+        times.append(sec)
     rec = cpu_baseline_record(statistics.mean(times), info)
+    rec["sample"] += f"; mean of {args.steps} steps"
     line = {"impl": "reference", "metric": METRIC, "value": rec["value"], "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -509,6 +585,57 @@ def run_conv(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(bo, ctx, dev, stream, a, args):
+    """The 256x256x128 Jacobian with the FP32, BF16-storage and FP64
+    preconditioners: per precision one untimed step, then args.mixed_steps
+    timed steps (value ingest, preconditioner update, CPR-FGMRES to 1e-8
+    from zero), CUDA events on the library's stream; returns (record, the
+    solutions on the host for the error report)."""
+    import torch
+    dims = MIXED_DIMS
+    n = 3 * int(np.prod(dims))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), a["rowptr"], a["col"], a["val"])
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info(dev)[0]
+    val = torch.from_numpy(np.ascontiguousarray(a["val"]).reshape(-1)).to(dev)
+    b = torch.from_numpy(a["b"]).to(dev)
+    rec = {"grid": list(dims), "unknowns": n, "nnzb": _nnzb(*dims), "matrix_gb": (free0 - free1) / 1e9,
+           "l2": "inputs larger than L2 (4.2 GB of FP64 matrix values)"}
+    xs = {}
+    for nm, pr in (("fp32", bo.BO_PREC_FP32), ("bf16", bo.BO_PREC_BF16), ("fp64", bo.BO_PREC_FP64)):
+        torch.cuda.synchronize()
+        f0 = torch.cuda.mem_get_info(dev)[0]
+        P = bo.Preconditioner(A, precision=pr)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+
+        def step():
+            A.update_values(val)
+            P.update()
+            return P.solve(b, x, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True, raise_on_error=False)
+
+        step()
+        torch.cuda.synchronize()
+        f1 = torch.cuda.mem_get_info(dev)[0]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [step() for _ in range(args.mixed_steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rec[nm] = {"ms": e0.elapsed_time(e1) / max(1, args.mixed_steps), "iters": [i["iters"] for i in infos],
+                   "status": [i["status"] for i in infos],
+                   "true_rel_res_max": max(i["true_rel_res"] for i in infos),
+                   "preconditioner_and_krylov_gb": (f0 - f1) / 1e9}
+        xs[nm] = x.cpu().numpy()
+        P.close()
+    A.close()
+    del val, b
+    torch.cuda.empty_cache()
+    return rec, xs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +649,11 @@ def main():
     ap.add_argument("--jacobians", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the 256x256x128 (8.4M-cell) mixed-precision Jacobian")
+    ap.add_argument("--mixed-steps", type=int, default=3, help="timed solves per precision at 256x256x128")
+    ap.add_argument("--mixed-ref-tol", type=float, default=1e-12,
+                    help="tolerance of the oracle's reference solution at 256x256x128")
     ap.add_argument("--secondary", default="fp64", choices=["fp32", "fp64", "bf16", "none"],
                     help="also time the other preconditioner precision on the same Jacobians")
     ap.add_argument("--dist-backend", default="nccl")
@@ -552,13 +684,34 @@ def main():
 
     # inputs first (spawned generator workers must start before CUDA)
     dims = tuple(args.dims)
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu_baseline
+    mixed = rank == 0 and not args.no_mixed
+    ref_pool = ref_async = None
+    if cpu_leg and mixed:
+        # the oracle's reference solution of the 8.4M-cell Jacobian takes
+        # minutes on one core: a spawned worker of the CPU leg computes it
+        # while the GPU runs
+        ref_pool = mp.get_context("spawn").Pool(1)
+        ref_async = ref_pool.apply_async(oracle_reference_job, ((MIXED_DIMS, SEED, 0, args.mixed_ref_tol),))
     jac = generate(dims, rank_seed(rank), args.jacobians, procs=min(16, os.cpu_count() or 1))
-    cpu_rec = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    mix_a = None
+    if mixed:
+        import bogen
+        mix_a = bogen.assemble(bogen.waterflood_case(*MIXED_DIMS, seed=SEED, day=0))
+    cpu_rec = cpu_spmv = xref = None
+    if cpu_leg:
+        # the oracle timed on the benchmark's first Jacobian itself, then
+        # continued (untimed) to the reference solution of the error report
         import oracle
         oracle.build()
-        s, info = oracle_sample()
-        cpu_rec = cpu_baseline_record(s, info, dims)
+        a0 = {"rowptr": jac[0][0], "col": jac[0][1], "val": jac[0][2], "b": jac[0][3]}
+        x8, info8, sec, Po = oracle_solve(a0, dims)
+        cpu_rec = cpu_baseline_record(sec, info8, dims)
+        xref, info_ref, sec_ref, _ = oracle_solve(a0, dims, tol=REF_TOL, x0=x8, prec=Po)
+        cpu_rec["reference_solution"] = {"tol": REF_TOL, "iters": info8["iters"] + info_ref["iters"],
+                                         "rel_res": info_ref["relres"], "converged": info_ref["converged"]}
+        cpu_spmv = cpu_spmv_record(a0, host_cores()[1])
+        del Po
 
     import torch
     import paper_1606_00556_gb300 as bo
@@ -719,6 +872,39 @@ def main():
                "d2h_bytes_per_step": n * 8,
                "host_cpus": f"{len(numa_cpus)} CPUs local to the GPU" if numa_cpus else "unbound"}
 
+    # error report: each preconditioner precision on the first Jacobian
+    # against the oracle's reference solution (overall and per component)
+    errors = {}
+    if xref is not None:
+        A.update_values(vals[0])
+        errors["reference"] = {"128x128x64": cpu_rec["reference_solution"]}
+        errors["128x128x64"] = {}
+        for nm, pr in (("fp64", bo.BO_PREC_FP64), ("fp32", bo.BO_PREC_FP32), ("bf16", bo.BO_PREC_BF16)):
+            Pe = bo.Preconditioner(A, precision=pr)
+            xe = torch.zeros(n, dtype=torch.float64, device=dev)
+            ie = Pe.solve(bs[0], xe, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True,
+                          raise_on_error=False)
+            errors["128x128x64"][nm] = {"status": ie["status"], "iters": ie["iters"],
+                                        "true_rel_res": ie["true_rel_res"],
+                                        **solution_errors(xe.cpu().numpy(), xref)}
+            Pe.close()
+
+    # the 256x256x128 Jacobian (8.4M cells, 25.2M unknowns) in every
+    # preconditioner precision: time to 1e-8 (ingest, setup and solve, as a
+    # step above), iterations, device memory
+    mixed_rec = None
+    mixed_x = {}
+    if mix_a is not None:
+        mixed_rec, mixed_x = run_mixed(bo, ctx, dev, stream, mix_a, args)
+        del mix_a
+    if ref_async is not None:
+        xr8, info_r8, sec_r8 = ref_async.get()
+        ref_pool.close()
+        errors.setdefault("reference", {})["256x256x128"] = {
+            "tol": args.mixed_ref_tol, "iters": info_r8["iters"], "rel_res": info_r8["relres"],
+            "converged": info_r8["converged"], "oracle_seconds": sec_r8}
+        errors["256x256x128"] = {nm: solution_errors(xm, xr8) for nm, xm in mixed_x.items()}
+
     if rank == 0:
         iters = [i["iters"] for i in infos]
         line = {
@@ -732,7 +918,12 @@ def main():
                          "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
                          "fp64_equivalent_tflops": ach_tf,
                          "avg_us": avg_s * 1e6 if avg_s else None, "launches": spmv_n},
-            "spmv": sp, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "spmv": sp, "spmv_cpu": cpu_spmv, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e,
+            "errors": errors or None, "mixed_256x256x128": mixed_rec,
+            "precision_note": ("no all-FP64 path is timed: even the FP64 preconditioner form computes the Arnoldi "
+                               "product in split FP32 pairs (2^-46 relative per term); convergence is decided "
+                               "on the FP64 true residual of the original system"),
+            "gpu_launches": launches, "clocks": clk,
             "iters": iters, "iters_mean": float(np.mean(iters)),
             "true_rel_res_max": max(i["true_rel_res"] for i in infos),
             "solves_per_s": agg["solves_per_s"],

@@ -71,7 +71,10 @@ enum {
   BO_STAGE_CPR = 0,           /* z = CPR(D_QI^{-1} r): the preconditioner FGMRES uses */
   BO_STAGE_ILU = 1,           /* z = R^{-1} r, R = red-black block ILU(0) of D_QI^{-1} A */
   BO_STAGE_AMG = 2,           /* z = Pi_p AMG(A_pp)^{-1} Pi_r r                         */
-  BO_STAGE_CPR_DECOUPLED = 3  /* z = CPR(r), Alg. 2 on an already decoupled r           */
+  BO_STAGE_CPR_DECOUPLED = 3, /* z = CPR(r), Alg. 2 on an already decoupled r          */
+  BO_STAGE_ARNOLDI_SPMV = 4   /* z = A r by FGMRES's own Arnoldi product: r split into
+                                 two floats per entry (48 significant bits), the split
+                                 copy of A, FP32 instructions (see bo_solve)           */
 };
 
 /* Structured grid (paper Sec. 3.3).  nx must be even (the red-black layout

@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
     if os.environ.get("BO_ORACLE_LIB"):
         return _LIB_PATH
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", src, "-o", _LIB_PATH])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", src, "-o", _LIB_PATH])
     return _LIB_PATH
 
 
@@ -126,6 +126,14 @@ def spmv(A: BsrMatrix, x) -> np.ndarray:
     x = _d(x)
     y = np.zeros(A.n)
     lib().or_bsr_spmv(*A.args(), _p(x, _D), _p(y, _D))
+    return y
+
+
+def spmv_threads(A: BsrMatrix, x, nthreads: int, y=None) -> np.ndarray:
+    """y = A x over nthreads host threads (the CPU SpMV bandwidth baseline)."""
+    x = _d(x)
+    y = np.zeros(A.n) if y is None else y
+    lib().or_bsr_spmv_threads(*A.args(), _p(x, _D), _p(y, _D), ctypes.c_int(int(nthreads)))
     return y
 
 

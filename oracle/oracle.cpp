@@ -18,6 +18,8 @@
 //   or_bicgstab            right-preconditioned BiCGSTAB (Sec. 3.3 solver list; the
 //                                                       solver of Sec. 4's scalability runs)
 //   or_rel_residual        ||b - A x|| / ||b||, compensated sums (Alg. 1 criterion)
+//   or_bsr_spmv_threads    y = A x over T host threads: the CPU bandwidth
+//                          baseline of the benchmark (the only threaded routine)
 //
 // Layout conventions: BSR with bs x bs blocks stored row-major inside a
 // block; block columns sorted ascending within a block row.  Unknown k of
@@ -28,6 +30,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -566,6 +569,32 @@ void or_bsr_spmv(int64_t nb, int bs, const int32_t* rowptr, const int32_t* col, 
                  const double* x, double* y) {
   Bsr A = make_bsr(nb, bs, rowptr, col, val);
   A.spmv(x, y);
+}
+
+// y = A x with the block rows split into T contiguous ranges, one host
+// thread each (no copy of A: the benchmark times this as the CPU's SpMV
+// bandwidth).  Same arithmetic as or_bsr_spmv row by row.
+void or_bsr_spmv_threads(int64_t nb, int bs, const int32_t* rowptr, const int32_t* col, const double* val,
+                         const double* x, double* y, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  auto rows = [=](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i)
+      for (int r = 0; r < bs; ++r) {
+        double acc = 0.0;
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+          const double* blk = val + (size_t)e * bs * bs + bs * r;
+          const double* xc = x + (size_t)col[e] * bs;
+          for (int c = 0; c < bs; ++c) acc += blk[c] * xc[c];
+        }
+        y[i * bs + r] = acc;
+      }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) {
+    const int64_t i0 = nb * t / nthreads, i1 = nb * (t + 1) / nthreads;
+    pool.emplace_back(rows, i0, i1);
+  }
+  for (auto& th : pool) th.join();
 }
 
 // out = D_QI^{-1} A (same pattern), g[3 nb] = the row-0 weights of D_QI^{-1} per cell

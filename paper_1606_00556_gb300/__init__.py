@@ -37,6 +37,7 @@ BO_STAGE_CPR = 0
 BO_STAGE_ILU = 1
 BO_STAGE_AMG = 2
 BO_STAGE_CPR_DECOUPLED = 3
+BO_STAGE_ARNOLDI_SPMV = 4
 BO_LAUNCH_STREAM = 0
 BO_LAUNCH_GRAPH = 1
 

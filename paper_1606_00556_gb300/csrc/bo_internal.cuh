@@ -500,6 +500,11 @@ int bicgstab(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
                    bo_solve_info* infos);
 int krylov_alloc(bo_prec* P, int m);
+// w = A v (internal order, FP64 in and out) by the FGMRES Arnoldi product
+// (split copy of A, v split into pairs; the FP64 planes where the split copy
+// is out of range); uses P's first preconditioned vector and the first FP32
+// shadow as scratch
+void launch_arnoldi_product(bo_prec* P, const double* v, double* w);
 void graphs_reset(bo_prec* P);
 // tcgen05 convolution for 32 -> 32 layers; mode 0 ReLU, 1 ReLU + residual,
 // 2 linear FP32 output.  BO_ERR_ARG where it does not apply.

@@ -351,12 +351,17 @@ int bo_prec_update(bo_prec* P) {
 }
 
 int bo_prec_apply(bo_prec* P, int stage, const double* r, double* z) {
-  if (!P || !r || !z || stage < BO_STAGE_CPR || stage > BO_STAGE_CPR_DECOUPLED) return BO_ERR_ARG;
+  if (!P || !r || !z || stage < BO_STAGE_CPR || stage > BO_STAGE_ARNOLDI_SPMV) return BO_ERR_ARG;
   cudaStream_t s = P->stream;
   const Geom& g = P->mat->g;
   cudaMemsetAsync(&P->st->done, 0, sizeof(int), s);
-  // r -> internal (xi as scratch), apply, z (precision T) -> FP64 internal -> natural
   launch_gather(g, r, P->bi, s);
+  if (stage == BO_STAGE_ARNOLDI_SPMV) {
+    launch_arnoldi_product(P, P->bi, P->xi);
+    launch_scatter(g, P->xi, z, s);
+    return cuda_status(cudaStreamSynchronize(s));
+  }
+  // r -> internal (bi), apply, z (precision T) -> FP64 internal -> natural
   launch_cpr(P, P->bi, P->Z, stage, P->st);
   launch_scatter(g, P->Z, z, s);
   return cuda_status(cudaStreamSynchronize(s));

@@ -761,6 +761,33 @@ struct Job {
 
 }  // namespace
 
+namespace {
+// v (FP64, internal order) -> split pairs: hi plane z[0..n), lo plane z[n..2n)
+__global__ void k_split_vec(int64_t n, const double* __restrict__ v, float* __restrict__ z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int bad = 0;
+    const float2 p = df_split_bits(v[i], &bad);
+    z[i] = p.x;
+    z[n + i] = p.y;
+  }
+}
+}  // namespace
+
+// w = A v on internal vectors by the solver's own Arnoldi product: v split
+// into pairs, the kernel every FGMRES iteration runs, w in FP64
+void launch_arnoldi_product(bo_prec* P, const double* v, double* w) {
+  cudaStream_t s = P->stream;
+  bo_mat* m = P->mat;
+  const Geom& g = m->g;
+  const int64_t n = 3 * g.N;
+  if (!m->a2_valid) launch_split_matrix(m, s);
+  float* z = (float*)P->Z;  // the first preconditioned vector's split planes as scratch
+  (k_split_vec<<<grid_for(n), kThreads, 0, s>>>(n, v, z), note_launch());
+  (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(g, m->A2, m->A, m->a2_range, z, w,
+                                                                                    P->Vs, P->st),
+   note_launch());
+}
+
 int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
   int rc = krylov_alloc(P, o->restart);
   if (rc != BO_OK) return rc;

@@ -196,7 +196,7 @@ def _compile(tmp_path, name, text):
     src = tmp_path / f"{name}.cpp"
     src.write_text(text)
     so = tmp_path / f"lib{name}.so"
-    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", str(src), "-o", str(so)])
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-pthread", "-shared", "-fPIC", str(src), "-o", str(so)])
     return str(so)
 
 

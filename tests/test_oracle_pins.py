@@ -43,6 +43,17 @@ def test_spmv_matches_dense_product():
     assert np.allclose(oracle.spmv(A, x), A.to_dense() @ x, rtol=1e-14, atol=1e-13)
 
 
+@pytest.mark.parametrize("nthreads", [1, 3, 7])
+def test_threaded_spmv_matches_dense_product(nthreads):
+    # the CPU bandwidth baseline: the dense product, and bitwise the serial
+    # SpMV (same sums per row, rows split over threads)
+    A = _random_bsr(6, 5, 3, 4)
+    x = np.random.default_rng(3).standard_normal(A.n)
+    y = oracle.spmv_threads(A, x, nthreads)
+    assert np.allclose(y, A.to_dense() @ x, rtol=1e-14, atol=1e-13)
+    assert np.array_equal(y, oracle.spmv(A, x))
+
+
 def test_qi_operator_multiplied_back_gives_A():
     # paper Sec. 3.2: D_QI = [[I, D_ps D_ss^-1, 0], [0, I, 0], [0, 0, I]] with
     # D_ps = diag(A_ps), D_ss = diag(A_ss); built here as a dense matrix in
