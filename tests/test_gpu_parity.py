@@ -10,12 +10,15 @@ Tolerances (derived from the arithmetic):
     rounding by the conditioning of the factors; tested element by element
     at 1e-12 ||ref||_inf (and at 1e-9 in norm).
   * FP32 preconditioner stages (values rounded to FP32 once, FP32
-    arithmetic): element by element at 1e-5 ||ref||_inf for the ILU and AMG
-    stages and 1e-4 ||ref||_inf for the CPR composition, whose two residuals
-    of the decoupled system cancel.
-  * The Arnoldi product (split copy of A, x split into pairs): each term
-    carries at most 2^-46 relative error from each split and about 2^-47 from
-    the split products and sums, so |y - y_ref| <= 1e-13 (|A| |x|)_i.
+    arithmetic, 2^-24 relative per operation, amplified by the two triangular
+    passes and the V-cycle): element by element at 1e-5 ||ref||_inf (measured
+    up to 8e-7).
+  * The Arnoldi product (split copy of A, x split into pairs): per term at
+    most 2^-46 relative from each of the two splits and 2^-48 from each of
+    the three dropped or rounded low products, and per accumulation step at
+    most 2 x 2^-48 of the running sum (21 steps), so |y - y_ref| <=
+    (2^-45 + 3 x 2^-48 + 42 x 2^-48) (|A| |x|)_i < 2e-13 (|A| |x|)_i
+    (measured up to 6.4e-14).
   * Solves (the spec bar): true FP64 residual ||b - A x|| / ||b|| <=
     1e-8 checked by the oracle's compensated residual, and
     ||x - x_ref|| / ||x_ref|| <= 1e-6 against the oracle solved to 1e-13.
@@ -231,7 +234,7 @@ def _close(z, ref, tol_elem, tol_norm=1e-9):
     assert np.linalg.norm(z - ref) <= max(tol_norm, tol_elem) * np.linalg.norm(ref)
 
 
-STAGE_TOL32 = {"ilu": 1e-5, "amg": 1e-5, "cpr_decoupled": 1e-4, "cpr": 1e-4}
+STAGE_TOL32 = {"ilu": 1e-5, "amg": 1e-5, "cpr_decoupled": 1e-5, "cpr": 1e-5}
 
 
 @pytest.mark.parametrize("dims", [(20, 20, 5), (96, 96, 40)])
@@ -264,7 +267,7 @@ def test_arnoldi_product_matches_oracle_elementwise(bo, ctx, dims):
     x = np.random.default_rng(20).standard_normal(Ao.n)
     y = P.apply(bo.BO_STAGE_ARNOLDI_SPMV, _dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda"))
     y = y.cpu().numpy()
-    assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x) + 1e-300)
+    assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 2e-13 * _absprod(Ao, x) + 1e-300)
 
 
 def test_arnoldi_product_fp64_fallback_matches_oracle_elementwise(bo, ctx):
