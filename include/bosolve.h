@@ -441,14 +441,19 @@ int bo_conv3d_backward_weights(bo_ctx* ctx, int nx, int ny, int nz, int batch, i
  * accumulator, TMA-fetched tiles; the default).  The other layers always use
  * mma.sync. */
 int bo_set_conv_engine(int engine);
-/* How the AMG V-cycle launches its multi-block levels (process-wide):
- * 1 (the default) = two cooperative launches per V-cycle, a down leg and an
- * up leg, whose blocks meet at grid-wide barriers between the Gauss-Seidel
- * half sweeps of paper Sec. 3.2's pressure AMG stage; 0 = one kernel per half
- * sweep, restriction and prolongation.  Both compute the same V-cycle.
+/* How the AMG V-cycle is launched (process-wide); every form computes the
+ * same V-cycle of paper Sec. 3.2's pressure AMG stage:
+ * 2 (the default) = level 0 in two cooperative launches, a down leg and an
+ *   up leg whose blocks meet at grid-wide barriers between the Gauss-Seidel
+ *   half sweeps, around one thread-block-cluster launch (up to 16 blocks,
+ *   hardware cluster barriers) for all coarser levels;
+ * 1 = the cooperative legs also smooth the coarser multi-block levels, the
+ *   levels of at most 4096 cells run in one block;
+ * 0 = one kernel per half sweep, restriction and prolongation.
  * Inside stream capture (CUDA-graph launch mode) the per-kernel form is used
- * whatever the setting.  A barrier that waits too long ends the launch and
- * the solve returns BO_ERR_TIMEOUT.  BO_ERR_ARG for another mode. */
+ * whatever the setting, and a form the device refuses falls back to it.  A
+ * grid barrier that waits too long ends the launch and the solve returns
+ * BO_ERR_TIMEOUT.  BO_ERR_ARG for another mode. */
 int bo_set_amg_cooperative(int on);
 /* Polls of a grid barrier of the cooperative AMG legs before it gives up
  * (process-wide; read at each V-cycle launch).  0 restores the default,

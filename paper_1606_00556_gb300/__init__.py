@@ -604,8 +604,9 @@ def bo_update_batched(precs, vals=None):
 
 
 def bo_set_amg_cooperative(on: int):
-    """1: the AMG's multi-block levels as two cooperative launches per
-    V-cycle (grid barriers between half sweeps); 0: one kernel per sweep."""
+    """2 (default): level 0 as two cooperative launches per V-cycle around
+    one cluster launch for the coarser levels; 1: the cooperative launches
+    cover every multi-block level; 0: one kernel per sweep."""
     _check(lib().bo_set_amg_cooperative(int(on)), "bo_set_amg_cooperative")
 
 

@@ -17,7 +17,7 @@ namespace bo {
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_pool_width{kMaxPoolStreams};
 std::atomic<int> g_conv_engine{1};
-std::atomic<int> g_amg_coop{1};
+std::atomic<int> g_amg_coop{2};
 std::atomic<unsigned> g_amg_spins{kAmgSpinsDefault};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
@@ -550,7 +550,7 @@ int bo_prec_residual_history(bo_prec* P, double* buf, int cap) {
 int64_t bo_kernel_launches(void) { return g_launches.load(); }
 
 int bo_set_amg_cooperative(int on) {
-  if (on != 0 && on != 1) return BO_ERR_ARG;
+  if (on < 0 || on > 2) return BO_ERR_ARG;
   g_amg_coop.store(on);
   return BO_OK;
 }

@@ -19,6 +19,7 @@
 // correction, black then red after it.  After a black half sweep only red
 // cells carry a residual, so restriction sums red residuals.  Levels of at
 // most kTailCells cells run inside one thread block (kernel k_tail).
+#include <atomic>
 #include <cstdio>
 
 #include "bo_internal.cuh"
@@ -965,39 +966,48 @@ struct LevelView {
   __device__ __forceinline__ T cc(int slot, int64_t cidx) const { return cv<T>(c[slot * d.n + cidx]); }
 };
 
-template <typename T, typename S>
+// Loads of iterates and right-hand sides.  CG = true: through L2 only, for
+// values that other thread blocks of the same launch wrote before a barrier
+// (the cluster form of the coarse levels); false: ordinary loads.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
+template <bool CG = false, typename T, typename S>
 __device__ __forceinline__ void gs_cell(const LevelView<T, S>& L, int64_t cidx, int color, int zero_guess) {
   const Ijk p = ijk_of(L.d, cidx);
   const int i = p.i, j = p.j, k = p.k;
   if (((i + j + k) & 1) != color) return;
-  T s = L.f[cidx];
+  T s = ldv<CG>(L.f + cidx);
   if (!zero_guess) {
     const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-    if (k > 0) s -= L.cc(kZm, cidx) * L.x[cidx - nxy];
-    if (j > 0) s -= L.cc(kYm, cidx) * L.x[cidx - L.d.nx];
-    if (i > 0) s -= L.cc(kXm, cidx) * L.x[cidx - 1];
-    if (i < L.d.nx - 1) s -= L.cc(kXp, cidx) * L.x[cidx + 1];
-    if (j < L.d.ny - 1) s -= L.cc(kYp, cidx) * L.x[cidx + L.d.nx];
-    if (k < L.d.nz - 1) s -= L.cc(kZp, cidx) * L.x[cidx + nxy];
+    if (k > 0) s -= L.cc(kZm, cidx) * ldv<CG>(L.x + cidx - nxy);
+    if (j > 0) s -= L.cc(kYm, cidx) * ldv<CG>(L.x + cidx - L.d.nx);
+    if (i > 0) s -= L.cc(kXm, cidx) * ldv<CG>(L.x + cidx - 1);
+    if (i < L.d.nx - 1) s -= L.cc(kXp, cidx) * ldv<CG>(L.x + cidx + 1);
+    if (j < L.d.ny - 1) s -= L.cc(kYp, cidx) * ldv<CG>(L.x + cidx + L.d.nx);
+    if (k < L.d.nz - 1) s -= L.cc(kZp, cidx) * ldv<CG>(L.x + cidx + nxy);
   }
   L.x[cidx] = s / L.cc(kDiag, cidx);
 }
 
-template <typename T, typename S>
+template <bool CG = false, typename T, typename S>
 __device__ __forceinline__ T residual_cell(const LevelView<T, S>& L, int i, int j, int k) {
   const int64_t cidx = nat_index(L.d, i, j, k);
   const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-  T r = L.f[cidx] - L.cc(kDiag, cidx) * L.x[cidx];
-  if (k > 0) r -= L.cc(kZm, cidx) * L.x[cidx - nxy];
-  if (j > 0) r -= L.cc(kYm, cidx) * L.x[cidx - L.d.nx];
-  if (i > 0) r -= L.cc(kXm, cidx) * L.x[cidx - 1];
-  if (i < L.d.nx - 1) r -= L.cc(kXp, cidx) * L.x[cidx + 1];
-  if (j < L.d.ny - 1) r -= L.cc(kYp, cidx) * L.x[cidx + L.d.nx];
-  if (k < L.d.nz - 1) r -= L.cc(kZp, cidx) * L.x[cidx + nxy];
+  T r = ldv<CG>(L.f + cidx) - L.cc(kDiag, cidx) * ldv<CG>(L.x + cidx);
+  if (k > 0) r -= L.cc(kZm, cidx) * ldv<CG>(L.x + cidx - nxy);
+  if (j > 0) r -= L.cc(kYm, cidx) * ldv<CG>(L.x + cidx - L.d.nx);
+  if (i > 0) r -= L.cc(kXm, cidx) * ldv<CG>(L.x + cidx - 1);
+  if (i < L.d.nx - 1) r -= L.cc(kXp, cidx) * ldv<CG>(L.x + cidx + 1);
+  if (j < L.d.ny - 1) r -= L.cc(kYp, cidx) * ldv<CG>(L.x + cidx + L.d.nx);
+  if (k < L.d.nz - 1) r -= L.cc(kZp, cidx) * ldv<CG>(L.x + cidx + nxy);
   return r;
 }
 
-template <typename T, typename S>
+template <bool CG = false, typename T, typename S>
 __device__ __forceinline__ T restrict_cell(const LevelView<T, S>& F, const LevelDims& C, int64_t I, int red_only) {
   const Ijk cc = ijk_of(C, I);
   const int ci = cc.i, cj = cc.j, ck = cc.k;
@@ -1008,36 +1018,36 @@ __device__ __forceinline__ T restrict_cell(const LevelView<T, S>& F, const Level
         const int i = 2 * ci + di, j = 2 * cj + dj, k = 2 * ck + dk;
         if (i >= F.d.nx || j >= F.d.ny || k >= F.d.nz) continue;
         if (red_only && ((i + j + k) & 1)) continue;
-        acc += residual_cell(F, i, j, k);
+        acc += residual_cell<CG>(F, i, j, k);
       }
   return acc;
 }
 
-template <typename T, typename S>
+template <bool CG = false, typename T, typename S>
 __device__ __forceinline__ void prolong_cell(const LevelView<T, S>& F, const LevelView<T, S>& C, int64_t cidx, T s) {
   const Ijk p = ijk_of(F.d, cidx);
   const int i = p.i, j = p.j, k = p.k;
-  F.x[cidx] += s * C.x[nat_index(C.d, i / 2, j / 2, k / 2)];
+  F.x[cidx] = ldv<CG>(F.x + cidx) + s * ldv<CG>(C.x + nat_index(C.d, i / 2, j / 2, k / 2));
 }
 
 // black half sweep with the coarse correction of the red neighbours folded in
 // (the natural-order counterpart of k_gs0_prolong)
-template <typename T, typename S>
+template <bool CG = false, typename T, typename S>
 __device__ __forceinline__ void gs_cell_prolong(const LevelView<T, S>& L, const LevelView<T, S>& C, int64_t cidx, T sc) {
   const Ijk p = ijk_of(L.d, cidx);
   const int i = p.i, j = p.j, k = p.k;
   if (((i + j + k) & 1) != 1) return;
   const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-  T s = L.f[cidx];
-  if (k > 0) s -= L.cc(kZm, cidx) * (L.x[cidx - nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k - 1) / 2)]);
-  if (j > 0) s -= L.cc(kYm, cidx) * (L.x[cidx - L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j - 1) / 2, k / 2)]);
-  if (i > 0) s -= L.cc(kXm, cidx) * (L.x[cidx - 1] + sc * C.x[nat_index(C.d, (i - 1) / 2, j / 2, k / 2)]);
-  if (i < L.d.nx - 1)
-    s -= L.cc(kXp, cidx) * (L.x[cidx + 1] + sc * C.x[nat_index(C.d, (i + 1) / 2, j / 2, k / 2)]);
-  if (j < L.d.ny - 1)
-    s -= L.cc(kYp, cidx) * (L.x[cidx + L.d.nx] + sc * C.x[nat_index(C.d, i / 2, (j + 1) / 2, k / 2)]);
-  if (k < L.d.nz - 1)
-    s -= L.cc(kZp, cidx) * (L.x[cidx + nxy] + sc * C.x[nat_index(C.d, i / 2, j / 2, (k + 1) / 2)]);
+  auto xv = [&](int64_t f, int ci, int cj, int ck) {
+    return ldv<CG>(L.x + f) + sc * ldv<CG>(C.x + nat_index(C.d, ci, cj, ck));
+  };
+  T s = ldv<CG>(L.f + cidx);
+  if (k > 0) s -= L.cc(kZm, cidx) * xv(cidx - nxy, i / 2, j / 2, (k - 1) / 2);
+  if (j > 0) s -= L.cc(kYm, cidx) * xv(cidx - L.d.nx, i / 2, (j - 1) / 2, k / 2);
+  if (i > 0) s -= L.cc(kXm, cidx) * xv(cidx - 1, (i - 1) / 2, j / 2, k / 2);
+  if (i < L.d.nx - 1) s -= L.cc(kXp, cidx) * xv(cidx + 1, (i + 1) / 2, j / 2, k / 2);
+  if (j < L.d.ny - 1) s -= L.cc(kYp, cidx) * xv(cidx + L.d.nx, i / 2, (j + 1) / 2, k / 2);
+  if (k < L.d.nz - 1) s -= L.cc(kZp, cidx) * xv(cidx + nxy, i / 2, j / 2, (k + 1) / 2);
   L.x[cidx] = s / L.cc(kDiag, cidx);
 }
 
@@ -1275,6 +1285,7 @@ struct CycleArgs {
   T* f0;
   T* x0;
   int tail_from;  // first level of the single-block tail
+  int legs_to;    // the down and up legs smooth levels 0 .. legs_to - 1 (the rest: the cluster kernel)
   int nu1, nu2;
   T s;
   unsigned spins;  // polls of a grid barrier before it gives up (BO_ERR_TIMEOUT)
@@ -1312,7 +1323,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
       if (fold && red_cell(C.d, I)) C.x[I] = fI / C.cc(kDiag, I);
     }
   }
-  for (int l = 1; l < a.tail_from; ++l) {
+  for (int l = 1; l < a.legs_to; ++l) {
     if (!grid_barrier(st, a.spins)) return;
     const LevelView<T, S>& L = a.lv[l];
     for (int sw = 0; sw < a.nu1; ++sw)
@@ -1342,7 +1353,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
   if (st->done) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
   const Geom& g = a.g;
-  for (int l = a.tail_from - 1; l >= 1; --l) {
+  for (int l = a.legs_to - 1; l >= 1; --l) {
     const LevelView<T, S>& L = a.lv[l];
     const LevelView<T, S>& C = a.lv[l + 1];
     if (a.nu2 == 0) {
@@ -1374,6 +1385,112 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
     if (!grid_barrier(st, a.spins)) return;
     sweep_batched<4>(t0, nt, g.Nh, a.x0, [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 0, 0, q); });
     if (sw + 1 < a.nu2 && !grid_barrier(st, a.spins)) return;
+  }
+}
+
+// ---- the coarse levels (1 .. coarsest) in one thread-block cluster
+// Hardware barrier of all threads of the cluster, with release / acquire
+// semantics at cluster scope: every global-memory write of the cluster's
+// thread blocks before it is visible to their reads after it (those reads
+// also go through L2, ldv<true>).  It is not a spin on a flag: every thread
+// of the cluster reaches every barrier (the control flow is uniform).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The levels below level 0 of one V-cycle, launched as a single cluster of
+// up to 16 blocks (one per SM) after the level-0 down leg has restricted
+// onto level 1: pre-smoothing and restriction of the multi-block levels,
+// the tail V-cycle (levels of at most kTailCells cells) in the first block,
+// in shared memory when it fits, then post-smoothing back up to level 1.
+// The same sweeps as the down and up legs, with a cluster barrier (a few
+// hundred nanoseconds) where they need a grid-wide one (several
+// microseconds), on the L2-resident coarse data.
+template <typename T, typename S>
+__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_coarse(CycleArgs<T, S> a, TailArgs<T, S> ta, int tail_smem,
+                                                               const DevState* st) {
+  if (st->done) return;  // uniform: every block reads the same flag
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  for (int l = 1; l < a.tail_from; ++l) {
+    const LevelView<T, S>& L = a.lv[l];
+    for (int sw = 0; sw < a.nu1; ++sw)
+      for (int color = 0; color < 2; ++color) {
+        if (sw == 0 && color == 0) continue;  // done with the restriction
+        for (int64_t c = t0; c < L.d.n; c += nt) gs_cell<true>(L, c, color, 0);
+        cluster_sync_all();
+      }
+    if (a.nu1 == 0) {
+      for (int64_t c = t0; c < L.d.n; c += nt) L.x[c] = T(0);
+      cluster_sync_all();
+    }
+    const LevelView<T, S>& C = a.lv[l + 1];
+    const bool fold = a.nu1 > 0 && l + 1 < a.tail_from;
+    for (int64_t I = t0; I < C.d.n; I += nt) {
+      const T fI = restrict_cell<true>(L, C.d, I, a.nu1 > 0);
+      C.f[I] = fI;
+      if (fold && red_cell(C.d, I)) C.x[I] = fI / C.cc(kDiag, I);
+    }
+    cluster_sync_all();
+  }
+  if (blockIdx.x == 0) {
+    if (tail_smem) {
+      __shared__ uint32_t off[73];
+      if (threadIdx.x == 0) {
+        uint32_t o = 0;
+        for (int l = ta.first; l <= ta.last; ++l) {
+          const uint32_t n = (uint32_t)ta.lv[l].d.n;
+          off[3 * l] = o;
+          o += (uint32_t)align16(7 * n * sizeof(S));
+          off[3 * l + 1] = o;
+          o += (uint32_t)align16(n * sizeof(T));
+          off[3 * l + 2] = o;
+          o += (uint32_t)align16(n * sizeof(T));
+        }
+        off[72] = o;
+      }
+      __syncthreads();
+      const TailSharedViews<T, S> vw{&ta, off};
+      for (int l = ta.first; l <= ta.last; ++l) {
+        const int64_t n = ta.lv[l].d.n;
+        S* c = const_cast<S*>(vw.lv(l).c);
+        const S* src = ta.lv[l].c;
+#pragma unroll 8
+        for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = src[i];
+      }
+      {
+        const int64_t n = ta.lv[ta.first].d.n;
+        T* f = vw.lv(ta.first).f;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = ldv<true>(ta.lv[ta.first].f + i);
+        const int64_t nc = ta.lv[ta.last].d.n;
+        S* inv = const_cast<S*>(vw.inv());
+#pragma unroll 8
+        for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = ta.inv[i];
+      }
+      __syncthreads();
+      tail_cycle(ta, vw);
+      const int64_t n = ta.lv[ta.first].d.n;
+      const T* x = vw.lv(ta.first).x;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ta.lv[ta.first].x[i] = x[i];
+    } else {
+      tail_cycle(ta, TailGlobalViews<T, S>{&ta});
+    }
+  }
+  cluster_sync_all();
+  for (int l = a.tail_from - 1; l >= 1; --l) {
+    const LevelView<T, S>& L = a.lv[l];
+    const LevelView<T, S>& C = a.lv[l + 1];
+    if (a.nu2 == 0) {
+      for (int64_t c = t0; c < L.d.n; c += nt) prolong_cell<true>(L, C, c, a.s);
+      cluster_sync_all();
+    }
+    for (int sw = 0; sw < a.nu2; ++sw)
+      for (int color = 1; color >= 0; --color) {
+        for (int64_t c = t0; c < L.d.n; c += nt) {
+          if (sw == 0 && color == 1) gs_cell_prolong<true>(L, C, c, a.s);
+          else gs_cell<true>(L, c, color, 0);
+        }
+        cluster_sync_all();
+      }
   }
 }
 
@@ -1437,6 +1554,44 @@ LevelView<T, S> view(bo_prec* P, int l) {
 
 LevelDims dims_of(const Level& L) { return LevelDims{L.nx, L.ny, L.nz, L.n}; }
 
+// Blocks of the cluster that runs the coarse AMG levels: 16 (a
+// non-portable cluster size) where the device can co-schedule them with
+// the tail's shared memory, else 8, else 0 (no cluster form).  Queried once
+// per instantiation.
+template <typename T, typename S>
+int coarse_cluster_size() {
+  static std::atomic<int> cached{-1};
+  int cs = cached.load();
+  if (cs >= 0) return cs;
+  cs = 0;
+  const void* k = (const void*)k_amg_coarse<T, S>;
+  if (cudaFuncSetAttribute(k_amg_coarse<T, S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(k_amg_coarse<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax) ==
+          cudaSuccess) {
+    for (int c : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(c, 1, 1);
+      cfg.blockDim = dim3(kCoopThreads, 1, 1);
+      cfg.dynamicSmemBytes = kTailSmemMax;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n >= 1) {
+        cs = c;
+        break;
+      }
+    }
+  }
+  cudaGetLastError();
+  cached.store(cs);
+  return cs;
+}
+
 template <typename T, typename S>
 void amg_vcycle(bo_prec* P, const DevState* st) {
   cudaStream_t s = P->stream;
@@ -1452,53 +1607,31 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   }
   const int ghalf = grid_for(g.Nh);
   const int last = P->nlev - 1;
-  // The multi-block levels as two cooperative launches (down leg, up leg)
-  // with grid barriers between half sweeps; inside stream capture, or if a
-  // cooperative launch is refused, one kernel per half sweep instead.
+  // Launch forms (all compute the same V-cycle):
+  //  mode 2: level 0 in two cooperative launches (down leg, up leg, grid
+  //          barriers between half sweeps) around one cluster launch for
+  //          every coarser level (cluster barriers);
+  //  mode 1: the cooperative legs also smooth the multi-block natural
+  //          levels, the tail levels in one block;
+  //  mode 0, or inside stream capture, or when a launch form is refused:
+  //          one kernel per half sweep, restriction and prolongation.
+  const int mode = g_amg_coop.load();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool coop = mode != 0 && cap == cudaStreamCaptureStatusNone;
+  const int cs = (coop && mode == 2) ? coarse_cluster_size<T, S>() : 0;
   CycleArgs<T, S> ca;
   ca.g = g;
   ca.At = At;
   ca.f0 = f0;
   ca.x0 = x0;
   ca.tail_from = P->tail_from;
+  ca.legs_to = cs ? 1 : P->tail_from;
   ca.nu1 = nu1;
   ca.nu2 = nu2;
   ca.s = sc;
   ca.spins = g_amg_spins.load();
   for (int l = 1; l <= last; ++l) ca.lv[l] = view<T, S>(P, l);
-  DevState* stw = const_cast<DevState*>(st);
-  void* cargs[] = {&ca, &stw};
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cap);
-  const bool coop = g_amg_coop.load() != 0 && cap == cudaStreamCaptureStatusNone;
-  bool down_done = false;
-  if (coop) {
-    const int gd = occ_grid((const void*)k_amg_down<T, S>, g.Nh, kCoopThreads);
-    down_done =
-        cudaLaunchCooperativeKernel((const void*)k_amg_down<T, S>, gd, kCoopThreads, cargs, 0, s) == cudaSuccess;
-    if (down_done) note_launch();
-    else cudaGetLastError();
-  }
-  if (!down_done) {
-  for (int sw = 0; sw < nu1; ++sw) {
-    (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
-    (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
-  }
-  if (nu1 == 0) (k_zero<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, x0, st), note_launch());
-  (k_restrict0<T, S><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (T*)P->lev[1].f,
-                                                             nu1 > 0, st), note_launch());
-  // multi-block natural levels down to the tail
-  for (int l = 1; l < P->tail_from; ++l) {
-    LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
-    const int gl = grid_for(L.d.n);
-    for (int sw = 0; sw < nu1; ++sw) {
-      (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, sw == 0, st), note_launch());
-      (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
-    }
-    if (nu1 == 0) (k_zero<T><<<gl, kThreads, 0, s>>>(L.d.n, L.x, st), note_launch());
-    (k_restrictn<T, S><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
-  }
-  }
   TailArgs<T, S> ta;
   ta.first = P->tail_from;
   ta.last = last;
@@ -1508,29 +1641,99 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   for (int l = 1; l <= last; ++l) ta.lv[l] = view<T, S>(P, l);
   ta.inv = (const S*)P->coarse_inv;
   const size_t tb = tail_smem_bytes(ta);
-  if (tb <= kTailSmemMax) {
-    cudaFuncSetAttribute(k_tail_smem<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);
-    (k_tail_smem<T, S><<<1, kTailThreads, tb, s>>>(ta, st), note_launch());
-  } else {
-    (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
-  }
+  DevState* stw = const_cast<DevState*>(st);
+  void* cargs[] = {&ca, &stw};
+
+  // per-kernel pre- and post-smoothing of the multi-block natural levels
+  auto natural_down = [&]() {
+    for (int l = 1; l < P->tail_from; ++l) {
+      LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
+      const int gl = grid_for(L.d.n);
+      for (int sw = 0; sw < nu1; ++sw) {
+        (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, sw == 0, st), note_launch());
+        (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+      }
+      if (nu1 == 0) (k_zero<T><<<gl, kThreads, 0, s>>>(L.d.n, L.x, st), note_launch());
+      (k_restrictn<T, S><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
+    }
+  };
+  auto natural_up = [&]() {
+    for (int l = P->tail_from - 1; l >= 1; --l) {
+      LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
+      const int gl = grid_for(L.d.n);
+      if (nu2 == 0) (k_prolongn<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+      for (int sw = 0; sw < nu2; ++sw) {
+        if (sw == 0) (k_gsn_prolong<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+        else (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+        (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
+      }
+    }
+  };
+  auto tail = [&]() {
+    if (tb <= kTailSmemMax) {
+      cudaFuncSetAttribute(k_tail_smem<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);
+      (k_tail_smem<T, S><<<1, kTailThreads, tb, s>>>(ta, st), note_launch());
+    } else {
+      (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+    }
+  };
+
+  // down leg
+  bool down_done = false;
   if (coop) {
+    const int gd = occ_grid((const void*)k_amg_down<T, S>, g.Nh, kCoopThreads);
+    down_done =
+        cudaLaunchCooperativeKernel((const void*)k_amg_down<T, S>, gd, kCoopThreads, cargs, 0, s) == cudaSuccess;
+    if (down_done) note_launch();
+    else cudaGetLastError();
+  }
+  if (!down_done) {
+    for (int sw = 0; sw < nu1; ++sw) {
+      (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
+      (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+    }
+    if (nu1 == 0) (k_zero<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, x0, st), note_launch());
+    (k_restrict0<T, S><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]),
+                                                               (T*)P->lev[1].f, nu1 > 0, st), note_launch());
+    natural_down();
+    tail();
+  } else if (cs > 0) {
+    // every coarser level in one cluster launch (or per kernel if refused)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(kCoopThreads, 1, 1);
+    cfg.dynamicSmemBytes = tb <= kTailSmemMax ? tb : 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_amg_coarse<T, S>, ca, ta, tb <= kTailSmemMax ? 1 : 0, st) == cudaSuccess) {
+      note_launch();
+    } else {
+      cudaGetLastError();
+      natural_down();
+      tail();
+      natural_up();
+    }
+  } else {
+    tail();
+  }
+
+  // up leg
+  if (down_done) {
     const int gu = occ_grid((const void*)k_amg_up<T, S>, g.Nh, kCoopThreads);
     if (cudaLaunchCooperativeKernel((const void*)k_amg_up<T, S>, gu, kCoopThreads, cargs, 0, s) == cudaSuccess) {
       note_launch();
       return;
     }
     cudaGetLastError();
-  }
-  for (int l = P->tail_from - 1; l >= 1; --l) {
-    LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
-    const int gl = grid_for(L.d.n);
-    if (nu2 == 0) (k_prolongn<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
-    for (int sw = 0; sw < nu2; ++sw) {
-      if (sw == 0) (k_gsn_prolong<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
-      else (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
-      (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
-    }
+    if (cs == 0) natural_up();
+  } else {
+    natural_up();
   }
   if (nu2 == 0)
     (k_prolong0<T><<<grid_for(g.N), kThreads, 0, s>>>(g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),

@@ -287,12 +287,14 @@ def test_arnoldi_product_fp64_fallback_matches_oracle_elementwise(bo, ctx):
     assert np.all(np.abs(y.cpu().numpy() - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x) + 1e-300)
 
 
-@pytest.fixture(params=[1, 0], ids=["cooperative", "per_kernel"])
+@pytest.fixture(params=[2, 1, 0], ids=["cluster", "cooperative", "per_kernel"])
 def amg_launch(bo, request):
-    # both launch forms of the AMG's multi-block levels compute the same V-cycle
+    # every launch form of the AMG V-cycle computes the same cycle: level 0
+    # cooperative with the coarse levels in one cluster (the default), the
+    # cooperative legs over all multi-block levels, one kernel per sweep
     bo.bo_set_amg_cooperative(request.param)
     yield request.param
-    bo.bo_set_amg_cooperative(1)
+    bo.bo_set_amg_cooperative(2)
 
 
 @pytest.mark.parametrize("nu1,nu2,s", [(1, 1, 1.0), (2, 2, 1.3), (1, 0, 1.0), (0, 2, 1.5), (3, 1, 1.7)])

@@ -25,7 +25,8 @@ def bo():
     return m
 
 
-def test_amg_barrier_timeout_is_reported_and_recoverable(bo):
+@pytest.mark.parametrize("mode", [2, 1])
+def test_amg_barrier_timeout_is_reported_and_recoverable(bo, mode):
     # 64 x 64 x 32: level 0 spans 64 cooperative blocks, so barriers wait
     dims = (64, 64, 32)
     a = bogen.assemble(bogen.waterflood_case(*dims, seed=5, day=0, corr=(8, 8, 2)))
@@ -33,7 +34,7 @@ def test_amg_barrier_timeout_is_reported_and_recoverable(bo):
     ctx = bo.Context(0)
     A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), a["rowptr"], a["col"], a["val"])
     b = torch.tensor(a["b"], dtype=torch.float64, device="cuda")
-    bo.bo_set_amg_cooperative(1)
+    bo.bo_set_amg_cooperative(mode)
     for precision in (bo.BO_PREC_FP64, bo.BO_PREC_FP32):
         P = bo.Preconditioner(A, precision=precision)
         x = torch.zeros_like(b)
@@ -50,4 +51,5 @@ def test_amg_barrier_timeout_is_reported_and_recoverable(bo):
         assert info["status"] == bo.BO_OK
         assert oracle.rel_residual(Ao, a["b"], x.cpu().numpy()) <= 1e-8
         P.close()
+    bo.bo_set_amg_cooperative(2)
     assert np.isfinite(float(b.norm()))
