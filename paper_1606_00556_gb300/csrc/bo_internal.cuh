@@ -216,6 +216,9 @@ __device__ __forceinline__ df df_fma_acc(df acc, df a, df b) {
   return df{s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, pe))};
 }
 __device__ __forceinline__ df df_norm(df a) { return df_fast_two_sum(a.hi, a.lo); }
+// the same with no assumption on the magnitudes (after a sum whose high
+// parts cancelled below the accumulated low parts)
+__device__ __forceinline__ df df_renorm(df a) { return df_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ df df_from(double v) {
   const float h = __double2float_rn(v);
   return df{h, __double2float_rn(v - (double)h)};
@@ -428,8 +431,8 @@ struct bo_prec {
   void* f0;                // N level-0 AMG right-hand side
   // Krylov workspace (FP64 unless noted)
   int mcap;                // restart length the workspace was sized for
-  double* V;               // (mcap+1) 3N basis
-  float* Vs;               // (mcap+1) 3N FP32 shadow of the basis (first Gram-Schmidt pass)
+  double* V;               // (mcap+1) 3N basis as split pairs (FGMRES; 8 bytes per entry), FP64 scratch otherwise
+  float* Vs;               // unused (kept NULL)
   double* Z;               // mcap 3N preconditioned vectors as split pairs: per vector a hi plane, then a lo plane
   double* H;               // (mcap+1) mcap
   double* cs;
@@ -490,6 +493,8 @@ void prec_free(bo_prec* P);
 void launch_cpr(bo_prec* P, const double* v, double* z, int stage, const DevState* st, const double* vs = nullptr);
 // the CPR stage with its output as split pairs (FP64 basis vector in, preconditioned vector out)
 void launch_cpr_split(bo_prec* P, const double* v, float* z, const DevState* st, const double* vs);
+// the same with a split-pair input vector (an FGMRES basis vector)
+void launch_cpr_split_in(bo_prec* P, const float* v, float* z, const DevState* st, const double* vs);
 // A2 = split copy of A, flagging values outside FP32's normal range
 void launch_split_matrix(bo_mat* m, cudaStream_t s);
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  // FP64 values of At rebuilt on the fly

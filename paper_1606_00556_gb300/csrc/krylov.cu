@@ -10,21 +10,27 @@
 //
 // Orthogonalisation: classical Gram-Schmidt applied twice (CGS2) for every
 // column: a multi-dot pass h1 = V^T w, an update pass w -= V h1, then the
-// same again, the second update also reducing ||w||^2 exactly and applying
-// the Givens step.  A second pass is necessary here: with a strong CPR
+// same again, the second update also reducing ||w||^2 and applying the
+// Givens step.  A second pass is necessary here: with a strong CPR
 // preconditioner A M^{-1} is close to the identity, so the new direction
 // cancels to 1e-6 of ||w|| and one classical pass alone loses all
 // orthogonality.  The basis vectors are stored unnormalised with their
 // scale 1/||v|| kept on the device; every reader applies it, so no pass is
-// spent normalising.  On GB300 these passes are bound jointly by FP64
-// arithmetic and HBM (one FMA per 8 bytes read).
+// spent normalising.
 //
-// The first coefficient pass reads an FP32 shadow of the basis (each basis
-// vector's leading 24 bits, written beside it) and sums in FP32: CGS2's
-// second pass, in FP64, removes whatever the first left in span(V), and the
-// FP64 updates subtract exactly the coefficients they are given, so the
-// Arnoldi relation A z_j = V h_j holds to FP64 rounding whatever the first
-// pass's error.  That takes a quarter of the FP64 work out of each column.
+// The basis is stored as split pairs (per vector a plane of high floats,
+// then a plane of low floats: 48 significant bits, the same 8 bytes per
+// entry as FP64), and the second coefficient pass and both updates compute
+// in split arithmetic (df below): GB300 issues about 64 times more FP32
+// than FP64 operations per clock, so these passes are bound by HBM instead
+// of by the FP64 pipe (in FP64 they ran at 51-67% of HBM).  A split
+// multiply-add keeps about 2^-46 of each term, so the Arnoldi relation
+// A z_j = V h_j + w holds to about 1e-14 and the twice-orthogonalised
+// vector is orthogonal to V to that level: far below the 1e-8 residual
+// target, which is decided on the FP64 true residual.  The first
+// coefficient pass reads only the high plane and sums in FP32: the second
+// pass removes whatever it left in span(V), and the updates subtract
+// exactly the coefficients they are given.
 //
 // The Arnoldi product w = A z_j reads a split copy of A (each value as an
 // unevaluated sum hi + lo of two floats, 48 significant bits; see df in
@@ -63,13 +69,15 @@ __device__ __forceinline__ df dfma3(df acc, float2 a0, df x0, float2 a1, df x1, 
   return df_fma_acc(acc, df{a2.x, a2.y}, x2);
 }
 
-// w = A z on internal vectors: z split pairs (planes of n = 3N), w FP64.
-// A2 is the split copy of A; where it could not hold every value (*range)
-// the product is formed in FP64 from A instead.
+// w = A z on internal vectors: z split pairs (planes of n = 3N); w split
+// pairs (W = float: an FGMRES basis vector) or FP64 (W = double: the
+// BiCGSTAB recurrences).  A2 is the split copy of A; where it could not
+// hold every value (*range) the product is formed in FP64 from A instead.
+template <typename W>
 __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2* __restrict__ A2,
                                                           const double* __restrict__ A, const int* __restrict__ range,
-                                                          const float* __restrict__ z, double* __restrict__ w,
-                                                          float* __restrict__ ws, const DevState* st) {
+                                                          const float* __restrict__ z, W* __restrict__ w,
+                                                          const DevState* st) {
   if (st->done) return;
   const int64_t n = 3 * g.N;
   const bool fp64 = *range != 0;
@@ -78,8 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
     const int64_t q = t - color * g.Nh;
     const Cell c = decode(g, color, q);
     const size_t P = (size_t)g.Nh;
-    double r0, r1, r2;
-    float h0, h1, h2;  // FP32 shadow of w for the first Gram-Schmidt pass
+    df n0, n1, n2;
     if (!fp64) {
       df a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f};
 #pragma unroll
@@ -94,13 +101,9 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
         a1 = dfma3(a1, __ldcs(a + 96), x0, __ldcs(a + 128), x1, __ldcs(a + 160), x2);
         a2 = dfma3(a2, __ldcs(a + 192), x0, __ldcs(a + 224), x1, __ldcs(a + 256), x2);
       }
-      const df n0 = df_norm(a0), n1 = df_norm(a1), n2 = df_norm(a2);
-      r0 = df_to_double(n0);
-      r1 = df_to_double(n1);
-      r2 = df_to_double(n2);
-      h0 = n0.hi;
-      h1 = n1.hi;
-      h2 = n2.hi;
+      n0 = df_renorm(a0);
+      n1 = df_renorm(a1);
+      n2 = df_renorm(a2);
     } else {
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int sl = 0; sl < 7; ++sl) {
@@ -115,19 +118,28 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
         a1 = fma3(a1, a[3 * P], x0, a[4 * P], x1, a[5 * P], x2);
         a2 = fma3(a2, a[6 * P], x0, a[7 * P], x1, a[8 * P], x2);
       }
-      r0 = a0;
-      r1 = a1;
-      r2 = a2;
-      h0 = (float)a0;
-      h1 = (float)a1;
-      h2 = (float)a2;
+      if constexpr (sizeof(W) == 8) {
+        w[t] = a0;
+        w[g.N + t] = a1;
+        w[2 * g.N + t] = a2;
+        continue;
+      }
+      n0 = df_from(a0);
+      n1 = df_from(a1);
+      n2 = df_from(a2);
     }
-    w[t] = r0;
-    w[g.N + t] = r1;
-    w[2 * g.N + t] = r2;
-    ws[t] = h0;
-    ws[g.N + t] = h1;
-    ws[2 * g.N + t] = h2;
+    if constexpr (sizeof(W) == 4) {
+      w[t] = n0.hi;
+      w[g.N + t] = n1.hi;
+      w[2 * g.N + t] = n2.hi;
+      w[n + t] = n0.lo;
+      w[n + g.N + t] = n1.lo;
+      w[n + 2 * g.N + t] = n2.lo;
+    } else {
+      w[t] = df_to_double(n0);
+      w[g.N + t] = df_to_double(n1);
+      w[2 * g.N + t] = df_to_double(n2);
+    }
   }
 }
 
@@ -219,14 +231,13 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
   }
 }
 
-// v = src / beta, and its FP32 shadow
-__global__ void k_scale_beta(int64_t n, const double* __restrict__ src, double* __restrict__ v,
-                             float* __restrict__ vs, const DevState* st) {
+// v = src / beta as split pairs (high plane, then low plane)
+__global__ void k_scale_beta(int64_t n, const double* __restrict__ src, float* __restrict__ v, const DevState* st) {
   const double s = st->beta > 0.0 ? 1.0 / st->beta : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double t = src[i] * s;
-    v[i] = t;
-    vs[i] = df_hi_bits(t);
+    const df t = df_from(src[i] * s);
+    v[i] = t.hi;
+    v[n + i] = t.lo;
   }
 }
 
@@ -273,16 +284,13 @@ struct ArnoldiArgs {
   double* hist;
 };
 
-// Gram-Schmidt coefficient pass: h[off + u] = vscale[u] <V_u, w> for u <= j.
-// Grid (chunks, j + 1): block (c, u) sums column u over chunk c (products
-// and the per-thread sum in R, the block sum in FP64); the block that
-// finishes last reduces each column's partials with one warp per column.
-// R = float: the first pass, on the FP32 shadows of V and w (ldv floats
-// apart); R = double: the second pass, on V and w in FP64.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const R* __restrict__ V, int64_t ldv,
-                                                     const R* __restrict__ w, double* partials, DevState* st,
-                                                     int off) {
+// First Gram-Schmidt coefficient pass: h[u] = vscale[u] <V_u, w> for u <=
+// j on the high planes only (FP32 products and per-thread sums).  Grid
+// (chunks, j + 1): block (c, u) sums column u over chunk c; the block that
+// finishes last reduces each column's partials (FP64) with one warp per
+// column.  V: the basis (vectors ldv floats apart), w: the new vector.
+__global__ void __launch_bounds__(kThreads) k_gs_dots32(int64_t n, const float* __restrict__ V, int64_t ldv,
+                                                       const float* __restrict__ w, double* partials, DevState* st) {
   __shared__ double sh[32];
   if (st->done) return;
   const int nv = gridDim.y;
@@ -291,9 +299,9 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const R* __rest
   const int64_t len = (n + nchunk - 1) / nchunk;
   const int64_t i0 = blockIdx.x * len;
   const int64_t i1 = min(n, i0 + len);
-  const R* a = V + (size_t)u * ldv;
-  R acc = R(0);
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fma(a[i], w[i], acc);
+  const float* a = V + (size_t)u * ldv;
+  float acc = 0.f;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fmaf(a[i], w[i], acc);
   const double sum = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
   if (!last_block(&st->counter[0], nchunk * nv)) return;
@@ -302,34 +310,70 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const R* __rest
     double t = 0.0;
     for (int b = lane; b < nchunk; b += 32) t += __ldcg(partials + (size_t)r * nchunk + b);
     t = warp_sum(t);
-    if (lane == 0) st->h[off + r] = t * st->vscale[r];
+    if (lane == 0) st->h[r] = t * st->vscale[r];
   }
   if (threadIdx.x == 0) st->counter[0] = 0;
 }
 
-// Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u.  In the
-// final pass (LAST) ||w||^2 is reduced exactly and the last block applies
-// the Givens step to h1 + h2 and stores 1/||w|| as the new column's scale
-// (w itself stays unnormalised).
+// Second coefficient pass: h[kMaxM + u] = vscale[u] <V_u, w> in split
+// arithmetic (each thread's products and sum as split pairs, the block and
+// chunk sums in FP64), same grid and reduction as the first.
+__global__ void __launch_bounds__(kThreads) k_gs_dots_df(int64_t n, const float* __restrict__ V, int64_t ldv,
+                                                        const float* __restrict__ w, double* partials, DevState* st) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  const int nv = gridDim.y;
+  const int nchunk = gridDim.x;
+  const int u = blockIdx.y;
+  const int64_t len = (n + nchunk - 1) / nchunk;
+  const int64_t i0 = blockIdx.x * len;
+  const int64_t i1 = min(n, i0 + len);
+  const float* a = V + (size_t)u * ldv;
+  df acc{0.f, 0.f};
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    acc = df_fma_acc(acc, df{a[i], a[n + i]}, df{w[i], w[n + i]});
+  const double sum = block_sum(df_to_double(df_renorm(acc)), sh);
+  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
+  if (!last_block(&st->counter[0], nchunk * nv)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < nv; r += kThreads / 32) {
+    double t = 0.0;
+    for (int b = lane; b < nchunk; b += 32) t += __ldcg(partials + (size_t)r * nchunk + b);
+    t = warp_sum(t);
+    if (lane == 0) st->h[kMaxM + r] = t * st->vscale[r];
+  }
+  if (threadIdx.x == 0) st->counter[0] = 0;
+}
+
+// Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
+// arithmetic (the coefficients rounded to split pairs once per block, each
+// entry's sum carried as a split pair and renormalised once).  In the final
+// pass (LAST) ||w||^2 is reduced in FP64 and the last block applies the
+// Givens step to h1 + h2 and stores 1/||w|| as the new column's scale (w
+// itself stays unnormalised).
 template <bool LAST>
-__global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const double* __restrict__ V, int64_t ldv,
-                                                       double* __restrict__ w, float* __restrict__ ws,
-                                                       double* partials, DevState* st, ArnoldiArgs aa) {
-  __shared__ double c[kMaxM + 1];
+__global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* __restrict__ V, int64_t ldv,
+                                                       float* __restrict__ w, double* partials, DevState* st,
+                                                       ArnoldiArgs aa) {
+  __shared__ df c[kMaxM + 1];
   __shared__ double sh[32];
   if (st->done) return;
   const int nv = aa.j + 1;
   const int off = LAST ? kMaxM : 0;
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = st->h[off + k] * st->vscale[k];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[off + k] * st->vscale[k]));
   __syncthreads();
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = w[i];
-    for (int k = 0; k < nv; ++k) s -= c[k] * V[(size_t)k * ldv + i];
-    w[i] = s;
+    df s{w[i], w[n + i]};
+    const float* a = V + i;
+#pragma unroll 4
+    for (int k = 0; k < nv; ++k) s = df_fma_acc(s, c[k], df{a[(size_t)k * ldv], a[(size_t)k * ldv + n]});
+    s = df_renorm(s);
+    w[i] = s.hi;
+    w[n + i] = s.lo;
     if (LAST) {
-      acc += s * s;
-      ws[i] = df_hi_bits(s);  // the new basis vector's FP32 shadow (integer operations)
+      const double d = df_to_double(s);
+      acc = fma(d, d, acc);
     }
   }
   if (!LAST) return;
@@ -423,8 +467,8 @@ int krylov_alloc(bo_prec* P, int m) {
     if (ok && cudaMalloc(&p, bytes) != cudaSuccess) { ok = false; return nullptr; }
     return p;
   };
-  P->V = (double*)al((size_t)(m + 1) * n * sizeof(double));
-  P->Vs = (float*)al((size_t)(m + 1) * n * sizeof(float));
+  P->V = (double*)al((size_t)(m + 1) * n * sizeof(double));  // split pairs (FGMRES) or FP64 (BiCGSTAB)
+  P->Vs = nullptr;
   P->Z = (double*)al((size_t)m * n * sizeof(double));
   P->H = (double*)al((size_t)(m + 1) * m * sizeof(double));
   P->cs = (double*)al((size_t)m * sizeof(double));
@@ -532,7 +576,7 @@ struct Job {
   void start_cycle() {
     cudaStream_t s = stream();
     (k_cycle_start<<<1, 64, 0, s>>>(P->st, P->gvec, o.restart), note_launch());
-    (k_scale_beta<<<grid_for(n()), kThreads, 0, s>>>(n(), P->rk, P->V, P->Vs, P->st), note_launch());
+    (k_scale_beta<<<grid_for(n()), kThreads, 0, s>>>(n(), P->rk, (float*)P->V, P->st), note_launch());
     j_enq = j_polled = 0;
     cycle_stop = false;
     phase = kColumns;
@@ -542,23 +586,23 @@ struct Job {
   void enqueue_column_kernels(int j, bool timed) {
     cudaStream_t s = stream();
     const Geom& g = geom();
-    const int64_t nn = n(), ldv = nn;
+    const int64_t nn = n(), ldv = 2 * nn;  // basis vectors as split pairs: 2n floats apart
     const int m = o.restart;
     DevState* st = P->st;
-    double* vj = P->V + (size_t)j * ldv;
-    double* w = P->V + (size_t)(j + 1) * ldv;
+    float* V = (float*)P->V;
+    const float* vj = V + (size_t)j * ldv;
+    float* w = V + (size_t)(j + 1) * ldv;
     float* zj = (float*)P->Z + (size_t)j * 2 * nn;  // split pairs: hi plane, lo plane
     double* dhist = P->partials + (P->npartials - kHistCap);
-    launch_cpr_split(P, vj, zj, st, &st->vscale[j]);
+    launch_cpr_split_in(P, vj, zj, st, &st->vscale[j]);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed && prof.size() < 512) {
       e0 = P->prof_ev[2 * prof.size()];
       e1 = P->prof_ev[2 * prof.size() + 1];
       cudaEventRecord(e0, s);
     }
-    float* ws = P->Vs + (size_t)(j + 1) * ldv;
-    (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(
-         g, P->mat->A2, P->mat->A, P->mat->a2_range, zj, w, ws, st),
+    (k_arnoldi_spmv<float><<<occ_grid((const void*)k_arnoldi_spmv<float>, g.N), kThreads, 0, s>>>(
+         g, P->mat->A2, P->mat->A, P->mat->a2_range, zj, w, st),
      note_launch());
     if (e1) {
       cudaEventRecord(e1, s);
@@ -568,10 +612,10 @@ struct Job {
     const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
     const dim3 gd(gs_chunks(nn), nv);
-    (k_gs_dots<float><<<gd, kThreads, 0, s>>>(nn, P->Vs, ldv, ws, P->partials, st, 0), note_launch());
-    (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, ws, P->partials, st, aa), note_launch());
-    (k_gs_dots<double><<<gd, kThreads, 0, s>>>(nn, P->V, ldv, w, P->partials, st, kMaxM), note_launch());
-    (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, P->V, ldv, w, ws, P->partials, st, aa), note_launch());
+    (k_gs_dots32<<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+    (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
+    (k_gs_dots_df<<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+    (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
 
   // Column j's kernels captured once into a CUDA graph (on a private stream,
@@ -771,10 +815,16 @@ __global__ void k_split_vec(int64_t n, const double* __restrict__ v, float* __re
     z[n + i] = p.y;
   }
 }
+// w = hi + lo (exact in FP64)
+__global__ void k_join_vec(int64_t n, const float* __restrict__ z, double* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = (double)z[i] + (double)z[n + i];
+}
 }  // namespace
 
 // w = A v on internal vectors by the solver's own Arnoldi product: v split
-// into pairs, the kernel every FGMRES iteration runs, w in FP64
+// into pairs, the kernel every FGMRES iteration runs, its split result
+// joined exactly into FP64 w
 void launch_arnoldi_product(bo_prec* P, const double* v, double* w) {
   cudaStream_t s = P->stream;
   bo_mat* m = P->mat;
@@ -782,10 +832,12 @@ void launch_arnoldi_product(bo_prec* P, const double* v, double* w) {
   const int64_t n = 3 * g.N;
   if (!m->a2_valid) launch_split_matrix(m, s);
   float* z = (float*)P->Z;  // the first preconditioned vector's split planes as scratch
+  float* ws = (float*)P->V;  // the first basis vector's split planes as scratch
   (k_split_vec<<<grid_for(n), kThreads, 0, s>>>(n, v, z), note_launch());
-  (k_arnoldi_spmv<<<occ_grid((const void*)k_arnoldi_spmv, g.N), kThreads, 0, s>>>(g, m->A2, m->A, m->a2_range, z, w,
-                                                                                    P->Vs, P->st),
+  (k_arnoldi_spmv<float><<<occ_grid((const void*)k_arnoldi_spmv<float>, g.N), kThreads, 0, s>>>(
+       g, m->A2, m->A, m->a2_range, z, ws, P->st),
    note_launch());
+  (k_join_vec<<<grid_for(n), kThreads, 0, s>>>(n, ws, w), note_launch());
 }
 
 int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
@@ -1026,16 +1078,15 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
   double* tv = P->V + 5 * nn;
   float* ph = (float*)P->Z;             // M^{-1} p as split pairs
   float* shs = (float*)P->Z + 2 * nn;   // M^{-1} s as split pairs
-  float* ws = P->Vs;                    // shadow written by the SpMV, unused here
   const int gn = grid_for(nn);
-  const int gs = occ_grid((const void*)k_arnoldi_spmv, g.N);
+  const int gs = occ_grid((const void*)k_arnoldi_spmv<double>, g.N);
   auto enqueue_iteration = [&]() {
     (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, rt, r, nullptr, nullptr, P->partials, st, kBcRho, -1),
      note_launch());
     (k_bc_scalar<0><<<1, 1, 0, s>>>(st), note_launch());
     (k_bc_p<<<gn, kThreads, 0, s>>>(nn, r, p, v, st), note_launch());
     launch_cpr_split(P, p, ph, st, nullptr);
-    (k_arnoldi_spmv<<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, ph, v, ws, st),
+    (k_arnoldi_spmv<double><<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, ph, v, st),
      note_launch());
     (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, rt, v, nullptr, nullptr, P->partials, st, kBcRtv, -1),
      note_launch());
@@ -1043,7 +1094,7 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
     (k_bc_s<<<kRedBlocks, kThreads, 0, s>>>(nn, r, v, sv, P->partials, st), note_launch());
     (k_bc_scalar<2><<<1, 1, 0, s>>>(st), note_launch());
     launch_cpr_split(P, sv, shs, st, nullptr);
-    (k_arnoldi_spmv<<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, shs, tv, ws, st),
+    (k_arnoldi_spmv<double><<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, shs, tv, st),
      note_launch());
     (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, tv, sv, tv, tv, P->partials, st, kBcTs, kBcTt), note_launch());
     (k_bc_scalar<3><<<1, 1, 0, s>>>(st), note_launch());

@@ -1945,6 +1945,15 @@ void launch_cpr_split(bo_prec* P, const double* v, float* z, const DevState* st,
   else cpr_apply<double, double>(P, in, out, BO_STAGE_CPR, st, vs);
 }
 
+void launch_cpr_split_in(bo_prec* P, const float* v, float* z, const DevState* st, const double* vs) {
+  const int64_t n = 3 * P->mat->g.N;
+  const InV in{nullptr, v, n};
+  const OutV out{nullptr, z, n};
+  if (P->bf16) cpr_apply<float, __nv_bfloat16>(P, in, out, BO_STAGE_CPR, st, vs);
+  else if (P->fp32) cpr_apply<float, float>(P, in, out, BO_STAGE_CPR, st, vs);
+  else cpr_apply<double, double>(P, in, out, BO_STAGE_CPR, st, vs);
+}
+
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {
   const Geom& g = P->mat->g;
   (k_spmv_dec64<<<grid_for(g.N), kThreads, 0, P->stream>>>(g, P->mat->A, P->w, x, y), note_launch());
