@@ -62,6 +62,29 @@ constexpr int kMaxM = 64;
 constexpr int kHistCap = 4096;
 constexpr int kDotBlocks = 2 * 152;  // most chunks of a coefficient pass (partials per column)
 
+// The split basis: vector k at k * ldv floats, ldv = 2 np, its high plane
+// at [0, n) and its low plane at [np, np + n), np = n rounded up to a
+// multiple of 4 so that every plane starts on a 16-byte boundary.  The
+// Gram-Schmidt kernels below read and write four consecutive entries per
+// thread with 16-byte accesses: with 4-byte ones a warp request carries
+// too few bytes to keep enough of them in flight to stream at HBM rate.
+// The last group of four of a plane may reach into the padding: its lanes
+// at or beyond n are neither used nor stored.
+__host__ __device__ __forceinline__ int64_t split_pad(int64_t n) { return (n + 3) & ~(int64_t)3; }
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float lane4(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+// v with the lanes at or beyond `valid` set to zero
+__device__ __forceinline__ float4 mask4(float4 v, int valid) {
+  if (valid < 4) {
+    if (valid < 4) v.w = 0.f;
+    if (valid < 3) v.z = 0.f;
+    if (valid < 2) v.y = 0.f;
+  }
+  return v;
+}
+
 // acc + a0 x0 + a1 x1 + a2 x2 in split arithmetic (low parts collected lazily)
 __device__ __forceinline__ df dfma3(df acc, float2 a0, df x0, float2 a1, df x1, float2 a2, df x2) {
   acc = df_fma_acc(acc, df{a0.x, a0.y}, x0);
@@ -78,6 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
                                                           const double* __restrict__ A, const int* __restrict__ range,
                                                           const float* __restrict__ z, W* __restrict__ w,
                                                           const DevState* st) {
+  const int64_t wlo = split_pad(3 * g.N);  // low plane of a split w (the basis layout)
   if (st->done) return;
   const int64_t n = 3 * g.N;
   const bool fp64 = *range != 0;
@@ -132,9 +156,9 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
       w[t] = n0.hi;
       w[g.N + t] = n1.hi;
       w[2 * g.N + t] = n2.hi;
-      w[n + t] = n0.lo;
-      w[n + g.N + t] = n1.lo;
-      w[n + 2 * g.N + t] = n2.lo;
+      w[wlo + t] = n0.lo;
+      w[wlo + g.N + t] = n1.lo;
+      w[wlo + 2 * g.N + t] = n2.lo;
     } else {
       w[t] = df_to_double(n0);
       w[g.N + t] = df_to_double(n1);
@@ -231,13 +255,14 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
   }
 }
 
-// v = src / beta as split pairs (high plane, then low plane)
+// v = src / beta as split pairs in the basis layout
 __global__ void k_scale_beta(int64_t n, const double* __restrict__ src, float* __restrict__ v, const DevState* st) {
   const double s = st->beta > 0.0 ? 1.0 / st->beta : 0.0;
+  const int64_t np = split_pad(n);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const df t = df_from(src[i] * s);
     v[i] = t.hi;
-    v[n + i] = t.lo;
+    v[np + i] = t.lo;
   }
 }
 
@@ -286,9 +311,9 @@ struct ArnoldiArgs {
 
 // First Gram-Schmidt coefficient pass: h[u] = vscale[u] <V_u, w> for u <=
 // j on the high planes only (FP32 products and per-thread sums).  Grid
-// (chunks, j + 1): block (c, u) sums column u over chunk c; the block that
-// finishes last reduces each column's partials (FP64) with one warp per
-// column.  V: the basis (vectors ldv floats apart), w: the new vector.
+// (chunks, j + 1): block (c, u) sums column u over chunk c of the groups of
+// four entries; the block that finishes last reduces each column's
+// partials (FP64) with one warp per column.
 __global__ void __launch_bounds__(kThreads) k_gs_dots32(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                        const float* __restrict__ w, double* partials, DevState* st) {
   __shared__ double sh[32];
@@ -296,12 +321,17 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots32(int64_t n, const float* 
   const int nv = gridDim.y;
   const int nchunk = gridDim.x;
   const int u = blockIdx.y;
-  const int64_t len = (n + nchunk - 1) / nchunk;
-  const int64_t i0 = blockIdx.x * len;
-  const int64_t i1 = min(n, i0 + len);
+  const int64_t ng = (n + 3) >> 2;
+  const int64_t len = (ng + nchunk - 1) / nchunk;
+  const int64_t g0 = blockIdx.x * len;
+  const int64_t g1 = min(ng, g0 + len);
   const float* a = V + (size_t)u * ldv;
   float acc = 0.f;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fmaf(a[i], w[i], acc);
+  for (int64_t q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
+    const int valid = (int)min((int64_t)4, n - 4 * q);
+    const float4 x = mask4(ld4(a + 4 * q), valid), y = mask4(ld4(w + 4 * q), valid);
+    acc = fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, fmaf(x.x, y.x, acc))));
+  }
   const double sum = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
   if (!last_block(&st->counter[0], nchunk * nv)) return;
@@ -325,13 +355,22 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots_df(int64_t n, const float*
   const int nv = gridDim.y;
   const int nchunk = gridDim.x;
   const int u = blockIdx.y;
-  const int64_t len = (n + nchunk - 1) / nchunk;
-  const int64_t i0 = blockIdx.x * len;
-  const int64_t i1 = min(n, i0 + len);
+  const int64_t np = split_pad(n);
+  const int64_t ng = (n + 3) >> 2;
+  const int64_t len = (ng + nchunk - 1) / nchunk;
+  const int64_t g0 = blockIdx.x * len;
+  const int64_t g1 = min(ng, g0 + len);
   const float* a = V + (size_t)u * ldv;
   df acc{0.f, 0.f};
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-    acc = df_fma_acc(acc, df{a[i], a[n + i]}, df{w[i], w[n + i]});
+  for (int64_t q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
+    const int valid = (int)min((int64_t)4, n - 4 * q);
+    const float4 ah = mask4(ld4(a + 4 * q), valid), al = mask4(ld4(a + np + 4 * q), valid);
+    const float4 wh = mask4(ld4(w + 4 * q), valid), wl = mask4(ld4(w + np + 4 * q), valid);
+    acc = df_fma_acc(acc, df{ah.x, al.x}, df{wh.x, wl.x});
+    acc = df_fma_acc(acc, df{ah.y, al.y}, df{wh.y, wl.y});
+    acc = df_fma_acc(acc, df{ah.z, al.z}, df{wh.z, wl.z});
+    acc = df_fma_acc(acc, df{ah.w, al.w}, df{wh.w, wl.w});
+  }
   const double sum = block_sum(df_to_double(df_renorm(acc)), sh);
   if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
   if (!last_block(&st->counter[0], nchunk * nv)) return;
@@ -347,10 +386,10 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots_df(int64_t n, const float*
 
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
 // arithmetic (the coefficients rounded to split pairs once per block, each
-// entry's sum carried as a split pair and renormalised once).  In the final
-// pass (LAST) ||w||^2 is reduced in FP64 and the last block applies the
-// Givens step to h1 + h2 and stores 1/||w|| as the new column's scale (w
-// itself stays unnormalised).
+// entry's sum carried as a split pair and renormalised once), four entries
+// per thread.  In the final pass (LAST) ||w||^2 is reduced in FP64 and the
+// last block applies the Givens step to h1 + h2 and stores 1/||w|| as the
+// new column's scale (w itself stays unnormalised).
 template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                        float* __restrict__ w, double* partials, DevState* st,
@@ -360,20 +399,43 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
   if (st->done) return;
   const int nv = aa.j + 1;
   const int off = LAST ? kMaxM : 0;
+  const int64_t np = split_pad(n);
+  const int64_t ng = (n + 3) >> 2;
   for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[off + k] * st->vscale[k]));
   __syncthreads();
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    df s{w[i], w[n + i]};
-    const float* a = V + i;
-#pragma unroll 4
-    for (int k = 0; k < nv; ++k) s = df_fma_acc(s, c[k], df{a[(size_t)k * ldv], a[(size_t)k * ldv + n]});
-    s = df_renorm(s);
-    w[i] = s.hi;
-    w[n + i] = s.lo;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ng; q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
+    df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
+    const float* a = V + 4 * q;
+#pragma unroll 2
+    for (int k = 0; k < nv; ++k) {
+      const float4 ah = ld4(a + (size_t)k * ldv), al = ld4(a + (size_t)k * ldv + np);
+      const df ck = c[k];
+      s0 = df_fma_acc(s0, ck, df{ah.x, al.x});
+      s1 = df_fma_acc(s1, ck, df{ah.y, al.y});
+      s2 = df_fma_acc(s2, ck, df{ah.z, al.z});
+      s3 = df_fma_acc(s3, ck, df{ah.w, al.w});
+    }
+    s0 = df_renorm(s0);
+    s1 = df_renorm(s1);
+    s2 = df_renorm(s2);
+    s3 = df_renorm(s3);
+    const int valid = (int)min((int64_t)4, n - 4 * q);
+    if (valid == 4) {
+      st4(w + 4 * q, make_float4(s0.hi, s1.hi, s2.hi, s3.hi));
+      st4(w + np + 4 * q, make_float4(s0.lo, s1.lo, s2.lo, s3.lo));
+    } else {
+      const df sv[4] = {s0, s1, s2, s3};
+      for (int e = 0; e < valid; ++e) {
+        w[4 * q + e] = sv[e].hi;
+        w[np + 4 * q + e] = sv[e].lo;
+      }
+    }
     if (LAST) {
-      const double d = df_to_double(s);
-      acc = fma(d, d, acc);
+      const double d0 = df_to_double(s0), d1 = valid > 1 ? df_to_double(s1) : 0.0,
+                   d2 = valid > 2 ? df_to_double(s2) : 0.0, d3 = valid > 3 ? df_to_double(s3) : 0.0;
+      acc = fma(d3, d3, fma(d2, d2, fma(d1, d1, fma(d0, d0, acc))));
     }
   }
   if (!LAST) return;
@@ -467,7 +529,7 @@ int krylov_alloc(bo_prec* P, int m) {
     if (ok && cudaMalloc(&p, bytes) != cudaSuccess) { ok = false; return nullptr; }
     return p;
   };
-  P->V = (double*)al((size_t)(m + 1) * n * sizeof(double));  // split pairs (FGMRES) or FP64 (BiCGSTAB)
+  P->V = (double*)al((size_t)(m + 1) * split_pad(n) * sizeof(double));  // split pairs (FGMRES) or FP64 (BiCGSTAB)
   P->Vs = nullptr;
   P->Z = (double*)al((size_t)m * n * sizeof(double));
   P->H = (double*)al((size_t)(m + 1) * m * sizeof(double));
@@ -586,7 +648,7 @@ struct Job {
   void enqueue_column_kernels(int j, bool timed) {
     cudaStream_t s = stream();
     const Geom& g = geom();
-    const int64_t nn = n(), ldv = 2 * nn;  // basis vectors as split pairs: 2n floats apart
+    const int64_t nn = n(), ldv = 2 * split_pad(nn);  // basis vectors as split pairs (split_pad)
     const int m = o.restart;
     DevState* st = P->st;
     float* V = (float*)P->V;
@@ -815,10 +877,11 @@ __global__ void k_split_vec(int64_t n, const double* __restrict__ v, float* __re
     z[n + i] = p.y;
   }
 }
-// w = hi + lo (exact in FP64)
+// w = hi + lo (exact in FP64) of a vector in the basis layout
 __global__ void k_join_vec(int64_t n, const float* __restrict__ z, double* __restrict__ w) {
+  const int64_t np = split_pad(n);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    w[i] = (double)z[i] + (double)z[n + i];
+    w[i] = (double)z[i] + (double)z[np + i];
 }
 }  // namespace
 

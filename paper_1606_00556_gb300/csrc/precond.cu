@@ -1947,7 +1947,7 @@ void launch_cpr_split(bo_prec* P, const double* v, float* z, const DevState* st,
 
 void launch_cpr_split_in(bo_prec* P, const float* v, float* z, const DevState* st, const double* vs) {
   const int64_t n = 3 * P->mat->g.N;
-  const InV in{nullptr, v, n};
+  const InV in{nullptr, v, (n + 3) & ~(int64_t)3};  // the basis layout: low plane at n rounded up to 4
   const OutV out{nullptr, z, n};
   if (P->bf16) cpr_apply<float, __nv_bfloat16>(P, in, out, BO_STAGE_CPR, st, vs);
   else if (P->fp32) cpr_apply<float, float>(P, in, out, BO_STAGE_CPR, st, vs);
