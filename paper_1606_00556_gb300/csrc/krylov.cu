@@ -60,7 +60,7 @@ namespace {
 constexpr int kRedBlocks = 4 * 152;  // blocks of single reductions
 constexpr int kMaxM = 64;
 constexpr int kHistCap = 4096;
-constexpr int kDotBlocks = 2 * 152;  // most chunks of a coefficient pass (partials per column)
+constexpr int kDotBlocks = 4 * 152;  // most chunks of a coefficient pass (partials per column)
 
 // The split basis: vector k at k * ldv floats, ldv = 2 np, its high plane
 // at [0, n) and its low plane at [np, np + n), np = n rounded up to a
@@ -309,77 +309,73 @@ struct ArnoldiArgs {
   double* hist;
 };
 
-// First Gram-Schmidt coefficient pass: h[u] = vscale[u] <V_u, w> for u <=
-// j on the high planes only (FP32 products and per-thread sums).  Grid
-// (chunks, j + 1): block (c, u) sums column u over chunk c of the groups of
-// four entries; the block that finishes last reduces each column's
-// partials (FP64) with one warp per column.
-__global__ void __launch_bounds__(kThreads) k_gs_dots32(int64_t n, const float* __restrict__ V, int64_t ldv,
-                                                       const float* __restrict__ w, double* partials, DevState* st) {
-  __shared__ double sh[32];
-  if (st->done) return;
-  const int nv = gridDim.y;
-  const int nchunk = gridDim.x;
-  const int u = blockIdx.y;
-  const int64_t ng = (n + 3) >> 2;
-  const int64_t len = (ng + nchunk - 1) / nchunk;
-  const int64_t g0 = blockIdx.x * len;
-  const int64_t g1 = min(ng, g0 + len);
-  const float* a = V + (size_t)u * ldv;
-  float acc = 0.f;
-  for (int64_t q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
-    const int valid = (int)min((int64_t)4, n - 4 * q);
-    const float4 x = mask4(ld4(a + 4 * q), valid), y = mask4(ld4(w + 4 * q), valid);
-    acc = fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, fmaf(x.x, y.x, acc))));
-  }
-  const double sum = block_sum((double)acc, sh);
-  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
-  if (!last_block(&st->counter[0], nchunk * nv)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < nv; r += kThreads / 32) {
-    double t = 0.0;
-    for (int b = lane; b < nchunk; b += 32) t += __ldcg(partials + (size_t)r * nchunk + b);
-    t = warp_sum(t);
-    if (lane == 0) st->h[r] = t * st->vscale[r];
-  }
-  if (threadIdx.x == 0) st->counter[0] = 0;
-}
+// Gram-Schmidt coefficient passes: h[off + u] = vscale[u] <V_u, w> for
+// u <= j.  Grid (chunks, ceil((j + 1) / kDotU)): block (c, y) sums the
+// columns u = kDotU y .. kDotU y + kDotU - 1 over chunk c of the groups of
+// four entries, so each chunk of w is read once per kDotU columns; the
+// block that finishes last reduces each column's partials (FP64) with one
+// warp per column.
+//   SPLIT = false: the first pass, on the high planes only (FP32 products
+//     and per-thread sums), off = 0;
+//   SPLIT = true: the second pass, in split arithmetic (each thread's
+//     products and sums as split pairs), off = kMaxM.
+// The block and chunk sums are FP64 in both.
+constexpr int kDotU = 8;
 
-// Second coefficient pass: h[kMaxM + u] = vscale[u] <V_u, w> in split
-// arithmetic (each thread's products and sum as split pairs, the block and
-// chunk sums in FP64), same grid and reduction as the first.
-__global__ void __launch_bounds__(kThreads) k_gs_dots_df(int64_t n, const float* __restrict__ V, int64_t ldv,
-                                                        const float* __restrict__ w, double* partials, DevState* st) {
+template <bool SPLIT>
+__global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __restrict__ V, int64_t ldv,
+                                                     const float* __restrict__ w, int nv, double* partials,
+                                                     DevState* st) {
   __shared__ double sh[32];
   if (st->done) return;
-  const int nv = gridDim.y;
   const int nchunk = gridDim.x;
-  const int u = blockIdx.y;
+  const int u0 = blockIdx.y * kDotU;
   const int64_t np = split_pad(n);
   const int64_t ng = (n + 3) >> 2;
   const int64_t len = (ng + nchunk - 1) / nchunk;
   const int64_t g0 = blockIdx.x * len;
   const int64_t g1 = min(ng, g0 + len);
-  const float* a = V + (size_t)u * ldv;
-  df acc{0.f, 0.f};
+  float acc32[kDotU];
+  df acc[kDotU];
+#pragma unroll
+  for (int uu = 0; uu < kDotU; ++uu) {
+    acc32[uu] = 0.f;
+    acc[uu] = df{0.f, 0.f};
+  }
   for (int64_t q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
     const int valid = (int)min((int64_t)4, n - 4 * q);
-    const float4 ah = mask4(ld4(a + 4 * q), valid), al = mask4(ld4(a + np + 4 * q), valid);
-    const float4 wh = mask4(ld4(w + 4 * q), valid), wl = mask4(ld4(w + np + 4 * q), valid);
-    acc = df_fma_acc(acc, df{ah.x, al.x}, df{wh.x, wl.x});
-    acc = df_fma_acc(acc, df{ah.y, al.y}, df{wh.y, wl.y});
-    acc = df_fma_acc(acc, df{ah.z, al.z}, df{wh.z, wl.z});
-    acc = df_fma_acc(acc, df{ah.w, al.w}, df{wh.w, wl.w});
+    const float4 wh = mask4(ld4(w + 4 * q), valid);
+    const float4 wl = SPLIT ? mask4(ld4(w + np + 4 * q), valid) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int uu = 0; uu < kDotU; ++uu) {
+      if (u0 + uu >= nv) break;
+      const float* a = V + (size_t)(u0 + uu) * ldv + 4 * q;
+      const float4 ah = mask4(ld4(a), valid);
+      if (SPLIT) {
+        const float4 al = mask4(ld4(a + np), valid);
+        acc[uu] = df_fma_acc(acc[uu], df{ah.x, al.x}, df{wh.x, wl.x});
+        acc[uu] = df_fma_acc(acc[uu], df{ah.y, al.y}, df{wh.y, wl.y});
+        acc[uu] = df_fma_acc(acc[uu], df{ah.z, al.z}, df{wh.z, wl.z});
+        acc[uu] = df_fma_acc(acc[uu], df{ah.w, al.w}, df{wh.w, wl.w});
+      } else {
+        acc32[uu] = fmaf(ah.w, wh.w, fmaf(ah.z, wh.z, fmaf(ah.y, wh.y, fmaf(ah.x, wh.x, acc32[uu]))));
+      }
+    }
   }
-  const double sum = block_sum(df_to_double(df_renorm(acc)), sh);
-  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
-  if (!last_block(&st->counter[0], nchunk * nv)) return;
+#pragma unroll
+  for (int uu = 0; uu < kDotU; ++uu) {
+    if (u0 + uu >= nv) break;
+    const double sum = block_sum(SPLIT ? df_to_double(df_renorm(acc[uu])) : (double)acc32[uu], sh);
+    if (threadIdx.x == 0) partials[(size_t)(u0 + uu) * nchunk + blockIdx.x] = sum;
+  }
+  if (!last_block(&st->counter[0], nchunk * gridDim.y)) return;
+  const int off = SPLIT ? kMaxM : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = warp; r < nv; r += kThreads / 32) {
     double t = 0.0;
     for (int b = lane; b < nchunk; b += 32) t += __ldcg(partials + (size_t)r * nchunk + b);
     t = warp_sum(t);
-    if (lane == 0) st->h[kMaxM + r] = t * st->vscale[r];
+    if (lane == 0) st->h[off + r] = t * st->vscale[r];
   }
   if (threadIdx.x == 0) st->counter[0] = 0;
 }
@@ -387,8 +383,8 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots_df(int64_t n, const float*
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
 // arithmetic (the coefficients rounded to split pairs once per block, each
 // entry's sum carried as a split pair and renormalised once), four entries
-// per thread.  In the final pass (LAST) ||w||^2 is reduced in FP64 and the
-// last block applies the Givens step to h1 + h2 and stores 1/||w|| as the
+// per thread.  In the final pass (LAST) ||w||^2 is reduced and the last
+// block applies the Givens step to h1 + h2 and stores 1/||w|| as the
 // new column's scale (w itself stays unnormalised).
 template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* __restrict__ V, int64_t ldv,
@@ -403,7 +399,10 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
   const int64_t ng = (n + 3) >> 2;
   for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[off + k] * st->vscale[k]));
   __syncthreads();
-  double acc = 0.0;
+  // ||w||^2 from the high parts in FP32 per thread (FP64 across threads):
+  // its 1e-7 relative accuracy only sets how close to unit length the next
+  // basis vector is, since the same ||w|| is both its scale and h_{j+1,j}
+  float acc32 = 0.f;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ng; q += (int64_t)gridDim.x * blockDim.x) {
     const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
     df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
@@ -433,13 +432,12 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
       }
     }
     if (LAST) {
-      const double d0 = df_to_double(s0), d1 = valid > 1 ? df_to_double(s1) : 0.0,
-                   d2 = valid > 2 ? df_to_double(s2) : 0.0, d3 = valid > 3 ? df_to_double(s3) : 0.0;
-      acc = fma(d3, d3, fma(d2, d2, fma(d1, d1, fma(d0, d0, acc))));
+      const float h1 = valid > 1 ? s1.hi : 0.f, h2 = valid > 2 ? s2.hi : 0.f, h3 = valid > 3 ? s3.hi : 0.f;
+      acc32 = fmaf(h3, h3, fmaf(h2, h2, fmaf(h1, h1, fmaf(s0.hi, s0.hi, acc32))));
     }
   }
   if (!LAST) return;
-  acc = block_sum(acc, sh);
+  double acc = block_sum((double)acc32, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
   if (!last_block(&st->counter[3], gridDim.x)) return;
   const double hn2 = reduce_partials(partials, gridDim.x, sh);
@@ -673,10 +671,10 @@ struct Job {
     const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
     const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
-    const dim3 gd(gs_chunks(nn), nv);
-    (k_gs_dots32<<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+    const dim3 gd(gs_chunks(nn), (nv + kDotU - 1) / kDotU);
+    (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, nv, P->partials, st), note_launch());
     (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
-    (k_gs_dots_df<<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+    (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, nv, P->partials, st), note_launch());
     (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
 
