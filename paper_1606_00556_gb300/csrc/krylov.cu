@@ -310,65 +310,63 @@ struct ArnoldiArgs {
 };
 
 // Gram-Schmidt coefficient passes: h[off + u] = vscale[u] <V_u, w> for
-// u <= j.  Grid (chunks, ceil((j + 1) / kDotU)): block (c, y) sums the
-// columns u = kDotU y .. kDotU y + kDotU - 1 over chunk c of the groups of
-// four entries, so each chunk of w is read once per kDotU columns; the
-// block that finishes last reduces each column's partials (FP64) with one
-// warp per column.
+// u <= j.  Grid (chunks, j + 1): block (c, u) sums column u over chunk c of
+// the groups of four entries, kDotB groups per thread at a time with all
+// their loads issued first (each thread keeps 2 kDotB, or 4 kDotB, 16-byte
+// loads in flight); the block that finishes last reduces each column's
+// partials (FP64) with one warp per column.
 //   SPLIT = false: the first pass, on the high planes only (FP32 products
 //     and per-thread sums), off = 0;
 //   SPLIT = true: the second pass, in split arithmetic (each thread's
 //     products and sums as split pairs), off = kMaxM.
 // The block and chunk sums are FP64 in both.
-constexpr int kDotU = 8;
+constexpr int kDotB = 4;
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __restrict__ V, int64_t ldv,
-                                                     const float* __restrict__ w, int nv, double* partials,
-                                                     DevState* st) {
+                                                     const float* __restrict__ w, double* partials, DevState* st) {
   __shared__ double sh[32];
   if (st->done) return;
+  const int nv = gridDim.y;
   const int nchunk = gridDim.x;
-  const int u0 = blockIdx.y * kDotU;
+  const int u = blockIdx.y;
   const int64_t np = split_pad(n);
   const int64_t ng = (n + 3) >> 2;
   const int64_t len = (ng + nchunk - 1) / nchunk;
   const int64_t g0 = blockIdx.x * len;
   const int64_t g1 = min(ng, g0 + len);
-  float acc32[kDotU];
-  df acc[kDotU];
+  const float* a = V + (size_t)u * ldv;
+  float acc32 = 0.f;
+  df acc{0.f, 0.f};
+  for (int64_t q0 = g0 + threadIdx.x; q0 < g1; q0 += (int64_t)kDotB * blockDim.x) {
+    float4 ah[kDotB], al[kDotB], wh[kDotB], wl[kDotB];
 #pragma unroll
-  for (int uu = 0; uu < kDotU; ++uu) {
-    acc32[uu] = 0.f;
-    acc[uu] = df{0.f, 0.f};
-  }
-  for (int64_t q = g0 + threadIdx.x; q < g1; q += blockDim.x) {
-    const int valid = (int)min((int64_t)4, n - 4 * q);
-    const float4 wh = mask4(ld4(w + 4 * q), valid);
-    const float4 wl = SPLIT ? mask4(ld4(w + np + 4 * q), valid) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int uu = 0; uu < kDotU; ++uu) {
-      if (u0 + uu >= nv) break;
-      const float* a = V + (size_t)(u0 + uu) * ldv + 4 * q;
-      const float4 ah = mask4(ld4(a), valid);
+    for (int b = 0; b < kDotB; ++b) {
+      const int64_t q = q0 + (int64_t)b * blockDim.x;
+      const int valid = q < g1 ? (int)min((int64_t)4, n - 4 * q) : 0;
+      const int64_t qq = q < g1 ? q : g0;  // an in-range group for the masked lanes
+      ah[b] = mask4(ld4(a + 4 * qq), valid);
+      wh[b] = mask4(ld4(w + 4 * qq), valid);
       if (SPLIT) {
-        const float4 al = mask4(ld4(a + np), valid);
-        acc[uu] = df_fma_acc(acc[uu], df{ah.x, al.x}, df{wh.x, wl.x});
-        acc[uu] = df_fma_acc(acc[uu], df{ah.y, al.y}, df{wh.y, wl.y});
-        acc[uu] = df_fma_acc(acc[uu], df{ah.z, al.z}, df{wh.z, wl.z});
-        acc[uu] = df_fma_acc(acc[uu], df{ah.w, al.w}, df{wh.w, wl.w});
+        al[b] = mask4(ld4(a + np + 4 * qq), valid);
+        wl[b] = mask4(ld4(w + np + 4 * qq), valid);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kDotB; ++b) {
+      if (SPLIT) {
+        acc = df_fma_acc(acc, df{ah[b].x, al[b].x}, df{wh[b].x, wl[b].x});
+        acc = df_fma_acc(acc, df{ah[b].y, al[b].y}, df{wh[b].y, wl[b].y});
+        acc = df_fma_acc(acc, df{ah[b].z, al[b].z}, df{wh[b].z, wl[b].z});
+        acc = df_fma_acc(acc, df{ah[b].w, al[b].w}, df{wh[b].w, wl[b].w});
       } else {
-        acc32[uu] = fmaf(ah.w, wh.w, fmaf(ah.z, wh.z, fmaf(ah.y, wh.y, fmaf(ah.x, wh.x, acc32[uu]))));
+        acc32 = fmaf(ah[b].w, wh[b].w, fmaf(ah[b].z, wh[b].z, fmaf(ah[b].y, wh[b].y, fmaf(ah[b].x, wh[b].x, acc32))));
       }
     }
   }
-#pragma unroll
-  for (int uu = 0; uu < kDotU; ++uu) {
-    if (u0 + uu >= nv) break;
-    const double sum = block_sum(SPLIT ? df_to_double(df_renorm(acc[uu])) : (double)acc32[uu], sh);
-    if (threadIdx.x == 0) partials[(size_t)(u0 + uu) * nchunk + blockIdx.x] = sum;
-  }
-  if (!last_block(&st->counter[0], nchunk * gridDim.y)) return;
+  const double sum = block_sum(SPLIT ? df_to_double(df_renorm(acc)) : (double)acc32, sh);
+  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
+  if (!last_block(&st->counter[0], nchunk * nv)) return;
   const int off = SPLIT ? kMaxM : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = warp; r < nv; r += kThreads / 32) {
@@ -671,10 +669,10 @@ struct Job {
     const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
     const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
-    const dim3 gd(gs_chunks(nn), (nv + kDotU - 1) / kDotU);
-    (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, nv, P->partials, st), note_launch());
+    const dim3 gd(gs_chunks(nn), nv);
+    (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
     (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
-    (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, nv, P->partials, st), note_launch());
+    (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
     (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
 
