@@ -75,12 +75,13 @@ __host__ __device__ __forceinline__ int64_t split_pad(int64_t n) { return (n + 3
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float lane4(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-// v with the lanes at or beyond `valid` set to zero
+// v with the lanes at or beyond `valid` (0..4) set to zero
 __device__ __forceinline__ float4 mask4(float4 v, int valid) {
   if (valid < 4) {
-    if (valid < 4) v.w = 0.f;
+    v.w = 0.f;
     if (valid < 3) v.z = 0.f;
     if (valid < 2) v.y = 0.f;
+    if (valid < 1) v.x = 0.f;
   }
   return v;
 }
