@@ -311,75 +311,63 @@ struct ArnoldiArgs {
 };
 
 // Gram-Schmidt coefficient passes: h[off + u] = vscale[u] <V_u, w> for
-// u <= j.  One block per chunk of the groups of four entries: the block
-// stages its chunk of w in shared memory once, then streams every column
-// V_u over the chunk (kDotB groups per thread at a time, their loads issued
-// first) against it, one block sum per column; the block that finishes last
-// reduces each column's partials (FP64) with one warp per column.  So w is
-// read from memory once per pass and there is one ticket per block, not
-// per column.
+// u <= j.  Grid (chunks, j + 1): block (c, u) sums column u over chunk c of
+// the groups of four entries, kDotB groups per thread at a time with all
+// their loads issued first (each thread keeps 2 kDotB, or 4 kDotB, 16-byte
+// loads in flight); the block that finishes last reduces each column's
+// partials (FP64) with one warp per column.
 //   SPLIT = false: the first pass, on the high planes only (FP32 products
 //     and per-thread sums), off = 0;
 //   SPLIT = true: the second pass, in split arithmetic (each thread's
 //     products and sums as split pairs), off = kMaxM.
 // The block and chunk sums are FP64 in both.
 constexpr int kDotB = 4;
-constexpr int kDotChunkGroups = 2560;  // most groups of four per chunk (40 KB of w's high plane)
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __restrict__ V, int64_t ldv,
-                                                     const float* __restrict__ w, int nv, double* partials,
-                                                     DevState* st) {
-  extern __shared__ float4 wsh[];  // the chunk of w: high groups, then (SPLIT) low groups
+                                                     const float* __restrict__ w, double* partials, DevState* st) {
   __shared__ double sh[32];
   if (st->done) return;
+  const int nv = gridDim.y;
   const int nchunk = gridDim.x;
+  const int u = blockIdx.y;
   const int64_t np = split_pad(n);
   const int64_t ng = (n + 3) >> 2;
   const int64_t len = (ng + nchunk - 1) / nchunk;
   const int64_t g0 = blockIdx.x * len;
   const int64_t g1 = min(ng, g0 + len);
-  const int cg = (int)max((int64_t)0, g1 - g0);
-  for (int q = threadIdx.x; q < cg; q += blockDim.x) {
-    const int valid = (int)min((int64_t)4, n - 4 * (g0 + q));
-    wsh[q] = mask4(ld4(w + 4 * (g0 + q)), valid);
-    if (SPLIT) wsh[cg + q] = mask4(ld4(w + np + 4 * (g0 + q)), valid);
-  }
-  __syncthreads();
-  for (int u = 0; u < nv; ++u) {
-    const float* a = V + (size_t)u * ldv + 4 * g0;
-    float acc32 = 0.f;
-    df acc{0.f, 0.f};
-    for (int q0 = threadIdx.x; q0 < cg; q0 += kDotB * blockDim.x) {
-      float4 ah[kDotB], al[kDotB];
+  const float* a = V + (size_t)u * ldv;
+  float acc32 = 0.f;
+  df acc{0.f, 0.f};
+  for (int64_t q0 = g0 + threadIdx.x; q0 < g1; q0 += (int64_t)kDotB * blockDim.x) {
+    float4 ah[kDotB], al[kDotB], wh[kDotB], wl[kDotB];
 #pragma unroll
-      for (int b = 0; b < kDotB; ++b) {
-        const int q = q0 + b * blockDim.x;
-        const int qq = q < cg ? q : 0;
-        const int valid = q < cg ? (int)min((int64_t)4, n - 4 * (g0 + q)) : 0;
-        ah[b] = mask4(ld4(a + 4 * qq), valid);
-        if (SPLIT) al[b] = mask4(ld4(a + np + 4 * qq), valid);
-      }
-#pragma unroll
-      for (int b = 0; b < kDotB; ++b) {
-        const int q = q0 + b * blockDim.x;
-        const int qq = q < cg ? q : 0;
-        const float4 wh = wsh[qq];
-        if (SPLIT) {
-          const float4 wl = wsh[cg + qq];
-          acc = df_fma_acc(acc, df{ah[b].x, al[b].x}, df{wh.x, wl.x});
-          acc = df_fma_acc(acc, df{ah[b].y, al[b].y}, df{wh.y, wl.y});
-          acc = df_fma_acc(acc, df{ah[b].z, al[b].z}, df{wh.z, wl.z});
-          acc = df_fma_acc(acc, df{ah[b].w, al[b].w}, df{wh.w, wl.w});
-        } else {
-          acc32 = fmaf(ah[b].w, wh.w, fmaf(ah[b].z, wh.z, fmaf(ah[b].y, wh.y, fmaf(ah[b].x, wh.x, acc32))));
-        }
+    for (int b = 0; b < kDotB; ++b) {
+      const int64_t q = q0 + (int64_t)b * blockDim.x;
+      const int valid = q < g1 ? (int)min((int64_t)4, n - 4 * q) : 0;
+      const int64_t qq = q < g1 ? q : g0;  // an in-range group for the masked lanes
+      ah[b] = mask4(ld4(a + 4 * qq), valid);
+      wh[b] = mask4(ld4(w + 4 * qq), valid);
+      if (SPLIT) {
+        al[b] = mask4(ld4(a + np + 4 * qq), valid);
+        wl[b] = mask4(ld4(w + np + 4 * qq), valid);
       }
     }
-    const double sum = block_sum(SPLIT ? df_to_double(df_renorm(acc)) : (double)acc32, sh);
-    if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
+#pragma unroll
+    for (int b = 0; b < kDotB; ++b) {
+      if (SPLIT) {
+        acc = df_fma_acc(acc, df{ah[b].x, al[b].x}, df{wh[b].x, wl[b].x});
+        acc = df_fma_acc(acc, df{ah[b].y, al[b].y}, df{wh[b].y, wl[b].y});
+        acc = df_fma_acc(acc, df{ah[b].z, al[b].z}, df{wh[b].z, wl[b].z});
+        acc = df_fma_acc(acc, df{ah[b].w, al[b].w}, df{wh[b].w, wl[b].w});
+      } else {
+        acc32 = fmaf(ah[b].w, wh[b].w, fmaf(ah[b].z, wh[b].z, fmaf(ah[b].y, wh[b].y, fmaf(ah[b].x, wh[b].x, acc32))));
+      }
+    }
   }
-  if (!last_block(&st->counter[0], nchunk)) return;
+  const double sum = block_sum(SPLIT ? df_to_double(df_renorm(acc)) : (double)acc32, sh);
+  if (threadIdx.x == 0) partials[(size_t)u * nchunk + blockIdx.x] = sum;
+  if (!last_block(&st->counter[0], nchunk * nv)) return;
   const int off = SPLIT ? kMaxM : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = warp; r < nv; r += kThreads / 32) {
@@ -389,18 +377,6 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __
     if (lane == 0) st->h[off + r] = t * st->vscale[r];
   }
   if (threadIdx.x == 0) st->counter[0] = 0;
-}
-
-// chunks of a coefficient pass over n entries: chunks of at most
-// kDotChunkGroups groups of four (the shared-memory stage), and at least two
-// per SM where there is enough work
-int gs_dot_chunks(int64_t n) {
-  const int64_t ng = (n + 3) / 4;
-  int64_t c = (ng + kDotChunkGroups - 1) / kDotChunkGroups;
-  const int64_t want = 2 * 152;
-  if (c < want) c = std::min<int64_t>(want, (ng + 255) / 256);
-  if (c < 1) c = 1;
-  return (int)c;
 }
 
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
@@ -471,6 +447,13 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
   const double hn = sqrt(hn2);
   givens_step(st, col, hn, aa.H, aa.cs, aa.sn, aa.gv, aa.j, aa.m, aa.ldh, aa.hist);
   st->vscale[aa.j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+int gs_chunks(int64_t n) {
+  int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
+  if (c < 1) c = 1;
+  if (c > kDotBlocks) c = kDotBlocks;
+  return (int)c;
 }
 
 // y = H(0:k, 0:k)^{-1} g (upper triangular after the rotations)
@@ -555,9 +538,7 @@ int krylov_alloc(bo_prec* P, int m) {
     P->xi = (double*)al((size_t)n * sizeof(double));
     P->bi = (double*)al((size_t)n * sizeof(double));
     P->rk = (double*)al((size_t)n * sizeof(double));
-    P->npartials = (int64_t)(kMaxM + 2) * std::max<int64_t>(kDotBlocks, gs_dot_chunks(n)) + kHistCap;
-    cudaFuncSetAttribute(k_gs_dots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * kDotChunkGroups * sizeof(float4)));
+    P->npartials = (int64_t)(kMaxM + 2) * kDotBlocks + kHistCap;
     P->partials = (double*)al((size_t)P->npartials * sizeof(double));
     P->hostio = (double*)al((size_t)2 * n * sizeof(double));
     if (ok && cudaMallocHost(&P->h_st, 4 * sizeof(DevState)) != cudaSuccess) ok = false;
@@ -689,13 +670,10 @@ struct Job {
     const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
     const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
-    const int nc = gs_dot_chunks(nn);
-    const int cgmax = (int)(((nn + 3) / 4 + nc - 1) / nc);  // groups of the largest chunk
-    (k_gs_dots<false><<<nc, kThreads, cgmax * sizeof(float4), s>>>(nn, V, ldv, w, nv, P->partials, st),
-     note_launch());
+    const dim3 gd(gs_chunks(nn), nv);
+    (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
     (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
-    (k_gs_dots<true><<<nc, kThreads, 2 * cgmax * sizeof(float4), s>>>(nn, V, ldv, w, nv, P->partials, st),
-     note_launch());
+    (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
     (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
 
