@@ -323,6 +323,111 @@ int64_t bo_kernel_launches(void);
 int bo_mat_residual_noalloc(bo_mat* A, const double* b, const double* x, double* r, double* norms);
 
 /* ---------------------------------------------------------------------------
+ * The black-oil model on the device and the inexact Newton method (paper
+ * Sec. 2.1 Eq. 3 with its closure relations, Sec. 2.3 Eq. 4, Sec. 3.1
+ * Alg. 1).  The residual of cell c and component (oil, water, gas) is
+ *   R = V / (5.615 dt) [M(x) - M(x^n)] - sum of face fluxes - well rates,
+ * M_w = phi Sw / Bw, M_o = phi So / Bo, M_g = phi (Sg / Bg + Rs So / Bo);
+ * face fluxes T lambda_up (Phi_b - Phi_a) per phase with two-point
+ * transmissibilities T = 0.001127 A 2 / (h / k_a + h / k_b), Corey curves and
+ * Stone II oil relative permeability, phase-potential upwinding, potentials
+ * p - rho D / 144; wells at fixed bottom-hole pressure with the cell's phase
+ * mobilities (producers) or total mobility (water injectors).  No-flow outer
+ * boundary.  b = -R(x), A = dR/dx (exact derivatives).  Units: ft, psi, mD,
+ * cp, day, stb, Mscf.  Unknowns (p, Sw, Sg) per cell, interleaved, natural
+ * cell order; depth grows with k.
+ * ------------------------------------------------------------------------- */
+typedef struct bo_model bo_model;
+
+/* Fluid, rock and saturation-function constants of the model (the paper gives
+ * none for synthetic cases): Bw = bw0 (1 - cw (p - pref)), Bo = bo0 + dbo
+ * (p - pref), Rs = rs0 + drs (p - pref) Mscf/stb, Bg = bg0 - dbg (p - pref)
+ * rb/Mscf, viscosities in cp, stock-tank densities in lb/ft^3, porosity
+ * phi0 (1 + cr (p - pref)); Corey end points swc, sorw, sorg, sgc and
+ * exponents nw, now, ng, nog; gravity 1 (hydrostatic terms) or 0. */
+typedef struct {
+  double pref;
+  double bw0, cw, muw;
+  double bo0, dbo, rs0, drs, muo;
+  double bg0, dbg, mug;
+  double rhow_sc, rhoo_sc, rhog_sc;
+  double cr;
+  double swc, sorw, sorg, sgc;
+  double nw, now, ng, nog;
+  double gravity;
+} bo_fluid;
+
+enum { BO_FORCING_FIXED = 0, BO_FORCING_EW1 = 1, BO_FORCING_EW2 = 2, BO_FORCING_EW3 = 3 };
+enum { BO_NEWTON_MAX_STEPS = 64 };
+
+typedef struct {
+  double eps;          /* stop when ||b(x^l)|| < eps; 0: eps = eps_rel ||b(x^0)||      */
+  double eps_rel;      /* (default 1e-8)                                              */
+  int32_t forcing;     /* BO_FORCING_*: the three choices of Sec. 3.1, or fixed theta  */
+  double theta_fixed;  /* BO_FORCING_FIXED: theta of every step (default 1e-2)         */
+  double theta_max;    /* theta_0, and the upper clip of every theta (default 0.1)     */
+  double theta_min;    /* lower clip (default 1e-10)                                   */
+  double gamma, beta;  /* the third choice: theta = gamma (||b_new|| / ||b_old||)^beta  */
+  int32_t maxit;       /* Newton steps, at most BO_NEWTON_MAX_STEPS (default 20)       */
+  int32_t restart;     /* FGMRES restart of the linear solves (default 30)             */
+  int32_t lin_maxit;   /* iteration cap of each linear solve (default 1000)            */
+} bo_newton_opts;
+
+typedef struct {
+  int32_t status;                            /* as returned                      */
+  int32_t iters;                             /* Newton steps taken               */
+  int32_t converged;                         /* ||b(x)|| < eps at exit           */
+  int32_t lin_total;                         /* linear iterations in all steps   */
+  double bnorm[BO_NEWTON_MAX_STEPS + 1];     /* ||b(x^l)||, l = 0 .. iters       */
+  double theta[BO_NEWTON_MAX_STEPS];         /* forcing term of step l           */
+  int32_t lin_iters[BO_NEWTON_MAX_STEPS];    /* FGMRES iterations of step l      */
+  double lin_rel_res[BO_NEWTON_MAX_STEPS];   /* ||b - A dx|| / ||b|| of step l   */
+} bo_newton_info;
+
+/* Defaults: eps 0 with eps_rel 1e-8, the third forcing term with gamma 0.9,
+ * beta 2, theta in [1e-10, 0.1], 20 steps, restart 30, 1000 linear its. */
+void bo_newton_opts_default(bo_newton_opts* o);
+
+/* The model of one reservoir on ctx's device.  Host arrays of nx ny nz
+ * values (natural order): permeabilities kx, ky, kz (mD, > 0), reference
+ * porosity phi0 (> 0), cell-centre depth (ft).  nperf perforations: cell
+ * perf_cell[e], well type perf_type[e] (0 water injector, 1 producer),
+ * bottom-hole pressure perf_bhp[e] (psi) at reference depth perf_dref[e],
+ * and well index perf_wi[e] (the Peaceman index of the completion, an input
+ * like the permeability).  Copied; grid rules as for bo_mat_create_bsr.
+ * BO_ERR_ARG for a bad size, a non-positive permeability or porosity, a
+ * perforation outside the grid.  Holds a reference on ctx.  Synchronises. */
+int bo_model_create(bo_ctx* ctx, const bo_grid* grid, const bo_fluid* fluid, const double* kx, const double* ky,
+                    const double* kz, const double* phi0, const double* depth, int32_t nperf,
+                    const int32_t* perf_cell, const int32_t* perf_type, const double* perf_bhp,
+                    const double* perf_dref, const double* perf_wi, bo_model** out);
+int bo_model_destroy(bo_model* M);
+/* Residual and Jacobian at state x (device, 3 nx ny nz doubles, (p, Sw, Sg)
+ * interleaved) with previous time level xn and time step dt (days): b =
+ * -R(x) into b (device, 3 nx ny nz; NULL: not copied out), the Jacobian values
+ * into val (device, 9 nnzb doubles in the BSR order of the 7-point pattern:
+ * rows in cell order, columns -z, -y, -x, diag, +x, +y, +z as they exist;
+ * NULL: not copied out), ||b||_2 into *bnorm (host; NULL: not computed).
+ * BO_ERR_BREAKDOWN if a cell's porosity or formation volume factor is not
+ * positive at x.  Synchronises. */
+int bo_model_assemble(bo_model* M, const double* x, const double* xn, double dt, double* b, double* val,
+                      double* bnorm);
+/* The inexact Newton method (Alg. 1) for one time step: from x (device, in:
+ * the initial guess x^0, out: the last iterate), while ||b(x^l)|| >= eps:
+ * assemble on the device, put the Jacobian into P's matrix and refresh P
+ * (as bo_mat_update_values and bo_prec_update), solve A dx = b with FGMRES and
+ * P to ||b - A dx|| <= theta_l ||b|| from a zero guess, x += dx, and compute
+ * the next theta from the chosen forcing term of Sec. 3.1 (the second with
+ * the absolute value of its difference), clipped to [theta_min, theta_max];
+ * theta_0 = theta_max.  P must be set up on a matrix of the model's grid and
+ * context.  Returns BO_OK when converged, BO_ERR_NOT_CONVERGED after maxit
+ * steps (x then holds the last iterate), or the first error of an assembly,
+ * setup or solve.  info (may be NULL) records every step.  No saturation
+ * chopping: the method as stated. */
+int bo_newton_solve(bo_model* M, bo_prec* P, double* x, const double* xn, double dt, const bo_newton_opts* opts,
+                    bo_newton_info* info);
+
+/* ---------------------------------------------------------------------------
  * Dual-porosity systems (paper Sec. 2.1, the dual-porosity model: fracture
  * and matrix continua per cell with a transfer term between them).
  *

@@ -56,6 +56,7 @@ EXPORTS = (
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
     "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins",
+    "bo_newton_opts_default", "bo_model_create", "bo_model_destroy", "bo_model_assemble", "bo_newton_solve",
 )
 
 
@@ -102,6 +103,40 @@ class bo_solve_info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_FLUID_FIELDS = ("pref", "bw0", "cw", "muw", "bo0", "dbo", "rs0", "drs", "muo", "bg0", "dbg", "mug",
+                 "rhow_sc", "rhoo_sc", "rhog_sc", "cr", "swc", "sorw", "sorg", "sgc", "nw", "now", "ng", "nog",
+                 "gravity")
+
+
+class bo_fluid(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _FLUID_FIELDS]
+
+
+BO_FORCING_FIXED, BO_FORCING_EW1, BO_FORCING_EW2, BO_FORCING_EW3 = 0, 1, 2, 3
+BO_NEWTON_MAX_STEPS = 64
+
+
+class bo_newton_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("eps_rel", ctypes.c_double), ("forcing", ctypes.c_int32),
+                ("theta_fixed", ctypes.c_double), ("theta_max", ctypes.c_double), ("theta_min", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("beta", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("lin_maxit", ctypes.c_int32)]
+
+
+class bo_newton_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("lin_total", ctypes.c_int32), ("bnorm", ctypes.c_double * (BO_NEWTON_MAX_STEPS + 1)),
+                ("theta", ctypes.c_double * BO_NEWTON_MAX_STEPS),
+                ("lin_iters", ctypes.c_int32 * BO_NEWTON_MAX_STEPS),
+                ("lin_rel_res", ctypes.c_double * BO_NEWTON_MAX_STEPS)]
+
+    def as_dict(self):
+        k = self.iters
+        return {"status": self.status, "iters": k, "converged": bool(self.converged), "lin_total": self.lin_total,
+                "norms": list(self.bnorm[:k + 1]), "thetas": list(self.theta[:k]),
+                "linear_iters": list(self.lin_iters[:k]), "linear_rel_res": list(self.lin_rel_res[:k])}
 
 
 _lib = None
@@ -180,6 +215,13 @@ def lib():
                                           ctypes.POINTER(bo_solve_opts), ctypes.c_char_p, ctypes.POINTER(bo_tune_result)]
         L.bo_learned_guess.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _i, _VP,
                                        ctypes.POINTER(ctypes.c_int)]
+        L.bo_newton_opts_default.argtypes = [ctypes.POINTER(bo_newton_opts)]
+        L.bo_model_create.argtypes = [_VP, ctypes.POINTER(bo_grid), ctypes.POINTER(bo_fluid), _VP, _VP, _VP, _VP, _VP,
+                                      ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)]
+        L.bo_model_destroy.argtypes = [_VP]
+        L.bo_model_assemble.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.POINTER(ctypes.c_double)]
+        L.bo_newton_solve.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.POINTER(bo_newton_opts),
+                                      ctypes.POINTER(bo_newton_info)]
         _lib = L
     return _lib
 
@@ -676,6 +718,88 @@ def _bits(t):
     """BF16 tensor -> the same storage as int16 bit patterns (no copy)."""
     import torch
     return t.view(torch.int16) if t.dtype == torch.bfloat16 else t
+
+
+def fluid(**values) -> bo_fluid:
+    """A bo_fluid from keyword values (every field of the struct required)."""
+    missing = [k for k in _FLUID_FIELDS if k not in values]
+    if missing:
+        raise BoArgError(f"fluid: missing {missing}")
+    return bo_fluid(**{k: float(values[k]) for k in _FLUID_FIELDS})
+
+
+class Model:
+    """bo_model: the black-oil residual and Jacobian on the device, and the
+    inexact Newton method around the solver (paper Sec. 2.1, 2.3, 3.1)."""
+
+    def __init__(self, ctx: Context, g: bo_grid, fl: bo_fluid, kx, ky, kz, phi0, depth, perf_cell=(),
+                 perf_type=(), perf_bhp=(), perf_dref=(), perf_wi=()):
+        N = g.nx * g.ny * g.nz
+        arrs = []
+        for nm, a in (("kx", kx), ("ky", ky), ("kz", kz), ("phi0", phi0), ("depth", depth)):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.size != N:
+                raise BoArgError(f"{nm}: {a.size} values for {N} cells")
+            arrs.append(a)
+        pc = np.ascontiguousarray(perf_cell, dtype=np.int32).ravel()
+        pt = np.ascontiguousarray(perf_type, dtype=np.int32).ravel()
+        pb, pd, pw = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (perf_bhp, perf_dref, perf_wi))
+        if not (pc.size == pt.size == pb.size == pd.size == pw.size):
+            raise BoArgError("perforation arrays of different lengths")
+        self._keep = (arrs, pc, pt, pb, pd, pw)
+        h = _VP()
+        vp = lambda a: _VP(a.ctypes.data) if a.size else None
+        _check(lib().bo_model_create(ctx.h, ctypes.byref(g), ctypes.byref(fl), *[vp(a) for a in arrs],
+                                     ctypes.c_int32(pc.size), vp(pc), vp(pt), vp(pb), vp(pd), vp(pw),
+                                     ctypes.byref(h)), "bo_model_create")
+        self.ctx, self.grid, self.h = ctx, g, h
+        self.n = 3 * N
+        self.nnzb = N + 2 * ((g.nx - 1) * g.ny * g.nz + g.nx * (g.ny - 1) * g.nz + g.nx * g.ny * (g.nz - 1))
+
+    def assemble(self, x, xn, dt, b=None, val=None):
+        """bo_model_assemble: b = -R(x) and the Jacobian values (BSR order of
+        the 7-point pattern) into the given device tensors; returns ||b||."""
+        nb = ctypes.c_double(0.0)
+        bp = _dvec(b, self.n, "b", self.ctx) if b is not None else None
+        vp = _dvec(val, 9 * self.nnzb, "val", self.ctx) if val is not None else None
+        _check(lib().bo_model_assemble(self.h, _dvec(x, self.n, "x", self.ctx), _dvec(xn, self.n, "xn", self.ctx),
+                                       float(dt), bp, vp, ctypes.byref(nb)), "bo_model_assemble")
+        return nb.value
+
+    def newton(self, P, x, xn, dt, raise_on_error=True, **opts):
+        """bo_newton_solve on x (device, in place); opts: the fields of
+        bo_newton_opts (forcing 'ew1' | 'ew2' | 'ew3' or a float theta).
+        Returns the info dict."""
+        o = bo_newton_opts()
+        lib().bo_newton_opts_default(ctypes.byref(o))
+        forcing = opts.pop("forcing", "ew3")
+        if isinstance(forcing, str):
+            o.forcing = {"ew1": BO_FORCING_EW1, "ew2": BO_FORCING_EW2, "ew3": BO_FORCING_EW3}[forcing]
+        else:
+            o.forcing, o.theta_fixed = BO_FORCING_FIXED, float(forcing)
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise BoArgError(f"newton: unknown option {k}")
+            setattr(o, k, v)
+        info = bo_newton_info()
+        rc = lib().bo_newton_solve(self.h, P.h, _dvec(x, self.n, "x", self.ctx), _dvec(xn, self.n, "xn", self.ctx),
+                                   float(dt), ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error and rc not in (BO_OK, BO_ERR_NOT_CONVERGED):
+            raise BoError(rc, "bo_newton_solve")
+        d = info.as_dict()
+        d["status"] = rc
+        return d
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_model_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class CNN:

@@ -499,6 +499,9 @@ void launch_cpr_split_in(bo_prec* P, const float* v, float* z, const DevState* s
 void launch_split_matrix(bo_mat* m, cudaStream_t s);
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y);  // FP64 values of At rebuilt on the fly
 
+// capi.cu: drop a reference on a context (frees it with the last one)
+void ctx_release_ref(bo_ctx* c);
+
 // krylov.cu
 int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
 int bicgstab(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);

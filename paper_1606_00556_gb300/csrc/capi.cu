@@ -118,6 +118,14 @@ void mat_release(bo_mat* m) {
   if (--m->refs == 0) mat_free(m);
 }
 
+}  // namespace
+
+namespace bo {
+void ctx_release_ref(bo_ctx* c) { ctx_release(c); }
+}  // namespace bo
+
+namespace {
+
 int mat_create(bo_ctx* ctx, const bo_grid* grid, int kind, int64_t nrows, int64_t nnz, const int32_t* rowptr,
                const int32_t* col, const double* val, int mem, bo_mat** out) {
   if (!ctx || !out || !rowptr || !col || !val || !grid_ok(grid) || nnz <= 0 || nnz > INT32_MAX) return BO_ERR_ARG;

@@ -140,6 +140,10 @@ def test_every_entry_point_rejects_missing_handles(libpath):
         "bo_conv3d_backward_data": (N, 8, 8, 8, 1, 32, 32, N, N, N),
         "bo_conv3d_backward_weights": (N, 8, 8, 8, 1, 32, 32, N, N, N, N),
         "bo_ctx_destroy": (N,),
+        "bo_model_create": (N, N, N, N, N, N, N, N, 0, N, N, N, N, N, N),
+        "bo_model_destroy": (N,),
+        "bo_model_assemble": (N, N, N, ctypes.c_double(1.0), N, N, N),
+        "bo_newton_solve": (N, N, N, N, ctypes.c_double(1.0), N, N),
     }
     for name, args in calls.items():
         assert getattr(L, name)(*args) == bo.BO_ERR_ARG, name
