@@ -297,9 +297,13 @@ def run_reference(args):
 def config_dict(args):
     dims = tuple(getattr(args, "dims", DIMS))
     nx, ny, nz = dims
+    seq = getattr(args, "sequence", "newton")
+    days = ("successive days advanced by the device Newton method" if seq == "newton"
+            else "successive days of synthetic front growth")
     return {"workload": (f"waterflood black-oil Jacobians {nx}x{ny}x{nz} (3 unknowns/cell, 3x3 BSR 7-point), "
-                         f"{args.jacobians} successive days, CPR-FGMRES({args.restart}) to 1e-8, "
+                         f"{args.jacobians} {days}, CPR-FGMRES({args.restart}) to 1e-8, "
                          f"preconditioner {args.precision}"),
+            "sequence": seq,
             "grid": list(dims), "unknowns": 3 * nx * ny * nz, "nnzb": _nnzb(*dims), "tol": 1e-8,
             "restart": args.restart, "precision": args.precision, "seed": SEED, "jacobians": args.jacobians,
             "l2": "inputs larger than L2 (524 MB of matrix values per step, 10 Jacobians resident)"}
@@ -585,6 +589,50 @@ def run_conv(args):
     print(json.dumps(line), flush=True)
 
 
+def newton_sequence(bo, ctx, dev, case, A, days, restart, eps_rel=1e-6):
+    """The first Newton Jacobian of each of `days` successive 1-day steps of
+    the waterflood `case`: day 0 at the case's state, each later day at the
+    state the device Newton method (Alg. 1, third forcing term, FP32 CPR,
+    ||b|| reduced by eps_rel) converged to on the previous day.  Returns
+    (values, right-hand sides) as device tensors and a record of the Newton
+    steps (iterations, linear iterations and CUDA-event time per day)."""
+    import bogen
+    import torch
+    m = bogen.model_inputs(case)
+    g = bo.grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz)
+    M = bo.Model(ctx, g, bo.fluid(**m["fluid"]), m["kx"], m["ky"], m["kz"], m["phi0"], m["depth"],
+                 m["perf_cell"], m["perf_type"], m["perf_bhp"], m["perf_dref"], m["perf_wi"])
+    Pn = bo.Preconditioner(A, precision=bo.BO_PREC_FP32)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(np.ascontiguousarray(case.x)).to(dev)
+    vals, bs, steps = [], [], []
+    for d in range(days):
+        val = torch.empty(9 * M.nnzb, dtype=torch.float64, device=dev)
+        b = torch.empty(M.n, dtype=torch.float64, device=dev)
+        M.assemble(x, x, case.dt, b, val)  # the first system of the step: x = x^n
+        vals.append(val)
+        bs.append(b)
+        if d + 1 == days:
+            break
+        xn = x.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = M.newton(Pn, x, xn, case.dt, forcing="ew3", eps_rel=eps_rel, maxit=20, restart=restart)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if info["status"] != bo.BO_OK:
+            raise RuntimeError(f"Newton step of day {d} failed: {info}")
+        steps.append({"day": d, "newton_iters": info["iters"], "linear_iters": info["linear_iters"],
+                      "ms": e0.elapsed_time(e1), "bnorm_reduction": info["norms"][-1] / info["norms"][0]})
+    Pn.close()
+    M.close()
+    rec = {"kind": "device Newton method, third forcing term (Sec. 3.1), FP32 CPR, ||b|| reduced by "
+                   f"{eps_rel:g} per day", "days": steps,
+           "newton_iters_total": sum(st["newton_iters"] for st in steps),
+           "ms_per_day_mean": float(np.mean([st["ms"] for st in steps])) if steps else None}
+    return vals, bs, rec
+
+
 def run_mixed(bo, ctx, dev, stream, a, args):
     """The 256x256x128 Jacobian with the FP32, BF16-storage and FP64
     preconditioners: per precision one untimed step, then args.mixed_steps
@@ -649,6 +697,9 @@ def main():
     ap.add_argument("--jacobians", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sequence", default="newton", choices=["newton", "synthetic"],
+                    help="the 1M-cell Jacobians of successive days: advanced by the device Newton method "
+                         "(default), or the generator's synthetic fronts")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the 256x256x128 (8.4M-cell) mixed-precision Jacobian")
     ap.add_argument("--mixed-steps", type=int, default=3, help="timed solves per precision at 256x256x128")
@@ -693,7 +744,17 @@ def main():
         # while the GPU runs
         ref_pool = mp.get_context("spawn").Pool(1)
         ref_async = ref_pool.apply_async(oracle_reference_job, ((MIXED_DIMS, SEED, 0, args.mixed_ref_tol),))
-    jac = generate(dims, rank_seed(rank), args.jacobians, procs=min(16, os.cpu_count() or 1))
+    if args.sequence == "synthetic":
+        jac = generate(dims, rank_seed(rank), args.jacobians, procs=min(16, os.cpu_count() or 1))
+        case0 = None
+    else:
+        # day 0 from the generator; the later days' Jacobians come from the
+        # device Newton method advancing the state (below)
+        import bogen
+        bogen.build()
+        case0 = bogen.waterflood_case(*dims, seed=rank_seed(rank), day=0)
+        a = bogen.assemble(case0)
+        jac = [(a["rowptr"], a["col"], a["val"].reshape(-1), a["b"], case0.x)]
     mix_a = None
     if mixed:
         import bogen
@@ -736,11 +797,15 @@ def main():
     n = 3 * N
     nnzb = _nnzb(*dims)
     rowptr, col = jac[0][0], jac[0][1]
-    vals = [torch.from_numpy(j[2]).to(dev) for j in jac]
-    bs = [torch.from_numpy(j[3]).to(dev) for j in jac]
     state = torch.from_numpy(jac[0][4]).to(dev)
     g = bo.grid(*dims)
     A = bo.Matrix.from_bsr(ctx, g, rowptr, col, jac[0][2])
+    newton_rec = None
+    if case0 is not None:
+        vals, bs, newton_rec = newton_sequence(bo, ctx, dev, case0, A, args.jacobians, args.restart)
+    else:
+        vals = [torch.from_numpy(j[2]).to(dev) for j in jac]
+        bs = [torch.from_numpy(j[3]).to(dev) for j in jac]
     prec = {"fp32": bo.BO_PREC_FP32, "bf16": bo.BO_PREC_BF16}.get(args.precision, bo.BO_PREC_FP64)
     P = bo.Preconditioner(A, precision=prec)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -854,8 +919,8 @@ def main():
     # cross PCIe/C2C inside the timed region
     e2e = None
     if args.e2e_steps > 0:
-        hv = [torch.from_numpy(j[2]).pin_memory() for j in jac[:args.e2e_steps]]
-        hb = [torch.from_numpy(j[3]).pin_memory() for j in jac[:args.e2e_steps]]
+        hv = [v.cpu().pin_memory() for v in vals[:args.e2e_steps]]
+        hb = [b.cpu().pin_memory() for b in bs[:args.e2e_steps]]
         hx = torch.zeros(n, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -876,13 +941,15 @@ def main():
     # against the oracle's reference solution (overall and per component)
     errors = {}
     if xref is not None:
-        A.update_values(vals[0])
+        # the generator's day-0 Jacobian itself (the one the oracle solved)
+        A.update_values(torch.from_numpy(a0["val"]).to(dev))
+        b0 = torch.from_numpy(a0["b"]).to(dev)
         errors["reference"] = {"128x128x64": cpu_rec["reference_solution"]}
         errors["128x128x64"] = {}
         for nm, pr in (("fp64", bo.BO_PREC_FP64), ("fp32", bo.BO_PREC_FP32), ("bf16", bo.BO_PREC_BF16)):
             Pe = bo.Preconditioner(A, precision=pr)
             xe = torch.zeros(n, dtype=torch.float64, device=dev)
-            ie = Pe.solve(bs[0], xe, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True,
+            ie = Pe.solve(b0, xe, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True,
                           raise_on_error=False)
             errors["128x128x64"][nm] = {"status": ie["status"], "iters": ie["iters"],
                                         "true_rel_res": ie["true_rel_res"],
@@ -919,7 +986,7 @@ def main():
                          "fp64_equivalent_tflops": ach_tf,
                          "avg_us": avg_s * 1e6 if avg_s else None, "launches": spmv_n},
             "spmv": sp, "spmv_cpu": cpu_spmv, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e,
-            "errors": errors or None, "mixed_256x256x128": mixed_rec,
+            "errors": errors or None, "mixed_256x256x128": mixed_rec, "newton_sequence": newton_rec,
             "precision_note": ("no all-FP64 path is timed: even the FP64 preconditioner form computes the Arnoldi "
                                "product in split FP32 pairs (2^-46 relative per term); convergence is decided "
                                "on the FP64 true residual of the original system"),

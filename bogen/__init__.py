@@ -195,6 +195,29 @@ def assemble(case: Case, jacobian: bool = True, x=None):
     return dict(rowptr=rowptr, col=col, val=val, R=R, b=-R)
 
 
+def model_inputs(case: Case) -> dict:
+    """The case's rock, wells and fluid as plain arrays, for a consumer that
+    assembles the same residual itself: kx, ky, kz, phi0, depth per cell; one
+    entry per perforation of perf_cell, perf_type (0 injector, 1 producer),
+    perf_bhp, perf_dref (the well's reference depth: its top perforation
+    unless given) and perf_wi (the Peaceman index the assembly uses); fluid
+    as a dict of the Fluid fields."""
+    fl = case.fluid if case.fluid is not None else default_fluid()
+    pc, pt, pb, pd, pw = [], [], [], [], []
+    for w in case.wells:
+        cells = np.asarray(w.cells).ravel()
+        dref = w.dref if w.dref else case.depth[int(np.min(cells))]
+        for c in cells:
+            pc.append(int(c))
+            pt.append(int(w.kind))
+            pb.append(float(w.bhp))
+            pd.append(float(dref))
+            pw.append(well_index(case, int(c)))
+    return dict(kx=_d(case.kx), ky=_d(case.ky), kz=_d(case.kz), phi0=_d(case.phi0), depth=_d(case.depth),
+                perf_cell=np.asarray(pc, np.int32), perf_type=np.asarray(pt, np.int32), perf_bhp=_d(pb),
+                perf_dref=_d(pd), perf_wi=_d(pw), fluid={k: getattr(fl, k) for k, _ in fl._fields_})
+
+
 def cell_mass(fluid: Fluid, phi0, p, sw, sg, comp) -> float:
     return lib().bg_cell_mass(ctypes.byref(fluid), phi0, p, sw, sg, comp)
 

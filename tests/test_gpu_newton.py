@@ -45,20 +45,10 @@ def ctx(bo):
 def _model(bo, ctx, case):
     """The device model of a generator case: the same rock, wells (with the
     generator's Peaceman indices and reference depths) and fluid."""
-    fl = case.fluid if case.fluid is not None else bogen.default_fluid()
-    fluid = bo.fluid(**{k: getattr(fl, k) for k, _ in fl._fields_})
-    pc, pt, pb, pd, pw = [], [], [], [], []
-    for w in case.wells:
-        cells = np.asarray(w.cells).ravel()
-        dref = w.dref if w.dref else case.depth[int(np.min(cells))]
-        for c in cells:
-            pc.append(int(c))
-            pt.append(int(w.kind))
-            pb.append(float(w.bhp))
-            pd.append(float(dref))
-            pw.append(bogen.well_index(case, int(c)))
+    m = bogen.model_inputs(case)
     g = bo.grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz)
-    return bo.Model(ctx, g, fluid, case.kx, case.ky, case.kz, case.phi0, case.depth, pc, pt, pb, pd, pw)
+    return bo.Model(ctx, g, bo.fluid(**m["fluid"]), m["kx"], m["ky"], m["kz"], m["phi0"], m["depth"],
+                    m["perf_cell"], m["perf_type"], m["perf_bhp"], m["perf_dref"], m["perf_wi"])
 
 
 def _dev(a):
