@@ -155,11 +155,16 @@ int bo_mat_create_csr(bo_ctx* ctx, const bo_grid* grid, int32_t nrows, int64_t n
  * not be solved with); BO_ERR_ARG for NULL or a bad mem. */
 int bo_mat_update_values(bo_mat* A, const double* val, int mem);
 /* y = alpha A x + beta y (paper Sec. 3.3 first basic operation); x, y
- * device vectors of length 3 nx ny nz.  precision BO_PREC_FP64: FP64 values
- * and sums.  BO_PREC_FP32 / BO_PREC_BF16: a reduced-precision copy of the
- * values (made on first use after each value update), x rounded to FP32 on
- * load, products and sums in FP32, y written in FP64 (the reduced-storage
- * matrix form of the mixed-precision path).  beta = 0 never reads y. */
+ * device vectors of length 3 nx ny nz.  precision BO_PREC_FP64: the values
+ * as split pairs of floats (48 significant bits, the copy the solver's
+ * Arnoldi product reads), x split the same way on load, products and sums in
+ * split arithmetic, so |y - exact| <= 2e-13 (|A| |x|)_i (before alpha and
+ * beta); a matrix with a value outside the split form's range [2^-120, 2^126]
+ * uses its FP64 values and FP64 products instead.  BO_PREC_FP32 /
+ * BO_PREC_BF16: a reduced-precision copy of the values (made on first use
+ * after each value update), x rounded to FP32 on load, products and sums in
+ * FP32, y written in FP64 (the reduced-storage matrix form of the
+ * mixed-precision path).  beta = 0 never reads y. */
 int bo_mat_spmv(bo_mat* A, double alpha, const double* x, double beta, double* y, int precision);
 /* BO_ERR_ARG for NULL; see bo_ctx_destroy for lifetimes. */
 int bo_mat_destroy(bo_mat* A);

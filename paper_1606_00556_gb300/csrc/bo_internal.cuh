@@ -378,9 +378,9 @@ struct bo_mat {
   int32_t* col;
   double* stage;       // device staging of values passed from the host
   double* A;           // 63 N FP64 values, colour-split planes
-  float* A32;          // FP32 copy for bo_mat_spmv(..., BO_PREC_FP32)
+  float* A32;          // FP32 copy for bo_mat_spmv(..., BO_PREC_FP32), tiled (a2_index)
   bool a32_valid;
-  __nv_bfloat16* A16;  // BF16 copy for bo_mat_spmv(..., BO_PREC_BF16)
+  __nv_bfloat16* A16;  // BF16 copy for bo_mat_spmv(..., BO_PREC_BF16), tiled (a2_index)
   bool a16_valid;
   float2* A2;          // split (hi, lo) copy of A for the Arnoldi product, tiled (a2_index)
   bool a2_valid;
@@ -480,6 +480,9 @@ int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s);
 void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
 void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s);
 void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision);
+// FP32 / BF16 copies of A in the tiled layout of the split copy (a2_size entries)
+void launch_to_tiled_f32(const bo_mat* m, float* dst, cudaStream_t s);
+void launch_to_tiled_bf16(const bo_mat* m, __nv_bfloat16* dst, cudaStream_t s);
 void launch_to_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t s);
 void launch_gather(const Geom& g, const double* nat, double* in, cudaStream_t s);
 void launch_scatter(const Geom& g, const double* in, double* nat, cudaStream_t s);

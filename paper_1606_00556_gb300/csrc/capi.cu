@@ -302,14 +302,15 @@ int bo_mat_update_values(bo_mat* m, const double* val, int mem) {
 int bo_mat_spmv(bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
   if (!m || !x || !y) return BO_ERR_ARG;
   if (precision != BO_PREC_FP64 && precision != BO_PREC_FP32 && precision != BO_PREC_BF16) return BO_ERR_ARG;
+  // the reduced-precision copies, in the split copy's tiled layout
   if (precision == BO_PREC_FP32 && !m->a32_valid) {
-    if (!m->A32 && cudaMalloc(&m->A32, (size_t)63 * m->g.N * sizeof(float)) != cudaSuccess) return BO_ERR_OOM;
-    launch_to_f32(m->A, m->A32, (size_t)63 * m->g.N, m->ctx->stream);
+    if (!m->A32 && cudaMalloc(&m->A32, a2_size(m->g) * sizeof(float)) != cudaSuccess) return BO_ERR_OOM;
+    launch_to_tiled_f32(m, m->A32, m->ctx->stream);
     m->a32_valid = true;
   }
   if (precision == BO_PREC_BF16 && !m->a16_valid) {
-    if (!m->A16 && cudaMalloc(&m->A16, (size_t)63 * m->g.N * sizeof(__nv_bfloat16)) != cudaSuccess) return BO_ERR_OOM;
-    launch_to_bf16(m->A, m->A16, (size_t)63 * m->g.N, m->ctx->stream);
+    if (!m->A16 && cudaMalloc(&m->A16, a2_size(m->g) * sizeof(__nv_bfloat16)) != cudaSuccess) return BO_ERR_OOM;
+    launch_to_tiled_bf16(m, m->A16, m->ctx->stream);
     m->a16_valid = true;
   }
   launch_spmv_nat(m, alpha, x, beta, y, precision);

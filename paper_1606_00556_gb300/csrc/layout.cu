@@ -149,6 +149,151 @@ __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restr
   }
 }
 
+// y = alpha A x + beta y on natural-order vectors from a tiled copy of the
+// values (the layout of the split copy: the 63 values of 32 consecutive half
+// indices of one colour in one 16 KB tile).  V = float2: the split copy
+// itself, products and sums in split FP32 pairs (48 significant bits, x split
+// on load by integer operations), bound by HBM rather than by GB300's FP64
+// rate; V = float or __nv_bfloat16: the reduced-precision copies, FP32
+// products and sums.  A thread takes the cell pairs (2q, 2q + 1) of Q
+// consecutive half indices q of one grid row (the two cells of a pair have
+// the two colours), so each of its value loads is 8 bytes wide: Q = 1 split
+// pair, 2 floats or 4 BF16 values.  Needs hx % Q == 0 (the Q pairs share a
+// row).
+template <typename V, int Q>
+__global__ void __launch_bounds__(kThreads) k_spmv_tiled(Geom g, const V* __restrict__ A, const double* __restrict__ x,
+                                                        double* __restrict__ y, double alpha, double beta,
+                                                        const double* __restrict__ A64, const int* __restrict__ range) {
+  constexpr bool SPLIT = sizeof(V) == 8;
+  // a split copy that could not hold every value: the FP64 planes instead
+  const bool fp64 = SPLIT && *range != 0;
+  const int64_t ng = (g.Nh + Q - 1) / Q;
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ng; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = Q * t;
+    const uint32_t row = (uint32_t)q0 / (uint32_t)g.hx;
+    const int ih0 = (int)((uint32_t)q0 - row * (uint32_t)g.hx);
+    const int j = (int)(row % (uint32_t)g.ny), k = (int)(row / (uint32_t)g.ny);
+    const int cA = (j + k) & 1;  // colour of the even cell of every pair of the group
+    float acc[Q][2][3];
+    df dacc[Q][2][3];
+#pragma unroll
+    for (int p = 0; p < Q; ++p)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          acc[p][h][r] = 0.f;
+          dacc[p][h][r] = df{0.f, 0.f};
+        }
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      const int64_t off = sl == kZm ? -nxy : sl == kYm ? -(int64_t)g.nx : sl == kXm ? -1 : sl == kDiag ? 0
+                          : sl == kXp ? 1 : sl == kYp ? (int64_t)g.nx : nxy;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int col = h ? 1 - cA : cA;
+        const V* a = A + a2_index(g, col, sl * 9, q0);
+        // the 9 entries of the block of each of the Q pairs' cell h
+        float av[9][Q];
+        df dv[9];
+#pragma unroll
+        for (int rc = 0; rc < 9; ++rc) {
+          // one load of Q consecutive entries: q0 is a multiple of Q, and Q
+          // divides the 32 entries of a tile row, so the load is aligned to
+          // its own width
+          if constexpr (SPLIT) {
+            const float2 v2 = __ldcs(reinterpret_cast<const float2*>(a) + 32 * rc);
+            dv[rc] = df{v2.x, v2.y};
+          } else if constexpr (sizeof(V) == 4 && Q == 2) {
+            const float2 v2 = __ldcs(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(a) + 32 * rc));
+            av[rc][0] = v2.x;
+            av[rc][Q - 1] = v2.y;
+          } else if constexpr (sizeof(V) == 4) {
+            av[rc][0] = __ldcs(reinterpret_cast<const float*>(a) + 32 * rc);
+          } else if constexpr (Q == 4) {
+            const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(a) + 32 * rc));
+            av[rc][0] = __uint_as_float(u.x << 16);
+            av[rc][Q > 1 ? 1 : 0] = __uint_as_float(u.x & 0xffff0000u);
+            av[rc][Q > 2 ? 2 : 0] = __uint_as_float(u.y << 16);
+            av[rc][Q > 3 ? 3 : 0] = __uint_as_float(u.y & 0xffff0000u);
+          } else if constexpr (Q == 2) {
+            const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(reinterpret_cast<const __nv_bfloat16*>(a) + 32 * rc));
+            av[rc][0] = __uint_as_float(u << 16);
+            av[rc][Q - 1] = __uint_as_float(u & 0xffff0000u);
+          } else {
+            const unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(a) + 32 * rc);
+            av[rc][0] = __uint_as_float((unsigned)u << 16);
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < Q; ++p) {
+          if (q0 + p >= g.Nh) continue;
+          const int i = 2 * (ih0 + p) + h;
+          const bool ok = sl == kZm ? k > 0 : sl == kYm ? j > 0 : sl == kXm ? i > 0 : sl == kDiag ? true
+                          : sl == kXp ? i < g.nx - 1 : sl == kYp ? j < g.ny - 1 : k < g.nz - 1;
+          if (!ok) continue;
+          const int64_t nc = 2 * (q0 + p) + h + off;
+          const double x0 = __ldg(x + 3 * nc), x1 = __ldg(x + 3 * nc + 1), x2 = __ldg(x + 3 * nc + 2);
+          if (fp64) {
+            const double* a64 = A64 + plane(g, col, sl, 0) + q0 + p;
+            const size_t P = (size_t)g.Nh;
+            double d[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) d[r] = fma3(0.0, a64[3 * r * P], x0, a64[(3 * r + 1) * P], x1, a64[(3 * r + 2) * P], x2);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) dacc[p][h][r] = df_add(dacc[p][h][r], df_from(d[r]));
+          } else if constexpr (SPLIT) {
+            int bad = 0;
+            const float2 s0 = df_split_bits(x0, &bad), s1 = df_split_bits(x1, &bad), s2 = df_split_bits(x2, &bad);
+            const df d0{s0.x, s0.y}, d1{s1.x, s1.y}, d2{s2.x, s2.y};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              dacc[p][h][r] = df_fma_acc(dacc[p][h][r], dv[3 * r], d0);
+              dacc[p][h][r] = df_fma_acc(dacc[p][h][r], dv[3 * r + 1], d1);
+              dacc[p][h][r] = df_fma_acc(dacc[p][h][r], dv[3 * r + 2], d2);
+            }
+          } else {
+            const float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+              acc[p][h][r] = fma3(acc[p][h][r], av[3 * r][p], f0, av[3 * r + 1][p], f1, av[3 * r + 2][p], f2);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+      if (q0 + p >= g.Nh) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        double* yo = y + 3 * (2 * (q0 + p) + h);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const double v = alpha * (SPLIT ? df_to_double(df_renorm(dacc[p][h][r])) : (double)acc[p][h][r]);
+          yo[r] = beta == 0.0 ? v : v + beta * yo[r];
+        }
+      }
+    }
+  }
+}
+
+// the FP64 planes rounded to T in the tiled layout (the reduced-precision
+// copies the public SpMV reads)
+template <typename T>
+__global__ void k_to_tiled(Geom g, const double* __restrict__ src, T* __restrict__ dst) {
+  const size_t n = (size_t)126 * g.Nh;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i / g.Nh);  // plane: colour * 63 + slot * 9 + rc
+    const int64_t q = (int64_t)(i - (size_t)p * g.Nh);
+    const double v = src[i];
+    T o;
+    if constexpr (sizeof(T) == 2) o = __float2bfloat16_rn((float)v);
+    else o = (T)v;
+    dst[a2_index(g, p / 63, p % 63, q)] = o;
+  }
+}
+
 __global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = __float2bfloat16_rn((float)src[i]);
@@ -214,14 +359,44 @@ void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
 }
 
 void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
-  const int grid = grid_for(precision == BO_PREC_FP64 ? m->g.Nh : m->g.N, kThreads, 152 * 64);
-  if (precision == BO_PREC_FP32)
-    (k_spmv_nat<float, float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A32, x, y, alpha, beta), note_launch());
-  else if (precision == BO_PREC_BF16)
-    (k_spmv_nat<__nv_bfloat16, float><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A16, x, y, alpha, beta),
+  const Geom& g = m->g;
+  cudaStream_t s = m->ctx->stream;
+  if (precision == BO_PREC_FP32) {
+    const int Q = g.hx % 2 == 0 ? 2 : 1;
+    if (Q == 2)
+      (k_spmv_tiled<float, 2><<<grid_for((g.Nh + 1) / 2), kThreads, 0, s>>>(g, m->A32, x, y, alpha, beta, nullptr,
+                                                                              nullptr),
+       note_launch());
+    else
+      (k_spmv_tiled<float, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A32, x, y, alpha, beta, nullptr, nullptr),
+       note_launch());
+  } else if (precision == BO_PREC_BF16) {
+    if (g.hx % 4 == 0)
+      (k_spmv_tiled<__nv_bfloat16, 4><<<grid_for((g.Nh + 3) / 4), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta,
+                                                                                      nullptr, nullptr),
+       note_launch());
+    else if (g.hx % 2 == 0)
+      (k_spmv_tiled<__nv_bfloat16, 2><<<grid_for((g.Nh + 1) / 2), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta,
+                                                                                      nullptr, nullptr),
+       note_launch());
+    else
+      (k_spmv_tiled<__nv_bfloat16, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta, nullptr,
+                                                                             nullptr),
+       note_launch());
+  } else {
+    bo_mat* mm = const_cast<bo_mat*>(m);
+    if (!mm->a2_valid) launch_split_matrix(mm, s);
+    (k_spmv_tiled<float2, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A2, x, y, alpha, beta, m->A, m->a2_range),
      note_launch());
-  else
-    (k_spmv_nat<double, double><<<grid, kThreads, 0, m->ctx->stream>>>(m->g, m->A, x, y, alpha, beta), note_launch());
+  }
+}
+
+void launch_to_tiled_f32(const bo_mat* m, float* dst, cudaStream_t s) {
+  (k_to_tiled<float><<<grid_for((int64_t)63 * m->g.N), kThreads, 0, s>>>(m->g, m->A, dst), note_launch());
+}
+
+void launch_to_tiled_bf16(const bo_mat* m, __nv_bfloat16* dst, cudaStream_t s) {
+  (k_to_tiled<__nv_bfloat16><<<grid_for((int64_t)63 * m->g.N), kThreads, 0, s>>>(m->g, m->A, dst), note_launch());
 }
 
 void launch_split_matrix(bo_mat* m, cudaStream_t s) {

@@ -2,8 +2,11 @@
 the same seeded inputs, through the C ABI.
 
 Tolerances (derived from the arithmetic):
-  * FP64 SpMV: each output sums 21 products, so |y - y_ref| <= 21 eps
-    (|A| |x|)_i; tested at 1e-13 (|A| |x|)_i.
+  * FP64 SpMV (the public bo_mat_spmv reads the split copy of A and forms
+    the products in split pairs, like the Arnoldi product below): |y -
+    y_ref| <= 2e-13 (|A| |x|)_i; the decoupled SpMV, FP64 throughout: 21
+    products, 21 eps (|A| |x|)_i, tested at 1e-12 (its rows are rebuilt
+    from A and the weights).
   * FP32 matrix values: value rounding 2^-24 per entry -> <= 21 * 6e-8
     (|A| |x|)_i; tested at 1e-5 (|A| |x|)_i.
   * FP64 ILU / AMG / CPR applications: triangular and coarse solves amplify
@@ -87,7 +90,7 @@ def test_spmv_fp64_matches_oracle(bo, ctx, dims):
     x = np.random.default_rng(1).standard_normal(Ao.n)
     y = A.spmv(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
     ref = oracle.spmv(Ao, x)
-    assert np.all(np.abs(y - ref) <= 1e-13 * _absprod(Ao, x) + 1e-300)
+    assert np.all(np.abs(y - ref) <= 2e-13 * _absprod(Ao, x) + 1e-300)
 
 
 def test_spmv_fp32_and_alpha_beta(bo, ctx):
@@ -99,7 +102,7 @@ def test_spmv_fp32_and_alpha_beta(bo, ctx):
     ref = 2.0 * oracle.spmv(Ao, x) + 0.5 * y0
     bound = 2.0 * _absprod(Ao, x) + 0.5 * np.abs(y0)
     y = A.spmv(_dev(x), _dev(y0), alpha=2.0, beta=0.5).cpu().numpy()
-    assert np.all(np.abs(y - ref) <= 1e-13 * bound)
+    assert np.all(np.abs(y - ref) <= 2e-13 * bound)
     y32 = A.spmv(_dev(x), _dev(y0), alpha=2.0, beta=0.5, precision=bo.BO_PREC_FP32).cpu().numpy()
     assert np.all(np.abs(y32 - ref) <= 1e-5 * bound)
     # BF16 values (relative rounding 2^-9 per entry), x in FP32, FP32 sums of 21 terms
@@ -145,7 +148,7 @@ def test_csr_input_equals_bsr_input(bo, ctx):
     A = bo.Matrix.from_csr(ctx, bo.grid(*dims), np.array(rp, np.int32), np.array(cols, np.int32), np.array(vals))
     x = rng.standard_normal(Ao.n)
     y = A.spmv(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
-    assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x))
+    assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 2e-13 * _absprod(Ao, x))
 
 
 def test_device_inputs_and_value_update(bo, ctx):
@@ -157,7 +160,7 @@ def test_device_inputs_and_value_update(bo, ctx):
     A.update_values(a1["val"].ravel())
     x = np.random.default_rng(6).standard_normal(Ao1.n)
     y = A.spmv(_dev(x), torch.zeros(Ao1.n, dtype=torch.float64, device="cuda")).cpu().numpy()
-    assert np.all(np.abs(y - oracle.spmv(Ao1, x)) <= 1e-13 * _absprod(Ao1, x))
+    assert np.all(np.abs(y - oracle.spmv(Ao1, x)) <= 2e-13 * _absprod(Ao1, x))
 
 
 def test_input_errors_are_reported(bo, ctx):
@@ -285,6 +288,21 @@ def test_arnoldi_product_fp64_fallback_matches_oracle_elementwise(bo, ctx):
     x = np.random.default_rng(21).standard_normal(Ao.n)
     y = P.apply(bo.BO_STAGE_ARNOLDI_SPMV, _dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda"))
     assert np.all(np.abs(y.cpu().numpy() - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x) + 1e-300)
+
+
+def test_public_spmv_fp64_fallback_matches_oracle_elementwise(bo, ctx):
+    # a value below the split copy's range: the public FP64 SpMV reads the
+    # FP64 planes instead (21 products in FP64 plus the final split sum)
+    dims = (20, 20, 5)
+    a, _ = _sys(bogen.tiny_case(4))
+    val = a["val"].copy()
+    e = next(k for k in range(a["rowptr"][7], a["rowptr"][8]) if a["col"][k] != 7)
+    val[e][1, 2] = 1e-40
+    Ao = oracle.BsrMatrix(a["rowptr"], a["col"], val)
+    A = _mat(bo, ctx, dims, dict(a, val=val))
+    x = np.random.default_rng(22).standard_normal(Ao.n)
+    y = A.spmv(_dev(x), torch.zeros(Ao.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x) + 1e-300)
 
 
 @pytest.fixture(params=[2, 1, 0], ids=["cluster", "cooperative", "per_kernel"])
@@ -470,7 +488,7 @@ def test_solve_waterflood_1m_cells(bo, ctx, precision, waterflood_1m):
     # sampled SpMV outputs at full size
     xs = np.random.default_rng(12).standard_normal(Ao.n)
     y = A.spmv(_dev(xs), torch.zeros_like(b)).cpu().numpy()
-    assert np.all(np.abs(y - oracle.spmv(Ao, xs)) <= 1e-13 * _absprod(Ao, xs))
+    assert np.all(np.abs(y - oracle.spmv(Ao, xs)) <= 2e-13 * _absprod(Ao, xs))
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])

@@ -58,7 +58,8 @@ def test_residual_noalloc_matches_oracle_and_existing_entry_points(which):
         torch.cuda.synchronize()
         rg = r.cpu().numpy()
         assert np.all(np.abs(rg - r_or) <= bound)
-        assert np.all(np.abs(rg - r_pub.cpu().numpy()) <= 2 * bound)
+        # (the public SpMV forms its products in split pairs: 2e-13 (|A| |x|)_i)
+        assert np.all(np.abs(rg - r_pub.cpu().numpy()) <= 3 * bound)
         nr, nb = norms.cpu().numpy()
         assert nb == pytest.approx(np.linalg.norm(a["b"]), rel=1e-13)
         # | ||r|| - ||r_or|| | <= ||r - r_or|| <= ||bound|| (triangle inequality),
