@@ -164,7 +164,10 @@ int bo_mat_update_values(bo_mat* A, const double* val, int mem);
  * BO_PREC_BF16: a reduced-precision copy of the values (made on first use
  * after each value update), x rounded to FP32 on load, products and sums in
  * FP32, y written in FP64 (the reduced-storage matrix form of the
- * mixed-precision path).  beta = 0 never reads y. */
+ * mixed-precision path).  beta = 0 never reads y.  x and y on a 16-byte
+ * boundary (as cudaMalloc and framework allocations are) take the tiled
+ * kernels; otherwise the FP64 values with FP64 products are used whatever
+ * the precision. */
 int bo_mat_spmv(bo_mat* A, double alpha, const double* x, double beta, double* y, int precision);
 /* BO_ERR_ARG for NULL; see bo_ctx_destroy for lifetimes. */
 int bo_mat_destroy(bo_mat* A);

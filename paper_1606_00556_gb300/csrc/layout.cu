@@ -1,6 +1,8 @@
 // Matrix ingest (BSR / CSR -> colour-split planes), the public BSR SpMV
 // (paper Sec. 3.3: y = alpha A x + beta y), natural <-> internal vector
 // permutations and the Newton update (paper Alg. 1: x^l = x^{l-1} + dx).
+#include <cstdint>
+
 #include "bo_internal.cuh"
 
 namespace bo {
@@ -155,125 +157,192 @@ __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restr
 // itself, products and sums in split FP32 pairs (48 significant bits, x split
 // on load by integer operations), bound by HBM rather than by GB300's FP64
 // rate; V = float or __nv_bfloat16: the reduced-precision copies, FP32
-// products and sums.  A thread takes the cell pairs (2q, 2q + 1) of Q
-// consecutive half indices q of one grid row (the two cells of a pair have
-// the two colours), so each of its value loads is 8 bytes wide: Q = 1 split
-// pair, 2 floats or 4 BF16 values.  Needs hx % Q == 0 (the Q pairs share a
-// row).
+// products and sums.  A thread takes the 2Q cells of Q consecutive half
+// indices q0 .. q0 + Q - 1 of one grid row (cells 2 q0 .. 2 q0 + 2Q - 1; the
+// two cells of a half index have the two colours), so each of its value
+// loads is 8 bytes wide: Q = 1 split pair, 2 floats or 4 BF16 values.  Needs
+// hx % Q == 0 (then every group lies in one row and Nh % Q == 0).  x is read
+// as contiguous 16-byte pieces of each neighbouring row (the cells' own row
+// with one cell on each side, and the rows at -z, -y, +y, +z), y written
+// the same way.
+
+// the 3 entries of cell e of a row segment held in registers
+template <int M>
+__device__ __forceinline__ void seg3(const double (&s)[M], int e, double& x0, double& x1, double& x2) {
+  x0 = s[3 * e];
+  x1 = s[3 * e + 1];
+  x2 = s[3 * e + 2];
+}
+
+template <typename V, int Q>
+__device__ __forceinline__ void load_vals(const V* a, float (&av)[9][Q], df (&dv)[9]) {
+  // one load of Q consecutive entries per block entry: q0 is a multiple of
+  // Q, and Q divides the 32 entries of a tile row, so the load is aligned to
+  // its own width
+#pragma unroll
+  for (int rc = 0; rc < 9; ++rc) {
+    if constexpr (sizeof(V) == 8) {
+      const float2 v2 = __ldcs(reinterpret_cast<const float2*>(a) + 32 * rc);
+      dv[rc] = df{v2.x, v2.y};
+    } else if constexpr (sizeof(V) == 4 && Q == 2) {
+      const float2 v2 = __ldcs(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(a) + 32 * rc));
+      av[rc][0] = v2.x;
+      av[rc][Q - 1] = v2.y;
+    } else if constexpr (sizeof(V) == 4) {
+      av[rc][0] = __ldcs(reinterpret_cast<const float*>(a) + 32 * rc);
+    } else if constexpr (Q == 4) {
+      const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(a) + 32 * rc));
+      av[rc][0] = __uint_as_float(u.x << 16);
+      av[rc][Q > 1 ? 1 : 0] = __uint_as_float(u.x & 0xffff0000u);
+      av[rc][Q > 2 ? 2 : 0] = __uint_as_float(u.y << 16);
+      av[rc][Q > 3 ? 3 : 0] = __uint_as_float(u.y & 0xffff0000u);
+    } else if constexpr (Q == 2) {
+      const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(reinterpret_cast<const __nv_bfloat16*>(a) + 32 * rc));
+      av[rc][0] = __uint_as_float(u << 16);
+      av[rc][Q - 1] = __uint_as_float(u & 0xffff0000u);
+    } else {
+      const unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(a) + 32 * rc);
+      av[rc][0] = __uint_as_float((unsigned)u << 16);
+    }
+  }
+}
+
 template <typename V, int Q>
 __global__ void __launch_bounds__(kThreads) k_spmv_tiled(Geom g, const V* __restrict__ A, const double* __restrict__ x,
                                                         double* __restrict__ y, double alpha, double beta,
                                                         const double* __restrict__ A64, const int* __restrict__ range) {
   constexpr bool SPLIT = sizeof(V) == 8;
+  constexpr int C = 2 * Q;  // cells of a group
   // a split copy that could not hold every value: the FP64 planes instead
   const bool fp64 = SPLIT && *range != 0;
-  const int64_t ng = (g.Nh + Q - 1) / Q;
+  const int64_t ng = g.Nh / Q;
   const int64_t nxy = (int64_t)g.nx * g.ny;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ng; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q0 = Q * t;
     const uint32_t row = (uint32_t)q0 / (uint32_t)g.hx;
-    const int ih0 = (int)((uint32_t)q0 - row * (uint32_t)g.hx);
+    const int i0 = 2 * (int)((uint32_t)q0 - row * (uint32_t)g.hx);
     const int j = (int)(row % (uint32_t)g.ny), k = (int)(row / (uint32_t)g.ny);
-    const int cA = (j + k) & 1;  // colour of the even cell of every pair of the group
-    float acc[Q][2][3];
-    df dacc[Q][2][3];
+    const int cA = (j + k) & 1;  // colour of the even cells of the group
+    const int64_t c0 = 2 * q0;
+    float acc[C][3];
+    df dacc[C][3];
 #pragma unroll
-    for (int p = 0; p < Q; ++p)
+    for (int e = 0; e < C; ++e)
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int r = 0; r < 3; ++r) {
+        acc[e][r] = 0.f;
+        dacc[e][r] = df{0.f, 0.f};
+      }
+    // add the block of slot sl (colour of cell e) times (x0, x1, x2) to cell e
+    auto add = [&](int e, const float (&av)[9][Q], const df (&dv)[9], int sl, int col, double x0, double x1,
+                   double x2) {
+      if (fp64) {
+        const double* a64 = A64 + plane(g, col, sl, 0) + q0 + e / 2;
+        const size_t P = (size_t)g.Nh;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          dacc[e][r] = df_add(dacc[e][r], df_from(fma3(0.0, a64[3 * r * P], x0, a64[(3 * r + 1) * P], x1,
+                                                       a64[(3 * r + 2) * P], x2)));
+      } else if constexpr (SPLIT) {
+        int bad = 0;
+        const float2 s0 = df_split_bits(x0, &bad), s1 = df_split_bits(x1, &bad), s2 = df_split_bits(x2, &bad);
+        const df d0{s0.x, s0.y}, d1{s1.x, s1.y}, d2{s2.x, s2.y};
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-          acc[p][h][r] = 0.f;
-          dacc[p][h][r] = df{0.f, 0.f};
+          dacc[e][r] = df_fma_acc(dacc[e][r], dv[3 * r], d0);
+          dacc[e][r] = df_fma_acc(dacc[e][r], dv[3 * r + 1], d1);
+          dacc[e][r] = df_fma_acc(dacc[e][r], dv[3 * r + 2], d2);
         }
+      } else {
+        const int p = e / 2;
+        const float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
 #pragma unroll
-    for (int sl = 0; sl < 7; ++sl) {
-      const int64_t off = sl == kZm ? -nxy : sl == kYm ? -(int64_t)g.nx : sl == kXm ? -1 : sl == kDiag ? 0
-                          : sl == kXp ? 1 : sl == kYp ? (int64_t)g.nx : nxy;
+        for (int r = 0; r < 3; ++r)
+          acc[e][r] = fma3(acc[e][r], av[3 * r][p], f0, av[3 * r + 1][p], f1, av[3 * r + 2][p], f2);
+      }
+    };
+    float av[2][9][Q];
+    df dv[2][9];
+    // rows at -z, -y, +y, +z: the C cells directly across, 3 C contiguous
+    // doubles starting at an even index (16-byte aligned)
+#pragma unroll
+    for (int which = 0; which < 4; ++which) {
+      const int sl = which == 0 ? kZm : which == 1 ? kYm : which == 2 ? kYp : kZp;
+      const bool ok = which == 0 ? k > 0 : which == 1 ? j > 0 : which == 2 ? j < g.ny - 1 : k < g.nz - 1;
+      if (!ok) continue;
+      const int64_t off = which == 0 ? -nxy : which == 1 ? -(int64_t)g.nx : which == 2 ? (int64_t)g.nx : nxy;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int col = h ? 1 - cA : cA;
-        const V* a = A + a2_index(g, col, sl * 9, q0);
-        // the 9 entries of the block of each of the Q pairs' cell h
-        float av[9][Q];
-        df dv[9];
+        load_vals<V, Q>(A + a2_index(g, col, sl * 9, q0), av[h], dv[h]);
+      }
+      double xs[3 * C];
+      const double2* xp = reinterpret_cast<const double2*>(x + 3 * (c0 + off));
 #pragma unroll
-        for (int rc = 0; rc < 9; ++rc) {
-          // one load of Q consecutive entries: q0 is a multiple of Q, and Q
-          // divides the 32 entries of a tile row, so the load is aligned to
-          // its own width
-          if constexpr (SPLIT) {
-            const float2 v2 = __ldcs(reinterpret_cast<const float2*>(a) + 32 * rc);
-            dv[rc] = df{v2.x, v2.y};
-          } else if constexpr (sizeof(V) == 4 && Q == 2) {
-            const float2 v2 = __ldcs(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(a) + 32 * rc));
-            av[rc][0] = v2.x;
-            av[rc][Q - 1] = v2.y;
-          } else if constexpr (sizeof(V) == 4) {
-            av[rc][0] = __ldcs(reinterpret_cast<const float*>(a) + 32 * rc);
-          } else if constexpr (Q == 4) {
-            const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(a) + 32 * rc));
-            av[rc][0] = __uint_as_float(u.x << 16);
-            av[rc][Q > 1 ? 1 : 0] = __uint_as_float(u.x & 0xffff0000u);
-            av[rc][Q > 2 ? 2 : 0] = __uint_as_float(u.y << 16);
-            av[rc][Q > 3 ? 3 : 0] = __uint_as_float(u.y & 0xffff0000u);
-          } else if constexpr (Q == 2) {
-            const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(reinterpret_cast<const __nv_bfloat16*>(a) + 32 * rc));
-            av[rc][0] = __uint_as_float(u << 16);
-            av[rc][Q - 1] = __uint_as_float(u & 0xffff0000u);
-          } else {
-            const unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(a) + 32 * rc);
-            av[rc][0] = __uint_as_float((unsigned)u << 16);
-          }
+      for (int u = 0; u < 3 * C / 2; ++u) {
+        const double2 v = __ldg(xp + u);
+        xs[2 * u] = v.x;
+        xs[2 * u + 1] = v.y;
+      }
+#pragma unroll
+      for (int e = 0; e < C; ++e) {
+        double x0, x1, x2;
+        seg3(xs, e, x0, x1, x2);
+        add(e, av[e & 1], dv[e & 1], sl, (e & 1) ? 1 - cA : cA, x0, x1, x2);
+      }
+    }
+    // the cells' own row: -x, diag, +x from the C cells and one on each side
+    {
+      double xs[3 * (C + 2)];  // cells c0 - 1 .. c0 + C
+      const double2* xp = reinterpret_cast<const double2*>(x + 3 * c0);
+#pragma unroll
+      for (int u = 0; u < 3 * C / 2; ++u) {
+        const double2 v = __ldg(xp + u);
+        xs[3 + 2 * u] = v.x;
+        xs[3 + 2 * u + 1] = v.y;
+      }
+      const bool has_l = i0 > 0, has_r = i0 + C < g.nx;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        xs[m] = has_l ? __ldg(x + 3 * (c0 - 1) + m) : 0.0;
+        xs[3 * (C + 1) + m] = has_r ? __ldg(x + 3 * (c0 + C) + m) : 0.0;
+      }
+#pragma unroll
+      for (int which = 0; which < 3; ++which) {
+        const int sl = which == 0 ? kXm : which == 1 ? kDiag : kXp;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = h ? 1 - cA : cA;
+          load_vals<V, Q>(A + a2_index(g, col, sl * 9, q0), av[h], dv[h]);
         }
 #pragma unroll
-        for (int p = 0; p < Q; ++p) {
-          if (q0 + p >= g.Nh) continue;
-          const int i = 2 * (ih0 + p) + h;
-          const bool ok = sl == kZm ? k > 0 : sl == kYm ? j > 0 : sl == kXm ? i > 0 : sl == kDiag ? true
-                          : sl == kXp ? i < g.nx - 1 : sl == kYp ? j < g.ny - 1 : k < g.nz - 1;
-          if (!ok) continue;
-          const int64_t nc = 2 * (q0 + p) + h + off;
-          const double x0 = __ldg(x + 3 * nc), x1 = __ldg(x + 3 * nc + 1), x2 = __ldg(x + 3 * nc + 2);
-          if (fp64) {
-            const double* a64 = A64 + plane(g, col, sl, 0) + q0 + p;
-            const size_t P = (size_t)g.Nh;
-            double d[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) d[r] = fma3(0.0, a64[3 * r * P], x0, a64[(3 * r + 1) * P], x1, a64[(3 * r + 2) * P], x2);
-#pragma unroll
-            for (int r = 0; r < 3; ++r) dacc[p][h][r] = df_add(dacc[p][h][r], df_from(d[r]));
-          } else if constexpr (SPLIT) {
-            int bad = 0;
-            const float2 s0 = df_split_bits(x0, &bad), s1 = df_split_bits(x1, &bad), s2 = df_split_bits(x2, &bad);
-            const df d0{s0.x, s0.y}, d1{s1.x, s1.y}, d2{s2.x, s2.y};
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              dacc[p][h][r] = df_fma_acc(dacc[p][h][r], dv[3 * r], d0);
-              dacc[p][h][r] = df_fma_acc(dacc[p][h][r], dv[3 * r + 1], d1);
-              dacc[p][h][r] = df_fma_acc(dacc[p][h][r], dv[3 * r + 2], d2);
-            }
-          } else {
-            const float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-              acc[p][h][r] = fma3(acc[p][h][r], av[3 * r][p], f0, av[3 * r + 1][p], f1, av[3 * r + 2][p], f2);
-          }
+        for (int e = 0; e < C; ++e) {
+          const int nb = e + (which == 0 ? -1 : which == 1 ? 0 : 1);  // neighbour within the segment
+          if (which == 0 && e == 0 && !has_l) continue;
+          if (which == 2 && e == C - 1 && !has_r) continue;
+          double x0, x1, x2;
+          seg3(xs, nb + 1, x0, x1, x2);
+          add(e, av[e & 1], dv[e & 1], sl, (e & 1) ? 1 - cA : cA, x0, x1, x2);
         }
       }
     }
+    // y: 3 C contiguous doubles from an even index
+    double ys[3 * C];
 #pragma unroll
-    for (int p = 0; p < Q; ++p) {
-      if (q0 + p >= g.Nh) continue;
+    for (int e = 0; e < C; ++e)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        double* yo = y + 3 * (2 * (q0 + p) + h);
+      for (int r = 0; r < 3; ++r)
+        ys[3 * e + r] = alpha * (SPLIT ? df_to_double(df_renorm(dacc[e][r])) : (double)acc[e][r]);
+    double2* yp = reinterpret_cast<double2*>(y + 3 * c0);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const double v = alpha * (SPLIT ? df_to_double(df_renorm(dacc[p][h][r])) : (double)acc[p][h][r]);
-          yo[r] = beta == 0.0 ? v : v + beta * yo[r];
-        }
+    for (int u = 0; u < 3 * C / 2; ++u) {
+      double2 v = make_double2(ys[2 * u], ys[2 * u + 1]);
+      if (beta != 0.0) {
+        const double2 o = yp[u];
+        v.x += beta * o.x;
+        v.y += beta * o.y;
       }
+      yp[u] = v;
     }
   }
 }
@@ -361,6 +430,13 @@ void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
 void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
   const Geom& g = m->g;
   cudaStream_t s = m->ctx->stream;
+  if ((((uintptr_t)x) | ((uintptr_t)y)) & 15) {
+    // vectors off a 16-byte boundary: the tiled kernels read and write them
+    // 16 bytes at a time, so the FP64 planes with scalar accesses instead
+    (k_spmv_nat<double, double><<<grid_for(g.Nh, kThreads, 152 * 64), kThreads, 0, s>>>(g, m->A, x, y, alpha, beta),
+     note_launch());
+    return;
+  }
   if (precision == BO_PREC_FP32) {
     const int Q = g.hx % 2 == 0 ? 2 : 1;
     if (Q == 2)

@@ -119,6 +119,21 @@ def test_spmv_fp32_and_alpha_beta(bo, ctx):
         assert np.all(np.abs(y2 - ref2) <= tol * b2)
 
 
+def test_spmv_on_unaligned_vectors_uses_fp64_values(bo, ctx):
+    # x and y 8 bytes off a 16-byte boundary: the FP64 planes, FP64 products
+    dims = (6, 5, 3)
+    a, Ao = _random_bsr(*dims, seed=23)
+    A = _mat(bo, ctx, dims, a)
+    x = np.random.default_rng(24).standard_normal(Ao.n)
+    xb = torch.zeros(Ao.n + 1, dtype=torch.float64, device="cuda")
+    xb[1:] = _dev(x)
+    yb = torch.zeros(Ao.n + 1, dtype=torch.float64, device="cuda")
+    for prec in (bo.BO_PREC_FP64, bo.BO_PREC_FP32, bo.BO_PREC_BF16):
+        A.spmv(xb[1:], yb[1:], precision=prec)
+        y = yb[1:].cpu().numpy()
+        assert np.all(np.abs(y - oracle.spmv(Ao, x)) <= 1e-13 * _absprod(Ao, x) + 1e-300)
+
+
 def test_spmv_beta_zero_ignores_nan_in_y(bo, ctx):
     a, Ao = _random_bsr(4, 3, 2, 0)
     A = _mat(bo, ctx, (4, 3, 2), a)
