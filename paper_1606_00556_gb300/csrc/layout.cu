@@ -447,11 +447,7 @@ void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta
       (k_spmv_tiled<float, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A32, x, y, alpha, beta, nullptr, nullptr),
        note_launch());
   } else if (precision == BO_PREC_BF16) {
-    if (g.hx % 4 == 0)
-      (k_spmv_tiled<__nv_bfloat16, 4><<<grid_for((g.Nh + 3) / 4), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta,
-                                                                                      nullptr, nullptr),
-       note_launch());
-    else if (g.hx % 2 == 0)
+    if (g.hx % 2 == 0)
       (k_spmv_tiled<__nv_bfloat16, 2><<<grid_for((g.Nh + 1) / 2), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta,
                                                                                       nullptr, nullptr),
        note_launch());
