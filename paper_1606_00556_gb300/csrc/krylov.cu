@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
 // arithmetic (the coefficients rounded to split pairs once per block, each
 // entry's sum carried as a split pair and renormalised once), four entries
-// per thread.  In the final pass (LAST) ||w||^2 is reduced and the last
-// block applies the Givens step to h1 + h2 and stores 1/||w|| as the
+// per thread.  In the final pass (LAST) ||w||^2 is reduced in FP64 and the
+// last block applies the Givens step to h1 + h2 and stores 1/||w|| as the
 // new column's scale (w itself stays unnormalised).
 template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* __restrict__ V, int64_t ldv,
@@ -398,10 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
   const int64_t ng = (n + 3) >> 2;
   for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[off + k] * st->vscale[k]));
   __syncthreads();
-  // ||w||^2 from the high parts in FP32 per thread (FP64 across threads):
-  // its 1e-7 relative accuracy only sets how close to unit length the next
-  // basis vector is, since the same ||w|| is both its scale and h_{j+1,j}
-  float acc32 = 0.f;
+  double acc = 0.0;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ng; q += (int64_t)gridDim.x * blockDim.x) {
     const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
     df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
@@ -431,12 +428,13 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
       }
     }
     if (LAST) {
-      const float h1 = valid > 1 ? s1.hi : 0.f, h2 = valid > 2 ? s2.hi : 0.f, h3 = valid > 3 ? s3.hi : 0.f;
-      acc32 = fmaf(h3, h3, fmaf(h2, h2, fmaf(h1, h1, fmaf(s0.hi, s0.hi, acc32))));
+      const double d0 = df_to_double(s0), d1 = valid > 1 ? df_to_double(s1) : 0.0,
+                   d2 = valid > 2 ? df_to_double(s2) : 0.0, d3 = valid > 3 ? df_to_double(s3) : 0.0;
+      acc = fma(d3, d3, fma(d2, d2, fma(d1, d1, fma(d0, d0, acc))));
     }
   }
   if (!LAST) return;
-  double acc = block_sum((double)acc32, sh);
+  acc = block_sum(acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
   if (!last_block(&st->counter[3], gridDim.x)) return;
   const double hn2 = reduce_partials(partials, gridDim.x, sh);
