@@ -315,6 +315,100 @@ def _make_ensemble_member(spec):
     return a["rowptr"], a["col"], a["val"].reshape(-1), a["b"]
 
 
+def _make_dual_member(spec):
+    from bogen import dual as D
+    a = D.assemble_dual(D.dual_case(spec["seed"], *spec["dims"], sigma_k=spec["sigma"]))
+    return a["rowptr"], a["col"], a["val"].reshape(-1), a["b"]
+
+
+def ensemble_inputs(n, procs, dual=False):
+    """The ensemble's seeded realisations (spawned workers; before any CUDA
+    call): specs and per realisation (rowptr, col, val, b)."""
+    import bogen
+    bogen.build()
+    specs = bogen.ensemble_specs(n=n)
+    with mp.get_context("spawn").Pool(max(1, min(16, procs))) as pool:
+        data = pool.map(_make_dual_member if dual else _make_ensemble_member, specs)
+    return specs, data
+
+
+def ensemble_record(bo, ctx, dev, specs, data, steps, warmup, restart=30, launch="auto", dual=False):
+    """A step re-ingests every realisation's values, refreshes its FP32
+    preconditioner and solves all realisations together (bo_solve_batched,
+    or bo_dp_solve_batched for the dual-porosity variant); a realisation
+    whose FP32-preconditioned solve stalls is solved again with an FP64
+    preconditioner (promotion).  Returns the record (solves/s, p50/p99 of
+    the per-realisation times, iterations)."""
+    import torch
+    mats, precs, vals, bs, xs, dps = [], [], [], [], [], []
+    for sp, (rp, cl, v, b) in zip(specs, data):
+        if dual:
+            dp = bo.DualPorosity(ctx, *sp["dims"], rp, cl, v)
+            dps.append(dp)
+            A = dp.fracture_matrix
+        else:
+            A = bo.Matrix.from_bsr(ctx, bo.grid(*sp["dims"]), rp, cl, v)
+        mats.append(A)
+        precs.append(bo.Preconditioner(A, precision=bo.BO_PREC_FP32))
+        vals.append(torch.from_numpy(v).to(dev))
+        bs.append(torch.from_numpy(b).to(dev))
+        xs.append(torch.zeros(b.size, dtype=torch.float64, device=dev))
+    tuned = None
+    if not dual and launch == "auto":
+        cache = os.path.join(ROOT, "paper_1606_00556_gb300", "_build", "tune_cache.json")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tuned = bo.bo_autotune_batched(precs, bs, xs, cache_path=cache, restart=restart, maxit=1000)
+    fallback = {}
+
+    def step():
+        if dual:
+            for dp, P, v in zip(dps, precs, vals):
+                dp.update_values(v)
+                P.update()
+            rc, infos = bo.bo_dp_solve_batched(dps, precs, bs, xs, tol=1e-8, restart=restart, maxit=1000)
+        else:
+            bo.bo_update_batched(precs, vals)
+            rc, infos = bo.bo_solve_batched(precs, bs, xs, tol=1e-8, restart=restart, maxit=1000)
+        for r, i in enumerate(infos):
+            if i["status"] != 0:
+                if r not in fallback:
+                    fallback[r] = bo.Preconditioner(mats[r], precision=bo.BO_PREC_FP64)
+                else:
+                    fallback[r].update()
+                if dual:
+                    i2 = dps[r].solve(fallback[r], bs[r], xs[r], tol=1e-8, restart=restart, maxit=1000,
+                                      raise_on_error=False)
+                else:
+                    i2 = fallback[r].solve(bs[r], xs[r], tol=1e-8, restart=restart, maxit=1000, raise_on_error=False)
+                i2["promoted"] = True
+                infos[r] = i2
+        return infos
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    all_infos = [step() for _ in range(steps)]
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    per = sorted(i["solve_ms"] for infos in all_infos for i in infos)
+    its = [i["iters"] for i in all_infos[-1]]
+    unknowns = sum((6 if dual else 3) * int(np.prod(sp["dims"])) for sp in specs)
+    rec = {"value": len(specs) * steps / el, "unit": "solves/s", "steps": steps, "warmup": warmup,
+           "ms_per_step": el * 1e3 / steps, "realisations": len(specs), "unknowns": unknowns,
+           "variant": ("dual porosity (fracture + matrix node per cell, shape factor 0.1 ft^-2), matrix unknowns "
+                       "condensed, fracture systems solved together" if dual else "single porosity"),
+           "per_realisation_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+           "iters": {"min": min(its), "mean": float(np.mean(its)), "max": max(its)},
+           "true_rel_res_max": max(i["true_rel_res"] for infos in all_infos for i in infos),
+           "failed": sum(i["status"] != 0 for infos in all_infos for i in infos),
+           "promoted_to_fp64": sorted(fallback.keys()), "tuned": tuned,
+           "grids": "nx,ny in 32..96 (nx even), nz in 8..24, sigma 0.5..2.0, seed 7"}
+    for P in list(precs) + list(fallback.values()):
+        P.close()
+    return rec
+
+
 def run_ensemble(args):
     """The batched-ensemble workload: 256 seeded realisations of uneven grid
     size (32..96 x 32..96 x 8..24 cells, 38.3M unknowns in all) solved
@@ -700,6 +794,9 @@ def main():
     ap.add_argument("--sequence", default="newton", choices=["newton", "synthetic"],
                     help="the 1M-cell Jacobians of successive days: advanced by the device Newton method "
                          "(default), or the generator's synthetic fronts")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the 256-realisation ensembles (single and dual porosity) of the default line")
+    ap.add_argument("--ensemble-steps", type=int, default=3, help="timed steps of each ensemble in the default line")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the 256x256x128 (8.4M-cell) mixed-precision Jacobian")
     ap.add_argument("--mixed-steps", type=int, default=3, help="timed solves per precision at 256x256x128")
@@ -755,6 +852,10 @@ def main():
         case0 = bogen.waterflood_case(*dims, seed=rank_seed(rank), day=0)
         a = bogen.assemble(case0)
         jac = [(a["rowptr"], a["col"], a["val"].reshape(-1), a["b"], case0.x)]
+    ens_in = dual_in = None
+    if rank == 0 and not args.no_ensemble:
+        ens_in = ensemble_inputs(args.ensemble, os.cpu_count() or 1)
+        dual_in = ensemble_inputs(args.ensemble, os.cpu_count() or 1, dual=True)
     mix_a = None
     if mixed:
         import bogen
@@ -964,6 +1065,14 @@ def main():
     if mix_a is not None:
         mixed_rec, mixed_x = run_mixed(bo, ctx, dev, stream, mix_a, args)
         del mix_a
+    ens_rec = dual_rec = None
+    if ens_in is not None:
+        # the batched ensembles (configs of 256 realisations, 38M unknowns)
+        ens_rec = ensemble_record(bo, ctx, dev, *ens_in, steps=args.ensemble_steps, warmup=1, restart=args.restart)
+        del ens_in
+        dual_rec = ensemble_record(bo, ctx, dev, *dual_in, steps=args.ensemble_steps, warmup=1,
+                                   restart=args.restart, dual=True)
+        del dual_in
     if ref_async is not None:
         xr8, info_r8, sec_r8 = ref_async.get()
         ref_pool.close()
@@ -987,6 +1096,7 @@ def main():
                          "avg_us": avg_s * 1e6 if avg_s else None, "launches": spmv_n},
             "spmv": sp, "spmv_cpu": cpu_spmv, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e,
             "errors": errors or None, "mixed_256x256x128": mixed_rec, "newton_sequence": newton_rec,
+            "ensemble": ens_rec, "ensemble_dual_porosity": dual_rec,
             "precision_note": ("no all-FP64 path is timed: even the FP64 preconditioner form computes the Arnoldi "
                                "product in split FP32 pairs (2^-46 relative per term); convergence is decided "
                                "on the FP64 true residual of the original system"),

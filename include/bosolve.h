@@ -473,6 +473,16 @@ bo_mat* bo_dp_fracture_matrix(bo_dp* dp);
  * passes' iterations and reports the full system's true_rel_res; returns
  * BO_OK or BO_ERR_NOT_CONVERGED (x then holds the last iterate). */
 int bo_dp_solve(bo_dp* dp, bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
+/* Solve nreal dual-porosity systems at once (an ensemble of dual-porosity
+ * realisations; no counterpart in the paper): every system condensed onto
+ * its fracture nodes, the condensed systems solved together as
+ * bo_solve_batched does (P[r] set up on bo_dp_fracture_matrix(dp[r])), the
+ * matrix unknowns recovered, and each full FP64 residual checked; a system
+ * that rounding left above tol is solved again alone as bo_dp_solve does.
+ * b, x: device arrays of 6 N_r doubles.  infos (may be NULL) per system;
+ * returns BO_OK or the first failing status.  Synchronises. */
+int bo_dp_solve_batched(bo_dp* const* dp, bo_prec* const* P, int nreal, const double* const* b, double* const* x,
+                        const bo_solve_opts* opts, bo_solve_info* infos);
 int bo_dp_destroy(bo_dp* dp);
 
 /* ---------------------------------------------------------------------------

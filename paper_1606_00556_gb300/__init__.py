@@ -53,7 +53,8 @@ EXPORTS = (
     "bo_cnn_get_grads", "bo_cnn_forward", "bo_cnn_backward", "bo_cnn_adam_step",
     "bo_conv3d_forward", "bo_conv3d_backward_data", "bo_conv3d_backward_weights",
     "bo_prec_set_coarse_space", "bo_learned_coarse_space", "bo_learned_guess",
-    "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_destroy",
+    "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_solve_batched",
+    "bo_dp_destroy",
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
     "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins",
     "bo_newton_opts_default", "bo_model_create", "bo_model_destroy", "bo_model_assemble", "bo_newton_solve",
@@ -204,6 +205,9 @@ def lib():
         L.bo_dp_fracture_matrix.argtypes = [_VP]
         L.bo_dp_solve.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
         L.bo_dp_destroy.argtypes = [_VP]
+        L.bo_dp_solve_batched.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
+                                          ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(bo_solve_opts),
+                                          ctypes.POINTER(bo_solve_info)]
         L.bo_prec_set_launch_mode.argtypes = [_VP, _i]
         L.bo_set_batch_streams.argtypes = [_i]
         L.bo_set_conv_engine.argtypes = [_i]
@@ -626,6 +630,25 @@ def bo_solve_batched(precs, bs, xs, tol=1e-8, restart=30, maxit=500, x0_is_zero=
         d = i.as_dict()
         out.append(d)
     return rc, out
+
+
+def bo_dp_solve_batched(dps, precs, bs, xs, tol=1e-8, restart=30, maxit=500, x0_is_zero=True):
+    """bo_dp_solve_batched: the dual-porosity systems dps[r] with
+    preconditioners precs[r] (on their fracture matrices), device vectors
+    bs[r], xs[r] of 6 N_r doubles.  Returns (status, list of info dicts)."""
+    n = len(dps)
+    if not (len(precs) == len(bs) == len(xs) == n) or n < 1:
+        raise BoArgError("bo_dp_solve_batched: lists of different lengths")
+    D = (_VP * n)(*[d.h for d in dps])
+    P = (_VP * n)(*[p.h for p in precs])
+    B = (_VP * n)(*[_dvec(b, 2 * d.N * 3, "b", d.ctx) for b, d in zip(bs, dps)])
+    X = (_VP * n)(*[_dvec(x, 2 * d.N * 3, "x", d.ctx) for x, d in zip(xs, dps)])
+    o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
+    infos = (bo_solve_info * n)()
+    rc = lib().bo_dp_solve_batched(D, P, n, B, X, ctypes.byref(o), infos)
+    if rc not in (BO_OK, BO_ERR_NOT_CONVERGED):
+        raise BoError(rc, "bo_dp_solve_batched")
+    return rc, [i.as_dict() for i in infos]
 
 
 def bo_update_batched(precs, vals=None):

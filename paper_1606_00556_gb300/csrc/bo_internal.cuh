@@ -508,8 +508,12 @@ void ctx_release_ref(bo_ctx* c);
 // krylov.cu
 int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
 int bicgstab(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
+// tols: per-system tolerances replacing o->tol (NULL: o->tol for all)
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
-                   bo_solve_info* infos);
+                   bo_solve_info* infos, const double* tols = nullptr);
+// capi.cu: the batched solve on the stream pool (argument checks done)
+int solve_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts& o,
+                  bo_solve_info* infos, const double* tols);
 int krylov_alloc(bo_prec* P, int m);
 // w = A v (internal order, FP64 in and out) by the FGMRES Arnoldi product
 // (split copy of A, v split into pairs; the FP64 planes where the split copy

@@ -219,6 +219,39 @@ int prec_refresh(bo_prec* P) {
 
 }  // namespace
 
+namespace bo {
+int solve_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts& o,
+                  bo_solve_info* infos, const double* tols) {
+  const int dev = P[0]->mat->ctx->device;
+  if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
+  std::vector<cudaStream_t> pool;
+  if (!stream_pool(dev, pool)) return BO_ERR_CUDA;
+  constexpr int kPool = kMaxPoolStreams;
+  // order the batch after everything already queued on the contexts' streams,
+  // and the contexts' streams after the batch
+  std::vector<cudaEvent_t> evs;
+  auto join = [&](cudaStream_t from, cudaStream_t to) {
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventRecord(e, from);
+    cudaStreamWaitEvent(to, e, 0);
+    evs.push_back(e);
+  };
+  const int width = std::min(kPool, std::max(1, g_pool_width.load()));
+  const int S = nreal < width ? nreal : width;
+  for (int r = 0; r < nreal; ++r) join(P[r]->mat->ctx->stream, pool[r % S]);
+  for (int r = 0; r < nreal; ++r) P[r]->stream = pool[r % S];
+  const int rc = fgmres_batched(P, nreal, b, x, &o, infos, tols);
+  for (int r = 0; r < nreal; ++r) {
+    join(pool[r % S], P[r]->mat->ctx->stream);
+    P[r]->stream = P[r]->mat->ctx->stream;
+  }
+  for (int r = 0; r < S; ++r) cudaStreamSynchronize(pool[r]);
+  for (auto e : evs) cudaEventDestroy(e);
+  return rc;
+}
+}  // namespace bo
+
 extern "C" {
 
 const char* bo_status_str(int s) {
@@ -455,32 +488,7 @@ int bo_solve_batched(bo_prec* const* P, int nreal, const double* const* b, doubl
     for (int q = 0; q < r; ++q)
       if (P[q] == P[r]) return BO_ERR_ARG;  // each solve needs its own workspace
   }
-  if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
-  std::vector<cudaStream_t> pool;
-  if (!stream_pool(dev, pool)) return BO_ERR_CUDA;
-  constexpr int kPool = kMaxPoolStreams;
-  // order the batch after everything already queued on the contexts' streams,
-  // and the contexts' streams after the batch
-  std::vector<cudaEvent_t> evs;
-  auto join = [&](cudaStream_t from, cudaStream_t to) {
-    cudaEvent_t e;
-    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    cudaEventRecord(e, from);
-    cudaStreamWaitEvent(to, e, 0);
-    evs.push_back(e);
-  };
-  const int width = std::min(kPool, std::max(1, g_pool_width.load()));
-  const int S = nreal < width ? nreal : width;
-  for (int r = 0; r < nreal; ++r) join(P[r]->mat->ctx->stream, pool[r % S]);
-  for (int r = 0; r < nreal; ++r) P[r]->stream = pool[r % S];
-  const int rc = fgmres_batched(P, nreal, b, x, &o, infos);
-  for (int r = 0; r < nreal; ++r) {
-    join(pool[r % S], P[r]->mat->ctx->stream);
-    P[r]->stream = P[r]->mat->ctx->stream;
-  }
-  for (int r = 0; r < S; ++r) cudaStreamSynchronize(pool[r]);
-  for (auto e : evs) cudaEventDestroy(e);
-  return rc;
+  return bo::solve_batched(P, nreal, b, x, o, infos, nullptr);
 }
 
 int bo_update_batched(bo_prec* const* P, int nreal, const double* const* val, int mem) {

@@ -423,6 +423,85 @@ int bo_dp_solve(bo_dp* d, bo_prec* P, const double* b, double* x, const bo_solve
   return acc.status;
 }
 
+int bo_dp_solve_batched(bo_dp* const* dps, bo_prec* const* P, int nreal, const double* const* b, double* const* x,
+                        const bo_solve_opts* opts, bo_solve_info* infos) {
+  if (!dps || !P || !b || !x || !opts || nreal < 1) return BO_ERR_ARG;
+  if (!(opts->tol > 0.0) || opts->restart < 1 || opts->restart > 64 || opts->maxit < 0) return BO_ERR_ARG;
+  const int dev = dps[0] ? dps[0]->ctx->device : -1;
+  for (int r = 0; r < nreal; ++r) {
+    if (!dps[r] || !P[r] || !b[r] || !x[r] || P[r]->mat != dps[r]->S || dps[r]->ctx->device != dev) return BO_ERR_ARG;
+    for (int q = 0; q < r; ++q)
+      if (P[q] == P[r] || dps[q] == dps[r]) return BO_ERR_ARG;
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) return BO_ERR_CUDA;
+  // condensed right-hand sides and the norms that set each fracture solve's
+  // tolerance (as in bo_dp_solve's first pass)
+  for (int r = 0; r < nreal; ++r) {
+    bo_dp* d = dps[r];
+    cudaStream_t s = d->ctx->stream;
+    bo::sq_norm(b[r], 6 * d->N, d->part, d->norms, s);
+    (bo::k_dp_rhs<<<bo::grid_for(d->N), bo::kThreads, 0, s>>>(d->N, d->val, d->fmap, d->minv, b[r], d->bhat),
+     bo::note_launch());
+    bo::sq_norm(d->bhat, 3 * d->N, d->part, d->norms + 1, s);
+    cudaMemcpyAsync(d->h_norms, d->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  }
+  std::vector<const double*> bh(nreal);
+  std::vector<double*> xs(nreal);
+  std::vector<double> tols(nreal);
+  std::vector<int> zero(nreal, 0);
+  for (int r = 0; r < nreal; ++r) {
+    bo_dp* d = dps[r];
+    if (cudaStreamSynchronize(d->ctx->stream) != cudaSuccess) return BO_ERR_CUDA;
+    const double nb = std::sqrt(d->h_norms[0]), nbh = std::sqrt(d->h_norms[1]);
+    bh[r] = d->bhat;
+    xs[r] = x[r];  // the fracture unknowns come first in x
+    tols[r] = nbh > 0.0 ? opts->tol * nb / nbh : opts->tol;
+    zero[r] = !(nbh > 0.0);
+  }
+  bo_solve_opts o = *opts;
+  o.mem = BO_MEM_DEVICE;
+  std::vector<bo_solve_info> si(nreal);
+  int rc = bo::solve_batched(P, nreal, bh.data(), xs.data(), o, si.data(), tols.data());
+  if (rc != BO_OK && rc != BO_ERR_NOT_CONVERGED) return rc;
+  // matrix unknowns and the full FP64 residual of every system
+  for (int r = 0; r < nreal; ++r) {
+    bo_dp* d = dps[r];
+    cudaStream_t s = d->ctx->stream;
+    if (zero[r]) cudaMemsetAsync(x[r], 0, 3 * d->N * sizeof(double), s);
+    (bo::k_dp_recover<<<bo::grid_for(d->N), bo::kThreads, 0, s>>>(d->N, d->val, d->mmap, d->minv, b[r], x[r]),
+     bo::note_launch());
+    (bo::k_dp_residual<<<bo::grid_for(2 * d->N), bo::kThreads, 0, s>>>(2 * d->N, d->rowptr, d->col, d->val, b[r],
+                                                                         x[r], d->r),
+     bo::note_launch());
+    bo::sq_norm(d->r, 6 * d->N, d->part, d->norms + 2, s);
+    cudaMemcpyAsync(d->h_norms + 2, d->norms + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+  }
+  int status = BO_OK;
+  for (int r = 0; r < nreal; ++r) {
+    bo_dp* d = dps[r];
+    if (cudaStreamSynchronize(d->ctx->stream) != cudaSuccess) return BO_ERR_CUDA;
+    const double nb = std::sqrt(d->h_norms[0]);
+    const double rel = nb > 0 ? std::sqrt(d->h_norms[2]) / nb : std::sqrt(d->h_norms[2]);
+    bo_solve_info inf = si[r];
+    inf.true_rel_res = rel;
+    inf.status = rel <= opts->tol ? BO_OK : BO_ERR_NOT_CONVERGED;
+    if (inf.status != BO_OK) {
+      // rounding left this one above tol (or its solve stopped short): the
+      // single solve with its refinement passes, from zero
+      bo_solve_opts o1 = *opts;
+      o1.mem = BO_MEM_DEVICE;
+      o1.x0_is_zero = 1;
+      bo_solve_info i1{};
+      bo_dp_solve(d, P[r], b[r], x[r], &o1, &i1);
+      i1.iters += inf.iters;
+      inf = i1;
+    }
+    if (infos) infos[r] = inf;
+    if (inf.status != BO_OK && status == BO_OK) status = inf.status;
+  }
+  return status;
+}
+
 int bo_dp_destroy(bo_dp* d) {
   if (!d) return BO_ERR_ARG;
   cudaStreamSynchronize(d->ctx->stream);

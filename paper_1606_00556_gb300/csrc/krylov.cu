@@ -1214,7 +1214,7 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
 }
 
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
-                   bo_solve_info* infos) {
+                   bo_solve_info* infos, const double* tols) {
   for (int r = 0; r < nreal; ++r) {
     const int rc = krylov_alloc(P[r], o->restart);
     if (rc != BO_OK) return rc;
@@ -1225,6 +1225,7 @@ int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double*
     jobs[r].b_in = b[r];
     jobs[r].x_in = x[r];
     jobs[r].o = *o;
+    if (tols) jobs[r].o.tol = tols[r];
     jobs[r].info = infos ? &infos[r] : nullptr;
   }
   int remaining = nreal;

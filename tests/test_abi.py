@@ -128,6 +128,7 @@ def test_every_entry_point_rejects_missing_handles(libpath):
         "bo_dp_update_values": (N, N, 0),
         "bo_dp_solve": (N, N, N, N, N, N),
         "bo_dp_destroy": (N,),
+        "bo_dp_solve_batched": (N, N, 0, N, N, N, N),
         "bo_cnn_create": (N, 8, 8, 8, 1, ctypes.c_uint64(0), N),
         "bo_cnn_destroy": (N,),
         "bo_cnn_get_params": (N, N, 0),
