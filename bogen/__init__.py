@@ -44,6 +44,7 @@ def lib():
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int]
         _lib.bg_nnzb.restype = ctypes.c_int64
         _lib.bg_assemble.restype = ctypes.c_int
+        _lib.bg_well_border.restype = ctypes.c_int
     return _lib
 
 
@@ -87,9 +88,14 @@ def incompressible_fluid(**over) -> Fluid:
 @dataclass
 class Well:
     kind: int            # 0 water injector, 1 producer
-    bhp: float           # psi at dref
+    bhp: float           # psi at dref (for a rate-controlled well: the current value of its unknown p_h)
     cells: np.ndarray    # perforated cell indices (int32)
     dref: float = 0.0    # reference depth of bhp; default: the top perforation
+    control: int = 0     # 0 fixed BHP; 1 water, 2 oil, 3 liquid rate (paper Sec. 2.3)
+    rate: float = 0.0    # the controlled rate into the reservoir, stb/day (> 0 injects, < 0 produces)
+
+
+CTRL_BHP, CTRL_WATER, CTRL_OIL, CTRL_LIQUID = 0, 1, 2, 3
 
 
 @dataclass
@@ -150,10 +156,35 @@ def pattern(nx, ny, nz):
     return rowptr, col
 
 
-def assemble(case: Case, jacobian: bool = True, x=None):
+def rate_wells(case: Case):
+    """The case's rate-controlled wells, in well order (the order of the
+    bordered system's well unknowns)."""
+    return [w for w in case.wells if w.control != CTRL_BHP]
+
+
+def _bhps(case: Case, ph):
+    """Every well's BHP, the rate-controlled ones taken from ph (if given)."""
+    out, v = [], 0
+    for w in case.wells:
+        if w.control != CTRL_BHP and ph is not None:
+            out.append(float(ph[v]))
+            v += 1
+        else:
+            out.append(float(w.bhp))
+    return out
+
+
+def assemble(case: Case, jacobian: bool = True, x=None, ph=None):
     """Residual R (3N) and BSR Jacobian of ``case``.
 
     Returns dict(rowptr, col, val (nnzb,3,3), R, b=-R).  Raises on a bad state.
+    With rate-controlled wells (Well.control != 0) their bottom-hole
+    pressures are unknowns too: ph (one per such well, in well order;
+    default: their Well.bhp) gives their values, and the result also holds
+    `border` = dict(perf_cell, perf_well (the well unknown of each
+    perforation), apw (P,3), awp (P,3), aww (W,), Rw (W,), bw = -Rw) of the
+    bordered Newton system (paper Sec. 2.3 and Sec. 3.2), and the full
+    right-hand side b_full = (b, bw).
     """
     L = lib()
     g = case.grid()
@@ -164,7 +195,7 @@ def assemble(case: Case, jacobian: bool = True, x=None):
     val = np.zeros((nnzb, 3, 3)) if jacobian else None
     xs = _d(case.x if x is None else x)
     wt = _i([w.kind for w in case.wells]) if case.wells else np.zeros(1, np.int32)
-    bhp = _d([w.bhp for w in case.wells]) if case.wells else np.zeros(1)
+    bhp = _d(_bhps(case, ph)) if case.wells else np.zeros(1)
     dref = _d([w.dref if w.dref else case.depth[int(np.min(w.cells))] for w in case.wells]) if case.wells else np.zeros(1)
     pptr = [0]
     cells, wis = [], []
@@ -192,7 +223,44 @@ def assemble(case: Case, jacobian: bool = True, x=None):
                        _ptr(val, ctypes.c_double) if val is not None else ctypes.cast(None, dp))
     if rc != 0:
         raise ValueError("assembly failed: non-positive pore volume or FVF")
-    return dict(rowptr=rowptr, col=col, val=val, R=R, b=-R)
+    out = dict(rowptr=rowptr, col=col, val=val, R=R, b=-R)
+    rw = rate_wells(case)
+    if rw:
+        W = len(rw)
+        P = sum(np.asarray(w.cells).size for w in rw)
+        ctrl = _i([w.control for w in case.wells])
+        rate = _d([w.rate for w in case.wells])
+        Rw, aww = np.zeros(W), np.zeros(W)
+        apw, awp = np.zeros((P, 3)), np.zeros((P, 3))
+        nv = L.bg_well_border(ctypes.byref(fl), _ptr(phi0, ctypes.c_double), _ptr(depth, ctypes.c_double),
+                              _ptr(xs, ctypes.c_double), ctypes.c_int32(len(case.wells)), _ptr(wt, ctypes.c_int32),
+                              _ptr(ctrl, ctypes.c_int32), _ptr(rate, ctypes.c_double), _ptr(bhp, ctypes.c_double),
+                              _ptr(dref, ctypes.c_double), _ptr(pptr, ctypes.c_int32), _ptr(cells, ctypes.c_int32),
+                              _ptr(wis, ctypes.c_double), _ptr(Rw, ctypes.c_double), _ptr(apw, ctypes.c_double),
+                              _ptr(awp, ctypes.c_double), _ptr(aww, ctypes.c_double))
+        if nv != W:
+            raise ValueError("invalid well control (an injector under an oil-rate control)")
+        pc = np.concatenate([np.asarray(w.cells, np.int32).ravel() for w in rw])
+        pw = np.concatenate([np.full(np.asarray(w.cells).size, v, np.int32) for v, w in enumerate(rw)])
+        out["border"] = dict(perf_cell=pc, perf_well=pw, apw=apw, awp=awp, aww=aww, Rw=Rw, bw=-Rw)
+        out["b_full"] = np.concatenate([-R, -Rw])
+    return out
+
+
+def with_rate_controls(case: Case, fraction: float = 0.8, producer_control: int = CTRL_LIQUID):
+    """A copy of ``case`` whose wells are rate-controlled: injectors under a
+    water rate, producers under `producer_control`, each target `fraction`
+    of the well's current rate at its BHP (so the bordered residual of the
+    case's state is nonzero in the well rows)."""
+    import copy
+    c = copy.deepcopy(case)
+    for w in c.wells:
+        w.control = CTRL_WATER if w.kind == 0 else producer_control
+        w.rate = 0.0
+    a = assemble(c, jacobian=False)
+    for w, r in zip(rate_wells(c), a["border"]["Rw"]):
+        w.rate = fraction * float(r)
+    return c
 
 
 def model_inputs(case: Case) -> dict:

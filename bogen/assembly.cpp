@@ -482,3 +482,73 @@ int bg_assemble_dual(const bg_grid* g, const bg_fluid* f,
 }
 
 }  // extern "C"
+
+namespace {
+// a cell-local dual lifted into the well's slots: (p, Sw, Sg) then p_h
+Dual<4> lift4(const Dual<3>& a) {
+  Dual<4> r(a.v);
+  for (int i = 0; i < 3; ++i) r.d[i] = a.d[i];
+  return r;
+}
+}  // namespace
+
+extern "C" {
+
+// Rate-controlled wells (paper Sec. 2.3): a well under a fixed water (ctrl 1),
+// oil (ctrl 2) or liquid (ctrl 3) rate has its bottom-hole pressure p_h as an
+// unknown and the constraint sum_m Q_ctrl,m(x, p_h) = rate, Q the component
+// rates into the perforated nodes of add_wells (stb/day; rate > 0 injects,
+// rate < 0 produces).  These wells' perforation terms enter R and the
+// diagonal blocks through bg_assemble with bhp[w] = the current p_h; this
+// function gives the border of the Newton system (paper Sec. 3.2's A_pw, A_wp,
+// A_ww), for the rate-controlled wells in well order (index v) and their
+// perforations in order (index e):
+//   Rw[v]         = sum_m Q_ctrl,m - rate[w]              (the well's residual)
+//   apw[3 e + c]  = dR_c,cell(e) / dp_h = -dQ_c / dp_h     (cell rows, well column)
+//   awp[3 e + u]  = dRw[v] / dx_cell(e),u                  (well row, cell columns)
+//   aww[v]        = dRw[v] / dp_h
+// ctrl[w] = 0 marks a fixed-BHP well (no unknown, skipped).  Returns the
+// number of rate-controlled wells, or -2 for an injector (type 0) under an
+// oil-rate control (its constraint would not depend on p_h).
+int bg_well_border(const bg_fluid* f, const double* phi0, const double* depth, const double* x, int32_t nw,
+                   const int32_t* wtype, const int32_t* ctrl, const double* rate, const double* bhp,
+                   const double* dref, const int32_t* perf_ptr, const int32_t* perf_cells, const double* perf_wi,
+                   double* Rw, double* apw, double* awp, double* aww) {
+  int v = 0;
+  int64_t e = 0;
+  for (int32_t w = 0; w < nw; ++w) {
+    if (ctrl[w] == 0) continue;
+    if (wtype[w] == 0 && ctrl[w] == 2) return -2;
+    Dual<4> total(0.0);
+    for (int32_t k = perf_ptr[w]; k < perf_ptr[w + 1]; ++k, ++e) {
+      const int64_t c = perf_cells[k];
+      const Props C = cell_props(*f, phi0[c], x[3 * c], x[3 * c + 1], x[3 * c + 2]);
+      const double WI = perf_wi[k];
+      const Dual<4> ph = Dual<4>::var(bhp[w], 3);
+      Dual<4> p = lift4(Dual<3>::var(x[3 * c], 0));
+      const double dzh = dref[w] - depth[c];
+      const Dual<4> dpo = ph - p - lift4(C.go) * dzh;
+      const Dual<4> dpw = ph - p - lift4(C.gw) * dzh;
+      const Dual<4> dpg = ph - p - lift4(C.gg) * dzh;
+      Dual<4> qo(0.0), qw(0.0), qg(0.0);
+      if (wtype[w] == 0) {
+        qw = WI * lift4(C.lt_res_w) * dpw;
+      } else {
+        qo = WI * lift4(C.lo) * dpo;
+        qw = WI * lift4(C.lw) * dpw;
+        qg = WI * (lift4(C.rs) * lift4(C.lo) * dpo + lift4(C.lg) * dpg);
+      }
+      const Dual<4>* Q[3] = {&qo, &qw, &qg};
+      for (int comp = 0; comp < 3; ++comp) apw[3 * e + comp] = -Q[comp]->d[3];
+      const Dual<4> qc = ctrl[w] == 1 ? qw : ctrl[w] == 2 ? qo : qo + qw;
+      for (int u = 0; u < 3; ++u) awp[3 * e + u] = qc.d[u];
+      total = total + qc;
+    }
+    Rw[v] = total.v - rate[w];
+    aww[v] = total.d[3];
+    ++v;
+  }
+  return v;
+}
+
+}  // extern "C"

@@ -97,3 +97,38 @@ def inexact_newton(case, eps, forcing="ew3", theta_max=0.1, theta_min=1e-10, gam
 
     return newton(case.x, assemble, solve, spmv, eps, forcing=forcing, theta_max=theta_max, theta_min=theta_min,
                   gamma=gamma, beta=beta, maxit=maxit)
+
+
+def inexact_newton_wells(case, eps, forcing="ew3", theta_max=0.1, theta_min=1e-10, gamma=0.9, beta=2.0, maxit=20,
+                         restart=30):
+    """Alg. 1 on a case with rate-controlled wells (paper Sec. 2.3): the
+    Newton unknowns are the cell states and the controlled wells' bottom-hole
+    pressures, x = (cells (3N), p_h (W)); each step assembles the bordered
+    system of Sec. 3.2 with the generator and solves it with the oracle's
+    bordered GMRES (natural block ILU(0) of the whole bordered matrix).
+    Returns newton's (x, info)."""
+    import bogen
+    from .bordered import bordered_bsr, bordered_matvec, bordered_solve
+    N = case.N
+    ph0 = np.array([w.bhp for w in bogen.rate_wells(case)], dtype=np.float64)
+    W = ph0.size
+
+    class Bordered:
+        def __init__(self, A, border):
+            self.A, self.border = A, border
+
+    def assemble(x):
+        a = bogen.assemble(case, x=x[:3 * N], ph=x[3 * N:])
+        return a["b_full"], Bordered(BsrMatrix(a["rowptr"], a["col"], a["val"]), a["border"])
+
+    def solve(Ab, b, theta):
+        dx, info = bordered_solve(Ab.A, Ab.border, b, tol=theta, m=restart, maxit=20000)
+        return dx, info["iters"]
+
+    def matvec(Ab, dx):
+        return bordered_matvec(Ab.A, Ab.border, dx)
+
+    x0 = np.concatenate([np.asarray(case.x, np.float64), ph0])
+    assert x0.size == 3 * N + W
+    return newton(x0, assemble, solve, matvec, eps, forcing=forcing, theta_max=theta_max, theta_min=theta_min,
+                  gamma=gamma, beta=beta, maxit=maxit)

@@ -89,6 +89,7 @@ MUTATIONS = [
 # source text, altered text, pin file, pin tests that must fail)
 C = "test_oracle_cnn_pins.py"
 N = "test_oracle_newton_pins.py"
+WP = "test_oracle_wells_pins.py"
 PY_MUTATIONS = [
     ("Convolution instead of correlation (taps mirrored)",
      "cnn.py", "y += _window(xp, dx, dy, dz, nz, ny, nx) @ w[t].T", "y += _window(xp, dx, dy, dz, nz, ny, nx) @ w[26 - t].T",
@@ -139,6 +140,15 @@ PY_MUTATIONS = [
      "newton.py", "return gamma * (float(np.linalg.norm(b_new)) / nb_old) ** beta",
      "return (float(np.linalg.norm(b_new)) / nb_old) ** beta",
      N, "test_forcing_terms_by_hand_on_one_unknown"),
+    ("Well column entries placed in the well's row of the cell block",
+     "bordered.py", "blk[:, 0] = apw[e]", "blk[0, :] = apw[e]",
+     WP, "test_bordered_matrix_is_the_jacobian_of_the_full_residual"),
+    ("Well diagonal block without A_ww",
+     "bordered.py", "vals.append(np.diag([aww[w], 1.0, 1.0]))", "vals.append(np.diag([1.0, 1.0, 1.0]))",
+     WP, "test_bordered_matrix_is_the_jacobian_of_the_full_residual"),
+    ("Well unknown embedded in the wrong slot of its block row",
+     "bordered.py", "out[3 * N::3] = v[3 * N:]", "out[3 * N + 1::3] = v[3 * N:]",
+     WP, "test_bordered_solve_matches_dense_lu"),
     ("Safeguard clips at theta_min only",
      "newton.py", "theta = min(max(forcing_term(forcing, b_new, nb_old, r, gamma, beta), theta_min), theta_max)",
      "theta = max(forcing_term(forcing, b_new, nb_old, r, gamma, beta), theta_min)",
@@ -186,6 +196,13 @@ GEN_MUTATIONS = [
     ("Dual-porosity transfer without the bulk volume",
      "kDarcy * sigma * km[c] * V, R);", "kDarcy * sigma * km[c], R);",
      "test_dual_transfer_closed_form"),
+    ("Well column of the border with the wrong sign",
+     "apw[3 * e + comp] = -Q[comp]->d[3];", "apw[3 * e + comp] = Q[comp]->d[3];",
+     "test_border_matches_central_differences"),
+    ("Liquid-rate control without the water rate",
+     "const Dual<4> qc = ctrl[w] == 1 ? qw : ctrl[w] == 2 ? qo : qo + qw;",
+     "const Dual<4> qc = ctrl[w] == 1 ? qw : ctrl[w] == 2 ? qo : qo;",
+     "test_newton_meets_the_rate_targets"),
     ("Dirichlet face transmissibility over a whole cell",
      "kx[c] / (0.5 * g->dx);", "kx[c] / g->dx;",
      "test_linear_pressure_profile_homogeneous"),
@@ -263,7 +280,7 @@ def original_gen_lib(tmp_path_factory):
 def _run_gen_pins(lib, tests):
     env = dict(os.environ, BO_BOGEN_LIB=lib)
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-           os.path.join(ROOT, "tests", G), "-k", tests]
+           os.path.join(ROOT, "tests", G), os.path.join(ROOT, "tests", WP), "-k", tests]
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
 
 
