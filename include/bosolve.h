@@ -486,6 +486,62 @@ int bo_dp_solve_batched(bo_dp* const* dp, bo_prec* const* P, int nreal, const do
 int bo_dp_destroy(bo_dp* dp);
 
 /* ---------------------------------------------------------------------------
+ * Rate-controlled wells (paper Sec. 2.3: a well under a fixed water, oil or
+ * liquid rate has its bottom-hole pressure p_h as an unknown and one
+ * constraint equation, the sum of its perforations' rates equal to the
+ * target).  The Newton system takes the bordered block form of Sec. 3.2,
+ *
+ *     [ A     A_pw ] [x  ]   [b  ]
+ *     [ A_wp  A_ww ] [x_w] = [b_w],
+ *
+ * A the reservoir matrix (a bo_mat), and per perforation e of well v in cell
+ * c: apw[3e + r] = the derivative of cell c's equation r with respect to
+ * p_h of v (column v of A_pw, rows 3c..3c+2), awp[3e + u] = the derivative
+ * of v's constraint with respect to unknown u of cell c (row v of A_wp);
+ * aww[v] = the derivative of v's constraint with respect to its own p_h
+ * (A_ww is diagonal: a constraint involves only its own well).  Vectors of
+ * the bordered system hold 3N + W doubles: the cells' (p, Sw, Sg), then the
+ * W well unknowns.
+ *
+ * The solve eliminates the wells exactly (Schur complement
+ * S = A - A_pw A_ww^{-1} A_wp on the reservoir unknowns), runs CPR-FGMRES on
+ * S with the preconditioner's well coupling corrected by the Woodbury
+ * identity (exact with respect to the CPR of A), and recovers
+ * x_w = A_ww^{-1} (b_w - A_wp x).  Convergence is judged on the bordered
+ * system's residual ||[b; b_w] - A_b [x; x_w]|| / ||[b; b_w]||.
+ * ------------------------------------------------------------------------- */
+typedef struct bo_wells bo_wells;
+
+/* The border's structure on matrix A: nwells (1..128) wells, nperf (>= 0)
+ * perforations with host arrays perf_cell[e] (natural cell index) and
+ * perf_well[e] (0..nwells-1, non-decreasing: perforations grouped by well).
+ * A cell may be perforated once (BO_ERR_ARG otherwise).  Holds a reference
+ * on A.  Synchronises. */
+int bo_wells_create(bo_mat* A, int32_t nwells, int32_t nperf, const int32_t* perf_cell, const int32_t* perf_well,
+                    bo_wells** out);
+/* The border's values (host or device per mem): apw, awp of 3 nperf
+ * doubles, aww of nwells.  BO_ERR_NONFINITE on NaN/Inf, BO_ERR_BREAKDOWN
+ * where aww[v] == 0.  Synchronises. */
+int bo_wells_update_values(bo_wells* w, const double* apw, const double* awp, const double* aww, int mem);
+/* 1 (default): the preconditioner carries the Woodbury correction of the
+ * well coupling (set up at the first solve after a change of the well
+ * values or of the preconditioner: nwells applications of the CPR); 0: the
+ * plain CPR of A (more iterations, no setup). */
+int bo_wells_set_coupling(bo_wells* w, int mode);
+/* y = alpha A_b x + beta y on device vectors of 3N + W doubles (FP64; the
+ * cell rows by bo_mat_spmv's FP64 product).  Synchronises. */
+int bo_wells_spmv(bo_wells* w, double alpha, const double* x, double beta, double* y);
+/* Solve the bordered system (device vectors of 3N + W doubles, opts->mem
+ * must be BO_MEM_DEVICE) with P set up on w's matrix.  A nonzero initial
+ * guess (opts->x0_is_zero == 0) is refined by a correction solve.  info
+ * reports the bordered system's true_rel_res.  Returns BO_OK,
+ * BO_ERR_NOT_CONVERGED (x holds the last iterate), or the status of a
+ * failed setup.  Synchronises. */
+int bo_solve_bordered(bo_prec* P, bo_wells* w, const double* b, double* x, const bo_solve_opts* opts,
+                      bo_solve_info* info);
+int bo_wells_destroy(bo_wells* w);
+
+/* ---------------------------------------------------------------------------
  * Learned Newton update.  No counterpart in the paper: an addition of this
  * library that feeds the Krylov solve of Sec. 3 a predicted initial guess
  * and a predicted coarse space; the architecture is this library's choice.

@@ -93,9 +93,20 @@ def extract(u, N, W):
 
 
 def bordered_matvec(A: BsrMatrix, border, x) -> np.ndarray:
-    """(A x + A_pw x_w, A_wp x + A_ww x_w) for x = (cells, wells)."""
-    N, W = A.nb, np.asarray(border["aww"]).size
-    return extract(spmv(bordered_bsr(A, border), embed(x, N, W)), N, W)
+    """(A x + A_pw x_w, A_wp x + A_ww x_w) for x = (cells, wells): the BSR
+    product of the cell rows, then one pass over the perforations."""
+    N = A.nb
+    aww = np.asarray(border["aww"], np.float64).ravel()
+    W = aww.size
+    x = np.asarray(x, np.float64)
+    xw = x[3 * N:]
+    y = np.concatenate([spmv(A, x[:3 * N]), aww * xw])
+    for e in range(np.asarray(border["perf_cell"]).size):
+        c, w = int(border["perf_cell"][e]), int(border["perf_well"][e])
+        for r in range(3):
+            y[3 * c + r] += border["apw"][e][r] * xw[w]
+            y[3 * N + w] += border["awp"][e][r] * x[3 * c + r]
+    return y
 
 
 def bordered_solve(A: BsrMatrix, border, b_full, tol=1e-13, m=30, maxit=20000, x0=None, B=None):

@@ -58,6 +58,8 @@ EXPORTS = (
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
     "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins",
     "bo_newton_opts_default", "bo_model_create", "bo_model_destroy", "bo_model_assemble", "bo_newton_solve",
+    "bo_wells_create", "bo_wells_update_values", "bo_wells_set_coupling", "bo_wells_spmv", "bo_solve_bordered",
+    "bo_wells_destroy",
 )
 
 
@@ -226,6 +228,13 @@ def lib():
         L.bo_model_assemble.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.POINTER(ctypes.c_double)]
         L.bo_newton_solve.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.POINTER(bo_newton_opts),
                                       ctypes.POINTER(bo_newton_info)]
+        L.bo_wells_create.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.POINTER(_VP)]
+        L.bo_wells_update_values.argtypes = [_VP, _VP, _VP, _VP, _i]
+        L.bo_wells_set_coupling.argtypes = [_VP, _i]
+        L.bo_wells_spmv.argtypes = [_VP, ctypes.c_double, _VP, ctypes.c_double, _VP]
+        L.bo_solve_bordered.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(bo_solve_opts),
+                                        ctypes.POINTER(bo_solve_info)]
+        L.bo_wells_destroy.argtypes = [_VP]
         _lib = L
     return _lib
 
@@ -482,6 +491,71 @@ class DualPorosity:
     def close(self):
         if self.h and _alive():
             lib().bo_dp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Wells:
+    """bo_wells: the border of rate-controlled wells on a matrix (see
+    include/bosolve.h).  perf_cell, perf_well: one entry per perforation,
+    grouped by well; values (apw, awp of 3 per perforation, aww per well)
+    through update_values."""
+
+    def __init__(self, mat: "Matrix", nwells, perf_cell, perf_well, apw=None, awp=None, aww=None):
+        pc = np.ascontiguousarray(perf_cell, dtype=np.int32)
+        pw = np.ascontiguousarray(perf_well, dtype=np.int32)
+        if pc.size != pw.size:
+            raise BoArgError("perf_cell and perf_well differ in length")
+        h = _VP()
+        _check(lib().bo_wells_create(mat.h, int(nwells), int(pc.size), _VP(pc.ctypes.data), _VP(pw.ctypes.data),
+                                     ctypes.byref(h)), "bo_wells_create")
+        self.h, self.mat, self.W, self.P = h, mat, int(nwells), int(pc.size)
+        self.n = mat.n + self.W
+        if aww is not None:
+            self.update_values(apw, awp, aww)
+
+    def update_values(self, apw, awp, aww):
+        apw, awp, aww = _f64(apw), _f64(awp), _f64(aww)
+        _need(apw, 3 * self.P, "apw")
+        _need(awp, 3 * self.P, "awp")
+        _need(aww, self.W, "aww")
+        (pa, ma), (pb, mb), (pc, mc) = _ptr(apw), _ptr(awp), _ptr(aww)
+        if not (ma == mb == mc):
+            raise BoArgError("apw, awp and aww must all be host or all device arrays")
+        _check(lib().bo_wells_update_values(self.h, pa, pb, pc, ma), "bo_wells_update_values")
+
+    def set_coupling(self, mode: int):
+        _check(lib().bo_wells_set_coupling(self.h, int(mode)), "bo_wells_set_coupling")
+
+    def spmv(self, x, y, alpha=1.0, beta=0.0):
+        """y = alpha A_b x + beta y (device vectors of 3N + W doubles)."""
+        ctx = self.mat.ctx
+        _check(lib().bo_wells_spmv(self.h, float(alpha), _dvec(x, self.n, "x", ctx), float(beta),
+                                   _dvec(y, self.n, "y", ctx)), "bo_wells_spmv")
+        return y
+
+    def solve(self, P: "Preconditioner", b, x, tol=1e-8, restart=30, maxit=500, x0_is_zero=True,
+              raise_on_error=True):
+        """bo_solve_bordered on device vectors of 3N + W doubles."""
+        ctx = self.mat.ctx
+        o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
+        info = bo_solve_info()
+        rc = lib().bo_solve_bordered(P.h, self.h, _dvec(b, self.n, "b", ctx), _dvec(x, self.n, "x", ctx),
+                                     ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error and rc != BO_OK:
+            raise BoError(rc, "bo_solve_bordered")
+        d = info.as_dict()
+        d["rc"] = rc
+        return d
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_wells_destroy(self.h)
         self.h = None
 
     def __del__(self):

@@ -403,6 +403,8 @@ struct Level {
 
 }  // namespace bo
 
+struct bo_wells;
+
 struct bo_prec {
   bo_mat* mat;
   cudaStream_t stream;     // stream of all preconditioner work (the context's, or a batch stream)
@@ -469,6 +471,13 @@ struct bo_prec {
   double* hist;            // host residual history of the last solve
   int nhist;
   int hist_cap;
+  // preconditioner setups so far (values refreshed or coarse space changed):
+  // state derived from this preconditioner checks it before reuse
+  unsigned long long setups = 0;
+  // rate-controlled wells of the bordered solve in progress (NULL otherwise),
+  // and those the captured Arnoldi-column graphs were recorded with
+  bo_wells* wl = nullptr;
+  const bo_wells* graph_wl = nullptr;
 };
 
 // ----------------------------------------------------------------- launchers
@@ -507,6 +516,15 @@ void ctx_release_ref(bo_ctx* c);
 
 // krylov.cu
 int fgmres(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
+// wells.cu: the bordered solve's corrections inside FGMRES (P->wl set):
+// after the preconditioner wrote z (split planes of n entries), after the
+// Arnoldi product wrote w (split planes, low plane at w + np), and after the
+// true residual of the iterate
+void wells_after_prec(bo_prec* P, float* z, int64_t n);
+void wells_after_product(bo_prec* P, float* w, int64_t np);
+void wells_after_residual(bo_prec* P);
+// capi.cu: drop a reference to a matrix
+void mat_release_ref(bo_mat* m);
 int bicgstab(bo_prec* P, const double* b_nat, double* x_nat, const bo_solve_opts* o, bo_solve_info* info);
 // tols: per-system tolerances replacing o->tol (NULL: o->tol for all)
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,

@@ -122,6 +122,7 @@ void mat_release(bo_mat* m) {
 
 namespace bo {
 void ctx_release_ref(bo_ctx* c) { ctx_release(c); }
+void mat_release_ref(bo_mat* m) { mat_release(m); }
 }  // namespace bo
 
 namespace {
@@ -212,6 +213,7 @@ int prec_refresh(bo_prec* P) {
   err = *P->mat->h_flags;
   cudaMemsetAsync(&P->st->err, 0, sizeof(int), s);
   cudaMemsetAsync(&P->st->done, 0, sizeof(int), s);
+  P->setups++;
   if (err & kErrBreakdown) return BO_ERR_BREAKDOWN;
   if (err & kErrNonfinite) return BO_ERR_NONFINITE;
   return BO_OK;

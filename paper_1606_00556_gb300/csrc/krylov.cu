@@ -624,6 +624,7 @@ struct Job {
     } else {
       (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
        note_launch());
+      if (P->wl) wells_after_residual(P);
     }
     mark(kPhaseSlot);
     P->nhist = 0;
@@ -652,6 +653,7 @@ struct Job {
     float* zj = (float*)P->Z + (size_t)j * 2 * nn;  // split pairs: hi plane, lo plane
     double* dhist = P->partials + (P->npartials - kHistCap);
     launch_cpr_split_in(P, vj, zj, st, &st->vscale[j]);
+    if (P->wl) wells_after_prec(P, zj, nn);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed && prof.size() < 512) {
       e0 = P->prof_ev[2 * prof.size()];
@@ -665,6 +667,7 @@ struct Job {
       cudaEventRecord(e1, s);
       prof.push_back({e0, e1});
     }
+    if (P->wl) wells_after_product(P, w, split_pad(nn));
     const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
     const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
@@ -680,9 +683,10 @@ struct Job {
   // instantiated; valid while the workspace and restart length stay put.
   bool ensure_graph(int j) {
     const int m = o.restart;
-    if (P->graph_m != m) {
+    if (P->graph_m != m || P->graph_wl != P->wl) {
       graphs_reset(P);
       P->graph_m = m;
+      P->graph_wl = P->wl;
     }
     if (P->col_exec[j]) return true;
     if (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
@@ -738,6 +742,7 @@ struct Job {
     else (k_xupdate<kMaxM><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
     (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(geom(), P->mat->A, P->bi, P->xi, P->rk, P->partials, P->st),
      note_launch());
+    if (P->wl) wells_after_residual(P);
     mark(kPhaseSlot);
     phase = kCycleWait;
   }

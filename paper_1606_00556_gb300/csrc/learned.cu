@@ -248,6 +248,7 @@ void learned_coarse_free(bo_prec* P) {
   fr(P->lc_z); fr(P->lc_E); fr(P->lc_Einv); fr(P->lc_y); fr(P->lc_u);
   P->lc_z = P->lc_E = P->lc_Einv = P->lc_y = P->lc_u = nullptr;
   P->lc_nt = 0;
+  P->setups++;
 }
 
 }  // namespace bo
@@ -281,6 +282,7 @@ int set_coarse_space(bo_prec* P, const T* dp, int stride, double scale, int tx, 
   P->lc_tile[0] = tx; P->lc_tile[1] = ty; P->lc_tile[2] = tz;
   P->lc_ntile[0] = ntx; P->lc_ntile[1] = nty; P->lc_ntile[2] = ntz;
   P->lc_nt = (int)nt;
+  P->setups++;
   cudaStream_t s = P->stream;
   cudaMemsetAsync(&P->st->err, 0, sizeof(P->st->err), s);
   (k_lc_perm<T><<<grid_for(g.N), kThreads, 0, s>>>(g, dp, stride, scale, P->lc_z), note_launch());

@@ -129,6 +129,12 @@ def test_every_entry_point_rejects_missing_handles(libpath):
         "bo_dp_solve": (N, N, N, N, N, N),
         "bo_dp_destroy": (N,),
         "bo_dp_solve_batched": (N, N, 0, N, N, N, N),
+        "bo_wells_create": (N, 1, 0, N, N, N),
+        "bo_wells_update_values": (N, N, N, N, 0),
+        "bo_wells_set_coupling": (N, 1),
+        "bo_wells_spmv": (N, ctypes.c_double(1.0), N, ctypes.c_double(0.0), N),
+        "bo_solve_bordered": (N, N, N, N, N, N),
+        "bo_wells_destroy": (N,),
         "bo_cnn_create": (N, 8, 8, 8, 1, ctypes.c_uint64(0), N),
         "bo_cnn_destroy": (N,),
         "bo_cnn_get_params": (N, N, 0),
