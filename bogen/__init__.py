@@ -299,3 +299,71 @@ def relperm(fluid: Fluid, sw: float, sg: float):
 from .fields import tiny_case, waterflood_case, gaussian_field, uniform_case, ensemble_specs, ensemble_case  # noqa: E402,F401,E501
 from . import learned  # noqa: E402,F401
 from . import dual  # noqa: E402,F401
+
+
+# ------------------------------------------------------------ two-phase oil-water
+def oil_water_fluid(**over) -> Fluid:
+    """Fluid of the two-phase oil-water model (paper Sec. 2.2): dead oil
+    (Rs = 0, no gas phase) and the paper's SPE10 relative permeabilities
+    k_rw = ((s_w - s_wc)/(1 - s_wc - s_or))^2, k_ro = ((1 - s_or - s_w)/(1 -
+    s_wc - s_or))^2 with s_wc = s_or = 0.2; other constants as default_fluid."""
+    v = dict(rs0=0.0, drs=0.0, swc=0.2, sorw=0.2, sorg=0.2, sgc=0.0, nw=2.0, now=2.0)
+    v.update(over)
+    return default_fluid(**v)
+
+
+def oil_water_case(nx: int = 128, ny: int = 128, nz: int = 64, seed: int = 42, **kw) -> Case:
+    """A two-phase oil-water case on the waterflood generator's grid, rock
+    and wells: the same permeability field and five-spot wells, the water
+    front's saturations mapped from [0.1, 0.85] onto [s_wc, 1 - s_or] =
+    [0.2, 0.8], no gas (Sg = 0 in the state vectors)."""
+    from .fields import waterflood_case
+    c = waterflood_case(nx, ny, nz, seed=seed, **kw)
+    for v in (c.x, c.xn):
+        sw = v[1::3]
+        v[1::3] = 0.2 + (sw - 0.1) * (0.6 / 0.75)
+        v[2::3] = 0.0
+    c.fluid = oil_water_fluid()
+    return c
+
+
+def tiny_oil_water_case(seed: int = 0, nx: int = 20, ny: int = 20, nz: int = 5) -> Case:
+    """The tiny case's grid, rock and wells with the two-phase fluid: state
+    (3000 psi, Sw 0.3) times U[0.95, 1.05] per unknown, previous state
+    uniform, Sg = 0."""
+    from .fields import tiny_case
+    c = tiny_case(seed, nx, ny, nz)
+    rng = np.random.default_rng(seed + 1000)
+    N = c.N
+    c.xn = np.tile([3000.0, 0.3, 0.0], N)
+    c.x = c.xn * np.concatenate([rng.uniform(0.95, 1.05, (N, 2)), np.ones((N, 1))], axis=1).ravel()
+    c.fluid = oil_water_fluid()
+    return c
+
+
+def assemble_ow(case: Case, jacobian: bool = True, x=None):
+    """Residual and 2x2 BSR Jacobian of the two-phase oil-water model (paper
+    Sec. 2.2): unknowns (p_o, S_w) and equations (oil, water) per cell.
+
+    The model is the three-phase one without gas: with Sg = 0 and Rs = 0 the
+    gas phase has no mass, flux or well rate, Stone II reduces to k_row
+    (k_ro(S_w, 0) = k_row(S_w)), and the oil and water equations are exactly
+    Sec. 2.2's.  So the residual is the three-phase residual's (oil, water)
+    rows at Sg = 0 and the Jacobian the (oil, water) x (p, S_w) part of each
+    block.  x: the two-phase state (2N), default the case's.  Returns
+    dict(rowptr, col, val (nnzb,2,2), R (2N), b = -R)."""
+    N = case.N
+    if x is None:
+        x3 = np.asarray(case.x, np.float64)
+    else:
+        x2 = np.asarray(x, np.float64).reshape(N, 2)
+        x3 = np.concatenate([x2, np.zeros((N, 1))], axis=1).ravel()
+    a = assemble(case, jacobian=jacobian, x=x3)
+    R = a["R"].reshape(N, 3)[:, :2].ravel().copy()
+    val = a["val"][:, :2, :2].copy() if jacobian else None
+    return dict(rowptr=a["rowptr"], col=a["col"], val=val, R=R, b=-R)
+
+
+def state_ow(case: Case) -> np.ndarray:
+    """The case's two-phase state (p_o, S_w) per cell."""
+    return np.asarray(case.x, np.float64).reshape(-1, 3)[:, :2].ravel().copy()

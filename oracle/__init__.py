@@ -151,6 +151,59 @@ def qi_decouple(A: BsrMatrix):
     return BsrMatrix(A.rowptr, A.col, out), w
 
 
+def abf_decouple(A: BsrMatrix) -> BsrMatrix:
+    """ABF decoupling (paper Sec. 3.2, the Alternate Block Factorization it
+    cites): D^{-1} A with D the block diagonal of A, every block of block
+    row i multiplied on the left by A_ii^{-1} (any block size)."""
+    val = np.empty_like(A.val)
+    for i in range(A.nb):
+        lo, hi = A.rowptr[i], A.rowptr[i + 1]
+        d = [e for e in range(lo, hi) if A.col[e] == i]
+        if len(d) != 1:
+            raise ValueError(f"block row {i} has no single diagonal block")
+        Dinv = np.linalg.inv(A.val[d[0]])
+        for e in range(lo, hi):
+            val[e] = Dinv @ A.val[e]
+    return BsrMatrix(A.rowptr, A.col, val)
+
+
+def abf_scale(A: BsrMatrix, v) -> np.ndarray:
+    """D^{-1} v for the ABF operator D of A (block diagonal of A)."""
+    v = np.asarray(v, np.float64).reshape(A.nb, A.bs)
+    out = np.empty_like(v)
+    for i in range(A.nb):
+        for e in range(A.rowptr[i], A.rowptr[i + 1]):
+            if A.col[e] == i:
+                out[i] = np.linalg.solve(A.val[e], v[i])
+    return out.ravel()
+
+
+def pad_two_phase(A: BsrMatrix) -> BsrMatrix:
+    """A 2x2 BSR matrix of the two-phase model (unknowns p_o, S_w) as 3x3
+    blocks with a third unknown that only its own unit diagonal touches, so
+    that the three-phase CPR applies; its solution is the 2x2 one with a zero
+    third component."""
+    val = np.zeros((A.val.shape[0], 3, 3))
+    val[:, :2, :2] = A.val
+    for i in range(A.nb):
+        for e in range(A.rowptr[i], A.rowptr[i + 1]):
+            if A.col[e] == i:
+                val[e, 2, 2] = 1.0
+    return BsrMatrix(A.rowptr, A.col, val)
+
+
+def solve_two_phase(A: BsrMatrix, b, dims, tol=1e-13, m=30, maxit=5000):
+    """x with ||b - A x|| <= tol ||b|| for a two-phase 2x2 system on an
+    nx x ny x nz grid: GMRES(m) with the CPR of the padded matrix (block
+    ILU(0) and AMG on the pressure block; natural-order ILU(0) alone stalls
+    on the pressure part).  Returns (x (2N), info)."""
+    P3 = pad_two_phase(A)
+    b3 = np.zeros((A.nb, 3))
+    b3[:, :2] = np.asarray(b, np.float64).reshape(A.nb, 2)
+    x3, info = gmres(P3, b3.ravel(), m=m, maxit=maxit, tol=tol, prec=cpr_prec(P3, dims))
+    return x3.reshape(A.nb, 3)[:, :2].ravel().copy(), info
+
+
 def red_black_perm(nx, ny, nz) -> np.ndarray:
     perm = np.zeros(nx * ny * nz, np.int64)
     lib().or_red_black_perm(nx, ny, nz, _p(perm, _I64))

@@ -90,6 +90,7 @@ MUTATIONS = [
 C = "test_oracle_cnn_pins.py"
 N = "test_oracle_newton_pins.py"
 WP = "test_oracle_wells_pins.py"
+OW = "test_oracle_oilwater_pins.py"
 PY_MUTATIONS = [
     ("Convolution instead of correlation (taps mirrored)",
      "cnn.py", "y += _window(xp, dx, dy, dz, nz, ny, nx) @ w[t].T", "y += _window(xp, dx, dy, dz, nz, ny, nx) @ w[26 - t].T",
@@ -149,6 +150,12 @@ PY_MUTATIONS = [
     ("Well unknown embedded in the wrong slot of its block row",
      "bordered.py", "out[3 * N::3] = v[3 * N:]", "out[3 * N + 1::3] = v[3 * N:]",
      WP, "test_bordered_solve_matches_dense_lu"),
+    ("ABF scaling applied on the right (A D^{-1})",
+     "__init__.py", "val[e] = Dinv @ A.val[e]", "val[e] = A.val[e] @ Dinv",
+     OW, "test_abf_decoupling_identities"),
+    ("Padded two-phase matrix without the third unknown's unit diagonal",
+     "__init__.py", "val[e, 2, 2] = 1.0", "val[e, 2, 2] = 0.0",
+     OW, "test_two_phase_reference_solutions_match_dense_lu"),
     ("Safeguard clips at theta_min only",
      "newton.py", "theta = min(max(forcing_term(forcing, b_new, nb_old, r, gamma, beta), theta_min), theta_max)",
      "theta = max(forcing_term(forcing, b_new, nb_old, r, gamma, beta), theta_min)",
