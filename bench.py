@@ -727,6 +727,58 @@ def newton_sequence(bo, ctx, dev, case, A, days, restart, eps_rel=1e-6):
     return vals, bs, rec
 
 
+def wells_record(bo, ctx, dev, dims, a, repeats=5):
+    """The benchmark's day-0 Jacobian with every well rate-controlled (paper
+    Sec. 2.3): the bordered system of 3N + 5 unknowns solved to 1e-8 with the
+    FP32 CPR corrected for the well coupling (Woodbury), against the same
+    solve without that correction and against the same reservoir matrix with
+    the wells at fixed BHP (no border).  Wall times around synchronised
+    solves (median of `repeats`); setup_ms is the correction's setup (one CPR
+    application per well) after a preconditioner refresh."""
+    import torch
+    bd = a["border"]
+    A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), a["rowptr"], a["col"], a["val"])
+    wl = bo.Wells(A, bd["aww"].size, bd["perf_cell"], bd["perf_well"], bd["apw"].ravel(), bd["awp"].ravel(),
+                  bd["aww"])
+    P = bo.Preconditioner(A, precision=bo.BO_PREC_FP32)
+    b = torch.tensor(a["b_full"], device=dev)
+    b3 = torch.tensor(a["b"], device=dev)
+    x = torch.zeros_like(b)
+    x3 = torch.zeros_like(b3)
+
+    def timed(fn):
+        ts, info = [], None
+        for _ in range(repeats + 1):
+            x.zero_()
+            x3.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts[1:])), info
+
+    ms, info = timed(lambda: wl.solve(P, b, x, tol=1e-8, maxit=400))
+    P.update()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    wl.solve(P, b, x, tol=1e-8, maxit=400)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3 - ms
+    wl.set_coupling(0)
+    ms0, info0 = timed(lambda: wl.solve(P, b, x, tol=1e-8, maxit=400, raise_on_error=False))
+    msb, infob = timed(lambda: P.solve(b3, x3, tol=1e-8, maxit=400))
+    rec = {"workload": (f"{dims[0]}x{dims[1]}x{dims[2]} waterflood day 0, 5 rate-controlled wells (4 water-rate "
+                        "injectors, 1 liquid-rate producer, targets 0.8 x their rates at the BHP), bordered system "
+                        f"of {3 * int(np.prod(dims))} + 5 unknowns, FP32 CPR, tol 1e-8"),
+           "ms": ms, "iters": info["iters"], "true_rel_res": info["true_rel_res"], "setup_ms": setup_ms,
+           "no_coupling": {"ms": ms0, "iters": info0["iters"], "true_rel_res": info0["true_rel_res"]},
+           "same_matrix_fixed_bhp": {"ms": msb, "iters": infob["iters"]}}
+    for o in (P, wl, A):
+        o.close()
+    return rec
+
+
 def run_mixed(bo, ctx, dev, stream, a, args):
     """The 256x256x128 Jacobian with the FP32, BF16-storage and FP64
     preconditioners: per precision one untimed step, then args.mixed_steps
@@ -794,6 +846,8 @@ def main():
     ap.add_argument("--sequence", default="newton", choices=["newton", "synthetic"],
                     help="the 1M-cell Jacobians of successive days: advanced by the device Newton method "
                          "(default), or the generator's synthetic fronts")
+    ap.add_argument("--no-wells", action="store_true",
+                    help="skip the rate-controlled-wells record of the default line")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 256-realisation ensembles (single and dual porosity) of the default line")
     ap.add_argument("--ensemble-steps", type=int, default=3, help="timed steps of each ensemble in the default line")
@@ -856,6 +910,11 @@ def main():
     if rank == 0 and not args.no_ensemble:
         ens_in = ensemble_inputs(args.ensemble, os.cpu_count() or 1)
         dual_in = ensemble_inputs(args.ensemble, os.cpu_count() or 1, dual=True)
+    wells_a = None
+    if rank == 0 and not args.no_wells:
+        import bogen
+        bogen.build()
+        wells_a = bogen.assemble(bogen.with_rate_controls(bogen.waterflood_case(*dims, seed=SEED, day=0)))
     mix_a = None
     if mixed:
         import bogen
@@ -1065,6 +1124,10 @@ def main():
     if mix_a is not None:
         mixed_rec, mixed_x = run_mixed(bo, ctx, dev, stream, mix_a, args)
         del mix_a
+    wells_rec = None
+    if wells_a is not None:
+        wells_rec = wells_record(bo, ctx, dev, dims, wells_a)
+        del wells_a
     ens_rec = dual_rec = None
     if ens_in is not None:
         # the batched ensembles (configs of 256 realisations, 38M unknowns)
@@ -1096,7 +1159,7 @@ def main():
                          "avg_us": avg_s * 1e6 if avg_s else None, "launches": spmv_n},
             "spmv": sp, "spmv_cpu": cpu_spmv, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e,
             "errors": errors or None, "mixed_256x256x128": mixed_rec, "newton_sequence": newton_rec,
-            "ensemble": ens_rec, "ensemble_dual_porosity": dual_rec,
+            "ensemble": ens_rec, "ensemble_dual_porosity": dual_rec, "rate_controlled_wells": wells_rec,
             "precision_note": ("no all-FP64 path is timed: even the FP64 preconditioner form computes the Arnoldi "
                                "product in split FP32 pairs (2^-46 relative per term); convergence is decided "
                                "on the FP64 true residual of the original system"),

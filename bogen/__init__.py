@@ -304,10 +304,14 @@ from . import dual  # noqa: E402,F401
 # ------------------------------------------------------------ two-phase oil-water
 def oil_water_fluid(**over) -> Fluid:
     """Fluid of the two-phase oil-water model (paper Sec. 2.2): dead oil
-    (Rs = 0, no gas phase) and the paper's SPE10 relative permeabilities
-    k_rw = ((s_w - s_wc)/(1 - s_wc - s_or))^2, k_ro = ((1 - s_or - s_w)/(1 -
-    s_wc - s_or))^2 with s_wc = s_or = 0.2; other constants as default_fluid."""
-    v = dict(rs0=0.0, drs=0.0, swc=0.2, sorw=0.2, sorg=0.2, sgc=0.0, nw=2.0, now=2.0)
+    (Rs = 0, no gas phase) with a compressibility of 1e-5 / psi (B_o =
+    1.25 (1 - 1e-5 (p - 3000)); the three-phase table's B_o grows with p,
+    which only dissolved gas makes physical: without it the oil would expand
+    under compression and the pressure equation lose its definiteness), and
+    the paper's SPE10 relative permeabilities k_rw = ((s_w - s_wc)/(1 - s_wc -
+    s_or))^2, k_ro = ((1 - s_or - s_w)/(1 - s_wc - s_or))^2 with s_wc = s_or =
+    0.2; other constants as default_fluid."""
+    v = dict(rs0=0.0, drs=0.0, dbo=-1.25e-5, swc=0.2, sorw=0.2, sorg=0.2, sgc=0.0, nw=2.0, now=2.0)
     v.update(over)
     return default_fluid(**v)
 

@@ -92,7 +92,20 @@ typedef struct {
   int32_t amg_nu2;        /* post-sweeps (default 2)                             */
   double amg_overcorr;    /* coarse correction scale s: x += s P x_c (default 1.3) */
   int32_t amg_coarse_max; /* coarsest level size, <= 128 (default 128)          */
+  int32_t decoupling;     /* BO_DECOUPLE_QI (default) or BO_DECOUPLE_ABF          */
 } bo_prec_opts;
+
+/* Decoupling operator D of the CPR (paper Sec. 3.2, D^{-1} A x = D^{-1} b).
+ * BO_DECOUPLE_QI: Quasi-IMPES, the pressure row of each cell becomes
+ *   row_o - (a_{o,Sw}/a_{w,Sw}) row_w - (a_{o,Sg}/a_{g,Sg}) row_g (where that
+ *   leaves a non-positive pressure pivot, the cell takes the ABF row).
+ * BO_DECOUPLE_ABF: Alternate Block Factorization, D = the block diagonal of
+ *   A.  Only the pressure row of D^{-1} A enters the AMG stage, and block
+ *   ILU(0) commutes with a block-diagonal left scaling (the factors of
+ *   D^{-1} A are those of A scaled row-blockwise), so the library applies
+ *   row 0 of each A_ii^{-1} to the pressure row and leaves the other rows:
+ *   the preconditioner equals the CPR of the fully ABF-scaled system. */
+enum { BO_DECOUPLE_QI = 0, BO_DECOUPLE_ABF = 1 };
 
 typedef struct {
   double tol;             /* relative to ||b||_2 (paper Alg. 1 criterion)         */
@@ -484,6 +497,43 @@ int bo_dp_solve(bo_dp* dp, bo_prec* P, const double* b, double* x, const bo_solv
 int bo_dp_solve_batched(bo_dp* const* dp, bo_prec* const* P, int nreal, const double* const* b, double* const* x,
                         const bo_solve_opts* opts, bo_solve_info* infos);
 int bo_dp_destroy(bo_dp* dp);
+
+/* ---------------------------------------------------------------------------
+ * Two-phase oil-water systems (paper Sec. 2.2: per cell the unknowns
+ * (p_o, S_w) and the (oil, water) conservation equations; 2x2 blocks on the
+ * 7-point pattern, rules as for bo_mat_create_bsr with 4 values per block,
+ * row-major).  Vectors hold 2N doubles, (p_o, S_w) of cell c at 2c, 2c+1.
+ *
+ * The system runs on the three-unknown layout: each block padded to 3x3
+ * with a unit diagonal for a third unknown that nothing else touches (its
+ * component stays zero in every vector), so every CPR stage is the 2x2
+ * stage (see bo_prec_opts.decoupling for Quasi-IMPES or ABF).  The padded
+ * matrix stores 9 values per block where a native 2x2 layout would store 4.
+ * ------------------------------------------------------------------------- */
+typedef struct bo_ow bo_ow;
+
+/* Copies pattern and values (host or device per mem); BO_ERR_PATTERN /
+ * BO_ERR_NONFINITE as bo_mat_create_bsr.  Holds a reference on ctx.
+ * Synchronises. */
+int bo_ow_create(bo_ctx* ctx, const bo_grid* grid, int32_t nbrows, int64_t nnzb, const int32_t* rowptr,
+                 const int32_t* col, const double* val, int mem, bo_ow** out);
+/* New 2x2 values on the same pattern (a preconditioner on bo_ow_matrix
+ * needs bo_prec_update afterwards).  Synchronises. */
+int bo_ow_update_values(bo_ow* w, const double* val, int mem);
+/* The padded matrix (owned by w, valid until bo_ow_destroy): set up the
+ * preconditioner on it with bo_prec_setup. */
+bo_mat* bo_ow_matrix(bo_ow* w);
+/* y = alpha A x + beta y, device vectors of 2N doubles (FP64 product).
+ * Synchronises. */
+int bo_ow_spmv(bo_ow* w, double alpha, const double* x, double beta, double* y);
+/* Solve A x = b (device vectors of 2N doubles; opts->mem must be
+ * BO_MEM_DEVICE) with P set up on bo_ow_matrix(w): CPR-FGMRES, or
+ * BiCGSTAB (the solver of the paper's oil-water scalability runs).  Status
+ * and info as bo_solve / bo_solve_bicgstab. */
+int bo_ow_solve(bo_ow* w, bo_prec* P, const double* b, double* x, const bo_solve_opts* opts, bo_solve_info* info);
+int bo_ow_solve_bicgstab(bo_ow* w, bo_prec* P, const double* b, double* x, const bo_solve_opts* opts,
+                         bo_solve_info* info);
+int bo_ow_destroy(bo_ow* w);
 
 /* ---------------------------------------------------------------------------
  * Rate-controlled wells (paper Sec. 2.3: a well under a fixed water, oil or

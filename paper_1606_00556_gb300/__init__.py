@@ -38,6 +38,8 @@ BO_STAGE_ILU = 1
 BO_STAGE_AMG = 2
 BO_STAGE_CPR_DECOUPLED = 3
 BO_STAGE_ARNOLDI_SPMV = 4
+BO_DECOUPLE_QI = 0
+BO_DECOUPLE_ABF = 1
 BO_LAUNCH_STREAM = 0
 BO_LAUNCH_GRAPH = 1
 
@@ -60,6 +62,8 @@ EXPORTS = (
     "bo_newton_opts_default", "bo_model_create", "bo_model_destroy", "bo_model_assemble", "bo_newton_solve",
     "bo_wells_create", "bo_wells_update_values", "bo_wells_set_coupling", "bo_wells_spmv", "bo_solve_bordered",
     "bo_wells_destroy",
+    "bo_ow_create", "bo_ow_update_values", "bo_ow_matrix", "bo_ow_spmv", "bo_ow_solve", "bo_ow_solve_bicgstab",
+    "bo_ow_destroy",
 )
 
 
@@ -86,7 +90,8 @@ class bo_grid(ctypes.Structure):
 
 class bo_prec_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("amg_nu1", ctypes.c_int32), ("amg_nu2", ctypes.c_int32),
-                ("amg_overcorr", ctypes.c_double), ("amg_coarse_max", ctypes.c_int32)]
+                ("amg_overcorr", ctypes.c_double), ("amg_coarse_max", ctypes.c_int32),
+                ("decoupling", ctypes.c_int32)]
 
 
 class bo_solve_opts(ctypes.Structure):
@@ -235,6 +240,15 @@ def lib():
         L.bo_solve_bordered.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(bo_solve_opts),
                                         ctypes.POINTER(bo_solve_info)]
         L.bo_wells_destroy.argtypes = [_VP]
+        L.bo_ow_create.argtypes = [_VP, ctypes.POINTER(bo_grid), ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, _i,
+                                   ctypes.POINTER(_VP)]
+        L.bo_ow_update_values.argtypes = [_VP, _VP, _i]
+        L.bo_ow_matrix.restype = _VP
+        L.bo_ow_matrix.argtypes = [_VP]
+        L.bo_ow_spmv.argtypes = [_VP, ctypes.c_double, _VP, ctypes.c_double, _VP]
+        for f in (L.bo_ow_solve, L.bo_ow_solve_bicgstab):
+            f.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(bo_solve_opts), ctypes.POINTER(bo_solve_info)]
+        L.bo_ow_destroy.argtypes = [_VP]
         _lib = L
     return _lib
 
@@ -500,6 +514,66 @@ class DualPorosity:
             pass
 
 
+class OilWater:
+    """bo_ow: a two-phase oil-water system (2x2 blocks, see
+    include/bosolve.h).  `matrix` is the padded three-unknown matrix to set
+    the preconditioner up on; vectors hold 2N doubles."""
+
+    def __init__(self, ctx: "Context", nx, ny, nz, rowptr, col, val, dx=100.0, dy=100.0, dz=20.0):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = _f64(val)
+        N = nx * ny * nz
+        nnzb = col.size
+        _need(val, 4 * nnzb, "val")
+        vp, mem = _ptr(val)
+        if mem == BO_MEM_DEVICE:
+            raise BoArgError("pass the pattern and first values as host arrays")
+        h = _VP()
+        g = bo_grid(nx, ny, nz, dx, dy, dz, 1)
+        _check(lib().bo_ow_create(ctx.h, ctypes.byref(g), N, nnzb, _VP(rowptr.ctypes.data), _VP(col.ctypes.data), vp,
+                                  BO_MEM_HOST, ctypes.byref(h)), "bo_ow_create")
+        self.h, self.ctx, self.N, self.nval = h, ctx, N, 4 * nnzb
+        self.n = 2 * N
+        self.matrix = Matrix(ctx, g, _VP(lib().bo_ow_matrix(h)), ())
+        self.matrix.close = lambda: None
+
+    def update_values(self, val):
+        val = _f64(val)
+        _need(val, self.nval, "val")
+        vp, mem = _ptr(val)
+        if mem == BO_MEM_DEVICE:
+            _on_device(val, self.ctx, "val")
+        _check(lib().bo_ow_update_values(self.h, vp, mem), "bo_ow_update_values")
+
+    def spmv(self, x, y, alpha=1.0, beta=0.0):
+        _check(lib().bo_ow_spmv(self.h, float(alpha), _dvec(x, self.n, "x", self.ctx), float(beta),
+                                _dvec(y, self.n, "y", self.ctx)), "bo_ow_spmv")
+        return y
+
+    def solve(self, P: "Preconditioner", b, x, tol=1e-8, restart=30, maxit=500, x0_is_zero=True,
+              raise_on_error=True, bicgstab=False):
+        o = bo_solve_opts(tol, restart, maxit, int(x0_is_zero), BO_MEM_DEVICE, 0)
+        info = bo_solve_info()
+        f = lib().bo_ow_solve_bicgstab if bicgstab else lib().bo_ow_solve
+        rc = f(self.h, P.h, _dvec(b, self.n, "b", self.ctx), _dvec(x, self.n, "x", self.ctx), ctypes.byref(o),
+               ctypes.byref(info))
+        if raise_on_error and rc != BO_OK:
+            raise BoError(rc, "bo_ow_solve")
+        return info.as_dict()
+
+    def close(self):
+        if self.h and _alive():
+            lib().bo_ow_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Wells:
     """bo_wells: the border of rate-controlled wells on a matrix (see
     include/bosolve.h).  perf_cell, perf_well: one entry per perforation,
@@ -568,8 +642,9 @@ class Wells:
 class Preconditioner:
     """bo_prec: CPR-FPF (decoupling + red-black block ILU(0) + AMG)."""
 
-    def __init__(self, mat: Matrix, precision=BO_PREC_FP64, nu1=2, nu2=2, overcorr=1.3, coarse_max=128):
-        o = bo_prec_opts(precision, nu1, nu2, overcorr, coarse_max)
+    def __init__(self, mat: Matrix, precision=BO_PREC_FP64, nu1=2, nu2=2, overcorr=1.3, coarse_max=128,
+                 decoupling=0):
+        o = bo_prec_opts(precision, nu1, nu2, overcorr, coarse_max, decoupling)
         h = _VP()
         _check(lib().bo_prec_setup(mat.h, ctypes.byref(o), ctypes.byref(h)), "bo_prec_setup")
         self.mat, self.h, self.opts = mat, h, o

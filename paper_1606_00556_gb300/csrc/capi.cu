@@ -278,6 +278,7 @@ void bo_prec_opts_default(bo_prec_opts* o) {
   o->amg_nu2 = 2;
   o->amg_overcorr = 1.3;
   o->amg_coarse_max = 128;
+  o->decoupling = BO_DECOUPLE_QI;
 }
 
 void bo_solve_opts_default(bo_solve_opts* o) {
@@ -365,6 +366,7 @@ int bo_prec_setup(bo_mat* m, const bo_prec_opts* opts, bo_prec** out) {
   if ((o.precision != BO_PREC_FP64 && o.precision != BO_PREC_FP32 && o.precision != BO_PREC_BF16) ||
       o.amg_nu1 < 0 || o.amg_nu2 < 0 ||
       o.amg_nu1 > 8 || o.amg_nu2 > 8 || o.amg_coarse_max < 1 || o.amg_coarse_max > 128 ||
+      (o.decoupling != BO_DECOUPLE_QI && o.decoupling != BO_DECOUPLE_ABF) ||
       !(o.amg_overcorr > 0.0 && o.amg_overcorr < 4.0))
     return BO_ERR_ARG;
   if (cudaSetDevice(m->ctx->device) != cudaSuccess) return BO_ERR_CUDA;

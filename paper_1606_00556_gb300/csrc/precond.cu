@@ -115,7 +115,10 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { ret
 // flooded to residual oil: the oil row carries no pressure information and
 // the water pivot is negative), the cell takes the exact local decoupling,
 // g = row 0 of A_ii^{-1} (pivot 1), which keeps the AMG operator's diagonal
-// positive for the Gauss-Seidel smoother.  Writes the weights [3][N] and the
+// positive for the Gauss-Seidel smoother.  With abf set every cell takes
+// that row: the ABF decoupling (D = block diagonal of A) restricted to the
+// pressure row, which is all of it the CPR needs (block ILU(0) is invariant
+// under a block-diagonal left scaling).  Writes the weights [3][N] and the
 // decoupled blocks in storage type S.  The weights are formed in FP64; for
 // FP32 or BF16 storage the decoupled rows are formed from the split copy of
 // A in split FP32 pairs (FP32 instructions; the result rounded once to S),
@@ -134,7 +137,7 @@ __device__ __forceinline__ __nv_bfloat16 store_split<__nv_bfloat16>(df v) {
 template <typename S>
 __global__ void k_decouple(Geom g, const double* __restrict__ A, const float2* __restrict__ A2,
                            const int* __restrict__ range, S* __restrict__ At, double* __restrict__ w,
-                           float* __restrict__ wf, DevState* st) {
+                           float* __restrict__ wf, int abf, DevState* st) {
   const bool split = sizeof(S) < sizeof(double) && A2 && !*range;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
@@ -148,7 +151,7 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, const float2* _
     } else {
       g1 = -D[1] / D[4];
       g2 = -D[2] / D[8];
-      if (!(g0 * D[0] + g1 * D[3] + g2 * D[6] > 0.0)) {
+      if (abf || !(g0 * D[0] + g1 * D[3] + g2 * D[6] > 0.0)) {
         double inv[9];
         if (inv3(D, inv)) {
           g0 = inv[0];
@@ -1814,7 +1817,7 @@ int values_impl(bo_prec* P) {
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
   (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, m->a2_valid ? m->A2 : nullptr, m->a2_range, (S*)P->At, P->w, P->wf,
-                                         P->st), note_launch());
+                                         P->opts.decoupling == BO_DECOUPLE_ABF, P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
   if (sizeof(S) < sizeof(double) && m->a2_valid) {

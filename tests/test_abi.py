@@ -83,7 +83,7 @@ def test_host_side_contract_without_a_gpu(libpath):
     po = bo.bo_prec_opts()
     L.bo_prec_opts_default(ctypes.byref(po))
     assert (po.precision, po.amg_nu1, po.amg_nu2, po.amg_coarse_max) == (bo.BO_PREC_FP64, 2, 2, 128)
-    assert po.amg_overcorr == 1.3
+    assert po.amg_overcorr == 1.3 and po.decoupling == bo.BO_DECOUPLE_QI
     so = bo.bo_solve_opts()
     L.bo_solve_opts_default(ctypes.byref(so))
     assert (so.tol, so.restart, so.maxit, so.mem) == (1e-8, 30, 500, bo.BO_MEM_DEVICE)
@@ -135,6 +135,12 @@ def test_every_entry_point_rejects_missing_handles(libpath):
         "bo_wells_spmv": (N, ctypes.c_double(1.0), N, ctypes.c_double(0.0), N),
         "bo_solve_bordered": (N, N, N, N, N, N),
         "bo_wells_destroy": (N,),
+        "bo_ow_create": (N, N, 0, 0, N, N, N, 0, N),
+        "bo_ow_update_values": (N, N, 0),
+        "bo_ow_spmv": (N, ctypes.c_double(1.0), N, ctypes.c_double(0.0), N),
+        "bo_ow_solve": (N, N, N, N, N, N),
+        "bo_ow_solve_bicgstab": (N, N, N, N, N, N),
+        "bo_ow_destroy": (N,),
         "bo_cnn_create": (N, 8, 8, 8, 1, ctypes.c_uint64(0), N),
         "bo_cnn_destroy": (N,),
         "bo_cnn_get_params": (N, N, 0),
@@ -155,5 +161,6 @@ def test_every_entry_point_rejects_missing_handles(libpath):
     for name, args in calls.items():
         assert getattr(L, name)(*args) == bo.BO_ERR_ARG, name
     assert L.bo_dp_fracture_matrix(None) is None
+    assert L.bo_ow_matrix(None) is None
     # the stream pool is 1..16 wide
     assert L.bo_set_batch_streams(0) == bo.BO_ERR_ARG and L.bo_set_batch_streams(17) == bo.BO_ERR_ARG
