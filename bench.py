@@ -779,6 +779,48 @@ def wells_record(bo, ctx, dev, dims, a, repeats=5):
     return rec
 
 
+def oil_water_record(bo, ctx, dev, dims, a, a3, repeats=5):
+    """The two-phase oil-water model (paper Sec. 2.2) on the benchmark's grid,
+    rock and wells (the day-0 waterflood front mapped onto [s_wc, 1 - s_or]):
+    time to 1e-8 with the FP32 CPR under Quasi-IMPES and ABF decoupling, by
+    FGMRES and by BiCGSTAB; and the three-phase day-0 Jacobian with ABF
+    against Quasi-IMPES.  Wall times around synchronised solves (median of
+    `repeats`)."""
+    import torch
+    ow = bo.OilWater(ctx, *dims, a["rowptr"], a["col"], a["val"].ravel())
+    b = torch.tensor(a["b"], device=dev)
+    x = torch.zeros_like(b)
+
+    def timed(fn, xv):
+        ts, info = [], None
+        for _ in range(repeats + 1):
+            xv.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return {"ms": float(np.median(ts[1:])), "iters": info["iters"], "true_rel_res": info["true_rel_res"]}
+
+    rec = {"workload": (f"two-phase oil-water {dims[0]}x{dims[1]}x{dims[2]} (2 unknowns/cell, 2x2 BSR stored "
+                        "padded to 3x3), day-0 waterflood front, FP32 CPR, tol 1e-8")}
+    for name, dec in (("qi", bo.BO_DECOUPLE_QI), ("abf", bo.BO_DECOUPLE_ABF)):
+        P = bo.Preconditioner(ow.matrix, precision=bo.BO_PREC_FP32, decoupling=dec)
+        rec[f"fgmres_{name}"] = timed(lambda: ow.solve(P, b, x, tol=1e-8, maxit=400), x)
+        rec[f"bicgstab_{name}"] = timed(lambda: ow.solve(P, b, x, tol=1e-8, maxit=400, bicgstab=True), x)
+        P.close()
+    ow.close()
+    A = bo.Matrix.from_bsr(ctx, bo.grid(*dims), a3["rowptr"], a3["col"], a3["val"])
+    b3 = torch.tensor(a3["b"], device=dev)
+    x3 = torch.zeros_like(b3)
+    for name, dec in (("qi", bo.BO_DECOUPLE_QI), ("abf", bo.BO_DECOUPLE_ABF)):
+        P = bo.Preconditioner(A, precision=bo.BO_PREC_FP32, decoupling=dec)
+        rec[f"three_phase_fgmres_{name}"] = timed(lambda: P.solve(b3, x3, tol=1e-8, maxit=400), x3)
+        P.close()
+    A.close()
+    return rec
+
+
 def run_mixed(bo, ctx, dev, stream, a, args):
     """The 256x256x128 Jacobian with the FP32, BF16-storage and FP64
     preconditioners: per precision one untimed step, then args.mixed_steps
@@ -847,7 +889,7 @@ def main():
                     help="the 1M-cell Jacobians of successive days: advanced by the device Newton method "
                          "(default), or the generator's synthetic fronts")
     ap.add_argument("--no-wells", action="store_true",
-                    help="skip the rate-controlled-wells record of the default line")
+                    help="skip the rate-controlled-wells and oil-water records of the default line")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 256-realisation ensembles (single and dual porosity) of the default line")
     ap.add_argument("--ensemble-steps", type=int, default=3, help="timed steps of each ensemble in the default line")
@@ -910,11 +952,12 @@ def main():
     if rank == 0 and not args.no_ensemble:
         ens_in = ensemble_inputs(args.ensemble, os.cpu_count() or 1)
         dual_in = ensemble_inputs(args.ensemble, os.cpu_count() or 1, dual=True)
-    wells_a = None
+    wells_a = ow_a = None
     if rank == 0 and not args.no_wells:
         import bogen
         bogen.build()
         wells_a = bogen.assemble(bogen.with_rate_controls(bogen.waterflood_case(*dims, seed=SEED, day=0)))
+        ow_a = bogen.assemble_ow(bogen.oil_water_case(*dims, seed=SEED, day=0))
     mix_a = None
     if mixed:
         import bogen
@@ -1124,10 +1167,14 @@ def main():
     if mix_a is not None:
         mixed_rec, mixed_x = run_mixed(bo, ctx, dev, stream, mix_a, args)
         del mix_a
-    wells_rec = None
+    wells_rec = ow_rec = None
     if wells_a is not None:
         wells_rec = wells_record(bo, ctx, dev, dims, wells_a)
         del wells_a
+    if ow_a is not None:
+        a3 = {"rowptr": jac[0][0], "col": jac[0][1], "val": jac[0][2], "b": jac[0][3]}
+        ow_rec = oil_water_record(bo, ctx, dev, dims, ow_a, a3)
+        del ow_a
     ens_rec = dual_rec = None
     if ens_in is not None:
         # the batched ensembles (configs of 256 realisations, 38M unknowns)
@@ -1160,6 +1207,7 @@ def main():
             "spmv": sp, "spmv_cpu": cpu_spmv, "secondary": second, "cpu_baseline": cpu_rec, "e2e": e2e,
             "errors": errors or None, "mixed_256x256x128": mixed_rec, "newton_sequence": newton_rec,
             "ensemble": ens_rec, "ensemble_dual_porosity": dual_rec, "rate_controlled_wells": wells_rec,
+            "oil_water": ow_rec,
             "precision_note": ("no all-FP64 path is timed: even the FP64 preconditioner form computes the Arnoldi "
                                "product in split FP32 pairs (2^-46 relative per term); convergence is decided "
                                "on the FP64 true residual of the original system"),
