@@ -692,6 +692,10 @@ int bo_set_amg_cooperative(int on);
  * solve starts clean.  No counterpart in the paper: it exists so the bounded
  * waits' error path can be exercised without hanging a GPU. */
 int bo_set_amg_barrier_spins(uint32_t spins);
+/* Gram-Schmidt form of the Arnoldi step (CGS2): 1 (default) three passes
+ * over the basis, the first update fused with the second coefficient pass;
+ * 0 four separate passes.  The same arithmetic; process-wide. */
+int bo_set_gs_fused(int on);
 /* BO_ERR_TIMEOUT if a tcgen05 convolution gave up waiting on one of its
  * barriers since the last call (its output is then incomplete), else BO_OK;
  * clears the flag.  Synchronises the device. */

@@ -58,7 +58,7 @@ EXPORTS = (
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_solve_batched",
     "bo_dp_destroy",
     "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
-    "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins",
+    "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins", "bo_set_gs_fused",
     "bo_newton_opts_default", "bo_model_create", "bo_model_destroy", "bo_model_assemble", "bo_newton_solve",
     "bo_wells_create", "bo_wells_update_values", "bo_wells_set_coupling", "bo_wells_spmv", "bo_solve_bordered",
     "bo_wells_destroy",
@@ -220,6 +220,7 @@ def lib():
         L.bo_set_conv_engine.argtypes = [_i]
         L.bo_set_amg_cooperative.argtypes = [_i]
         L.bo_set_amg_barrier_spins.argtypes = [ctypes.c_uint32]
+        L.bo_set_gs_fused.argtypes = [_i]
         L.bo_tc_status.argtypes = []
         L.bo_update_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), _i]
         L.bo_autotune_batched.argtypes = [ctypes.POINTER(_VP), _i, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -822,6 +823,12 @@ def bo_set_amg_cooperative(on: int):
     one cluster launch for the coarser levels; 1: the cooperative launches
     cover every multi-block level; 0: one kernel per sweep."""
     _check(lib().bo_set_amg_cooperative(int(on)), "bo_set_amg_cooperative")
+
+
+def bo_set_gs_fused(on: int):
+    """1 (default): CGS2 in three passes (first update fused with the second
+    coefficient pass); 0: four separate passes."""
+    _check(lib().bo_set_gs_fused(int(on)), "bo_set_gs_fused")
 
 
 def bo_set_amg_barrier_spins(spins: int):

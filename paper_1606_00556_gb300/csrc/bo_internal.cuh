@@ -339,6 +339,9 @@ extern std::atomic<int> g_amg_coop;
 // polls of an AMG grid barrier before it gives up (default 2^22, about 0.1 s)
 constexpr unsigned kAmgSpinsDefault = 1u << 22;
 extern std::atomic<unsigned> g_amg_spins;
+// Gram-Schmidt form: 1 (default) three passes (first update fused with the
+// second coefficients), 0 four separate passes
+extern std::atomic<int> g_gs_fused;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // grid size for a grid-stride loop over n items

@@ -19,6 +19,7 @@ std::atomic<int> g_pool_width{kMaxPoolStreams};
 std::atomic<int> g_conv_engine{1};
 std::atomic<int> g_amg_coop{1};
 std::atomic<unsigned> g_amg_spins{kAmgSpinsDefault};
+std::atomic<int> g_gs_fused{1};
 
 int occ_grid(const void* kernel, int64_t n, int threads, size_t smem) {
   static std::mutex mu;
@@ -578,6 +579,12 @@ int bo_set_amg_cooperative(int on) {
 
 int bo_set_amg_barrier_spins(uint32_t spins) {
   g_amg_spins.store(spins == 0 ? kAmgSpinsDefault : spins);
+  return BO_OK;
+}
+
+int bo_set_gs_fused(int on) {
+  if (on != 0 && on != 1) return BO_ERR_ARG;
+  g_gs_fused.store(on);
   return BO_OK;
 }
 

@@ -379,6 +379,136 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __
   if (threadIdx.x == 0) st->counter[0] = 0;
 }
 
+// Gram-Schmidt coefficients with every column in one pass: each thread
+// reads its groups of four entries of w once and accumulates the products
+// with every column in registers (NVMAX accumulators, the column count
+// rounded up to a bucket), so w is read once instead of once per column;
+// the sums are reduced once, at the end: over the warp by shuffles, over
+// the block in shared memory (fixed order), one partial per column and
+// block, and the block that finishes last reduces each column's partials
+// as k_gs_dots does.
+//   FUSED = false: CGS2's first pass, h[u] = vscale[u] <V_u, w> on the high
+//     planes (FP32 products and per-thread sums);
+//   FUSED = true: CGS2's first update and second pass in one: the thread
+//     forms w1 = w - sum_k h[k] vscale[k] V_k for its group (as k_gs_update
+//     does), stores it, and sums <V_u, w1> in split arithmetic into
+//     h[kMaxM + u] from the same group of w1.  Each V_u is read twice by
+//     the thread, the second time from cache, so DRAM sees one pass over
+//     the basis where the separate update and dots passes made two.
+// Grid: as many blocks as the partials hold for the bucket's columns.
+template <bool FUSED, int NVMAX>
+__global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __restrict__ V, int64_t ldv,
+                                                     float* __restrict__ w, double* partials, DevState* st, int nv) {
+  __shared__ df c[kMaxM + 1];
+  __shared__ double wacc[kThreads / 32][NVMAX];
+  if (st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t np = split_pad(n);
+  const int64_t ng = (n + 3) >> 2;
+  if (FUSED)
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[k] * st->vscale[k]));
+  __syncthreads();
+  df acc[NVMAX];
+  float acc32[NVMAX];
+#pragma unroll
+  for (int u = 0; u < NVMAX; ++u) {
+    acc[u] = df{0.f, 0.f};
+    acc32[u] = 0.f;
+  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ng; q += (int64_t)gridDim.x * blockDim.x) {
+    const int valid = (int)min((int64_t)4, n - 4 * q);
+    const float* a = V + 4 * q;
+    if (FUSED) {
+      const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
+      df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
+#pragma unroll 2
+      for (int k = 0; k < nv; ++k) {
+        const float4 ah = ld4(a + (size_t)k * ldv), al = ld4(a + (size_t)k * ldv + np);
+        const df ck = c[k];
+        s0 = df_fma_acc(s0, ck, df{ah.x, al.x});
+        s1 = df_fma_acc(s1, ck, df{ah.y, al.y});
+        s2 = df_fma_acc(s2, ck, df{ah.z, al.z});
+        s3 = df_fma_acc(s3, ck, df{ah.w, al.w});
+      }
+      s0 = df_renorm(s0);
+      s1 = df_renorm(s1);
+      s2 = df_renorm(s2);
+      s3 = df_renorm(s3);
+      if (valid == 4) {
+        st4(w + 4 * q, make_float4(s0.hi, s1.hi, s2.hi, s3.hi));
+        st4(w + np + 4 * q, make_float4(s0.lo, s1.lo, s2.lo, s3.lo));
+      } else {
+        const df sv[4] = {s0, s1, s2, s3};
+        for (int e = 0; e < valid; ++e) {
+          w[4 * q + e] = sv[e].hi;
+          w[np + 4 * q + e] = sv[e].lo;
+        }
+      }
+      const float4 xh = mask4(make_float4(s0.hi, s1.hi, s2.hi, s3.hi), valid);
+      const float4 xl = mask4(make_float4(s0.lo, s1.lo, s2.lo, s3.lo), valid);
+#pragma unroll
+      for (int u = 0; u < NVMAX; ++u) {
+        if (u < nv) {
+          const float4 ah = ld4(a + (size_t)u * ldv), al = ld4(a + (size_t)u * ldv + np);
+          acc[u] = df_fma_acc(acc[u], df{ah.x, al.x}, df{xh.x, xl.x});
+          acc[u] = df_fma_acc(acc[u], df{ah.y, al.y}, df{xh.y, xl.y});
+          acc[u] = df_fma_acc(acc[u], df{ah.z, al.z}, df{xh.z, xl.z});
+          acc[u] = df_fma_acc(acc[u], df{ah.w, al.w}, df{xh.w, xl.w});
+        }
+      }
+    } else {
+      const float4 xh = mask4(ld4(w + 4 * q), valid);
+#pragma unroll
+      for (int u = 0; u < NVMAX; ++u) {
+        if (u < nv) {
+          const float4 ah = mask4(ld4(a + (size_t)u * ldv), valid);
+          acc32[u] = fmaf(ah.w, xh.w, fmaf(ah.z, xh.z, fmaf(ah.y, xh.y, fmaf(ah.x, xh.x, acc32[u]))));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NVMAX; ++u) {
+    if (u < nv) {
+      const double p = warp_sum(FUSED ? df_to_double(df_renorm(acc[u])) : (double)acc32[u]);
+      if (lane == 0) wacc[warp][u] = p;
+    }
+  }
+  __syncthreads();
+  const int nblk = gridDim.x;
+  for (int u = threadIdx.x; u < nv; u += blockDim.x) {
+    double t = 0.0;
+    for (int r = 0; r < kThreads / 32; ++r) t += wacc[r][u];
+    partials[(size_t)u * nblk + blockIdx.x] = t;
+  }
+  if (!last_block(&st->counter[0], nblk)) return;
+  const int off = FUSED ? kMaxM : 0;
+  for (int r = warp; r < nv; r += kThreads / 32) {
+    double t = 0.0;
+    for (int b = lane; b < nblk; b += 32) t += __ldcg(partials + (size_t)r * nblk + b);
+    t = warp_sum(t);
+    if (lane == 0) st->h[off + r] = t * st->vscale[r];
+  }
+  if (threadIdx.x == 0) st->counter[0] = 0;
+}
+
+// launch of k_gs_pass with the column bucket for nv columns
+template <bool FUSED>
+void launch_gs_pass(int64_t n, const float* V, int64_t ldv, float* w, double* partials, DevState* st, int nv,
+                    cudaStream_t s) {
+  const int64_t ng = (n + 3) >> 2;
+  // the partials hold (kMaxM + 2) kDotBlocks values: as many blocks per
+  // column as fit for the bucket's column count
+  auto go = [&](const void* k, auto kern, int nvmax) {
+    const int g = std::min(occ_grid(k, ng), (kMaxM + 2) * kDotBlocks / nvmax);
+    (kern<<<g, kThreads, 0, s>>>(n, V, ldv, w, partials, st, nv), note_launch());
+  };
+  if (nv <= 8) go((const void*)k_gs_pass<FUSED, 8>, k_gs_pass<FUSED, 8>, 8);
+  else if (nv <= 16) go((const void*)k_gs_pass<FUSED, 16>, k_gs_pass<FUSED, 16>, 16);
+  else if (nv <= 32) go((const void*)k_gs_pass<FUSED, 32>, k_gs_pass<FUSED, 32>, 32);
+  else go((const void*)k_gs_pass<FUSED, kMaxM + 1>, k_gs_pass<FUSED, kMaxM + 1>, kMaxM + 1);
+}
+
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
 // arithmetic (the coefficients rounded to split pairs once per block, each
 // entry's sum carried as a split pair and renormalised once), four entries
@@ -671,10 +801,17 @@ struct Job {
     const ArnoldiArgs aa{P->H, P->cs, P->sn, P->gvec, j, m, m, dhist};
     const int nv = j + 1;
     const int gu = occ_grid((const void*)k_gs_update<true>, nn);
-    const dim3 gd(gs_chunks(nn), nv);
-    (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
-    (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
-    (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+    if (g_gs_fused.load()) {
+      // CGS2 in three passes over the basis: the first coefficients, the
+      // first update fused with the second coefficients, the final update
+      launch_gs_pass<false>(nn, V, ldv, w, P->partials, st, nv, s);
+      launch_gs_pass<true>(nn, V, ldv, w, P->partials, st, nv, s);
+    } else {
+      const dim3 gd(gs_chunks(nn), nv);
+      (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+      (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
+      (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+    }
     (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
 

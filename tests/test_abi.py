@@ -89,6 +89,7 @@ def test_host_side_contract_without_a_gpu(libpath):
     assert (so.tol, so.restart, so.maxit, so.mem) == (1e-8, 30, 500, bo.BO_MEM_DEVICE)
     assert L.bo_set_amg_cooperative(3) == bo.BO_ERR_ARG and L.bo_set_amg_cooperative(-1) == bo.BO_ERR_ARG
     assert L.bo_set_amg_cooperative(1) == bo.BO_OK and L.bo_set_amg_cooperative(2) == bo.BO_OK
+    assert L.bo_set_gs_fused(2) == bo.BO_ERR_ARG and L.bo_set_gs_fused(1) == bo.BO_OK
     assert L.bo_set_conv_engine(7) == bo.BO_ERR_ARG
     for f in ("bo_solve", "bo_solve_bicgstab"):
         assert getattr(L, f)(None, None, None, None, None) == bo.BO_ERR_ARG

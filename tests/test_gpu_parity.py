@@ -387,6 +387,34 @@ def test_solve_tiny_matches_oracle(bo, ctx, seed, precision):
     assert hist.size == info["iters"] and np.all(np.isfinite(hist))
 
 
+@pytest.mark.parametrize("restart", [8, 30, 40])
+def test_gram_schmidt_forms_agree(bo, ctx, restart):
+    # CGS2 in three passes (first update fused with the second coefficients;
+    # the default) and in four separate passes: the same Arnoldi step, so
+    # the same iteration count, the same Hessenberg estimates to rounding,
+    # and both solutions within the parity bar (restart 40 exercises the
+    # widest column bucket)
+    dims = (20, 20, 5)
+    a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(1), dims)
+    b = _dev(a["b"])
+    xr = _xref(Ao, a["b"])
+    out = {}
+    try:
+        for mode in (0, 1):
+            bo.bo_set_gs_fused(mode)
+            x = torch.zeros_like(b)
+            info = P.solve(b, x, tol=1e-10, restart=restart, maxit=300)
+            out[mode] = (info, P.residual_history(), x.cpu().numpy())
+    finally:
+        bo.bo_set_gs_fused(1)
+    (i0, h0, x0), (i1, h1, x1) = out[0], out[1]
+    assert i0["iters"] == i1["iters"] and i0["status"] == i1["status"] == bo.BO_OK
+    assert np.all(np.abs(h0 - h1) <= 1e-6 * h0)
+    for xg in (x0, x1):
+        assert oracle.rel_residual(Ao, a["b"], xg) <= 1e-10
+        assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
 def test_solve_edge_cases(bo, ctx):
     dims = (20, 20, 5)
     a, Ao, A, P = _cpr_pair(bo, ctx, bogen.tiny_case(0), dims)
