@@ -312,20 +312,27 @@ struct ArnoldiArgs {
 
 // Gram-Schmidt coefficient passes: h[off + u] = vscale[u] <V_u, w> for
 // u <= j.  Grid (chunks, j + 1): block (c, u) sums column u over chunk c of
-// the groups of four entries, kDotB groups per thread at a time with all
-// their loads issued first (each thread keeps 2 kDotB, or 4 kDotB, 16-byte
-// loads in flight); the block that finishes last reduces each column's
-// partials (FP64) with one warp per column.
+// the groups of four entries, B groups per thread at a time with all their
+// loads issued first (2 B, or 4 B, 16-byte loads in flight per thread); the
+// block that finishes last reduces each column's partials (FP64) with one
+// warp per column.  A block streams one contiguous stretch of one column
+// (w, read once per column, stays in L2), and the chunk count makes the
+// grid about one wave of resident blocks: measured at 3.1M entries, this
+// reads the basis at 64-85% of HBM bandwidth for 2-30 columns, against
+// 34-36% when every thread reads every column.
 //   SPLIT = false: the first pass, on the high planes only (FP32 products
-//     and per-thread sums), off = 0;
-//   SPLIT = true: the second pass, in split arithmetic (each thread's
-//     products and sums as split pairs), off = kMaxM.
+//     and per-thread sums), off = 0, B = 8;
+//   SPLIT = true: the second pass of the four-pass form, in split
+//     arithmetic (each thread's products and sums as split pairs),
+//     off = kMaxM, B = 4.
 // The block and chunk sums are FP64 in both.
-constexpr int kDotB = 4;
+template <bool SPLIT>
+__host__ __device__ constexpr int dot_groups() { return SPLIT ? 4 : 8; }
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                      const float* __restrict__ w, double* partials, DevState* st) {
+  constexpr int kDotB = dot_groups<SPLIT>();
   __shared__ double sh[32];
   if (st->done) return;
   const int nv = gridDim.y;
@@ -379,90 +386,97 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __
   if (threadIdx.x == 0) st->counter[0] = 0;
 }
 
-// Gram-Schmidt coefficients with every column in one pass: each thread
-// reads its groups of four entries of w once and accumulates the products
-// with every column in registers (NVMAX accumulators, the column count
-// rounded up to a bucket), so w is read once instead of once per column;
-// the sums are reduced once, at the end: over the warp by shuffles, over
+// CGS2's first update and second coefficient pass in one pass over the
+// basis: each thread forms w1 = w - sum_k h[k] vscale[k] V_k for its group of
+// four entries (as k_gs_update does), stores it, and sums <V_u, w1> in split
+// arithmetic into per-thread accumulators for every column (NVMAX of them,
+// the column count rounded up to a bucket), so h[kMaxM + u] needs no second
+// pass over w1.  Each V_u is read twice by the thread, the second time from
+// cache, so DRAM sees one pass over the basis where the separate update and
+// coefficient passes made two.  Both loops take the columns in batches of
+// kGsBatch, all of a batch's loads issued before its arithmetic (with a
+// conditional load per column the loads of successive columns were not in
+// flight together: 40-45% of HBM against 50-56% batched, at 3.1M entries).
+// The sums are reduced once, at the end: over the warp by shuffles, over
 // the block in shared memory (fixed order), one partial per column and
-// block, and the block that finishes last reduces each column's partials
-// as k_gs_dots does.
-//   FUSED = false: CGS2's first pass, h[u] = vscale[u] <V_u, w> on the high
-//     planes (FP32 products and per-thread sums);
-//   FUSED = true: CGS2's first update and second pass in one: the thread
-//     forms w1 = w - sum_k h[k] vscale[k] V_k for its group (as k_gs_update
-//     does), stores it, and sums <V_u, w1> in split arithmetic into
-//     h[kMaxM + u] from the same group of w1.  Each V_u is read twice by
-//     the thread, the second time from cache, so DRAM sees one pass over
-//     the basis where the separate update and dots passes made two.
+// block, and the block that finishes last reduces each column's partials.
 // Grid: as many blocks as the partials hold for the bucket's columns.
-template <bool FUSED, int NVMAX>
+constexpr int kGsBatch = 4;
+
+template <int NVMAX>
 __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                      float* __restrict__ w, double* partials, DevState* st, int nv) {
+  constexpr int B = kGsBatch;
   __shared__ df c[kMaxM + 1];
   __shared__ double wacc[kThreads / 32][NVMAX];
   if (st->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t np = split_pad(n);
   const int64_t ng = (n + 3) >> 2;
-  if (FUSED)
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[k] * st->vscale[k]));
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[k] * st->vscale[k]));
   __syncthreads();
   df acc[NVMAX];
-  float acc32[NVMAX];
 #pragma unroll
-  for (int u = 0; u < NVMAX; ++u) {
-    acc[u] = df{0.f, 0.f};
-    acc32[u] = 0.f;
-  }
+  for (int u = 0; u < NVMAX; ++u) acc[u] = df{0.f, 0.f};
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ng; q += (int64_t)gridDim.x * blockDim.x) {
     const int valid = (int)min((int64_t)4, n - 4 * q);
     const float* a = V + 4 * q;
-    if (FUSED) {
-      const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
-      df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
-#pragma unroll 2
-      for (int k = 0; k < nv; ++k) {
-        const float4 ah = ld4(a + (size_t)k * ldv), al = ld4(a + (size_t)k * ldv + np);
-        const df ck = c[k];
-        s0 = df_fma_acc(s0, ck, df{ah.x, al.x});
-        s1 = df_fma_acc(s1, ck, df{ah.y, al.y});
-        s2 = df_fma_acc(s2, ck, df{ah.z, al.z});
-        s3 = df_fma_acc(s3, ck, df{ah.w, al.w});
-      }
-      s0 = df_renorm(s0);
-      s1 = df_renorm(s1);
-      s2 = df_renorm(s2);
-      s3 = df_renorm(s3);
-      if (valid == 4) {
-        st4(w + 4 * q, make_float4(s0.hi, s1.hi, s2.hi, s3.hi));
-        st4(w + np + 4 * q, make_float4(s0.lo, s1.lo, s2.lo, s3.lo));
-      } else {
-        const df sv[4] = {s0, s1, s2, s3};
-        for (int e = 0; e < valid; ++e) {
-          w[4 * q + e] = sv[e].hi;
-          w[np + 4 * q + e] = sv[e].lo;
-        }
-      }
-      const float4 xh = mask4(make_float4(s0.hi, s1.hi, s2.hi, s3.hi), valid);
-      const float4 xl = mask4(make_float4(s0.lo, s1.lo, s2.lo, s3.lo), valid);
+    const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
+    df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
+    for (int k0 = 0; k0 < nv; k0 += B) {
+      float4 ah[B], al[B];
 #pragma unroll
-      for (int u = 0; u < NVMAX; ++u) {
-        if (u < nv) {
-          const float4 ah = ld4(a + (size_t)u * ldv), al = ld4(a + (size_t)u * ldv + np);
-          acc[u] = df_fma_acc(acc[u], df{ah.x, al.x}, df{xh.x, xl.x});
-          acc[u] = df_fma_acc(acc[u], df{ah.y, al.y}, df{xh.y, xl.y});
-          acc[u] = df_fma_acc(acc[u], df{ah.z, al.z}, df{xh.z, xl.z});
-          acc[u] = df_fma_acc(acc[u], df{ah.w, al.w}, df{xh.w, xl.w});
+      for (int b = 0; b < B; ++b) {
+        const int k = k0 + b < nv ? k0 + b : nv - 1;  // past the last column: a repeat, not used
+        ah[b] = ld4(a + (size_t)k * ldv);
+        al[b] = ld4(a + (size_t)k * ldv + np);
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (k0 + b < nv) {
+          const df ck = c[k0 + b];
+          s0 = df_fma_acc(s0, ck, df{ah[b].x, al[b].x});
+          s1 = df_fma_acc(s1, ck, df{ah[b].y, al[b].y});
+          s2 = df_fma_acc(s2, ck, df{ah[b].z, al[b].z});
+          s3 = df_fma_acc(s3, ck, df{ah[b].w, al[b].w});
         }
       }
+    }
+    s0 = df_renorm(s0);
+    s1 = df_renorm(s1);
+    s2 = df_renorm(s2);
+    s3 = df_renorm(s3);
+    if (valid == 4) {
+      st4(w + 4 * q, make_float4(s0.hi, s1.hi, s2.hi, s3.hi));
+      st4(w + np + 4 * q, make_float4(s0.lo, s1.lo, s2.lo, s3.lo));
     } else {
-      const float4 xh = mask4(ld4(w + 4 * q), valid);
+      const df sv[4] = {s0, s1, s2, s3};
+      for (int e = 0; e < valid; ++e) {
+        w[4 * q + e] = sv[e].hi;
+        w[np + 4 * q + e] = sv[e].lo;
+      }
+    }
+    const float4 xh = mask4(make_float4(s0.hi, s1.hi, s2.hi, s3.hi), valid);
+    const float4 xl = mask4(make_float4(s0.lo, s1.lo, s2.lo, s3.lo), valid);
 #pragma unroll
-      for (int u = 0; u < NVMAX; ++u) {
-        if (u < nv) {
-          const float4 ah = mask4(ld4(a + (size_t)u * ldv), valid);
-          acc32[u] = fmaf(ah.w, xh.w, fmaf(ah.z, xh.z, fmaf(ah.y, xh.y, fmaf(ah.x, xh.x, acc32[u]))));
+    for (int k0 = 0; k0 < NVMAX; k0 += B) {
+      if (k0 < nv) {
+        float4 ah[B], al[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const int k = k0 + b < nv ? k0 + b : nv - 1;
+          ah[b] = ld4(a + (size_t)k * ldv);
+          al[b] = ld4(a + (size_t)k * ldv + np);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const int u = k0 + b;
+          if (u < nv) {
+            acc[u] = df_fma_acc(acc[u], df{ah[b].x, al[b].x}, df{xh.x, xl.x});
+            acc[u] = df_fma_acc(acc[u], df{ah[b].y, al[b].y}, df{xh.y, xl.y});
+            acc[u] = df_fma_acc(acc[u], df{ah[b].z, al[b].z}, df{xh.z, xl.z});
+            acc[u] = df_fma_acc(acc[u], df{ah[b].w, al[b].w}, df{xh.w, xl.w});
+          }
         }
       }
     }
@@ -470,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __
 #pragma unroll
   for (int u = 0; u < NVMAX; ++u) {
     if (u < nv) {
-      const double p = warp_sum(FUSED ? df_to_double(df_renorm(acc[u])) : (double)acc32[u]);
+      const double p = warp_sum(df_to_double(df_renorm(acc[u])));
       if (lane == 0) wacc[warp][u] = p;
     }
   }
@@ -482,18 +496,16 @@ __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __
     partials[(size_t)u * nblk + blockIdx.x] = t;
   }
   if (!last_block(&st->counter[0], nblk)) return;
-  const int off = FUSED ? kMaxM : 0;
   for (int r = warp; r < nv; r += kThreads / 32) {
     double t = 0.0;
     for (int b = lane; b < nblk; b += 32) t += __ldcg(partials + (size_t)r * nblk + b);
     t = warp_sum(t);
-    if (lane == 0) st->h[off + r] = t * st->vscale[r];
+    if (lane == 0) st->h[kMaxM + r] = t * st->vscale[r];
   }
   if (threadIdx.x == 0) st->counter[0] = 0;
 }
 
 // launch of k_gs_pass with the column bucket for nv columns
-template <bool FUSED>
 void launch_gs_pass(int64_t n, const float* V, int64_t ldv, float* w, double* partials, DevState* st, int nv,
                     cudaStream_t s) {
   const int64_t ng = (n + 3) >> 2;
@@ -503,22 +515,32 @@ void launch_gs_pass(int64_t n, const float* V, int64_t ldv, float* w, double* pa
     const int g = std::min(occ_grid(k, ng), (kMaxM + 2) * kDotBlocks / nvmax);
     (kern<<<g, kThreads, 0, s>>>(n, V, ldv, w, partials, st, nv), note_launch());
   };
-  if (nv <= 8) go((const void*)k_gs_pass<FUSED, 8>, k_gs_pass<FUSED, 8>, 8);
-  else if (nv <= 16) go((const void*)k_gs_pass<FUSED, 16>, k_gs_pass<FUSED, 16>, 16);
-  else if (nv <= 32) go((const void*)k_gs_pass<FUSED, 32>, k_gs_pass<FUSED, 32>, 32);
-  else go((const void*)k_gs_pass<FUSED, kMaxM + 1>, k_gs_pass<FUSED, kMaxM + 1>, kMaxM + 1);
+  if (nv <= 8) go((const void*)k_gs_pass<8>, k_gs_pass<8>, 8);
+  else if (nv <= 16) go((const void*)k_gs_pass<16>, k_gs_pass<16>, 16);
+  else if (nv <= 32) go((const void*)k_gs_pass<32>, k_gs_pass<32>, 32);
+  else go((const void*)k_gs_pass<kMaxM + 1>, k_gs_pass<kMaxM + 1>, kMaxM + 1);
 }
 
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
 // arithmetic (the coefficients rounded to split pairs once per block, each
 // entry's sum carried as a split pair and renormalised once), four entries
-// per thread.  In the final pass (LAST) ||w||^2 is reduced in FP64 and the
-// last block applies the Givens step to h1 + h2 and stores 1/||w|| as the
-// new column's scale (w itself stays unnormalised).
+// per thread, the columns in batches of kGsBatch with all of a batch's loads
+// issued first (78-95% of HBM for 10-30 columns at 3.1M entries, against
+// 70-79% two columns at a time).  In the final pass (LAST) ||w||^2 is
+// reduced in FP64 and the last block applies the Givens step to h1 + h2 and
+// stores 1/||w|| as the new column's scale (w itself stays unnormalised).
+// The squares are summed in split arithmetic (FP32 instructions only; GB300's
+// FP64 pipe is narrow and this pass runs for every column) for groups whose
+// high parts all lie in [2^-50, 2^56] (or are zero), so every square and its
+// rounding error stay normal FP32 numbers and a thread's sum of up to 2^15
+// of them stays in range, and in FP64 for any other group; both keep about
+// 2^-46 of each term.  (A squared norm summed from the high parts
+// alone in FP32 has stalled ill-conditioned solves.)
 template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                        float* __restrict__ w, double* partials, DevState* st,
                                                        ArnoldiArgs aa) {
+  constexpr int B = kGsBatch;
   __shared__ df c[kMaxM + 1];
   __shared__ double sh[32];
   if (st->done) return;
@@ -528,19 +550,30 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
   const int64_t ng = (n + 3) >> 2;
   for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[off + k] * st->vscale[k]));
   __syncthreads();
-  double acc = 0.0;
+  double acc = 0.0;  // squares of the groups outside the split range
+  df accs{0.f, 0.f};  // squares in split arithmetic
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ng; q += (int64_t)gridDim.x * blockDim.x) {
     const float4 wh = ld4(w + 4 * q), wl = ld4(w + np + 4 * q);
     df s0{wh.x, wl.x}, s1{wh.y, wl.y}, s2{wh.z, wl.z}, s3{wh.w, wl.w};
     const float* a = V + 4 * q;
-#pragma unroll 2
-    for (int k = 0; k < nv; ++k) {
-      const float4 ah = ld4(a + (size_t)k * ldv), al = ld4(a + (size_t)k * ldv + np);
-      const df ck = c[k];
-      s0 = df_fma_acc(s0, ck, df{ah.x, al.x});
-      s1 = df_fma_acc(s1, ck, df{ah.y, al.y});
-      s2 = df_fma_acc(s2, ck, df{ah.z, al.z});
-      s3 = df_fma_acc(s3, ck, df{ah.w, al.w});
+    for (int k0 = 0; k0 < nv; k0 += B) {
+      float4 ah[B], al[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int k = k0 + b < nv ? k0 + b : nv - 1;  // past the last column: a repeat, not used
+        ah[b] = ld4(a + (size_t)k * ldv);
+        al[b] = ld4(a + (size_t)k * ldv + np);
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (k0 + b < nv) {
+          const df ck = c[k0 + b];
+          s0 = df_fma_acc(s0, ck, df{ah[b].x, al[b].x});
+          s1 = df_fma_acc(s1, ck, df{ah[b].y, al[b].y});
+          s2 = df_fma_acc(s2, ck, df{ah[b].z, al[b].z});
+          s3 = df_fma_acc(s3, ck, df{ah[b].w, al[b].w});
+        }
+      }
     }
     s0 = df_renorm(s0);
     s1 = df_renorm(s1);
@@ -558,13 +591,29 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
       }
     }
     if (LAST) {
-      const double d0 = df_to_double(s0), d1 = valid > 1 ? df_to_double(s1) : 0.0,
-                   d2 = valid > 2 ? df_to_double(s2) : 0.0, d3 = valid > 3 ? df_to_double(s3) : 0.0;
-      acc = fma(d3, d3, fma(d2, d2, fma(d1, d1, fma(d0, d0, acc))));
+      const float4 xh = mask4(make_float4(s0.hi, s1.hi, s2.hi, s3.hi), valid);
+      const float4 xl = mask4(make_float4(s0.lo, s1.lo, s2.lo, s3.lo), valid);
+      const df e[4] = {{xh.x, xl.x}, {xh.y, xl.y}, {xh.z, xl.z}, {xh.w, xl.w}};
+      bool safe = true;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float m = fabsf(e[i].hi);
+        safe = safe && (m == 0.f || (m >= 0x1p-50f && m <= 0x1p56f));
+      }
+      if (safe) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) accs = df_fma_acc(accs, e[i], e[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const double d = df_to_double(e[i]);
+          acc = fma(d, d, acc);
+        }
+      }
     }
   }
   if (!LAST) return;
-  acc = block_sum(acc, sh);
+  acc = block_sum(acc + df_to_double(df_renorm(accs)), sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
   if (!last_block(&st->counter[3], gridDim.x)) return;
   const double hn2 = reduce_partials(partials, gridDim.x, sh);
@@ -577,10 +626,16 @@ __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* 
   st->vscale[aa.j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
 }
 
-int gs_chunks(int64_t n) {
-  int64_t c = (n + 8 * kThreads - 1) / (8 * kThreads);
-  if (c < 1) c = 1;
+// chunks per column of a coefficient pass over nv columns: about one wave of
+// resident blocks in all, at most kDotBlocks per column (the partials' room)
+template <bool SPLIT>
+int gs_chunks(int64_t n, int nv) {
+  const int64_t ng = (n + 3) >> 2;
+  int64_t c = occ_grid((const void*)k_gs_dots<SPLIT>, ng) / nv;
+  const int64_t most = (ng + (int64_t)dot_groups<SPLIT>() * kThreads - 1) / ((int64_t)dot_groups<SPLIT>() * kThreads);
+  if (c > most) c = most;
   if (c > kDotBlocks) c = kDotBlocks;
+  if (c < 1) c = 1;
   return (int)c;
 }
 
@@ -804,13 +859,15 @@ struct Job {
     if (g_gs_fused.load()) {
       // CGS2 in three passes over the basis: the first coefficients, the
       // first update fused with the second coefficients, the final update
-      launch_gs_pass<false>(nn, V, ldv, w, P->partials, st, nv, s);
-      launch_gs_pass<true>(nn, V, ldv, w, P->partials, st, nv, s);
+      (k_gs_dots<false><<<dim3(gs_chunks<false>(nn, nv), nv), kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st),
+       note_launch());
+      launch_gs_pass(nn, V, ldv, w, P->partials, st, nv, s);
     } else {
-      const dim3 gd(gs_chunks(nn), nv);
-      (k_gs_dots<false><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+      (k_gs_dots<false><<<dim3(gs_chunks<false>(nn, nv), nv), kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st),
+       note_launch());
       (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
-      (k_gs_dots<true><<<gd, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st), note_launch());
+      (k_gs_dots<true><<<dim3(gs_chunks<true>(nn, nv), nv), kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st),
+       note_launch());
     }
     (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
