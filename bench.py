@@ -883,7 +883,7 @@ def main():
                          "storage of the preconditioner, FP32 arithmetic) or fp64")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--jacobians", type=int, default=10)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sequence", default="newton", choices=["newton", "synthetic"],
                     help="the 1M-cell Jacobians of successive days: advanced by the device Newton method "
@@ -1125,12 +1125,17 @@ def main():
         hv = [v.cpu().pin_memory() for v in vals[:args.e2e_steps]]
         hb = [b.cpu().pin_memory() for b in bs[:args.e2e_steps]]
         hx = torch.zeros(n, dtype=torch.float64).pin_memory()
+        # one untimed step first: the host-buffer path's staging is set up
+        # on its first use
+        A.update_values(hv[-1])
+        P.update()
+        P.solve(hb[-1], hx, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
-            A.update_values(hv[k])
+            A.update_values(hv[k % len(hv)])
             P.update()
-            info = P.solve(hb[k], hx, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True)
+            info = P.solve(hb[k % len(hb)], hx, tol=1e-8, restart=args.restart, maxit=1000, x0_is_zero=True)
             if info["status"] != 0:
                 raise RuntimeError(f"e2e solve failed: {info}")
         torch.cuda.synchronize()
