@@ -779,14 +779,19 @@ __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_res
     T acc[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) acc[r] = T(0);
+    // every slot's loads are issued whether or not its neighbour exists
+    // (a missing one reads the cell's own entries and is masked to zero),
+    // so all of a cell's loads can be in flight at once
 #pragma unroll
     for (int sl = 0; sl < 7; ++sl) {
-      const int64_t nq = nbr(g, c, q, sl);
-      if (nq < 0) continue;
-      const int xc = (sl == kDiag) ? color : (color ^ 1);
+      const int64_t nb = nbr(g, c, q, sl);
+      const bool ok = nb >= 0;
+      const int64_t nq = ok ? nb : q;
+      const int xc = (sl == kDiag || !ok) ? color : (color ^ 1);
       T x0 = z[vidx(g, 0, xc, nq)];
       if (ROWS == 3) x0 += e[(size_t)xc * g.Nh + nq];
-      const T x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
+      T x1 = z[vidx(g, 1, xc, nq)], x2 = z[vidx(g, 2, xc, nq)];
+      if (!ok) x0 = x1 = x2 = T(0);
       const S* a = At + at_index(g, color, sl * 9, q);
       constexpr size_t P = 32;  // entries (rc) of a block lie 32 apart in a tile
 #pragma unroll
@@ -1190,10 +1195,11 @@ __host__ __device__ size_t tail_smem_bytes(const TailArgs<T, S>& a) {
 // copied in once, every sweep then reads shared memory instead of L2, and
 // only the first tail level's iterate (read by the next finer level's
 // prolongation) is copied back.
+// Offsets of the tail levels in the dynamic shared memory (per level: the
+// coefficients, the right-hand side and the iterate; the coarse inverse at
+// off[72]), computed by thread 0.
 template <typename T, typename S>
-__global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, const DevState* st) {
-  if (st->done) return;
-  __shared__ uint32_t off[73];
+__device__ void tail_offsets(const TailArgs<T, S>& a, uint32_t* off) {
   if (threadIdx.x == 0) {
     uint32_t o = 0;
     for (int l = a.first; l <= a.last; ++l) {
@@ -1207,8 +1213,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
     }
     off[72] = o;
   }
-  __syncthreads();
-  const TailSharedViews<T, S> vw{&a, off};
+}
+
+// Copies the tail levels' coefficients and the coarse inverse into shared
+// memory (they do not change during a V-cycle; the caller synchronises).
+template <typename T, typename S>
+__device__ void tail_stage_coefficients(const TailArgs<T, S>& a, const TailSharedViews<T, S>& vw) {
   for (int l = a.first; l <= a.last; ++l) {
     const int64_t n = a.lv[l].d.n;
     S* c = const_cast<S*>(vw.lv(l).c);
@@ -1216,20 +1226,35 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
 #pragma unroll 8
     for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = src[i];
   }
-  {
-    const int64_t n = a.lv[a.first].d.n;
-    T* f = vw.lv(a.first).f;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = a.lv[a.first].f[i];
-    const int64_t nc = a.lv[a.last].d.n;
-    S* inv = const_cast<S*>(vw.inv());
+  const int64_t nc = a.lv[a.last].d.n;
+  S* inv = const_cast<S*>(vw.inv());
 #pragma unroll 8
-    for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = a.inv[i];
-  }
+  for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = a.inv[i];
+}
+
+// The tail V-cycle on staged coefficients: the first tail level's
+// right-hand side comes in from global memory (through L2: other blocks of
+// a cooperative launch wrote it), and only its iterate goes back.
+template <typename T, typename S>
+__device__ void tail_run_staged(const TailArgs<T, S>& a, const TailSharedViews<T, S>& vw) {
+  const int64_t n = a.lv[a.first].d.n;
+  T* f = vw.lv(a.first).f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = __ldcg(a.lv[a.first].f + i);
   __syncthreads();
   tail_cycle(a, vw);
-  const int64_t n = a.lv[a.first].d.n;
   const T* x = vw.lv(a.first).x;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a.lv[a.first].x[i] = x[i];
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, const DevState* st) {
+  if (st->done) return;
+  __shared__ uint32_t off[73];
+  tail_offsets(a, off);
+  __syncthreads();
+  const TailSharedViews<T, S> vw{&a, off};
+  tail_stage_coefficients(a, vw);
+  tail_run_staged(a, vw);
 }
 
 // ---- the multi-block AMG levels in two cooperative launches
@@ -1243,11 +1268,24 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, co
 // barrier of four 256-thread blocks, for the same threads
 constexpr int kCoopThreads = 1024;
 
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The arrival is a release (every write the block made before the barrier,
+// ordered by the block barrier ahead of it, is visible to whoever acquires
+// the flipped word) and the polls are acquires; no separate fences.
 __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned spins) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* word = &st->counter[5];
     volatile int* err = &st->err;
     int good = !(*err & kErrTimeout);
     if (good) {
@@ -1256,10 +1294,9 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned spins) {
       // the last one flips the word's top bit; a block has passed when the
       // top bit differs from the one its own addition saw.
       const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
-      __threadfence();
-      const unsigned old = atomicAdd(&st->counter[5], inc);
+      const unsigned old = atom_add_release(&st->counter[5], inc);
       unsigned it = 0;
-      while (((*word ^ old) & 0x80000000u) == 0) {
+      while (((ld_acquire(&st->counter[5]) ^ old) & 0x80000000u) == 0) {
         if (++it > spins || (*err & kErrTimeout)) {
           atomicOr(&st->err, kErrTimeout);
           good = 0;
@@ -1267,7 +1304,6 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned spins) {
         }
         __nanosleep(32);
       }
-      __threadfence();
     }
     ok = good;
   }
@@ -1299,8 +1335,7 @@ struct CycleArgs {
 // natural-order levels 1 .. tail_from - 1, a grid barrier after every half
 // sweep (the kernel-per-half-sweep form launches each separately).
 template <typename T, typename S>
-__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a, DevState* st) {
-  if (st->done) return;
+__device__ bool amg_down(const CycleArgs<T, S>& a, DevState* st) {
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
   const Geom& g = a.g;
   for (int sw = 0; sw < a.nu1; ++sw)
@@ -1308,11 +1343,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
       const int zero = sw == 0 && color == 0;
       sweep_batched<4>(t0, nt, g.Nh, a.x0 + (size_t)color * g.Nh,
                        [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, color, zero, q); });
-      if (!grid_barrier(st, a.spins)) return;
+      if (!grid_barrier(st, a.spins)) return false;
     }
   if (a.nu1 == 0) {
     for (int64_t t = t0; t < g.N; t += nt) a.x0[t] = T(0);
-    if (!grid_barrier(st, a.spins)) return;
+    if (!grid_barrier(st, a.spins)) return false;
   }
   // The first pre-smoothing half sweep of a multi-block level starts from
   // zero, x_r = f_r / a_rr: the thread that restricts a red cell's
@@ -1327,17 +1362,17 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
     }
   }
   for (int l = 1; l < a.legs_to; ++l) {
-    if (!grid_barrier(st, a.spins)) return;
+    if (!grid_barrier(st, a.spins)) return false;
     const LevelView<T, S>& L = a.lv[l];
     for (int sw = 0; sw < a.nu1; ++sw)
       for (int color = 0; color < 2; ++color) {
         if (sw == 0 && color == 0) continue;  // done with the restriction
         for (int64_t c = t0; c < L.d.n; c += nt) gs_cell(L, c, color, 0);
-        if (!grid_barrier(st, a.spins)) return;
+        if (!grid_barrier(st, a.spins)) return false;
       }
     if (a.nu1 == 0) {
       for (int64_t c = t0; c < L.d.n; c += nt) L.x[c] = T(0);
-      if (!grid_barrier(st, a.spins)) return;
+      if (!grid_barrier(st, a.spins)) return false;
     }
     const LevelView<T, S>& C = a.lv[l + 1];
     const bool fold = a.nu1 > 0 && l + 1 < a.tail_from;
@@ -1347,13 +1382,13 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a,
       if (fold && red_cell(C.d, I)) C.x[I] = fI / C.cc(kDiag, I);
     }
   }
+  return true;
 }
 
 // Up leg: post-smoothing of levels tail_from - 1 .. 1 and then level 0, the
 // first (black) half sweep of each level reading the coarse correction
 template <typename T, typename S>
-__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, DevState* st) {
-  if (st->done) return;
+__device__ bool amg_up(const CycleArgs<T, S>& a, DevState* st) {
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
   const Geom& g = a.g;
   for (int l = a.legs_to - 1; l >= 1; --l) {
@@ -1361,7 +1396,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
     const LevelView<T, S>& C = a.lv[l + 1];
     if (a.nu2 == 0) {
       for (int64_t c = t0; c < L.d.n; c += nt) prolong_cell(L, C, c, a.s);
-      if (!grid_barrier(st, a.spins)) return;
+      if (!grid_barrier(st, a.spins)) return false;
     }
     for (int sw = 0; sw < a.nu2; ++sw)
       for (int color = 1; color >= 0; --color) {
@@ -1369,13 +1404,13 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
           if (sw == 0 && color == 1) gs_cell_prolong(L, C, c, a.s);
           else gs_cell(L, c, color, 0);
         }
-        if (!grid_barrier(st, a.spins)) return;
+        if (!grid_barrier(st, a.spins)) return false;
       }
   }
   const LevelView<T, S>& C1 = a.lv[1];
   if (a.nu2 == 0) {
     for (int64_t t = t0; t < g.N; t += nt) prolong0_cell<T>(g, a.x0, C1.d, C1.x, a.s, t);
-    return;
+    return true;
   }
   for (int sw = 0; sw < a.nu2; ++sw) {
     if (sw == 0)
@@ -1385,10 +1420,23 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, D
     else
       sweep_batched<4>(t0, nt, g.Nh, a.x0 + g.Nh,
                        [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 1, 0, q); });
-    if (!grid_barrier(st, a.spins)) return;
+    if (!grid_barrier(st, a.spins)) return false;
     sweep_batched<4>(t0, nt, g.Nh, a.x0, [&](int64_t q) { return gs0_value<T, S>(g, a.At, a.f0, a.x0, 0, 0, q); });
-    if (sw + 1 < a.nu2 && !grid_barrier(st, a.spins)) return;
+    if (sw + 1 < a.nu2 && !grid_barrier(st, a.spins)) return false;
   }
+  return true;
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a, DevState* st) {
+  if (st->done) return;
+  amg_down(a, st);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, DevState* st) {
+  if (st->done) return;
+  amg_up(a, st);
 }
 
 // ---- the coarse levels (1 .. coarsest) in one thread-block cluster
@@ -1438,42 +1486,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_coarse(CycleArgs<T, S> 
   if (blockIdx.x == 0) {
     if (tail_smem) {
       __shared__ uint32_t off[73];
-      if (threadIdx.x == 0) {
-        uint32_t o = 0;
-        for (int l = ta.first; l <= ta.last; ++l) {
-          const uint32_t n = (uint32_t)ta.lv[l].d.n;
-          off[3 * l] = o;
-          o += (uint32_t)align16(7 * n * sizeof(S));
-          off[3 * l + 1] = o;
-          o += (uint32_t)align16(n * sizeof(T));
-          off[3 * l + 2] = o;
-          o += (uint32_t)align16(n * sizeof(T));
-        }
-        off[72] = o;
-      }
+      tail_offsets(ta, off);
       __syncthreads();
       const TailSharedViews<T, S> vw{&ta, off};
-      for (int l = ta.first; l <= ta.last; ++l) {
-        const int64_t n = ta.lv[l].d.n;
-        S* c = const_cast<S*>(vw.lv(l).c);
-        const S* src = ta.lv[l].c;
-#pragma unroll 8
-        for (int64_t i = threadIdx.x; i < 7 * n; i += blockDim.x) c[i] = src[i];
-      }
-      {
-        const int64_t n = ta.lv[ta.first].d.n;
-        T* f = vw.lv(ta.first).f;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = ldv<true>(ta.lv[ta.first].f + i);
-        const int64_t nc = ta.lv[ta.last].d.n;
-        S* inv = const_cast<S*>(vw.inv());
-#pragma unroll 8
-        for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = ta.inv[i];
-      }
-      __syncthreads();
-      tail_cycle(ta, vw);
-      const int64_t n = ta.lv[ta.first].d.n;
-      const T* x = vw.lv(ta.first).x;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ta.lv[ta.first].x[i] = x[i];
+      tail_stage_coefficients(ta, vw);
+      tail_run_staged(ta, vw);
     } else {
       tail_cycle(ta, TailGlobalViews<T, S>{&ta});
     }
