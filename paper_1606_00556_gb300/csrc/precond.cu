@@ -676,12 +676,16 @@ __device__ __forceinline__ void offdiag_sum(const Geom& g, const S* __restrict__
                                             const Cell& c, const T* __restrict__ u, T s[3]) {
   const int oc = color ^ 1;
   s[0] = s[1] = s[2] = T(0);
+  // (every slot's loads are issued; a missing neighbour reads this cell's
+  // own entries and is masked to zero, so all loads can be in flight)
 #pragma unroll
   for (int sl = 0; sl < 7; ++sl) {
     if (sl == kDiag) continue;
-    const int64_t nq = nbr(g, c, q, sl);
-    if (nq < 0) continue;
-    const T u0 = u[vidx(g, 0, oc, nq)], u1 = u[vidx(g, 1, oc, nq)], u2 = u[vidx(g, 2, oc, nq)];
+    const int64_t nb = nbr(g, c, q, sl);
+    const bool ok = nb >= 0;
+    const int64_t nq = ok ? nb : q;
+    T u0 = u[vidx(g, 0, oc, nq)], u1 = u[vidx(g, 1, oc, nq)], u2 = u[vidx(g, 2, oc, nq)];
+    if (!ok) u0 = u1 = u2 = T(0);
     const S* a = At + at_index(g, color, sl * 9, q);
     constexpr size_t P = 32;  // entries (rc) of a block lie 32 apart in a tile
     s[0] = fma3(s[0], cv<T>(ld_stream(a)), u0, cv<T>(ld_stream(a + P)), u1, cv<T>(ld_stream(a + 2 * P)), u2);
@@ -828,9 +832,9 @@ __device__ __forceinline__ T gs0_value(const Geom& g, const S* __restrict__ At, 
 #pragma unroll
     for (int sl = 0; sl < 7; ++sl) {
       if (sl == kDiag) continue;
-      const int64_t nq = nbr(g, c, q, sl);
-      if (nq < 0) continue;
-      s -= cv<T>(At[at_index(g, color, sl * 9, q)]) * x[(size_t)oc * g.Nh + nq];
+      const int64_t nb = nbr(g, c, q, sl);
+      const T xv = x[(size_t)oc * g.Nh + (nb >= 0 ? nb : q)];
+      s -= cv<T>(At[at_index(g, color, sl * 9, q)]) * (nb >= 0 ? xv : T(0));
     }
   }
   return s / cv<T>(At[at_index(g, color, kDiag * 9, q)]);
@@ -886,10 +890,11 @@ __device__ __forceinline__ T gs0_prolong_value(const Geom& g, const S* __restric
 #pragma unroll
   for (int sl = 0; sl < 7; ++sl) {
     if (sl == kDiag) continue;
-    const int64_t nq = nbr(g, c, q, sl);
-    if (nq < 0) continue;
-    const T xv = x[nq] + sc * xc[nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2)];
-    s -= cv<T>(At[at_index(g, 1, sl * 9, q)]) * xv;
+    const int64_t nb = nbr(g, c, q, sl);
+    const bool ok = nb >= 0;
+    const int64_t cn = ok ? nat_index(C, (c.i + di[sl]) / 2, (c.j + dj[sl]) / 2, (c.k + dk[sl]) / 2) : 0;
+    const T xv = x[ok ? nb : q] + sc * xc[cn];
+    s -= cv<T>(At[at_index(g, 1, sl * 9, q)]) * (ok ? xv : T(0));
   }
   return s / cv<T>(At[at_index(g, 1, kDiag * 9, q)]);
 }
@@ -990,13 +995,17 @@ __device__ __forceinline__ void gs_cell(const LevelView<T, S>& L, int64_t cidx, 
   if (((i + j + k) & 1) != color) return;
   T s = ldv<CG>(L.f + cidx);
   if (!zero_guess) {
+    // every neighbour's loads are issued; a missing one reads the cell
+    // itself and the value read is replaced by zero
     const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-    if (k > 0) s -= L.cc(kZm, cidx) * ldv<CG>(L.x + cidx - nxy);
-    if (j > 0) s -= L.cc(kYm, cidx) * ldv<CG>(L.x + cidx - L.d.nx);
-    if (i > 0) s -= L.cc(kXm, cidx) * ldv<CG>(L.x + cidx - 1);
-    if (i < L.d.nx - 1) s -= L.cc(kXp, cidx) * ldv<CG>(L.x + cidx + 1);
-    if (j < L.d.ny - 1) s -= L.cc(kYp, cidx) * ldv<CG>(L.x + cidx + L.d.nx);
-    if (k < L.d.nz - 1) s -= L.cc(kZp, cidx) * ldv<CG>(L.x + cidx + nxy);
+    const bool ok[6] = {k > 0, j > 0, i > 0, i < L.d.nx - 1, j < L.d.ny - 1, k < L.d.nz - 1};
+    const int slot[6] = {kZm, kYm, kXm, kXp, kYp, kZp};
+    const int64_t off[6] = {-nxy, -(int64_t)L.d.nx, -1, 1, (int64_t)L.d.nx, nxy};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const T xv = ldv<CG>(L.x + (ok[d] ? cidx + off[d] : cidx));
+      s -= L.cc(slot[d], cidx) * (ok[d] ? xv : T(0));
+    }
   }
   L.x[cidx] = s / L.cc(kDiag, cidx);
 }
@@ -1046,16 +1055,20 @@ __device__ __forceinline__ void gs_cell_prolong(const LevelView<T, S>& L, const 
   const int i = p.i, j = p.j, k = p.k;
   if (((i + j + k) & 1) != 1) return;
   const int64_t nxy = (int64_t)L.d.nx * L.d.ny;
-  auto xv = [&](int64_t f, int ci, int cj, int ck) {
-    return ldv<CG>(L.x + f) + sc * ldv<CG>(C.x + nat_index(C.d, ci, cj, ck));
-  };
   T s = ldv<CG>(L.f + cidx);
-  if (k > 0) s -= L.cc(kZm, cidx) * xv(cidx - nxy, i / 2, j / 2, (k - 1) / 2);
-  if (j > 0) s -= L.cc(kYm, cidx) * xv(cidx - L.d.nx, i / 2, (j - 1) / 2, k / 2);
-  if (i > 0) s -= L.cc(kXm, cidx) * xv(cidx - 1, (i - 1) / 2, j / 2, k / 2);
-  if (i < L.d.nx - 1) s -= L.cc(kXp, cidx) * xv(cidx + 1, (i + 1) / 2, j / 2, k / 2);
-  if (j < L.d.ny - 1) s -= L.cc(kYp, cidx) * xv(cidx + L.d.nx, i / 2, (j + 1) / 2, k / 2);
-  if (k < L.d.nz - 1) s -= L.cc(kZp, cidx) * xv(cidx + nxy, i / 2, j / 2, (k + 1) / 2);
+  const bool ok[6] = {k > 0, j > 0, i > 0, i < L.d.nx - 1, j < L.d.ny - 1, k < L.d.nz - 1};
+  const int slot[6] = {kZm, kYm, kXm, kXp, kYp, kZp};
+  const int64_t off[6] = {-nxy, -(int64_t)L.d.nx, -1, 1, (int64_t)L.d.nx, nxy};
+  const int ci[6] = {i / 2, i / 2, (i - 1) / 2, (i + 1) / 2, i / 2, i / 2};
+  const int cj[6] = {j / 2, (j - 1) / 2, j / 2, j / 2, (j + 1) / 2, j / 2};
+  const int ck[6] = {(k - 1) / 2, k / 2, k / 2, k / 2, k / 2, (k + 1) / 2};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int64_t fi = ok[d] ? cidx + off[d] : cidx;
+    const int64_t cn = ok[d] ? nat_index(C.d, ci[d], cj[d], ck[d]) : nat_index(C.d, i / 2, j / 2, k / 2);
+    const T xv = ldv<CG>(L.x + fi) + sc * ldv<CG>(C.x + cn);
+    s -= L.cc(slot[d], cidx) * (ok[d] ? xv : T(0));
+  }
   L.x[cidx] = s / L.cc(kDiag, cidx);
 }
 
