@@ -269,8 +269,13 @@ __global__ void __launch_bounds__(kThreads) k_spmv_tiled(Geom g, const V* __rest
     for (int which = 0; which < 4; ++which) {
       const int sl = which == 0 ? kZm : which == 1 ? kYm : which == 2 ? kYp : kZp;
       const bool ok = which == 0 ? k > 0 : which == 1 ? j > 0 : which == 2 ? j < g.ny - 1 : k < g.nz - 1;
-      if (!ok) continue;
-      const int64_t off = which == 0 ? -nxy : which == 1 ? -(int64_t)g.nx : which == 2 ? (int64_t)g.nx : nxy;
+      // BF16 and split values: a missing row is read as the cells' own row
+      // (every load issued, so all of a thread's loads can be in flight) and
+      // its x replaced by zero (measured faster: BF16 53 -> 48 us at
+      // 128x128x64); FP32 values skip it (the masked form measured slower)
+      if (sizeof(V) == 4 && !ok) continue;
+      const int64_t off =
+          !ok ? 0 : which == 0 ? -nxy : which == 1 ? -(int64_t)g.nx : which == 2 ? (int64_t)g.nx : nxy;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int col = h ? 1 - cA : cA;
@@ -281,8 +286,8 @@ __global__ void __launch_bounds__(kThreads) k_spmv_tiled(Geom g, const V* __rest
 #pragma unroll
       for (int u = 0; u < 3 * C / 2; ++u) {
         const double2 v = __ldg(xp + u);
-        xs[2 * u] = v.x;
-        xs[2 * u + 1] = v.y;
+        xs[2 * u] = ok ? v.x : 0.0;
+        xs[2 * u + 1] = ok ? v.y : 0.0;
       }
 #pragma unroll
       for (int e = 0; e < C; ++e) {
