@@ -672,13 +672,13 @@ int bo_conv3d_backward_weights(bo_ctx* ctx, int nx, int ny, int nz, int batch, i
 int bo_set_conv_engine(int engine);
 /* How the AMG V-cycle is launched (process-wide); every form computes the
  * same V-cycle of paper Sec. 3.2's pressure AMG stage:
- * 1 (the default) = two cooperative launches, a down leg and an up leg
- *   whose blocks meet at grid-wide barriers between the Gauss-Seidel half
- *   sweeps of level 0 and of the coarser multi-block levels, around one
+ * 2 (the default) = levels 0 and 1 in two cooperative launches, a down leg
+ *   and an up leg whose blocks meet at grid-wide barriers between the
+ *   Gauss-Seidel half sweeps, around one thread-block-cluster launch (up to
+ *   16 blocks, hardware cluster barriers) for all coarser levels, the
+ *   levels of at most 4096 cells in one of its blocks;
+ * 1 = the cooperative legs smooth every multi-block level, around one
  *   block for the levels of at most 4096 cells;
- * 2 = the cooperative legs smooth level 0 only, around one
- *   thread-block-cluster launch (up to 16 blocks, hardware cluster
- *   barriers) for all coarser levels;
  * 0 = one kernel per half sweep, restriction and prolongation.
  * Inside stream capture (CUDA-graph launch mode) the per-kernel form is used
  * whatever the setting, and a form the device refuses falls back to it.  A

@@ -334,7 +334,9 @@ constexpr int kMaxPoolStreams = 16;
 extern std::atomic<int> g_pool_width;
 // convolution engine of the 32 -> 32 layers: 0 mma.sync, 1 tcgen05 (conv_tc.cu)
 extern std::atomic<int> g_conv_engine;
-// AMG multi-block levels: 1 cooperative down/up launches, 0 one kernel per sweep
+// AMG launch form: 2 (default) cooperative legs for levels 0-1 around a cluster
+// launch for the coarser levels, 1 cooperative legs for every multi-block
+// level around a one-block tail, 0 one kernel per sweep
 extern std::atomic<int> g_amg_coop;
 // polls of an AMG grid barrier before it gives up (default 2^22, about 0.1 s)
 constexpr unsigned kAmgSpinsDefault = 1u << 22;

@@ -17,7 +17,7 @@ namespace bo {
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_pool_width{kMaxPoolStreams};
 std::atomic<int> g_conv_engine{1};
-std::atomic<int> g_amg_coop{1};
+std::atomic<int> g_amg_coop{2};
 std::atomic<unsigned> g_amg_spins{kAmgSpinsDefault};
 std::atomic<int> g_gs_fused{1};
 

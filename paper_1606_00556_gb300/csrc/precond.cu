@@ -1245,6 +1245,31 @@ __device__ void tail_stage_coefficients(const TailArgs<T, S>& a, const TailShare
   for (int64_t i = threadIdx.x; i < nc * nc; i += blockDim.x) inv[i] = a.inv[i];
 }
 
+// The same staging with asynchronous copies (cp.async, 16 bytes each; a
+// remainder below 16 bytes is copied directly), so the block can go on with
+// other work while they land; the caller waits (cp.async.wait_all) and
+// synchronises before the staged values are read.  The sources are device
+// allocations and the shared-memory offsets multiples of 16 bytes.
+__device__ __forceinline__ void copy_to_shared_async(void* dst, const void* src, size_t bytes) {
+  const size_t n16 = bytes / 16;
+  const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
+  for (size_t i = threadIdx.x; i < n16; i += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + (uint32_t)(16 * i)),
+                 "l"(reinterpret_cast<const char*>(src) + 16 * i)
+                 : "memory");
+  for (size_t b = 16 * n16 + threadIdx.x; b < bytes; b += blockDim.x)
+    reinterpret_cast<char*>(dst)[b] = reinterpret_cast<const char*>(src)[b];
+}
+
+template <typename T, typename S>
+__device__ void tail_stage_coefficients_async(const TailArgs<T, S>& a, const TailSharedViews<T, S>& vw) {
+  for (int l = a.first; l <= a.last; ++l)
+    copy_to_shared_async(const_cast<S*>(vw.lv(l).c), a.lv[l].c, (size_t)7 * a.lv[l].d.n * sizeof(S));
+  const int64_t nc = a.lv[a.last].d.n;
+  copy_to_shared_async(const_cast<S*>(vw.inv()), a.inv, (size_t)nc * nc * sizeof(S));
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // The tail V-cycle on staged coefficients: the first tail level's
 // right-hand side comes in from global memory (through L2: other blocks of
 // a cooperative launch wrote it), and only its iterate goes back.
@@ -1462,11 +1487,13 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// The levels below level 0 of one V-cycle, launched as a single cluster of
-// up to 16 blocks (one per SM) after the level-0 down leg has restricted
-// onto level 1: pre-smoothing and restriction of the multi-block levels,
-// the tail V-cycle (levels of at most kTailCells cells) in the first block,
-// in shared memory when it fits, then post-smoothing back up to level 1.
+// The levels from a.legs_to (level 2; level 1, 131k cells at 128x128x64,
+// stays in the cooperative legs, which give it the whole GPU) down to the
+// coarsest, launched as a single cluster of up to 16 blocks (one per SM)
+// after the down leg has restricted onto level a.legs_to: pre-smoothing and
+// restriction of the multi-block levels, the tail V-cycle (levels of at
+// most kTailCells cells) in the last block, in shared memory when it fits,
+// then post-smoothing back up to level a.legs_to.
 // The same sweeps as the down and up legs, with a cluster barrier (a few
 // hundred nanoseconds) where they need a grid-wide one (several
 // microseconds), on the L2-resident coarse data.
@@ -1475,7 +1502,17 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_coarse(CycleArgs<T, S> 
                                                                const DevState* st) {
   if (st->done) return;  // uniform: every block reads the same flag
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
-  for (int l = 1; l < a.tail_from; ++l) {
+  // the last block runs the tail; it stages the tail's coefficients and
+  // coarse inverse asynchronously at the start, under the multi-block levels
+  const bool tail_block = blockIdx.x == gridDim.x - 1;
+  __shared__ uint32_t off[73];
+  const TailSharedViews<T, S> vw{&ta, off};
+  if (tail_smem && tail_block) {
+    tail_offsets(ta, off);
+    __syncthreads();
+    tail_stage_coefficients_async(ta, vw);
+  }
+  for (int l = a.legs_to; l < a.tail_from; ++l) {
     const LevelView<T, S>& L = a.lv[l];
     for (int sw = 0; sw < a.nu1; ++sw)
       for (int color = 0; color < 2; ++color) {
@@ -1496,20 +1533,17 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_coarse(CycleArgs<T, S> 
     }
     cluster_sync_all();
   }
-  if (blockIdx.x == 0) {
+  if (tail_block) {
     if (tail_smem) {
-      __shared__ uint32_t off[73];
-      tail_offsets(ta, off);
+      asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
-      const TailSharedViews<T, S> vw{&ta, off};
-      tail_stage_coefficients(ta, vw);
       tail_run_staged(ta, vw);
     } else {
       tail_cycle(ta, TailGlobalViews<T, S>{&ta});
     }
   }
   cluster_sync_all();
-  for (int l = a.tail_from - 1; l >= 1; --l) {
+  for (int l = a.tail_from - 1; l >= a.legs_to; --l) {
     const LevelView<T, S>& L = a.lv[l];
     const LevelView<T, S>& C = a.lv[l + 1];
     if (a.nu2 == 0) {
@@ -1641,9 +1675,9 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   const int ghalf = grid_for(g.Nh);
   const int last = P->nlev - 1;
   // Launch forms (all compute the same V-cycle):
-  //  mode 2: level 0 in two cooperative launches (down leg, up leg, grid
-  //          barriers between half sweeps) around one cluster launch for
-  //          every coarser level (cluster barriers);
+  //  mode 2: levels 0 and 1 in two cooperative launches (down leg, up leg,
+  //          grid barriers between half sweeps) around one cluster launch
+  //          for every coarser level (cluster barriers);
   //  mode 1: the cooperative legs also smooth the multi-block natural
   //          levels, the tail levels in one block;
   //  mode 0, or inside stream capture, or when a launch form is refused:
@@ -1659,7 +1693,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   ca.f0 = f0;
   ca.x0 = x0;
   ca.tail_from = P->tail_from;
-  ca.legs_to = cs ? 1 : P->tail_from;
+  ca.legs_to = cs ? (P->tail_from < 2 ? P->tail_from : 2) : P->tail_from;
   ca.nu1 = nu1;
   ca.nu2 = nu2;
   ca.s = sc;
