@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(Geom g, const float2*
                                                           const double* __restrict__ A, const int* __restrict__ range,
                                                           const float* __restrict__ z, W* __restrict__ w,
                                                           const DevState* st) {
+  wait_prior_grid();
   const int64_t wlo = split_pad(3 * g.N);  // low plane of a split w (the basis layout)
   if (st->done) return;
   const int64_t n = 3 * g.N;
@@ -179,6 +180,7 @@ __device__ double reduce_partials(const double* partials, int np, double* sh) {
 __global__ void __launch_bounds__(kThreads) k_true_residual(Geom g, const double* __restrict__ A,
                                                            const double* __restrict__ b, const double* __restrict__ x,
                                                            double* __restrict__ r, double* partials, DevState* st) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(Geom g, const double
 
 // ||v|| -> st->bnorm
 __global__ void k_norm(int64_t n, const double* __restrict__ v, double* partials, DevState* st) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -233,9 +236,13 @@ __global__ void k_norm(int64_t n, const double* __restrict__ v, double* partials
 }
 
 // zero initial guess: r0 = b, so ||r0|| = ||b||
-__global__ void k_beta_is_bnorm(DevState* st) { st->beta = st->bnorm; }
+__global__ void k_beta_is_bnorm(DevState* st) {
+  wait_prior_grid();
+  st->beta = st->bnorm;
+}
 
 __global__ void k_set_target(DevState* st, double tol) {
+  wait_prior_grid();
   st->target = tol * st->bnorm;
   st->err = 0;
   st->counter[5] = 0;  // the AMG grid barrier's word (its low 31 bits must start at 0)
@@ -245,6 +252,7 @@ __global__ void k_set_target(DevState* st, double tol) {
 
 // start of a cycle: g = (beta, 0, ...), flags cleared
 __global__ void k_cycle_start(DevState* st, double* gv, int m) {
+  wait_prior_grid();
   for (int i = threadIdx.x; i <= m; i += blockDim.x) gv[i] = (i == 0) ? st->beta : 0.0;
   if (threadIdx.x == 0) {
     st->done = 0;
@@ -258,6 +266,7 @@ __global__ void k_cycle_start(DevState* st, double* gv, int m) {
 
 // v = src / beta as split pairs in the basis layout
 __global__ void k_scale_beta(int64_t n, const double* __restrict__ src, float* __restrict__ v, const DevState* st) {
+  wait_prior_grid();
   const double s = st->beta > 0.0 ? 1.0 / st->beta : 0.0;
   const int64_t np = split_pad(n);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -332,6 +341,7 @@ __host__ __device__ constexpr int dot_groups() { return SPLIT ? 4 : 8; }
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                      const float* __restrict__ w, double* partials, DevState* st) {
+  wait_prior_grid();
   constexpr int kDotB = dot_groups<SPLIT>();
   __shared__ double sh[32];
   if (st->done) return;
@@ -406,6 +416,7 @@ constexpr int kGsBatch = 4;
 template <int NVMAX>
 __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                      float* __restrict__ w, double* partials, DevState* st, int nv) {
+  wait_prior_grid();
   constexpr int B = kGsBatch;
   __shared__ df c[kMaxM + 1];
   __shared__ double wacc[kThreads / 32][NVMAX];
@@ -513,7 +524,7 @@ void launch_gs_pass(int64_t n, const float* V, int64_t ldv, float* w, double* pa
   // column as fit for the bucket's column count
   auto go = [&](const void* k, auto kern, int nvmax) {
     const int g = std::min(occ_grid(k, ng), (kMaxM + 2) * kDotBlocks / nvmax);
-    (kern<<<g, kThreads, 0, s>>>(n, V, ldv, w, partials, st, nv), note_launch());
+    (launch_pdl(kern, g, kThreads, 0, s, n, V, ldv, w, partials, st, nv), note_launch());
   };
   if (nv <= 8) go((const void*)k_gs_pass<8>, k_gs_pass<8>, 8);
   else if (nv <= 16) go((const void*)k_gs_pass<16>, k_gs_pass<16>, 16);
@@ -540,6 +551,7 @@ template <bool LAST>
 __global__ void __launch_bounds__(kThreads) k_gs_update(int64_t n, const float* __restrict__ V, int64_t ldv,
                                                        float* __restrict__ w, double* partials, DevState* st,
                                                        ArnoldiArgs aa) {
+  wait_prior_grid();
   constexpr int B = kGsBatch;
   __shared__ df c[kMaxM + 1];
   __shared__ double sh[32];
@@ -641,6 +653,7 @@ int gs_chunks(int64_t n, int nv) {
 
 // y = H(0:k, 0:k)^{-1} g (upper triangular after the rotations)
 __global__ void k_trisolve(DevState* st, const double* H, const double* gv, double* y, int ldh) {
+  wait_prior_grid();
   if (threadIdx.x != 0) return;
   if (st->err & kErrNonfinite) { st->k = 0; return; }
   const int k = st->k;
@@ -676,6 +689,7 @@ __device__ __forceinline__ df lincomb(const df* c, const float* __restrict__ V, 
 template <int NU>
 __global__ void __launch_bounds__(kThreads, 2) k_xupdate(int64_t n, double* __restrict__ x, const float* __restrict__ Z, int64_t ldz,
                           const double* __restrict__ y, const DevState* st) {
+  wait_prior_grid();
   __shared__ df ys[kMaxM];
   const int k = st->k;
   for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = df_from(y[l]);
@@ -801,13 +815,13 @@ struct Job {
     launch_gather(g, b_d, P->bi, s);
     if (o.x0_is_zero) cudaMemsetAsync(P->xi, 0, nn * sizeof(double), s);
     else launch_gather(g, x_d, P->xi, s);
-    (k_norm<<<kRedBlocks, kThreads, 0, s>>>(nn, P->bi, P->partials, st), note_launch());
-    (k_set_target<<<1, 1, 0, s>>>(st, o.tol), note_launch());
+    (launch_pdl(k_norm, kRedBlocks, kThreads, 0, s, nn, P->bi, P->partials, st), note_launch());
+    (launch_pdl(k_set_target, 1, 1, 0, s, st, o.tol), note_launch());
     if (o.x0_is_zero) {  // r0 = b: no pass over the matrix
       cudaMemcpyAsync(P->rk, P->bi, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
-      (k_beta_is_bnorm<<<1, 1, 0, s>>>(st), note_launch());
+      (launch_pdl(k_beta_is_bnorm, 1, 1, 0, s, st), note_launch());
     } else {
-      (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+      (launch_pdl(k_true_residual, kRedBlocks, kThreads, 0, s, g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
        note_launch());
       if (P->wl) wells_after_residual(P);
     }
@@ -818,8 +832,8 @@ struct Job {
 
   void start_cycle() {
     cudaStream_t s = stream();
-    (k_cycle_start<<<1, 64, 0, s>>>(P->st, P->gvec, o.restart), note_launch());
-    (k_scale_beta<<<grid_for(n()), kThreads, 0, s>>>(n(), P->rk, (float*)P->V, P->st), note_launch());
+    (launch_pdl(k_cycle_start, 1, 64, 0, s, P->st, P->gvec, o.restart), note_launch());
+    (launch_pdl(k_scale_beta, grid_for(n()), kThreads, 0, s, n(), P->rk, (float*)P->V, P->st), note_launch());
     j_enq = j_polled = 0;
     cycle_stop = false;
     phase = kColumns;
@@ -845,7 +859,7 @@ struct Job {
       e1 = P->prof_ev[2 * prof.size() + 1];
       cudaEventRecord(e0, s);
     }
-    (k_arnoldi_spmv<float><<<occ_grid((const void*)k_arnoldi_spmv<float>, g.N), kThreads, 0, s>>>(
+    (launch_pdl(k_arnoldi_spmv<float>, occ_grid((const void*)k_arnoldi_spmv<float>, g.N), kThreads, 0, s, 
          g, P->mat->A2, P->mat->A, P->mat->a2_range, zj, w, st),
      note_launch());
     if (e1) {
@@ -859,17 +873,17 @@ struct Job {
     if (g_gs_fused.load()) {
       // CGS2 in three passes over the basis: the first coefficients, the
       // first update fused with the second coefficients, the final update
-      (k_gs_dots<false><<<dim3(gs_chunks<false>(nn, nv), nv), kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st),
+      (launch_pdl(k_gs_dots<false>, dim3(gs_chunks<false>(nn, nv), nv), kThreads, 0, s, nn, V, ldv, w, P->partials, st),
        note_launch());
       launch_gs_pass(nn, V, ldv, w, P->partials, st, nv, s);
     } else {
-      (k_gs_dots<false><<<dim3(gs_chunks<false>(nn, nv), nv), kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st),
+      (launch_pdl(k_gs_dots<false>, dim3(gs_chunks<false>(nn, nv), nv), kThreads, 0, s, nn, V, ldv, w, P->partials, st),
        note_launch());
-      (k_gs_update<false><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
-      (k_gs_dots<true><<<dim3(gs_chunks<true>(nn, nv), nv), kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st),
+      (launch_pdl(k_gs_update<false>, gu, kThreads, 0, s, nn, V, ldv, w, P->partials, st, aa), note_launch());
+      (launch_pdl(k_gs_dots<true>, dim3(gs_chunks<true>(nn, nv), nv), kThreads, 0, s, nn, V, ldv, w, P->partials, st),
        note_launch());
     }
-    (k_gs_update<true><<<gu, kThreads, 0, s>>>(nn, V, ldv, w, P->partials, st, aa), note_launch());
+    (launch_pdl(k_gs_update<true>, gu, kThreads, 0, s, nn, V, ldv, w, P->partials, st, aa), note_launch());
   }
 
   // Column j's kernels captured once into a CUDA graph (on a private stream,
@@ -929,12 +943,12 @@ struct Job {
     cudaStream_t s = stream();
     const int64_t nn = n();
     const int gn = grid_for(nn);
-    (k_trisolve<<<1, 32, 0, s>>>(P->st, P->H, P->gvec, P->y, o.restart), note_launch());
+    (launch_pdl(k_trisolve, 1, 32, 0, s, P->st, P->H, P->gvec, P->y, o.restart), note_launch());
     const float* Z = (const float*)P->Z;
-    if (o.restart <= 16) (k_xupdate<16><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
-    else if (o.restart <= 32) (k_xupdate<32><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
-    else (k_xupdate<kMaxM><<<gn, kThreads, 0, s>>>(nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
-    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(geom(), P->mat->A, P->bi, P->xi, P->rk, P->partials, P->st),
+    if (o.restart <= 16) (launch_pdl(k_xupdate<16>, gn, kThreads, 0, s, nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
+    else if (o.restart <= 32) (launch_pdl(k_xupdate<32>, gn, kThreads, 0, s, nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
+    else (launch_pdl(k_xupdate<kMaxM>, gn, kThreads, 0, s, nn, P->xi, Z, 2 * nn, P->y, P->st), note_launch());
+    (launch_pdl(k_true_residual, kRedBlocks, kThreads, 0, s, geom(), P->mat->A, P->bi, P->xi, P->rk, P->partials, P->st),
      note_launch());
     if (P->wl) wells_after_residual(P);
     mark(kPhaseSlot);
@@ -1064,6 +1078,7 @@ struct Job {
 namespace {
 // v (FP64, internal order) -> split pairs: hi plane z[0..n), lo plane z[n..2n)
 __global__ void k_split_vec(int64_t n, const double* __restrict__ v, float* __restrict__ z) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int bad = 0;
     const float2 p = df_split_bits(v[i], &bad);
@@ -1073,6 +1088,7 @@ __global__ void k_split_vec(int64_t n, const double* __restrict__ v, float* __re
 }
 // w = hi + lo (exact in FP64) of a vector in the basis layout
 __global__ void k_join_vec(int64_t n, const float* __restrict__ z, double* __restrict__ w) {
+  wait_prior_grid();
   const int64_t np = split_pad(n);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     w[i] = (double)z[i] + (double)z[np + i];
@@ -1090,11 +1106,11 @@ void launch_arnoldi_product(bo_prec* P, const double* v, double* w) {
   if (!m->a2_valid) launch_split_matrix(m, s);
   float* z = (float*)P->Z;  // the first preconditioned vector's split planes as scratch
   float* ws = (float*)P->V;  // the first basis vector's split planes as scratch
-  (k_split_vec<<<grid_for(n), kThreads, 0, s>>>(n, v, z), note_launch());
-  (k_arnoldi_spmv<float><<<occ_grid((const void*)k_arnoldi_spmv<float>, g.N), kThreads, 0, s>>>(
+  (launch_pdl(k_split_vec, grid_for(n), kThreads, 0, s, n, v, z), note_launch());
+  (launch_pdl(k_arnoldi_spmv<float>, occ_grid((const void*)k_arnoldi_spmv<float>, g.N), kThreads, 0, s, 
        g, m->A2, m->A, m->a2_range, z, ws, P->st),
    note_launch());
-  (k_join_vec<<<grid_for(n), kThreads, 0, s>>>(n, ws, w), note_launch());
+  (launch_pdl(k_join_vec, grid_for(n), kThreads, 0, s, n, ws, w), note_launch());
 }
 
 int fgmres(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* o, bo_solve_info* info) {
@@ -1142,6 +1158,7 @@ __global__ void __launch_bounds__(kThreads) k_bc_dots(int64_t n, const double* _
                                                      const double* __restrict__ b, const double* __restrict__ c,
                                                      const double* __restrict__ d, double* partials, DevState* st,
                                                      int o1, int o2) {
+  wait_prior_grid();
   __shared__ double sh[32];
   if (st->done) return;
   double s1 = 0.0, s2 = 0.0;
@@ -1168,6 +1185,7 @@ __global__ void __launch_bounds__(kThreads) k_bc_dots(int64_t n, const double* _
 // the scalar steps of an iteration (one thread)
 template <int PHASE>
 __global__ void k_bc_scalar(DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   double* h = st->h;
   auto stop = [&](int why) {
@@ -1197,6 +1215,7 @@ __global__ void k_bc_scalar(DevState* st) {
 // p = r + beta (p - omega v)
 __global__ void k_bc_p(int64_t n, const double* __restrict__ r, double* __restrict__ p, const double* __restrict__ v,
                        const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   const double beta = st->h[kBcBeta], omega = st->h[kBcOmega];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1207,6 +1226,7 @@ __global__ void k_bc_p(int64_t n, const double* __restrict__ r, double* __restri
 __global__ void __launch_bounds__(kThreads) k_bc_s(int64_t n, const double* __restrict__ r,
                                                   const double* __restrict__ v, double* __restrict__ s,
                                                   double* partials, DevState* st) {
+  wait_prior_grid();
   __shared__ double sh[32];
   if (st->done) return;
   const double alpha = st->h[kBcAlpha];
@@ -1236,6 +1256,7 @@ __global__ void __launch_bounds__(kThreads) k_bc_xr(int64_t n, double* __restric
                                                    const float* __restrict__ shs, const double* __restrict__ s,
                                                    const double* __restrict__ t, double* __restrict__ r,
                                                    double* partials, DevState* st) {
+  wait_prior_grid();
   __shared__ double sh[32];
   if (st->done) return;
   const double alpha = st->h[kBcAlpha], omega = st->h[kBcOmega];
@@ -1259,6 +1280,7 @@ __global__ void __launch_bounds__(kThreads) k_bc_xr(int64_t n, double* __restric
 // the cycle stopped after a BiCG half step whose residual met the target:
 // x += alpha p^ (runs after the stop, so not gated by it)
 __global__ void k_bc_xs(int64_t n, double* __restrict__ x, const float* __restrict__ ph, const DevState* st) {
+  wait_prior_grid();
   if (st->h[kBcReason] != kBcSDone) return;
   const double alpha = st->h[kBcAlpha];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1268,6 +1290,7 @@ __global__ void k_bc_xs(int64_t n, double* __restrict__ x, const float* __restri
 // start of a cycle from the true residual rk: r = rt = rk, p = v = 0
 __global__ void k_bc_start_vec(int64_t n, const double* __restrict__ rk, double* __restrict__ r,
                                double* __restrict__ rt, double* __restrict__ p, double* __restrict__ v) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     r[i] = rk[i];
     rt[i] = rk[i];
@@ -1277,6 +1300,7 @@ __global__ void k_bc_start_vec(int64_t n, const double* __restrict__ rk, double*
 }
 
 __global__ void k_bc_start(DevState* st) {
+  wait_prior_grid();
   st->h[kBcRhoPrev] = st->h[kBcAlpha] = st->h[kBcOmega] = 1.0;
   st->h[kBcReason] = kBcGoing;
   st->done = 0;
@@ -1305,13 +1329,13 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
   launch_gather(g, b_d, P->bi, s);
   if (o->x0_is_zero) cudaMemsetAsync(P->xi, 0, nn * sizeof(double), s);
   else launch_gather(g, x_d, P->xi, s);
-  (k_norm<<<kRedBlocks, kThreads, 0, s>>>(nn, P->bi, P->partials, st), note_launch());
-  (k_set_target<<<1, 1, 0, s>>>(st, o->tol), note_launch());
+  (launch_pdl(k_norm, kRedBlocks, kThreads, 0, s, nn, P->bi, P->partials, st), note_launch());
+  (launch_pdl(k_set_target, 1, 1, 0, s, st, o->tol), note_launch());
   if (o->x0_is_zero) {
     cudaMemcpyAsync(P->rk, P->bi, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    (k_beta_is_bnorm<<<1, 1, 0, s>>>(st), note_launch());
+    (launch_pdl(k_beta_is_bnorm, 1, 1, 0, s, st), note_launch());
   } else {
-    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+    (launch_pdl(k_true_residual, kRedBlocks, kThreads, 0, s, g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
      note_launch());
   }
   auto read_state = [&](int slot) -> bool {
@@ -1338,29 +1362,29 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
   const int gn = grid_for(nn);
   const int gs = occ_grid((const void*)k_arnoldi_spmv<double>, g.N);
   auto enqueue_iteration = [&]() {
-    (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, rt, r, nullptr, nullptr, P->partials, st, kBcRho, -1),
+    (launch_pdl(k_bc_dots, kRedBlocks, kThreads, 0, s, nn, rt, r, nullptr, nullptr, P->partials, st, kBcRho, -1),
      note_launch());
-    (k_bc_scalar<0><<<1, 1, 0, s>>>(st), note_launch());
-    (k_bc_p<<<gn, kThreads, 0, s>>>(nn, r, p, v, st), note_launch());
+    (launch_pdl(k_bc_scalar<0>, 1, 1, 0, s, st), note_launch());
+    (launch_pdl(k_bc_p, gn, kThreads, 0, s, nn, r, p, v, st), note_launch());
     launch_cpr_split(P, p, ph, st, nullptr);
-    (k_arnoldi_spmv<double><<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, ph, v, st),
+    (launch_pdl(k_arnoldi_spmv<double>, gs, kThreads, 0, s, g, P->mat->A2, P->mat->A, P->mat->a2_range, ph, v, st),
      note_launch());
-    (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, rt, v, nullptr, nullptr, P->partials, st, kBcRtv, -1),
+    (launch_pdl(k_bc_dots, kRedBlocks, kThreads, 0, s, nn, rt, v, nullptr, nullptr, P->partials, st, kBcRtv, -1),
      note_launch());
-    (k_bc_scalar<1><<<1, 1, 0, s>>>(st), note_launch());
-    (k_bc_s<<<kRedBlocks, kThreads, 0, s>>>(nn, r, v, sv, P->partials, st), note_launch());
-    (k_bc_scalar<2><<<1, 1, 0, s>>>(st), note_launch());
+    (launch_pdl(k_bc_scalar<1>, 1, 1, 0, s, st), note_launch());
+    (launch_pdl(k_bc_s, kRedBlocks, kThreads, 0, s, nn, r, v, sv, P->partials, st), note_launch());
+    (launch_pdl(k_bc_scalar<2>, 1, 1, 0, s, st), note_launch());
     launch_cpr_split(P, sv, shs, st, nullptr);
-    (k_arnoldi_spmv<double><<<gs, kThreads, 0, s>>>(g, P->mat->A2, P->mat->A, P->mat->a2_range, shs, tv, st),
+    (launch_pdl(k_arnoldi_spmv<double>, gs, kThreads, 0, s, g, P->mat->A2, P->mat->A, P->mat->a2_range, shs, tv, st),
      note_launch());
-    (k_bc_dots<<<kRedBlocks, kThreads, 0, s>>>(nn, tv, sv, tv, tv, P->partials, st, kBcTs, kBcTt), note_launch());
-    (k_bc_scalar<3><<<1, 1, 0, s>>>(st), note_launch());
-    (k_bc_xr<<<kRedBlocks, kThreads, 0, s>>>(nn, P->xi, ph, shs, sv, tv, r, P->partials, st), note_launch());
-    (k_bc_scalar<4><<<1, 1, 0, s>>>(st), note_launch());
+    (launch_pdl(k_bc_dots, kRedBlocks, kThreads, 0, s, nn, tv, sv, tv, tv, P->partials, st, kBcTs, kBcTt), note_launch());
+    (launch_pdl(k_bc_scalar<3>, 1, 1, 0, s, st), note_launch());
+    (launch_pdl(k_bc_xr, kRedBlocks, kThreads, 0, s, nn, P->xi, ph, shs, sv, tv, r, P->partials, st), note_launch());
+    (launch_pdl(k_bc_scalar<4>, 1, 1, 0, s, st), note_launch());
   };
   while (status == BO_OK && bnorm > 0.0 && beta > target && its < o->maxit) {
-    (k_bc_start_vec<<<gn, kThreads, 0, s>>>(nn, P->rk, r, rt, p, v), note_launch());
-    (k_bc_start<<<1, 1, 0, s>>>(st), note_launch());
+    (launch_pdl(k_bc_start_vec, gn, kThreads, 0, s, nn, P->rk, r, rt, p, v), note_launch());
+    (launch_pdl(k_bc_start, 1, 1, 0, s, st), note_launch());
     // iterations, polled one behind: a stop leaves the queued iteration's kernels idle
     int enq = 0, polled = 0;
     bool stop = false;
@@ -1376,8 +1400,8 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
       if (P->h_st[polled % 2].done) stop = true;
       ++polled;
     }
-    (k_bc_xs<<<gn, kThreads, 0, s>>>(nn, P->xi, ph, st), note_launch());
-    (k_true_residual<<<kRedBlocks, kThreads, 0, s>>>(g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
+    (launch_pdl(k_bc_xs, gn, kThreads, 0, s, nn, P->xi, ph, st), note_launch());
+    (launch_pdl(k_true_residual, kRedBlocks, kThreads, 0, s, g, P->mat->A, P->bi, P->xi, P->rk, P->partials, st),
      note_launch());
     if (!read_state(3)) return BO_ERR_CUDA;
     const DevState& h = P->h_st[3];

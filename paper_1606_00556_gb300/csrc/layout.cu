@@ -14,6 +14,7 @@ namespace {
 __global__ void k_ingest_bsr(Geom g, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                              const double* __restrict__ val, int64_t nnz, double* __restrict__ A,
                              float2* __restrict__ A2, int* flags, int* range) {
+  wait_prior_grid();
   int split_bad = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Nat n = decode_nat(g, c);
@@ -52,6 +53,7 @@ __global__ void k_ingest_bsr(Geom g, const int32_t* __restrict__ rowptr, const i
 __global__ void k_ingest_csr(Geom g, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                              const double* __restrict__ val, int64_t nnz, double* __restrict__ A,
                              float2* __restrict__ A2, int* flags, int* range) {
+  wait_prior_grid();
   int split_bad = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Nat n = decode_nat(g, c);
@@ -83,6 +85,7 @@ __global__ void k_ingest_csr(Geom g, const int32_t* __restrict__ rowptr, const i
 }
 
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  wait_prior_grid();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
 }
@@ -106,6 +109,7 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return _
 template <typename TM, typename TA>
 __global__ void __launch_bounds__(kThreads) k_spmv_nat(Geom g, const TM* __restrict__ A, const double* __restrict__ x,
                                                       double* __restrict__ y, double alpha, double beta) {
+  wait_prior_grid();
   constexpr int H = sizeof(TA) == 8 ? 2 : 1;  // cells per thread
   const int64_t nxy = (int64_t)g.nx * g.ny;
   const int64_t off[7] = {-nxy, -(int64_t)g.nx, -1, 0, 1, (int64_t)g.nx, nxy};
@@ -211,6 +215,7 @@ template <typename V, int Q>
 __global__ void __launch_bounds__(kThreads) k_spmv_tiled(Geom g, const V* __restrict__ A, const double* __restrict__ x,
                                                         double* __restrict__ y, double alpha, double beta,
                                                         const double* __restrict__ A64, const int* __restrict__ range) {
+  wait_prior_grid();
   constexpr bool SPLIT = sizeof(V) == 8;
   constexpr int C = 2 * Q;  // cells of a group
   // a split copy that could not hold every value: the FP64 planes instead
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_tiled(Geom g, const V* __rest
 // copies the public SpMV reads)
 template <typename T>
 __global__ void k_to_tiled(Geom g, const double* __restrict__ src, T* __restrict__ dst) {
+  wait_prior_grid();
   const size_t n = (size_t)126 * g.Nh;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(i / g.Nh);  // plane: colour * 63 + slot * 9 + rc
@@ -369,6 +375,7 @@ __global__ void k_to_tiled(Geom g, const double* __restrict__ src, T* __restrict
 }
 
 __global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+  wait_prior_grid();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = __float2bfloat16_rn((float)src[i]);
 }
@@ -376,6 +383,7 @@ __global__ void k_to_bf16(const double* __restrict__ src, __nv_bfloat16* __restr
 // split (hi, lo) copy of the matrix values for the Arnoldi product, in the
 // tiled layout; *range flags values the split form cannot hold
 __global__ void k_split_matrix(Geom g, const double* __restrict__ src, float2* __restrict__ dst, int* range) {
+  wait_prior_grid();
   int bad = 0;
   const size_t n = (size_t)126 * g.Nh;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -387,11 +395,13 @@ __global__ void k_split_matrix(Geom g, const double* __restrict__ src, float2* _
 }
 
 __global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
+  wait_prior_grid();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (double)src[i];
 }
 
 __global__ void k_gather(Geom g, const double* __restrict__ nat, double* __restrict__ in) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Nat n = decode_nat(g, c);
     for (int k = 0; k < 3; ++k) in[vidx(g, k, n.color, n.q)] = nat[3 * c + k];
@@ -399,6 +409,7 @@ __global__ void k_gather(Geom g, const double* __restrict__ nat, double* __restr
 }
 
 __global__ void k_scatter(Geom g, const double* __restrict__ in, double* __restrict__ nat) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Nat n = decode_nat(g, c);
     for (int k = 0; k < 3; ++k) nat[3 * c + k] = in[vidx(g, k, n.color, n.q)];
@@ -406,6 +417,7 @@ __global__ void k_scatter(Geom g, const double* __restrict__ in, double* __restr
 }
 
 __global__ void k_axpy1(double* __restrict__ s, const double* __restrict__ d, int64_t n) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s[i] += d[i];
 }
@@ -414,7 +426,7 @@ __global__ void k_axpy1(double* __restrict__ s, const double* __restrict__ d, in
 
 int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s) {
   cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
-  (k_ingest_bsr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
+  (launch_pdl(k_ingest_bsr, grid_for(m->g.N), kThreads, 0, s, m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
                                                       m->a2_range), note_launch());
   m->a2_valid = true;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
@@ -422,14 +434,14 @@ int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s) {
 
 int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s) {
   cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
-  (k_ingest_csr<<<grid_for(m->g.N), kThreads, 0, s>>>(m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
+  (launch_pdl(k_ingest_csr, grid_for(m->g.N), kThreads, 0, s, m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
                                                       m->a2_range), note_launch());
   m->a2_valid = true;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
 void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
-  (k_to_f32<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
+  (launch_pdl(k_to_f32, grid_for((int64_t)n), kThreads, 0, s, src, dst, n), note_launch());
 }
 
 void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta, double* y, int precision) {
@@ -438,68 +450,68 @@ void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta
   if ((((uintptr_t)x) | ((uintptr_t)y)) & 15) {
     // vectors off a 16-byte boundary: the tiled kernels read and write them
     // 16 bytes at a time, so the FP64 planes with scalar accesses instead
-    (k_spmv_nat<double, double><<<grid_for(g.Nh, kThreads, 152 * 64), kThreads, 0, s>>>(g, m->A, x, y, alpha, beta),
+    (launch_pdl(k_spmv_nat<double, double>, grid_for(g.Nh, kThreads, 152 * 64), kThreads, 0, s, g, m->A, x, y, alpha, beta),
      note_launch());
     return;
   }
   if (precision == BO_PREC_FP32) {
     const int Q = g.hx % 2 == 0 ? 2 : 1;
     if (Q == 2)
-      (k_spmv_tiled<float, 2><<<grid_for((g.Nh + 1) / 2), kThreads, 0, s>>>(g, m->A32, x, y, alpha, beta, nullptr,
+      (launch_pdl(k_spmv_tiled<float, 2>, grid_for((g.Nh + 1) / 2), kThreads, 0, s, g, m->A32, x, y, alpha, beta, nullptr,
                                                                               nullptr),
        note_launch());
     else
-      (k_spmv_tiled<float, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A32, x, y, alpha, beta, nullptr, nullptr),
+      (launch_pdl(k_spmv_tiled<float, 1>, grid_for(g.Nh), kThreads, 0, s, g, m->A32, x, y, alpha, beta, nullptr, nullptr),
        note_launch());
   } else if (precision == BO_PREC_BF16) {
     if (g.hx % 2 == 0)
-      (k_spmv_tiled<__nv_bfloat16, 2><<<grid_for((g.Nh + 1) / 2), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta,
+      (launch_pdl(k_spmv_tiled<__nv_bfloat16, 2>, grid_for((g.Nh + 1) / 2), kThreads, 0, s, g, m->A16, x, y, alpha, beta,
                                                                                       nullptr, nullptr),
        note_launch());
     else
-      (k_spmv_tiled<__nv_bfloat16, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A16, x, y, alpha, beta, nullptr,
+      (launch_pdl(k_spmv_tiled<__nv_bfloat16, 1>, grid_for(g.Nh), kThreads, 0, s, g, m->A16, x, y, alpha, beta, nullptr,
                                                                              nullptr),
        note_launch());
   } else {
     bo_mat* mm = const_cast<bo_mat*>(m);
     if (!mm->a2_valid) launch_split_matrix(mm, s);
-    (k_spmv_tiled<float2, 1><<<grid_for(g.Nh), kThreads, 0, s>>>(g, m->A2, x, y, alpha, beta, m->A, m->a2_range),
+    (launch_pdl(k_spmv_tiled<float2, 1>, grid_for(g.Nh), kThreads, 0, s, g, m->A2, x, y, alpha, beta, m->A, m->a2_range),
      note_launch());
   }
 }
 
 void launch_to_tiled_f32(const bo_mat* m, float* dst, cudaStream_t s) {
-  (k_to_tiled<float><<<grid_for((int64_t)63 * m->g.N), kThreads, 0, s>>>(m->g, m->A, dst), note_launch());
+  (launch_pdl(k_to_tiled<float>, grid_for((int64_t)63 * m->g.N), kThreads, 0, s, m->g, m->A, dst), note_launch());
 }
 
 void launch_to_tiled_bf16(const bo_mat* m, __nv_bfloat16* dst, cudaStream_t s) {
-  (k_to_tiled<__nv_bfloat16><<<grid_for((int64_t)63 * m->g.N), kThreads, 0, s>>>(m->g, m->A, dst), note_launch());
+  (launch_pdl(k_to_tiled<__nv_bfloat16>, grid_for((int64_t)63 * m->g.N), kThreads, 0, s, m->g, m->A, dst), note_launch());
 }
 
 void launch_split_matrix(bo_mat* m, cudaStream_t s) {
   cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
-  (k_split_matrix<<<grid_for((int64_t)63 * m->g.N), kThreads, 0, s>>>(m->g, m->A, m->A2, m->a2_range), note_launch());
+  (launch_pdl(k_split_matrix, grid_for((int64_t)63 * m->g.N), kThreads, 0, s, m->g, m->A, m->A2, m->a2_range), note_launch());
   m->a2_valid = true;
 }
 
 void launch_to_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t s) {
-  (k_to_bf16<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
+  (launch_pdl(k_to_bf16, grid_for((int64_t)n), kThreads, 0, s, src, dst, n), note_launch());
 }
 
 void launch_widen(const float* src, double* dst, size_t n, cudaStream_t s) {
-  (k_widen<<<grid_for((int64_t)n), kThreads, 0, s>>>(src, dst, n), note_launch());
+  (launch_pdl(k_widen, grid_for((int64_t)n), kThreads, 0, s, src, dst, n), note_launch());
 }
 
 void launch_gather(const Geom& g, const double* nat, double* in, cudaStream_t s) {
-  (k_gather<<<grid_for(g.N), kThreads, 0, s>>>(g, nat, in), note_launch());
+  (launch_pdl(k_gather, grid_for(g.N), kThreads, 0, s, g, nat, in), note_launch());
 }
 
 void launch_scatter(const Geom& g, const double* in, double* nat, cudaStream_t s) {
-  (k_scatter<<<grid_for(g.N), kThreads, 0, s>>>(g, in, nat), note_launch());
+  (launch_pdl(k_scatter, grid_for(g.N), kThreads, 0, s, g, in, nat), note_launch());
 }
 
 void launch_newton_update(double* state, const double* dx, int64_t n, cudaStream_t s) {
-  (k_axpy1<<<grid_for(n), kThreads, 0, s>>>(state, dx, n), note_launch());
+  (launch_pdl(k_axpy1, grid_for(n), kThreads, 0, s, state, dx, n), note_launch());
 }
 
 }  // namespace bo

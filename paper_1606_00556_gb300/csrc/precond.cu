@@ -138,6 +138,7 @@ template <typename S>
 __global__ void k_decouple(Geom g, const double* __restrict__ A, const float2* __restrict__ A2,
                            const int* __restrict__ range, S* __restrict__ At, double* __restrict__ w,
                            float* __restrict__ wf, int abf, DevState* st) {
+  wait_prior_grid();
   const bool split = sizeof(S) < sizeof(double) && A2 && !*range;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
@@ -226,6 +227,7 @@ __global__ void k_decouple(Geom g, const double* __restrict__ A, const float2* _
 template <typename S, bool SPLIT>
 __global__ void k_ilu_red(Geom g, const double* __restrict__ A, const double* __restrict__ w, S* __restrict__ Dinv,
                           double* __restrict__ red64, DevState* st) {
+  wait_prior_grid();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     double d[9], inv[9];
     dec_block(g, A, w, 0, kDiag, q, d);
@@ -294,6 +296,7 @@ template <typename S>
 __global__ void k_ilu_black_split(Geom g, const float2* __restrict__ A2, const double* __restrict__ A,
                                   const int* __restrict__ range, const double* __restrict__ w,
                                   const float2* __restrict__ red2, S* __restrict__ Dinv, DevState* st) {
+  wait_prior_grid();
   if (*range) {  // a value outside the split form's range: the FP64 products, from A
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
       const Cell c = decode(g, 1, q);
@@ -362,6 +365,7 @@ __global__ void k_ilu_black_split(Geom g, const float2* __restrict__ A2, const d
 template <typename S>
 __global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* __restrict__ w,
                             const double* __restrict__ red64, S* __restrict__ Dinv, DevState* st) {
+  wait_prior_grid();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
     double Sc[9], inv[9];
@@ -389,6 +393,7 @@ __global__ void k_ilu_black(Geom g, const double* __restrict__ A, const double* 
 
 template <typename S>
 __global__ void k_convert(const double* __restrict__ src, S* __restrict__ dst, size_t n) {
+  wait_prior_grid();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = to_store<S>(src[i]);
 }
@@ -428,6 +433,7 @@ __device__ __forceinline__ int dir_slot(int di, int dj, int dk) {
 // and the weights): coarse entry (I, J) = sum of fine a_ij, i in I, j in J.
 __global__ void k_galerkin0(Geom g, const double* __restrict__ A, const double* __restrict__ w, LevelDims C,
                             double* __restrict__ c64, DevState* st) {
+  wait_prior_grid();
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
     const Ijk cc = ijk_of(C, I);
   const int ci = cc.i, cj = cc.j, ck = cc.k;
@@ -459,6 +465,7 @@ __global__ void k_galerkin0(Geom g, const double* __restrict__ A, const double* 
 // Galerkin level l+1 from natural-order level l
 __global__ void k_galerkinn(LevelDims F, const double* __restrict__ f64, LevelDims C, double* __restrict__ c64,
                             DevState* st) {
+  wait_prior_grid();
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x) {
     const Ijk cc = ijk_of(C, I);
   const int ci = cc.i, cj = cc.j, ck = cc.k;
@@ -486,6 +493,7 @@ __global__ void k_galerkinn(LevelDims F, const double* __restrict__ f64, LevelDi
 // colour-split index order (index = colour * N/2 + q)
 __global__ void k_dense_from_level(LevelDims L, const double* __restrict__ c64, Geom g, const double* __restrict__ A,
                                    const double* __restrict__ w, int level0, double* __restrict__ M) {
+  wait_prior_grid();
   const int64_t n = L.n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n; t += (int64_t)gridDim.x * blockDim.x)
     M[t] = 0.0;
@@ -530,6 +538,7 @@ __global__ void k_dense_from_level(LevelDims L, const double* __restrict__ c64, 
 // written to Minv in type S.
 template <typename S>
 __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __restrict__ M, S* __restrict__ Minv, DevState* st) {
+  wait_prior_grid();
   extern __shared__ double sm[];
   double* a = sm;                 // n * n
   int* perm = (int*)(a + n * n);  // n
@@ -614,6 +623,7 @@ template <typename T, typename S, bool DEC>
 __global__ void k_cpr_entry(Geom g, InV v, const double* __restrict__ vs, const double* __restrict__ w,
                             const float* __restrict__ wf, const S* __restrict__ Dinv, T* __restrict__ f,
                             T* __restrict__ tv, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   const double sc = vs ? *vs : 1.0;  // scale of an unnormalised Krylov vector
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -657,6 +667,7 @@ __device__ __forceinline__ void out_put(const OutV& o, size_t i, T v) {
 
 template <typename T>
 __global__ void k_widen_t(int64_t n, const T* __restrict__ a, double* __restrict__ b, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
@@ -664,6 +675,7 @@ __global__ void k_widen_t(int64_t n, const T* __restrict__ a, double* __restrict
 
 template <typename T>
 __global__ void k_copy_vec(int64_t n, const double* __restrict__ v, T* __restrict__ f, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     f[t] = (T)v[t];
@@ -709,6 +721,7 @@ template <typename T, typename S, bool OUT>
 __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_b(Geom g, const S* __restrict__ At, const S* __restrict__ Dinv, const T* __restrict__ src,
                         T* __restrict__ tv, T* __restrict__ z, const T* __restrict__ e, OutV zo,
                         const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 1, q);
@@ -743,6 +756,7 @@ template <typename T, typename S, bool OUT>
 __global__ void __launch_bounds__(kThreads, ilu_min_blocks<T>()) k_ilu_r2(Geom g, const S* __restrict__ At, const S* __restrict__ Dinv, const T* __restrict__ tv,
                          const T* __restrict__ ub, T* __restrict__ z, const T* __restrict__ e, OutV zo,
                          const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x) {
     const Cell c = decode(g, 0, q);
@@ -775,6 +789,7 @@ template <typename T, typename S, int ROWS>
 __global__ void __launch_bounds__(kThreads, res_min_blocks<T, ROWS>()) k_cpr_residual(Geom g, const S* __restrict__ At, const T* __restrict__ f, const T* __restrict__ z,
                                const T* __restrict__ e, T* __restrict__ out, const S* __restrict__ Dinv,
                                T* __restrict__ tv, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
@@ -870,6 +885,7 @@ __device__ __forceinline__ void sweep_batched(int64_t t0, int64_t nt, int64_t n,
 template <typename T, typename S>
 __global__ void k_gs0(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x, int color,
                       int zero_guess, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x)
     gs0_cell<T, S>(g, At, f, x, color, zero_guess, q);
@@ -909,6 +925,7 @@ __device__ __forceinline__ void gs0_prolong_cell(const Geom& g, const S* __restr
 template <typename T, typename S>
 __global__ void k_gs0_prolong(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x,
                               LevelDims C, const T* __restrict__ xc, T sc, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x)
     gs0_prolong_cell<T, S>(g, At, f, x, C, xc, sc, q);
@@ -947,6 +964,7 @@ __device__ __forceinline__ T restrict0_cell(const Geom& g, const S* __restrict__
 template <typename T, typename S>
 __global__ void k_restrict0(Geom g, const S* __restrict__ At, const T* __restrict__ f, const T* __restrict__ x,
                             LevelDims C, T* __restrict__ fc, int red_only, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.n; I += (int64_t)gridDim.x * blockDim.x)
     fc[I] = restrict0_cell<T, S>(g, At, f, x, C, I, red_only);
@@ -963,6 +981,7 @@ __device__ __forceinline__ void prolong0_cell(const Geom& g, T* __restrict__ x, 
 
 template <typename T>
 __global__ void k_prolong0(Geom g, T* __restrict__ x, LevelDims C, const T* __restrict__ xc, T s, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x)
     prolong0_cell<T>(g, x, C, xc, s, t);
@@ -1074,6 +1093,7 @@ __device__ __forceinline__ void gs_cell_prolong(const LevelView<T, S>& L, const 
 
 template <typename T, typename S>
 __global__ void k_gsn_prolong(LevelView<T, S> L, LevelView<T, S> C, T sc, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.d.n; c += (int64_t)gridDim.x * blockDim.x)
     gs_cell_prolong(L, C, c, sc);
@@ -1081,6 +1101,7 @@ __global__ void k_gsn_prolong(LevelView<T, S> L, LevelView<T, S> C, T sc, const 
 
 template <typename T, typename S>
 __global__ void k_gsn(LevelView<T, S> L, int color, int zero_guess, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.d.n; c += (int64_t)gridDim.x * blockDim.x)
     gs_cell(L, c, color, zero_guess);
@@ -1088,6 +1109,7 @@ __global__ void k_gsn(LevelView<T, S> L, int color, int zero_guess, const DevSta
 
 template <typename T, typename S>
 __global__ void k_restrictn(LevelView<T, S> F, LevelView<T, S> C, int red_only, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < C.d.n; I += (int64_t)gridDim.x * blockDim.x)
     C.f[I] = restrict_cell(F, C.d, I, red_only);
@@ -1095,6 +1117,7 @@ __global__ void k_restrictn(LevelView<T, S> F, LevelView<T, S> C, int red_only, 
 
 template <typename T, typename S>
 __global__ void k_prolongn(LevelView<T, S> F, LevelView<T, S> C, T s, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < F.d.n; c += (int64_t)gridDim.x * blockDim.x)
     prolong_cell(F, C, c, s);
@@ -1188,6 +1211,7 @@ __device__ void tail_cycle(const TailArgs<T, S>& a, const Views& vw) {
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T, S> a, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   tail_cycle(a, TailGlobalViews<T, S>{&a});
 }
@@ -1286,6 +1310,7 @@ __device__ void tail_run_staged(const TailArgs<T, S>& a, const TailSharedViews<T
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kTailThreads) k_tail_smem(TailArgs<T, S> a, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   __shared__ uint32_t off[73];
   tail_offsets(a, off);
@@ -1467,12 +1492,14 @@ __device__ bool amg_up(const CycleArgs<T, S>& a, DevState* st) {
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_down(CycleArgs<T, S> a, DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   amg_down(a, st);
 }
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_up(CycleArgs<T, S> a, DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   amg_up(a, st);
 }
@@ -1500,6 +1527,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 template <typename T, typename S>
 __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_coarse(CycleArgs<T, S> a, TailArgs<T, S> ta, int tail_smem,
                                                                const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;  // uniform: every block reads the same flag
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
   // the last block runs the tail; it stages the tail's coefficients and
@@ -1565,6 +1593,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_amg_coarse(CycleArgs<T, S> 
 template <typename T, typename S>
 __global__ void k_dense0(int64_t n, const S* __restrict__ inv, const T* __restrict__ f, T* __restrict__ x,
                          const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
@@ -1575,6 +1604,7 @@ __global__ void k_dense0(int64_t n, const S* __restrict__ inv, const T* __restri
 
 template <typename T>
 __global__ void k_zero(int64_t n, T* __restrict__ x, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = T(0);
@@ -1583,6 +1613,7 @@ __global__ void k_zero(int64_t n, T* __restrict__ x, const DevState* st) {
 // z = Pi_p e (stage AMG alone), FP64 output
 template <typename T>
 __global__ void k_place_p(Geom g, const T* __restrict__ e, double* __restrict__ z, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     z[t] = (double)e[t];
@@ -1594,6 +1625,7 @@ __global__ void k_place_p(Geom g, const T* __restrict__ e, double* __restrict__ 
 // y = At x with At rebuilt in FP64 from A and the weights (parity checks)
 __global__ void k_spmv_dec64(Geom g, const double* __restrict__ A, const double* __restrict__ w,
                              const double* __restrict__ x, double* __restrict__ y) {
+  wait_prior_grid();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = (int)(t / g.Nh);
     const int64_t q = t - color * g.Nh;
@@ -1669,7 +1701,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   const int nu1 = P->opts.amg_nu1, nu2 = P->opts.amg_nu2;
   const T sc = (T)P->opts.amg_overcorr;
   if (P->nlev == 1) {
-    (k_dense0<T, S><<<grid_for(g.N), kThreads, 0, s>>>(g.N, (const S*)P->coarse_inv, f0, x0, st), note_launch());
+    (launch_pdl(k_dense0<T, S>, grid_for(g.N), kThreads, 0, s, g.N, (const S*)P->coarse_inv, f0, x0, st), note_launch());
     return;
   }
   const int ghalf = grid_for(g.Nh);
@@ -1717,31 +1749,31 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
       LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
       const int gl = grid_for(L.d.n);
       for (int sw = 0; sw < nu1; ++sw) {
-        (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, sw == 0, st), note_launch());
-        (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
+        (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 0, sw == 0, st), note_launch());
+        (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 1, 0, st), note_launch());
       }
-      if (nu1 == 0) (k_zero<T><<<gl, kThreads, 0, s>>>(L.d.n, L.x, st), note_launch());
-      (k_restrictn<T, S><<<grid_for(C.d.n), kThreads, 0, s>>>(L, C, nu1 > 0, st), note_launch());
+      if (nu1 == 0) (launch_pdl(k_zero<T>, gl, kThreads, 0, s, L.d.n, L.x, st), note_launch());
+      (launch_pdl(k_restrictn<T, S>, grid_for(C.d.n), kThreads, 0, s, L, C, nu1 > 0, st), note_launch());
     }
   };
   auto natural_up = [&]() {
     for (int l = P->tail_from - 1; l >= 1; --l) {
       LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
       const int gl = grid_for(L.d.n);
-      if (nu2 == 0) (k_prolongn<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
+      if (nu2 == 0) (launch_pdl(k_prolongn<T, S>, gl, kThreads, 0, s, L, C, sc, st), note_launch());
       for (int sw = 0; sw < nu2; ++sw) {
-        if (sw == 0) (k_gsn_prolong<T, S><<<gl, kThreads, 0, s>>>(L, C, sc, st), note_launch());
-        else (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 1, 0, st), note_launch());
-        (k_gsn<T, S><<<gl, kThreads, 0, s>>>(L, 0, 0, st), note_launch());
+        if (sw == 0) (launch_pdl(k_gsn_prolong<T, S>, gl, kThreads, 0, s, L, C, sc, st), note_launch());
+        else (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 1, 0, st), note_launch());
+        (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 0, 0, st), note_launch());
       }
     }
   };
   auto tail = [&]() {
     if (tb <= kTailSmemMax) {
       cudaFuncSetAttribute(k_tail_smem<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb);
-      (k_tail_smem<T, S><<<1, kTailThreads, tb, s>>>(ta, st), note_launch());
+      (launch_pdl(k_tail_smem<T, S>, 1, kTailThreads, tb, s, ta, st), note_launch());
     } else {
-      (k_tail<T, S><<<1, kTailThreads, 0, s>>>(ta, st), note_launch());
+      (launch_pdl(k_tail<T, S>, 1, kTailThreads, 0, s, ta, st), note_launch());
     }
   };
 
@@ -1756,11 +1788,11 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   }
   if (!down_done) {
     for (int sw = 0; sw < nu1; ++sw) {
-      (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, sw == 0, st), note_launch());
-      (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
+      (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 0, sw == 0, st), note_launch());
+      (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 1, 0, st), note_launch());
     }
-    if (nu1 == 0) (k_zero<T><<<grid_for(g.N), kThreads, 0, s>>>(g.N, x0, st), note_launch());
-    (k_restrict0<T, S><<<grid_for(P->lev[1].n), kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]),
+    if (nu1 == 0) (launch_pdl(k_zero<T>, grid_for(g.N), kThreads, 0, s, g.N, x0, st), note_launch());
+    (launch_pdl(k_restrict0<T, S>, grid_for(P->lev[1].n), kThreads, 0, s, g, At, f0, x0, dims_of(P->lev[1]),
                                                                (T*)P->lev[1].f, nu1 > 0, st), note_launch());
     natural_down();
     tail();
@@ -1803,15 +1835,15 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     natural_up();
   }
   if (nu2 == 0)
-    (k_prolong0<T><<<grid_for(g.N), kThreads, 0, s>>>(g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
+    (launch_pdl(k_prolong0<T>, grid_for(g.N), kThreads, 0, s, g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
      note_launch());
   for (int sw = 0; sw < nu2; ++sw) {
     if (sw == 0)
-      (k_gs0_prolong<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
+      (launch_pdl(k_gs0_prolong<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
        note_launch());
     else
-      (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 1, 0, st), note_launch());
-    (k_gs0<T, S><<<ghalf, kThreads, 0, s>>>(g, At, f0, x0, 0, 0, st), note_launch());
+      (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 1, 0, st), note_launch());
+    (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 0, 0, st), note_launch());
   }
 }
 
@@ -1830,46 +1862,46 @@ void cpr_apply(bo_prec* P, InV v, OutV zo, int stage, const DevState* st, const 
   T* f0 = (T*)P->f0;
   T* z1 = (T*)P->z1;
   if (stage == BO_STAGE_AMG) {  // (v is a caller's FP64 vector here: vs is NULL)
-    (k_copy_vec<T><<<gN, kThreads, 0, s>>>(g.N, v.d, f0, st), note_launch());
+    (launch_pdl(k_copy_vec<T>, gN, kThreads, 0, s, g.N, v.d, f0, st), note_launch());
     amg_vcycle<T, S>(P, st);
     learned_coarse_apply(P, st);
-    (k_place_p<T><<<gN, kThreads, 0, s>>>(g, e0, zo.d, st), note_launch());
+    (launch_pdl(k_place_p<T>, gN, kThreads, 0, s, g, e0, zo.d, st), note_launch());
     return;
   }
   // x1 = R^{-1} f with f = D_QI^{-1} v (stage CPR) or f = v
   if (stage == BO_STAGE_CPR)
-    (k_cpr_entry<T, S, true><<<occ_grid((const void*)k_cpr_entry<T, S, true>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, P->wf,
+    (launch_pdl(k_cpr_entry<T, S, true>, occ_grid((const void*)k_cpr_entry<T, S, true>, g.N), kThreads, 0, s, g, v, vs, P->w, P->wf,
                                                                                                   D, f, tv, st),
      note_launch());
   else
-    (k_cpr_entry<T, S, false><<<occ_grid((const void*)k_cpr_entry<T, S, false>, g.N), kThreads, 0, s>>>(g, v, vs, P->w, P->wf,
+    (launch_pdl(k_cpr_entry<T, S, false>, occ_grid((const void*)k_cpr_entry<T, S, false>, g.N), kThreads, 0, s, g, v, vs, P->w, P->wf,
                                                                                                     D, f, tv, st),
      note_launch());
-  (k_ilu_b<T, S, false><<<occ_grid((const void*)k_ilu_b<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, f, tv, z1, nullptr,
+  (launch_pdl(k_ilu_b<T, S, false>, occ_grid((const void*)k_ilu_b<T, S, false>, g.Nh), kThreads, 0, s, g, At, D, f, tv, z1, nullptr,
                                                                                           OutV{}, st),
    note_launch());
   // (ub and z are both z1: the pass reads its black half and writes its red half)
-  (k_ilu_r2<T, S, false><<<occ_grid((const void*)k_ilu_r2<T, S, false>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, z1, z1,
+  (launch_pdl(k_ilu_r2<T, S, false>, occ_grid((const void*)k_ilu_r2<T, S, false>, g.Nh), kThreads, 0, s, g, At, D, tv, z1, z1,
                                                                                             nullptr, OutV{}, st),
    note_launch());
   if (stage == BO_STAGE_ILU) {
-    (k_widen_t<T><<<grid_for(3 * g.N), kThreads, 0, s>>>(3 * g.N, z1, zo.d, st), note_launch());
+    (launch_pdl(k_widen_t<T>, grid_for(3 * g.N), kThreads, 0, s, 3 * g.N, z1, zo.d, st), note_launch());
     return;
   }
   // x2 = x1 + Pi_p AMG(A_pp)^{-1} Pi_r (f - At x1)
-  (k_cpr_residual<T, S, 1><<<occ_grid((const void*)k_cpr_residual<T, S, 1>, g.N), kThreads, 0, s>>>(
+  (launch_pdl(k_cpr_residual<T, S, 1>, occ_grid((const void*)k_cpr_residual<T, S, 1>, g.N), kThreads, 0, s, 
        g, At, f, z1, nullptr, f0, nullptr, nullptr, st),
    note_launch());
   amg_vcycle<T, S>(P, st);
   learned_coarse_apply(P, st);
   // r = f - At x2 (with the red pass of R^{-1} r fused);  x3 = x2 + R^{-1} r
-  (k_cpr_residual<T, S, 3><<<occ_grid((const void*)k_cpr_residual<T, S, 3>, g.N), kThreads, 0, s>>>(g, At, f, z1, e0, r,
+  (launch_pdl(k_cpr_residual<T, S, 3>, occ_grid((const void*)k_cpr_residual<T, S, 3>, g.N), kThreads, 0, s, g, At, f, z1, e0, r,
                                                                                                 D, tv, st),
    note_launch());
-  (k_ilu_b<T, S, true><<<occ_grid((const void*)k_ilu_b<T, S, true>, g.Nh), kThreads, 0, s>>>(g, At, D, r, tv, z1, e0, zo,
+  (launch_pdl(k_ilu_b<T, S, true>, occ_grid((const void*)k_ilu_b<T, S, true>, g.Nh), kThreads, 0, s, g, At, D, r, tv, z1, e0, zo,
                                                                                         st),
    note_launch());
-  (k_ilu_r2<T, S, true><<<occ_grid((const void*)k_ilu_r2<T, S, true>, g.Nh), kThreads, 0, s>>>(g, At, D, tv, tv, z1, e0,
+  (launch_pdl(k_ilu_r2<T, S, true>, occ_grid((const void*)k_ilu_r2<T, S, true>, g.Nh), kThreads, 0, s, g, At, D, tv, tv, z1, e0,
                                                                                           zo, st),
    note_launch());
 }
@@ -1880,39 +1912,39 @@ int values_impl(bo_prec* P) {
   cudaStream_t s = P->stream;
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
-  (k_decouple<S><<<gN, kThreads, 0, s>>>(g, m->A, m->a2_valid ? m->A2 : nullptr, m->a2_range, (S*)P->At, P->w, P->wf,
+  (launch_pdl(k_decouple<S>, gN, kThreads, 0, s, g, m->A, m->a2_valid ? m->A2 : nullptr, m->a2_range, (S*)P->At, P->w, P->wf,
                                          P->opts.decoupling == BO_DECOUPLE_ABF, P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
   if (sizeof(S) < sizeof(double) && m->a2_valid) {
     // black pivots in split arithmetic (the kernel takes the FP64 products
     // itself where the split copy of A could not hold every value)
-    (k_ilu_red<S, true><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
-    (k_ilu_black_split<S><<<gh, kThreads, 0, s>>>(g, m->A2, m->A, m->a2_range, P->w,
+    (launch_pdl(k_ilu_red<S, true>, gh, kThreads, 0, s, g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
+    (launch_pdl(k_ilu_black_split<S>, gh, kThreads, 0, s, g, m->A2, m->A, m->a2_range, P->w,
                                                  reinterpret_cast<const float2*>(red64), (S*)P->Dinv, P->st),
      note_launch());
   } else {
-    (k_ilu_red<S, false><<<gh, kThreads, 0, s>>>(g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
-    (k_ilu_black<S><<<gh, kThreads, 0, s>>>(g, m->A, P->w, red64, (S*)P->Dinv, P->st), note_launch());
+    (launch_pdl(k_ilu_red<S, false>, gh, kThreads, 0, s, g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
+    (launch_pdl(k_ilu_black<S>, gh, kThreads, 0, s, g, m->A, P->w, red64, (S*)P->Dinv, P->st), note_launch());
   }
   // AMG hierarchy values
   for (int l = 1; l < P->nlev; ++l) {
     Level& C = P->lev[l];
     if (l == 1)
-      (k_galerkin0<<<grid_for(C.n), kThreads, 0, s>>>(g, m->A, P->w, dims_of(C), C.c64, P->st), note_launch());
+      (launch_pdl(k_galerkin0, grid_for(C.n), kThreads, 0, s, g, m->A, P->w, dims_of(C), C.c64, P->st), note_launch());
     else
-      (k_galerkinn<<<grid_for(C.n), kThreads, 0, s>>>(dims_of(P->lev[l - 1]), P->lev[l - 1].c64, dims_of(C), C.c64,
+      (launch_pdl(k_galerkinn, grid_for(C.n), kThreads, 0, s, dims_of(P->lev[l - 1]), P->lev[l - 1].c64, dims_of(C), C.c64,
                                                      P->st), note_launch());
-    (k_convert<S><<<grid_for(7 * C.n), kThreads, 0, s>>>(C.c64, (S*)C.c, (size_t)7 * C.n), note_launch());
+    (launch_pdl(k_convert<S>, grid_for(7 * C.n), kThreads, 0, s, C.c64, (S*)C.c, (size_t)7 * C.n), note_launch());
   }
   const int last = P->nlev - 1;
   LevelDims cd = last == 0 ? LevelDims{g.nx, g.ny, g.nz, g.N} : dims_of(P->lev[last]);
-  (k_dense_from_level<<<1, kThreads, 0, s>>>(cd, last == 0 ? nullptr : P->lev[last].c64, g, m->A, P->w, last == 0,
+  (launch_pdl(k_dense_from_level, 1, kThreads, 0, s, cd, last == 0 ? nullptr : P->lev[last].c64, g, m->A, P->w, last == 0,
                                             P->coarse64), note_launch());
   const int n = (int)P->ncoarse;
   const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
   cudaFuncSetAttribute(k_gj_inverse<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  (k_gj_inverse<S><<<1, 1024, smem, s>>>(n, P->coarse64, (S*)P->coarse_inv, P->st), note_launch());
+  (launch_pdl(k_gj_inverse<S>, 1, 1024, smem, s, n, P->coarse64, (S*)P->coarse_inv, P->st), note_launch());
   if (cudaGetLastError() != cudaSuccess) return BO_ERR_CUDA;
   return learned_coarse_values(P);
 }
@@ -1990,7 +2022,7 @@ int launch_dense_inverse64(int n, const double* M, double* Minv, DevState* st, c
   if (n < 1 || n > kCoarseMax) return BO_ERR_ARG;
   const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
   cudaFuncSetAttribute(k_gj_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  (k_gj_inverse<double><<<1, 1024, smem, s>>>(n, M, Minv, st), note_launch());
+  (launch_pdl(k_gj_inverse<double>, 1, 1024, smem, s, n, M, Minv, st), note_launch());
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
 
@@ -2023,7 +2055,7 @@ void launch_cpr_split_in(bo_prec* P, const float* v, float* z, const DevState* s
 
 void launch_spmv_decoupled_internal(bo_prec* P, const double* x, double* y) {
   const Geom& g = P->mat->g;
-  (k_spmv_dec64<<<grid_for(g.N), kThreads, 0, P->stream>>>(g, P->mat->A, P->w, x, y), note_launch());
+  (launch_pdl(k_spmv_dec64, grid_for(g.N), kThreads, 0, P->stream, g, P->mat->A, P->w, x, y), note_launch());
 }
 
 }  // namespace bo
