@@ -98,6 +98,7 @@ __device__ __forceinline__ void mv3(const double a[9], const double x[3], double
 __global__ void k_dp_condense(Geom g, const double* __restrict__ val, const int32_t* __restrict__ fmap,
                               const int32_t* __restrict__ mmap, double* __restrict__ A, double* __restrict__ minv,
                               int* flags) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
     const int color = (i + j + k) & 1;
@@ -134,6 +135,7 @@ __global__ void k_dp_condense(Geom g, const double* __restrict__ val, const int3
 // b_hat = b_f - A_fm A_mm^{-1} b_m
 __global__ void k_dp_rhs(int64_t N, const double* __restrict__ val, const int32_t* __restrict__ fmap,
                          const double* __restrict__ minv, const double* __restrict__ b, double* __restrict__ bhat) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
     double Mi[9], Af[9], bm[3], t[3], u[3];
     for (int e = 0; e < 9; ++e) {
@@ -150,6 +152,7 @@ __global__ void k_dp_rhs(int64_t N, const double* __restrict__ val, const int32_
 // x_m = A_mm^{-1} (b_m - A_mf x_f)
 __global__ void k_dp_recover(int64_t N, const double* __restrict__ val, const int32_t* __restrict__ mmap,
                              const double* __restrict__ minv, const double* __restrict__ b, double* __restrict__ x) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
     double Mi[9], Am[9], xf[3], t[3], y[3];
     for (int e = 0; e < 9; ++e) {
@@ -168,6 +171,7 @@ __global__ void k_dp_recover(int64_t N, const double* __restrict__ val, const in
 __global__ void k_dp_residual(int64_t nb, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                               const double* __restrict__ val, const double* __restrict__ b,
                               const double* __restrict__ x, double* __restrict__ r) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
     double s[3] = {b[3 * i], b[3 * i + 1], b[3 * i + 2]};
     for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -184,6 +188,7 @@ __global__ void k_dp_residual(int64_t nb, const int32_t* __restrict__ rowptr, co
 
 // fixed-order sum of squares: per-block partials, then one block sums them
 __global__ void k_sq_partials(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -193,6 +198,7 @@ __global__ void k_sq_partials(const double* __restrict__ x, int64_t n, double* _
 }
 
 __global__ void k_sum_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
@@ -201,14 +207,15 @@ __global__ void k_sum_final(const double* __restrict__ part, int nb, double* __r
 }
 
 __global__ void k_add(int64_t n, double* __restrict__ x, const double* __restrict__ dx) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] += dx[i];
 }
 
 void sq_norm(const double* x, int64_t n, double* part, double* out, cudaStream_t s) {
   const int gb = grid_for(n, kThreads, kRedGrid);
-  (k_sq_partials<<<gb, kThreads, 0, s>>>(x, n, part), note_launch());
-  (k_sum_final<<<1, kThreads, 0, s>>>(part, gb, out), note_launch());
+  (launch_pdl(k_sq_partials, gb, kThreads, 0, s, x, n, part), note_launch());
+  (launch_pdl(k_sum_final, 1, kThreads, 0, s, part, gb, out), note_launch());
 }
 
 void dp_free(bo_dp* d) {
@@ -224,7 +231,7 @@ void dp_free(bo_dp* d) {
 int dp_condense(bo_dp* d) {
   cudaStream_t s = d->ctx->stream;
   cudaMemsetAsync(d->flags, 0, sizeof(int), s);
-  (k_dp_condense<<<grid_for(d->N), kThreads, 0, s>>>(d->g, d->val, d->fmap, d->mmap, d->S->A, d->minv, d->flags),
+  (launch_pdl(k_dp_condense, grid_for(d->N), kThreads, 0, s, d->g, d->val, d->fmap, d->mmap, d->S->A, d->minv, d->flags),
    note_launch());
   d->S->a32_valid = false;
   d->S->a16_valid = false;
@@ -379,7 +386,7 @@ int bo_dp_solve(bo_dp* d, bo_prec* P, const double* b, double* x, const bo_solve
   int rc = BO_OK;
   const int kPasses = 3;   // the solve plus up to two refinement passes
   for (int pass = 0; pass < kPasses; ++pass) {
-    (bo::k_dp_rhs<<<gN, bo::kThreads, 0, s>>>(N, d->val, d->fmap, d->minv, rhs, d->bhat), bo::note_launch());
+    (bo::launch_pdl(bo::k_dp_rhs, gN, bo::kThreads, 0, s, N, d->val, d->fmap, d->minv, rhs, d->bhat), bo::note_launch());
     bo::sq_norm(d->bhat, 3 * N, d->part, d->norms + 1, s);
     cudaMemcpyAsync(d->h_norms, d->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return BO_ERR_CUDA;
@@ -403,10 +410,10 @@ int bo_dp_solve(bo_dp* d, bo_prec* P, const double* b, double* x, const bo_solve
       acc.est_rel_res = si.est_rel_res;
       if (rc != BO_OK && rc != BO_ERR_NOT_CONVERGED) return rc;
     }
-    (bo::k_dp_recover<<<gN, bo::kThreads, 0, s>>>(N, d->val, d->mmap, d->minv, rhs, xs), bo::note_launch());
-    if (pass > 0) (bo::k_add<<<bo::grid_for(6 * N), bo::kThreads, 0, s>>>(6 * N, x, xs), bo::note_launch());
+    (bo::launch_pdl(bo::k_dp_recover, gN, bo::kThreads, 0, s, N, d->val, d->mmap, d->minv, rhs, xs), bo::note_launch());
+    if (pass > 0) (bo::launch_pdl(bo::k_add, bo::grid_for(6 * N), bo::kThreads, 0, s, 6 * N, x, xs), bo::note_launch());
     // the full system's FP64 residual
-    (bo::k_dp_residual<<<bo::grid_for(2 * N), bo::kThreads, 0, s>>>(2 * N, d->rowptr, d->col, d->val, b, x, d->r),
+    (bo::launch_pdl(bo::k_dp_residual, bo::grid_for(2 * N), bo::kThreads, 0, s, 2 * N, d->rowptr, d->col, d->val, b, x, d->r),
      bo::note_launch());
     bo::sq_norm(d->r, 6 * N, d->part, d->norms + 2, s);
     cudaMemcpyAsync(d->h_norms + 2, d->norms + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -440,7 +447,7 @@ int bo_dp_solve_batched(bo_dp* const* dps, bo_prec* const* P, int nreal, const d
     bo_dp* d = dps[r];
     cudaStream_t s = d->ctx->stream;
     bo::sq_norm(b[r], 6 * d->N, d->part, d->norms, s);
-    (bo::k_dp_rhs<<<bo::grid_for(d->N), bo::kThreads, 0, s>>>(d->N, d->val, d->fmap, d->minv, b[r], d->bhat),
+    (bo::launch_pdl(bo::k_dp_rhs, bo::grid_for(d->N), bo::kThreads, 0, s, d->N, d->val, d->fmap, d->minv, b[r], d->bhat),
      bo::note_launch());
     bo::sq_norm(d->bhat, 3 * d->N, d->part, d->norms + 1, s);
     cudaMemcpyAsync(d->h_norms, d->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -468,9 +475,9 @@ int bo_dp_solve_batched(bo_dp* const* dps, bo_prec* const* P, int nreal, const d
     bo_dp* d = dps[r];
     cudaStream_t s = d->ctx->stream;
     if (zero[r]) cudaMemsetAsync(x[r], 0, 3 * d->N * sizeof(double), s);
-    (bo::k_dp_recover<<<bo::grid_for(d->N), bo::kThreads, 0, s>>>(d->N, d->val, d->mmap, d->minv, b[r], x[r]),
+    (bo::launch_pdl(bo::k_dp_recover, bo::grid_for(d->N), bo::kThreads, 0, s, d->N, d->val, d->mmap, d->minv, b[r], x[r]),
      bo::note_launch());
-    (bo::k_dp_residual<<<bo::grid_for(2 * d->N), bo::kThreads, 0, s>>>(2 * d->N, d->rowptr, d->col, d->val, b[r],
+    (bo::launch_pdl(bo::k_dp_residual, bo::grid_for(2 * d->N), bo::kThreads, 0, s, 2 * d->N, d->rowptr, d->col, d->val, b[r],
                                                                          x[r], d->r),
      bo::note_launch());
     bo::sq_norm(d->r, 6 * d->N, d->part, d->norms + 2, s);

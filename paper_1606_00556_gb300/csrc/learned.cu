@@ -38,6 +38,7 @@ __device__ __forceinline__ int tile_of(const Tiles& T, int i, int j, int k) {
 // field (stride 1) or channel 0 of a network prediction [N][4] (stride 4)
 template <typename T>
 __global__ void k_lc_perm(Geom g, const T* __restrict__ dp, int stride, double scale, double* __restrict__ z) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
     z[((i + j + k) & 1) * g.Nh + (c >> 1)] = scale * (double)dp[c * stride];
@@ -52,6 +53,7 @@ __global__ void k_lc_perm(Geom g, const T* __restrict__ dp, int stride, double s
 // correction on it is zero either way).
 __global__ void k_lc_galerkin(Geom g, Tiles T, const double* __restrict__ A, const double* __restrict__ w,
                               const double* __restrict__ z, double* __restrict__ E, int nt) {
+  wait_prior_grid();
   __shared__ double sh[32];
   const int s = blockIdx.x;
   const int a = s % T.nx, b = (s / T.nx) % T.ny, c = s / (T.nx * T.ny);
@@ -104,6 +106,7 @@ __global__ void k_lc_galerkin(Geom g, Tiles T, const double* __restrict__ A, con
 template <typename T>
 __global__ void k_lc_restrict(Geom g, Tiles Tl, const double* __restrict__ z, const T* __restrict__ f,
                               double* __restrict__ y, const DevState* st) {
+  wait_prior_grid();
   __shared__ double sh[32];
   if (st->done) return;
   const int s = blockIdx.x;
@@ -123,6 +126,7 @@ __global__ void k_lc_restrict(Geom g, Tiles Tl, const double* __restrict__ z, co
 // u = E^{-1} y (one block)
 __global__ void k_lc_solve(int nt, const double* __restrict__ Einv, const double* __restrict__ y,
                            double* __restrict__ u, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int r = threadIdx.x; r < nt; r += blockDim.x) {
     double s = 0.0;
@@ -135,6 +139,7 @@ __global__ void k_lc_solve(int nt, const double* __restrict__ Einv, const double
 template <typename T>
 __global__ void k_lc_prolong(Geom g, Tiles Tl, const double* __restrict__ z, const double* __restrict__ u,
                              T* __restrict__ e, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int color = t >= g.Nh;
@@ -146,6 +151,7 @@ __global__ void k_lc_prolong(Geom g, Tiles Tl, const double* __restrict__ z, con
 // x0[3 c + k] = scale[k] pred[c][k] for k < ncomp, else 0 (natural order)
 __global__ void k_guess(int64_t N, const float* __restrict__ pred, double s0, double s1, double s2, int ncomp,
                         double* __restrict__ x0) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
     x0[3 * c] = s0 * (double)pred[4 * c];
     x0[3 * c + 1] = ncomp > 1 ? s1 * (double)pred[4 * c + 1] : 0.0;
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_guess_norms(Geom g, const double* 
                                                          const double* __restrict__ b,
                                                          const double* __restrict__ x, double* partials,
                                                          DevState* st, double* __restrict__ out) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double rr = 0.0, bb = 0.0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_guess_norms(Geom g, const double* 
 }
 
 __global__ void k_zero64(int64_t n, double* __restrict__ x) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = 0.0;
 }
@@ -219,7 +227,7 @@ int learned_coarse_values(bo_prec* P) {
   cudaStream_t s = P->stream;
   const int nt = P->lc_nt;
   cudaMemsetAsync(P->lc_E, 0, (size_t)nt * nt * sizeof(double), s);
-  (k_lc_galerkin<<<nt, kThreads, 0, s>>>(g, tiles_of(P), P->mat->A, P->w, P->lc_z, P->lc_E, nt), note_launch());
+  (launch_pdl(k_lc_galerkin, nt, kThreads, 0, s, g, tiles_of(P), P->mat->A, P->w, P->lc_z, P->lc_E, nt), note_launch());
   return launch_dense_inverse64(nt, P->lc_E, P->lc_Einv, P->st, s);
 }
 
@@ -229,16 +237,16 @@ void learned_coarse_apply(bo_prec* P, const DevState* st) {
   cudaStream_t s = P->stream;
   const Tiles T = tiles_of(P);
   if (P->fp32) {
-    (k_lc_restrict<float><<<P->lc_nt, kThreads, 0, s>>>(g, T, P->lc_z, (const float*)P->f0, P->lc_y, st),
+    (launch_pdl(k_lc_restrict<float>, P->lc_nt, kThreads, 0, s, g, T, P->lc_z, (const float*)P->f0, P->lc_y, st),
      note_launch());
-    (k_lc_solve<<<1, kThreads, 0, s>>>(P->lc_nt, P->lc_Einv, P->lc_y, P->lc_u, st), note_launch());
-    (k_lc_prolong<float><<<grid_for(g.N), kThreads, 0, s>>>(g, T, P->lc_z, P->lc_u, (float*)P->e0, st),
+    (launch_pdl(k_lc_solve, 1, kThreads, 0, s, P->lc_nt, P->lc_Einv, P->lc_y, P->lc_u, st), note_launch());
+    (launch_pdl(k_lc_prolong<float>, grid_for(g.N), kThreads, 0, s, g, T, P->lc_z, P->lc_u, (float*)P->e0, st),
      note_launch());
   } else {
-    (k_lc_restrict<double><<<P->lc_nt, kThreads, 0, s>>>(g, T, P->lc_z, (const double*)P->f0, P->lc_y, st),
+    (launch_pdl(k_lc_restrict<double>, P->lc_nt, kThreads, 0, s, g, T, P->lc_z, (const double*)P->f0, P->lc_y, st),
      note_launch());
-    (k_lc_solve<<<1, kThreads, 0, s>>>(P->lc_nt, P->lc_Einv, P->lc_y, P->lc_u, st), note_launch());
-    (k_lc_prolong<double><<<grid_for(g.N), kThreads, 0, s>>>(g, T, P->lc_z, P->lc_u, (double*)P->e0, st),
+    (launch_pdl(k_lc_solve, 1, kThreads, 0, s, P->lc_nt, P->lc_Einv, P->lc_y, P->lc_u, st), note_launch());
+    (launch_pdl(k_lc_prolong<double>, grid_for(g.N), kThreads, 0, s, g, T, P->lc_z, P->lc_u, (double*)P->e0, st),
      note_launch());
   }
 }
@@ -285,7 +293,7 @@ int set_coarse_space(bo_prec* P, const T* dp, int stride, double scale, int tx, 
   P->setups++;
   cudaStream_t s = P->stream;
   cudaMemsetAsync(&P->st->err, 0, sizeof(P->st->err), s);
-  (k_lc_perm<T><<<grid_for(g.N), kThreads, 0, s>>>(g, dp, stride, scale, P->lc_z), note_launch());
+  (launch_pdl(k_lc_perm<T>, grid_for(g.N), kThreads, 0, s, g, dp, stride, scale, P->lc_z), note_launch());
   int rc = learned_coarse_values(P);
   DevState h;
   if (cudaMemcpyAsync(&h, P->st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -315,19 +323,19 @@ int bo_learned_guess(bo_prec* P, const double* b, const float* pred, const doubl
   if (cudaSetDevice(P->mat->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   const bo::Geom& g = P->mat->g;
   cudaStream_t s = P->mat->ctx->stream;
-  (bo::k_guess<<<bo::grid_for(g.N), bo::kThreads, 0, s>>>(g.N, pred, scale[0], scale[1], scale[2], ncomp, x0),
+  (bo::launch_pdl(bo::k_guess, bo::grid_for(g.N), bo::kThreads, 0, s, g.N, pred, scale[0], scale[1], scale[2], ncomp, x0),
    bo::note_launch());
   // ||b - A x0|| against ||b||: partial sums in the preconditioner's own
   // reduction memory, the two norms at the start of the idle Krylov basis
   double* norms = P->V;
-  (bo::k_guess_norms<<<bo::grid_for(g.N), bo::kThreads, 0, s>>>(g, P->mat->A, b, x0, P->partials, P->st, norms),
+  (bo::launch_pdl(bo::k_guess_norms, bo::grid_for(g.N), bo::kThreads, 0, s, g, P->mat->A, b, x0, P->partials, P->st, norms),
    bo::note_launch());
   double h[2];
   if (cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return BO_ERR_CUDA;
   const int keep = std::isfinite(h[0]) && h[0] < h[1];
-  if (!keep) (bo::k_zero64<<<bo::grid_for(3 * g.N), bo::kThreads, 0, s>>>(3 * g.N, x0), bo::note_launch());
+  if (!keep) (bo::launch_pdl(bo::k_zero64, bo::grid_for(3 * g.N), bo::kThreads, 0, s, 3 * g.N, x0), bo::note_launch());
   if (used) *used = keep;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }

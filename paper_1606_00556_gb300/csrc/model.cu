@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_cell_props(Geom g, bo_fluid f, dou
                                                         const double* __restrict__ cperf, double* __restrict__ props,
                                                         double* __restrict__ racc, double* __restrict__ dacc,
                                                         int* err) {
+  wait_prior_grid();
   const double scale = dx * dy * dz / (kFt3PerBbl * dt);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const Dn<3> p = dn_var<3>(x[3 * c], 0), sw = dn_var<3>(x[3 * c + 1], 1), sg = dn_var<3>(x[3 * c + 2], 2);
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_faces(Geom g, int fam, double area
                                                    const double* __restrict__ perm, const double* __restrict__ depth,
                                                    const double* __restrict__ x, const double* __restrict__ props,
                                                    double* __restrict__ out) {
+  wait_prior_grid();
   const int64_t stride = fam == 0 ? 1 : fam == 1 ? (int64_t)g.nx : (int64_t)g.nx * g.ny;
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < g.N; a += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = a / g.nx;
@@ -374,6 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(Geom g, const int32_t* __re
                                                     const double* __restrict__ racc, const double* __restrict__ dacc,
                                                     const double* __restrict__ face, double* __restrict__ bvec,
                                                     double* __restrict__ val) {
+  wait_prior_grid();
   const int64_t strides[3] = {1, (int64_t)g.nx, (int64_t)g.nx * g.ny};
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.N; c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = c / g.nx;
@@ -442,6 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(Geom g, const int32_t* __re
 __global__ void __launch_bounds__(kThreads) k_sqnorm(int64_t n, const double* __restrict__ u,
                                                     const double* __restrict__ v, double* partials,
                                                     unsigned* counter, double* out) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -461,6 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_sqnorm(int64_t n, const double* __
 }
 
 __global__ void k_copy64(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  wait_prior_grid();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
 }
@@ -470,7 +475,7 @@ constexpr int kNormBlocks = 2 * 152;
 // ||u|| or ||u - v|| on the model's stream (synchronises)
 int model_norm(bo_model* M, int64_t n, const double* u, const double* v, double* out) {
   cudaStream_t s = M->ctx->stream;
-  (k_sqnorm<<<kNormBlocks, kThreads, 0, s>>>(n, u, v, M->partials, M->counter, M->red), note_launch());
+  (launch_pdl(k_sqnorm, kNormBlocks, kThreads, 0, s, n, u, v, M->partials, M->counter, M->red), note_launch());
   if (cudaMemcpyAsync(M->h_red, M->red, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return BO_ERR_CUDA;
@@ -484,13 +489,13 @@ int model_assemble(bo_model* M, const double* x, const double* xn, double dt) {
   const bo_grid& gr = M->grid;
   cudaMemsetAsync(M->err, 0, sizeof(int), s);
   const int gc = grid_for(g.N);
-  (k_cell_props<<<gc, kThreads, 0, s>>>(g, M->fluid, gr.dx, gr.dy, gr.dz, M->phi0, M->depth, x, xn, dt,
+  (launch_pdl(k_cell_props, gc, kThreads, 0, s, g, M->fluid, gr.dx, gr.dy, gr.dz, M->phi0, M->depth, x, xn, dt,
                                         M->cperf_ptr, M->cperf, M->props, M->racc, M->dacc, M->err),
    note_launch());
-  (k_faces<<<gc, kThreads, 0, s>>>(g, 0, gr.dy * gr.dz, gr.dx, M->kx, M->depth, x, M->props, M->face), note_launch());
-  (k_faces<<<gc, kThreads, 0, s>>>(g, 1, gr.dx * gr.dz, gr.dy, M->ky, M->depth, x, M->props, M->face), note_launch());
-  (k_faces<<<gc, kThreads, 0, s>>>(g, 2, gr.dx * gr.dy, gr.dz, M->kz, M->depth, x, M->props, M->face), note_launch());
-  (k_gather<<<gc, kThreads, 0, s>>>(g, M->rowptr, M->racc, M->dacc, M->face, M->b, M->val), note_launch());
+  (launch_pdl(k_faces, gc, kThreads, 0, s, g, 0, gr.dy * gr.dz, gr.dx, M->kx, M->depth, x, M->props, M->face), note_launch());
+  (launch_pdl(k_faces, gc, kThreads, 0, s, g, 1, gr.dx * gr.dz, gr.dy, M->ky, M->depth, x, M->props, M->face), note_launch());
+  (launch_pdl(k_faces, gc, kThreads, 0, s, g, 2, gr.dx * gr.dy, gr.dz, M->kz, M->depth, x, M->props, M->face), note_launch());
+  (launch_pdl(k_gather, gc, kThreads, 0, s, g, M->rowptr, M->racc, M->dacc, M->face, M->b, M->val), note_launch());
   int h = 0;
   if (cudaMemcpyAsync(&h, M->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -652,8 +657,8 @@ int bo_model_assemble(bo_model* M, const double* x, const double* xn, double dt,
   if (rc != BO_OK) return rc;
   cudaStream_t s = M->ctx->stream;
   const int64_t n = 3 * M->N;
-  if (b) (k_copy64<<<grid_for(n), kThreads, 0, s>>>(n, M->b, b), note_launch());
-  if (val) (k_copy64<<<grid_for(9 * M->nnzb), kThreads, 0, s>>>(9 * M->nnzb, M->val, val), note_launch());
+  if (b) (launch_pdl(k_copy64, grid_for(n), kThreads, 0, s, n, M->b, b), note_launch());
+  if (val) (launch_pdl(k_copy64, grid_for(9 * M->nnzb), kThreads, 0, s, 9 * M->nnzb, M->val, val), note_launch());
   if (bnorm) {
     rc = model_norm(M, n, M->b, nullptr, bnorm);
     if (rc != BO_OK) return rc;
@@ -708,7 +713,7 @@ int bo_newton_solve(bo_model* M, bo_prec* P, double* x, const double* xn, double
     rc = bo_solve(P, M->b, M->dx, &so, &si);
     if (rc != BO_OK && rc != BO_ERR_NOT_CONVERGED) return finish(rc);
     // r = b - A dx with this step's A; x^{l+1} = x^l + dx
-    (k_copy64<<<grid_for(n), kThreads, 0, s>>>(n, M->b, M->r), note_launch());
+    (launch_pdl(k_copy64, grid_for(n), kThreads, 0, s, n, M->b, M->r), note_launch());
     launch_spmv_nat(A, -1.0, M->dx, 1.0, M->r, BO_PREC_FP64);
     launch_newton_update(x, M->dx, n, s);
     double nr = 0.0;

@@ -37,6 +37,7 @@ namespace {
 // 2x2 blocks -> 3x3 blocks with a unit (2,2) entry on the diagonal block
 __global__ void k_ow_pad_matrix(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ v4, double* __restrict__ v9) {
+  wait_prior_grid();
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
     for (int32_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
       const double* a = v4 + 4 * (size_t)e;
@@ -56,6 +57,7 @@ __global__ void k_ow_pad_matrix(int64_t N, const int32_t* __restrict__ rowptr, c
 
 // (p, Sw) per cell -> (p, Sw, 0)
 __global__ void k_ow_pad_vec(int64_t N, const double* __restrict__ v2, double* __restrict__ v3) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
     v3[3 * c] = v2[2 * c];
     v3[3 * c + 1] = v2[2 * c + 1];
@@ -64,6 +66,7 @@ __global__ void k_ow_pad_vec(int64_t N, const double* __restrict__ v2, double* _
 }
 
 __global__ void k_ow_unpad_vec(int64_t N, const double* __restrict__ v3, double* __restrict__ v2) {
+  wait_prior_grid();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
     v2[2 * c] = v3[3 * c];
     v2[2 * c + 1] = v3[3 * c + 1];
@@ -94,7 +97,7 @@ int ow_pad(bo_ow* w, const double* val, int mem) {
     if (e != cudaSuccess) return ow_status(e);
     v4 = w->val4;
   }
-  (k_ow_pad_matrix<<<grid_for(w->N), kThreads, 0, s>>>(w->N, w->rowptr, w->col, v4, w->val9), note_launch());
+  (launch_pdl(k_ow_pad_matrix, grid_for(w->N), kThreads, 0, s, w->N, w->rowptr, w->col, v4, w->val9), note_launch());
   return BO_OK;
 }
 
@@ -167,10 +170,10 @@ int bo_ow_spmv(bo_ow* w, double alpha, const double* x, double beta, double* y) 
   if (cudaSetDevice(w->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   cudaStream_t s = w->ctx->stream;
   const int gN = grid_for(w->N);
-  (k_ow_pad_vec<<<gN, kThreads, 0, s>>>(w->N, x, w->x3), note_launch());
-  if (beta != 0.0) (k_ow_pad_vec<<<gN, kThreads, 0, s>>>(w->N, y, w->b3), note_launch());
+  (launch_pdl(k_ow_pad_vec, gN, kThreads, 0, s, w->N, x, w->x3), note_launch());
+  if (beta != 0.0) (launch_pdl(k_ow_pad_vec, gN, kThreads, 0, s, w->N, y, w->b3), note_launch());
   launch_spmv_nat(w->m, alpha, w->x3, beta, w->b3, BO_PREC_FP64);
-  (k_ow_unpad_vec<<<gN, kThreads, 0, s>>>(w->N, w->b3, y), note_launch());
+  (launch_pdl(k_ow_unpad_vec, gN, kThreads, 0, s, w->N, w->b3, y), note_launch());
   return ow_status(cudaStreamSynchronize(s));
 }
 
@@ -187,10 +190,10 @@ static int ow_solve(bo_ow* w, bo_prec* P, const double* b, double* x, const bo_s
   if (cudaSetDevice(w->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   cudaStream_t s = P->stream;
   const int gN = grid_for(w->N);
-  (k_ow_pad_vec<<<gN, kThreads, 0, s>>>(w->N, b, w->b3), note_launch());
-  if (!o.x0_is_zero) (k_ow_pad_vec<<<gN, kThreads, 0, s>>>(w->N, x, w->x3), note_launch());
+  (launch_pdl(k_ow_pad_vec, gN, kThreads, 0, s, w->N, b, w->b3), note_launch());
+  if (!o.x0_is_zero) (launch_pdl(k_ow_pad_vec, gN, kThreads, 0, s, w->N, x, w->x3), note_launch());
   const int rc = solver == 0 ? fgmres(P, w->b3, w->x3, &o, info) : bicgstab(P, w->b3, w->x3, &o, info);
-  (k_ow_unpad_vec<<<gN, kThreads, 0, s>>>(w->N, w->x3, x), note_launch());
+  (launch_pdl(k_ow_unpad_vec, gN, kThreads, 0, s, w->N, w->x3, x), note_launch());
   const int rs = ow_status(cudaStreamSynchronize(s));
   return rc != BO_OK ? rc : rs;
 }

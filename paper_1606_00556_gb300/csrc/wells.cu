@@ -107,6 +107,7 @@ __device__ void perf_dots(int W, const int32_t* wstart, const int32_t* perf_t, i
 __global__ void k_wl_coeffs(int W, const int32_t* wstart, const int32_t* perf_t, int64_t N, const double* awp,
                             const float* z, int64_t n, const double* Cinv, const double* aww, int coupling,
                             double* t, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   __shared__ double s[kMaxWells];
   perf_dots<float>(W, wstart, perf_t, N, awp, z, n, s);
@@ -127,6 +128,7 @@ __global__ void k_wl_coeffs(int W, const int32_t* wstart, const int32_t* perf_t,
 __global__ void __launch_bounds__(kThreads) k_wl_woodbury(int64_t n, int W, const float* __restrict__ MU,
                                                           const double* __restrict__ t, float* __restrict__ z,
                                                           const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   __shared__ df ts[kMaxWells];
   for (int v = threadIdx.x; v < W; v += blockDim.x) ts[v] = df_from(t[v]);
@@ -144,6 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_wl_woodbury(int64_t n, int W, cons
 // (split planes, low plane at w + np).  One block.
 __global__ void k_wl_product(int P, int W, const int32_t* perf_t, const int32_t* perf_well, int64_t N,
                              const double* apw, const double* t, float* w, int64_t np, const DevState* st) {
+  wait_prior_grid();
   if (st->done) return;
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     const double tv = t[W + perf_well[e]];
@@ -162,6 +165,7 @@ __global__ void k_wl_product(int P, int W, const int32_t* perf_t, const int32_t*
 // perforated rows (x, r FP64 internal).  One block.
 __global__ void k_wl_residual(int W, const int32_t* wstart, const int32_t* perf_t, int64_t N, const double* awp,
                               const double* apw, const double* aww, const double* x, double* r) {
+  wait_prior_grid();
   __shared__ double s[kMaxWells];
   perf_dots<double>(W, wstart, perf_t, N, awp, x, 0, s);
   __syncthreads();
@@ -178,6 +182,7 @@ __global__ void k_wl_residual(int W, const int32_t* wstart, const int32_t* perf_
 // ||r|| -> st->beta (the solver's reduction pattern; counter[1] is free
 // once the true-residual kernel before it has finished)
 __global__ void k_wl_beta(int64_t n, const double* __restrict__ r, double* partials, DevState* st) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -197,6 +202,7 @@ __global__ void k_wl_beta(int64_t n, const double* __restrict__ r, double* parti
 
 // out[slot] = sum of squares of v[0..n), deterministic two-phase reduction
 __global__ void k_wl_sumsq(int64_t n, const double* __restrict__ v, double* partials) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -205,6 +211,7 @@ __global__ void k_wl_sumsq(int64_t n, const double* __restrict__ v, double* part
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 __global__ void k_wl_sumsq_finish(int np, const double* partials, double* out) {
+  wait_prior_grid();
   __shared__ double sh[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
@@ -215,6 +222,7 @@ __global__ void k_wl_sumsq_finish(int np, const double* partials, double* out) {
 // g = b - A_pw A_ww^{-1} b_w on the perforated rows of a copy of b (natural order)
 __global__ void k_wl_rhs(int P, int64_t N, const int32_t* perf_cell, const int32_t* perf_well, const double* apw,
                          const double* aww, const double* b, double* g) {
+  wait_prior_grid();
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     const int v = perf_well[e];
     const double tv = b[3 * N + v] / aww[v];
@@ -227,6 +235,7 @@ __global__ void k_wl_rhs(int P, int64_t N, const int32_t* perf_cell, const int32
 // x_w = A_ww^{-1} (b_w - A_wp x) (natural order; x_w at x + 3N)
 __global__ void k_wl_recover(int W, const int32_t* wstart, const int32_t* perf_cell, int64_t N, const double* awp,
                              const double* aww, const double* b, double* x) {
+  wait_prior_grid();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int v = warp; v < W; v += nw) {
     double acc = 0.0;
@@ -245,6 +254,7 @@ __global__ void k_wl_recover(int W, const int32_t* wstart, const int32_t* perf_c
 __global__ void k_wl_border_product(int W, const int32_t* wstart, const int32_t* perf_cell, int64_t N,
                                     const double* apw, const double* awp, const double* aww, double alpha,
                                     const double* x, double beta, double* y) {
+  wait_prior_grid();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int v = warp; v < W; v += nw) {
     double acc = 0.0;
@@ -269,6 +279,7 @@ __global__ void k_wl_border_product(int W, const int32_t* wstart, const int32_t*
 // order; the rest of u is zero)
 __global__ void k_wl_unit(int v, const int32_t* wstart, const int32_t* perf_t, int64_t N, const double* apw,
                           const double* aww, double* u) {
+  wait_prior_grid();
   for (int e = wstart[v] + threadIdx.x; e < wstart[v + 1]; e += blockDim.x) {
     const int64_t t0 = perf_t[e];
 #pragma unroll
@@ -279,6 +290,7 @@ __global__ void k_wl_unit(int v, const int32_t* wstart, const int32_t* perf_t, i
 // C = I - A_wp (M U): block u forms column u, one warp per row v
 __global__ void k_wl_cmat(int W, const int32_t* wstart, const int32_t* perf_t, int64_t N, const double* awp,
                           const float* MU, double* C) {
+  wait_prior_grid();
   const int u = blockIdx.x;
   const float* mu = MU + (size_t)u * 3 * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -363,11 +375,11 @@ void wells_after_prec(bo_prec* P, float* z, int64_t n) {
   bo_wells* wl = P->wl;
   cudaStream_t s = P->stream;
   const int64_t N = P->mat->g.N;
-  (k_wl_coeffs<<<1, kThreads, 0, s>>>(wl->W, wl->wstart, wl->perf_t, N, wl->awp, z, n, wl->Cinv, wl->aww,
+  (launch_pdl(k_wl_coeffs, 1, kThreads, 0, s, wl->W, wl->wstart, wl->perf_t, N, wl->awp, z, n, wl->Cinv, wl->aww,
                                       wl->coupling, wl->t, P->st),
    note_launch());
   if (wl->coupling)
-    (k_wl_woodbury<<<occ_grid((const void*)k_wl_woodbury, n), kThreads, 0, s>>>(n, wl->W, wl->MU, wl->t, z, P->st),
+    (launch_pdl(k_wl_woodbury, occ_grid((const void*)k_wl_woodbury, n), kThreads, 0, s, n, wl->W, wl->MU, wl->t, z, P->st),
      note_launch());
 }
 
@@ -375,7 +387,7 @@ void wells_after_prec(bo_prec* P, float* z, int64_t n) {
 void wells_after_product(bo_prec* P, float* w, int64_t np) {
   bo_wells* wl = P->wl;
   if (wl->P == 0) return;
-  (k_wl_product<<<1, kThreads, 0, P->stream>>>(wl->P, wl->W, wl->perf_t, wl->perf_well, P->mat->g.N, wl->apw, wl->t,
+  (launch_pdl(k_wl_product, 1, kThreads, 0, P->stream, wl->P, wl->W, wl->perf_t, wl->perf_well, P->mat->g.N, wl->apw, wl->t,
                                                w, np, P->st),
    note_launch());
 }
@@ -386,9 +398,9 @@ void wells_after_residual(bo_prec* P) {
   if (wl->P == 0) return;
   cudaStream_t s = P->stream;
   const int64_t N = P->mat->g.N;
-  (k_wl_residual<<<1, kThreads, 0, s>>>(wl->W, wl->wstart, wl->perf_t, N, wl->awp, wl->apw, wl->aww, P->xi, P->rk),
+  (launch_pdl(k_wl_residual, 1, kThreads, 0, s, wl->W, wl->wstart, wl->perf_t, N, wl->awp, wl->apw, wl->aww, P->xi, P->rk),
    note_launch());
-  (k_wl_beta<<<kRed, kThreads, 0, s>>>(3 * N, P->rk, P->partials, P->st), note_launch());
+  (launch_pdl(k_wl_beta, kRed, kThreads, 0, s, 3 * N, P->rk, P->partials, P->st), note_launch());
 }
 
 }  // namespace bo
@@ -405,13 +417,13 @@ int wells_prepare(bo_wells* wl, bo_prec* P) {
   double* z = P->xi;
   for (int v = 0; v < W; ++v) {
     cudaMemsetAsync(u, 0, n * sizeof(double), s);
-    (k_wl_unit<<<1, kThreads, 0, s>>>(v, wl->wstart, wl->perf_t, g.N, wl->apw, wl->aww, u), note_launch());
+    (launch_pdl(k_wl_unit, 1, kThreads, 0, s, v, wl->wstart, wl->perf_t, g.N, wl->apw, wl->aww, u), note_launch());
     cudaMemsetAsync(&P->st->done, 0, sizeof(int), s);
     launch_cpr(P, u, z, BO_STAGE_CPR, P->st);
     launch_to_f32(z, wl->MU + (size_t)v * n, (size_t)n, s);
   }
   double* C = wl->rfull;  // scratch of W x W doubles (rfull holds 3N + W >= W^2)
-  (k_wl_cmat<<<W, kThreads, 0, s>>>(W, wl->wstart, wl->perf_t, g.N, wl->awp, wl->MU, C), note_launch());
+  (launch_pdl(k_wl_cmat, W, kThreads, 0, s, W, wl->wstart, wl->perf_t, g.N, wl->awp, wl->MU, C), note_launch());
   std::vector<double> hc((size_t)W * W), hinv;
   int err = 0;
   cudaError_t e = cudaMemcpyAsync(hc.data(), C, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -435,8 +447,8 @@ int wells_prepare(bo_wells* wl, bo_prec* P) {
 
 // squared norm of v[0..n) into wl->norms[slot]
 void sumsq(bo_wells* wl, const double* v, int64_t n, int slot, cudaStream_t s) {
-  (k_wl_sumsq<<<kRed, kThreads, 0, s>>>(n, v, wl->partials), note_launch());
-  (k_wl_sumsq_finish<<<1, kThreads, 0, s>>>(kRed, wl->partials, wl->norms + slot), note_launch());
+  (launch_pdl(k_wl_sumsq, kRed, kThreads, 0, s, n, v, wl->partials), note_launch());
+  (launch_pdl(k_wl_sumsq_finish, 1, kThreads, 0, s, kRed, wl->partials, wl->norms + slot), note_launch());
 }
 
 }  // namespace
@@ -552,7 +564,7 @@ int bo_wells_spmv(bo_wells* w, double alpha, const double* x, double beta, doubl
   bo_mat* m = w->mat;
   if (cudaSetDevice(m->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   launch_spmv_nat(m, alpha, x, beta, y, BO_PREC_FP64);
-  (k_wl_border_product<<<1, kThreads, 0, m->ctx->stream>>>(w->W, w->wstart, w->perf_cell, m->g.N, w->apw, w->awp,
+  (launch_pdl(k_wl_border_product, 1, kThreads, 0, m->ctx->stream, w->W, w->wstart, w->perf_cell, m->g.N, w->apw, w->awp,
                                                             w->aww, alpha, x, beta, y),
    note_launch());
   return status_of(cudaStreamSynchronize(m->ctx->stream));
@@ -581,7 +593,7 @@ int bo_solve_bordered(bo_prec* P, bo_wells* w, const double* b, double* x, const
   if (!o.x0_is_zero) {
     cudaMemcpyAsync(w->rfull, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, s);
     launch_spmv_nat(m, -1.0, x, 1.0, w->rfull, BO_PREC_FP64);
-    (k_wl_border_product<<<1, kThreads, 0, s>>>(w->W, w->wstart, w->perf_cell, N, w->apw, w->awp, w->aww, -1.0, x,
+    (launch_pdl(k_wl_border_product, 1, kThreads, 0, s, w->W, w->wstart, w->perf_cell, N, w->apw, w->awp, w->aww, -1.0, x,
                                                 1.0, w->rfull),
      note_launch());
     rb = w->rfull;
@@ -589,7 +601,7 @@ int bo_solve_bordered(bo_prec* P, bo_wells* w, const double* b, double* x, const
   }
   cudaMemcpyAsync(w->g, rb, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (w->P > 0)
-    (k_wl_rhs<<<1, kThreads, 0, s>>>(w->P, N, w->perf_cell, w->perf_well, w->apw, w->aww, rb, w->g), note_launch());
+    (launch_pdl(k_wl_rhs, 1, kThreads, 0, s, w->P, N, w->perf_cell, w->perf_well, w->apw, w->aww, rb, w->g), note_launch());
   sumsq(w, b, nf, 0, s);
   sumsq(w, w->g, n, 1, s);
   cudaError_t e = cudaMemcpyAsync(w->h_norms, w->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -623,7 +635,7 @@ int bo_solve_bordered(bo_prec* P, bo_wells* w, const double* b, double* x, const
     inf.est_rel_res *= gnorm / bnorm;
     for (int i = 0; i < P->nhist; ++i) P->hist[i] *= gnorm / bnorm;
   }
-  (k_wl_recover<<<1, kThreads, 0, s>>>(w->W, w->wstart, w->perf_cell, N, w->awp, w->aww, rb, d), note_launch());
+  (launch_pdl(k_wl_recover, 1, kThreads, 0, s, w->W, w->wstart, w->perf_cell, N, w->awp, w->aww, rb, d), note_launch());
   if (!o.x0_is_zero) launch_newton_update(x, w->dx, nf, s);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return status_of(e);
