@@ -482,6 +482,7 @@ struct bo_prec {
   double* hostio;          // device staging of host b / x
   bo::DevState* st;        // device state
   bo::DevState* h_st;      // pinned host mirror (three column slots, one phase slot)
+  bo::DevState* h_st_dev;  // its device address (written by a kernel), or NULL
   cudaEvent_t ev[4];
   cudaEvent_t prof_ev[2 * 512];
   bool prof_ready;
