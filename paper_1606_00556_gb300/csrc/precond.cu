@@ -566,9 +566,11 @@ __global__ void __launch_bounds__(1024) k_gj_inverse(int n, const double* __rest
         a[piv * n + j] = t;
       }
     __syncthreads();
-    const double pv = a[k * n + k];
+    // the pivot row scaled by one reciprocal (an FP64 division is a long
+    // sequence on GB300's narrow FP64 pipe; one per row instead of n)
+    const double rp = 1.0 / a[k * n + k];
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) / pv;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * rp;
     __syncthreads();
     // eliminate column k from every other row; factors first, so that the
     // row updates below read unmodified values
