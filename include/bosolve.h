@@ -65,7 +65,7 @@ enum { BO_PREC_FP64 = 0, BO_PREC_FP32 = 1, BO_PREC_BF16 = 2 };
 /* How bo_solve issues the kernels of each Arnoldi column: one launch per
  * kernel on the stream, or one CUDA-graph launch per column (captured on
  * first use and replayed; no per-column SpMV timing then). */
-enum { BO_LAUNCH_STREAM = 0, BO_LAUNCH_GRAPH = 1 };
+enum { BO_LAUNCH_STREAM = 0, BO_LAUNCH_GRAPH = 1, BO_LAUNCH_BATCH_GRAPH = 2 };
 /* stages of the preconditioner that bo_prec_apply can run on their own */
 enum {
   BO_STAGE_CPR = 0,           /* z = CPR(D_QI^{-1} r): the preconditioner FGMRES uses */
@@ -207,10 +207,16 @@ int bo_prec_amg_levels(bo_prec* P, int32_t* dims, int cap);
 /* Synchronises P's stream and frees its workspace; drops P's reference on
  * its matrix.  BO_ERR_ARG for NULL. */
 int bo_prec_destroy(bo_prec* P);
-/* Launch mode of P's solves (BO_LAUNCH_STREAM default, BO_LAUNCH_GRAPH).
- * Graph mode captures the kernels of each Arnoldi column once per restart
- * length and replays them; the graphs are rebuilt after a change of restart
- * length or of the learned coarse space.  No counterpart in the paper: a
+/* Launch mode of P's solves (BO_LAUNCH_STREAM default, BO_LAUNCH_GRAPH,
+ * BO_LAUNCH_BATCH_GRAPH).  Graph mode captures the kernels of each Arnoldi
+ * column once per restart length and replays them; the graphs are rebuilt
+ * after a change of restart length or of the learned coarse space.  Batch
+ * graph mode applies to bo_solve_batched when every system of the batch has
+ * it (and no rate-controlled wells): the systems run their FGMRES cycles in
+ * lockstep, Arnoldi column j of all of them captured as one CUDA graph (one
+ * branch per pool stream) and launched once per column for the whole batch;
+ * the two most recent batches' graphs are kept for reuse.  A single solve
+ * in that mode runs as in stream mode.  No counterpart in the paper: a
  * launch-overhead measure for batches of small systems. */
 int bo_prec_set_launch_mode(bo_prec* P, int mode);
 
@@ -231,13 +237,13 @@ typedef struct {
   int32_t streams;       /* chosen stream-pool width */
   double best_ms;        /* wall time of the chosen configuration's batch */
   int32_t from_cache;    /* 1: taken from the cache without timing */
-  double trial_ms[6];    /* stream x {4, 8, 16}, then graph x {4, 8, 16} */
+  double trial_ms[9];    /* stream x {4, 8, 16}, graph x {4, 8, 16}, batch graph x {4, 8, 16} */
 } bo_tune_result;
 
 /* Autotuner for bo_solve_batched (no counterpart in the paper).  Times the
  * caller's batch (same arguments as bo_solve_batched; x is overwritten,
- * solves start from zero) under every launch mode and stream-pool width of
- * 4, 8 and 16, two passes each (the first untimed), applies the fastest to
+ * solves start from zero) under every launch mode (stream, graph, batch
+ * graph) and stream-pool width of 4, 8 and 16, two passes each (the first untimed), applies the fastest to
  * all P and to the pool, and records it in the JSON file cache_path (NULL:
  * no cache) under a key of the batch's shape (count, total and largest cell
  * counts as powers of two, FP32 preconditioners, restart).  With an entry

@@ -42,6 +42,7 @@ BO_DECOUPLE_QI = 0
 BO_DECOUPLE_ABF = 1
 BO_LAUNCH_STREAM = 0
 BO_LAUNCH_GRAPH = 1
+BO_LAUNCH_BATCH_GRAPH = 2
 
 # every symbol include/bosolve.h declares
 EXPORTS = (
@@ -101,7 +102,7 @@ class bo_solve_opts(ctypes.Structure):
 
 class bo_tune_result(ctypes.Structure):
     _fields_ = [("launch_mode", ctypes.c_int32), ("streams", ctypes.c_int32), ("best_ms", ctypes.c_double),
-                ("from_cache", ctypes.c_int32), ("trial_ms", ctypes.c_double * 6)]
+                ("from_cache", ctypes.c_int32), ("trial_ms", ctypes.c_double * 9)]
 
 
 class bo_solve_info(ctypes.Structure):
@@ -709,7 +710,8 @@ class Preconditioner:
         return d
 
     def set_launch_mode(self, mode):
-        """BO_LAUNCH_STREAM or BO_LAUNCH_GRAPH (per-column CUDA graphs)."""
+        """BO_LAUNCH_STREAM, BO_LAUNCH_GRAPH (per-column CUDA graphs) or BO_LAUNCH_BATCH_GRAPH
+        (one graph per column for a whole bo_solve_batched batch, in lockstep)."""
         _check(lib().bo_prec_set_launch_mode(self.h, int(mode)), "bo_prec_set_launch_mode")
 
     def set_coarse_space(self, dp, tile=(16, 16, 8)):

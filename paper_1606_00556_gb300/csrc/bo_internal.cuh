@@ -501,6 +501,7 @@ struct bo_prec {
   int graph_m = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t col_exec[64] = {};
+  unsigned long long graph_gen = 0;  // bumped whenever captured graphs go stale
   long long col_nodes[64] = {};
   double* hist;            // host residual history of the last solve
   int nhist;

@@ -595,7 +595,7 @@ int bo_set_conv_engine(int engine) {
 }
 
 int bo_prec_set_launch_mode(bo_prec* P, int mode) {
-  if (!P || (mode != BO_LAUNCH_STREAM && mode != BO_LAUNCH_GRAPH)) return BO_ERR_ARG;
+  if (!P || (mode != BO_LAUNCH_STREAM && mode != BO_LAUNCH_GRAPH && mode != BO_LAUNCH_BATCH_GRAPH)) return BO_ERR_ARG;
   P->launch_mode = mode;
   return BO_OK;
 }

@@ -51,6 +51,7 @@
 #include <algorithm>
 #include <cstring>
 #include <vector>
+#include <mutex>
 
 #include "bo_internal.cuh"
 
@@ -721,7 +722,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_xupdate(int64_t n, double* __re
 
 }  // namespace
 
+// process-wide source of graph generations: a preconditioner created at the
+// address of a freed one never matches graphs recorded for the old one
+std::atomic<unsigned long long> g_graph_gen{0};
+
 void graphs_reset(bo_prec* P) {
+  P->graph_gen = ++g_graph_gen;  // batch graphs recorded with this preconditioner are stale
   for (int j = 0; j < 64; ++j)
     if (P->col_exec[j]) {
       cudaGraphExecDestroy(P->col_exec[j]);
@@ -1461,6 +1467,170 @@ int bicgstab(bo_prec* P, const double* b_in, double* x_in, const bo_solve_opts* 
   return status;
 }
 
+namespace {
+
+// ---- lockstep batched solve (BO_LAUNCH_BATCH_GRAPH)
+// Every realisation of the batch runs its FGMRES cycle in step with the
+// others: Arnoldi column j of all of them is one CUDA graph (captured once,
+// one branch per stream of the capture pool, the realisations spread over
+// the branches), so one graph launch advances the whole batch by a column
+// and the host reads every realisation's published state once per column.
+// A realisation whose cycle has stopped has its column kernels return at
+// once (its device state's done flag).  The cycle's start and end run on
+// each realisation's own stream, as in the stream-pool form.
+struct BatchGraphs {
+  std::vector<bo_prec*> P;
+  std::vector<unsigned long long> gen;
+  int m = 0, width = 0;
+  std::vector<cudaGraphExec_t> col;
+  std::vector<long long> nodes;
+  void release() {
+    for (auto& e : col)
+      if (e) cudaGraphExecDestroy(e);
+    col.clear();
+  }
+};
+
+constexpr int kBranchesPerStream = 4;
+std::mutex g_bg_mu;
+std::vector<BatchGraphs> g_bg;  // the two most recent batches' graphs
+cudaStream_t g_bg_drv = nullptr;
+std::vector<cudaStream_t> g_bg_cap;
+std::vector<cudaEvent_t> g_bg_ev;  // fork, one join per capture stream, three column events
+
+bool batch_streams(int width) {
+  if (!g_bg_drv && cudaStreamCreateWithFlags(&g_bg_drv, cudaStreamNonBlocking) != cudaSuccess) return false;
+  while ((int)g_bg_cap.size() < width) {
+    cudaStream_t c;
+    if (cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) return false;
+    g_bg_cap.push_back(c);
+  }
+  while ((int)g_bg_ev.size() < kBranchesPerStream * kMaxPoolStreams + 4) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    g_bg_ev.push_back(e);
+  }
+  return true;
+}
+
+BatchGraphs& batch_graphs(const std::vector<Job*>& act, int m, int width) {
+  std::vector<bo_prec*> P;
+  std::vector<unsigned long long> gen;
+  for (Job* jb : act) {
+    P.push_back(jb->P);
+    gen.push_back(jb->P->graph_gen);
+  }
+  for (auto& c : g_bg)
+    if (c.P == P && c.gen == gen && c.m == m && c.width == width) return c;
+  if (g_bg.size() >= 2) {
+    g_bg.front().release();
+    g_bg.erase(g_bg.begin());
+  }
+  g_bg.emplace_back();
+  BatchGraphs& c = g_bg.back();
+  c.P = P;
+  c.gen = gen;
+  c.m = m;
+  c.width = width;
+  c.col.assign(m, nullptr);
+  c.nodes.assign(m, 0);
+  return c;
+}
+
+// capture column j of every realisation of `act` into one graph
+bool capture_batch_column(BatchGraphs& c, const std::vector<Job*>& act, int j) {
+  const int W = std::min(c.width, (int)act.size());
+  cudaStream_t drv = g_bg_drv;
+  const long long l0 = g_launches.load();
+  if (cudaStreamBeginCapture(drv, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  cudaEvent_t fork = g_bg_ev[0];
+  cudaEventRecord(fork, drv);
+  for (int w = 0; w < W; ++w) cudaStreamWaitEvent(g_bg_cap[w], fork, 0);
+  for (size_t r = 0; r < act.size(); ++r) {
+    Job* jb = act[r];
+    cudaStream_t saved = jb->P->stream;
+    jb->P->stream = g_bg_cap[r % W];
+    jb->enqueue_column_kernels(j, false);
+    publish_state(jb->P, jb->P->st, j % kRing, jb->P->stream);
+    jb->P->stream = saved;
+  }
+  for (int w = 0; w < W; ++w) {
+    cudaEventRecord(g_bg_ev[1 + w], g_bg_cap[w]);
+    cudaStreamWaitEvent(drv, g_bg_ev[1 + w], 0);
+  }
+  cudaGraph_t gr = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(drv, &gr);
+  const long long nodes = g_launches.load() - l0;
+  g_launches.fetch_sub(nodes);  // captured, not run: counted at each replay instead
+  if (e != cudaSuccess || !gr) return false;
+  const cudaError_t ei = cudaGraphInstantiate(&c.col[j], gr, 0);
+  cudaGraphDestroy(gr);
+  if (ei != cudaSuccess) {
+    c.col[j] = nullptr;
+    return false;
+  }
+  c.nodes[j] = nodes;
+  return true;
+}
+
+// returns BO_OK or BO_ERR_CUDA; per-realisation results are in the jobs
+int fgmres_lockstep(std::vector<Job>& jobs) {
+  // branches of a column graph: four per pool stream of the tuned width
+  const int width = kBranchesPerStream * std::min(kMaxPoolStreams, std::max(1, g_pool_width.load()));
+  std::lock_guard<std::mutex> lk(g_bg_mu);
+  if (!batch_streams(width)) return BO_ERR_CUDA;
+  cudaStream_t drv = g_bg_drv;
+  for (auto& jb : jobs) jb.start();
+  for (auto& jb : jobs)
+    while (jb.phase == Job::kInitWait) jb.advance(true);
+  for (;;) {
+    std::vector<Job*> act;
+    for (auto& jb : jobs)
+      if (jb.phase == Job::kColumns) act.push_back(&jb);
+    if (act.empty()) break;
+    const int m = act[0]->o.restart;
+    int L = m;  // columns this cycle: no realisation passes its iteration limit
+    for (Job* jb : act) L = std::min(L, jb->o.maxit - jb->its);
+    // the drive stream after every realisation's cycle start
+    for (Job* jb : act) {
+      cudaEventRecord(jb->P->ev[kPhaseSlot], jb->P->stream);
+      cudaStreamWaitEvent(drv, jb->P->ev[kPhaseSlot], 0);
+    }
+    BatchGraphs& c = batch_graphs(act, m, width);
+    cudaEvent_t* colev = &g_bg_ev[1 + kBranchesPerStream * kMaxPoolStreams];
+    int launched = 0;
+    bool stop = false;
+    while (!stop && launched < L) {
+      const int j = launched;
+      if (!c.col[j] && !capture_batch_column(c, act, j)) return BO_ERR_CUDA;
+      if (cudaGraphLaunch(c.col[j], drv) != cudaSuccess) return BO_ERR_CUDA;
+      g_launches.fetch_add(c.nodes[j]);
+      cudaEventRecord(colev[j % 3], drv);
+      ++launched;
+      if (j >= 1) {  // one column of lag: the states of column j - 1
+        if (cudaEventSynchronize(colev[(j - 1) % 3]) != cudaSuccess) return BO_ERR_CUDA;
+        bool all = true;
+        for (Job* jb : act) all = all && jb->P->h_st[(j - 1) % kRing].done;
+        stop = all;
+      }
+    }
+    // every realisation's stream after the drive stream, then its cycle end
+    cudaEventRecord(colev[0], drv);
+    for (Job* jb : act) {
+      cudaStreamWaitEvent(jb->P->stream, colev[0], 0);
+      jb->j_enq = launched;
+      jb->end_cycle();
+    }
+    for (Job* jb : act)
+      while (jb->phase == Job::kCycleWait) jb->advance(true);
+  }
+  for (auto& jb : jobs)
+    while (jb.phase != Job::kDone) jb.advance(true);
+  return BO_OK;
+}
+
+}  // namespace
+
 int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double* const* x, const bo_solve_opts* o,
                    bo_solve_info* infos, const double* tols) {
   for (int r = 0; r < nreal; ++r) {
@@ -1476,7 +1646,13 @@ int fgmres_batched(bo_prec* const* P, int nreal, const double* const* b, double*
     if (tols) jobs[r].o.tol = tols[r];
     jobs[r].info = infos ? &infos[r] : nullptr;
   }
-  int remaining = nreal;
+  bool lockstep = true;
+  for (int r = 0; r < nreal; ++r) lockstep = lockstep && P[r]->launch_mode == BO_LAUNCH_BATCH_GRAPH && !P[r]->wl;
+  if (lockstep) {
+    const int rc = fgmres_lockstep(jobs);
+    if (rc != BO_OK) return rc;
+  }
+  int remaining = lockstep ? 0 : nreal;
   while (remaining > 0) {
     bool moved = false;
     remaining = 0;

@@ -1,6 +1,7 @@
 // Autotuner for batched solves (no counterpart in the paper): times the
 // launch configurations of bo_solve_batched on the caller's own batch
-// (per-kernel stream launches or per-column CUDA graphs, and the width of
+// (per-kernel stream launches, per-column CUDA graphs per realisation, or
+// one graph per column for the whole batch in lockstep, and the width of
 // the stream pool) and keeps the winner in a small JSON cache keyed by the
 // batch's shape, so that later runs apply it without timing.
 #include <algorithm>
@@ -96,16 +97,16 @@ int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, do
     }
     return BO_OK;
   }
-  const int modes[2] = {BO_LAUNCH_STREAM, BO_LAUNCH_GRAPH};
+  const int modes[3] = {BO_LAUNCH_STREAM, BO_LAUNCH_GRAPH, BO_LAUNCH_BATCH_GRAPH};
   const int widths[3] = {4, 8, 16};
   bo_solve_opts o = *opts;
   o.x0_is_zero = 1;
   o.profile = 0;
   double best = 1e300;
   int best_mode = BO_LAUNCH_STREAM, best_w = bo::kMaxPoolStreams;
-  double ms[6] = {0, 0, 0, 0, 0, 0};
+  double ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int k = 0;
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < 3; ++mi)
     for (int wi = 0; wi < 3; ++wi, ++k) {
       apply(P, nreal, modes[mi], widths[wi]);
       // one untimed pass (graph capture, first-touch), then the timed one
@@ -131,7 +132,7 @@ int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, do
     out->streams = best_w;
     out->best_ms = best;
     out->from_cache = 0;
-    for (int i = 0; i < 6; ++i) out->trial_ms[i] = ms[i];
+    for (int i = 0; i < 9; ++i) out->trial_ms[i] = ms[i];
   }
   return wrote ? BO_OK : BO_ERR_ARG;
 }

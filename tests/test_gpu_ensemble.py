@@ -92,6 +92,17 @@ def test_graph_launch_is_bitwise_equal_to_stream_launch(precision):
         assert rc == bo.BO_OK
         for x, (xr, it, _), info in zip(xs, ref, infos):
             assert info["iters"] == it and torch.equal(x, xr)
+    # lockstep: one graph per column for the whole batch; a system that has
+    # converged idles through the others' columns, its result unchanged
+    for P in precs:
+        P.set_launch_mode(bo.BO_LAUNCH_BATCH_GRAPH)
+    for rep in range(2):  # the second run replays the batch graphs
+        xs = [torch.zeros_like(b) for b in bs]
+        rc, infos = bo.bo_solve_batched(precs, bs, xs, tol=1e-8)
+        assert rc == bo.BO_OK
+        for x, (xr, it, hist), info, P in zip(xs, ref, infos, precs):
+            assert info["iters"] == it and torch.equal(x, xr)
+            np.testing.assert_array_equal(P.residual_history(), hist)
 
 
 def test_graph_launch_follows_restart_and_coarse_space_changes():
@@ -122,7 +133,8 @@ def test_autotuner_picks_and_caches(tmp_path):
     xs = [torch.zeros_like(b) for b in bs]
     path = str(tmp_path / "tune.json")
     r1 = bo.bo_autotune_batched(precs, bs, xs, cache_path=path)
-    assert not r1["from_cache"] and r1["launch_mode"] in (0, 1) and r1["streams"] in (4, 8, 16)
+    assert not r1["from_cache"] and r1["launch_mode"] in (0, 1, 2) and r1["streams"] in (4, 8, 16)
+    assert len(r1["trial_ms"]) == 9
     assert all(t > 0 for t in r1["trial_ms"]) and r1["best_ms"] == min(r1["trial_ms"])
     r2 = bo.bo_autotune_batched(precs, bs, xs, cache_path=path)
     assert r2["from_cache"] and (r2["launch_mode"], r2["streams"]) == (r1["launch_mode"], r1["streams"])
