@@ -1743,7 +1743,6 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   ta.inv = (const S*)P->coarse_inv;
   const size_t tb = tail_smem_bytes(ta);
   DevState* stw = const_cast<DevState*>(st);
-  void* cargs[] = {&ca, &stw};
 
   // per-kernel pre- and post-smoothing of the multi-block natural levels
   auto natural_down = [&]() {
@@ -1779,12 +1778,28 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     }
   };
 
+  // a cooperative launch that may also start as soon as the previous
+  // kernel's blocks have finished (programmatic dependent launch)
+  auto launch_coop = [&](auto kern, int grid) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kCoopThreads, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, ca, stw) == cudaSuccess;
+  };
+
   // down leg
   bool down_done = false;
   if (coop) {
     const int gd = occ_grid((const void*)k_amg_down<T, S>, g.Nh, kCoopThreads);
-    down_done =
-        cudaLaunchCooperativeKernel((const void*)k_amg_down<T, S>, gd, kCoopThreads, cargs, 0, s) == cudaSuccess;
+    down_done = launch_coop(k_amg_down<T, S>, gd);
     if (down_done) note_launch();
     else cudaGetLastError();
   }
@@ -1805,13 +1820,15 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     cfg.blockDim = dim3(kCoopThreads, 1, 1);
     cfg.dynamicSmemBytes = tb <= kTailSmemMax ? tb : 0;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     if (cudaLaunchKernelEx(&cfg, k_amg_coarse<T, S>, ca, ta, tb <= kTailSmemMax ? 1 : 0, st) == cudaSuccess) {
       note_launch();
     } else {
@@ -1827,7 +1844,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   // up leg
   if (down_done) {
     const int gu = occ_grid((const void*)k_amg_up<T, S>, g.Nh, kCoopThreads);
-    if (cudaLaunchCooperativeKernel((const void*)k_amg_up<T, S>, gu, kCoopThreads, cargs, 0, s) == cudaSuccess) {
+    if (launch_coop(k_amg_up<T, S>, gu)) {
       note_launch();
       return;
     }
