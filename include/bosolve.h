@@ -219,6 +219,15 @@ int bo_prec_destroy(bo_prec* P);
  * in that mode runs as in stream mode.  No counterpart in the paper: a
  * launch-overhead measure for batches of small systems. */
 int bo_prec_set_launch_mode(bo_prec* P, int mode);
+/* Tile parameters of the per-kernel form of P's AMG V-cycle, the form its
+ * CUDA-graph launch modes run (captured graphs cannot hold cooperative
+ * launches): `cells` level-0 Gauss-Seidel cells per thread (1, 2 or 4, all
+ * of a thread's loads issued before its stores) and `threads` per block
+ * (128, 256 or 512) for every per-kernel AMG launch.  The V-cycle is the
+ * same whatever the shape.  Captured graphs are rebuilt after a change.
+ * Default 1 and 256; BO_ERR_ARG for another value.  No counterpart in the
+ * paper: a tile choice the batch autotuner makes. */
+int bo_prec_set_amg_tile(bo_prec* P, int cells, int threads);
 
 /* New values for many systems at once: for each r, the values val[r]
  * (host or device per mem; NULL keeps the matrix's values) go into P[r]'s
@@ -238,12 +247,17 @@ typedef struct {
   double best_ms;        /* wall time of the chosen configuration's batch */
   int32_t from_cache;    /* 1: taken from the cache without timing */
   double trial_ms[9];    /* stream x {4, 8, 16}, graph x {4, 8, 16}, batch graph x {4, 8, 16} */
+  int32_t amg_cells;     /* chosen tile of the per-kernel AMG form (bo_prec_set_amg_tile) */
+  int32_t amg_threads;
+  double tile_ms[5];     /* graph forms only: (cells, threads) = (2, 256), (4, 256), (1, 128),
+                            (2, 128), (1, 512) with the chosen form and width; 0 otherwise */
 } bo_tune_result;
 
 /* Autotuner for bo_solve_batched (no counterpart in the paper).  Times the
  * caller's batch (same arguments as bo_solve_batched; x is overwritten,
  * solves start from zero) under every launch mode (stream, graph, batch
- * graph) and stream-pool width of 4, 8 and 16, two passes each (the first untimed), applies the fastest to
+ * graph) and stream-pool width of 4, 8 and 16, then, when a graph form wins,
+ * under five more tiles of the per-kernel AMG form with that form and width, two passes each (the first untimed), applies the fastest to
  * all P and to the pool, and records it in the JSON file cache_path (NULL:
  * no cache) under a key of the batch's shape (count, total and largest cell
  * counts as powers of two, FP32 preconditioners, restart).  With an entry

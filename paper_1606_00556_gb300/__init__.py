@@ -58,7 +58,7 @@ EXPORTS = (
     "bo_prec_set_coarse_space", "bo_learned_coarse_space", "bo_learned_guess",
     "bo_dp_create", "bo_dp_update_values", "bo_dp_fracture_matrix", "bo_dp_solve", "bo_dp_solve_batched",
     "bo_dp_destroy",
-    "bo_prec_set_launch_mode", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
+    "bo_prec_set_launch_mode", "bo_prec_set_amg_tile", "bo_set_batch_streams", "bo_autotune_batched", "bo_update_batched",
     "bo_set_conv_engine", "bo_tc_status", "bo_set_amg_cooperative", "bo_set_amg_barrier_spins", "bo_set_gs_fused",
     "bo_newton_opts_default", "bo_model_create", "bo_model_destroy", "bo_model_assemble", "bo_newton_solve",
     "bo_wells_create", "bo_wells_update_values", "bo_wells_set_coupling", "bo_wells_spmv", "bo_solve_bordered",
@@ -102,7 +102,8 @@ class bo_solve_opts(ctypes.Structure):
 
 class bo_tune_result(ctypes.Structure):
     _fields_ = [("launch_mode", ctypes.c_int32), ("streams", ctypes.c_int32), ("best_ms", ctypes.c_double),
-                ("from_cache", ctypes.c_int32), ("trial_ms", ctypes.c_double * 9)]
+                ("from_cache", ctypes.c_int32), ("trial_ms", ctypes.c_double * 9),
+                ("amg_cells", ctypes.c_int32), ("amg_threads", ctypes.c_int32), ("tile_ms", ctypes.c_double * 5)]
 
 
 class bo_solve_info(ctypes.Structure):
@@ -217,6 +218,7 @@ def lib():
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(bo_solve_opts),
                                           ctypes.POINTER(bo_solve_info)]
         L.bo_prec_set_launch_mode.argtypes = [_VP, _i]
+        L.bo_prec_set_amg_tile.argtypes = [_VP, _i, _i]
         L.bo_set_batch_streams.argtypes = [_i]
         L.bo_set_conv_engine.argtypes = [_i]
         L.bo_set_amg_cooperative.argtypes = [_i]
@@ -714,6 +716,11 @@ class Preconditioner:
         (one graph per column for a whole bo_solve_batched batch, in lockstep)."""
         _check(lib().bo_prec_set_launch_mode(self.h, int(mode)), "bo_prec_set_launch_mode")
 
+    def set_amg_tile(self, cells, threads):
+        """bo_prec_set_amg_tile: level-0 cells per thread and threads per block of the
+        per-kernel AMG form."""
+        _check(lib().bo_prec_set_amg_tile(self.h, int(cells), int(threads)), "bo_prec_set_amg_tile")
+
     def set_coarse_space(self, dp, tile=(16, 16, 8)):
         """Learned coarse space from a predicted pressure update dp (device
         float64, one value per cell, natural order); None removes it."""
@@ -865,7 +872,8 @@ def bo_autotune_batched(precs, bs, xs, cache_path=None, tol=1e-8, restart=30, ma
     path = cache_path.encode() if cache_path else None
     _check(lib().bo_autotune_batched(P, n, B, X, ctypes.byref(o), path, ctypes.byref(res)), "bo_autotune_batched")
     return {"launch_mode": res.launch_mode, "streams": res.streams, "best_ms": res.best_ms,
-            "from_cache": bool(res.from_cache), "trial_ms": list(res.trial_ms)}
+            "from_cache": bool(res.from_cache), "trial_ms": list(res.trial_ms),
+            "amg_cells": res.amg_cells, "amg_threads": res.amg_threads, "tile_ms": list(res.tile_ms)}
 
 
 def bo_kernel_launches() -> int:

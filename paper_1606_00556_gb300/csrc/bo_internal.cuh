@@ -502,6 +502,10 @@ struct bo_prec {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t col_exec[64] = {};
   unsigned long long graph_gen = 0;  // bumped whenever captured graphs go stale
+  // tile parameters of the per-kernel AMG form (the form inside captured
+  // graphs): threads per block and level-0 Gauss-Seidel cells per thread
+  int amg_threads = 256;
+  int amg_cells = 1;
   long long col_nodes[64] = {};
   double* hist;            // host residual history of the last solve
   int nhist;

@@ -600,6 +600,17 @@ int bo_prec_set_launch_mode(bo_prec* P, int mode) {
   return BO_OK;
 }
 
+int bo_prec_set_amg_tile(bo_prec* P, int cells, int threads) {
+  if (!P || (cells != 1 && cells != 2 && cells != 4) || (threads != 128 && threads != 256 && threads != 512))
+    return BO_ERR_ARG;
+  if (P->amg_cells != cells || P->amg_threads != threads) {
+    P->amg_cells = cells;
+    P->amg_threads = threads;
+    graphs_reset(P);  // captured columns hold the old launch shapes
+  }
+  return BO_OK;
+}
+
 int bo_newton_update(bo_ctx* ctx, double* state, const double* dx, int64_t n) {
   if (!ctx || !state || !dx || n < 0) return BO_ERR_ARG;
   launch_newton_update(state, dx, n, ctx->stream);

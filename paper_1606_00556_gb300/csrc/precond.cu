@@ -857,12 +857,6 @@ __device__ __forceinline__ T gs0_value(const Geom& g, const S* __restrict__ At, 
   return s / cv<T>(At[at_index(g, color, kDiag * 9, q)]);
 }
 
-template <typename T, typename S>
-__device__ __forceinline__ void gs0_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
-                                         T* __restrict__ x, int color, int zero_guess, int64_t q) {
-  x[(size_t)color * g.Nh + q] = gs0_value<T, S>(g, At, f, x, color, zero_guess, q);
-}
-
 // A level-0 half sweep over a grid-stride range, B cells per thread at a
 // time: the loads of all B cells are issued before any store (the stores go
 // to this colour's half of x, which no cell of the sweep reads), so a
@@ -884,13 +878,15 @@ __device__ __forceinline__ void sweep_batched(int64_t t0, int64_t nt, int64_t n,
   }
 }
 
-template <typename T, typename S>
+// (B cells per thread at a time, their loads issued before their stores:
+// a tile parameter of the per-kernel form that the batch autotuner sets)
+template <typename T, typename S, int B>
 __global__ void k_gs0(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x, int color,
                       int zero_guess, const DevState* st) {
   wait_prior_grid();
   if (st->done) return;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x)
-    gs0_cell<T, S>(g, At, f, x, color, zero_guess, q);
+  sweep_batched<B>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, g.Nh,
+                   x + (size_t)color * g.Nh, [&](int64_t q) { return gs0_value<T, S>(g, At, f, x, color, zero_guess, q); });
 }
 
 // First post-smoothing half sweep (black cells) with the coarse correction
@@ -917,20 +913,13 @@ __device__ __forceinline__ T gs0_prolong_value(const Geom& g, const S* __restric
   return s / cv<T>(At[at_index(g, 1, kDiag * 9, q)]);
 }
 
-template <typename T, typename S>
-__device__ __forceinline__ void gs0_prolong_cell(const Geom& g, const S* __restrict__ At, const T* __restrict__ f,
-                                                 T* __restrict__ x, const LevelDims& C, const T* __restrict__ xc,
-                                                 T sc, int64_t q) {
-  x[(size_t)g.Nh + q] = gs0_prolong_value<T, S>(g, At, f, x, C, xc, sc, q);
-}
-
-template <typename T, typename S>
+template <typename T, typename S, int B>
 __global__ void k_gs0_prolong(Geom g, const S* __restrict__ At, const T* __restrict__ f, T* __restrict__ x,
                               LevelDims C, const T* __restrict__ xc, T sc, const DevState* st) {
   wait_prior_grid();
   if (st->done) return;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.Nh; q += (int64_t)gridDim.x * blockDim.x)
-    gs0_prolong_cell<T, S>(g, At, f, x, C, xc, sc, q);
+  sweep_batched<B>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, g.Nh, x + g.Nh,
+                   [&](int64_t q) { return gs0_prolong_value<T, S>(g, At, f, x, C, xc, sc, q); });
 }
 
 // Sum of level-0 residuals over aggregate I (red cells only when the last
@@ -1706,7 +1695,23 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     (launch_pdl(k_dense0<T, S>, grid_for(g.N), kThreads, 0, s, g.N, (const S*)P->coarse_inv, f0, x0, st), note_launch());
     return;
   }
-  const int ghalf = grid_for(g.Nh);
+  // tile parameters of the per-kernel form (set by the batch autotuner):
+  // threads per block and level-0 cells per thread
+  const int TB = P->amg_threads;
+  const int CB = P->amg_cells;
+  const int ghalf = grid_for((g.Nh + CB - 1) / CB, TB);
+  auto gs0 = [&](int color, int zero) {
+    if (CB == 4) (launch_pdl(k_gs0<T, S, 4>, ghalf, TB, 0, s, g, At, f0, x0, color, zero, st), note_launch());
+    else if (CB == 2) (launch_pdl(k_gs0<T, S, 2>, ghalf, TB, 0, s, g, At, f0, x0, color, zero, st), note_launch());
+    else (launch_pdl(k_gs0<T, S, 1>, ghalf, TB, 0, s, g, At, f0, x0, color, zero, st), note_launch());
+  };
+  auto gs0_prolong = [&]() {
+    const LevelDims C1 = dims_of(P->lev[1]);
+    const T* xc = (const T*)P->lev[1].x;
+    if (CB == 4) (launch_pdl(k_gs0_prolong<T, S, 4>, ghalf, TB, 0, s, g, At, f0, x0, C1, xc, sc, st), note_launch());
+    else if (CB == 2) (launch_pdl(k_gs0_prolong<T, S, 2>, ghalf, TB, 0, s, g, At, f0, x0, C1, xc, sc, st), note_launch());
+    else (launch_pdl(k_gs0_prolong<T, S, 1>, ghalf, TB, 0, s, g, At, f0, x0, C1, xc, sc, st), note_launch());
+  };
   const int last = P->nlev - 1;
   // Launch forms (all compute the same V-cycle):
   //  mode 2: levels 0 and 1 in two cooperative launches (down leg, up leg,
@@ -1748,24 +1753,24 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   auto natural_down = [&]() {
     for (int l = 1; l < P->tail_from; ++l) {
       LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
-      const int gl = grid_for(L.d.n);
+      const int gl = grid_for(L.d.n, TB);
       for (int sw = 0; sw < nu1; ++sw) {
-        (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 0, sw == 0, st), note_launch());
-        (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 1, 0, st), note_launch());
+        (launch_pdl(k_gsn<T, S>, gl, TB, 0, s, L, 0, sw == 0, st), note_launch());
+        (launch_pdl(k_gsn<T, S>, gl, TB, 0, s, L, 1, 0, st), note_launch());
       }
-      if (nu1 == 0) (launch_pdl(k_zero<T>, gl, kThreads, 0, s, L.d.n, L.x, st), note_launch());
-      (launch_pdl(k_restrictn<T, S>, grid_for(C.d.n), kThreads, 0, s, L, C, nu1 > 0, st), note_launch());
+      if (nu1 == 0) (launch_pdl(k_zero<T>, gl, TB, 0, s, L.d.n, L.x, st), note_launch());
+      (launch_pdl(k_restrictn<T, S>, grid_for(C.d.n, TB), TB, 0, s, L, C, nu1 > 0, st), note_launch());
     }
   };
   auto natural_up = [&]() {
     for (int l = P->tail_from - 1; l >= 1; --l) {
       LevelView<T, S> L = view<T, S>(P, l), C = view<T, S>(P, l + 1);
-      const int gl = grid_for(L.d.n);
-      if (nu2 == 0) (launch_pdl(k_prolongn<T, S>, gl, kThreads, 0, s, L, C, sc, st), note_launch());
+      const int gl = grid_for(L.d.n, TB);
+      if (nu2 == 0) (launch_pdl(k_prolongn<T, S>, gl, TB, 0, s, L, C, sc, st), note_launch());
       for (int sw = 0; sw < nu2; ++sw) {
-        if (sw == 0) (launch_pdl(k_gsn_prolong<T, S>, gl, kThreads, 0, s, L, C, sc, st), note_launch());
-        else (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 1, 0, st), note_launch());
-        (launch_pdl(k_gsn<T, S>, gl, kThreads, 0, s, L, 0, 0, st), note_launch());
+        if (sw == 0) (launch_pdl(k_gsn_prolong<T, S>, gl, TB, 0, s, L, C, sc, st), note_launch());
+        else (launch_pdl(k_gsn<T, S>, gl, TB, 0, s, L, 1, 0, st), note_launch());
+        (launch_pdl(k_gsn<T, S>, gl, TB, 0, s, L, 0, 0, st), note_launch());
       }
     }
   };
@@ -1805,11 +1810,11 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
   }
   if (!down_done) {
     for (int sw = 0; sw < nu1; ++sw) {
-      (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 0, sw == 0, st), note_launch());
-      (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 1, 0, st), note_launch());
+      gs0(0, sw == 0);
+      gs0(1, 0);
     }
-    if (nu1 == 0) (launch_pdl(k_zero<T>, grid_for(g.N), kThreads, 0, s, g.N, x0, st), note_launch());
-    (launch_pdl(k_restrict0<T, S>, grid_for(P->lev[1].n), kThreads, 0, s, g, At, f0, x0, dims_of(P->lev[1]),
+    if (nu1 == 0) (launch_pdl(k_zero<T>, grid_for(g.N, TB), TB, 0, s, g.N, x0, st), note_launch());
+    (launch_pdl(k_restrict0<T, S>, grid_for(P->lev[1].n, TB), TB, 0, s, g, At, f0, x0, dims_of(P->lev[1]),
                                                                (T*)P->lev[1].f, nu1 > 0, st), note_launch());
     natural_down();
     tail();
@@ -1854,15 +1859,12 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     natural_up();
   }
   if (nu2 == 0)
-    (launch_pdl(k_prolong0<T>, grid_for(g.N), kThreads, 0, s, g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
+    (launch_pdl(k_prolong0<T>, grid_for(g.N, TB), TB, 0, s, g, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
      note_launch());
   for (int sw = 0; sw < nu2; ++sw) {
-    if (sw == 0)
-      (launch_pdl(k_gs0_prolong<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, dims_of(P->lev[1]), (const T*)P->lev[1].x, sc, st),
-       note_launch());
-    else
-      (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 1, 0, st), note_launch());
-    (launch_pdl(k_gs0<T, S>, ghalf, kThreads, 0, s, g, At, f0, x0, 0, 0, st), note_launch());
+    if (sw == 0) gs0_prolong();
+    else gs0(1, 0);
+    gs0(0, 0);
   }
 }
 

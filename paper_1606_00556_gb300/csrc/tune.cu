@@ -36,7 +36,9 @@ std::string tune_key(bo_prec* const* P, int nreal, const bo_solve_opts* o) {
   return k.str();
 }
 
-// the cache: one line per entry, "key": [launch_mode, streams, ms]
+// the cache: one line per entry, "key": [launch_mode, streams, ms, amg_cells,
+// amg_threads] (entries of three values, from before the tile search, keep
+// the default tile)
 std::map<std::string, std::vector<double>> read_cache(const char* path) {
   std::map<std::string, std::vector<double>> out;
   if (!path) return out;
@@ -49,7 +51,8 @@ std::map<std::string, std::vector<double>> read_cache(const char* path) {
     std::stringstream ss(line.substr(l + 1, r - l - 1));
     std::string tok;
     while (std::getline(ss, tok, ',')) v.push_back(std::atof(tok.c_str()));
-    if (v.size() == 3) out[line.substr(a + 1, b - a - 1)] = v;
+    if (v.size() == 3) v.insert(v.end(), {1.0, 256.0});
+    if (v.size() == 5) out[line.substr(a + 1, b - a - 1)] = v;
   }
   return out;
 }
@@ -64,15 +67,18 @@ bool write_cache(const char* path, const std::map<std::string, std::vector<doubl
     size_t i = 0;
     for (const auto& kv : c) {
       f << "  \"" << kv.first << "\": [" << (int)kv.second[0] << ", " << (int)kv.second[1] << ", " << kv.second[2]
-        << "]" << (++i < c.size() ? "," : "") << "\n";
+        << ", " << (int)kv.second[3] << ", " << (int)kv.second[4] << "]" << (++i < c.size() ? "," : "") << "\n";
     }
     f << "}\n";
   }
   return std::rename(tmp.c_str(), path) == 0;
 }
 
-void apply(bo_prec* const* P, int nreal, int mode, int streams) {
-  for (int r = 0; r < nreal; ++r) P[r]->launch_mode = mode;
+void apply(bo_prec* const* P, int nreal, int mode, int streams, int cells = 1, int threads = 256) {
+  for (int r = 0; r < nreal; ++r) {
+    P[r]->launch_mode = mode;
+    bo_prec_set_amg_tile(P[r], cells, threads);
+  }
   bo::g_pool_width.store(std::max(1, std::min(bo::kMaxPoolStreams, streams)));
 }
 
@@ -87,13 +93,16 @@ int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, do
   auto cache = read_cache(cache_path);
   auto it = cache.find(key);
   if (it != cache.end()) {
-    apply(P, nreal, (int)it->second[0], (int)it->second[1]);
+    const std::vector<double>& v = it->second;
+    apply(P, nreal, (int)v[0], (int)v[1], (int)v[3], (int)v[4]);
     if (out) {
       std::memset(out, 0, sizeof(*out));
-      out->launch_mode = (int)it->second[0];
-      out->streams = (int)it->second[1];
-      out->best_ms = it->second[2];
+      out->launch_mode = (int)v[0];
+      out->streams = (int)v[1];
+      out->best_ms = v[2];
       out->from_cache = 1;
+      out->amg_cells = (int)v[3];
+      out->amg_threads = (int)v[4];
     }
     return BO_OK;
   }
@@ -123,8 +132,31 @@ int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, do
         best_w = widths[wi];
       }
     }
-  apply(P, nreal, best_mode, best_w);
-  cache[key] = {(double)best_mode, (double)best_w, best};
+  // the tile of the per-kernel AMG form, which the graph forms run: level-0
+  // cells per thread and threads per block, tried with the best form and
+  // width (the default, 1 cell and 256 threads, was timed above)
+  const int tiles[5][2] = {{2, 256}, {4, 256}, {1, 128}, {2, 128}, {1, 512}};
+  double tms[5] = {0, 0, 0, 0, 0};
+  int best_cells = 1, best_threads = 256;
+  if (best_mode != BO_LAUNCH_STREAM) {
+    for (int ti = 0; ti < 5; ++ti) {
+      apply(P, nreal, best_mode, best_w, tiles[ti][0], tiles[ti][1]);
+      for (int pass = 0; pass < 2; ++pass) {
+        const auto t0 = std::chrono::steady_clock::now();
+        const int rc = bo_solve_batched(P, nreal, b, x, &o, nullptr);
+        const double t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (rc != BO_OK && rc != BO_ERR_NOT_CONVERGED) return rc;
+        if (pass == 1) tms[ti] = t;
+      }
+      if (tms[ti] < best) {
+        best = tms[ti];
+        best_cells = tiles[ti][0];
+        best_threads = tiles[ti][1];
+      }
+    }
+  }
+  apply(P, nreal, best_mode, best_w, best_cells, best_threads);
+  cache[key] = {(double)best_mode, (double)best_w, best, (double)best_cells, (double)best_threads};
   const bool wrote = write_cache(cache_path, cache);
   if (out) {
     std::memset(out, 0, sizeof(*out));
@@ -133,6 +165,9 @@ int bo_autotune_batched(bo_prec* const* P, int nreal, const double* const* b, do
     out->best_ms = best;
     out->from_cache = 0;
     for (int i = 0; i < 9; ++i) out->trial_ms[i] = ms[i];
+    out->amg_cells = best_cells;
+    out->amg_threads = best_threads;
+    for (int i = 0; i < 5; ++i) out->tile_ms[i] = tms[i];
   }
   return wrote ? BO_OK : BO_ERR_ARG;
 }

@@ -119,6 +119,7 @@ def test_every_entry_point_rejects_missing_handles(libpath):
         "bo_prec_spmv_decoupled": (N, N, N),
         "bo_prec_amg_levels": (N, N, 0),
         "bo_prec_set_launch_mode": (N, 0),
+        "bo_prec_set_amg_tile": (N, 1, 256),
         "bo_prec_set_coarse_space": (N, N, 1, 1, 1),
         "bo_learned_coarse_space": (N, N, ctypes.c_double(1.0), 1, 1, 1),
         "bo_prec_residual_history": (N, N, 0),

@@ -135,9 +135,15 @@ def test_autotuner_picks_and_caches(tmp_path):
     r1 = bo.bo_autotune_batched(precs, bs, xs, cache_path=path)
     assert not r1["from_cache"] and r1["launch_mode"] in (0, 1, 2) and r1["streams"] in (4, 8, 16)
     assert len(r1["trial_ms"]) == 9
-    assert all(t > 0 for t in r1["trial_ms"]) and r1["best_ms"] == min(r1["trial_ms"])
+    assert all(t > 0 for t in r1["trial_ms"])
+    assert (r1["amg_cells"], r1["amg_threads"]) in ((1, 256), (2, 256), (4, 256), (1, 128), (2, 128), (1, 512))
+    tiles = [t for t in r1["tile_ms"] if t > 0]
+    assert len(tiles) == (5 if r1["launch_mode"] != bo.BO_LAUNCH_STREAM else 0)
+    assert r1["best_ms"] == min(r1["trial_ms"] + tiles)
     r2 = bo.bo_autotune_batched(precs, bs, xs, cache_path=path)
-    assert r2["from_cache"] and (r2["launch_mode"], r2["streams"]) == (r1["launch_mode"], r1["streams"])
+    assert r2["from_cache"]
+    for k in ("launch_mode", "streams", "amg_cells", "amg_threads"):
+        assert r2[k] == r1[k]
     import json
     with open(path) as f:
         assert len(json.load(f)) == 1
@@ -178,3 +184,29 @@ def test_batched_update_equals_individual_updates():
     with pytest.raises(bo.BoError) as e:
         bo.bo_update_batched(precs, bad)
     assert e.value.status == bo.BO_ERR_NONFINITE
+
+
+def test_amg_tile_shapes_give_identical_solves():
+    # the per-kernel AMG form (the one captured graphs run) under every tile
+    # shape: each cell's arithmetic is the same, only its thread changes
+    import paper_1606_00556_gb300 as bo
+    ctx = bo.Context(0)
+    mats, precs, bs, sys = _ensemble(bo, ctx, 1, SPECS[4:6])
+    ref = None
+    for cells, threads in ((1, 256), (2, 256), (4, 256), (1, 128), (2, 128), (1, 512), (4, 512)):
+        out = []
+        for P, b in zip(precs, bs):
+            P.set_launch_mode(bo.BO_LAUNCH_GRAPH)
+            P.set_amg_tile(cells, threads)
+            x = torch.zeros_like(b)
+            info = P.solve(b, x, tol=1e-8)
+            assert info["status"] == 0
+            out.append((x, info["iters"]))
+        if ref is None:
+            ref = out
+        for (x, it), (xr, itr) in zip(out, ref):
+            assert it == itr and torch.equal(x, xr)
+    with pytest.raises(bo.BoError):
+        precs[0].set_amg_tile(3, 256)
+    with pytest.raises(bo.BoError):
+        precs[0].set_amg_tile(1, 64)
