@@ -11,7 +11,8 @@
 // Orthogonalisation: classical Gram-Schmidt applied twice (CGS2) for every
 // column: a multi-dot pass h1 = V^T w, an update pass w -= V h1, then the
 // same again, the second update also reducing ||w||^2 and applying the
-// Givens step.  A second pass is necessary here: with a strong CPR
+// Givens step; the first update and the second multi-dot share one pass over
+// the basis, so a column takes three passes.  A second pass is necessary here: with a strong CPR
 // preconditioner A M^{-1} is close to the identity, so the new direction
 // cancels to 1e-6 of ||w|| and one classical pass alone loses all
 // orthogonality.  The basis vectors are stored unnormalised with their
