@@ -226,13 +226,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv3d_tc(const __grid_consta
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t hb = hbase + bf * kHaloBuf;
         const uint32_t dacc = tmem + (uint32_t)(a * 32);
+        // The 54 descriptors differ from the buffer's first ones only in
+        // their start-address field (address / 16 in the low 14 bits), by
+        // offsets that are compile-time constants once the loops are
+        // unrolled: one add per MMA instead of building each descriptor
+        // (the single issuing thread otherwise spent most of a tile on it).
+        const uint64_t da0 = smem_desc(hb, kChunkStride, kHX * 16);
+        const uint64_t db0 = smem_desc(wbase, 512, 128);
+#pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
           const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
           const uint32_t rowoff = ((1 + dz) * kHY + (1 + dy)) * kHX + (1 + dx);
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t da = smem_desc(hb + 2 * ks * kChunkStride + rowoff * 16, kChunkStride, kHX * 16);
-            const uint64_t db = smem_desc(wbase + tap * 2048 + 2 * ks * 512, 512, 128);
+            const uint64_t da = da0 + (uint64_t)((2 * ks * kChunkStride + rowoff * 16) >> 4);
+            const uint64_t db = db0 + (uint64_t)((tap * 2048 + 2 * ks * 512) >> 4);
             const uint32_t acc = (tap | ks) ? 1u : 0u;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
