@@ -75,6 +75,19 @@ constexpr int kDotBlocks = 4 * 152;  // most chunks of a coefficient pass (parti
 __host__ __device__ __forceinline__ int64_t split_pad(int64_t n) { return (n + 3) & ~(int64_t)3; }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// 16-byte loads with L1 eviction priorities: the fused Gram-Schmidt pass
+// reads each column twice per thread, and asks L1 to keep the first read
+// (evict_last) and to drop the second (evict_first)
+__device__ __forceinline__ float4 ld4_keep(const float* p) {
+  float4 v;
+  asm volatile("ld.global.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld4_last(const float* p) {
+  float4 v;
+  asm volatile("ld.global.L1::evict_first.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float lane4(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
 // v with the lanes at or beyond `valid` (0..4) set to zero
@@ -441,8 +454,8 @@ __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int k = k0 + b < nv ? k0 + b : nv - 1;  // past the last column: a repeat, not used
-        ah[b] = ld4(a + (size_t)k * ldv);
-        al[b] = ld4(a + (size_t)k * ldv + np);
+        ah[b] = ld4_keep(a + (size_t)k * ldv);
+        al[b] = ld4_keep(a + (size_t)k * ldv + np);
       }
 #pragma unroll
       for (int b = 0; b < B; ++b) {
@@ -478,8 +491,8 @@ __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __
 #pragma unroll
         for (int b = 0; b < B; ++b) {
           const int k = k0 + b < nv ? k0 + b : nv - 1;
-          ah[b] = ld4(a + (size_t)k * ldv);
-          al[b] = ld4(a + (size_t)k * ldv + np);
+          ah[b] = ld4_last(a + (size_t)k * ldv);
+          al[b] = ld4_last(a + (size_t)k * ldv + np);
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
