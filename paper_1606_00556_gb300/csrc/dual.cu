@@ -478,7 +478,7 @@ int bo_dp_solve_batched(bo_dp* const* dps, bo_prec* const* P, int nreal, const d
     (bo::launch_pdl(bo::k_dp_recover, bo::grid_for(d->N), bo::kThreads, 0, s, d->N, d->val, d->mmap, d->minv, b[r], x[r]),
      bo::note_launch());
     (bo::launch_pdl(bo::k_dp_residual, bo::grid_for(2 * d->N), bo::kThreads, 0, s, 2 * d->N, d->rowptr, d->col, d->val, b[r],
-                                                                         x[r], d->r),
+        x[r], d->r),
      bo::note_launch());
     bo::sq_norm(d->r, 6 * d->N, d->part, d->norms + 2, s);
     cudaMemcpyAsync(d->h_norms + 2, d->norms + 2, sizeof(double), cudaMemcpyDeviceToHost, s);

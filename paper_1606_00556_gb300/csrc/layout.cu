@@ -427,7 +427,7 @@ __global__ void k_axpy1(double* __restrict__ s, const double* __restrict__ d, in
 int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s) {
   cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
   (launch_pdl(k_ingest_bsr, grid_for(m->g.N), kThreads, 0, s, m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
-                                                      m->a2_range), note_launch());
+      m->a2_range), note_launch());
   m->a2_valid = true;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
@@ -435,7 +435,7 @@ int ingest_bsr(bo_mat* m, const double* dval, cudaStream_t s) {
 int ingest_csr(bo_mat* m, const double* dval, cudaStream_t s) {
   cudaMemsetAsync(m->a2_range, 0, sizeof(int), s);
   (launch_pdl(k_ingest_csr, grid_for(m->g.N), kThreads, 0, s, m->g, m->rowptr, m->col, dval, m->nnz, m->A, m->A2, m->flags,
-                                                      m->a2_range), note_launch());
+      m->a2_range), note_launch());
   m->a2_valid = true;
   return cudaGetLastError() == cudaSuccess ? BO_OK : BO_ERR_CUDA;
 }
@@ -458,7 +458,7 @@ void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta
     const int Q = g.hx % 2 == 0 ? 2 : 1;
     if (Q == 2)
       (launch_pdl(k_spmv_tiled<float, 2>, grid_for((g.Nh + 1) / 2), kThreads, 0, s, g, m->A32, x, y, alpha, beta, nullptr,
-                                                                              nullptr),
+          nullptr),
        note_launch());
     else
       (launch_pdl(k_spmv_tiled<float, 1>, grid_for(g.Nh), kThreads, 0, s, g, m->A32, x, y, alpha, beta, nullptr, nullptr),
@@ -466,11 +466,11 @@ void launch_spmv_nat(const bo_mat* m, double alpha, const double* x, double beta
   } else if (precision == BO_PREC_BF16) {
     if (g.hx % 2 == 0)
       (launch_pdl(k_spmv_tiled<__nv_bfloat16, 2>, grid_for((g.Nh + 1) / 2), kThreads, 0, s, g, m->A16, x, y, alpha, beta,
-                                                                                      nullptr, nullptr),
+          nullptr, nullptr),
        note_launch());
     else
       (launch_pdl(k_spmv_tiled<__nv_bfloat16, 1>, grid_for(g.Nh), kThreads, 0, s, g, m->A16, x, y, alpha, beta, nullptr,
-                                                                             nullptr),
+          nullptr),
        note_launch());
   } else {
     bo_mat* mm = const_cast<bo_mat*>(m);

@@ -490,7 +490,7 @@ int model_assemble(bo_model* M, const double* x, const double* xn, double dt) {
   cudaMemsetAsync(M->err, 0, sizeof(int), s);
   const int gc = grid_for(g.N);
   (launch_pdl(k_cell_props, gc, kThreads, 0, s, g, M->fluid, gr.dx, gr.dy, gr.dz, M->phi0, M->depth, x, xn, dt,
-                                        M->cperf_ptr, M->cperf, M->props, M->racc, M->dacc, M->err),
+      M->cperf_ptr, M->cperf, M->props, M->racc, M->dacc, M->err),
    note_launch());
   (launch_pdl(k_faces, gc, kThreads, 0, s, g, 0, gr.dy * gr.dz, gr.dx, M->kx, M->depth, x, M->props, M->face), note_launch());
   (launch_pdl(k_faces, gc, kThreads, 0, s, g, 1, gr.dx * gr.dz, gr.dy, M->ky, M->depth, x, M->props, M->face), note_launch());

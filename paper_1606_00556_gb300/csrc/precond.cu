@@ -1815,7 +1815,7 @@ void amg_vcycle(bo_prec* P, const DevState* st) {
     }
     if (nu1 == 0) (launch_pdl(k_zero<T>, grid_for(g.N, TB), TB, 0, s, g.N, x0, st), note_launch());
     (launch_pdl(k_restrict0<T, S>, grid_for(P->lev[1].n, TB), TB, 0, s, g, At, f0, x0, dims_of(P->lev[1]),
-                                                               (T*)P->lev[1].f, nu1 > 0, st), note_launch());
+        (T*)P->lev[1].f, nu1 > 0, st), note_launch());
     natural_down();
     tail();
   } else if (cs > 0) {
@@ -1892,18 +1892,18 @@ void cpr_apply(bo_prec* P, InV v, OutV zo, int stage, const DevState* st, const 
   // x1 = R^{-1} f with f = D_QI^{-1} v (stage CPR) or f = v
   if (stage == BO_STAGE_CPR)
     (launch_pdl(k_cpr_entry<T, S, true>, occ_grid((const void*)k_cpr_entry<T, S, true>, g.N), kThreads, 0, s, g, v, vs, P->w, P->wf,
-                                                                                                  D, f, tv, st),
+        D, f, tv, st),
      note_launch());
   else
     (launch_pdl(k_cpr_entry<T, S, false>, occ_grid((const void*)k_cpr_entry<T, S, false>, g.N), kThreads, 0, s, g, v, vs, P->w, P->wf,
-                                                                                                    D, f, tv, st),
+        D, f, tv, st),
      note_launch());
   (launch_pdl(k_ilu_b<T, S, false>, occ_grid((const void*)k_ilu_b<T, S, false>, g.Nh), kThreads, 0, s, g, At, D, f, tv, z1, nullptr,
-                                                                                          OutV{}, st),
+      OutV{}, st),
    note_launch());
   // (ub and z are both z1: the pass reads its black half and writes its red half)
   (launch_pdl(k_ilu_r2<T, S, false>, occ_grid((const void*)k_ilu_r2<T, S, false>, g.Nh), kThreads, 0, s, g, At, D, tv, z1, z1,
-                                                                                            nullptr, OutV{}, st),
+      nullptr, OutV{}, st),
    note_launch());
   if (stage == BO_STAGE_ILU) {
     (launch_pdl(k_widen_t<T>, grid_for(3 * g.N), kThreads, 0, s, 3 * g.N, z1, zo.d, st), note_launch());
@@ -1917,13 +1917,13 @@ void cpr_apply(bo_prec* P, InV v, OutV zo, int stage, const DevState* st, const 
   learned_coarse_apply(P, st);
   // r = f - At x2 (with the red pass of R^{-1} r fused);  x3 = x2 + R^{-1} r
   (launch_pdl(k_cpr_residual<T, S, 3>, occ_grid((const void*)k_cpr_residual<T, S, 3>, g.N), kThreads, 0, s, g, At, f, z1, e0, r,
-                                                                                                D, tv, st),
+      D, tv, st),
    note_launch());
   (launch_pdl(k_ilu_b<T, S, true>, occ_grid((const void*)k_ilu_b<T, S, true>, g.Nh), kThreads, 0, s, g, At, D, r, tv, z1, e0, zo,
-                                                                                        st),
+      st),
    note_launch());
   (launch_pdl(k_ilu_r2<T, S, true>, occ_grid((const void*)k_ilu_r2<T, S, true>, g.Nh), kThreads, 0, s, g, At, D, tv, tv, z1, e0,
-                                                                                          zo, st),
+      zo, st),
    note_launch());
 }
 
@@ -1934,7 +1934,7 @@ int values_impl(bo_prec* P) {
   const Geom& g = m->g;
   const int gN = grid_for(g.N), gh = grid_for(g.Nh);
   (launch_pdl(k_decouple<S>, gN, kThreads, 0, s, g, m->A, m->a2_valid ? m->A2 : nullptr, m->a2_range, (S*)P->At, P->w, P->wf,
-                                         P->opts.decoupling == BO_DECOUPLE_ABF, P->st), note_launch());
+      P->opts.decoupling == BO_DECOUPLE_ABF, P->st), note_launch());
   // FP64 red inverses for the black pass: the Krylov basis is idle during setup
   double* red64 = P->V;
   if (sizeof(S) < sizeof(double) && m->a2_valid) {
@@ -1942,7 +1942,7 @@ int values_impl(bo_prec* P) {
     // itself where the split copy of A could not hold every value)
     (launch_pdl(k_ilu_red<S, true>, gh, kThreads, 0, s, g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
     (launch_pdl(k_ilu_black_split<S>, gh, kThreads, 0, s, g, m->A2, m->A, m->a2_range, P->w,
-                                                 reinterpret_cast<const float2*>(red64), (S*)P->Dinv, P->st),
+        reinterpret_cast<const float2*>(red64), (S*)P->Dinv, P->st),
      note_launch());
   } else {
     (launch_pdl(k_ilu_red<S, false>, gh, kThreads, 0, s, g, m->A, P->w, (S*)P->Dinv, red64, P->st), note_launch());
@@ -1955,13 +1955,13 @@ int values_impl(bo_prec* P) {
       (launch_pdl(k_galerkin0, grid_for(C.n), kThreads, 0, s, g, m->A, P->w, dims_of(C), C.c64, P->st), note_launch());
     else
       (launch_pdl(k_galerkinn, grid_for(C.n), kThreads, 0, s, dims_of(P->lev[l - 1]), P->lev[l - 1].c64, dims_of(C), C.c64,
-                                                     P->st), note_launch());
+          P->st), note_launch());
     (launch_pdl(k_convert<S>, grid_for(7 * C.n), kThreads, 0, s, C.c64, (S*)C.c, (size_t)7 * C.n), note_launch());
   }
   const int last = P->nlev - 1;
   LevelDims cd = last == 0 ? LevelDims{g.nx, g.ny, g.nz, g.N} : dims_of(P->lev[last]);
   (launch_pdl(k_dense_from_level, 1, kThreads, 0, s, cd, last == 0 ? nullptr : P->lev[last].c64, g, m->A, P->w, last == 0,
-                                            P->coarse64), note_launch());
+      P->coarse64), note_launch());
   const int n = (int)P->ncoarse;
   const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
   cudaFuncSetAttribute(k_gj_inverse<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

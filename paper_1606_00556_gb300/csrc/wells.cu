@@ -388,7 +388,7 @@ void wells_after_product(bo_prec* P, float* w, int64_t np) {
   bo_wells* wl = P->wl;
   if (wl->P == 0) return;
   (launch_pdl(k_wl_product, 1, kThreads, 0, P->stream, wl->P, wl->W, wl->perf_t, wl->perf_well, P->mat->g.N, wl->apw, wl->t,
-                                               w, np, P->st),
+      w, np, P->st),
    note_launch());
 }
 
@@ -565,7 +565,7 @@ int bo_wells_spmv(bo_wells* w, double alpha, const double* x, double beta, doubl
   if (cudaSetDevice(m->ctx->device) != cudaSuccess) return BO_ERR_CUDA;
   launch_spmv_nat(m, alpha, x, beta, y, BO_PREC_FP64);
   (launch_pdl(k_wl_border_product, 1, kThreads, 0, m->ctx->stream, w->W, w->wstart, w->perf_cell, m->g.N, w->apw, w->awp,
-                                                            w->aww, alpha, x, beta, y),
+      w->aww, alpha, x, beta, y),
    note_launch());
   return status_of(cudaStreamSynchronize(m->ctx->stream));
 }
@@ -594,7 +594,7 @@ int bo_solve_bordered(bo_prec* P, bo_wells* w, const double* b, double* x, const
     cudaMemcpyAsync(w->rfull, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, s);
     launch_spmv_nat(m, -1.0, x, 1.0, w->rfull, BO_PREC_FP64);
     (launch_pdl(k_wl_border_product, 1, kThreads, 0, s, w->W, w->wstart, w->perf_cell, N, w->apw, w->awp, w->aww, -1.0, x,
-                                                1.0, w->rfull),
+        1.0, w->rfull),
      note_launch());
     rb = w->rfull;
     d = w->dx;
