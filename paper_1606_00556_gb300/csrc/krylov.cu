@@ -426,6 +426,9 @@ __global__ void __launch_bounds__(kThreads) k_gs_dots(int64_t n, const float* __
 // the block in shared memory (fixed order), one partial per column and
 // block, and the block that finishes last reduces each column's partials.
 // Grid: as many blocks as the partials hold for the bucket's columns.
+// This form serves up to 16 and more than 32 columns; from 17 to 32,
+// k_gs_pass_reg below holds each entry's columns in registers and reads the
+// basis once (launch_gs_pass gives the measurements behind the split).
 constexpr int kGsBatch = 4;
 
 template <int NVMAX>
@@ -531,20 +534,117 @@ __global__ void __launch_bounds__(kThreads) k_gs_pass(int64_t n, const float* __
   if (threadIdx.x == 0) st->counter[0] = 0;
 }
 
-// launch of k_gs_pass with the column bucket for nv columns
+// The same fused pass with each thread's columns held in registers: a
+// thread takes one entry at a time, loads that entry of every column
+// (high and low planes, all 2 nv loads issued before any arithmetic),
+// forms w1, and sums its products with the same registers, so the basis is
+// read once and nothing is re-read from cache.  NVMAX is the column count
+// rounded up to a multiple of four (loads past the last column repeat it
+// and go unused); the registers this takes (two per column for the entries
+// and two for the sums) limit it to NVMAX <= 32.  Blocks of kGsRegThreads
+// threads, at most 127 registers a thread up to 24 columns (four blocks per
+// SM) and 168 above (three).
+constexpr int kGsRegThreads = 128;
+
+// a coefficient read from shared memory where it is used: a volatile load
+// is not hoisted out of the loop over entries, which would hold every
+// coefficient in two registers for the whole kernel (p 8-byte aligned)
+__device__ __forceinline__ df ld_shared_df(const df* p) {
+  df v;
+  asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(v.hi), "=f"(v.lo) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+
+template <int NVMAX>
+__global__ void __launch_bounds__(kGsRegThreads, NVMAX <= 24 ? 4 : 3)
+    k_gs_pass_reg(int64_t n, const float* __restrict__ V, int64_t ldv, float* __restrict__ w, double* partials,
+                  DevState* st, int nv) {
+  wait_prior_grid();
+  __shared__ __align__(8) df c[NVMAX];  // 8-byte aligned for ld_shared_df
+  __shared__ double wacc[kGsRegThreads / 32][NVMAX];
+  if (st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t np = split_pad(n);
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) c[k] = df_neg(df_from(st->h[k] * st->vscale[k]));
+  __syncthreads();
+  df acc[NVMAX];
+#pragma unroll
+  for (int u = 0; u < NVMAX; ++u) acc[u] = df{0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float vh[NVMAX], vl[NVMAX];
+    // one pointer stepped from column to column (past the last column it
+    // stays there: a repeat, not used), rather than a 64-bit offset per
+    // column that the compiler would keep in registers across entries
+    const float* a = V + i;
+#pragma unroll
+    for (int k = 0; k < NVMAX; ++k) {
+      vh[k] = a[0];
+      vl[k] = a[np];
+      if (k + 1 < nv) a += ldv;
+    }
+    df s{w[i], w[np + i]};
+#pragma unroll
+    for (int k = 0; k < NVMAX; ++k)
+      if (k < nv) s = df_fma_acc(s, ld_shared_df(&c[k]), df{vh[k], vl[k]});
+    s = df_renorm(s);
+    w[i] = s.hi;
+    w[np + i] = s.lo;
+#pragma unroll
+    for (int u = 0; u < NVMAX; ++u)
+      if (u < nv) acc[u] = df_fma_acc(acc[u], df{vh[u], vl[u]}, s);
+  }
+#pragma unroll
+  for (int u = 0; u < NVMAX; ++u) {
+    if (u < nv) {
+      const double p = warp_sum(df_to_double(df_renorm(acc[u])));
+      if (lane == 0) wacc[warp][u] = p;
+    }
+  }
+  __syncthreads();
+  const int nblk = gridDim.x;
+  for (int u = threadIdx.x; u < nv; u += blockDim.x) {
+    double t = 0.0;
+    for (int r = 0; r < kGsRegThreads / 32; ++r) t += wacc[r][u];
+    partials[(size_t)u * nblk + blockIdx.x] = t;
+  }
+  if (!last_block(&st->counter[0], nblk)) return;
+  for (int r = warp; r < nv; r += kGsRegThreads / 32) {
+    double t = 0.0;
+    for (int b = lane; b < nblk; b += 32) t += __ldcg(partials + (size_t)r * nblk + b);
+    t = warp_sum(t);
+    if (lane == 0) st->h[kMaxM + r] = t * st->vscale[r];
+  }
+  if (threadIdx.x == 0) st->counter[0] = 0;
+}
+
+// launch of the fused pass for nv columns.  The register form serves 17 to
+// 32 columns (its bucket rounded up to a multiple of four); up to 16 the
+// cached form with four entries per thread is faster (measured at 3.1M
+// entries: 322 and 755 us for the columns 1-8 and 9-16 of a 20-iteration
+// solve, against 359 and 821 us in registers, whose single dependent chain
+// per entry leaves the loads idle), and from 17 on the registers are
+// (140 us against 157 us a launch at 17-20 columns, where the cached
+// re-reads fall out of L1).  Past 32 columns the registers run out.
 void launch_gs_pass(int64_t n, const float* V, int64_t ldv, float* w, double* partials, DevState* st, int nv,
                     cudaStream_t s) {
   const int64_t ng = (n + 3) >> 2;
   // the partials hold (kMaxM + 2) kDotBlocks values: as many blocks per
   // column as fit for the bucket's column count
-  auto go = [&](const void* k, auto kern, int nvmax) {
+  auto cached = [&](const void* k, auto kern, int nvmax) {
     const int g = std::min(occ_grid(k, ng), (kMaxM + 2) * kDotBlocks / nvmax);
     (launch_pdl(kern, g, kThreads, 0, s, n, V, ldv, w, partials, st, nv), note_launch());
   };
-  if (nv <= 8) go((const void*)k_gs_pass<8>, k_gs_pass<8>, 8);
-  else if (nv <= 16) go((const void*)k_gs_pass<16>, k_gs_pass<16>, 16);
-  else if (nv <= 32) go((const void*)k_gs_pass<32>, k_gs_pass<32>, 32);
-  else go((const void*)k_gs_pass<kMaxM + 1>, k_gs_pass<kMaxM + 1>, kMaxM + 1);
+  auto reg = [&](const void* k, auto kern, int nvmax) {
+    const int g = std::min(occ_grid(k, n, kGsRegThreads), (kMaxM + 2) * kDotBlocks / nvmax);
+    (launch_pdl(kern, g, kGsRegThreads, 0, s, n, V, ldv, w, partials, st, nv), note_launch());
+  };
+  if (nv <= 8) cached((const void*)k_gs_pass<8>, k_gs_pass<8>, 8);
+  else if (nv <= 16) cached((const void*)k_gs_pass<16>, k_gs_pass<16>, 16);
+  else if (nv <= 20) reg((const void*)k_gs_pass_reg<20>, k_gs_pass_reg<20>, 20);
+  else if (nv <= 24) reg((const void*)k_gs_pass_reg<24>, k_gs_pass_reg<24>, 24);
+  else if (nv <= 28) reg((const void*)k_gs_pass_reg<28>, k_gs_pass_reg<28>, 28);
+  else if (nv <= 32) reg((const void*)k_gs_pass_reg<32>, k_gs_pass_reg<32>, 32);
+  else cached((const void*)k_gs_pass<kMaxM + 1>, k_gs_pass<kMaxM + 1>, kMaxM + 1);
 }
 
 // Gram-Schmidt update pass: w -= sum_u h[off + u] vscale[u] V_u in split
@@ -701,8 +801,9 @@ __global__ void k_trisolve(DevState* st, const double* H, const double* gv, doub
 }
 
 // sum_{k < nv} c_k V_k[i] in split arithmetic (nv <= NU), in batches of B
-// columns: each batch is unrolled with the bound as a predicate, so its 2 B
-// loads are in flight at once
+// columns: each batch's 2 B loads are unconditional (past the last column
+// they repeat it, unused), so all of them are in flight at once; only the
+// arithmetic carries the bound
 template <int NU, int B = NU>
 __device__ __forceinline__ df lincomb(const df* c, const float* __restrict__ V, int64_t ldv, int64_t n, int64_t i,
                                       int nv) {
@@ -710,12 +811,16 @@ __device__ __forceinline__ df lincomb(const df* c, const float* __restrict__ V, 
 #pragma unroll 1
   for (int k0 = 0; k0 < NU; k0 += B) {
     if (k0 >= nv) break;
+    float vh[B], vl[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const float* a = V + (size_t)(k0 + k < nv ? k0 + k : nv - 1) * ldv;
+      vh[k] = a[i];
+      vl[k] = a[n + i];
+    }
 #pragma unroll
     for (int k = 0; k < B; ++k)
-      if (k0 + k < nv) {
-        const float* a = V + (size_t)(k0 + k) * ldv;
-        s = df_fma_acc(s, c[k0 + k], df{a[i], a[n + i]});
-      }
+      if (k0 + k < nv) s = df_fma_acc(s, c[k0 + k], df{vh[k], vl[k]});
   }
   return df_norm(s);
 }
